@@ -1,0 +1,306 @@
+"""Benchmark: FMM evaluation points/s at eps = 1e-6 for the three tilings.
+
+Workload (one step): for each tiling (quadtree, septree, triangle quadtree)
+one full FMM - fmm2d_build (keys, sort, cells, lists) + fmm2d_evaluate
+(P2M, M2M, M2L, L2L, L2P, P2P) - over N = M = 2^20 seeded points uniform in
+the unit square (sources = targets), FP32 points and strengths uniform in
+[-1, 1], p and L from the planner for eps = 1e-6, mixed precision.
+value = 3 * M / (device time of one step), all ranks summed.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+build) on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_POINTS = 2 ** 20
+EPS = 1e-6
+TILINGS = ("quad", "sept", "tri")
+SEED = 2
+MUFU_PER_CLK_SM = 16      # lg2 results per clock per SM (MUFU pipe)
+FP32_LANES_SM = 128       # FP32 FMA lanes per SM
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """Sample SM clocks and throttle reasons with nvidia-smi while running."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if len(r) > 3 + i and r[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def oracle_sample(tilings=TILINGS, n=16384, seed=SEED):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
+    N = M = n uniform points per tiling, the planner's L and p for eps."""
+    from oracle.fmm import fmm, make_tiling
+    from oracle.params import auto_levels, p_from_eps
+    from paper_1204_3105_gb300.inputs import uniform_square
+    xy, u = uniform_square(n, seed=seed, dtype=np.float32)
+    xy = xy.astype(np.float64)
+    u = u.astype(np.float64)
+    t0 = time.perf_counter()
+    for t in tilings:
+        T = make_tiling(t, auto_levels(t, n))
+        fmm(T, xy, u, xy, p_from_eps(t, EPS))
+    dt = time.perf_counter() - t0
+    return len(tilings) * n / dt, dt
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+        return dist, rank, ws
+    return None, rank, ws
+
+
+def run_reference(args):
+    dist, rank, ws = dist_setup(args)
+    if rank != 0:
+        return
+    n = args.ref_points
+    for _ in range(args.warmup):
+        oracle_sample(n=max(1024, n // 8))
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_sample(n=n)
+        times.append(dt)
+    ms = 1e3 * statistics.mean(times)
+    value = len(TILINGS) * n / (ms / 1e3)
+    line = {"impl": "reference", "metric": "FMM eval points/s at eps=1e-6 (3 tilings)",
+            "value": value, "unit": "points/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "N=M=%d uniform unit square, quad+sept+tri, eps=1e-6 (oracle sample)" % n},
+            "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle",
+                             "sample": "N=M=%d per tiling, 3 tilings, one evaluation per step" % n},
+            "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    from paper_1204_3105_gb300 import fmm2d
+    from paper_1204_3105_gb300.inputs import uniform_square
+
+    dist, rank, ws = dist_setup(args)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    fmm2d.lib()
+
+    xy, u = uniform_square(N_POINTS, seed=SEED, dtype=np.float32)
+    xy_d = torch.from_numpy(xy).to(dev)
+    u_d = torch.from_numpy(u).to(dev)
+    outs = {t: torch.empty(N_POINTS, dtype=torch.float64, device=dev) for t in args.tilings}
+    prec = {"mixed": fmm2d.PREC_MIXED, "fp64": fmm2d.PREC_FP64}[args.prec]
+    plans = {t: fmm2d.Plan(t, 0, 0, EPS, prec | fmm2d.IN_F32) for t in args.tilings}
+    flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def step(per):
+        for t in args.tilings:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plans[t].build(xy_d, N_POINTS, xy_d, N_POINTS, stream)
+            plans[t].evaluate(u_d, outs[t], stream)
+            e1.record(stream)
+            per[t].append((e0, e1))
+            flush.zero_()
+
+    warm = {t: [] for t in args.tilings}
+    for _ in range(args.warmup):
+        step(warm)
+    torch.cuda.synchronize()
+    for t in args.tilings:
+        plans[t].set_profiling(True)
+    per = {t: [] for t in args.tilings}
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            step(per)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    tt = {t: [a.elapsed_time(b) for a, b in per[t]] for t in args.tilings}
+    stage = {t: plans[t].stage_times() for t in args.tilings}
+    info = {t: plans[t].query() for t in args.tilings}
+    ms_step = sum(statistics.mean(tt[t]) for t in args.tilings)
+    if dist:
+        tm = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ms_step = float(tm.item())
+    value = ws * len(args.tilings) * N_POINTS / (ms_step / 1e3)
+
+    # e2e: host buffers, copies inside the timed region, through the same ABI
+    xy_h = torch.from_numpy(xy).pin_memory()
+    u_h = torch.from_numpy(u).pin_memory()
+    res_h = {t: torch.empty(N_POINTS, dtype=torch.float64).pin_memory() for t in args.tilings}
+    e2e = []
+    for it in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xd = xy_h.to(dev, non_blocking=True)
+        ud = u_h.to(dev, non_blocking=True)
+        for t in args.tilings:
+            plans[t].build(xd, N_POINTS, xd, N_POINTS, stream)
+            plans[t].evaluate(ud, outs[t], stream)
+            res_h[t].copy_(outs[t], non_blocking=True)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            e2e.append(time.perf_counter() - t0)
+    e2e_v = ws * len(args.tilings) * N_POINTS / statistics.mean(e2e)
+
+    # roofline of the dominant kernel
+    peaks, src = _peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    tot = {}
+    for t in args.tilings:
+        for k, (ms, n) in stage[t].items():
+            tot.setdefault(k, [0.0, 0])
+            tot[k][0] += ms / args.steps
+            tot[k][1] += n / args.steps
+    dom = max(tot, key=lambda k: tot[k][0])
+    if dom == "p2p":
+        pairs = sum(info[t]["n_p2p_pairs"] for t in args.tilings)
+        peak = sm_count * MUFU_PER_CLK_SM * clk_mhz * 1e6 / 1e9
+        ach = pairs / (tot[dom][0] / 1e3) / 1e9
+        roof = {"kernel": "p2p", "bound": "alu", "achieved": ach, "peak": peak, "unit": "Gpair/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": "%d SMs x %d lg2/clk x %.0f MHz" % (sm_count, MUFU_PER_CLK_SM, clk_mhz)}
+    else:
+        fl = 0.0
+        for t in args.tilings:
+            p = info[t]["p"]
+            fl += info[t]["n_m2l"] * 8.0 * p * (p + 1)
+        peak = sm_count * FP32_LANES_SM * 2 * clk_mhz * 1e6 / 1e12
+        ach = fl / (tot[dom][0] / 1e3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": "%d SMs x %d FP32 lanes x 2 x %.0f MHz" % (sm_count, FP32_LANES_SM, clk_mhz)}
+
+    cpu_v, cpu_dt = (None, None)
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu_v, cpu_dt = oracle_sample(n=args.ref_points)
+    launches = int(sum(tot[k][1] for k in tot))
+    if rank == 0:
+        line = {
+            "metric": "FMM eval points/s at eps=1e-6 (3 tilings)", "value": value, "unit": "points/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.prec == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": "N=M=2^20 uniform unit square (sources=targets), FP32 points and "
+                                   "strengths, quad+sept+tri, eps=1e-6, planner L/p, %s form" % args.prec,
+                       "global_batch": N_POINTS, "l2": "flushed between tilings (256 MB write)",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "per_tiling": {t: {"points_per_s": N_POINTS / (statistics.mean(tt[t]) / 1e3),
+                               "ms": statistics.mean(tt[t]), "L": info[t]["levels"], "p": info[t]["p"],
+                               "m2l": info[t]["n_m2l"], "p2p_pairs": info[t]["n_p2p_pairs"],
+                               "stages_ms": {k: v[0] / args.steps for k, v in stage[t].items()}}
+                           for t in args.tilings},
+            "roofline": roof,
+            "peaks_source": src,
+            "cpu_baseline": None if cpu_v is None else {
+                "value": cpu_v, "unit": "points/s", "cores": 1, "kind": "oracle",
+                "sample": "N=M=%d per tiling, 3 tilings, one FP64 evaluation (%.1f s)" % (args.ref_points, cpu_dt)},
+            "e2e": {"value": e2e_v, "unit": "points/s",
+                    "h2d_bytes_per_step": int(xy.nbytes + u.nbytes),
+                    "d2h_bytes_per_step": int(8 * N_POINTS * len(args.tilings))},
+            "gpu_launches": launches * args.steps,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line))
+    for p_ in plans.values():
+        p_.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--tilings", default=",".join(TILINGS))
+    ap.add_argument("--ref-points", type=int, default=16384)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.tilings = tuple(args.tilings.split(","))
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,214 @@
+/*
+ * fmm2d.h - C ABI of the GB300 (sm_103a) 2D fast multipole method over three
+ * tilings of the plane: quadtree, septree of hexagons and triangle quadtree
+ * (Luo & Duraiswami, "Alternative tilings for the fast multipole method on
+ * the plane", arXiv:1204.3105).
+ *
+ * What is computed (Sec. 2, eqs. 1-2): for sources x_i with real strengths
+ * u_i and targets y_j in the plane (points as complex numbers),
+ *
+ *     Phi_j = sum_{i : x_i != y_j} u_i log|y_j - x_i|
+ *
+ * i.e. the real part of sum_i u_i log(y_j - x_i) (the complex logarithm of
+ * eq. 1 is multivalued; its real part, the 2D Coulomb potential, is not).
+ * A source that coincides with the target is skipped.
+ *
+ * The evaluation is the hierarchical FMM of Sec. 2: every point is keyed with
+ * the tiling's CellIndex (Sec. 4-6) and sorted; occupied cells of every level
+ * get Near lists (the cell and its Neighbors, Sec. 4) and M2L lists
+ * (NeighborsE4, eq. 3, read as Children[Parent(n) u Neighbors(Parent(n))]
+ * minus Near(n)); then P2M, M2M, M2L, L2L, L2P and the P2P near-field sum.
+ * Every step runs in the library's own CUDA kernels; there is no CPU
+ * fallback.
+ *
+ * Conventions for every call below
+ *   - Pointers named *_dev are device pointers (cudaMalloc / PyTorch CUDA
+ *     memory) on the current device; pointers named *_host are host memory.
+ *     The caller owns every buffer it passes; the library never frees them.
+ *   - Points are interleaved (x, y) pairs: 2*n values of float64, or of
+ *     float32 when the plan was created with FMM2D_IN_F32.  Strengths are n
+ *     values of the same type.  Potentials are always float64.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All device
+ *     work is ordered on it; a call returns once its work is enqueued, except
+ *     fmm2d_build, which waits for its own work (it reads back the cell
+ *     counts that size the evaluation).
+ *   - Errors are status codes; no C++ exception crosses the ABI.  The text of
+ *     the last error of a plan is available from fmm2d_last_error.
+ *   - A plan is not thread safe; distinct plans may be used concurrently.
+ */
+#ifndef FMM2D_H
+#define FMM2D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { FMM2D_QUAD = 0, FMM2D_SEPT = 1, FMM2D_TRI = 2 } fmm2d_tiling;
+
+typedef enum {
+  FMM2D_OK = 0,
+  FMM2D_EINVAL = 1,    /* bad argument (tiling, levels, p, sizes, null pointer) */
+  FMM2D_ENOMEM = 2,    /* a device or host allocation failed */
+  FMM2D_EDOMAIN = 3,   /* a point lies outside the plan's domain square */
+  FMM2D_ECUDA = 4,     /* a CUDA runtime call failed (message in fmm2d_last_error) */
+  FMM2D_EBUSY = 5,     /* server: no admission possible right now */
+  FMM2D_ETIMEOUT = 6,  /* a bounded wait gave up */
+  FMM2D_ENOTREADY = 7  /* server: ticket not finished yet / plan not built */
+} fmm2d_status;
+
+/* Plan flags (bitwise or). */
+#define FMM2D_PREC_FP64     0x0u  /* every expansion, translation and P2P in FP64 */
+#define FMM2D_PREC_MIXED    0x1u  /* FP32 expansions, translations and P2P; the
+                                     leading Q log term, L_0 and the final sums in FP64 */
+#define FMM2D_PREC_MIXED_TC 0x2u  /* as MIXED, with M2L on the tensor cores
+                                     (split hi/lo TF32 products, FP32 accumulation) */
+#define FMM2D_PREC_MASK     0x3u
+#define FMM2D_IN_F32        0x10u /* points and strengths are float32 (default float64) */
+
+typedef struct fmm2d_plan fmm2d_plan;
+
+/* Plan description returned by fmm2d_plan_query. */
+typedef struct {
+  int32_t tiling;          /* fmm2d_tiling */
+  int32_t levels;          /* leaf level L (root = level 0) */
+  int32_t p;               /* highest expansion power (p coefficients + Q) */
+  int32_t l_min;           /* first level with M2L translations */
+  uint32_t flags;
+  int32_t built;           /* 1 after a successful fmm2d_build */
+  double eps;              /* requested tolerance */
+  double domain[3];        /* x0, y0, S: domain square [x0, x0+S) x [y0, y0+S) */
+  double leaf_scale;       /* septree: leaf hexagon circumradius r; triangle:
+                              root inradius rho0; quadtree: 2^-L (frame units) */
+  int64_t n_src, n_tgt;
+  int64_t n_cells[24];     /* occupied cells per level 0..L */
+  int64_t n_m2l;           /* M2L translations (list entries) */
+  int64_t n_p2p_pairs;     /* source-target pairs summed directly */
+  int32_t n_m2l_ops;       /* distinct M2L operators (lattice offsets) */
+  int32_t max_far;         /* longest M2L list (P4 of Table 2 for interior cells) */
+  int32_t max_near;        /* longest Near list (P2 of Table 2) */
+  int32_t reserved;
+} fmm2d_info;
+
+/*
+ * fmm2d_default_params - the planner's rules, exposed for callers and tests.
+ *   levels_out: smallest leaf level L whose expected mean points per occupied
+ *     leaf of a uniform input of n_points points is <= leaf_target (the
+ *     tiling's leaf area times n_points).
+ *   p_out: smallest p with kappa^(p+1) <= eps, kappa = 1/(1 + rho/r) from
+ *     Table 2 (Sec. 8; septree rho/r measured on the GBT aggregates, giving
+ *     kappa = 0.525).
+ *   leaf_scale_out: septree leaf circumradius for that L (frame units; the
+ *     smallest 2^-40 multiple for which every point of the domain square has
+ *     its nearest hexagon centre inside the L-digit GBT region), triangle root
+ *     inradius, or 2^-L for the quadtree.
+ * Any output pointer may be NULL.  Returns FMM2D_EINVAL for a bad tiling,
+ * eps outside (0, 1) or n_points < 0.
+ */
+fmm2d_status fmm2d_default_params(int tiling, int64_t n_points, int leaf_target, double eps,
+                                  int *levels_out, int *p_out, double *leaf_scale_out);
+
+/*
+ * fmm2d_plan_create - make an empty plan.
+ *   tiling: FMM2D_QUAD, FMM2D_SEPT or FMM2D_TRI.
+ *   levels: leaf level L (1..12 quadtree/triangle, 1..9 septree), or 0 to
+ *     choose it at fmm2d_build time with fmm2d_default_params (leaf target 64).
+ *   p: highest expansion power 1..48, or 0 to derive it from eps.
+ *   eps: requested relative tolerance (used when p == 0), 0 < eps < 1.
+ *   flags: FMM2D_PREC_* | FMM2D_IN_F32.
+ * The domain defaults to the unit square [0,1)^2.  On success *out owns all
+ * plan memory until fmm2d_plan_destroy.  Errors: FMM2D_EINVAL, FMM2D_ENOMEM.
+ */
+fmm2d_status fmm2d_plan_create(int tiling, int levels, int p, double eps, unsigned flags,
+                               fmm2d_plan **out);
+
+/*
+ * fmm2d_plan_set_domain - set the domain square [x0, x0+S) x [y0, y0+S)
+ * (S > 0).  Every source and target must lie in it (else fmm2d_build returns
+ * FMM2D_EDOMAIN).  Invalidates a previous build.
+ */
+fmm2d_status fmm2d_plan_set_domain(fmm2d_plan *plan, double x0, double y0, double size);
+
+/*
+ * fmm2d_build - key, sort and tree the point sets (Sec. 4-6: CellIndex,
+ * Parent/Children, Neighbors, NeighborsE4).
+ *   src_xy_dev: n_src interleaved points; tgt_xy_dev: n_tgt points.  Passing
+ *   the same pointer and count for both marks the sets as identical (the
+ *   sort is shared).  n_src, n_tgt >= 0.
+ * The points are copied (sorted, relative to their leaf centres) into plan
+ * memory; the caller may reuse its buffers after the call returns.  The call
+ * synchronises `stream` once to read back the per-level cell counts.
+ * Errors: FMM2D_EINVAL, FMM2D_ENOMEM, FMM2D_EDOMAIN (plan left unbuilt),
+ * FMM2D_ECUDA.
+ */
+fmm2d_status fmm2d_build(fmm2d_plan *plan, const void *src_xy_dev, int64_t n_src,
+                         const void *tgt_xy_dev, int64_t n_tgt, void *stream);
+
+/*
+ * fmm2d_evaluate - one FMM evaluation on the built geometry (Sec. 2):
+ * P2M, M2M, M2L, L2L, L2P and P2P, then the potentials are written in the
+ * caller's original target order.
+ *   strengths_dev: n_src values (float64, or float32 with FMM2D_IN_F32).
+ *   potentials_dev: n_tgt float64 outputs, Re Phi_j.
+ * May be called any number of times with new strengths.  Asynchronous on
+ * `stream`.  Errors: FMM2D_ENOTREADY (not built), FMM2D_EINVAL, FMM2D_ECUDA.
+ */
+fmm2d_status fmm2d_evaluate(fmm2d_plan *plan, const void *strengths_dev, double *potentials_dev,
+                            void *stream);
+
+/* fmm2d_plan_query - fill *info (host struct) with the plan's parameters and
+ * counts.  Errors: FMM2D_EINVAL. */
+fmm2d_status fmm2d_plan_query(const fmm2d_plan *plan, fmm2d_info *info);
+
+/*
+ * fmm2d_debug_export - copy one intermediate of the last build / evaluate to
+ * host memory for verification (synchronises the plan's last stream).
+ *   what:
+ *     1 source keys (int64, leaf key of every source, input order)
+ *     2 source sort permutation (int64, sorted position -> input index)
+ *     3 target keys, 4 target sort permutation (as 1, 2)
+ *     5 occupied cell keys of `level` (int64, ascending)
+ *     6 Near list pairs at the leaf level (int64 pairs: target key, source key)
+ *     7 M2L list pairs of `level` (int64 pairs: target key, source key)
+ *     8 multipoles of `level`: per cell (in the order of 5) p+1 complex128
+ *       values, Q then a_1..a_p, unscaled (Greengard-Rokhlin form about the
+ *       cell centre)
+ *     9 locals of `level`: per cell p+1 complex128 values b_0..b_p (b_0 real
+ *       part only)
+ *    10 near-field part of Phi (float64, input target order)
+ *    11 far-field part of Phi (float64, input target order)
+ *    12 cell centres of `level` (complex128, order of 5, original coordinates)
+ *   host_buf / cap: destination and its size in bytes; with host_buf NULL only
+ *   *written (required bytes) is set.
+ * Errors: FMM2D_EINVAL (unknown what / level, cap too small),
+ * FMM2D_ENOTREADY.
+ */
+fmm2d_status fmm2d_debug_export(fmm2d_plan *plan, int what, int level, void *host_buf,
+                                size_t cap, size_t *written);
+
+/*
+ * fmm2d_plan_set_profiling - when on (1), fmm2d_build / fmm2d_evaluate
+ * record CUDA events around every stage on the launching stream, and
+ * fmm2d_stage_times returns the accumulated milliseconds per stage
+ * (keys, sort, tree, lists, p2m, m2m, m2l, l2l, l2p, p2p, other) and the
+ * number of launches of each.  Resets the accumulators.
+ */
+fmm2d_status fmm2d_plan_set_profiling(fmm2d_plan *plan, int on);
+fmm2d_status fmm2d_stage_times(fmm2d_plan *plan, double *ms_host, int64_t *launches_host,
+                               int cap, int *n_stages);
+
+/* fmm2d_plan_destroy - free all plan memory (device and host).  NULL is a no-op. */
+void fmm2d_plan_destroy(fmm2d_plan *plan);
+
+/* fmm2d_last_error - text of the plan's last error ("" if none).  The
+ * pointer stays valid until the next call on the plan.  NULL plan: the last
+ * error of a failed fmm2d_plan_create on this thread. */
+const char *fmm2d_last_error(const fmm2d_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMM2D_H */

@@ -87,7 +87,7 @@ def leaf_area(tiling, L):
 def auto_levels(tiling, n_points, leaf_target=64):
     """Smallest leaf level L whose expected mean points per occupied leaf of
     a uniform input does not exceed ``leaf_target``."""
-    top = {"quad": 15, "tri": 15, "sept": 8}[tiling]
+    top = {"quad": 12, "tri": 12, "sept": 8}[tiling]
     for L in range(1, top + 1):
         if n_points * leaf_area(tiling, L) <= leaf_target:
             return L

@@ -1,0 +1,994 @@
+// api.cu - the C ABI of libfmm2d (include/fmm2d.h): planner rules, per-plan
+// stencils and operator tables, and the orchestration of build / evaluate.
+// Host code only; every numerical step of the FMM runs in the kernels of
+// keys.cu, sort.cu, tree.cu, expand.cu and p2p.cu.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "plan.h"
+
+struct fmm2d_plan : public fmm2d::Plan {};
+
+namespace fmm2d {
+
+using cd = std::complex<double>;
+
+static thread_local std::string g_create_err;
+static const double kSqrt3 = std::sqrt(3.0);
+
+cudaError_t dbuf_reserve(DBuf &b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return cudaSuccess;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e == cudaSuccess) b.bytes = bytes;
+  return e;
+}
+void dbuf_free(DBuf &b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+// ------------------------------------------------------------ planner rules
+static int64_t sept_min_outside_norm(int L) {
+  static std::mutex mu;
+  static std::map<int, int64_t> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(L);
+  if (it != cache.end()) return it->second;
+  const int R = (int)(0.6 * std::pow(7.0, L / 2.0)) + 4;
+  int64_t best = INT64_MAX;
+  for (int a = -R; a <= R; ++a)
+    for (int b = -R; b <= R; ++b) {
+      int64_t n = (int64_t)a * a + (int64_t)a * b + (int64_t)b * b;
+      if (n >= best) continue;
+      uint32_t k;
+      if (!eis_to_key(a, b, L, &k)) best = n;
+    }
+  cache[L] = best;
+  return best;
+}
+
+// Septree leaf circumradius r_L: every point of the frame square (inside the
+// disc of radius sqrt(1/2)) has its nearest leaf-lattice point (spacing r
+// sqrt3, covering radius r) inside the L-digit GBT region.
+static double sept_leaf_r(int L) {
+  double m = std::sqrt((double)sept_min_outside_norm(L));
+  double raw = std::sqrt(0.5) / (kSqrt3 * m - 1.0);
+  return std::ceil(raw * 1099511627776.0) / 1099511627776.0;   // 2^40
+}
+
+// Triangle root inradius: the upright triangle centred at the origin that
+// contains the frame square [-1/2, 1/2)^2, widened by 2^-20.
+static double tri_rho0() { return (kSqrt3 + 1.0) / 4.0 * (1.0 + std::ldexp(1.0, -20)); }
+
+static double kappa(int tiling) {
+  if (tiling == FMM2D_QUAD) return 1.0 / (1.0 + 2.0 * (std::sqrt(2.0) - 1.0));
+  if (tiling == FMM2D_SEPT) return 0.525;
+  return 1.0 / (1.0 + (std::sqrt(7.0) - 2.0));
+}
+
+static int max_levels(int tiling) { return tiling == FMM2D_SEPT ? 9 : 12; }
+
+static double leaf_area(int tiling, int L) {
+  if (tiling == FMM2D_QUAD) return std::pow(4.0, -L);
+  if (tiling == FMM2D_TRI) {
+    double rho0 = tri_rho0();
+    return 3.0 * kSqrt3 * rho0 * rho0 / std::pow(4.0, L);
+  }
+  double r = sept_leaf_r(L);
+  return 1.5 * kSqrt3 * r * r;
+}
+
+static int auto_levels(int tiling, int64_t n, int leaf_target) {
+  int top = tiling == FMM2D_SEPT ? 8 : 12;
+  for (int L = 1; L <= top; ++L)
+    if ((double)n * leaf_area(tiling, L) <= (double)leaf_target) return L;
+  return top;
+}
+
+static int p_from_eps(int tiling, double eps) {
+  int p = (int)std::ceil(std::log(eps) / std::log(kappa(tiling))) - 1;
+  return std::max(1, p);
+}
+
+static int key_bits(int tiling, int L) {
+  if (tiling != FMM2D_SEPT) return 2 * L;
+  uint64_t v = 1;
+  for (int i = 0; i < L; ++i) v *= 7;
+  int b = 0;
+  while ((1ull << b) < v) ++b;
+  return b;
+}
+
+// ------------------------------------------------------------ stencils
+struct I3 { int a, b, c; };
+static bool operator==(const I3 &x, const I3 &y) { return x.a == y.a && x.b == y.b && x.c == y.c; }
+
+static std::vector<I3> tri_near(I3 c, int l) {
+  bool up = tri_up(c.a, c.b, c.c, l);
+  I3 v[3];
+  if (up) v[0] = {c.a + 1, c.b, c.c}, v[1] = {c.a, c.b + 1, c.c}, v[2] = {c.a, c.b, c.c + 1};
+  else v[0] = {c.a, c.b + 1, c.c + 1}, v[1] = {c.a + 1, c.b, c.c + 1}, v[2] = {c.a + 1, c.b + 1, c.c};
+  std::vector<I3> out;
+  for (auto &x : v) {
+    I3 t[6] = {{x.a - 1, x.b, x.c}, {x.a, x.b - 1, x.c}, {x.a, x.b, x.c - 1},
+               {x.a - 1, x.b - 1, x.c}, {x.a - 1, x.b, x.c - 1}, {x.a, x.b - 1, x.c - 1}};
+    for (auto &y : t)
+      if (std::find(out.begin(), out.end(), y) == out.end()) out.push_back(y);
+  }
+  return out;
+}
+static I3 tri_child3(I3 p, int l, int t) {
+  I3 c;
+  tri_child(p.a, p.b, p.c, tri_up(p.a, p.b, p.c, l), t, &c.a, &c.b, &c.c);
+  return c;
+}
+
+struct OpKey { int u, v; bool operator<(const OpKey &o) const { return u != o.u ? u < o.u : v < o.v; } };
+
+struct Tables {
+  Stencils st;
+  std::vector<cd> zeta;          // per M2L operator
+  std::vector<cd> cw, csig;      // per child class: w and sigma of M2M / L2L
+  int n_classes;
+};
+
+static void add_far(Tables &T, int cls, I3 d, OpKey key, cd z, std::map<OpKey, int> &ids) {
+  auto it = ids.find(key);
+  int id;
+  if (it == ids.end()) {
+    id = (int)T.zeta.size();
+    ids[key] = id;
+    T.zeta.push_back(z);
+  } else {
+    id = it->second;
+  }
+  int e = T.st.far_len[cls]++;
+  T.st.far_d[cls][e][0] = d.a;
+  T.st.far_d[cls][e][1] = d.b;
+  T.st.far_d[cls][e][2] = d.c;
+  T.st.far_op[cls][e] = (uint16_t)id;
+}
+
+static Tables make_tables(int tiling) {
+  Tables T;
+  std::memset(&T.st, 0, sizeof(T.st));
+  std::map<OpKey, int> ids;
+  const double s2 = std::sqrt(2.0);
+  if (tiling == FMM2D_QUAD) {
+    T.n_classes = 4;
+    for (int d = 0; d < 4; ++d) {
+      int bx = d & 1, by = d >> 1, ci = 32 + bx, cj = 32 + by;
+      for (int dpj = -1; dpj <= 1; ++dpj)
+        for (int dpi = -1; dpi <= 1; ++dpi)
+          for (int cy = 0; cy < 2; ++cy)
+            for (int cx = 0; cx < 2; ++cx) {
+              int di = 2 * (16 + dpi) + cx - ci, dj = 2 * (16 + dpj) + cy - cj;
+              if (std::abs(di) <= 1 && std::abs(dj) <= 1) continue;
+              add_far(T, d, {di, dj, 0}, {di, dj}, s2 * cd(di, dj), ids);
+            }
+      T.cw.push_back(cd(bx - 0.5, by - 0.5) / s2);
+      T.csig.push_back(cd(0.5, 0));
+    }
+    T.st.near_len[0] = 0;
+    for (int dj = -1; dj <= 1; ++dj)
+      for (int di = -1; di <= 1; ++di) {
+        int e = T.st.near_len[0]++;
+        T.st.near_d[0][e][0] = di;
+        T.st.near_d[0][e][1] = dj;
+      }
+  } else if (tiling == FMM2D_SEPT) {
+    T.n_classes = 7;
+    const cd w6(0.5, kSqrt3 / 2), beta(2.0, kSqrt3);
+    auto unit = [](int d) { return I3{unit_a(d), unit_b(d), 0}; };
+    auto is_near = [&](I3 x) {
+      for (int d = 0; d < 7; ++d)
+        if (x.a == unit_a(d) && x.b == unit_b(d)) return true;
+      return false;
+    };
+    for (int d = 0; d < 7; ++d) {
+      I3 E = unit(d);   // a level-l cell whose parent is the origin
+      for (int dp = 0; dp < 7; ++dp) {
+        I3 P = unit(dp);
+        I3 BP = {P.a - 2 * P.b, 2 * P.a + 3 * P.b, 0};   // beta * P
+        for (int d2 = 0; d2 < 7; ++d2) {
+          I3 ch = {BP.a + unit_a(d2), BP.b + unit_b(d2), 0};
+          I3 del = {ch.a - E.a, ch.b - E.b, 0};
+          if (is_near(del)) continue;
+          add_far(T, d, del, {del.a, del.b}, kSqrt3 * (double(del.a) + double(del.b) * w6), ids);
+        }
+      }
+      cd e = d == 0 ? cd(0, 0) : std::polar(1.0, (d - 1) * M_PI / 3.0);
+      T.cw.push_back(kSqrt3 * e / beta);
+      T.csig.push_back(1.0 / beta);
+    }
+    for (int d = 0; d < 7; ++d) {
+      T.st.near_d[0][d][0] = unit_a(d);
+      T.st.near_d[0][d][1] = unit_b(d);
+    }
+    T.st.near_len[0] = 7;
+  } else {
+    T.n_classes = 8;
+    const int lp = 7, lc = 8;
+    for (int pinv = 0; pinv < 2; ++pinv) {
+      I3 par = pinv ? I3{42, 42, 42} : I3{42, 42, 43};
+      std::vector<I3> pn = tri_near(par, lp);
+      for (int t = 0; t < 4; ++t) {
+        int cls = t + 4 * pinv;
+        I3 cell = tri_child3(par, lp, t);
+        bool cup = tri_up(cell.a, cell.b, cell.c, lc);
+        std::vector<I3> ex = tri_near(cell, lc);
+        for (auto &q : pn)
+          for (int t2 = 0; t2 < 4; ++t2) {
+            I3 ch = tri_child3(q, lp, t2);
+            if (std::find(ex.begin(), ex.end(), ch) != ex.end()) continue;
+            bool sup = tri_up(ch.a, ch.b, ch.c, lc);
+            int di = ch.a - cell.a, dj = ch.b - cell.b, dk = ch.c - cell.c;
+            int dob = (sup ? 1 : 2) - (cup ? 1 : 2);
+            int u = dk - dj, v = 3 * di + dob;
+            add_far(T, cls, {di, dj, dk}, {u, v}, cd(kSqrt3 / 2 * u, 0.5 * v), ids);
+          }
+        double up_p = pinv ? -1.0 : 1.0;
+        cd w = t == 0 ? cd(0, 0) : 0.5 * std::polar(1.0, up_p * (M_PI / 2 + 2 * (t - 1) * M_PI / 3));
+        T.cw.push_back(w);
+        T.csig.push_back(cd(0.5, 0));
+      }
+    }
+    I3 reps[2] = {{84, 85, 86}, {84, 85, 85}};   // upright, inverted (level 8)
+    for (int o = 0; o < 2; ++o) {
+      std::vector<I3> nb = tri_near(reps[o], 8);
+      T.st.near_len[o] = (int)nb.size();
+      for (size_t e = 0; e < nb.size(); ++e) {
+        T.st.near_d[o][e][0] = nb[e].a - reps[o].a;
+        T.st.near_d[o][e][1] = nb[e].b - reps[o].b;
+        T.st.near_d[o][e][2] = nb[e].c - reps[o].c;
+      }
+    }
+  }
+  T.st.n_classes = T.n_classes;
+  return T;
+}
+
+// ------------------------------------------------------------ operators
+static double binom(int n, int k) {
+  if (k < 0 || k > n) return 0.0;
+  double r = 1.0;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return r;
+}
+
+// M2L operator on scaled coefficients, (p+1) x (p+1), column 0 = Q column.
+static void m2l_op(cd z, int p, std::vector<cd> &out) {
+  const int P1 = p + 1;
+  out.assign((size_t)P1 * P1, cd(0, 0));
+  std::vector<cd> ip(2 * p + 2);
+  cd inv = 1.0 / z;
+  ip[0] = 1.0;
+  for (int i = 1; i < 2 * p + 2; ++i) ip[i] = ip[i - 1] * inv;
+  for (int l = 0; l <= p; ++l) {
+    if (l >= 1) out[(size_t)l * P1] = -ip[l] / double(l);
+    for (int k = 1; k <= p; ++k)
+      out[(size_t)l * P1 + k] = binom(l + k - 1, k - 1) * ((k & 1) ? -1.0 : 1.0) * ip[l + k];
+  }
+}
+static void m2m_op(cd w, cd sig, int p, std::vector<cd> &out) {
+  const int P1 = p + 1;
+  out.assign((size_t)P1 * P1, cd(0, 0));
+  for (int l = 1; l <= p; ++l) {
+    out[(size_t)l * P1] = -std::pow(w, l) / double(l);
+    for (int k = 1; k <= l; ++k)
+      out[(size_t)l * P1 + k] = binom(l - 1, k - 1) * std::pow(sig, k) * std::pow(w, l - k);
+  }
+}
+static void l2l_op(cd w, cd sig, int p, std::vector<cd> &out) {
+  const int P1 = p + 1;
+  out.assign((size_t)P1 * P1, cd(0, 0));
+  for (int k = 0; k <= p; ++k)
+    for (int l = k; l <= p; ++l)
+      out[(size_t)k * P1 + l] = binom(l, k) * std::pow(w, l - k) * std::pow(sig, k);
+}
+
+}  // namespace fmm2d
+
+using namespace fmm2d;
+
+// ------------------------------------------------------------ plan helpers
+namespace {
+
+fmm2d_status fail(fmm2d_plan *pl, fmm2d_status st, const std::string &msg) {
+  if (pl) pl->err = msg;
+  return st;
+}
+fmm2d_status cuda_fail(fmm2d_plan *pl, cudaError_t e, const char *where) {
+  return fail(pl, FMM2D_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define CK(expr, where)                                  \
+  do {                                                   \
+    cudaError_t _e = (expr);                             \
+    if (_e != cudaSuccess) return cuda_fail(pl, _e, where); \
+  } while (0)
+
+bool is_fp64(const fmm2d_plan *pl) { return (pl->flags & FMM2D_PREC_MASK) == FMM2D_PREC_FP64; }
+
+struct StageScope {
+  fmm2d_plan *pl;
+  int st;
+  cudaStream_t s;
+  cudaEvent_t b = nullptr, e = nullptr;
+  StageScope(fmm2d_plan *p, int stage, cudaStream_t str, int launches) : pl(p), st(stage), s(str) {
+    if (!pl->profiling) return;
+    pl->stage_launches[st] += launches;
+    b = get();
+    e = get();
+    cudaEventRecord(b, s);
+  }
+  cudaEvent_t get() {
+    if (pl->ev_used >= pl->ev_pool.size()) {
+      cudaEvent_t ev;
+      cudaEventCreate(&ev);
+      pl->ev_pool.push_back(ev);
+    }
+    return pl->ev_pool[pl->ev_used++];
+  }
+  ~StageScope() {
+    if (!pl->profiling) return;
+    cudaEventRecord(e, s);
+    pl->ev_pending.push_back({st, {b, e}});
+  }
+};
+
+void flush_events(fmm2d_plan *pl) {
+  for (auto &x : pl->ev_pending) {
+    cudaEventSynchronize(x.second.second);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, x.second.first, x.second.second);
+    pl->stage_ms[x.first] += ms;
+  }
+  pl->ev_pending.clear();
+  pl->ev_used = 0;
+}
+
+// Geometry, stencils and operator tables for the current (tiling, L, p).
+fmm2d_status setup_geometry(fmm2d_plan *pl) {
+  Geo &g = pl->geo;
+  g.tiling = pl->tiling;
+  g.L = pl->L;
+  g.b = pl->b;
+  g.x0 = pl->x0;
+  g.y0 = pl->y0;
+  g.S = pl->S;
+  const int L = pl->L;
+  if (pl->tiling == FMM2D_QUAD) g.leaf_scale = std::ldexp(1.0, -L);
+  else if (pl->tiling == FMM2D_TRI) g.leaf_scale = tri_rho0();
+  else g.leaf_scale = sept_leaf_r(L);
+  int64_t off = 0, pw = 1;
+  for (int l = 0; l <= L; ++l) {
+    g.map_off[l] = off;
+    off += pw;
+    pw *= pl->b;
+  }
+  g.map_off[L + 1] = off;
+  pl->map_size = off;
+  const cd beta(2.0, kSqrt3), e6 = std::polar(1.0, M_PI / 6);
+  for (int l = 0; l <= L; ++l) {
+    cd s;
+    if (pl->tiling == FMM2D_QUAD) {
+      s = cd(pl->S * std::ldexp(1.0, -l) * std::sqrt(2.0) / 2, 0);
+      g.unit_re[l] = g.unit_im[l] = 0;
+    } else if (pl->tiling == FMM2D_TRI) {
+      s = cd(pl->S * 2.0 * g.leaf_scale * std::ldexp(1.0, -l), 0);
+      g.unit_re[l] = g.unit_im[l] = 0;
+    } else {
+      cd bl = std::pow(beta, L - l);
+      cd unit = g.leaf_scale * kSqrt3 * e6 * bl;   // frame lattice unit g_l
+      g.unit_re[l] = unit.real();
+      g.unit_im[l] = unit.imag();
+      s = pl->S * g.leaf_scale * e6 * bl;
+    }
+    pl->scale_re[l] = s.real();
+    pl->scale_im[l] = s.imag();
+    pl->log_abs_scale[l] = std::log(std::abs(s));
+  }
+  Tables T = make_tables(pl->tiling);
+  pl->sten = T.st;
+  pl->n_ops = (int)T.zeta.size();
+  pl->max_far = 0;
+  for (int c = 0; c < T.n_classes; ++c) pl->max_far = std::max(pl->max_far, T.st.far_len[c]);
+  pl->max_near = std::max(T.st.near_len[0], T.st.near_len[1]);
+  const int p = pl->p, P1 = p + 1;
+  std::vector<cd> m2l((size_t)pl->n_ops * P1 * P1), m2m((size_t)T.n_classes * P1 * P1),
+      l2l((size_t)T.n_classes * P1 * P1), tmp;
+  pl->m2l_logz_host.resize(pl->n_ops);
+  for (int o = 0; o < pl->n_ops; ++o) {
+    m2l_op(T.zeta[o], p, tmp);
+    std::copy(tmp.begin(), tmp.end(), m2l.begin() + (size_t)o * P1 * P1);
+    pl->m2l_logz_host[o] = std::log(std::abs(T.zeta[o]));
+  }
+  for (int c = 0; c < T.n_classes; ++c) {
+    m2m_op(T.cw[c], T.csig[c], p, tmp);
+    std::copy(tmp.begin(), tmp.end(), m2m.begin() + (size_t)c * P1 * P1);
+    l2l_op(T.cw[c], T.csig[c], p, tmp);
+    std::copy(tmp.begin(), tmp.end(), l2l.begin() + (size_t)c * P1 * P1);
+  }
+  const bool f64 = is_fp64(pl);
+  auto upload = [&](DBuf &b, const std::vector<cd> &v) -> cudaError_t {
+    if (f64) {
+      cudaError_t e = dbuf_reserve(b, v.size() * sizeof(double2));
+      if (e) return e;
+      return cudaMemcpy(b.p, v.data(), v.size() * sizeof(double2), cudaMemcpyHostToDevice);
+    }
+    std::vector<float2> f(v.size());
+    for (size_t i = 0; i < v.size(); ++i) f[i] = make_float2((float)v[i].real(), (float)v[i].imag());
+    cudaError_t e = dbuf_reserve(b, f.size() * sizeof(float2));
+    if (e) return e;
+    return cudaMemcpy(b.p, f.data(), f.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  };
+  CK(upload(pl->d_m2l_ops, m2l), "upload m2l");
+  CK(upload(pl->d_m2m_ops, m2m), "upload m2m");
+  CK(upload(pl->d_l2l_ops, l2l), "upload l2l");
+  CK(dbuf_reserve(pl->d_m2l_logz, pl->n_ops * sizeof(double)), "alloc logz");
+  CK(cudaMemcpy(pl->d_m2l_logz.p, pl->m2l_logz_host.data(), pl->n_ops * sizeof(double),
+                cudaMemcpyHostToDevice), "upload logz");
+  CK(dbuf_reserve(pl->d_sten, sizeof(Stencils)), "alloc stencils");
+  CK(cudaMemcpy(pl->d_sten.p, &pl->sten, sizeof(Stencils), cudaMemcpyHostToDevice), "upload stencils");
+  CK(dbuf_reserve(pl->d_geo_scale, (MAXLEV + 1) * sizeof(double)), "alloc scale");
+  CK(cudaMemcpy(pl->d_geo_scale.p, pl->log_abs_scale, (MAXLEV + 1) * sizeof(double),
+                cudaMemcpyHostToDevice), "upload scale");
+  return FMM2D_OK;
+}
+
+template <typename R>
+fmm2d_status evaluate_t(fmm2d_plan *pl, const void *u, double *out, cudaStream_t s) {
+  const bool f32_in = (pl->flags & FMM2D_IN_F32) != 0;
+  const int L = pl->L;
+  R *src4 = (R *)pl->d_src4.p;
+  const R *tgt = pl->same_sets ? src4 : (const R *)pl->d_tgt2.p;
+  const int tstride = pl->same_sets ? 4 : 2;
+  const uint32_t *tperm = (const uint32_t *)(pl->same_sets ? pl->d_perm_s.p : pl->d_perm_t.p);
+  const int *tst = (const int *)(pl->same_sets ? pl->d_src_start.p : pl->d_tgt_start.p);
+  const int *ten = (const int *)(pl->same_sets ? pl->d_src_end.p : pl->d_tgt_end.p);
+  Cx<R> *ma = (Cx<R> *)pl->d_ma.p, *lb = (Cx<R> *)pl->d_lb.p;
+  double *mQ = (double *)pl->d_mQ.p, *lL0 = (double *)pl->d_lL0.p;
+  ExpandArgs a;
+  a.p = pl->p;
+  a.P = pl->P;
+  a.L = L;
+  a.l_min = pl->l_min;
+  a.b = pl->b;
+  a.leaf_first = pl->lev_first[L];
+  a.n_leaves = pl->lev_count[L];
+  cd inv_s = 1.0 / cd(pl->scale_re[L], pl->scale_im[L]);
+  a.inv_s_re = inv_s.real();
+  a.inv_s_im = inv_s.imag();
+  {
+    StageScope sc(pl, ST_OTHER, s, 1);
+    CK(launch_gather_u<R>(u, f32_in, (const uint32_t *)pl->d_perm_s.p, pl->n_src, src4, s), "gather");
+  }
+  {
+    StageScope sc(pl, ST_P2M, s, 1);
+    CK(launch_p2m<R>(a, src4, (const int *)pl->d_src_start.p, (const int *)pl->d_src_end.p, mQ, ma, s), "p2m");
+  }
+  {
+    StageScope sc(pl, ST_M2M, s, std::max(0, L - pl->l_min));
+    for (int l = L - 1; l >= pl->l_min; --l)
+      CK(launch_m2m<R>(a, pl->geo, l, pl->lev_first[l], pl->lev_count[l], (const int *)pl->d_map.p,
+                       (const uint32_t *)pl->d_cell_key.p, (const uint8_t *)pl->d_cell_cls.p,
+                       (const uint8_t *)pl->d_cell_hsrc.p, (const Cx<R> *)pl->d_m2m_ops.p, mQ, ma, s),
+         "m2m");
+  }
+  if (L < pl->l_min) {
+    CK(cudaMemsetAsync(lL0, 0, pl->n_cells * sizeof(double), s), "zero locals");
+    CK(cudaMemsetAsync(lb, 0, pl->n_cells * pl->P * sizeof(Cx<R>), s), "zero locals");
+  } else {
+    StageScope sc(pl, ST_M2L, s, 1);
+    CK(launch_m2l<R>(a, pl->lev_first[pl->l_min], pl->n_far_cells, (const int64_t *)pl->d_lev_first.p,
+                     (const double *)pl->d_geo_scale.p, 0, (const int *)pl->d_far_cnt.p,
+                     (const int *)pl->d_far_src.p, (const uint16_t *)pl->d_far_op.p,
+                     (const Cx<R> *)pl->d_m2l_ops.p, (const double *)pl->d_m2l_logz.p, mQ, ma, lL0,
+                     lb, s),
+       "m2l");
+  }
+  {
+    StageScope sc(pl, ST_L2L, s, std::max(0, L - pl->l_min));
+    for (int l = pl->l_min + 1; l <= L; ++l)
+      CK(launch_l2l<R>(a, pl->geo, l, pl->lev_first[l], pl->lev_count[l], (const int *)pl->d_map.p,
+                       (const uint32_t *)pl->d_cell_key.p, (const uint8_t *)pl->d_cell_cls.p,
+                       (const Cx<R> *)pl->d_l2l_ops.p, lL0, lb, s),
+         "l2l");
+  }
+  {
+    StageScope sc(pl, ST_P2P, s, 1);
+    CK(launch_p2p<R>(a.leaf_first, a.n_leaves, src4, tgt, tstride, (const int *)pl->d_src_start.p,
+                     (const int *)pl->d_src_end.p, tst, ten, (const int *)pl->d_near_cnt.p,
+                     (const int *)pl->d_near_src.p, (const double2 *)pl->d_cell_ctr.p,
+                     (double *)pl->d_phi_near.p, s),
+       "p2p");
+  }
+  {
+    StageScope sc(pl, ST_L2P, s, 1);
+    CK(launch_l2p<R>(a, tgt, tstride, tst, ten, tperm, lL0, lb, (const double *)pl->d_phi_near.p,
+                     (double *)pl->d_phi_far.p, out, s),
+       "l2p");
+  }
+  return FMM2D_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ C ABI
+extern "C" {
+
+fmm2d_status fmm2d_default_params(int tiling, int64_t n_points, int leaf_target, double eps,
+                                  int *levels_out, int *p_out, double *leaf_scale_out) {
+  if (tiling < 0 || tiling > 2 || n_points < 0 || !(eps > 0.0 && eps < 1.0) || leaf_target < 1)
+    return FMM2D_EINVAL;
+  int L = auto_levels(tiling, n_points, leaf_target);
+  if (levels_out) *levels_out = L;
+  if (p_out) *p_out = p_from_eps(tiling, eps);
+  if (leaf_scale_out) {
+    if (tiling == FMM2D_QUAD) *leaf_scale_out = std::ldexp(1.0, -L);
+    else if (tiling == FMM2D_TRI) *leaf_scale_out = tri_rho0();
+    else *leaf_scale_out = sept_leaf_r(L);
+  }
+  return FMM2D_OK;
+}
+
+fmm2d_status fmm2d_plan_create(int tiling, int levels, int p, double eps, unsigned flags,
+                               fmm2d_plan **out) {
+  if (!out) return FMM2D_EINVAL;
+  *out = nullptr;
+  if (tiling < 0 || tiling > 2) { g_create_err = "unknown tiling"; return FMM2D_EINVAL; }
+  if (levels < 0 || levels > max_levels(tiling)) { g_create_err = "levels out of range"; return FMM2D_EINVAL; }
+  if (p < 0 || p > MAXP) { g_create_err = "p out of range (0..48)"; return FMM2D_EINVAL; }
+  if (p == 0 && !(eps > 0.0 && eps < 1.0)) { g_create_err = "eps must be in (0, 1)"; return FMM2D_EINVAL; }
+  if ((flags & FMM2D_PREC_MASK) == 3u || (flags & ~(FMM2D_PREC_MASK | FMM2D_IN_F32)) != 0) {
+    g_create_err = "unknown flags";
+    return FMM2D_EINVAL;
+  }
+  if ((flags & FMM2D_PREC_MASK) == FMM2D_PREC_MIXED_TC) {
+    g_create_err = "tensor-core M2L is not available in this build";
+    return FMM2D_EINVAL;
+  }
+  fmm2d_plan *pl = new (std::nothrow) fmm2d_plan();
+  if (!pl) { g_create_err = "out of host memory"; return FMM2D_ENOMEM; }
+  pl->tiling = tiling;
+  pl->levels_req = levels;
+  pl->p_req = p;
+  pl->eps = eps;
+  pl->flags = flags;
+  pl->b = tiling == FMM2D_SEPT ? 7 : 4;
+  pl->l_min = tiling == FMM2D_SEPT ? 1 : 2;
+  *out = pl;
+  return FMM2D_OK;
+}
+
+fmm2d_status fmm2d_plan_set_domain(fmm2d_plan *pl, double x0, double y0, double size) {
+  if (!pl) return FMM2D_EINVAL;
+  if (!(size > 0.0) || !std::isfinite(x0) || !std::isfinite(y0) || !std::isfinite(size))
+    return fail(pl, FMM2D_EINVAL, "domain size must be positive and finite");
+  pl->x0 = x0;
+  pl->y0 = y0;
+  pl->S = size;
+  pl->built = false;
+  return FMM2D_OK;
+}
+
+fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const void *tgt,
+                         int64_t n_tgt, void *stream) {
+  if (!pl) return FMM2D_EINVAL;
+  pl->built = false;
+  if (n_src < 0 || n_tgt < 0) return fail(pl, FMM2D_EINVAL, "negative point count");
+  if ((n_src > 0 && !src) || (n_tgt > 0 && !tgt)) return fail(pl, FMM2D_EINVAL, "null point pointer");
+  if (n_src >= (int64_t)INT_MAX || n_tgt >= (int64_t)INT_MAX) return fail(pl, FMM2D_EINVAL, "too many points");
+  cudaStream_t s = (cudaStream_t)stream;
+  pl->last_stream = s;
+  const bool f32 = (pl->flags & FMM2D_IN_F32) != 0;
+  const bool f64 = is_fp64(pl);
+  pl->same_sets = (src == tgt && n_src == n_tgt);
+  pl->n_src = n_src;
+  pl->n_tgt = n_tgt;
+  int L = pl->levels_req, p = pl->p_req;
+  if (L == 0) L = auto_levels(pl->tiling, std::max(n_src, n_tgt), 64);
+  if (p == 0) p = p_from_eps(pl->tiling, pl->eps);
+  if (L < 1 || L > max_levels(pl->tiling)) return fail(pl, FMM2D_EINVAL, "levels out of range");
+  pl->L = L;
+  pl->p = p;
+  pl->P = (p + 1) & ~1;   // even stride: rows of complex values stay 16-byte aligned
+  fmm2d_status st = setup_geometry(pl);
+  if (st != FMM2D_OK) return st;
+  const Geo &g = pl->geo;
+  const int64_t nmax = std::max<int64_t>(1, std::max(n_src, n_tgt));
+  // ---- buffers sized by points
+  CK(dbuf_reserve(pl->d_key_s, nmax * 4), "alloc");
+  CK(dbuf_reserve(pl->d_perm_s, nmax * 4), "alloc");
+  CK(dbuf_reserve(pl->d_key_t, nmax * 4), "alloc");
+  CK(dbuf_reserve(pl->d_perm_t, nmax * 4), "alloc");
+  CK(dbuf_reserve(pl->d_tmp_k, nmax * 4), "alloc");
+  CK(dbuf_reserve(pl->d_tmp_v, nmax * 4), "alloc");
+  size_t scr = std::max(radix_sort_scratch_bytes(nmax), scan_scratch_bytes(pl->map_size));
+  CK(dbuf_reserve(pl->d_sort_scratch, scr), "alloc");
+  const size_t rsz = f64 ? sizeof(double) : sizeof(float);
+  CK(dbuf_reserve(pl->d_src4, std::max<int64_t>(1, n_src) * 4 * rsz), "alloc");
+  CK(dbuf_reserve(pl->d_tgt2, std::max<int64_t>(1, n_tgt) * 2 * rsz), "alloc");
+  CK(dbuf_reserve(pl->d_phi_near, std::max<int64_t>(1, n_tgt) * 8), "alloc");
+  CK(dbuf_reserve(pl->d_phi_far, std::max<int64_t>(1, n_tgt) * 8), "alloc");
+  CK(dbuf_reserve(pl->d_err, 16), "alloc");
+  CK(dbuf_reserve(pl->d_lev_first, (MAXLEV + 2) * 8), "alloc");
+  // ---- map-sized buffers
+  const int64_t ms = pl->map_size;
+  CK(dbuf_reserve(pl->d_occ, ms * 4), "alloc");
+  CK(dbuf_reserve(pl->d_hsrc, ms * 4), "alloc");
+  CK(dbuf_reserve(pl->d_scan, ms * 4), "alloc");
+  CK(dbuf_reserve(pl->d_map, ms * 4), "alloc");
+  const int64_t cap = ms;   // upper bound on occupied cells
+  CK(dbuf_reserve(pl->d_cell_key, cap * 4), "alloc");
+  CK(dbuf_reserve(pl->d_cell_crd, cap * sizeof(int4)), "alloc");
+  CK(dbuf_reserve(pl->d_cell_ctr, cap * sizeof(double2)), "alloc");
+  CK(dbuf_reserve(pl->d_cell_cls, cap), "alloc");
+  CK(dbuf_reserve(pl->d_cell_hsrc, cap), "alloc");
+
+  CK(cudaMemsetAsync(pl->d_err.p, 0, 16, s), "memset");
+  const int bits = key_bits(pl->tiling, L);
+  uint32_t *ks = (uint32_t *)pl->d_key_s.p, *ps = (uint32_t *)pl->d_perm_s.p;
+  uint32_t *kt = (uint32_t *)pl->d_key_t.p, *pt = (uint32_t *)pl->d_perm_t.p;
+  {
+    StageScope sc(pl, ST_KEYS, s, pl->same_sets ? 1 : 2);
+    CK(launch_keys(g, src, f32, n_src, ks, ps, (int *)pl->d_err.p, s), "keys");
+    if (!pl->same_sets) CK(launch_keys(g, tgt, f32, n_tgt, kt, pt, (int *)pl->d_err.p, s), "keys");
+  }
+  {
+    const int per_sort = n_src > 1 ? 5 * ((bits + 7) / 8) : 0;
+    const int per_sort_t = n_tgt > 1 ? 5 * ((bits + 7) / 8) : 0;
+    StageScope sc(pl, ST_SORT, s, per_sort + (pl->same_sets ? 0 : per_sort_t));
+    CK(radix_sort_pairs(ks, ps, (uint32_t *)pl->d_tmp_k.p, (uint32_t *)pl->d_tmp_v.p, n_src, bits,
+                        pl->d_sort_scratch.p, s), "sort");
+    if (!pl->same_sets)
+      CK(radix_sort_pairs(kt, pt, (uint32_t *)pl->d_tmp_k.p, (uint32_t *)pl->d_tmp_v.p, n_tgt, bits,
+                          pl->d_sort_scratch.p, s), "sort");
+  }
+  int64_t lev_first_h[MAXLEV + 2];
+  int err_h = 0;
+  {
+    StageScope sc(pl, ST_TREE, s, (pl->same_sets ? 1 : 2) + 3 + 1 + 1);
+    CK(cudaMemsetAsync(pl->d_occ.p, 0, ms * 4, s), "memset");
+    CK(cudaMemsetAsync(pl->d_hsrc.p, 0, ms * 4, s), "memset");
+    CK(launch_mark(g, ks, n_src, (int *)pl->d_occ.p, (int *)pl->d_hsrc.p, s), "mark");
+    if (!pl->same_sets) CK(launch_mark(g, kt, n_tgt, (int *)pl->d_occ.p, nullptr, s), "mark");
+    CK(exclusive_scan((const int *)pl->d_occ.p, (int *)pl->d_scan.p, ms, pl->d_sort_scratch.p, s), "scan");
+    CK(launch_compact(g, (const int *)pl->d_occ.p, (const int *)pl->d_scan.p, (const int *)pl->d_hsrc.p,
+                      ms, (int *)pl->d_map.p, (uint32_t *)pl->d_cell_key.p, (int4 *)pl->d_cell_crd.p,
+                      (double2 *)pl->d_cell_ctr.p, (uint8_t *)pl->d_cell_cls.p,
+                      (uint8_t *)pl->d_cell_hsrc.p, s), "compact");
+    CK(launch_level_first(g, (const int *)pl->d_scan.p, (const int *)pl->d_occ.p, ms,
+                          (int64_t *)pl->d_lev_first.p, s), "levels");
+  }
+  CK(cudaMemcpyAsync(lev_first_h, pl->d_lev_first.p, (L + 2) * 8, cudaMemcpyDeviceToHost, s), "readback");
+  CK(cudaMemcpyAsync(&err_h, pl->d_err.p, 4, cudaMemcpyDeviceToHost, s), "readback");
+  CK(cudaStreamSynchronize(s), "build sync");
+  if (err_h) return fail(pl, FMM2D_EDOMAIN, "a point lies outside the domain square or root cell");
+  for (int l = 0; l <= L + 1; ++l) pl->lev_first[l] = lev_first_h[l];
+  pl->n_cells = lev_first_h[L + 1];
+  for (int l = 0; l <= L; ++l) pl->lev_count[l] = pl->lev_first[l + 1] - pl->lev_first[l];
+  for (int l = L + 1; l <= MAXLEV + 1; ++l) pl->lev_first[l] = pl->n_cells;
+  // ---- cell-sized buffers
+  const int64_t nc = std::max<int64_t>(1, pl->n_cells);
+  const size_t csz = f64 ? sizeof(double2) : sizeof(float2);
+  CK(dbuf_reserve(pl->d_src_start, nc * 4), "alloc");
+  CK(dbuf_reserve(pl->d_src_end, nc * 4), "alloc");
+  CK(dbuf_reserve(pl->d_tgt_start, nc * 4), "alloc");
+  CK(dbuf_reserve(pl->d_tgt_end, nc * 4), "alloc");
+  CK(dbuf_reserve(pl->d_mQ, nc * 8), "alloc");
+  CK(dbuf_reserve(pl->d_lL0, nc * 8), "alloc");
+  CK(dbuf_reserve(pl->d_ma, nc * pl->P * csz), "alloc");
+  CK(dbuf_reserve(pl->d_lb, nc * pl->P * csz), "alloc");
+  const int64_t lfirst = L >= pl->l_min ? pl->lev_first[pl->l_min] : pl->n_cells;
+  pl->n_far_cells = pl->n_cells - lfirst;
+  const int64_t nfar = std::max<int64_t>(1, pl->n_far_cells);
+  const int64_t nleaf = std::max<int64_t>(1, pl->lev_count[L]);
+  CK(dbuf_reserve(pl->d_far_cnt, std::max(nfar, nleaf) * 4), "alloc");
+  CK(dbuf_reserve(pl->d_far_src, nfar * FAR_MAX * 4), "alloc");
+  CK(dbuf_reserve(pl->d_far_op, nfar * FAR_MAX * 2), "alloc");
+  CK(dbuf_reserve(pl->d_near_cnt, nleaf * 4), "alloc");
+  CK(dbuf_reserve(pl->d_near_src, nleaf * NEAR_MAX * 4), "alloc");
+  {
+    StageScope sc(pl, ST_TREE, s, pl->same_sets ? 2 : 4);
+    CK(cudaMemsetAsync(pl->d_src_start.p, 0, nc * 4, s), "memset");
+    CK(cudaMemsetAsync(pl->d_src_end.p, 0, nc * 4, s), "memset");
+    CK(launch_leaf_ranges(g, ks, n_src, (const int *)pl->d_map.p, (int *)pl->d_src_start.p,
+                          (int *)pl->d_src_end.p, s), "ranges");
+    if (!pl->same_sets) {
+      CK(cudaMemsetAsync(pl->d_tgt_start.p, 0, nc * 4, s), "memset");
+      CK(cudaMemsetAsync(pl->d_tgt_end.p, 0, nc * 4, s), "memset");
+      CK(launch_leaf_ranges(g, kt, n_tgt, (const int *)pl->d_map.p, (int *)pl->d_tgt_start.p,
+                            (int *)pl->d_tgt_end.p, s), "ranges");
+    }
+    CK(launch_rel_coords(g, f32, !f64, src, ps, ks, n_src, (const int *)pl->d_map.p,
+                         (const double2 *)pl->d_cell_ctr.p, pl->d_src4.p, 4, s), "rel");
+    if (!pl->same_sets)
+      CK(launch_rel_coords(g, f32, !f64, tgt, pt, kt, n_tgt, (const int *)pl->d_map.p,
+                           (const double2 *)pl->d_cell_ctr.p, pl->d_tgt2.p, 2, s), "rel");
+  }
+  if (pl->n_far_cells > 0) {
+    StageScope sc(pl, ST_LISTS, s, 1);
+    CK(launch_lists2(g, (const Stencils *)pl->d_sten.p, lfirst, pl->n_far_cells,
+                     (const int *)pl->d_map.p, (const uint8_t *)pl->d_cell_cls.p,
+                     (const int4 *)pl->d_cell_crd.p, (const uint8_t *)pl->d_cell_hsrc.p,
+                     (int *)pl->d_far_cnt.p, (int *)pl->d_far_src.p, (uint16_t *)pl->d_far_op.p,
+                     pl->lev_first[L], (int *)pl->d_near_cnt.p, (int *)pl->d_near_src.p,
+                     (const int64_t *)pl->d_lev_first.p, s), "lists");
+  } else {
+    // leaves above l_min: only Near lists are needed; build them with an
+    // empty M2L stencil over the leaf level.
+    Stencils st2 = pl->sten;
+    for (int c = 0; c < MAX_CLASSES; ++c) st2.far_len[c] = 0;
+    CK(dbuf_reserve(pl->d_counts, sizeof(Stencils)), "alloc");
+    CK(cudaMemcpyAsync(pl->d_counts.p, &st2, sizeof(Stencils), cudaMemcpyHostToDevice, s), "upload");
+    CK(cudaStreamSynchronize(s), "sync");
+    StageScope sc(pl, ST_LISTS, s, 1);
+    CK(launch_lists2(g, (const Stencils *)pl->d_counts.p, pl->lev_first[L], pl->lev_count[L],
+                     (const int *)pl->d_map.p, (const uint8_t *)pl->d_cell_cls.p,
+                     (const int4 *)pl->d_cell_crd.p, (const uint8_t *)pl->d_cell_hsrc.p,
+                     (int *)pl->d_far_cnt.p, (int *)pl->d_far_src.p, (uint16_t *)pl->d_far_op.p,
+                     pl->lev_first[L], (int *)pl->d_near_cnt.p, (int *)pl->d_near_src.p,
+                     (const int64_t *)pl->d_lev_first.p, s), "lists");
+  }
+  CK(cudaGetLastError(), "build");
+  pl->n_m2l = -1;
+  pl->n_p2p_pairs = -1;
+  pl->built = true;
+  return FMM2D_OK;
+}
+
+fmm2d_status fmm2d_evaluate(fmm2d_plan *pl, const void *u, double *out, void *stream) {
+  if (!pl) return FMM2D_EINVAL;
+  if (!pl->built) return fail(pl, FMM2D_ENOTREADY, "plan is not built");
+  if ((pl->n_src > 0 && !u) || (pl->n_tgt > 0 && !out)) return fail(pl, FMM2D_EINVAL, "null pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  pl->last_stream = s;
+  if (pl->n_tgt == 0) return FMM2D_OK;
+  if (is_fp64(pl)) return evaluate_t<double>(pl, u, out, s);
+  return evaluate_t<float>(pl, u, out, s);
+}
+
+fmm2d_status fmm2d_plan_query(const fmm2d_plan *cpl, fmm2d_info *info) {
+  if (!cpl || !info) return FMM2D_EINVAL;
+  fmm2d_plan *pl = const_cast<fmm2d_plan *>(cpl);
+  std::memset(info, 0, sizeof(*info));
+  info->tiling = pl->tiling;
+  info->levels = pl->built ? pl->L : pl->levels_req;
+  info->p = pl->built ? pl->p : pl->p_req;
+  info->l_min = pl->l_min;
+  info->flags = pl->flags;
+  info->built = pl->built ? 1 : 0;
+  info->eps = pl->eps;
+  info->domain[0] = pl->x0;
+  info->domain[1] = pl->y0;
+  info->domain[2] = pl->S;
+  info->n_src = pl->n_src;
+  info->n_tgt = pl->n_tgt;
+  if (!pl->built) return FMM2D_OK;
+  info->leaf_scale = pl->geo.leaf_scale;
+  for (int l = 0; l <= pl->L && l < 24; ++l) info->n_cells[l] = pl->lev_count[l];
+  info->n_m2l_ops = pl->n_ops;
+  info->max_far = pl->max_far;
+  info->max_near = pl->max_near;
+  if (pl->n_m2l < 0) {
+    cudaStreamSynchronize(pl->last_stream);
+    std::vector<int> fc(std::max<int64_t>(1, pl->n_far_cells));
+    int64_t tot = 0;
+    if (pl->n_far_cells > 0) {
+      cudaMemcpy(fc.data(), pl->d_far_cnt.p, pl->n_far_cells * 4, cudaMemcpyDeviceToHost);
+      for (int64_t i = 0; i < pl->n_far_cells; ++i) tot += fc[i];
+    }
+    pl->n_m2l = tot;
+    const int64_t nl = pl->lev_count[pl->L];
+    std::vector<int> nc(std::max<int64_t>(1, nl)), ns(std::max<int64_t>(1, nl * NEAR_MAX));
+    std::vector<int> ss(pl->n_cells), se(pl->n_cells), ts(pl->n_cells), te(pl->n_cells);
+    int64_t pairs = 0;
+    if (nl > 0) {
+      cudaMemcpy(nc.data(), pl->d_near_cnt.p, nl * 4, cudaMemcpyDeviceToHost);
+      cudaMemcpy(ns.data(), pl->d_near_src.p, nl * NEAR_MAX * 4, cudaMemcpyDeviceToHost);
+      cudaMemcpy(ss.data(), pl->d_src_start.p, pl->n_cells * 4, cudaMemcpyDeviceToHost);
+      cudaMemcpy(se.data(), pl->d_src_end.p, pl->n_cells * 4, cudaMemcpyDeviceToHost);
+      const void *tsp = pl->same_sets ? pl->d_src_start.p : pl->d_tgt_start.p;
+      const void *tep = pl->same_sets ? pl->d_src_end.p : pl->d_tgt_end.p;
+      cudaMemcpy(ts.data(), tsp, pl->n_cells * 4, cudaMemcpyDeviceToHost);
+      cudaMemcpy(te.data(), tep, pl->n_cells * 4, cudaMemcpyDeviceToHost);
+      for (int64_t i = 0; i < nl; ++i) {
+        int64_t gt = pl->lev_first[pl->L] + i;
+        int64_t nt = te[gt] - ts[gt];
+        for (int e = 0; e < nc[i]; ++e) {
+          int sl = ns[i * NEAR_MAX + e];
+          pairs += nt * (int64_t)(se[sl] - ss[sl]);
+        }
+      }
+    }
+    pl->n_p2p_pairs = pairs;
+  }
+  info->n_m2l = pl->n_m2l;
+  info->n_p2p_pairs = pl->n_p2p_pairs;
+  return FMM2D_OK;
+}
+
+fmm2d_status fmm2d_debug_export(fmm2d_plan *pl, int what, int level, void *host_buf, size_t cap,
+                                size_t *written) {
+  if (!pl) return FMM2D_EINVAL;
+  if (!pl->built) return fail(pl, FMM2D_ENOTREADY, "plan is not built");
+  const int L = pl->L;
+  if ((what >= 5 && what <= 9) || what == 12) {
+    if (level < 0 || level > L) return fail(pl, FMM2D_EINVAL, "level out of range");
+  }
+  CK(cudaStreamSynchronize(pl->last_stream), "export sync");
+  std::vector<uint8_t> out;
+  auto put64 = [&](int64_t v) { out.insert(out.end(), (uint8_t *)&v, (uint8_t *)&v + 8); };
+  auto putd = [&](double v) { out.insert(out.end(), (uint8_t *)&v, (uint8_t *)&v + 8); };
+  const bool same = pl->same_sets;
+  const int64_t lf = (what >= 5) ? pl->lev_first[level < 0 ? 0 : level] : 0;
+  const int64_t lc = (what >= 5) ? pl->lev_count[level < 0 ? 0 : level] : 0;
+  std::vector<uint32_t> ckey(std::max<int64_t>(1, pl->n_cells));
+  if (pl->n_cells > 0)
+    CK(cudaMemcpy(ckey.data(), pl->d_cell_key.p, pl->n_cells * 4, cudaMemcpyDeviceToHost), "copy");
+  switch (what) {
+    case 1: case 2: case 3: case 4: {
+      bool tg = what >= 3;
+      int64_t n = tg ? pl->n_tgt : pl->n_src;
+      const void *kp = (tg && !same) ? pl->d_key_t.p : pl->d_key_s.p;
+      const void *pp = (tg && !same) ? pl->d_perm_t.p : pl->d_perm_s.p;
+      std::vector<uint32_t> k(std::max<int64_t>(1, n)), pm(std::max<int64_t>(1, n));
+      if (n > 0) {
+        CK(cudaMemcpy(k.data(), kp, n * 4, cudaMemcpyDeviceToHost), "copy");
+        CK(cudaMemcpy(pm.data(), pp, n * 4, cudaMemcpyDeviceToHost), "copy");
+      }
+      if (what == 1 || what == 3) {
+        std::vector<int64_t> ko(n);
+        for (int64_t i = 0; i < n; ++i) ko[pm[i]] = k[i];
+        for (int64_t i = 0; i < n; ++i) put64(ko[i]);
+      } else {
+        for (int64_t i = 0; i < n; ++i) put64(pm[i]);
+      }
+      break;
+    }
+    case 5:
+      for (int64_t i = 0; i < lc; ++i) put64(ckey[lf + i]);
+      break;
+    case 6: case 7: {
+      if (what == 6) level = L;
+      const int64_t f = pl->lev_first[level], c = pl->lev_count[level];
+      const int64_t lfirst = pl->n_cells - pl->n_far_cells;
+      if (what == 7 && (level < pl->l_min || pl->n_far_cells == 0)) break;
+      const int stride = what == 6 ? NEAR_MAX : FAR_MAX;
+      const int64_t base = what == 6 ? f - pl->lev_first[L] : f - lfirst;
+      std::vector<int> cnt(std::max<int64_t>(1, c)), src(std::max<int64_t>(1, c * stride));
+      if (c > 0) {
+        const char *cp = (const char *)(what == 6 ? pl->d_near_cnt.p : pl->d_far_cnt.p);
+        const char *sp = (const char *)(what == 6 ? pl->d_near_src.p : pl->d_far_src.p);
+        CK(cudaMemcpy(cnt.data(), cp + base * 4, c * 4, cudaMemcpyDeviceToHost), "copy");
+        CK(cudaMemcpy(src.data(), sp + base * stride * 4, c * stride * 4, cudaMemcpyDeviceToHost), "copy");
+      }
+      for (int64_t i = 0; i < c; ++i)
+        for (int e = 0; e < cnt[i]; ++e) {
+          put64(ckey[f + i]);
+          put64(ckey[src[i * stride + e]]);
+        }
+      break;
+    }
+    case 8: case 9: case 12: {
+      const bool f64 = is_fp64(pl);
+      const int p = pl->p, P = pl->P;
+      std::vector<double> q(std::max<int64_t>(1, lc));
+      std::vector<double2> c2(std::max<int64_t>(1, lc * P));
+      if (what == 12) {
+        std::vector<double2> ct(std::max<int64_t>(1, lc));
+        if (lc) CK(cudaMemcpy(ct.data(), (double2 *)pl->d_cell_ctr.p + lf, lc * 16, cudaMemcpyDeviceToHost), "copy");
+        for (int64_t i = 0; i < lc; ++i) { putd(ct[i].x); putd(ct[i].y); }
+        break;
+      }
+      const void *qs = what == 8 ? pl->d_mQ.p : pl->d_lL0.p;
+      const char *cs = (const char *)(what == 8 ? pl->d_ma.p : pl->d_lb.p);
+      if (lc) {
+        CK(cudaMemcpy(q.data(), (const double *)qs + lf, lc * 8, cudaMemcpyDeviceToHost), "copy");
+        if (f64) {
+          CK(cudaMemcpy(c2.data(), cs + lf * P * 16, lc * P * 16, cudaMemcpyDeviceToHost), "copy");
+        } else {
+          std::vector<float2> c1(lc * P);
+          CK(cudaMemcpy(c1.data(), cs + lf * P * 8, lc * P * 8, cudaMemcpyDeviceToHost), "copy");
+          for (int64_t i = 0; i < lc * P; ++i) c2[i] = make_double2(c1[i].x, c1[i].y);
+        }
+      }
+      const cd sl(pl->scale_re[level], pl->scale_im[level]);
+      for (int64_t i = 0; i < lc; ++i) {
+        putd(q[i]);
+        putd(0.0);
+        cd pw = 1.0;
+        for (int k = 1; k <= p; ++k) {
+          pw *= sl;
+          cd v(c2[i * P + k - 1].x, c2[i * P + k - 1].y);
+          cd u = what == 8 ? v * pw : v / pw;
+          putd(u.real());
+          putd(u.imag());
+        }
+      }
+      break;
+    }
+    case 10: case 11: {
+      const int64_t n = pl->n_tgt;
+      std::vector<double> v(std::max<int64_t>(1, n));
+      std::vector<uint32_t> pm(std::max<int64_t>(1, n));
+      if (n) {
+        CK(cudaMemcpy(v.data(), what == 10 ? pl->d_phi_near.p : pl->d_phi_far.p, n * 8,
+                      cudaMemcpyDeviceToHost), "copy");
+        CK(cudaMemcpy(pm.data(), same ? pl->d_perm_s.p : pl->d_perm_t.p, n * 4,
+                      cudaMemcpyDeviceToHost), "copy");
+      }
+      std::vector<double> o(n);
+      for (int64_t i = 0; i < n; ++i) o[pm[i]] = v[i];
+      for (int64_t i = 0; i < n; ++i) putd(o[i]);
+      break;
+    }
+    default:
+      return fail(pl, FMM2D_EINVAL, "unknown export item");
+  }
+  if (written) *written = out.size();
+  if (!host_buf) return FMM2D_OK;
+  if (cap < out.size()) return fail(pl, FMM2D_EINVAL, "export buffer too small");
+  std::memcpy(host_buf, out.data(), out.size());
+  return FMM2D_OK;
+}
+
+fmm2d_status fmm2d_plan_set_profiling(fmm2d_plan *pl, int on) {
+  if (!pl) return FMM2D_EINVAL;
+  flush_events(pl);
+  pl->profiling = on != 0;
+  for (int i = 0; i < ST_COUNT; ++i) {
+    pl->stage_ms[i] = 0;
+    pl->stage_launches[i] = 0;
+  }
+  return FMM2D_OK;
+}
+
+fmm2d_status fmm2d_stage_times(fmm2d_plan *pl, double *ms, int64_t *launches, int cap, int *n_stages) {
+  if (!pl) return FMM2D_EINVAL;
+  flush_events(pl);
+  if (n_stages) *n_stages = ST_COUNT;
+  for (int i = 0; i < ST_COUNT && i < cap; ++i) {
+    if (ms) ms[i] = pl->stage_ms[i];
+    if (launches) launches[i] = pl->stage_launches[i];
+  }
+  return FMM2D_OK;
+}
+
+void fmm2d_plan_destroy(fmm2d_plan *pl) {
+  if (!pl) return;
+  flush_events(pl);
+  for (auto ev : pl->ev_pool) cudaEventDestroy(ev);
+  DBuf *bufs[] = {&pl->d_key_s, &pl->d_perm_s, &pl->d_key_t, &pl->d_perm_t, &pl->d_tmp_k,
+                  &pl->d_tmp_v, &pl->d_sort_scratch, &pl->d_err, &pl->d_occ, &pl->d_hsrc,
+                  &pl->d_scan, &pl->d_map, &pl->d_cell_key, &pl->d_cell_crd, &pl->d_cell_ctr,
+                  &pl->d_cell_cls, &pl->d_cell_hsrc, &pl->d_src_start, &pl->d_src_end,
+                  &pl->d_tgt_start, &pl->d_tgt_end, &pl->d_lev_first, &pl->d_far_cnt,
+                  &pl->d_far_src, &pl->d_far_op, &pl->d_near_cnt, &pl->d_near_src, &pl->d_src4,
+                  &pl->d_tgt2, &pl->d_mQ, &pl->d_ma, &pl->d_lL0, &pl->d_lb, &pl->d_phi_near,
+                  &pl->d_phi_far, &pl->d_sten, &pl->d_geo_scale, &pl->d_m2l_ops, &pl->d_m2l_logz,
+                  &pl->d_m2m_ops, &pl->d_l2l_ops, &pl->d_counts};
+  for (DBuf *b : bufs) dbuf_free(*b);
+  delete pl;
+}
+
+const char *fmm2d_last_error(const fmm2d_plan *pl) {
+  if (!pl) return g_create_err.c_str();
+  return pl->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,172 @@
+// plan.h - internal plan object of the fmm2d library and the launchers of
+// every kernel (defined in keys.cu, sort.cu, tree.cu, expand.cu, p2p.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "fmm2d.h"
+
+namespace fmm2d {
+
+constexpr int MAXLEV = 23;
+constexpr int MAXP = 48;
+constexpr int MAX_CLASSES = 8;   // tri: 4 child types x 2 parent orientations
+constexpr int FAR_MAX = 48;      // longest M2L stencil (septree: 42)
+constexpr int NEAR_MAX = 16;     // longest Near stencil (triangle: 13)
+
+enum Stage { ST_KEYS, ST_SORT, ST_TREE, ST_LISTS, ST_P2M, ST_M2M, ST_M2L, ST_L2L, ST_L2P, ST_P2P,
+             ST_OTHER, ST_COUNT };
+
+// Grow-only device buffer owned by a plan.
+struct DBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+// Tiling geometry passed by value to kernels.
+struct Geo {
+  int tiling, L, b;
+  double x0, y0, S;
+  double leaf_scale;                 // sept r, tri rho0, quad 2^-L (frame units)
+  double unit_re[MAXLEV + 1];        // septree: level-l lattice unit g_l (frame)
+  double unit_im[MAXLEV + 1];
+  int64_t map_off[MAXLEV + 2];       // offset of level l in the key -> slot map
+};
+
+// Stencils of one plan (host copy; device copy in Plan::d_sten).
+struct Stencils {
+  int n_classes;
+  int far_len[MAX_CLASSES];
+  int far_d[MAX_CLASSES][FAR_MAX][3];      // lattice offsets
+  uint16_t far_op[MAX_CLASSES][FAR_MAX];   // M2L operator id of each entry
+  int near_len[2];
+  int near_d[2][NEAR_MAX][3];              // [orientation][entry] (quad/sept use [0])
+};
+
+struct Plan {
+  // parameters
+  int tiling = 0, levels_req = 0, p_req = 0;
+  double eps = 1e-6;
+  unsigned flags = 0;
+  double x0 = 0, y0 = 0, S = 1;
+  // derived at build
+  int L = 0, p = 0, P = 0, l_min = 0, b = 4;
+  Geo geo;
+  Stencils sten;
+  int n_ops = 0;
+  bool built = false, same_sets = false;
+  int64_t n_src = 0, n_tgt = 0;
+  int64_t map_size = 0;
+  int64_t lev_first[MAXLEV + 2] = {0}, lev_count[MAXLEV + 2] = {0};
+  int64_t n_cells = 0, n_far_cells = 0, n_m2l = 0, n_p2p_pairs = 0;
+  int max_far = 0, max_near = 0;
+  double scale_re[MAXLEV + 1], scale_im[MAXLEV + 1], log_abs_scale[MAXLEV + 1];
+  std::string err;
+  cudaStream_t last_stream = nullptr;
+  // profiling
+  bool profiling = false;
+  double stage_ms[ST_COUNT] = {0};
+  int64_t stage_launches[ST_COUNT] = {0};
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+  size_t ev_used = 0;
+
+  // device buffers
+  DBuf d_key_s, d_perm_s, d_key_t, d_perm_t, d_tmp_k, d_tmp_v, d_sort_scratch;
+  DBuf d_err;
+  DBuf d_occ, d_hsrc, d_scan, d_map;
+  DBuf d_cell_key, d_cell_crd, d_cell_ctr, d_cell_cls, d_cell_hsrc;
+  DBuf d_src_start, d_src_end, d_tgt_start, d_tgt_end, d_lev_first;
+  DBuf d_far_cnt, d_far_src, d_far_op, d_near_cnt, d_near_src;
+  DBuf d_src4, d_tgt2;
+  DBuf d_mQ, d_ma, d_lL0, d_lb;
+  DBuf d_phi_near, d_phi_far;
+  DBuf d_sten, d_geo_scale;
+  DBuf d_m2l_ops, d_m2l_logz, d_m2m_ops, d_l2l_ops;   // element type per precision
+  DBuf d_counts;
+  std::vector<double> m2l_logz_host;
+};
+
+// ---------------------------------------------------------------- helpers
+cudaError_t dbuf_reserve(DBuf &b, size_t bytes);
+void dbuf_free(DBuf &b);
+
+// ---------------------------------------------------------------- keys.cu
+cudaError_t launch_keys(const Geo &g, const void *xy, bool f32, int64_t n, uint32_t *key,
+                        uint32_t *perm_iota, int *err, cudaStream_t s);
+
+// ---------------------------------------------------------------- sort.cu
+size_t radix_sort_scratch_bytes(int64_t n);
+// Stable LSD sort of (key, val) pairs on the low `bits` bits; result in keys/vals.
+cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *tmp_k, uint32_t *tmp_v,
+                             int64_t n, int bits, void *scratch, cudaStream_t s);
+size_t scan_scratch_bytes(int64_t n);
+// Exclusive prefix sum of int32 values; out may alias in.
+cudaError_t exclusive_scan(const int *in, int *out, int64_t n, void *scratch, cudaStream_t s);
+
+// ---------------------------------------------------------------- tree.cu
+cudaError_t launch_mark(const Geo &g, const uint32_t *key_sorted, int64_t n, int *occ, int *hsrc,
+                        cudaStream_t s);
+cudaError_t launch_compact(const Geo &g, const int *occ, const int *scan, const int *hsrc,
+                           int64_t map_size, int *map, uint32_t *cell_key, int4 *cell_crd,
+                           double2 *cell_ctr, uint8_t *cell_cls, uint8_t *cell_hsrc, cudaStream_t s);
+cudaError_t launch_leaf_ranges(const Geo &g, const uint32_t *key_sorted, int64_t n, const int *map,
+                               int *start, int *end, cudaStream_t s);
+cudaError_t launch_rel_coords(const Geo &g, bool f32_in, bool f32_out, const void *xy,
+                              const uint32_t *perm, const uint32_t *key_sorted, int64_t n,
+                              const int *map, const double2 *ctr, void *out, int out_stride,
+                              cudaStream_t s);
+cudaError_t launch_level_first(const Geo &g, const int *scan, const int *occ, int64_t map_size,
+                               int64_t *out, cudaStream_t s);
+cudaError_t launch_lists2(const Geo &g, const Stencils *d_sten, int64_t first, int64_t count,
+                          const int *map, const uint8_t *cell_cls, const int4 *cell_crd,
+                          const uint8_t *cell_hsrc, int *far_cnt, int *far_src, uint16_t *far_op,
+                          int64_t leaf_first, int *near_cnt, int *near_src,
+                          const int64_t *lev_first_dev, cudaStream_t s);
+
+// ---------------------------------------------------------------- expand.cu
+struct ExpandArgs {
+  int p, P, L, l_min, b;
+  int64_t leaf_first, n_leaves;
+  double inv_s_re, inv_s_im;          // 1 / s_L
+};
+template <typename R>
+cudaError_t launch_gather_u(const void *u, bool f32_in, const uint32_t *perm, int64_t n, R *src4,
+                            cudaStream_t s);
+template <typename R>
+cudaError_t launch_p2m(const ExpandArgs &a, const R *src4, const int *start, const int *end,
+                       double *mQ, Cx<R> *ma, cudaStream_t s);
+template <typename R>
+cudaError_t launch_m2m(const ExpandArgs &a, const Geo &g, int level, int64_t first, int64_t count,
+                       const int *map, const uint32_t *cell_key, const uint8_t *cell_cls,
+                       const uint8_t *cell_hsrc, const Cx<R> *ops, double *mQ, Cx<R> *ma,
+                       cudaStream_t s);
+template <typename R>
+cudaError_t launch_m2l(const ExpandArgs &a, int64_t first, int64_t count, const int64_t *lev_of_cell_first,
+                       const double *log_abs_scale_dev, int64_t far_base, const int *far_cnt,
+                       const int *far_src, const uint16_t *far_op, const Cx<R> *ops,
+                       const double *logz, const double *mQ, const Cx<R> *ma, double *lL0,
+                       Cx<R> *lb, cudaStream_t s);
+template <typename R>
+cudaError_t launch_l2l(const ExpandArgs &a, const Geo &g, int level, int64_t first, int64_t count,
+                       const int *map, const uint32_t *cell_key, const uint8_t *cell_cls,
+                       const Cx<R> *ops, double *lL0, Cx<R> *lb, cudaStream_t s);
+template <typename R>
+cudaError_t launch_l2p(const ExpandArgs &a, const R *tgt, int tstride, const int *start,
+                       const int *end, const uint32_t *perm, const double *lL0, const Cx<R> *lb,
+                       const double *phi_near, double *phi_far, double *out, cudaStream_t s);
+
+// ---------------------------------------------------------------- p2p.cu
+template <typename R>
+cudaError_t launch_p2p(int64_t leaf_first, int64_t n_leaves, const R *src4, const R *tgt,
+                       int tstride, const int *src_start, const int *src_end,
+                       const int *tgt_start, const int *tgt_end, const int *near_cnt,
+                       const int *near_src, const double2 *ctr, double *phi_near,
+                       cudaStream_t s);
+
+}  // namespace fmm2d

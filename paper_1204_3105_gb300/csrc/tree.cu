@@ -1,0 +1,255 @@
+// tree.cu - occupied cells of every level, their lattice coordinates and
+// centres, per-leaf point ranges, and the Near / M2L lists (Sec. 4-6).
+//
+// Cells of all levels live in one array ordered by (level, key): a key ->
+// slot map of sum_l b^l entries is filled from an occupancy flag array
+// (every occupied leaf marks all its ancestors, Parent(n) = n div b) and one
+// exclusive scan.  Lists come from per-class integer stencils of lattice
+// offsets (the offsets of Neighbors and of NeighborsE4 = Children[Parent(n)
+// u Neighbors(Parent(n))] minus {n} u Neighbors(n), eq. 3), looked up in the
+// map; only cells holding sources enter a list.
+#include "plan.h"
+
+namespace fmm2d {
+
+namespace {
+
+__device__ __forceinline__ uint32_t parent_key(int tiling, uint32_t key, int up_levels) {
+  if (tiling == FMM2D_SEPT) {
+    for (int i = 0; i < up_levels; ++i) key /= 7u;
+    return key;
+  }
+  return key >> (2 * up_levels);
+}
+
+__global__ void k_mark(Geo g, const uint32_t *__restrict__ key, int64_t n, int *__restrict__ occ,
+                       int *__restrict__ hsrc) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t k = key[i];
+  if (i > 0 && key[i - 1] == k) return;
+  for (int l = g.L; l >= 0; --l) {
+    uint32_t kl = parent_key(g.tiling, k, g.L - l);
+    occ[g.map_off[l] + kl] = 1;
+    if (hsrc) hsrc[g.map_off[l] + kl] = 1;
+  }
+}
+
+__device__ __forceinline__ int level_of_map(const Geo &g, int64_t m) {
+  int l = 0;
+  while (l < g.L && m >= g.map_off[l + 1]) ++l;
+  return l;
+}
+
+__global__ void k_compact(Geo g, const int *__restrict__ occ, const int *__restrict__ scan,
+                          const int *__restrict__ hsrc, int64_t map_size, int *__restrict__ map,
+                          uint32_t *__restrict__ cell_key, int4 *__restrict__ cell_crd,
+                          double2 *__restrict__ cell_ctr, uint8_t *__restrict__ cell_cls,
+                          uint8_t *__restrict__ cell_hsrc) {
+  int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (m >= map_size) return;
+  if (!occ[m]) {
+    map[m] = -1;
+    return;
+  }
+  const int l = level_of_map(g, m);
+  const uint32_t key = (uint32_t)(m - g.map_off[l]);
+  const int slot = scan[m];
+  map[m] = slot;
+  cell_key[slot] = key;
+  cell_hsrc[slot] = (uint8_t)(hsrc[m] != 0);
+  int4 crd = make_int4(0, 0, 0, 0);
+  double X, Y;    // centre in the tiling frame
+  uint8_t cls = 0;
+  if (g.tiling == FMM2D_QUAD) {
+    int i = (int)compact_bits(key), j = (int)compact_bits(key >> 1);
+    crd = make_int4(i, j, 0, 0);
+    double h = ldexp(1.0, -l);
+    X = (i + 0.5) * h;
+    Y = (j + 0.5) * h;
+    cls = (uint8_t)(key & 3u);
+  } else if (g.tiling == FMM2D_SEPT) {
+    int64_t a, b;
+    key_to_eis(key, l, &a, &b);
+    crd = make_int4((int)a, (int)b, 0, 0);
+    // frame centre g_l (a + b w), w = e^{i pi/3}
+    double er = (double)a + 0.5 * (double)b, ei = 0.8660254037844386 * (double)b;
+    X = g.unit_re[l] * er - g.unit_im[l] * ei;
+    Y = g.unit_re[l] * ei + g.unit_im[l] * er;
+    cls = (uint8_t)(key % 7u);
+  } else {
+    int i, j, k;
+    tri_key_to_coords(key, l, &i, &j, &k);
+    bool up = tri_up(i, j, k, l);
+    crd = make_int4(i, j, k, up ? 1 : 0);
+    double o = up ? 1.0 : 2.0, rho0 = g.leaf_scale, inv = ldexp(1.0, -l);
+    Y = rho0 * (3.0 * i + o) * inv - rho0;
+    X = 1.7320508075688772 * rho0 * (double)(k - j) * inv;
+    if (l > 0) {
+      bool pup = tri_up(i >> 1, j >> 1, k >> 1, l - 1);
+      cls = (uint8_t)((key & 3u) + (pup ? 0u : 4u));
+    }
+  }
+  if (g.tiling != FMM2D_QUAD) {
+    X += 0.5;
+    Y += 0.5;
+  }
+  cell_crd[slot] = crd;
+  cell_ctr[slot] = make_double2(g.x0 + g.S * X, g.y0 + g.S * Y);
+  cell_cls[slot] = cls;
+}
+
+__global__ void k_level_first(Geo g, const int *__restrict__ scan, const int *__restrict__ occ,
+                              int64_t map_size, int64_t *__restrict__ out) {
+  int l = threadIdx.x;
+  if (l <= g.L) out[l] = scan[g.map_off[l]];
+  if (l == g.L + 1) out[l] = (int64_t)scan[map_size - 1] + occ[map_size - 1];
+}
+
+__global__ void k_leaf_ranges(Geo g, const uint32_t *__restrict__ key, int64_t n,
+                              const int *__restrict__ map, int *__restrict__ start,
+                              int *__restrict__ end) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t k = key[i];
+  int slot = map[g.map_off[g.L] + k];
+  if (i == 0 || key[i - 1] != k) start[slot] = (int)i;
+  if (i == n - 1 || key[i + 1] != k) end[slot] = (int)(i + 1);
+}
+
+template <typename TI, typename TO>
+__global__ void k_rel(Geo g, const TI *__restrict__ xy, const uint32_t *__restrict__ perm,
+                      const uint32_t *__restrict__ key, int64_t n, const int *__restrict__ map,
+                      const double2 *__restrict__ ctr, TO *__restrict__ out, int stride) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t o = perm[i];
+  int slot = map[g.map_off[g.L] + key[i]];
+  double2 c = ctr[slot];
+  double x = (double)xy[2 * (int64_t)o], y = (double)xy[2 * (int64_t)o + 1];
+  TO *dst = out + i * stride;
+  dst[0] = (TO)(x - c.x);
+  dst[1] = (TO)(y - c.y);
+  for (int q = 2; q < stride; ++q) dst[q] = (TO)0;
+}
+
+// Key of the level-l cell at lattice coordinates c, or false if none.
+__device__ __forceinline__ bool cell_at(const Geo &g, int l, int4 c, uint32_t *key) {
+  if (g.tiling == FMM2D_QUAD) {
+    int n = 1 << l;
+    if (c.x < 0 || c.y < 0 || c.x >= n || c.y >= n) return false;
+    *key = morton((uint32_t)c.x, (uint32_t)c.y);
+    return true;
+  }
+  if (g.tiling == FMM2D_SEPT) return eis_to_key(c.x, c.y, l, key);
+  return tri_coords_to_key(c.x, c.y, c.z, l, key);
+}
+
+__global__ void k_lists(Geo g, const Stencils *__restrict__ st, int64_t first, int64_t count,
+                        const int *__restrict__ map, const uint8_t *__restrict__ cell_cls,
+                        const int4 *__restrict__ cell_crd, const uint8_t *__restrict__ cell_hsrc,
+                        int64_t lev_first_lmin, int *__restrict__ far_cnt,
+                        int *__restrict__ far_src, uint16_t *__restrict__ far_op,
+                        int64_t leaf_first, int *__restrict__ near_cnt, int *__restrict__ near_src,
+                        const int64_t *__restrict__ lev_first) {
+  int64_t gslot = first + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gslot >= first + count) return;
+  int l = 0;
+  while (l < g.L && gslot >= lev_first[l + 1]) ++l;
+  const int4 c = cell_crd[gslot];
+  const int cls = cell_cls[gslot];
+  const int64_t fi = gslot - lev_first_lmin;
+  int cnt = 0;
+  for (int e = 0; e < st->far_len[cls]; ++e) {
+    int4 q = make_int4(c.x + st->far_d[cls][e][0], c.y + st->far_d[cls][e][1],
+                       c.z + st->far_d[cls][e][2], 0);
+    uint32_t k;
+    if (!cell_at(g, l, q, &k)) continue;
+    int s = map[g.map_off[l] + k];
+    if (s < 0 || !cell_hsrc[s]) continue;
+    far_src[fi * FAR_MAX + cnt] = s;
+    far_op[fi * FAR_MAX + cnt] = st->far_op[cls][e];
+    ++cnt;
+  }
+  far_cnt[fi] = cnt;
+  if (gslot >= leaf_first) {
+    const int o = (g.tiling == FMM2D_TRI && c.w == 0) ? 1 : 0;
+    const int64_t ni = gslot - leaf_first;
+    int nc = 0;
+    for (int e = 0; e < st->near_len[o]; ++e) {
+      int4 q = make_int4(c.x + st->near_d[o][e][0], c.y + st->near_d[o][e][1],
+                         c.z + st->near_d[o][e][2], 0);
+      uint32_t k;
+      if (!cell_at(g, l, q, &k)) continue;
+      int s = map[g.map_off[l] + k];
+      if (s < 0 || !cell_hsrc[s]) continue;
+      near_src[ni * NEAR_MAX + nc] = s;
+      ++nc;
+    }
+    near_cnt[ni] = nc;
+  }
+}
+
+inline unsigned nblk(int64_t n, int th) { return (unsigned)((n + th - 1) / th); }
+
+}  // namespace
+
+cudaError_t launch_mark(const Geo &g, const uint32_t *key_sorted, int64_t n, int *occ, int *hsrc,
+                        cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_mark<<<nblk(n, 256), 256, 0, s>>>(g, key_sorted, n, occ, hsrc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const Geo &g, const int *occ, const int *scan, const int *hsrc,
+                           int64_t map_size, int *map, uint32_t *cell_key, int4 *cell_crd,
+                           double2 *cell_ctr, uint8_t *cell_cls, uint8_t *cell_hsrc,
+                           cudaStream_t s) {
+  k_compact<<<nblk(map_size, 256), 256, 0, s>>>(g, occ, scan, hsrc, map_size, map, cell_key,
+                                                 cell_crd, cell_ctr, cell_cls, cell_hsrc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_level_first(const Geo &g, const int *scan, const int *occ, int64_t map_size,
+                               int64_t *out, cudaStream_t s) {
+  k_level_first<<<1, 64, 0, s>>>(g, scan, occ, map_size, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_ranges(const Geo &g, const uint32_t *key_sorted, int64_t n, const int *map,
+                               int *start, int *end, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_leaf_ranges<<<nblk(n, 256), 256, 0, s>>>(g, key_sorted, n, map, start, end);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rel_coords(const Geo &g, bool f32_in, bool f32_out, const void *xy,
+                              const uint32_t *perm, const uint32_t *key_sorted, int64_t n,
+                              const int *map, const double2 *ctr, void *out, int out_stride,
+                              cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  unsigned b = nblk(n, 256);
+  if (f32_in && f32_out)
+    k_rel<float, float><<<b, 256, 0, s>>>(g, (const float *)xy, perm, key_sorted, n, map, ctr, (float *)out, out_stride);
+  else if (f32_in)
+    k_rel<float, double><<<b, 256, 0, s>>>(g, (const float *)xy, perm, key_sorted, n, map, ctr, (double *)out, out_stride);
+  else if (f32_out)
+    k_rel<double, float><<<b, 256, 0, s>>>(g, (const double *)xy, perm, key_sorted, n, map, ctr, (float *)out, out_stride);
+  else
+    k_rel<double, double><<<b, 256, 0, s>>>(g, (const double *)xy, perm, key_sorted, n, map, ctr, (double *)out, out_stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lists2(const Geo &g, const Stencils *d_sten, int64_t first, int64_t count,
+                          const int *map, const uint8_t *cell_cls, const int4 *cell_crd,
+                          const uint8_t *cell_hsrc, int *far_cnt, int *far_src, uint16_t *far_op,
+                          int64_t leaf_first, int *near_cnt, int *near_src,
+                          const int64_t *lev_first_dev, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_lists<<<nblk(count, 128), 128, 0, s>>>(g, d_sten, first, count, map, cell_cls, cell_crd,
+                                            cell_hsrc, first, far_cnt, far_src, far_op, leaf_first,
+                                            near_cnt, near_src, lev_first_dev);
+  return cudaGetLastError();
+}
+
+}  // namespace fmm2d

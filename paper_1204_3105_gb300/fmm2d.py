@@ -1,0 +1,203 @@
+"""Thin ctypes binding of libfmm2d (include/fmm2d.h): argument marshalling only.
+
+Every function of the C ABI is exposed under the same name; ``Plan`` wraps a
+plan handle.  Device buffers may be given as integers (device pointers) or as
+objects with ``data_ptr()`` (e.g. torch CUDA tensors); a stream may be an
+integer cudaStream_t, an object with ``cuda_stream``, or None for the legacy
+default stream.  The library is loaded from this package directory; if it
+has not been built the import of ``lib()`` raises - there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfmm2d.so")
+
+QUAD, SEPT, TRI = 0, 1, 2
+TILINGS = {"quad": QUAD, "sept": SEPT, "tri": TRI}
+PREC_FP64, PREC_MIXED, PREC_MIXED_TC = 0x0, 0x1, 0x2
+IN_F32 = 0x10
+
+OK, EINVAL, ENOMEM, EDOMAIN, ECUDA, EBUSY, ETIMEOUT, ENOTREADY = range(8)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "EDOMAIN", "ECUDA", "EBUSY", "ETIMEOUT", "ENOTREADY"]
+STAGES = ["keys", "sort", "tree", "lists", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "other"]
+
+EXPORTS = {"src_keys": 1, "src_perm": 2, "tgt_keys": 3, "tgt_perm": 4, "cells": 5, "near": 6,
+           "far": 7, "multipoles": 8, "locals": 9, "phi_near": 10, "phi_far": 11, "centers": 12}
+
+SYMBOLS = ["fmm2d_default_params", "fmm2d_plan_create", "fmm2d_plan_set_domain", "fmm2d_build",
+           "fmm2d_evaluate", "fmm2d_plan_query", "fmm2d_debug_export", "fmm2d_plan_set_profiling",
+           "fmm2d_stage_times", "fmm2d_plan_destroy", "fmm2d_last_error"]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("tiling", ctypes.c_int32), ("levels", ctypes.c_int32), ("p", ctypes.c_int32),
+                ("l_min", ctypes.c_int32), ("flags", ctypes.c_uint32), ("built", ctypes.c_int32),
+                ("eps", ctypes.c_double), ("domain", ctypes.c_double * 3),
+                ("leaf_scale", ctypes.c_double), ("n_src", ctypes.c_int64),
+                ("n_tgt", ctypes.c_int64), ("n_cells", ctypes.c_int64 * 24),
+                ("n_m2l", ctypes.c_int64), ("n_p2p_pairs", ctypes.c_int64),
+                ("n_m2l_ops", ctypes.c_int32), ("max_far", ctypes.c_int32),
+                ("max_near", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class FMM2DError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < 8 else status, msg))
+        self.status = status
+
+
+_LIB = None
+
+
+def lib():
+    """Load libfmm2d.so (raises if it is missing) and declare its signatures."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libfmm2d.so is not built (run __graft_entry__.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, c_int, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    L.fmm2d_default_params.argtypes = [c_int, i64, c_int, dbl, ctypes.POINTER(c_int),
+                                       ctypes.POINTER(c_int), ctypes.POINTER(dbl)]
+    L.fmm2d_plan_create.argtypes = [c_int, c_int, c_int, dbl, ctypes.c_uint, ctypes.POINTER(vp)]
+    L.fmm2d_plan_set_domain.argtypes = [vp, dbl, dbl, dbl]
+    L.fmm2d_build.argtypes = [vp, vp, i64, vp, i64, vp]
+    L.fmm2d_evaluate.argtypes = [vp, vp, vp, vp]
+    L.fmm2d_plan_query.argtypes = [vp, ctypes.POINTER(Info)]
+    L.fmm2d_debug_export.argtypes = [vp, c_int, c_int, vp, ctypes.c_size_t,
+                                     ctypes.POINTER(ctypes.c_size_t)]
+    L.fmm2d_plan_set_profiling.argtypes = [vp, c_int]
+    L.fmm2d_stage_times.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64), c_int,
+                                    ctypes.POINTER(c_int)]
+    L.fmm2d_plan_destroy.argtypes = [vp]
+    L.fmm2d_plan_destroy.restype = None
+    L.fmm2d_last_error.argtypes = [vp]
+    L.fmm2d_last_error.restype = ctypes.c_char_p
+    for name in SYMBOLS:
+        if name not in ("fmm2d_plan_destroy", "fmm2d_last_error"):
+            getattr(L, name).restype = c_int
+    _LIB = L
+    return L
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return int(x)
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    return int(s)
+
+
+def fmm2d_default_params(tiling, n_points, leaf_target=64, eps=1e-6):
+    L, p = ctypes.c_int(), ctypes.c_int()
+    r = ctypes.c_double()
+    st = lib().fmm2d_default_params(TILINGS.get(tiling, tiling), int(n_points), int(leaf_target),
+                                    float(eps), ctypes.byref(L), ctypes.byref(p), ctypes.byref(r))
+    if st:
+        raise FMM2DError(st, "fmm2d_default_params")
+    return L.value, p.value, r.value
+
+
+class Plan:
+    """A plan handle: ``fmm2d_plan_create`` on construction,
+    ``fmm2d_plan_destroy`` on ``close``."""
+
+    def __init__(self, tiling, levels=0, p=0, eps=1e-6, flags=PREC_MIXED):
+        self._h = ctypes.c_void_p()
+        self.lib = lib()
+        st = self.lib.fmm2d_plan_create(TILINGS.get(tiling, tiling), int(levels), int(p),
+                                        float(eps), int(flags), ctypes.byref(self._h))
+        if st:
+            raise FMM2DError(st, self.lib.fmm2d_last_error(None).decode())
+        self.flags = flags
+
+    def _check(self, st, what):
+        if st:
+            raise FMM2DError(st, "%s: %s" % (what, self.lib.fmm2d_last_error(self._h).decode()))
+
+    def fmm2d_plan_set_domain(self, x0, y0, size):
+        self._check(self.lib.fmm2d_plan_set_domain(self._h, float(x0), float(y0), float(size)),
+                    "set_domain")
+
+    set_domain = fmm2d_plan_set_domain
+
+    def fmm2d_build(self, src_xy, n_src, tgt_xy, n_tgt, stream=None):
+        self._check(self.lib.fmm2d_build(self._h, _ptr(src_xy), int(n_src), _ptr(tgt_xy),
+                                         int(n_tgt), _stream(stream)), "build")
+
+    build = fmm2d_build
+
+    def fmm2d_evaluate(self, strengths, potentials, stream=None):
+        self._check(self.lib.fmm2d_evaluate(self._h, _ptr(strengths), _ptr(potentials),
+                                            _stream(stream)), "evaluate")
+
+    evaluate = fmm2d_evaluate
+
+    def fmm2d_plan_query(self):
+        info = Info()
+        self._check(self.lib.fmm2d_plan_query(self._h, ctypes.byref(info)), "query")
+        d = {f: getattr(info, f) for f, _ in Info._fields_}
+        d["domain"] = list(info.domain)
+        d["n_cells"] = list(info.n_cells)[: max(0, info.levels) + 1]
+        return d
+
+    query = fmm2d_plan_query
+
+    def fmm2d_debug_export(self, what, level=0):
+        w = EXPORTS.get(what, what)
+        n = ctypes.c_size_t()
+        self._check(self.lib.fmm2d_debug_export(self._h, w, int(level), None, 0, ctypes.byref(n)),
+                    "export")
+        buf = np.zeros(max(1, n.value), np.uint8)
+        self._check(self.lib.fmm2d_debug_export(self._h, w, int(level), buf.ctypes.data, buf.nbytes,
+                                                ctypes.byref(n)), "export")
+        buf = buf[: n.value]
+        if w in (1, 2, 3, 4, 5):
+            return buf.view(np.int64)
+        if w in (6, 7):
+            return buf.view(np.int64).reshape(-1, 2)
+        if w in (8, 9):
+            p = self.query()["p"]
+            return buf.view(np.complex128).reshape(-1, p + 1)
+        if w == 12:
+            return buf.view(np.complex128)
+        return buf.view(np.float64)
+
+    export = fmm2d_debug_export
+
+    def fmm2d_plan_set_profiling(self, on=True):
+        self._check(self.lib.fmm2d_plan_set_profiling(self._h, 1 if on else 0), "profiling")
+
+    set_profiling = fmm2d_plan_set_profiling
+
+    def fmm2d_stage_times(self):
+        ms = (ctypes.c_double * 16)()
+        ln = (ctypes.c_int64 * 16)()
+        n = ctypes.c_int()
+        self._check(self.lib.fmm2d_stage_times(self._h, ms, ln, 16, ctypes.byref(n)), "stage_times")
+        return {STAGES[i]: (ms[i], ln[i]) for i in range(min(n.value, len(STAGES)))}
+
+    stage_times = fmm2d_stage_times
+
+    def close(self):
+        if self._h:
+            self.lib.fmm2d_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,64 @@
+"""CPU checks of the C ABI library: it builds, loads, exports every symbol
+include/fmm2d.h declares, and its planner rules agree with the oracle's."""
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+from oracle import params as op
+
+
+@pytest.fixture(scope="module")
+def fm():
+    from paper_1204_3105_gb300 import build, fmm2d
+    build.build()
+    fmm2d.lib()
+    return fmm2d
+
+
+def _declared():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names.update(re.findall(r"\b(fmm2d_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_exports_every_declared_symbol(fm):
+    names = _declared()
+    assert "fmm2d_build" in names and "fmm2d_evaluate" in names
+    L = fm.lib()
+    for n in sorted(names):
+        assert hasattr(L, n), n
+    assert set(fm.SYMBOLS) <= names
+
+
+@pytest.mark.parametrize("tiling", ["quad", "sept", "tri"])
+def test_planner_rules_match_oracle(fm, tiling):
+    for n in (1000, 8192, 100000, 2 ** 20, 4 * 10 ** 6):
+        L, p, r = fm.fmm2d_default_params(tiling, n, 64, 1e-6)
+        assert L == op.auto_levels(tiling, n)
+        assert p == op.p_from_eps(tiling, 1e-6)
+        if tiling == "sept":
+            assert r == op.sept_leaf_circumradius(L)          # bit-exact
+        elif tiling == "tri":
+            assert r == op.tri_root_inradius()
+    for eps in (1e-3, 1e-4, 1e-8, 1e-10):
+        assert fm.fmm2d_default_params(tiling, 1000, 64, eps)[1] == op.p_from_eps(tiling, eps)
+
+
+def test_bad_arguments_rejected_without_gpu(fm):
+    with pytest.raises(fm.FMM2DError) as e:
+        fm.Plan("quad", levels=40)
+    assert e.value.status == fm.EINVAL
+    with pytest.raises(fm.FMM2DError):
+        fm.Plan(7)
+    with pytest.raises(fm.FMM2DError):
+        fm.Plan("quad", p=0, eps=2.0)
+    with pytest.raises(fm.FMM2DError):
+        fm.fmm2d_default_params("quad", 100, 64, 0.0)

@@ -1,0 +1,163 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Integer work (keys, sort permutation, cells, lists) is compared bit for bit.
+Potentials: the FP64 GPU form must match the FP64 oracle FMM of the same
+(L, p) to 1e-11 relative (eps_rel_inf; only the summation order differs);
+the mixed form (FP32 expansions and P2P, FP64 leading term) to 1e-6, the
+tolerance requested of the configurations (relative eps = 1e-6).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_util import run_gpu
+from oracle.direct import direct, rel_inf_error
+from oracle.fmm import fmm, make_tiling
+from paper_1204_3105_gb300.inputs import gaussian_mixture, sample_targets, uniform_square
+
+pytestmark = pytest.mark.gpu
+
+CASES = [("quad", 4, 12), ("sept", 3, 12), ("tri", 4, 12)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1204_3105_gb300 import build, fmm2d
+    build.build()
+    fmm2d.lib()
+
+
+def _oracle(tiling, L, src, u, tgt, p, domain=(0.0, 0.0, 1.0)):
+    T = make_tiling(tiling, L, domain)
+    return fmm(T, src, u, src if tgt is None else tgt, p, record=True), T
+
+
+@pytest.mark.parametrize("tiling,L,p", CASES)
+@pytest.mark.parametrize("n", [1, 37, 4099, 20011])
+def test_keys_sort_cells_lists_bitexact(tiling, L, p, n):
+    xy, u = uniform_square(n, seed=100 + n)
+    phi, plan = run_gpu(tiling, xy, u, levels=L, p=p, prec="fp64", keep=True)
+    r, T = _oracle(tiling, L, xy, u, None, p)
+    assert np.array_equal(plan.export("src_keys"), r.src_keys)
+    assert np.array_equal(plan.export("src_perm"), r.src_perm)      # stable sort
+    for l in range(L + 1):
+        assert np.array_equal(plan.export("cells", l), np.array(r.cells[l], np.int64))
+    near = {tuple(x) for x in plan.export("near").tolist()}
+    want = {(t, s) for t, lst in r.near.items() for s in lst}
+    assert near == want
+    for l in range(T.l_min, L + 1):
+        far = {tuple(x) for x in plan.export("far", l).tolist()}
+        want = {(n_, m) for (ll, n_), lst in r.far.items() if ll == l for m in lst}
+        assert far == want, (tiling, l)
+    # cell centres agree with CellCenter of the paper (eqs. 6, 12)
+    for l in (0, L):
+        c = plan.export("centers", l)
+        want = np.array([T.center(int(k), l) for k in r.cells[l]])
+        assert np.max(np.abs(c - want), initial=0) < 1e-12
+    plan.close()
+
+
+@pytest.mark.parametrize("tiling,L,p", CASES)
+def test_fp64_path_matches_oracle(tiling, L, p):
+    n = 6007
+    xy, u = uniform_square(n, seed=5)
+    phi, plan = run_gpu(tiling, xy, u, levels=L, p=p, prec="fp64", keep=True)
+    r, T = _oracle(tiling, L, xy, u, None, p)
+    assert rel_inf_error(phi, r.phi) < 1e-11
+    assert rel_inf_error(plan.export("phi_near"), r.phi_near) < 1e-11
+    # multipoles and locals per level, unscaled, against the oracle's
+    for l in range(T.l_min, L + 1):
+        mg = plan.export("multipoles", l)
+        lg = plan.export("locals", l)
+        cells = r.cells[l]
+        for i, key in enumerate(cells):
+            if (l, key) in r.mult:
+                Q, a = r.mult[(l, key)]
+                assert abs(mg[i, 0].real - Q) <= 1e-12 * max(1.0, abs(Q))
+                scale = np.abs(a).max() + 1e-300
+                assert np.max(np.abs(mg[i, 1:] - a)) <= 1e-10 * scale
+            b = r.loc[(l, key)]
+            assert abs(lg[i, 0].real - b[0].real) <= 1e-10 * max(1.0, np.abs(b).max())
+            assert np.max(np.abs(lg[i, 1:] - b[1:])) <= 1e-9 * (np.abs(b[1:]).max() + 1e-300)
+    plan.close()
+
+
+@pytest.mark.parametrize("tiling,L,p", CASES)
+@pytest.mark.parametrize("f32", [False, True])
+def test_mixed_path_matches_oracle(tiling, L, p, f32):
+    n = 12007
+    xy, u = uniform_square(n, seed=9, dtype=np.float32 if f32 else np.float64)
+    phi, _ = run_gpu(tiling, xy, u, levels=L, p=p, prec="mixed", f32=f32)
+    r, _ = _oracle(tiling, L, xy.astype(np.float64), u.astype(np.float64), None, p)
+    assert rel_inf_error(phi, r.phi) < 1e-6
+
+
+def test_separate_targets_domain_and_clusters():
+    rng = np.random.default_rng(3)
+    dom = (-2.0, 1.0, 3.0)
+    src = np.column_stack([dom[0] + dom[2] * rng.random(5000), dom[1] + dom[2] * rng.random(5000)])
+    tgt = np.column_stack([dom[0] + dom[2] * rng.random(3001), dom[1] + dom[2] * rng.random(3001)])
+    tgt[:7] = src[:7]
+    u = rng.normal(size=5000)
+    ref = direct(src, u, tgt)
+    for tiling, L in (("quad", 4), ("sept", 3), ("tri", 4)):
+        phi, _ = run_gpu(tiling, src, u, tgt, levels=L, p=30, prec="fp64", domain=dom)
+        assert rel_inf_error(phi, ref) < 1e-11
+        phi, _ = run_gpu(tiling, src, u, tgt, levels=L, p=20, prec="mixed", domain=dom)
+        assert rel_inf_error(phi, ref) < 2e-6
+    xy, uu = gaussian_mixture(20000, seed=3, k=8)
+    ref = direct(xy, uu, xy)
+    for tiling, L in (("quad", 5), ("sept", 4), ("tri", 5)):
+        phi, _ = run_gpu(tiling, xy, uu, levels=L, p=24, prec="fp64")
+        assert rel_inf_error(phi, ref) < 1e-9
+
+
+def test_points_on_cell_edges():
+    # points exactly on quadtree lines and lattice-aligned coordinates
+    g = np.arange(64) / 64.0
+    xy = np.array([(a, b) for a in g for b in g[::3]])
+    u = np.cos(np.arange(len(xy)))
+    ref = direct(xy, u, xy)
+    for tiling, L in (("quad", 3), ("sept", 3), ("tri", 3)):
+        phi, plan = run_gpu(tiling, xy, u, levels=L, p=30, prec="fp64", keep=True)
+        r, _ = _oracle(tiling, L, xy, u, None, 30)
+        assert np.array_equal(plan.export("src_keys"), r.src_keys)
+        assert rel_inf_error(phi, ref) < 1e-10
+        plan.close()
+
+
+def test_domain_error_and_empty():
+    from paper_1204_3105_gb300 import fmm2d
+    xy = np.array([[0.5, 0.5], [1.5, 0.2]])
+    with pytest.raises(fmm2d.FMM2DError) as e:
+        run_gpu("quad", xy, np.ones(2), levels=2, p=4)
+    assert e.value.status == fmm2d.EDOMAIN
+    # no targets / no sources
+    src, u = uniform_square(100, seed=1)
+    phi, _ = run_gpu("tri", src, u, np.zeros((0, 2)), levels=3, p=8)
+    assert phi.shape == (0,)
+    phi, _ = run_gpu("sept", np.zeros((0, 2)), np.zeros(0), src, levels=3, p=8)
+    assert np.all(phi == 0)
+
+
+@pytest.mark.parametrize("tiling", ["quad", "sept", "tri"])
+def test_full_size_sampled(tiling):
+    """N = M = 2^20 uniform points, FP32 inputs, eps = 1e-6 with the planner's
+    L and p (the benchmark configuration): keys bit-exact against the oracle's
+    CellIndex, potentials against direct summation on 384 sampled targets."""
+    n = 2 ** 20
+    xy, u = uniform_square(n, seed=2, dtype=np.float32)
+    phi, plan = run_gpu(tiling, xy, u, prec="mixed", f32=True, eps=1e-6, keep=True)
+    info = plan.query()
+    T = make_tiling(tiling, info["levels"])
+    x64 = xy.astype(np.float64)
+    assert np.array_equal(plan.export("src_keys"), T.keys(x64[:, 0], x64[:, 1]))
+    plan.close()
+    idx = sample_targets(n, 384, seed=2)
+    ref = direct(x64, u.astype(np.float64), x64[idx])
+    err = np.max(np.abs(phi[idx] - ref)) / np.max(np.abs(ref))
+    assert err < 1e-6, err
