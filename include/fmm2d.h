@@ -207,6 +207,42 @@ void fmm2d_plan_destroy(fmm2d_plan *plan);
  * error of a failed fmm2d_plan_create on this thread. */
 const char *fmm2d_last_error(const fmm2d_plan *plan);
 
+/*
+ * fmm2d_keys_sort_noalloc - leaf keys of a point set and their stable sort,
+ * for callers that cannot allocate GPU memory.  The paper has no
+ * counterpart: this is a library convenience, not a step of the method.
+ *
+ * Who needs it: code that runs where cudaMalloc is not allowed - inside a
+ * memory arena owned by someone else, in a stream-ordered region that must
+ * not synchronise on the allocator, or under a framework that forbids
+ * allocations outside its own pool.  It does the keying (CellIndex, Sec. 4-6)
+ * and sorting steps of fmm2d_build without creating a plan and without
+ * allocating anything: the sort temporaries live in a static device array of
+ * about 8.5 MiB that every GPU loading the library keeps until the process
+ * exits.
+ *   tiling, levels: as fmm2d_plan_create (levels >= 1).
+ *   leaf_scale: septree only - the leaf circumradius that
+ *     fmm2d_default_params returns for `levels`; ignored otherwise.
+ *   domain: NULL for the unit square, else {x0, y0, S}.
+ *   xy_dev: n interleaved points (float64, or float32 with FMM2D_IN_F32 in
+ *     flags), 0 <= n <= 1048576 (larger n: FMM2D_EINVAL, use fmm2d_build).
+ *   keys_sorted_dev, perm_dev: n uint32 outputs (caller-owned device memory):
+ *     the leaf keys in ascending order and, for each sorted position, the
+ *     input index (equal keys keep their input order) - the same values
+ *     fmm2d_debug_export reports for a plan built on these points.
+ *   err_buf / err_cap: optional caller buffer that receives the error text.
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress; make that first call before any stream capture.
+ * The call waits for its own work (it reads back the domain-error flag).
+ * All calls share the array, so calls whose GPU work overlaps race and must
+ * be serialised by the caller.  Errors: FMM2D_EINVAL, FMM2D_EDOMAIN,
+ * FMM2D_ECUDA.
+ */
+fmm2d_status fmm2d_keys_sort_noalloc(int tiling, int levels, double leaf_scale,
+                                     const double *domain, const void *xy_dev, int64_t n,
+                                     unsigned flags, uint32_t *keys_sorted_dev, uint32_t *perm_dev,
+                                     void *stream, char *err_buf, size_t err_cap);
+
 #ifdef __cplusplus
 }
 #endif

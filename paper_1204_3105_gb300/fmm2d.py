@@ -29,7 +29,8 @@ EXPORTS = {"src_keys": 1, "src_perm": 2, "tgt_keys": 3, "tgt_perm": 4, "cells": 
 
 SYMBOLS = ["fmm2d_default_params", "fmm2d_plan_create", "fmm2d_plan_set_domain", "fmm2d_build",
            "fmm2d_evaluate", "fmm2d_plan_query", "fmm2d_debug_export", "fmm2d_plan_set_profiling",
-           "fmm2d_stage_times", "fmm2d_plan_destroy", "fmm2d_last_error"]
+           "fmm2d_stage_times", "fmm2d_plan_destroy", "fmm2d_last_error",
+           "fmm2d_keys_sort_noalloc"]
 
 
 class Info(ctypes.Structure):
@@ -77,6 +78,9 @@ def lib():
     L.fmm2d_plan_destroy.restype = None
     L.fmm2d_last_error.argtypes = [vp]
     L.fmm2d_last_error.restype = ctypes.c_char_p
+    L.fmm2d_keys_sort_noalloc.argtypes = [c_int, c_int, dbl, ctypes.POINTER(dbl), vp, i64,
+                                          ctypes.c_uint, vp, vp, vp, ctypes.c_char_p,
+                                          ctypes.c_size_t]
     for name in SYMBOLS:
         if name not in ("fmm2d_plan_destroy", "fmm2d_last_error"):
             getattr(L, name).restype = c_int
@@ -108,6 +112,20 @@ def fmm2d_default_params(tiling, n_points, leaf_target=64, eps=1e-6):
     if st:
         raise FMM2DError(st, "fmm2d_default_params")
     return L.value, p.value, r.value
+
+
+def fmm2d_keys_sort_noalloc(tiling, levels, leaf_scale, domain, xy, n, flags, keys_out,
+                            perm_out, stream=None):
+    """Leaf keys and stable sort permutation without any GPU allocation (see
+    include/fmm2d.h); keys_out / perm_out are caller-owned n-element uint32
+    (or int32) device buffers."""
+    buf = ctypes.create_string_buffer(256)
+    dom = None if domain is None else (ctypes.c_double * 3)(*domain)
+    st = lib().fmm2d_keys_sort_noalloc(TILINGS.get(tiling, tiling), int(levels), float(leaf_scale),
+                                       dom, _ptr(xy), int(n), int(flags), _ptr(keys_out),
+                                       _ptr(perm_out), _stream(stream), buf, 256)
+    if st:
+        raise FMM2DError(st, buf.value.decode())
 
 
 class Plan:
