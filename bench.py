@@ -158,7 +158,7 @@ def run_ours(args):
     xy_d = torch.from_numpy(xy).to(dev)
     u_d = torch.from_numpy(u).to(dev)
     outs = {t: torch.empty(N_POINTS, dtype=torch.float64, device=dev) for t in args.tilings}
-    prec = {"mixed": fmm2d.PREC_MIXED, "fp64": fmm2d.PREC_FP64}[args.prec]
+    prec = {"tc": fmm2d.PREC_MIXED_TC, "mixed": fmm2d.PREC_MIXED, "fp64": fmm2d.PREC_FP64}[args.prec]
     plans = {t: fmm2d.Plan(t, 0, 0, EPS, prec | fmm2d.IN_F32) for t in args.tilings}
     flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device=dev)   # 256 MB > L2
 
@@ -256,7 +256,7 @@ def run_ours(args):
             "metric": "FMM eval points/s at eps=1e-6 (3 tilings)", "value": value, "unit": "points/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64" if args.prec == "mixed" else "f64", "data": "synthetic",
+            "dtype": "f64" if args.prec == "fp64" else "tf32x3+f32+f64", "data": "synthetic",
             "config": {"workload": "N=M=2^20 uniform unit square (sources=targets), FP32 points and "
                                    "strengths, quad+sept+tri, eps=1e-6, planner L/p, %s form" % args.prec,
                        "global_batch": N_POINTS, "l2": "flushed between tilings (256 MB write)",
@@ -290,7 +290,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--prec", default="tc", choices=["tc", "mixed", "fp64"])
     ap.add_argument("--tilings", default=",".join(TILINGS))
     ap.add_argument("--ref-points", type=int, default=16384)
     ap.add_argument("--no-cpu-baseline", action="store_true")

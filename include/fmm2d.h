@@ -89,7 +89,8 @@ typedef struct {
   int32_t n_m2l_ops;       /* distinct M2L operators (lattice offsets) */
   int32_t max_far;         /* longest M2L list (P4 of Table 2 for interior cells) */
   int32_t max_near;        /* longest Near list (P2 of Table 2) */
-  int32_t reserved;
+  int32_t device_error;    /* nonzero if a kernel of the last evaluation gave up a
+                              bounded wait (results of that evaluation invalid) */
 } fmm2d_info;
 
 /*

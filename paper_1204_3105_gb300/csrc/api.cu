@@ -6,6 +6,7 @@
 #include <climits>
 #include <cmath>
 #include <complex>
+#include <cstddef>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -436,6 +437,20 @@ fmm2d_status setup_geometry(fmm2d_plan *pl) {
     return cudaMemcpy(b.p, f.data(), f.size() * sizeof(float2), cudaMemcpyHostToDevice);
   };
   CK(upload(pl->d_m2l_ops, m2l), "upload m2l");
+  if ((pl->flags & FMM2D_PREC_MASK) == FMM2D_PREC_MIXED_TC) {
+    std::vector<double> re(m2l.size()), im(m2l.size());
+    for (size_t i = 0; i < m2l.size(); ++i) {
+      re[i] = m2l[i].real();
+      im[i] = m2l[i].imag();
+    }
+    std::vector<uint32_t> tab;
+    tc_build_tables(re, im, pl->n_ops, p, pl->tc_K, pl->tc_N, tab);
+    CK(dbuf_reserve(pl->d_tc_ops, tab.size() * 4), "alloc tc ops");
+    CK(cudaMemcpy(pl->d_tc_ops.p, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice), "upload tc ops");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    CK(cudaDeviceGetAttribute(&pl->n_sms, cudaDevAttrMultiProcessorCount, dev), "sm count");
+  }
   CK(upload(pl->d_m2m_ops, m2m), "upload m2m");
   CK(upload(pl->d_l2l_ops, l2l), "upload l2l");
   CK(dbuf_reserve(pl->d_m2l_logz, pl->n_ops * sizeof(double)), "alloc logz");
@@ -491,6 +506,32 @@ fmm2d_status evaluate_t(fmm2d_plan *pl, const void *u, double *out, cudaStream_t
   if (L < pl->l_min) {
     CK(cudaMemsetAsync(lL0, 0, pl->n_cells * sizeof(double), s), "zero locals");
     CK(cudaMemsetAsync(lb, 0, pl->n_cells * pl->P * sizeof(Cx<R>), s), "zero locals");
+  } else if ((pl->flags & FMM2D_PREC_MASK) == FMM2D_PREC_MIXED_TC) {
+    StageScope sc(pl, ST_M2L, s, 1);
+    TcArgs t;
+    t.p = pl->p;
+    t.P = pl->P;
+    t.n_classes = pl->sten.n_classes;
+    t.sms = pl->n_sms;
+    t.far_first = pl->lev_first[pl->l_min];
+    t.cls_cap = std::max<int64_t>(1, pl->n_far_cells);
+    t.cls_cnt = (const int *)pl->d_cls_cnt.p;
+    t.cls_cells = (const int *)pl->d_cls_cells.p;
+    t.far_full = (const int *)pl->d_far_full.p;
+    t.sten_ops = (const uint16_t *)((const char *)pl->d_sten.p + offsetof(Stencils, far_op));
+    t.sten_len = (const int *)((const char *)pl->d_sten.p + offsetof(Stencils, far_len));
+    t.btab = (const unsigned char *)pl->d_tc_ops.p;
+    t.logz = (const double *)pl->d_m2l_logz.p;
+    t.log_abs_scale = (const double *)pl->d_geo_scale.p;
+    t.lev_first = (const int64_t *)pl->d_lev_first.p;
+    t.l_min = pl->l_min;
+    t.L = L;
+    t.mQ = mQ;
+    t.ma = (const float2 *)ma;
+    t.lL0 = lL0;
+    t.lb = (float2 *)lb;
+    t.err = (int *)pl->d_dev_err.p;
+    CK(launch_m2l_tc(t, pl->tc_K, pl->tc_N, pl->n_far_cells, s), "m2l_tc");
   } else {
     StageScope sc(pl, ST_M2L, s, 1);
     CK(launch_m2l<R>(a, pl->lev_first[pl->l_min], pl->n_far_cells, (const int64_t *)pl->d_lev_first.p,
@@ -557,10 +598,6 @@ fmm2d_status fmm2d_plan_create(int tiling, int levels, int p, double eps, unsign
     g_create_err = "unknown flags";
     return FMM2D_EINVAL;
   }
-  if ((flags & FMM2D_PREC_MASK) == FMM2D_PREC_MIXED_TC) {
-    g_create_err = "tensor-core M2L is not available in this build";
-    return FMM2D_EINVAL;
-  }
   fmm2d_plan *pl = new (std::nothrow) fmm2d_plan();
   if (!pl) { g_create_err = "out of host memory"; return FMM2D_ENOMEM; }
   pl->tiling = tiling;
@@ -603,6 +640,9 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
   if (L == 0) L = auto_levels(pl->tiling, std::max(n_src, n_tgt), 64);
   if (p == 0) p = p_from_eps(pl->tiling, pl->eps);
   if (L < 1 || L > max_levels(pl->tiling)) return fail(pl, FMM2D_EINVAL, "levels out of range");
+  const bool tc = (pl->flags & FMM2D_PREC_MASK) == FMM2D_PREC_MIXED_TC;
+  if (tc && !tc_shape(p, &pl->tc_K, &pl->tc_N))
+    return fail(pl, FMM2D_EINVAL, "tensor-core M2L supports p <= 31");
   pl->L = L;
   pl->p = p;
   pl->P = (p + 1) & ~1;   // even stride: rows of complex values stay 16-byte aligned
@@ -700,6 +740,14 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
   CK(dbuf_reserve(pl->d_far_cnt, std::max(nfar, nleaf) * 4), "alloc");
   CK(dbuf_reserve(pl->d_far_src, nfar * FAR_MAX * 4), "alloc");
   CK(dbuf_reserve(pl->d_far_op, nfar * FAR_MAX * 2), "alloc");
+  if (tc) {
+    CK(dbuf_reserve(pl->d_far_full, nfar * FAR_MAX * 4), "alloc");
+    CK(dbuf_reserve(pl->d_cls_cnt, MAX_CLASSES * 4), "alloc");
+    CK(dbuf_reserve(pl->d_cls_cells, (size_t)MAX_CLASSES * nfar * 4), "alloc");
+    CK(cudaMemsetAsync(pl->d_cls_cnt.p, 0, MAX_CLASSES * 4, s), "memset");
+  }
+  CK(dbuf_reserve(pl->d_dev_err, 16), "alloc");
+  CK(cudaMemsetAsync(pl->d_dev_err.p, 0, 16, s), "memset");
   CK(dbuf_reserve(pl->d_near_cnt, nleaf * 4), "alloc");
   CK(dbuf_reserve(pl->d_near_src, nleaf * NEAR_MAX * 4), "alloc");
   {
@@ -727,7 +775,9 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
                      (const int4 *)pl->d_cell_crd.p, (const uint8_t *)pl->d_cell_hsrc.p,
                      (int *)pl->d_far_cnt.p, (int *)pl->d_far_src.p, (uint16_t *)pl->d_far_op.p,
                      pl->lev_first[L], (int *)pl->d_near_cnt.p, (int *)pl->d_near_src.p,
-                     (const int64_t *)pl->d_lev_first.p, s), "lists");
+                     (const int64_t *)pl->d_lev_first.p, tc ? (int *)pl->d_far_full.p : nullptr,
+                     tc ? (int *)pl->d_cls_cnt.p : nullptr, tc ? (int *)pl->d_cls_cells.p : nullptr,
+                     nfar, s), "lists");
   } else {
     // leaves above l_min: only Near lists are needed; build them with an
     // empty M2L stencil over the leaf level.
@@ -742,7 +792,7 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
                      (const int4 *)pl->d_cell_crd.p, (const uint8_t *)pl->d_cell_hsrc.p,
                      (int *)pl->d_far_cnt.p, (int *)pl->d_far_src.p, (uint16_t *)pl->d_far_op.p,
                      pl->lev_first[L], (int *)pl->d_near_cnt.p, (int *)pl->d_near_src.p,
-                     (const int64_t *)pl->d_lev_first.p, s), "lists");
+                     (const int64_t *)pl->d_lev_first.p, nullptr, nullptr, nullptr, 0, s), "lists");
   }
   CK(cudaGetLastError(), "build");
   pl->n_m2l = -1;
@@ -816,6 +866,14 @@ fmm2d_status fmm2d_plan_query(const fmm2d_plan *cpl, fmm2d_info *info) {
       }
     }
     pl->n_p2p_pairs = pairs;
+  }
+  {
+    int derr = 0;
+    if (pl->d_dev_err.p) {
+      cudaStreamSynchronize(pl->last_stream);
+      cudaMemcpy(&derr, pl->d_dev_err.p, 4, cudaMemcpyDeviceToHost);
+    }
+    info->device_error = derr;
   }
   info->n_m2l = pl->n_m2l;
   info->n_p2p_pairs = pl->n_p2p_pairs;
@@ -981,7 +1039,8 @@ void fmm2d_plan_destroy(fmm2d_plan *pl) {
                   &pl->d_far_src, &pl->d_far_op, &pl->d_near_cnt, &pl->d_near_src, &pl->d_src4,
                   &pl->d_tgt2, &pl->d_mQ, &pl->d_ma, &pl->d_lL0, &pl->d_lb, &pl->d_phi_near,
                   &pl->d_phi_far, &pl->d_sten, &pl->d_geo_scale, &pl->d_m2l_ops, &pl->d_m2l_logz,
-                  &pl->d_m2m_ops, &pl->d_l2l_ops, &pl->d_counts};
+                  &pl->d_m2m_ops, &pl->d_l2l_ops, &pl->d_counts, &pl->d_far_full,
+                  &pl->d_cls_cnt, &pl->d_cls_cells, &pl->d_tc_ops, &pl->d_dev_err};
   for (DBuf *b : bufs) dbuf_free(*b);
   delete pl;
 }

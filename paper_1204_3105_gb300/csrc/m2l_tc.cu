@@ -1,0 +1,398 @@
+// m2l_tc.cu - M2L on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// The M2L of a target cell is a sum over its NeighborsE4 list (eq. 3) of
+// operator x multipole products.  On scaled coefficients the operator depends
+// only on the lattice offset, i.e. on (child class, stencil entry), and not on
+// the level, so all M2L targets of one class - whatever their level - share
+// one operator per stencil entry.  A CTA takes 128 targets of one class and,
+// for every stencil entry e, accumulates
+//
+//      D[128 x N] += A_e[128 x K] . B_op(e)[K x N]
+//
+// where row t of A_e is the gathered source multipole of target t for entry e
+// as real numbers (Re a^_1, Im a^_1, ..., Re a^_p, Im a^_p, Q, 0...) and B is
+// the real form of the complex (p+1) x (p+1) operator (output columns
+// Re b^_0, Im b^_0, ..., Re b^_p, Im b^_p, 0...).  Both operands are split
+// into TF32 parts: the gathered multipole in two (A = A0 + A1, i.e. rounded
+// once to 22 significant bits) and the precomputed operator in three
+// (B = B0 + B1 + B2, 33 bits).  Five products A0.B0 + A0.B1 + A0.B2 + A1.B0 +
+// A1.B1, accumulated in FP32 in tensor memory, leave out only terms of
+// relative size 2^-33, so the result has FP32-class accuracy (the one-time
+// 22-bit rounding of A, 2^-23, dominates).  The Q log|z0| part of L_0 is
+// accumulated separately in FP64 on the CUDA cores.
+//
+// Data movement: operator tiles (already split and laid out as the MMA reads
+// them) arrive by cp.async.bulk (TMA bulk copy) into shared memory; the
+// threads gather and split the multipole rows.  Two stages are pipelined with
+// mbarriers: tcgen05.commit releases a stage once its MMAs have read it.
+// Every wait is bounded: on time-out the kernel sets an error word, lets its
+// copies in flight land, frees its tensor memory and returns.
+#include <cstring>
+
+#include "plan.h"
+
+namespace fmm2d {
+
+namespace {
+
+constexpr int TC_THREADS = 128;
+constexpr int TC_M = 128;
+constexpr int NACC = 4;                  // accumulators, entry e -> e % NACC
+constexpr uint32_t TMEM_COLS = 64 * NACC;
+constexpr long long WAIT_CYCLES = 2000000000ll;   // ~1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on one phase of an mbarrier; false on time-out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > WAIT_CYCLES) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+// Shared-memory matrix descriptor: no swizzle, K-major core matrices of
+// 8 rows x 16 bytes; lbo = byte step between core matrices along K, sbo =
+// byte step between 8-row groups along M / N.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Byte offset of element (row, k) in a K-major no-swizzle operand tile.
+__host__ __device__ __forceinline__ uint32_t core_off(int row, int k, int K) {
+  return (uint32_t)((row >> 3) * (K / 4) * 128 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+template <int K, int N>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  constexpr uint32_t A_BYTES = TC_M * K * 4, B_BYTES = N * K * 4;
+  constexpr uint32_t STAGE = 2 * A_BYTES + 3 * B_BYTES;
+  constexpr uint32_t SBO_A = (K / 4) * 128, SBO_B = (K / 4) * 128, LBO = 128;
+  constexpr uint32_t IDESC = idesc_tf32(TC_M, N);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * STAGE);   // full[2], mma[2]
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4);
+  int *s_cnt = reinterpret_cast<int *>(tmem_slot + 2);               // [MAX_CLASSES]
+  volatile int *s_abort = s_cnt + MAX_CLASSES;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (warp == 0) tmem_alloc(tmem_slot, TMEM_COLS);
+  if (tid == 0) {
+    for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
+    fence_barrier_init();
+    *s_abort = 0;
+  }
+  if (tid < MAX_CLASSES) s_cnt[tid] = tid < a.n_classes ? a.cls_cnt[tid] : 0;
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  int total_tiles = 0;
+  for (int c = 0; c < a.n_classes; ++c) total_tiles += (s_cnt[c] + TC_M - 1) / TC_M;
+
+  uint32_t it = 0;          // stage uses so far (global over tiles)
+  uint32_t full_use0 = 0, full_use1 = 0;   // bulk copies issued per stage
+  const int p = a.p;
+  for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+    int c = 0, t0 = tile;
+    while (t0 >= (s_cnt[c] + TC_M - 1) / TC_M) {
+      t0 -= (s_cnt[c] + TC_M - 1) / TC_M;
+      ++c;
+    }
+    const int row0 = t0 * TC_M;
+    const int nrows = min(TC_M, s_cnt[c] - row0);
+    const int g = tid < nrows ? a.cls_cells[(int64_t)c * a.cls_cap + row0 + tid] : -1;
+    const int64_t fi = g >= 0 ? (int64_t)g - a.far_first : 0;
+    double ls = 0.0;
+    if (g >= 0) {
+      int l = a.l_min;
+      while (l < a.L && (int64_t)g >= a.lev_first[l + 1]) ++l;
+      ls = a.log_abs_scale[l];
+    }
+    double L0 = 0.0;
+    const int E = a.sten_len[c];
+    for (int e = 0; e < E; ++e, ++it) {
+      const int s = it & 1;
+      const uint32_t use = it >> 1;
+      unsigned char *A_hi = smem + s * STAGE, *A_lo = A_hi + A_BYTES;
+      unsigned char *B_hi = A_lo + A_BYTES;
+      if (use >= 1) {
+        if (!mbar_wait(&bars[2 + s], (use - 1) & 1)) *s_abort = 1;
+      }
+      const int op = a.sten_ops[c * FAR_MAX + e];
+      if (tid == 0 && !*s_abort) {
+        mbar_expect_tx(&bars[s], 3 * B_BYTES);
+        bulk_g2s(B_hi, a.btab + (size_t)op * 3 * B_BYTES, 3 * B_BYTES, &bars[s]);
+        if (s) ++full_use1; else ++full_use0;
+      }
+      // gather row tid: source multipole of entry e, split into TF32 hi / lo
+      const int src = g >= 0 ? a.far_full[fi * FAR_MAX + e] : -1;
+      float v[K];
+      const float4 *row = reinterpret_cast<const float4 *>(a.ma + (int64_t)(src >= 0 ? src : 0) * a.P);
+      const float qf = src >= 0 ? (float)a.mQ[src] : 0.f;
+#pragma unroll
+      for (int q = 0; q < K / 4; ++q) {
+        const float4 f = (src >= 0 && 4 * q < 2 * p) ? row[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        v[k] = k < 2 * p ? v[k] : 0.f;
+        v[k] = k == 2 * p ? qf : v[k];
+      }
+      if (src >= 0) L0 += a.mQ[src] * (ls + a.logz[op]);
+#pragma unroll
+      for (int q = 0; q < K / 4; ++q) {
+        float4 h, l;
+        h.x = tf32_rna(v[4 * q]);     l.x = tf32_rna(v[4 * q] - h.x);
+        h.y = tf32_rna(v[4 * q + 1]); l.y = tf32_rna(v[4 * q + 1] - h.y);
+        h.z = tf32_rna(v[4 * q + 2]); l.z = tf32_rna(v[4 * q + 2] - h.z);
+        h.w = tf32_rna(v[4 * q + 3]); l.w = tf32_rna(v[4 * q + 3] - h.w);
+        const uint32_t off = core_off(tid, 4 * q, K);
+        *reinterpret_cast<float4 *>(A_hi + off) = h;
+        *reinterpret_cast<float4 *>(A_lo + off) = l;
+      }
+      fence_proxy_async();
+      __syncthreads();
+      if (*s_abort) break;
+      if (tid == 0) {
+        if (!mbar_wait(&bars[s], ((s ? full_use1 : full_use0) - 1) & 1)) {
+          *s_abort = 1;
+        } else {
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(A_hi), a1 = a0 + A_BYTES;
+          const uint32_t b0 = a1 + A_BYTES, b1 = b0 + B_BYTES, b2 = b1 + B_BYTES;
+#pragma unroll
+          for (int ks = 0; ks < K / 8; ++ks) {
+            const uint32_t o = ks * 2 * LBO;
+            const uint64_t da0 = sdesc(a0 + o, LBO, SBO_A), da1 = sdesc(a1 + o, LBO, SBO_A);
+            const uint32_t acc = tmem + (uint32_t)(e % NACC) * 64;
+            mma_tf32(acc, da0, sdesc(b0 + o, LBO, SBO_B), IDESC, (e >= NACC || ks > 0) ? 1u : 0u);
+            mma_tf32(acc, da0, sdesc(b1 + o, LBO, SBO_B), IDESC, 1u);
+            mma_tf32(acc, da0, sdesc(b2 + o, LBO, SBO_B), IDESC, 1u);
+            mma_tf32(acc, da1, sdesc(b0 + o, LBO, SBO_B), IDESC, 1u);
+            mma_tf32(acc, da1, sdesc(b1 + o, LBO, SBO_B), IDESC, 1u);
+          }
+          mma_commit(&bars[2 + s]);
+        }
+      }
+    }
+    __syncthreads();
+    if (*s_abort) break;
+    // wait for the last commit of this tile, then read the accumulator
+    {
+      const uint32_t last = it - 1;
+      if (!mbar_wait(&bars[2 + (last & 1)], (last >> 1) & 1)) *s_abort = 1;
+    }
+    tc_fence_after();
+    __syncthreads();
+    if (*s_abort) break;
+    // sum the used accumulators in FP64, 16 columns at a time
+    const int nacc = E < NACC ? E : NACC;
+#pragma unroll
+    for (int q = 0; q < N / 16; ++q) {
+      double d[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) d[i] = 0.0;
+      for (int ac = 0; ac < nacc; ++ac) {
+        float t16[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)ac * 64 + q * 16, t16);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) d[i] += (double)t16[i];
+      }
+      if (g >= 0) {
+        if (q == 0) a.lL0[g] = L0 + d[0];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int l = 8 * q + i;
+          if (l >= 1 && l <= p)
+            a.lb[(int64_t)g * a.P + l - 1] = make_float2((float)d[2 * i], (float)d[2 * i + 1]);
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+  if (*s_abort) {
+    if (tid == 0) {
+      atomicOr(a.err, 1);
+      // let the bulk copies in flight land before the CTA exits
+      if (full_use0) mbar_wait(&bars[0], (full_use0 - 1) & 1);
+      if (full_use1) mbar_wait(&bars[1], (full_use1 - 1) & 1);
+    }
+  } else if (it > 0 && tid == 0) {
+    // every commit has been waited on except possibly the other stage's last
+    const uint32_t last = it - 1;
+    mbar_wait(&bars[2 + (last & 1)], (last >> 1) & 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+  (void)lane;
+}
+
+template <int K, int N>
+cudaError_t launch_tc(const TcArgs &a, int64_t n_far_cells, cudaStream_t s) {
+  constexpr size_t STAGE = 2 * (size_t)TC_M * K * 4 + 3 * (size_t)N * K * 4;
+  const size_t smem = 2 * STAGE + 4 * 8 + 8 + (MAX_CLASSES + 1) * 4 + 16;
+  cudaError_t e = cudaFuncSetAttribute(k_m2l_tc<K, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  int64_t tiles = (n_far_cells + TC_M - 1) / TC_M + a.n_classes;
+  int grid = (int)std::min<int64_t>(tiles, a.sms);
+  if (grid < 1) return cudaSuccess;
+  k_m2l_tc<K, N><<<grid, TC_THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+uint32_t tf32_round_host(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  u += 0x1000u;
+  u &= ~0x1FFFu;
+  return u;
+}
+
+}  // namespace
+
+bool tc_shape(int p, int *K, int *N) {
+  if (p <= 23) { *K = 48; *N = 48; return true; }
+  if (p <= 27) { *K = 56; *N = 64; return true; }
+  if (p <= 31) { *K = 64; *N = 64; return true; }
+  return false;
+}
+
+void tc_build_tables(const std::vector<double> &re, const std::vector<double> &im, int n_ops, int p,
+                     int K, int N, std::vector<uint32_t> &out) {
+  const int P1 = p + 1;
+  const size_t words = (size_t)N * K;    // one operand tile in 32-bit words
+  out.assign((size_t)n_ops * 3 * words, 0u);
+  for (int o = 0; o < n_ops; ++o) {
+    uint32_t *w0 = out.data() + (size_t)o * 3 * words, *w1 = w0 + words, *w2 = w1 + words;
+    for (int n = 0; n < N; ++n) {
+      const int l = n >> 1, part = n & 1;
+      for (int kk = 0; kk < K; ++kk) {
+        double val = 0.0;
+        if (l <= p) {
+          if (kk < 2 * p) {
+            const int k = kk / 2 + 1, comp = kk & 1;
+            const size_t idx = (size_t)o * P1 * P1 + (size_t)l * P1 + k;
+            const double tr = re[idx], ti = im[idx];
+            val = part == 0 ? (comp == 0 ? tr : -ti) : (comp == 0 ? ti : tr);
+          } else if (kk == 2 * p) {
+            const size_t idx = (size_t)o * P1 * P1 + (size_t)l * P1;
+            val = part == 0 ? re[idx] : im[idx];
+          }
+        }
+        // three TF32 parts of the FP64 value: B0 + B1 + B2 (33 bits)
+        const uint32_t off = core_off(n, kk, K) / 4;
+        double rest = val;
+        uint32_t *dst[3] = {w0, w1, w2};
+        for (int part = 0; part < 3; ++part) {
+          const uint32_t w = tf32_round_host((float)rest);
+          float wf;
+          std::memcpy(&wf, &w, 4);
+          dst[part][off] = w;
+          rest -= (double)wf;
+        }
+      }
+    }
+  }
+}
+
+cudaError_t launch_m2l_tc(const TcArgs &a, int K, int N, int64_t n_far_cells, cudaStream_t s) {
+  if (n_far_cells <= 0) return cudaSuccess;
+  if (K == 48 && N == 48) return launch_tc<48, 48>(a, n_far_cells, s);
+  if (K == 56 && N == 64) return launch_tc<56, 64>(a, n_far_cells, s);
+  if (K == 64 && N == 64) return launch_tc<64, 64>(a, n_far_cells, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace fmm2d

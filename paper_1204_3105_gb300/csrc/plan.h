@@ -89,6 +89,8 @@ struct Plan {
   DBuf d_sten, d_geo_scale;
   DBuf d_m2l_ops, d_m2l_logz, d_m2m_ops, d_l2l_ops;   // element type per precision
   DBuf d_counts;
+  DBuf d_far_full, d_cls_cnt, d_cls_cells, d_tc_ops, d_dev_err;
+  int tc_K = 0, tc_N = 0, n_sms = 148;
   std::vector<double> m2l_logz_host;
 };
 
@@ -127,7 +129,8 @@ cudaError_t launch_lists2(const Geo &g, const Stencils *d_sten, int64_t first, i
                           const int *map, const uint8_t *cell_cls, const int4 *cell_crd,
                           const uint8_t *cell_hsrc, int *far_cnt, int *far_src, uint16_t *far_op,
                           int64_t leaf_first, int *near_cnt, int *near_src,
-                          const int64_t *lev_first_dev, cudaStream_t s);
+                          const int64_t *lev_first_dev, int *far_full, int *cls_cnt,
+                          int *cls_cells, int64_t cls_cap, cudaStream_t s);
 
 // ---------------------------------------------------------------- expand.cu
 struct ExpandArgs {
@@ -160,6 +163,30 @@ template <typename R>
 cudaError_t launch_l2p(const ExpandArgs &a, const R *tgt, int tstride, const int *start,
                        const int *end, const uint32_t *perm, const double *lL0, const Cx<R> *lb,
                        const double *phi_near, double *phi_far, double *out, cudaStream_t s);
+
+// ---------------------------------------------------------------- m2l_tc.cu
+// Tensor-core M2L (tcgen05, TF32 hi/lo split, FP32 accumulation in TMEM).
+struct TcArgs {
+  int p, P, n_classes, sms;
+  int64_t far_first, cls_cap;
+  const int *cls_cnt, *cls_cells, *far_full;
+  const uint16_t *sten_ops;           // [MAX_CLASSES][FAR_MAX] operator id per stencil entry
+  const int *sten_len;                // [MAX_CLASSES]
+  const unsigned char *btab;          // per operator: B hi then B lo, core-matrix layout
+  const double *logz, *log_abs_scale;
+  const int64_t *lev_first;
+  int l_min, L;
+  const double *mQ;
+  const float2 *ma;
+  double *lL0;
+  float2 *lb;
+  int *err;
+};
+bool tc_shape(int p, int *K, int *N);
+// B tables (hi/lo TF32 splits of the real-ified operators) for all operators.
+void tc_build_tables(const std::vector<double> &m2l_re, const std::vector<double> &m2l_im,
+                     int n_ops, int p, int K, int N, std::vector<uint32_t> &out);
+cudaError_t launch_m2l_tc(const TcArgs &a, int K, int N, int64_t n_far_cells, cudaStream_t s);
 
 // ---------------------------------------------------------------- p2p.cu
 template <typename R>

@@ -151,7 +151,8 @@ __global__ void k_lists(Geo g, const Stencils *__restrict__ st, int64_t first, i
                         int64_t lev_first_lmin, int *__restrict__ far_cnt,
                         int *__restrict__ far_src, uint16_t *__restrict__ far_op,
                         int64_t leaf_first, int *__restrict__ near_cnt, int *__restrict__ near_src,
-                        const int64_t *__restrict__ lev_first) {
+                        const int64_t *__restrict__ lev_first, int *__restrict__ far_full,
+                        int *__restrict__ cls_cnt, int *__restrict__ cls_cells, int64_t cls_cap) {
   int64_t gslot = first + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (gslot >= first + count) return;
   int l = 0;
@@ -164,14 +165,23 @@ __global__ void k_lists(Geo g, const Stencils *__restrict__ st, int64_t first, i
     int4 q = make_int4(c.x + st->far_d[cls][e][0], c.y + st->far_d[cls][e][1],
                        c.z + st->far_d[cls][e][2], 0);
     uint32_t k;
-    if (!cell_at(g, l, q, &k)) continue;
-    int s = map[g.map_off[l] + k];
-    if (s < 0 || !cell_hsrc[s]) continue;
+    int s = -1;
+    if (cell_at(g, l, q, &k)) {
+      s = map[g.map_off[l] + k];
+      if (s >= 0 && !cell_hsrc[s]) s = -1;
+    }
+    if (far_full) far_full[fi * FAR_MAX + e] = s;
+    if (s < 0) continue;
     far_src[fi * FAR_MAX + cnt] = s;
     far_op[fi * FAR_MAX + cnt] = st->far_op[cls][e];
     ++cnt;
   }
   far_cnt[fi] = cnt;
+  if (cls_cnt && st->far_len[cls] > 0) {
+    // group the M2L targets by stencil class for the tensor-core M2L
+    int pos = atomicAdd(&cls_cnt[cls], 1);
+    cls_cells[(int64_t)cls * cls_cap + pos] = (int)gslot;
+  }
   if (gslot >= leaf_first) {
     const int o = (g.tiling == FMM2D_TRI && c.w == 0) ? 1 : 0;
     const int64_t ni = gslot - leaf_first;
@@ -244,11 +254,13 @@ cudaError_t launch_lists2(const Geo &g, const Stencils *d_sten, int64_t first, i
                           const int *map, const uint8_t *cell_cls, const int4 *cell_crd,
                           const uint8_t *cell_hsrc, int *far_cnt, int *far_src, uint16_t *far_op,
                           int64_t leaf_first, int *near_cnt, int *near_src,
-                          const int64_t *lev_first_dev, cudaStream_t s) {
+                          const int64_t *lev_first_dev, int *far_full, int *cls_cnt,
+                          int *cls_cells, int64_t cls_cap, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   k_lists<<<nblk(count, 128), 128, 0, s>>>(g, d_sten, first, count, map, cell_cls, cell_crd,
                                             cell_hsrc, first, far_cnt, far_src, far_op, leaf_first,
-                                            near_cnt, near_src, lev_first_dev);
+                                            near_cnt, near_src, lev_first_dev, far_full, cls_cnt,
+                                            cls_cells, cls_cap);
   return cudaGetLastError();
 }
 

@@ -96,6 +96,22 @@ def test_mixed_path_matches_oracle(tiling, L, p, f32):
     assert rel_inf_error(phi, r.phi) < 1e-6
 
 
+@pytest.mark.parametrize("tiling,L,p", CASES + [("quad", 5, 22), ("sept", 4, 21), ("tri", 5, 27)])
+def test_tensor_core_m2l_matches_oracle(tiling, L, p):
+    """Mixed form with M2L on the tensor cores (split TF32, FP32 accumulation):
+    far field and total potential within 1e-6 of the FP64 oracle."""
+    n = 12007
+    xy, u = uniform_square(n, seed=9)
+    phi, plan = run_gpu(tiling, xy, u, levels=L, p=p, prec="tc", keep=True)
+    assert plan.query()["device_error"] == 0
+    far = plan.export("phi_far")
+    plan.close()
+    r, _ = _oracle(tiling, L, xy, u, None, p)
+    scale = np.max(np.abs(r.phi))
+    assert np.max(np.abs(far - r.phi_far)) / scale < 1e-6
+    assert rel_inf_error(phi, r.phi) < 1e-6
+
+
 def test_separate_targets_domain_and_clusters():
     rng = np.random.default_rng(3)
     dom = (-2.0, 1.0, 3.0)
@@ -144,15 +160,17 @@ def test_domain_error_and_empty():
     assert np.all(phi == 0)
 
 
+@pytest.mark.parametrize("prec", ["mixed", "tc"])
 @pytest.mark.parametrize("tiling", ["quad", "sept", "tri"])
-def test_full_size_sampled(tiling):
+def test_full_size_sampled(tiling, prec):
     """N = M = 2^20 uniform points, FP32 inputs, eps = 1e-6 with the planner's
     L and p (the benchmark configuration): keys bit-exact against the oracle's
     CellIndex, potentials against direct summation on 384 sampled targets."""
     n = 2 ** 20
     xy, u = uniform_square(n, seed=2, dtype=np.float32)
-    phi, plan = run_gpu(tiling, xy, u, prec="mixed", f32=True, eps=1e-6, keep=True)
+    phi, plan = run_gpu(tiling, xy, u, prec=prec, f32=True, eps=1e-6, keep=True)
     info = plan.query()
+    assert info["device_error"] == 0
     T = make_tiling(tiling, info["levels"])
     x64 = xy.astype(np.float64)
     assert np.array_equal(plan.export("src_keys"), T.keys(x64[:, 0], x64[:, 1]))
