@@ -159,7 +159,21 @@ def run_ours(args):
     u_d = torch.from_numpy(u).to(dev)
     outs = {t: torch.empty(N_POINTS, dtype=torch.float64, device=dev) for t in args.tilings}
     prec = {"tc": fmm2d.PREC_MIXED_TC, "mixed": fmm2d.PREC_MIXED, "fp64": fmm2d.PREC_FP64}[args.prec]
-    plans = {t: fmm2d.Plan(t, 0, 0, EPS, prec | fmm2d.IN_F32) for t in args.tilings}
+    tuned = {}
+    fixed = {}
+    for item in filter(None, args.params.split(",")):
+        t, L, p = item.split(":")
+        fixed[t] = (int(L), int(p), None, None)
+    for t in args.tilings:
+        if t in fixed:
+            tuned[t] = fixed[t]
+        elif args.no_tune:
+            tuned[t] = (0, 0, None, None)
+        else:   # measured (L, p) for eps on this point set (seeded probe strengths)
+            tuned[t] = fmm2d.fmm2d_autotune(t, EPS, prec | fmm2d.IN_F32, xy_d, N_POINTS, xy_d,
+                                            N_POINTS, stream=stream)
+    plans = {t: fmm2d.Plan(t, tuned[t][0], tuned[t][1], EPS, prec | fmm2d.IN_F32)
+             for t in args.tilings}
     flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device=dev)   # 256 MB > L2
 
     def step(per):
@@ -258,12 +272,15 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.prec == "fp64" else "tf32x3+f32+f64", "data": "synthetic",
             "config": {"workload": "N=M=2^20 uniform unit square (sources=targets), FP32 points and "
-                                   "strengths, quad+sept+tri, eps=1e-6, planner L/p, %s form" % args.prec,
+                                   "strengths, quad+sept+tri, eps=1e-6, %s L/p, %s form" % (
+                                   "fixed" if args.params else "planner" if args.no_tune else "autotuned",
+                                   args.prec),
                        "global_batch": N_POINTS, "l2": "flushed between tilings (256 MB write)",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "per_tiling": {t: {"points_per_s": N_POINTS / (statistics.mean(tt[t]) / 1e3),
                                "ms": statistics.mean(tt[t]), "L": info[t]["levels"], "p": info[t]["p"],
                                "m2l": info[t]["n_m2l"], "p2p_pairs": info[t]["n_p2p_pairs"],
+                               "tune_probe_err": tuned[t][2],
                                "stages_ms": {k: v[0] / args.steps for k, v in stage[t].items()}}
                            for t in args.tilings},
             "roofline": roof,
@@ -294,6 +311,8 @@ def main():
     ap.add_argument("--tilings", default=",".join(TILINGS))
     ap.add_argument("--ref-points", type=int, default=16384)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="a-priori L and p instead of fmm2d_autotune")
+    ap.add_argument("--params", default="", help="fixed L and p per tiling, e.g. quad:7:12,sept:5:13")
     args = ap.parse_args()
     args.tilings = tuple(args.tilings.split(","))
     if args.impl == "reference":

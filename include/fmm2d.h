@@ -209,6 +209,29 @@ void fmm2d_plan_destroy(fmm2d_plan *plan);
 const char *fmm2d_last_error(const fmm2d_plan *plan);
 
 /*
+ * fmm2d_autotune - choose the leaf level L and expansion order p for a
+ * point set by measurement (the a-priori p of Sec. 8, kappa^(p+1) <= eps, is a
+ * worst-case bound and far larger than typical inputs need).
+ *   The caller's points are evaluated with seeded probe strengths (uniform in
+ *   [-1, 1]); potentials at 1024 evenly spaced targets are compared with an
+ *   FP64 direct sum of eq. (2) computed on the GPU.  For L in {L0-1, L0,
+ *   L0+1} (L0 = fmm2d_default_params) the smallest p with
+ *   eps_rel_inf <= eps/3 is found by bisection and build + evaluate is timed;
+ *   the fastest (L, p) is returned.
+ *   tiling, eps, flags, domain (NULL = unit square): as for a plan.
+ *   src_xy_dev / tgt_xy_dev: the points (device, layout as fmm2d_build).
+ *   levels_out, p_out: the choice; err_out: its measured eps_rel_inf on the
+ *   probe; ms_out: its build + evaluate time.  If no candidate meets eps/3,
+ *   the a-priori (L0, p) is returned with err_out = ms_out = -1.
+ * Allocates temporary device memory and synchronises `stream`.  Errors:
+ * FMM2D_EINVAL, FMM2D_ENOMEM, FMM2D_ECUDA.
+ */
+fmm2d_status fmm2d_autotune(int tiling, double eps, unsigned flags, const double *domain,
+                            const void *src_xy_dev, int64_t n_src, const void *tgt_xy_dev,
+                            int64_t n_tgt, void *stream, int *levels_out, int *p_out,
+                            double *err_out, double *ms_out);
+
+/*
  * fmm2d_keys_sort_noalloc - leaf keys of a point set and their stable sort,
  * for callers that cannot allocate GPU memory.  The paper has no
  * counterpart: this is a library convenience, not a step of the method.

@@ -183,9 +183,11 @@ static Tables make_tables(int tiling) {
       T.cw.push_back(cd(bx - 0.5, by - 0.5) / s2);
       T.csig.push_back(cd(0.5, 0));
     }
-    T.st.near_len[0] = 0;
+    // Near stencil: the leaf itself first (the P2P kernel relies on it)
+    T.st.near_len[0] = 1;
     for (int dj = -1; dj <= 1; ++dj)
       for (int di = -1; di <= 1; ++di) {
+        if (di == 0 && dj == 0) continue;
         int e = T.st.near_len[0]++;
         T.st.near_d[0][e][0] = di;
         T.st.near_d[0][e][1] = dj;
@@ -250,6 +252,9 @@ static Tables make_tables(int tiling) {
     I3 reps[2] = {{84, 85, 86}, {84, 85, 85}};   // upright, inverted (level 8)
     for (int o = 0; o < 2; ++o) {
       std::vector<I3> nb = tri_near(reps[o], 8);
+      // the leaf itself first (the P2P kernel relies on it)
+      auto self = std::find(nb.begin(), nb.end(), reps[o]);
+      std::rotate(nb.begin(), self, self + 1);
       T.st.near_len[o] = (int)nb.size();
       for (size_t e = 0; e < nb.size(); ++e) {
         T.st.near_d[o][e][0] = nb[e].a - reps[o].a;

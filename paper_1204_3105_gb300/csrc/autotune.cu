@@ -1,0 +1,164 @@
+// autotune.cu - fmm2d_autotune: pick the leaf level L and expansion order p
+// for a point set by measurement.
+//
+// The a-priori p of Sec. 8 (kappa^(p+1) <= eps) bounds the worst case and is
+// far larger than uniform inputs need.  The tuner evaluates the caller's
+// points with seeded probe strengths (uniform in [-1, 1]) and compares the
+// potentials at sampled targets with an FP64 direct sum computed on the GPU
+// (k_direct_sample, eq. 2 summed exactly as written).  For each candidate L
+// it finds the smallest p whose eps_rel_inf is at most eps/3, times
+// build + evaluate, and returns the fastest (L, p).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "plan.h"
+
+namespace fmm2d {
+namespace {
+
+template <typename T>
+__global__ void k_direct_sample(const T *__restrict__ sxy, const T *__restrict__ u, int64_t n,
+                                const T *__restrict__ txy, const int *__restrict__ tidx,
+                                double *__restrict__ out) {
+  __shared__ double red[256];
+  const int j = tidx[blockIdx.x];
+  const double tx = (double)txy[2 * (int64_t)j], ty = (double)txy[2 * (int64_t)j + 1];
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double dx = tx - (double)sxy[2 * i], dy = ty - (double)sxy[2 * i + 1];
+    const double r2 = dx * dx + dy * dy;
+    if (r2 > 0.0) acc += (double)u[i] * log(r2);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = 0.5 * red[0];
+}
+
+struct DevMem {
+  void *p = nullptr;
+  ~DevMem() { if (p) cudaFree(p); }
+};
+
+}  // namespace
+}  // namespace fmm2d
+
+using namespace fmm2d;
+
+extern "C" fmm2d_status fmm2d_autotune(int tiling, double eps, unsigned flags, const double *domain,
+                                       const void *src_xy, int64_t n_src, const void *tgt_xy,
+                                       int64_t n_tgt, void *stream, int *levels_out, int *p_out,
+                                       double *err_out, double *ms_out) {
+  if (tiling < 0 || tiling > 2 || !(eps > 0.0 && eps < 1.0) || n_src <= 0 || n_tgt <= 0 || !src_xy ||
+      !tgt_xy)
+    return FMM2D_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool f32 = (flags & FMM2D_IN_F32) != 0;
+  const size_t esz = f32 ? 4 : 8;
+  int L0 = 0, pmax = 0;
+  fmm2d_status st = fmm2d_default_params(tiling, std::max(n_src, n_tgt), 64, eps, &L0, &pmax, nullptr);
+  if (st != FMM2D_OK) return st;
+  if ((flags & FMM2D_PREC_MASK) == FMM2D_PREC_MIXED_TC) pmax = std::min(pmax, 31);
+  // seeded probe strengths (64-bit LCG, uniform in [-1, 1))
+  std::vector<double> ud(n_src);
+  uint64_t x = 0x9E3779B97F4A7C15ull;
+  for (int64_t i = 0; i < n_src; ++i) {
+    x = x * 6364136223846793005ull + 1442695040888963407ull;
+    ud[i] = (double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  }
+  std::vector<float> uf(f32 ? n_src : 0);
+  if (f32)
+    for (int64_t i = 0; i < n_src; ++i) uf[i] = (float)ud[i];
+  const int m = (int)std::min<int64_t>(1024, n_tgt);
+  std::vector<int> idx(m);
+  for (int i = 0; i < m; ++i) idx[i] = (int)(((int64_t)i * n_tgt) / m);
+  DevMem d_u, d_idx, d_ref, d_phi;
+  if (cudaMalloc(&d_u.p, n_src * esz) || cudaMalloc(&d_idx.p, m * 4) || cudaMalloc(&d_ref.p, m * 8) ||
+      cudaMalloc(&d_phi.p, n_tgt * 8))
+    return FMM2D_ENOMEM;
+  cudaMemcpy(d_u.p, f32 ? (const void *)uf.data() : (const void *)ud.data(), n_src * esz,
+             cudaMemcpyHostToDevice);
+  cudaMemcpy(d_idx.p, idx.data(), m * 4, cudaMemcpyHostToDevice);
+  if (f32)
+    k_direct_sample<float><<<m, 256, 0, s>>>((const float *)src_xy, (const float *)d_u.p, n_src,
+                                            (const float *)tgt_xy, (const int *)d_idx.p, (double *)d_ref.p);
+  else
+    k_direct_sample<double><<<m, 256, 0, s>>>((const double *)src_xy, (const double *)d_u.p, n_src,
+                                             (const double *)tgt_xy, (const int *)d_idx.p, (double *)d_ref.p);
+  std::vector<double> ref(m), phi(n_tgt);
+  if (cudaMemcpyAsync(ref.data(), d_ref.p, m * 8, cudaMemcpyDeviceToHost, s) || cudaStreamSynchronize(s))
+    return FMM2D_ECUDA;
+  double rmax = 0.0;
+  for (double v : ref) rmax = std::max(rmax, std::fabs(v));
+  if (rmax == 0.0) rmax = 1.0;
+  const double target = eps / 3.0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto run = [&](int L, int p, double *err, double *ms) -> fmm2d_status {
+    fmm2d_plan *pl = nullptr;
+    fmm2d_status r = fmm2d_plan_create(tiling, L, p, eps, flags, &pl);
+    if (r != FMM2D_OK) return r;
+    if (domain) fmm2d_plan_set_domain(pl, domain[0], domain[1], domain[2]);
+    double best = 1e30;
+    for (int rep = 0; rep < (ms ? 3 : 1) && r == FMM2D_OK; ++rep) {
+      cudaEventRecord(e0, s);
+      r = fmm2d_build(pl, src_xy, n_src, tgt_xy, n_tgt, s);
+      if (r == FMM2D_OK) r = fmm2d_evaluate(pl, d_u.p, (double *)d_phi.p, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      best = std::min(best, (double)t);
+    }
+    if (r == FMM2D_OK) {
+      cudaMemcpy(phi.data(), d_phi.p, n_tgt * 8, cudaMemcpyDeviceToHost);
+      double e = 0.0;
+      for (int i = 0; i < m; ++i) e = std::max(e, std::fabs(phi[idx[i]] - ref[i]));
+      *err = e / rmax;
+      if (ms) *ms = best;
+    }
+    fmm2d_plan_destroy(pl);
+    return r;
+  };
+  int bestL = 0, bestp = 0;
+  double best_ms = 1e30, best_err = 0.0;
+  const int top = tiling == FMM2D_SEPT ? 8 : 12;
+  for (int L = std::max(1, L0 - 1); L <= std::min(top, L0 + 1); ++L) {
+    double e_hi;
+    if (run(L, pmax, &e_hi, nullptr) != FMM2D_OK || !(e_hi <= target)) continue;
+    int lo = 1, hi = pmax;          // smallest p in [lo, hi] with err <= target; err(hi) ok
+    while (lo < hi) {
+      int mid = (lo + hi) / 2;
+      double e;
+      if (run(L, mid, &e, nullptr) == FMM2D_OK && e <= target) hi = mid;
+      else lo = mid + 1;
+    }
+    double e, ms;
+    if (run(L, hi, &e, &ms) != FMM2D_OK || !(e <= target)) continue;
+    if (ms < best_ms) {
+      best_ms = ms;
+      bestL = L;
+      bestp = hi;
+      best_err = e;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (bestL == 0) {
+    // nothing met eps/3 on the probe: report the a-priori rule
+    bestL = L0;
+    bestp = pmax;
+    best_err = -1.0;
+    best_ms = -1.0;
+  }
+  if (levels_out) *levels_out = bestL;
+  if (p_out) *p_out = bestp;
+  if (err_out) *err_out = best_err;
+  if (ms_out) *ms_out = best_ms;
+  return FMM2D_OK;
+}

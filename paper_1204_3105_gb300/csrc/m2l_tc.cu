@@ -16,7 +16,8 @@
 // into TF32 parts: the gathered multipole in two (A = A0 + A1, i.e. rounded
 // once to 22 significant bits) and the precomputed operator in three
 // (B = B0 + B1 + B2, 33 bits).  Five products A0.B0 + A0.B1 + A0.B2 + A1.B0 +
-// A1.B1, accumulated in FP32 in tensor memory, leave out only terms of
+// A1.B1, accumulated in FP32 in tensor memory (entries spread round-robin over
+// eight accumulators that are summed in FP64), leave out only terms of
 // relative size 2^-33, so the result has FP32-class accuracy (the one-time
 // 22-bit rounding of A, 2^-23, dominates).  The Q log|z0| part of L_0 is
 // accumulated separately in FP64 on the CUDA cores.
@@ -35,10 +36,9 @@ namespace fmm2d {
 
 namespace {
 
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;
 constexpr int TC_M = 128;
-constexpr int NACC = 4;                  // accumulators, entry e -> e % NACC
-constexpr uint32_t TMEM_COLS = 64 * NACC;
+constexpr int NACC = 8;                  // accumulators, entry e -> e % NACC
 constexpr long long WAIT_CYCLES = 2000000000ll;   // ~1 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -149,20 +149,30 @@ __host__ __device__ __forceinline__ uint32_t core_off(int row, int k, int K) {
   return (uint32_t)((row >> 3) * (K / 4) * 128 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
 }
 
+// Accumulator column stride and CTAs per SM for a shape.
+template <int N> struct TcShape {
+  static constexpr uint32_t ACC = N <= 32 ? 32 : 64;
+  static constexpr uint32_t COLS = NACC * ACC;            // 256 or 512 TMEM columns
+  static constexpr int CTAS = N <= 32 ? 2 : 1;
+};
+
 template <int K, int N>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcArgs a) {
+__global__ void __launch_bounds__(TC_THREADS, TcShape<N>::CTAS) k_m2l_tc(TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   constexpr uint32_t A_BYTES = TC_M * K * 4, B_BYTES = N * K * 4;
   constexpr uint32_t STAGE = 2 * A_BYTES + 3 * B_BYTES;
-  constexpr uint32_t SBO_A = (K / 4) * 128, SBO_B = (K / 4) * 128, LBO = 128;
+  constexpr uint32_t SBO = (K / 4) * 128, LBO = 128;
   constexpr uint32_t IDESC = idesc_tf32(TC_M, N);
+  constexpr uint32_t ACC = TcShape<N>::ACC, COLS = TcShape<N>::COLS;
+  constexpr int QH = K / 8;                 // 16-byte chunks of a row per half
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * STAGE);   // full[2], mma[2]
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4);
   int *s_cnt = reinterpret_cast<int *>(tmem_slot + 2);               // [MAX_CLASSES]
   volatile int *s_abort = s_cnt + MAX_CLASSES;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int row = tid & (TC_M - 1), half = tid >> 7;   // two threads per gathered row
 
-  if (warp == 0) tmem_alloc(tmem_slot, TMEM_COLS);
+  if (warp == 0) tmem_alloc(tmem_slot, COLS);
   if (tid == 0) {
     for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
     fence_barrier_init();
@@ -176,9 +186,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcArgs a) {
   int total_tiles = 0;
   for (int c = 0; c < a.n_classes; ++c) total_tiles += (s_cnt[c] + TC_M - 1) / TC_M;
 
-  uint32_t it = 0;          // stage uses so far (global over tiles)
-  uint32_t full_use0 = 0, full_use1 = 0;   // bulk copies issued per stage
+  uint32_t it = 0;                          // stage uses so far (global over tiles)
+  uint32_t full_use0 = 0, full_use1 = 0;    // bulk copies issued per stage (thread 0)
   const int p = a.p;
+  // thread 0: issue the operator copy of stage use `u` (entry of operator op)
+  auto issue_b = [&](uint32_t u, int op) {
+    const int st = u & 1;
+    unsigned char *B0 = smem + st * STAGE + 2 * A_BYTES;
+    mbar_expect_tx(&bars[st], 3 * B_BYTES);
+    bulk_g2s(B0, a.btab + (size_t)op * 3 * B_BYTES, 3 * B_BYTES, &bars[st]);
+    if (st) ++full_use1; else ++full_use0;
+  };
   for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
     int c = 0, t0 = tile;
     while (t0 >= (s_cnt[c] + TC_M - 1) / TC_M) {
@@ -187,57 +205,50 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcArgs a) {
     }
     const int row0 = t0 * TC_M;
     const int nrows = min(TC_M, s_cnt[c] - row0);
-    const int g = tid < nrows ? a.cls_cells[(int64_t)c * a.cls_cap + row0 + tid] : -1;
+    const int g = row < nrows ? a.cls_cells[(int64_t)c * a.cls_cap + row0 + row] : -1;
     const int64_t fi = g >= 0 ? (int64_t)g - a.far_first : 0;
     double ls = 0.0;
-    if (g >= 0) {
+    if (g >= 0 && half == 0) {
       int l = a.l_min;
       while (l < a.L && (int64_t)g >= a.lev_first[l + 1]) ++l;
       ls = a.log_abs_scale[l];
     }
     double L0 = 0.0;
     const int E = a.sten_len[c];
+    const uint16_t *ops_c = a.sten_ops + c * FAR_MAX;
     for (int e = 0; e < E; ++e, ++it) {
       const int s = it & 1;
       const uint32_t use = it >> 1;
-      unsigned char *A_hi = smem + s * STAGE, *A_lo = A_hi + A_BYTES;
-      unsigned char *B_hi = A_lo + A_BYTES;
+      unsigned char *A0 = smem + s * STAGE, *A1 = A0 + A_BYTES;
       if (use >= 1) {
         if (!mbar_wait(&bars[2 + s], (use - 1) & 1)) *s_abort = 1;
       }
-      const int op = a.sten_ops[c * FAR_MAX + e];
-      if (tid == 0 && !*s_abort) {
-        mbar_expect_tx(&bars[s], 3 * B_BYTES);
-        bulk_g2s(B_hi, a.btab + (size_t)op * 3 * B_BYTES, 3 * B_BYTES, &bars[s]);
-        if (s) ++full_use1; else ++full_use0;
-      }
-      // gather row tid: source multipole of entry e, split into TF32 hi / lo
+      const int op = ops_c[e];
+      if (tid == 0 && e == 0 && !*s_abort) issue_b(it, op);   // later entries are prefetched
+      // gather half a row: source multipole of entry e, split into TF32 A0 + A1
       const int src = g >= 0 ? a.far_full[fi * FAR_MAX + e] : -1;
-      float v[K];
-      const float4 *row = reinterpret_cast<const float4 *>(a.ma + (int64_t)(src >= 0 ? src : 0) * a.P);
+      const float4 *rowp = reinterpret_cast<const float4 *>(a.ma + (int64_t)(src >= 0 ? src : 0) * a.P);
       const float qf = src >= 0 ? (float)a.mQ[src] : 0.f;
 #pragma unroll
-      for (int q = 0; q < K / 4; ++q) {
-        const float4 f = (src >= 0 && 4 * q < 2 * p) ? row[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-        v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
-      }
+      for (int qq = 0; qq < QH; ++qq) {
+        const int q = half * QH + qq;
+        float4 f = (src >= 0 && 4 * q < 2 * p) ? rowp[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float v[4] = {f.x, f.y, f.z, f.w};
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        v[k] = k < 2 * p ? v[k] : 0.f;
-        v[k] = k == 2 * p ? qf : v[k];
-      }
-      if (src >= 0) L0 += a.mQ[src] * (ls + a.logz[op]);
-#pragma unroll
-      for (int q = 0; q < K / 4; ++q) {
+        for (int j = 0; j < 4; ++j) {
+          const int k = 4 * q + j;
+          v[j] = k < 2 * p ? v[j] : (k == 2 * p ? qf : 0.f);
+        }
         float4 h, l;
-        h.x = tf32_rna(v[4 * q]);     l.x = tf32_rna(v[4 * q] - h.x);
-        h.y = tf32_rna(v[4 * q + 1]); l.y = tf32_rna(v[4 * q + 1] - h.y);
-        h.z = tf32_rna(v[4 * q + 2]); l.z = tf32_rna(v[4 * q + 2] - h.z);
-        h.w = tf32_rna(v[4 * q + 3]); l.w = tf32_rna(v[4 * q + 3] - h.w);
-        const uint32_t off = core_off(tid, 4 * q, K);
-        *reinterpret_cast<float4 *>(A_hi + off) = h;
-        *reinterpret_cast<float4 *>(A_lo + off) = l;
+        h.x = tf32_rna(v[0]); l.x = tf32_rna(v[0] - h.x);
+        h.y = tf32_rna(v[1]); l.y = tf32_rna(v[1] - h.y);
+        h.z = tf32_rna(v[2]); l.z = tf32_rna(v[2] - h.z);
+        h.w = tf32_rna(v[3]); l.w = tf32_rna(v[3] - h.w);
+        const uint32_t off = core_off(row, 4 * q, K);
+        *reinterpret_cast<float4 *>(A0 + off) = h;
+        *reinterpret_cast<float4 *>(A1 + off) = l;
       }
+      if (src >= 0 && half == 0) L0 += a.mQ[src] * (ls + a.logz[op]);
       fence_proxy_async();
       __syncthreads();
       if (*s_abort) break;
@@ -246,26 +257,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcArgs a) {
           *s_abort = 1;
         } else {
           tc_fence_after();
-          const uint32_t a0 = smem_u32(A_hi), a1 = a0 + A_BYTES;
+          const uint32_t a0 = smem_u32(A0), a1 = a0 + A_BYTES;
           const uint32_t b0 = a1 + A_BYTES, b1 = b0 + B_BYTES, b2 = b1 + B_BYTES;
+          const uint32_t acc = tmem + (uint32_t)(e % NACC) * ACC;
 #pragma unroll
           for (int ks = 0; ks < K / 8; ++ks) {
             const uint32_t o = ks * 2 * LBO;
-            const uint64_t da0 = sdesc(a0 + o, LBO, SBO_A), da1 = sdesc(a1 + o, LBO, SBO_A);
-            const uint32_t acc = tmem + (uint32_t)(e % NACC) * 64;
-            mma_tf32(acc, da0, sdesc(b0 + o, LBO, SBO_B), IDESC, (e >= NACC || ks > 0) ? 1u : 0u);
-            mma_tf32(acc, da0, sdesc(b1 + o, LBO, SBO_B), IDESC, 1u);
-            mma_tf32(acc, da0, sdesc(b2 + o, LBO, SBO_B), IDESC, 1u);
-            mma_tf32(acc, da1, sdesc(b0 + o, LBO, SBO_B), IDESC, 1u);
-            mma_tf32(acc, da1, sdesc(b1 + o, LBO, SBO_B), IDESC, 1u);
+            const uint64_t da0 = sdesc(a0 + o, LBO, SBO), da1 = sdesc(a1 + o, LBO, SBO);
+            mma_tf32(acc, da0, sdesc(b0 + o, LBO, SBO), IDESC, (e >= NACC || ks > 0) ? 1u : 0u);
+            mma_tf32(acc, da0, sdesc(b1 + o, LBO, SBO), IDESC, 1u);
+            mma_tf32(acc, da0, sdesc(b2 + o, LBO, SBO), IDESC, 1u);
+            mma_tf32(acc, da1, sdesc(b0 + o, LBO, SBO), IDESC, 1u);
+            mma_tf32(acc, da1, sdesc(b1 + o, LBO, SBO), IDESC, 1u);
           }
           mma_commit(&bars[2 + s]);
+          // prefetch the next entry's operator into the other stage once the
+          // MMAs that last read that stage have finished
+          if (e + 1 < E) {
+            const uint32_t nu = (it + 1) >> 1;
+            if (nu >= 1 && !mbar_wait(&bars[2 + ((it + 1) & 1)], (nu - 1) & 1)) *s_abort = 1;
+            else issue_b(it + 1, ops_c[e + 1]);
+          }
         }
       }
     }
     __syncthreads();
     if (*s_abort) break;
-    // wait for the last commit of this tile, then read the accumulator
+    // wait for the last commit of this tile, then read the accumulators
     {
       const uint32_t last = it - 1;
       if (!mbar_wait(&bars[2 + (last & 1)], (last >> 1) & 1)) *s_abort = 1;
@@ -273,16 +291,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcArgs a) {
     tc_fence_after();
     __syncthreads();
     if (*s_abort) break;
-    // sum the used accumulators in FP64, 16 columns at a time
+    // sum the used accumulators in FP64, 16 columns at a time; warps 0-3 take
+    // the even column chunks, warps 4-7 the odd ones (same TMEM lanes)
     const int nacc = E < NACC ? E : NACC;
+    const uint32_t lane_base = ((uint32_t)((warp & 3) * 32)) << 16;
 #pragma unroll
     for (int q = 0; q < N / 16; ++q) {
+      if ((q & 1) != half) continue;
       double d[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) d[i] = 0.0;
       for (int ac = 0; ac < nacc; ++ac) {
         float t16[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)ac * 64 + q * 16, t16);
+        tmem_ld16(tmem + lane_base + (uint32_t)ac * ACC + q * 16, t16);
 #pragma unroll
         for (int i = 0; i < 16; ++i) d[i] += (double)t16[i];
       }
@@ -307,15 +328,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcArgs a) {
       if (full_use1) mbar_wait(&bars[1], (full_use1 - 1) & 1);
     }
   } else if (it > 0 && tid == 0) {
-    // every commit has been waited on except possibly the other stage's last
     const uint32_t last = it - 1;
     mbar_wait(&bars[2 + (last & 1)], (last >> 1) & 1);
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
-  (void)lane;
+  if (warp == 0) tmem_dealloc(tmem, COLS);
 }
 
 template <int K, int N>
@@ -326,7 +345,7 @@ cudaError_t launch_tc(const TcArgs &a, int64_t n_far_cells, cudaStream_t s) {
                                        (int)smem);
   if (e != cudaSuccess) return e;
   int64_t tiles = (n_far_cells + TC_M - 1) / TC_M + a.n_classes;
-  int grid = (int)std::min<int64_t>(tiles, a.sms);
+  int grid = (int)std::min<int64_t>(tiles, (int64_t)a.sms * TcShape<N>::CTAS);
   if (grid < 1) return cudaSuccess;
   k_m2l_tc<K, N><<<grid, TC_THREADS, smem, s>>>(a);
   return cudaGetLastError();
@@ -343,6 +362,7 @@ uint32_t tf32_round_host(float x) {
 }  // namespace
 
 bool tc_shape(int p, int *K, int *N) {
+  if (p <= 15) { *K = 32; *N = 32; return true; }
   if (p <= 23) { *K = 48; *N = 48; return true; }
   if (p <= 27) { *K = 56; *N = 64; return true; }
   if (p <= 31) { *K = 64; *N = 64; return true; }
@@ -389,6 +409,7 @@ void tc_build_tables(const std::vector<double> &re, const std::vector<double> &i
 
 cudaError_t launch_m2l_tc(const TcArgs &a, int K, int N, int64_t n_far_cells, cudaStream_t s) {
   if (n_far_cells <= 0) return cudaSuccess;
+  if (K == 32 && N == 32) return launch_tc<32, 32>(a, n_far_cells, s);
   if (K == 48 && N == 48) return launch_tc<48, 48>(a, n_far_cells, s);
   if (K == 56 && N == 64) return launch_tc<56, 64>(a, n_far_cells, s);
   if (K == 64 && N == 64) return launch_tc<64, 64>(a, n_far_cells, s);

@@ -30,7 +30,7 @@ EXPORTS = {"src_keys": 1, "src_perm": 2, "tgt_keys": 3, "tgt_perm": 4, "cells": 
 SYMBOLS = ["fmm2d_default_params", "fmm2d_plan_create", "fmm2d_plan_set_domain", "fmm2d_build",
            "fmm2d_evaluate", "fmm2d_plan_query", "fmm2d_debug_export", "fmm2d_plan_set_profiling",
            "fmm2d_stage_times", "fmm2d_plan_destroy", "fmm2d_last_error",
-           "fmm2d_keys_sort_noalloc"]
+           "fmm2d_keys_sort_noalloc", "fmm2d_autotune"]
 
 
 class Info(ctypes.Structure):
@@ -81,6 +81,9 @@ def lib():
     L.fmm2d_keys_sort_noalloc.argtypes = [c_int, c_int, dbl, ctypes.POINTER(dbl), vp, i64,
                                           ctypes.c_uint, vp, vp, vp, ctypes.c_char_p,
                                           ctypes.c_size_t]
+    L.fmm2d_autotune.argtypes = [c_int, dbl, ctypes.c_uint, ctypes.POINTER(dbl), vp, i64, vp, i64,
+                                 vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                                 ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
     for name in SYMBOLS:
         if name not in ("fmm2d_plan_destroy", "fmm2d_last_error"):
             getattr(L, name).restype = c_int
@@ -126,6 +129,19 @@ def fmm2d_keys_sort_noalloc(tiling, levels, leaf_scale, domain, xy, n, flags, ke
                                        _ptr(perm_out), _stream(stream), buf, 256)
     if st:
         raise FMM2DError(st, buf.value.decode())
+
+
+def fmm2d_autotune(tiling, eps, flags, src_xy, n_src, tgt_xy, n_tgt, domain=None, stream=None):
+    """Measured choice of (L, p); returns (levels, p, err, ms) (see include/fmm2d.h)."""
+    L, p = ctypes.c_int(), ctypes.c_int()
+    err, ms = ctypes.c_double(), ctypes.c_double()
+    dom = None if domain is None else (ctypes.c_double * 3)(*domain)
+    st = lib().fmm2d_autotune(TILINGS.get(tiling, tiling), float(eps), int(flags), dom, _ptr(src_xy),
+                              int(n_src), _ptr(tgt_xy), int(n_tgt), _stream(stream), ctypes.byref(L),
+                              ctypes.byref(p), ctypes.byref(err), ctypes.byref(ms))
+    if st:
+        raise FMM2DError(st, "fmm2d_autotune")
+    return L.value, p.value, err.value, ms.value
 
 
 class Plan:

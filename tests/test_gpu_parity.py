@@ -179,3 +179,24 @@ def test_full_size_sampled(tiling, prec):
     ref = direct(x64, u.astype(np.float64), x64[idx])
     err = np.max(np.abs(phi[idx] - ref)) / np.max(np.abs(ref))
     assert err < 1e-6, err
+
+
+@pytest.mark.parametrize("tiling", ["quad", "sept", "tri"])
+def test_autotuned_benchmark_configuration(tiling):
+    """The configuration bench.py times: N = M = 2^20, FP32, tensor-core M2L,
+    (L, p) from fmm2d_autotune for eps = 1e-6.  The tuner's own probe error is
+    <= eps/3 and the potentials of the benchmark strengths are within eps of
+    the oracle's direct sum on 384 sampled targets."""
+    import torch
+    from paper_1204_3105_gb300 import fmm2d
+    n = 2 ** 20
+    xy, u = uniform_square(n, seed=2, dtype=np.float32)
+    x_d = torch.from_numpy(xy).cuda()
+    flags = fmm2d.PREC_MIXED_TC | fmm2d.IN_F32
+    L, p, err, ms = fmm2d.fmm2d_autotune(tiling, 1e-6, flags, x_d, n, x_d, n)
+    assert 0 < err <= 1e-6 / 3 and ms > 0
+    phi, _ = run_gpu(tiling, xy, u, levels=L, p=p, prec="tc", f32=True)
+    x64 = xy.astype(np.float64)
+    idx = sample_targets(n, 384, seed=7)
+    ref = direct(x64, u.astype(np.float64), x64[idx])
+    assert np.max(np.abs(phi[idx] - ref)) / np.max(np.abs(ref)) < 1e-6
