@@ -192,7 +192,7 @@ def run_ours(args):
         step(warm)
     torch.cuda.synchronize()
     for t in args.tilings:
-        plans[t].set_profiling(True)
+        plans[t].set_profiling(not args.no_profile)
     per = {t: [] for t in args.tilings}
     if dist:
         dist.barrier()
@@ -232,9 +232,10 @@ def run_ours(args):
             e2e.append(time.perf_counter() - t0)
     e2e_v = ws * len(args.tilings) * N_POINTS / statistics.mean(e2e)
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel (ALU peaks measured on this device)
     peaks, src = _peaks()
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu = fmm2d.fmm2d_measure_alu_peaks()
+    sm_count = alu["sms"]
     clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     tot = {}
     for t in args.tilings:
@@ -243,23 +244,26 @@ def run_ours(args):
             tot[k][0] += ms / args.steps
             tot[k][1] += n / args.steps
     dom = max(tot, key=lambda k: tot[k][0])
-    if dom == "p2p":
+    if tot[dom][0] <= 0.0:
+        roof = None
+    elif dom == "p2p":
+        # one MUFU log2 per pair; peak = measured lg2 throughput
         pairs = sum(info[t]["n_p2p_pairs"] for t in args.tilings)
-        peak = sm_count * MUFU_PER_CLK_SM * clk_mhz * 1e6 / 1e9
+        peak = alu["lg2_gops"]
         ach = pairs / (tot[dom][0] / 1e3) / 1e9
         roof = {"kernel": "p2p", "bound": "alu", "achieved": ach, "peak": peak, "unit": "Gpair/s",
                 "frac": ach / peak, "traffic": None,
-                "peak_source": "%d SMs x %d lg2/clk x %.0f MHz" % (sm_count, MUFU_PER_CLK_SM, clk_mhz)}
+                "peak_source": "measured MUFU lg2 rate (fmm2d_measure_alu_peaks), one lg2 per pair"}
     else:
         fl = 0.0
         for t in args.tilings:
             p = info[t]["p"]
             fl += info[t]["n_m2l"] * 8.0 * p * (p + 1)
-        peak = sm_count * FP32_LANES_SM * 2 * clk_mhz * 1e6 / 1e12
+        peak = alu["fp32_tflops"]
         ach = fl / (tot[dom][0] / 1e3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": None,
-                "peak_source": "%d SMs x %d FP32 lanes x 2 x %.0f MHz" % (sm_count, FP32_LANES_SM, clk_mhz)}
+                "peak_source": "measured FP32 FMA rate (fmm2d_measure_alu_peaks)"}
 
     cpu_v, cpu_dt = (None, None)
     if rank == 0 and not args.no_cpu_baseline:
@@ -285,6 +289,8 @@ def run_ours(args):
                            for t in args.tilings},
             "roofline": roof,
             "peaks_source": src,
+            "alu_peaks": alu,
+            "stage_ms_total": {k: v[0] for k, v in tot.items()},
             "cpu_baseline": None if cpu_v is None else {
                 "value": cpu_v, "unit": "points/s", "cores": 1, "kind": "oracle",
                 "sample": "N=M=%d per tiling, 3 tilings, one FP64 evaluation (%.1f s)" % (args.ref_points, cpu_dt)},
@@ -312,6 +318,7 @@ def main():
     ap.add_argument("--ref-points", type=int, default=16384)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="a-priori L and p instead of fmm2d_autotune")
+    ap.add_argument("--no-profile", action="store_true", help="no per-stage events in the timed region")
     ap.add_argument("--params", default="", help="fixed L and p per tiling, e.g. quad:7:12,sept:5:13")
     args = ap.parse_args()
     args.tilings = tuple(args.tilings.split(","))

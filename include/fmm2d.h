@@ -209,6 +209,18 @@ void fmm2d_plan_destroy(fmm2d_plan *plan);
 const char *fmm2d_last_error(const fmm2d_plan *plan);
 
 /*
+ * fmm2d_measure_alu_peaks - measured peak rates of the units the kernels are
+ * bound by, for roofline denominators (the paper has no counterpart).
+ *   out[0]: FP32 FMA throughput, TFLOP/s (2 flops per FMA)
+ *   out[1]: MUFU log2 throughput, 1e9 results/s
+ *   out[2]: FP64 FMA throughput, TFLOP/s
+ *   out[3]: number of SMs
+ * Runs three short kernels on the current device (legacy default stream) and
+ * synchronises.  Errors: FMM2D_EINVAL, FMM2D_ENOMEM, FMM2D_ECUDA.
+ */
+fmm2d_status fmm2d_measure_alu_peaks(double *out_host);
+
+/*
  * fmm2d_autotune - choose the leaf level L and expansion order p for a
  * point set by measurement (the a-priori p of Sec. 8, kappa^(p+1) <= eps, is a
  * worst-case bound and far larger than typical inputs need).

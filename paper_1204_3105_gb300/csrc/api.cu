@@ -559,7 +559,8 @@ fmm2d_status evaluate_t(fmm2d_plan *pl, const void *u, double *out, cudaStream_t
     CK(launch_p2p<R>(a.leaf_first, a.n_leaves, src4, tgt, tstride, (const int *)pl->d_src_start.p,
                      (const int *)pl->d_src_end.p, tst, ten, (const int *)pl->d_near_cnt.p,
                      (const int *)pl->d_near_src.p, (const double2 *)pl->d_cell_ctr.p,
-                     (double *)pl->d_phi_near.p, s),
+                     (double *)pl->d_phi_near.p,
+                     a.n_leaves > 0 ? (double)pl->n_tgt / (double)a.n_leaves : 0.0, s),
        "p2p");
   }
   {

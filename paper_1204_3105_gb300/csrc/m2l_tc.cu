@@ -17,7 +17,7 @@
 // once to 22 significant bits) and the precomputed operator in three
 // (B = B0 + B1 + B2, 33 bits).  Five products A0.B0 + A0.B1 + A0.B2 + A1.B0 +
 // A1.B1, accumulated in FP32 in tensor memory (entries spread round-robin over
-// eight accumulators that are summed in FP64), leave out only terms of
+// eight accumulators added with compensation at the end), leave out only terms of
 // relative size 2^-33, so the result has FP32-class accuracy (the one-time
 // 22-bit rounding of A, 2^-23, dominates).  The Q log|z0| part of L_0 is
 // accumulated separately in FP64 on the CUDA cores.
@@ -150,23 +150,32 @@ __host__ __device__ __forceinline__ uint32_t core_off(int row, int k, int K) {
 }
 
 // Accumulator column stride and CTAs per SM for a shape.
-template <int N> struct TcShape {
+template <int K, int N> struct TcShape {
   static constexpr uint32_t ACC = N <= 32 ? 32 : 64;
   static constexpr uint32_t COLS = NACC * ACC;            // 256 or 512 TMEM columns
   static constexpr int CTAS = N <= 32 ? 2 : 1;
+  static constexpr int NB = K <= 48 ? 4 : 2;              // operator stages
+  static constexpr int D = NB - 2;                        // operator prefetch distance
+  static constexpr uint32_t A_BYTES = 128 * K * 4, B_BYTES = N * K * 4;
+  static constexpr uint32_t SMEM = 2 * (2 * A_BYTES) + NB * (3 * B_BYTES);
 };
 
 template <int K, int N>
-__global__ void __launch_bounds__(TC_THREADS, TcShape<N>::CTAS) k_m2l_tc(TcArgs a) {
+__global__ void __launch_bounds__(TC_THREADS, (TcShape<K, N>::CTAS)) k_m2l_tc(TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  constexpr uint32_t A_BYTES = TC_M * K * 4, B_BYTES = N * K * 4;
-  constexpr uint32_t STAGE = 2 * A_BYTES + 3 * B_BYTES;
+  using SH = TcShape<K, N>;
+  constexpr uint32_t A_BYTES = SH::A_BYTES, B_BYTES = SH::B_BYTES;
+  constexpr int NB = SH::NB, D = SH::D;
   constexpr uint32_t SBO = (K / 4) * 128, LBO = 128;
   constexpr uint32_t IDESC = idesc_tf32(TC_M, N);
-  constexpr uint32_t ACC = TcShape<N>::ACC, COLS = TcShape<N>::COLS;
+  constexpr uint32_t ACC = SH::ACC, COLS = SH::COLS;
   constexpr int QH = K / 8;                 // 16-byte chunks of a row per half
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * STAGE);   // full[2], mma[2]
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4);
+  // layout: A stages [2] x (A0, A1), operator stages [NB] x (B0, B1, B2), then
+  // barriers: mma[2] (A stage released), full[NB] (operator landed)
+  unsigned char *const Bbase = smem + 2 * (2 * A_BYTES);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SH::SMEM);
+  uint64_t *mma_bar = bars, *full_bar = bars + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 + NB);
   int *s_cnt = reinterpret_cast<int *>(tmem_slot + 2);               // [MAX_CLASSES]
   volatile int *s_abort = s_cnt + MAX_CLASSES;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -174,7 +183,7 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<N>::CTAS) k_m2l_tc(TcArgs 
 
   if (warp == 0) tmem_alloc(tmem_slot, COLS);
   if (tid == 0) {
-    for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
+    for (int i = 0; i < 2 + NB; ++i) mbar_init(&bars[i], 1);
     fence_barrier_init();
     *s_abort = 0;
   }
@@ -186,16 +195,16 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<N>::CTAS) k_m2l_tc(TcArgs 
   int total_tiles = 0;
   for (int c = 0; c < a.n_classes; ++c) total_tiles += (s_cnt[c] + TC_M - 1) / TC_M;
 
-  uint32_t it = 0;                          // stage uses so far (global over tiles)
-  uint32_t full_use0 = 0, full_use1 = 0;    // bulk copies issued per stage (thread 0)
+  uint32_t it = 0;                          // entries processed so far (global over tiles)
+  uint32_t issued = 0;                      // operator copies issued (thread 0)
   const int p = a.p;
-  // thread 0: issue the operator copy of stage use `u` (entry of operator op)
+  // thread 0: issue the operator copy of global entry u into stage u % NB
   auto issue_b = [&](uint32_t u, int op) {
-    const int st = u & 1;
-    unsigned char *B0 = smem + st * STAGE + 2 * A_BYTES;
-    mbar_expect_tx(&bars[st], 3 * B_BYTES);
-    bulk_g2s(B0, a.btab + (size_t)op * 3 * B_BYTES, 3 * B_BYTES, &bars[st]);
-    if (st) ++full_use1; else ++full_use0;
+    const int st = u % NB;
+    unsigned char *B0 = Bbase + st * (3 * B_BYTES);
+    mbar_expect_tx(&full_bar[st], 3 * B_BYTES);
+    bulk_g2s(B0, a.btab + (size_t)op * 3 * B_BYTES, 3 * B_BYTES, &full_bar[st]);
+    issued = u + 1;
   };
   for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
     int c = 0, t0 = tile;
@@ -216,24 +225,49 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<N>::CTAS) k_m2l_tc(TcArgs 
     double L0 = 0.0;
     const int E = a.sten_len[c];
     const uint16_t *ops_c = a.sten_ops + c * FAR_MAX;
+    const int *srcs = a.far_full + fi * FAR_MAX;
+    // software pipeline of the gather: the rows of entry e+1 are loaded while
+    // entry e is split, stored and multiplied; source indices two ahead
+    auto load_row = [&](int src, float4 (&f)[QH], double &q) {
+      const float4 *rowp = reinterpret_cast<const float4 *>(a.ma + (int64_t)(src >= 0 ? src : 0) * a.P);
+#pragma unroll
+      for (int qq = 0; qq < QH; ++qq) {
+        const int qi = half * QH + qq;
+        f[qq] = (src >= 0 && 4 * qi < 2 * p) ? rowp[qi] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      q = src >= 0 ? a.mQ[src] : 0.0;
+    };
+    int src = g >= 0 ? srcs[0] : -1;
+    int src_n = (g >= 0 && E > 1) ? srcs[1] : -1;
+    float4 fc[QH];
+    double qc;
+    load_row(src, fc, qc);
     for (int e = 0; e < E; ++e, ++it) {
       const int s = it & 1;
       const uint32_t use = it >> 1;
-      unsigned char *A0 = smem + s * STAGE, *A1 = A0 + A_BYTES;
+      unsigned char *A0 = smem + s * (2 * A_BYTES), *A1 = A0 + A_BYTES;
+      // A stage s and operator stage (it + D) % NB were last read by the MMAs
+      // of entry it - 2
       if (use >= 1) {
-        if (!mbar_wait(&bars[2 + s], (use - 1) & 1)) *s_abort = 1;
+        if (!mbar_wait(&mma_bar[s], (use - 1) & 1)) *s_abort = 1;
       }
       const int op = ops_c[e];
-      if (tid == 0 && e == 0 && !*s_abort) issue_b(it, op);   // later entries are prefetched
-      // gather half a row: source multipole of entry e, split into TF32 A0 + A1
-      const int src = g >= 0 ? a.far_full[fi * FAR_MAX + e] : -1;
-      const float4 *rowp = reinterpret_cast<const float4 *>(a.ma + (int64_t)(src >= 0 ? src : 0) * a.P);
-      const float qf = src >= 0 ? (float)a.mQ[src] : 0.f;
+      if (tid == 0 && !*s_abort) {
+        if (e == 0)
+          for (int d = 0; d < D && d < E; ++d) issue_b(it + d, ops_c[d]);
+        if (e + D < E) issue_b(it + D, ops_c[e + D]);
+      }
+      float4 fn[QH];
+      double qn = 0.0;
+      int src_nn = -1;
+      if (e + 1 < E) load_row(src_n, fn, qn);
+      if (g >= 0 && e + 2 < E) src_nn = srcs[e + 2];
+      // split the current row into TF32 A0 + A1 (Q sits at index 2p)
+      const float qf = (float)qc;
 #pragma unroll
       for (int qq = 0; qq < QH; ++qq) {
         const int q = half * QH + qq;
-        float4 f = (src >= 0 && 4 * q < 2 * p) ? rowp[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float v[4] = {f.x, f.y, f.z, f.w};
+        float v[4] = {fc[qq].x, fc[qq].y, fc[qq].z, fc[qq].w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int k = 4 * q + j;
@@ -248,17 +282,18 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<N>::CTAS) k_m2l_tc(TcArgs 
         *reinterpret_cast<float4 *>(A0 + off) = h;
         *reinterpret_cast<float4 *>(A1 + off) = l;
       }
-      if (src >= 0 && half == 0) L0 += a.mQ[src] * (ls + a.logz[op]);
+      if (src >= 0 && half == 0) L0 += qc * (ls + a.logz[op]);
       fence_proxy_async();
       __syncthreads();
       if (*s_abort) break;
       if (tid == 0) {
-        if (!mbar_wait(&bars[s], ((s ? full_use1 : full_use0) - 1) & 1)) {
+        const int bs = it % NB;
+        if (!mbar_wait(&full_bar[bs], (it / NB) & 1)) {
           *s_abort = 1;
         } else {
           tc_fence_after();
           const uint32_t a0 = smem_u32(A0), a1 = a0 + A_BYTES;
-          const uint32_t b0 = a1 + A_BYTES, b1 = b0 + B_BYTES, b2 = b1 + B_BYTES;
+          const uint32_t b0 = smem_u32(Bbase + bs * (3 * B_BYTES)), b1 = b0 + B_BYTES, b2 = b1 + B_BYTES;
           const uint32_t acc = tmem + (uint32_t)(e % NACC) * ACC;
 #pragma unroll
           for (int ks = 0; ks < K / 8; ++ks) {
@@ -270,50 +305,53 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<N>::CTAS) k_m2l_tc(TcArgs 
             mma_tf32(acc, da1, sdesc(b0 + o, LBO, SBO), IDESC, 1u);
             mma_tf32(acc, da1, sdesc(b1 + o, LBO, SBO), IDESC, 1u);
           }
-          mma_commit(&bars[2 + s]);
-          // prefetch the next entry's operator into the other stage once the
-          // MMAs that last read that stage have finished
-          if (e + 1 < E) {
-            const uint32_t nu = (it + 1) >> 1;
-            if (nu >= 1 && !mbar_wait(&bars[2 + ((it + 1) & 1)], (nu - 1) & 1)) *s_abort = 1;
-            else issue_b(it + 1, ops_c[e + 1]);
-          }
+          mma_commit(&mma_bar[s]);
         }
       }
+#pragma unroll
+      for (int qq = 0; qq < QH; ++qq) fc[qq] = fn[qq];
+      qc = qn;
+      src = src_n;
+      src_n = src_nn;
     }
     __syncthreads();
     if (*s_abort) break;
     // wait for the last commit of this tile, then read the accumulators
     {
       const uint32_t last = it - 1;
-      if (!mbar_wait(&bars[2 + (last & 1)], (last >> 1) & 1)) *s_abort = 1;
+      if (!mbar_wait(&mma_bar[last & 1], (last >> 1) & 1)) *s_abort = 1;
     }
     tc_fence_after();
     __syncthreads();
     if (*s_abort) break;
-    // sum the used accumulators in FP64, 16 columns at a time; warps 0-3 take
-    // the even column chunks, warps 4-7 the odd ones (same TMEM lanes)
+    // sum the used accumulators in FP32 with Kahan compensation, 16 columns
+    // at a time; warps 0-3 take the even column chunks, warps 4-7 the odd
+    // ones (same TMEM lanes)
     const int nacc = E < NACC ? E : NACC;
     const uint32_t lane_base = ((uint32_t)((warp & 3) * 32)) << 16;
 #pragma unroll
     for (int q = 0; q < N / 16; ++q) {
       if ((q & 1) != half) continue;
-      double d[16];
+      float d[16], cmp[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) d[i] = 0.0;
+      for (int i = 0; i < 16; ++i) d[i] = cmp[i] = 0.f;
       for (int ac = 0; ac < nacc; ++ac) {
         float t16[16];
         tmem_ld16(tmem + lane_base + (uint32_t)ac * ACC + q * 16, t16);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) d[i] += (double)t16[i];
+        for (int i = 0; i < 16; ++i) {
+          const float y = t16[i] - cmp[i];
+          const float t = d[i] + y;
+          cmp[i] = (t - d[i]) - y;
+          d[i] = t;
+        }
       }
       if (g >= 0) {
-        if (q == 0) a.lL0[g] = L0 + d[0];
+        if (q == 0) a.lL0[g] = L0 + (double)d[0];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int l = 8 * q + i;
-          if (l >= 1 && l <= p)
-            a.lb[(int64_t)g * a.P + l - 1] = make_float2((float)d[2 * i], (float)d[2 * i + 1]);
+          if (l >= 1 && l <= p) a.lb[(int64_t)g * a.P + l - 1] = make_float2(d[2 * i], d[2 * i + 1]);
         }
       }
     }
@@ -323,13 +361,13 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<N>::CTAS) k_m2l_tc(TcArgs 
   if (*s_abort) {
     if (tid == 0) {
       atomicOr(a.err, 1);
-      // let the bulk copies in flight land before the CTA exits
-      if (full_use0) mbar_wait(&bars[0], (full_use0 - 1) & 1);
-      if (full_use1) mbar_wait(&bars[1], (full_use1 - 1) & 1);
+      // let the operator copies in flight land before the CTA exits: the
+      // copies of entries it .. issued-1 were not waited on
+      for (uint32_t u = it; u < issued; ++u) mbar_wait(&full_bar[u % NB], (u / NB) & 1);
     }
   } else if (it > 0 && tid == 0) {
     const uint32_t last = it - 1;
-    mbar_wait(&bars[2 + (last & 1)], (last >> 1) & 1);
+    mbar_wait(&mma_bar[last & 1], (last >> 1) & 1);
   }
   tc_fence_before();
   __syncthreads();
@@ -339,13 +377,13 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<N>::CTAS) k_m2l_tc(TcArgs 
 
 template <int K, int N>
 cudaError_t launch_tc(const TcArgs &a, int64_t n_far_cells, cudaStream_t s) {
-  constexpr size_t STAGE = 2 * (size_t)TC_M * K * 4 + 3 * (size_t)N * K * 4;
-  const size_t smem = 2 * STAGE + 4 * 8 + 8 + (MAX_CLASSES + 1) * 4 + 16;
+  using SH = TcShape<K, N>;
+  const size_t smem = SH::SMEM + (2 + SH::NB) * 8 + 8 + (MAX_CLASSES + 1) * 4 + 16;
   cudaError_t e = cudaFuncSetAttribute(k_m2l_tc<K, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   int64_t tiles = (n_far_cells + TC_M - 1) / TC_M + a.n_classes;
-  int grid = (int)std::min<int64_t>(tiles, (int64_t)a.sms * TcShape<N>::CTAS);
+  int grid = (int)std::min<int64_t>(tiles, (int64_t)a.sms * SH::CTAS);
   if (grid < 1) return cudaSuccess;
   k_m2l_tc<K, N><<<grid, TC_THREADS, smem, s>>>(a);
   return cudaGetLastError();

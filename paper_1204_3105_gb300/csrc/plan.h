@@ -194,6 +194,6 @@ cudaError_t launch_p2p(int64_t leaf_first, int64_t n_leaves, const R *src4, cons
                        int tstride, const int *src_start, const int *src_end,
                        const int *tgt_start, const int *tgt_end, const int *near_cnt,
                        const int *near_src, const double2 *ctr, double *phi_near,
-                       cudaStream_t s);
+                       double mean_targets, cudaStream_t s);
 
 }  // namespace fmm2d

@@ -30,7 +30,7 @@ EXPORTS = {"src_keys": 1, "src_perm": 2, "tgt_keys": 3, "tgt_perm": 4, "cells": 
 SYMBOLS = ["fmm2d_default_params", "fmm2d_plan_create", "fmm2d_plan_set_domain", "fmm2d_build",
            "fmm2d_evaluate", "fmm2d_plan_query", "fmm2d_debug_export", "fmm2d_plan_set_profiling",
            "fmm2d_stage_times", "fmm2d_plan_destroy", "fmm2d_last_error",
-           "fmm2d_keys_sort_noalloc", "fmm2d_autotune"]
+           "fmm2d_keys_sort_noalloc", "fmm2d_autotune", "fmm2d_measure_alu_peaks"]
 
 
 class Info(ctypes.Structure):
@@ -84,6 +84,7 @@ def lib():
     L.fmm2d_autotune.argtypes = [c_int, dbl, ctypes.c_uint, ctypes.POINTER(dbl), vp, i64, vp, i64,
                                  vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                                  ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+    L.fmm2d_measure_alu_peaks.argtypes = [ctypes.POINTER(dbl)]
     for name in SYMBOLS:
         if name not in ("fmm2d_plan_destroy", "fmm2d_last_error"):
             getattr(L, name).restype = c_int
@@ -142,6 +143,15 @@ def fmm2d_autotune(tiling, eps, flags, src_xy, n_src, tgt_xy, n_tgt, domain=None
     if st:
         raise FMM2DError(st, "fmm2d_autotune")
     return L.value, p.value, err.value, ms.value
+
+
+def fmm2d_measure_alu_peaks():
+    """{"fp32_tflops", "lg2_gops", "fp64_tflops", "sms"} measured on the current device."""
+    out = (ctypes.c_double * 4)()
+    st = lib().fmm2d_measure_alu_peaks(out)
+    if st:
+        raise FMM2DError(st, "fmm2d_measure_alu_peaks")
+    return {"fp32_tflops": out[0], "lg2_gops": out[1], "fp64_tflops": out[2], "sms": int(out[3])}
 
 
 class Plan:
