@@ -519,7 +519,7 @@ fmm2d_status evaluate_t(fmm2d_plan *pl, const void *u, double *out, cudaStream_t
     t.n_classes = pl->sten.n_classes;
     t.sms = pl->n_sms;
     t.far_first = pl->lev_first[pl->l_min];
-    t.cls_cap = std::max<int64_t>(1, pl->n_far_cells);
+    t.cls_cap = pl->cls_cap;
     t.cls_cnt = (const int *)pl->d_cls_cnt.p;
     t.cls_cells = (const int *)pl->d_cls_cells.p;
     t.far_full = (const int *)pl->d_far_full.p;
@@ -695,8 +695,9 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
     if (!pl->same_sets) CK(launch_keys(g, tgt, f32, n_tgt, kt, pt, (int *)pl->d_err.p, s), "keys");
   }
   {
-    const int per_sort = n_src > 1 ? 5 * ((bits + 7) / 8) : 0;
-    const int per_sort_t = n_tgt > 1 ? 5 * ((bits + 7) / 8) : 0;
+    const int per_pass = (int64_t)256 * ((std::max<int64_t>(1, nmax) + 4095) / 4096) <= 8192 ? 3 : 5;
+    const int per_sort = n_src > 1 ? per_pass * ((bits + 7) / 8) : 0;
+    const int per_sort_t = n_tgt > 1 ? per_pass * ((bits + 7) / 8) : 0;
     StageScope sc(pl, ST_SORT, s, per_sort + (pl->same_sets ? 0 : per_sort_t));
     CK(radix_sort_pairs(ks, ps, (uint32_t *)pl->d_tmp_k.p, (uint32_t *)pl->d_tmp_v.p, n_src, bits,
                         pl->d_sort_scratch.p, s), "sort");
@@ -704,10 +705,43 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
       CK(radix_sort_pairs(kt, pt, (uint32_t *)pl->d_tmp_k.p, (uint32_t *)pl->d_tmp_v.p, n_tgt, bits,
                           pl->d_sort_scratch.p, s), "sort");
   }
-  int64_t lev_first_h[MAXLEV + 2];
-  int err_h = 0;
+  // ---- capacities: a level holds at most min(b^l, points) occupied cells,
+  // so every later buffer and launch can be sized before the counts are known
+  // and the build needs no host synchronisation until its end
+  const int64_t npts = pl->same_sets ? n_src : n_src + n_tgt;
+  int64_t cap_l[MAXLEV + 2], cap_cells = 0, pw = 1;
+  for (int l = 0; l <= L; ++l) {
+    cap_l[l] = std::max<int64_t>(1, std::min<int64_t>(pw, npts));
+    cap_cells += cap_l[l];
+    pw = pw > ((int64_t)1 << 40) ? pw : pw * pl->b;
+  }
+  const int lo_level = L >= pl->l_min ? pl->l_min : L;   // first level with lists
+  int64_t cap_list = 0;
+  for (int l = lo_level; l <= L; ++l) cap_list += cap_l[l];
+  const int64_t cap_leaf = cap_l[L];
+  const size_t csz = f64 ? sizeof(double2) : sizeof(float2);
+  CK(dbuf_reserve(pl->d_src_start, cap_cells * 4), "alloc");
+  CK(dbuf_reserve(pl->d_src_end, cap_cells * 4), "alloc");
+  CK(dbuf_reserve(pl->d_tgt_start, cap_cells * 4), "alloc");
+  CK(dbuf_reserve(pl->d_tgt_end, cap_cells * 4), "alloc");
+  CK(dbuf_reserve(pl->d_mQ, cap_cells * 8), "alloc");
+  CK(dbuf_reserve(pl->d_lL0, cap_cells * 8), "alloc");
+  CK(dbuf_reserve(pl->d_ma, cap_cells * pl->P * csz), "alloc");
+  CK(dbuf_reserve(pl->d_lb, cap_cells * pl->P * csz), "alloc");
+  CK(dbuf_reserve(pl->d_far_cnt, cap_list * 4), "alloc");
+  CK(dbuf_reserve(pl->d_far_src, cap_list * FAR_MAX * 4), "alloc");
+  CK(dbuf_reserve(pl->d_far_op, cap_list * FAR_MAX * 2), "alloc");
+  if (tc) {
+    CK(dbuf_reserve(pl->d_far_full, cap_list * FAR_MAX * 4), "alloc");
+    CK(dbuf_reserve(pl->d_cls_cnt, MAX_CLASSES * 4), "alloc");
+    CK(dbuf_reserve(pl->d_cls_cells, (size_t)MAX_CLASSES * cap_list * 4), "alloc");
+  }
+  CK(dbuf_reserve(pl->d_dev_err, 16), "alloc");
+  CK(dbuf_reserve(pl->d_near_cnt, cap_leaf * 4), "alloc");
+  CK(dbuf_reserve(pl->d_near_src, cap_leaf * NEAR_MAX * 4), "alloc");
+  pl->cls_cap = cap_list;
   {
-    StageScope sc(pl, ST_TREE, s, (pl->same_sets ? 1 : 2) + 3 + 1 + 1);
+    StageScope sc(pl, ST_TREE, s, (pl->same_sets ? 1 : 2) + (ms <= 8192 ? 1 : 3) + 1 + 1);
     CK(cudaMemsetAsync(pl->d_occ.p, 0, ms * 4, s), "memset");
     CK(cudaMemsetAsync(pl->d_hsrc.p, 0, ms * 4, s), "memset");
     CK(launch_mark(g, ks, n_src, (int *)pl->d_occ.p, (int *)pl->d_hsrc.p, s), "mark");
@@ -716,10 +750,42 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
     CK(launch_compact(g, (const int *)pl->d_occ.p, (const int *)pl->d_scan.p, (const int *)pl->d_hsrc.p,
                       ms, (int *)pl->d_map.p, (uint32_t *)pl->d_cell_key.p, (int4 *)pl->d_cell_crd.p,
                       (double2 *)pl->d_cell_ctr.p, (uint8_t *)pl->d_cell_cls.p,
-                      (uint8_t *)pl->d_cell_hsrc.p, s), "compact");
+                      (uint8_t *)pl->d_cell_hsrc.p, (int *)pl->d_src_start.p, (int *)pl->d_src_end.p,
+                      pl->same_sets ? nullptr : (int *)pl->d_tgt_start.p,
+                      pl->same_sets ? nullptr : (int *)pl->d_tgt_end.p, s), "compact");
     CK(launch_level_first(g, (const int *)pl->d_scan.p, (const int *)pl->d_occ.p, ms,
                           (int64_t *)pl->d_lev_first.p, s), "levels");
   }
+  {
+    StageScope sc(pl, ST_TREE, s, pl->same_sets ? 2 : 4);
+    CK(launch_leaf_ranges(g, ks, n_src, (const int *)pl->d_map.p, (int *)pl->d_src_start.p,
+                          (int *)pl->d_src_end.p, s), "ranges");
+    if (!pl->same_sets)
+      CK(launch_leaf_ranges(g, kt, n_tgt, (const int *)pl->d_map.p, (int *)pl->d_tgt_start.p,
+                            (int *)pl->d_tgt_end.p, s), "ranges");
+    CK(launch_rel_coords(g, f32, !f64, src, ps, ks, n_src, (const int *)pl->d_map.p,
+                         (const double2 *)pl->d_cell_ctr.p, pl->d_src4.p, 4, s), "rel");
+    if (!pl->same_sets)
+      CK(launch_rel_coords(g, f32, !f64, tgt, pt, kt, n_tgt, (const int *)pl->d_map.p,
+                           (const double2 *)pl->d_cell_ctr.p, pl->d_tgt2.p, 2, s), "rel");
+  }
+  {
+    StageScope sc(pl, ST_LISTS, s, 1);
+    if (tc) CK(cudaMemsetAsync(pl->d_cls_cnt.p, 0, MAX_CLASSES * 4, s), "memset");
+    CK(cudaMemsetAsync(pl->d_dev_err.p, 0, 16, s), "memset");
+    CK(launch_lists(g, (const Stencils *)pl->d_sten.p, lo_level, pl->l_min, cap_list,
+                    (const int *)pl->d_map.p, (const uint8_t *)pl->d_cell_cls.p,
+                    (const int4 *)pl->d_cell_crd.p, (const uint8_t *)pl->d_cell_hsrc.p,
+                    (int *)pl->d_far_cnt.p, (int *)pl->d_far_src.p, (uint16_t *)pl->d_far_op.p,
+                    (int *)pl->d_near_cnt.p, (int *)pl->d_near_src.p,
+                    (const int64_t *)pl->d_lev_first.p, tc ? (int *)pl->d_far_full.p : nullptr,
+                    tc ? (int *)pl->d_cls_cnt.p : nullptr, tc ? (int *)pl->d_cls_cells.p : nullptr,
+                    cap_list, s), "lists");
+  }
+  // ---- the one synchronisation: level counts for the evaluation and the
+  // domain check
+  int64_t lev_first_h[MAXLEV + 2];
+  int err_h = 0;
   CK(cudaMemcpyAsync(lev_first_h, pl->d_lev_first.p, (L + 2) * 8, cudaMemcpyDeviceToHost, s), "readback");
   CK(cudaMemcpyAsync(&err_h, pl->d_err.p, 4, cudaMemcpyDeviceToHost, s), "readback");
   CK(cudaStreamSynchronize(s), "build sync");
@@ -728,78 +794,8 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
   pl->n_cells = lev_first_h[L + 1];
   for (int l = 0; l <= L; ++l) pl->lev_count[l] = pl->lev_first[l + 1] - pl->lev_first[l];
   for (int l = L + 1; l <= MAXLEV + 1; ++l) pl->lev_first[l] = pl->n_cells;
-  // ---- cell-sized buffers
-  const int64_t nc = std::max<int64_t>(1, pl->n_cells);
-  const size_t csz = f64 ? sizeof(double2) : sizeof(float2);
-  CK(dbuf_reserve(pl->d_src_start, nc * 4), "alloc");
-  CK(dbuf_reserve(pl->d_src_end, nc * 4), "alloc");
-  CK(dbuf_reserve(pl->d_tgt_start, nc * 4), "alloc");
-  CK(dbuf_reserve(pl->d_tgt_end, nc * 4), "alloc");
-  CK(dbuf_reserve(pl->d_mQ, nc * 8), "alloc");
-  CK(dbuf_reserve(pl->d_lL0, nc * 8), "alloc");
-  CK(dbuf_reserve(pl->d_ma, nc * pl->P * csz), "alloc");
-  CK(dbuf_reserve(pl->d_lb, nc * pl->P * csz), "alloc");
   const int64_t lfirst = L >= pl->l_min ? pl->lev_first[pl->l_min] : pl->n_cells;
   pl->n_far_cells = pl->n_cells - lfirst;
-  const int64_t nfar = std::max<int64_t>(1, pl->n_far_cells);
-  const int64_t nleaf = std::max<int64_t>(1, pl->lev_count[L]);
-  CK(dbuf_reserve(pl->d_far_cnt, std::max(nfar, nleaf) * 4), "alloc");
-  CK(dbuf_reserve(pl->d_far_src, nfar * FAR_MAX * 4), "alloc");
-  CK(dbuf_reserve(pl->d_far_op, nfar * FAR_MAX * 2), "alloc");
-  if (tc) {
-    CK(dbuf_reserve(pl->d_far_full, nfar * FAR_MAX * 4), "alloc");
-    CK(dbuf_reserve(pl->d_cls_cnt, MAX_CLASSES * 4), "alloc");
-    CK(dbuf_reserve(pl->d_cls_cells, (size_t)MAX_CLASSES * nfar * 4), "alloc");
-    CK(cudaMemsetAsync(pl->d_cls_cnt.p, 0, MAX_CLASSES * 4, s), "memset");
-  }
-  CK(dbuf_reserve(pl->d_dev_err, 16), "alloc");
-  CK(cudaMemsetAsync(pl->d_dev_err.p, 0, 16, s), "memset");
-  CK(dbuf_reserve(pl->d_near_cnt, nleaf * 4), "alloc");
-  CK(dbuf_reserve(pl->d_near_src, nleaf * NEAR_MAX * 4), "alloc");
-  {
-    StageScope sc(pl, ST_TREE, s, pl->same_sets ? 2 : 4);
-    CK(cudaMemsetAsync(pl->d_src_start.p, 0, nc * 4, s), "memset");
-    CK(cudaMemsetAsync(pl->d_src_end.p, 0, nc * 4, s), "memset");
-    CK(launch_leaf_ranges(g, ks, n_src, (const int *)pl->d_map.p, (int *)pl->d_src_start.p,
-                          (int *)pl->d_src_end.p, s), "ranges");
-    if (!pl->same_sets) {
-      CK(cudaMemsetAsync(pl->d_tgt_start.p, 0, nc * 4, s), "memset");
-      CK(cudaMemsetAsync(pl->d_tgt_end.p, 0, nc * 4, s), "memset");
-      CK(launch_leaf_ranges(g, kt, n_tgt, (const int *)pl->d_map.p, (int *)pl->d_tgt_start.p,
-                            (int *)pl->d_tgt_end.p, s), "ranges");
-    }
-    CK(launch_rel_coords(g, f32, !f64, src, ps, ks, n_src, (const int *)pl->d_map.p,
-                         (const double2 *)pl->d_cell_ctr.p, pl->d_src4.p, 4, s), "rel");
-    if (!pl->same_sets)
-      CK(launch_rel_coords(g, f32, !f64, tgt, pt, kt, n_tgt, (const int *)pl->d_map.p,
-                           (const double2 *)pl->d_cell_ctr.p, pl->d_tgt2.p, 2, s), "rel");
-  }
-  if (pl->n_far_cells > 0) {
-    StageScope sc(pl, ST_LISTS, s, 1);
-    CK(launch_lists2(g, (const Stencils *)pl->d_sten.p, lfirst, pl->n_far_cells,
-                     (const int *)pl->d_map.p, (const uint8_t *)pl->d_cell_cls.p,
-                     (const int4 *)pl->d_cell_crd.p, (const uint8_t *)pl->d_cell_hsrc.p,
-                     (int *)pl->d_far_cnt.p, (int *)pl->d_far_src.p, (uint16_t *)pl->d_far_op.p,
-                     pl->lev_first[L], (int *)pl->d_near_cnt.p, (int *)pl->d_near_src.p,
-                     (const int64_t *)pl->d_lev_first.p, tc ? (int *)pl->d_far_full.p : nullptr,
-                     tc ? (int *)pl->d_cls_cnt.p : nullptr, tc ? (int *)pl->d_cls_cells.p : nullptr,
-                     nfar, s), "lists");
-  } else {
-    // leaves above l_min: only Near lists are needed; build them with an
-    // empty M2L stencil over the leaf level.
-    Stencils st2 = pl->sten;
-    for (int c = 0; c < MAX_CLASSES; ++c) st2.far_len[c] = 0;
-    CK(dbuf_reserve(pl->d_counts, sizeof(Stencils)), "alloc");
-    CK(cudaMemcpyAsync(pl->d_counts.p, &st2, sizeof(Stencils), cudaMemcpyHostToDevice, s), "upload");
-    CK(cudaStreamSynchronize(s), "sync");
-    StageScope sc(pl, ST_LISTS, s, 1);
-    CK(launch_lists2(g, (const Stencils *)pl->d_counts.p, pl->lev_first[L], pl->lev_count[L],
-                     (const int *)pl->d_map.p, (const uint8_t *)pl->d_cell_cls.p,
-                     (const int4 *)pl->d_cell_crd.p, (const uint8_t *)pl->d_cell_hsrc.p,
-                     (int *)pl->d_far_cnt.p, (int *)pl->d_far_src.p, (uint16_t *)pl->d_far_op.p,
-                     pl->lev_first[L], (int *)pl->d_near_cnt.p, (int *)pl->d_near_src.p,
-                     (const int64_t *)pl->d_lev_first.p, nullptr, nullptr, nullptr, 0, s), "lists");
-  }
   CK(cudaGetLastError(), "build");
   pl->n_m2l = -1;
   pl->n_p2p_pairs = -1;

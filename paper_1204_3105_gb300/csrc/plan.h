@@ -91,6 +91,7 @@ struct Plan {
   DBuf d_counts;
   DBuf d_far_full, d_cls_cnt, d_cls_cells, d_tc_ops, d_dev_err;
   int tc_K = 0, tc_N = 0, n_sms = 148;
+  int64_t cls_cap = 1;
   std::vector<double> m2l_logz_host;
 };
 
@@ -116,7 +117,9 @@ cudaError_t launch_mark(const Geo &g, const uint32_t *key_sorted, int64_t n, int
                         cudaStream_t s);
 cudaError_t launch_compact(const Geo &g, const int *occ, const int *scan, const int *hsrc,
                            int64_t map_size, int *map, uint32_t *cell_key, int4 *cell_crd,
-                           double2 *cell_ctr, uint8_t *cell_cls, uint8_t *cell_hsrc, cudaStream_t s);
+                           double2 *cell_ctr, uint8_t *cell_cls, uint8_t *cell_hsrc,
+                           int *src_start, int *src_end, int *tgt_start, int *tgt_end,
+                           cudaStream_t s);
 cudaError_t launch_leaf_ranges(const Geo &g, const uint32_t *key_sorted, int64_t n, const int *map,
                                int *start, int *end, cudaStream_t s);
 cudaError_t launch_rel_coords(const Geo &g, bool f32_in, bool f32_out, const void *xy,
@@ -125,12 +128,14 @@ cudaError_t launch_rel_coords(const Geo &g, bool f32_in, bool f32_out, const voi
                               cudaStream_t s);
 cudaError_t launch_level_first(const Geo &g, const int *scan, const int *occ, int64_t map_size,
                                int64_t *out, cudaStream_t s);
-cudaError_t launch_lists2(const Geo &g, const Stencils *d_sten, int64_t first, int64_t count,
-                          const int *map, const uint8_t *cell_cls, const int4 *cell_crd,
-                          const uint8_t *cell_hsrc, int *far_cnt, int *far_src, uint16_t *far_op,
-                          int64_t leaf_first, int *near_cnt, int *near_src,
-                          const int64_t *lev_first_dev, int *far_full, int *cls_cnt,
-                          int *cls_cells, int64_t cls_cap, cudaStream_t s);
+// Near lists of the leaves and M2L lists of levels >= l_min, for the cells
+// of levels lo_level..L (count read on the device; cap = launch bound).
+cudaError_t launch_lists(const Geo &g, const Stencils *d_sten, int lo_level, int l_min, int64_t cap,
+                         const int *map, const uint8_t *cell_cls, const int4 *cell_crd,
+                         const uint8_t *cell_hsrc, int *far_cnt, int *far_src, uint16_t *far_op,
+                         int *near_cnt, int *near_src, const int64_t *lev_first_dev,
+                         int *far_full, int *cls_cnt, int *cls_cells, int64_t cls_cap,
+                         cudaStream_t s);
 
 // ---------------------------------------------------------------- expand.cu
 struct ExpandArgs {

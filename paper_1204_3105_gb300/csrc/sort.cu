@@ -76,6 +76,37 @@ __global__ void k_scan_sums(int *sums, int nb) {
   }
 }
 
+// Single block: exclusive scan of n values (in place allowed), chunks of
+// 1024 threads x 8 items with a running carry.  Used for small arrays.
+__global__ void __launch_bounds__(1024) k_scan_single(const int *__restrict__ in,
+                                                      int *__restrict__ out, int64_t n) {
+  __shared__ int sm[33];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  constexpr int IPT = 8;
+  for (int64_t base = 0; base < n; base += 1024 * IPT) {
+    int v[IPT], s = 0;
+    const int64_t b0 = base + (int64_t)threadIdx.x * IPT;
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      v[i] = b0 + i < n ? in[b0 + i] : 0;
+      s += v[i];
+    }
+    int ex;
+    const int tot = block_excl_scan(s, ex, sm);
+    int run = carry + ex;
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      if (b0 + i < n) out[b0 + i] = run;
+      run += v[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+}
+
 __global__ void k_scan_tile(const int *__restrict__ in, int *__restrict__ out, int64_t n,
                             const int *__restrict__ sums) {
   __shared__ int tile[SCAN_TILE];
@@ -176,6 +207,10 @@ size_t scan_scratch_bytes(int64_t n) {
 
 cudaError_t exclusive_scan(const int *in, int *out, int64_t n, void *scratch, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  if (n <= 8192) {   // one launch for small arrays
+    k_scan_single<<<1, 1024, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+  }
   int nb = (int)((n + SCAN_TILE - 1) / SCAN_TILE);
   int *sums = (int *)scratch;
   k_scan_reduce<<<nb, SCAN_TH, 0, s>>>(in, n, sums);

@@ -45,7 +45,9 @@ __global__ void k_compact(Geo g, const int *__restrict__ occ, const int *__restr
                           const int *__restrict__ hsrc, int64_t map_size, int *__restrict__ map,
                           uint32_t *__restrict__ cell_key, int4 *__restrict__ cell_crd,
                           double2 *__restrict__ cell_ctr, uint8_t *__restrict__ cell_cls,
-                          uint8_t *__restrict__ cell_hsrc) {
+                          uint8_t *__restrict__ cell_hsrc, int *__restrict__ src_start,
+                          int *__restrict__ src_end, int *__restrict__ tgt_start,
+                          int *__restrict__ tgt_end) {
   int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (m >= map_size) return;
   if (!occ[m]) {
@@ -57,6 +59,8 @@ __global__ void k_compact(Geo g, const int *__restrict__ occ, const int *__restr
   const int slot = scan[m];
   map[m] = slot;
   cell_key[slot] = key;
+  src_start[slot] = src_end[slot] = 0;   // leaf ranges are filled in later
+  if (tgt_start) tgt_start[slot] = tgt_end[slot] = 0;
   cell_hsrc[slot] = (uint8_t)(hsrc[m] != 0);
   int4 crd = make_int4(0, 0, 0, 0);
   double X, Y;    // centre in the tiling frame
@@ -145,23 +149,25 @@ __device__ __forceinline__ bool cell_at(const Geo &g, int l, int4 c, uint32_t *k
   return tri_coords_to_key(c.x, c.y, c.z, l, key);
 }
 
-__global__ void k_lists(Geo g, const Stencils *__restrict__ st, int64_t first, int64_t count,
+__global__ void k_lists(Geo g, const Stencils *__restrict__ st, int lo_level, int l_min,
                         const int *__restrict__ map, const uint8_t *__restrict__ cell_cls,
                         const int4 *__restrict__ cell_crd, const uint8_t *__restrict__ cell_hsrc,
-                        int64_t lev_first_lmin, int *__restrict__ far_cnt,
-                        int *__restrict__ far_src, uint16_t *__restrict__ far_op,
-                        int64_t leaf_first, int *__restrict__ near_cnt, int *__restrict__ near_src,
-                        const int64_t *__restrict__ lev_first, int *__restrict__ far_full,
-                        int *__restrict__ cls_cnt, int *__restrict__ cls_cells, int64_t cls_cap) {
-  int64_t gslot = first + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (gslot >= first + count) return;
-  int l = 0;
+                        int *__restrict__ far_cnt, int *__restrict__ far_src,
+                        uint16_t *__restrict__ far_op, int *__restrict__ near_cnt,
+                        int *__restrict__ near_src, const int64_t *__restrict__ lev_first,
+                        int *__restrict__ far_full, int *__restrict__ cls_cnt,
+                        int *__restrict__ cls_cells, int64_t cls_cap) {
+  const int64_t first = lev_first[lo_level];
+  const int64_t gslot = first + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gslot >= lev_first[g.L + 1]) return;
+  int l = lo_level;
   while (l < g.L && gslot >= lev_first[l + 1]) ++l;
   const int4 c = cell_crd[gslot];
   const int cls = cell_cls[gslot];
-  const int64_t fi = gslot - lev_first_lmin;
+  const int64_t fi = gslot - first;
+  const int n_far = l >= l_min ? st->far_len[cls] : 0;
   int cnt = 0;
-  for (int e = 0; e < st->far_len[cls]; ++e) {
+  for (int e = 0; e < n_far; ++e) {
     int4 q = make_int4(c.x + st->far_d[cls][e][0], c.y + st->far_d[cls][e][1],
                        c.z + st->far_d[cls][e][2], 0);
     uint32_t k;
@@ -177,14 +183,14 @@ __global__ void k_lists(Geo g, const Stencils *__restrict__ st, int64_t first, i
     ++cnt;
   }
   far_cnt[fi] = cnt;
-  if (cls_cnt && st->far_len[cls] > 0) {
+  if (cls_cnt && n_far > 0) {
     // group the M2L targets by stencil class for the tensor-core M2L
     int pos = atomicAdd(&cls_cnt[cls], 1);
     cls_cells[(int64_t)cls * cls_cap + pos] = (int)gslot;
   }
-  if (gslot >= leaf_first) {
+  if (l == g.L) {
     const int o = (g.tiling == FMM2D_TRI && c.w == 0) ? 1 : 0;
-    const int64_t ni = gslot - leaf_first;
+    const int64_t ni = gslot - lev_first[g.L];
     int nc = 0;
     for (int e = 0; e < st->near_len[o]; ++e) {
       int4 q = make_int4(c.x + st->near_d[o][e][0], c.y + st->near_d[o][e][1],
@@ -214,9 +220,11 @@ cudaError_t launch_mark(const Geo &g, const uint32_t *key_sorted, int64_t n, int
 cudaError_t launch_compact(const Geo &g, const int *occ, const int *scan, const int *hsrc,
                            int64_t map_size, int *map, uint32_t *cell_key, int4 *cell_crd,
                            double2 *cell_ctr, uint8_t *cell_cls, uint8_t *cell_hsrc,
+                           int *src_start, int *src_end, int *tgt_start, int *tgt_end,
                            cudaStream_t s) {
   k_compact<<<nblk(map_size, 256), 256, 0, s>>>(g, occ, scan, hsrc, map_size, map, cell_key,
-                                                 cell_crd, cell_ctr, cell_cls, cell_hsrc);
+                                                 cell_crd, cell_ctr, cell_cls, cell_hsrc, src_start,
+                                                 src_end, tgt_start, tgt_end);
   return cudaGetLastError();
 }
 
@@ -250,17 +258,16 @@ cudaError_t launch_rel_coords(const Geo &g, bool f32_in, bool f32_out, const voi
   return cudaGetLastError();
 }
 
-cudaError_t launch_lists2(const Geo &g, const Stencils *d_sten, int64_t first, int64_t count,
-                          const int *map, const uint8_t *cell_cls, const int4 *cell_crd,
-                          const uint8_t *cell_hsrc, int *far_cnt, int *far_src, uint16_t *far_op,
-                          int64_t leaf_first, int *near_cnt, int *near_src,
-                          const int64_t *lev_first_dev, int *far_full, int *cls_cnt,
-                          int *cls_cells, int64_t cls_cap, cudaStream_t s) {
-  if (count <= 0) return cudaSuccess;
-  k_lists<<<nblk(count, 128), 128, 0, s>>>(g, d_sten, first, count, map, cell_cls, cell_crd,
-                                            cell_hsrc, first, far_cnt, far_src, far_op, leaf_first,
-                                            near_cnt, near_src, lev_first_dev, far_full, cls_cnt,
-                                            cls_cells, cls_cap);
+cudaError_t launch_lists(const Geo &g, const Stencils *d_sten, int lo_level, int l_min, int64_t cap,
+                         const int *map, const uint8_t *cell_cls, const int4 *cell_crd,
+                         const uint8_t *cell_hsrc, int *far_cnt, int *far_src, uint16_t *far_op,
+                         int *near_cnt, int *near_src, const int64_t *lev_first_dev,
+                         int *far_full, int *cls_cnt, int *cls_cells, int64_t cls_cap,
+                         cudaStream_t s) {
+  if (cap <= 0) return cudaSuccess;
+  k_lists<<<nblk(cap, 128), 128, 0, s>>>(g, d_sten, lo_level, l_min, map, cell_cls, cell_crd,
+                                          cell_hsrc, far_cnt, far_src, far_op, near_cnt, near_src,
+                                          lev_first_dev, far_full, cls_cnt, cls_cells, cls_cap);
   return cudaGetLastError();
 }
 
