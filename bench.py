@@ -307,6 +307,79 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _pool(n_max, seed):
+    """Two seeded point sets (uniform, 8-cluster mixture) of n_max FP32 points;
+    a request of size n uses the first n points of one of them."""
+    from paper_1204_3105_gb300.inputs import gaussian_mixture, uniform_square
+    uxy, uu = uniform_square(n_max, seed=seed, dtype=np.float32)
+    gxy, gu = gaussian_mixture(n_max, seed=seed + 1, k=8, dtype=np.float32)
+    return (uxy, uu), (gxy, gu.astype(np.float32))
+
+
+def run_server_workload(args):
+    """Batched instances (--workload batch) or a Poisson request stream
+    (--workload serve) through fmm2d_serve_*, host buffers in and out."""
+    from paper_1204_3105_gb300 import fmm2d
+    from paper_1204_3105_gb300.inputs import rng
+    fmm2d.lib()
+    g = rng(SEED + 40)
+    if args.workload == "batch":
+        count = args.instances
+        sizes = np.exp(g.uniform(np.log(256), np.log(65536), count)).astype(np.int64)
+        tilings = g.integers(0, 3, count)
+        eps = np.full(count, 1e-6)
+        cluster = np.zeros(count, bool)
+        arrivals = np.zeros(count)
+        n_max = int(sizes.max())
+    else:
+        lam = args.rate
+        count = max(1, int(lam * args.duration))
+        arrivals = np.cumsum(g.exponential(1.0 / lam, count))
+        sizes = np.exp(g.uniform(np.log(1e3), np.log(2e6), count)).astype(np.int64)
+        tilings = g.integers(0, 3, count)
+        eps = np.where(g.random(count) < 0.5, 1e-4, 1e-8)
+        cluster = g.random(count) < 0.5
+        n_max = int(sizes.max())
+    (uxy, uu), (gxy, gu) = _pool(n_max, SEED + 41)
+    names = ("quad", "sept", "tri")
+    sv = fmm2d.Server(int(args.budget_gb * (1 << 30)), max_slots=args.slots)
+    outs, tickets, t_sub = [], [], []
+    t0 = time.perf_counter()
+    for i in range(count):
+        wait = t0 + arrivals[i] - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        xy, u = (gxy, gu) if cluster[i] else (uxy, uu)
+        n = int(sizes[i])
+        o = np.empty(n)
+        outs.append(o)
+        tickets.append(sv.submit(names[tilings[i]], xy[:n], u[:n], o, eps=float(eps[i])))
+    res = [sv.wait(t, 600000.0) for t in tickets]
+    t1 = time.perf_counter()
+    sv.close()
+    lat = np.array([r["latency_ms"] for r in res])
+    ok = sum(r["status"] == 0 for r in res)
+    points = int(sizes.sum())
+    line = {
+        "metric": ("batched FMM points/s (4096-instance config)" if args.workload == "batch"
+                   else "served FMM requests: p50/p99 latency and points/s"),
+        "value": points / (t1 - t0), "unit": "points/s", "n_gpus": 1,
+        "higher_is_better": True, "data": "synthetic", "workload": args.workload,
+        "requests": count, "completed_ok": int(ok), "wall_s": t1 - t0,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "max": float(lat.max())},
+        "run_ms_mean": float(np.mean([r["run_ms"] for r in res])),
+        "config": {"slots": args.slots, "hbm_budget_gb": args.budget_gb,
+                   "sizes": "log-uniform [256, 65536]" if args.workload == "batch"
+                   else "log-uniform [1e3, 2e6]",
+                   "eps": "1e-6" if args.workload == "batch" else "1e-4 / 1e-8 (FP64 form)",
+                   "arrival_rate_per_s": None if args.workload == "batch" else args.rate,
+                   "points": "uniform" if args.workload == "batch" else "uniform / 8-cluster mixture",
+                   "io": "host numpy buffers, copies inside each request"},
+    }
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -320,8 +393,17 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="a-priori L and p instead of fmm2d_autotune")
     ap.add_argument("--no-profile", action="store_true", help="no per-stage events in the timed region")
     ap.add_argument("--params", default="", help="fixed L and p per tiling, e.g. quad:7:12,sept:5:13")
+    ap.add_argument("--workload", default="fmm", choices=["fmm", "batch", "serve"])
+    ap.add_argument("--instances", type=int, default=4096, help="batch: number of instances")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: arrivals per second")
+    ap.add_argument("--duration", type=float, default=1.0, help="serve: seconds of arrivals")
+    ap.add_argument("--slots", type=int, default=16, help="batch/serve: server slots")
+    ap.add_argument("--budget-gb", type=float, default=80.0, help="batch/serve: HBM budget")
     args = ap.parse_args()
     args.tilings = tuple(args.tilings.split(","))
+    if args.workload != "fmm" and args.impl != "reference":
+        run_server_workload(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -126,6 +126,13 @@ fmm2d_status fmm2d_plan_create(int tiling, int levels, int p, double eps, unsign
                                fmm2d_plan **out);
 
 /*
+ * fmm2d_plan_set_params - change the leaf level, expansion order and
+ * tolerance of a plan (same meaning and ranges as fmm2d_plan_create); the
+ * plan's device memory is kept and reused.  Invalidates a previous build.
+ */
+fmm2d_status fmm2d_plan_set_params(fmm2d_plan *plan, int levels, int p, double eps);
+
+/*
  * fmm2d_plan_set_domain - set the domain square [x0, x0+S) x [y0, y0+S)
  * (S > 0).  Every source and target must lie in it (else fmm2d_build returns
  * FMM2D_EDOMAIN).  Invalidates a previous build.
@@ -278,6 +285,82 @@ fmm2d_status fmm2d_keys_sort_noalloc(int tiling, int levels, double leaf_scale,
                                      const double *domain, const void *xy_dev, int64_t n,
                                      unsigned flags, uint32_t *keys_sorted_dev, uint32_t *perm_dev,
                                      void *stream, char *err_buf, size_t err_cap);
+
+/* ------------------------------------------------------------------------
+ * Serving: a continuous-batching server for FMM solves.  The paper has no
+ * serving layer; each request runs the evaluation of fmm2d_build +
+ * fmm2d_evaluate.
+ * ---------------------------------------------------------------------- */
+typedef struct fmm2d_server fmm2d_server;
+
+/* One solve.  All pointers are HOST memory owned by the caller and must stay
+ * valid until the request completes. */
+typedef struct {
+  int32_t tiling;          /* fmm2d_tiling */
+  int32_t levels;          /* leaf level, 0 = planner */
+  int32_t p;               /* expansion order, 0 = from eps */
+  uint32_t flags;          /* FMM2D_IN_F32 and optionally FMM2D_PREC_*; with no
+                              precision bit the server uses the tensor-core
+                              mixed form for eps >= 1e-6 and FP64 below */
+  double eps;
+  double domain[3];        /* x0, y0, S; S <= 0 means the unit square */
+  const void *src_xy;      /* n_src interleaved points */
+  int64_t n_src;
+  const void *tgt_xy;      /* n_tgt points, or NULL: targets = sources */
+  int64_t n_tgt;
+  const void *strengths;   /* n_src values */
+  double *potentials;      /* output, one per target */
+} fmm2d_request;
+
+typedef struct {
+  int32_t status;          /* fmm2d_status of the solve */
+  int32_t levels, p;       /* parameters used */
+  uint32_t flags;          /* precision used */
+  int32_t slot;            /* execution slot that ran it */
+  double queue_ms;         /* submit -> start */
+  double run_ms;           /* start -> potentials in host memory */
+  double latency_ms;       /* submit -> completion */
+} fmm2d_result;
+
+typedef struct {
+  int64_t queued, running, completed;
+  size_t bytes_in_use, budget_bytes;
+  int32_t slots;
+} fmm2d_serve_info;
+
+/*
+ * fmm2d_serve_create - start a server on the current device with `max_slots`
+ * execution slots (host threads, each with its own stream and plans; 1..256)
+ * and an HBM budget in bytes for the requests running at once.
+ * Errors: FMM2D_EINVAL, FMM2D_ENOMEM, FMM2D_ECUDA (no device).
+ */
+fmm2d_status fmm2d_serve_create(size_t hbm_budget_bytes, int max_slots, fmm2d_server **out);
+
+/*
+ * fmm2d_serve_submit - queue a request (non-blocking) and return its ticket.
+ * Requests are admitted oldest first as a slot frees and their memory
+ * estimate fits the budget next to the running ones; a request that does not
+ * fit lets later, smaller ones go first.  Errors: FMM2D_EINVAL (bad request),
+ * FMM2D_EBUSY (its estimate alone exceeds the budget), FMM2D_ENOMEM.
+ */
+fmm2d_status fmm2d_serve_submit(fmm2d_server *server, const fmm2d_request *request,
+                                uint64_t *ticket);
+
+/* fmm2d_serve_poll - FMM2D_ENOTREADY while the request runs; FMM2D_OK once it
+ * is complete (the result is copied and the ticket released).  EINVAL for an
+ * unknown ticket. */
+fmm2d_status fmm2d_serve_poll(fmm2d_server *server, uint64_t ticket, fmm2d_result *result);
+
+/* fmm2d_serve_wait - block until the request completes or `timeout_ms`
+ * passes (FMM2D_ETIMEOUT, ticket kept). */
+fmm2d_status fmm2d_serve_wait(fmm2d_server *server, uint64_t ticket, double timeout_ms,
+                              fmm2d_result *result);
+
+/* fmm2d_serve_stats - queue and memory counters. */
+fmm2d_status fmm2d_serve_stats(fmm2d_server *server, fmm2d_serve_info *info);
+
+/* fmm2d_serve_destroy - finish running requests, drop queued ones, free all. */
+void fmm2d_serve_destroy(fmm2d_server *server);
 
 #ifdef __cplusplus
 }

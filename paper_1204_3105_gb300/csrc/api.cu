@@ -367,7 +367,12 @@ void flush_events(fmm2d_plan *pl) {
 }
 
 // Geometry, stencils and operator tables for the current (tiling, L, p).
+// Skipped when the plan already holds them for the same parameters.
 fmm2d_status setup_geometry(fmm2d_plan *pl) {
+  if (pl->geo_valid && pl->geo_key_L == pl->L && pl->geo_key_p == pl->p &&
+      pl->geo_key_x0 == pl->x0 && pl->geo_key_y0 == pl->y0 && pl->geo_key_S == pl->S)
+    return FMM2D_OK;
+  pl->geo_valid = false;
   Geo &g = pl->geo;
   g.tiling = pl->tiling;
   g.L = pl->L;
@@ -466,6 +471,12 @@ fmm2d_status setup_geometry(fmm2d_plan *pl) {
   CK(dbuf_reserve(pl->d_geo_scale, (MAXLEV + 1) * sizeof(double)), "alloc scale");
   CK(cudaMemcpy(pl->d_geo_scale.p, pl->log_abs_scale, (MAXLEV + 1) * sizeof(double),
                 cudaMemcpyHostToDevice), "upload scale");
+  pl->geo_valid = true;
+  pl->geo_key_L = pl->L;
+  pl->geo_key_p = pl->p;
+  pl->geo_key_x0 = pl->x0;
+  pl->geo_key_y0 = pl->y0;
+  pl->geo_key_S = pl->S;
   return FMM2D_OK;
 }
 
@@ -614,6 +625,18 @@ fmm2d_status fmm2d_plan_create(int tiling, int levels, int p, double eps, unsign
   pl->b = tiling == FMM2D_SEPT ? 7 : 4;
   pl->l_min = tiling == FMM2D_SEPT ? 1 : 2;
   *out = pl;
+  return FMM2D_OK;
+}
+
+fmm2d_status fmm2d_plan_set_params(fmm2d_plan *pl, int levels, int p, double eps) {
+  if (!pl) return FMM2D_EINVAL;
+  if (levels < 0 || levels > max_levels(pl->tiling)) return fail(pl, FMM2D_EINVAL, "levels out of range");
+  if (p < 0 || p > MAXP) return fail(pl, FMM2D_EINVAL, "p out of range (0..48)");
+  if (p == 0 && !(eps > 0.0 && eps < 1.0)) return fail(pl, FMM2D_EINVAL, "eps must be in (0, 1)");
+  pl->levels_req = levels;
+  pl->p_req = p;
+  pl->eps = eps;
+  pl->built = false;
   return FMM2D_OK;
 }
 

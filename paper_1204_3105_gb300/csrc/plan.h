@@ -92,6 +92,10 @@ struct Plan {
   DBuf d_far_full, d_cls_cnt, d_cls_cells, d_tc_ops, d_dev_err;
   int tc_K = 0, tc_N = 0, n_sms = 148;
   int64_t cls_cap = 1;
+  // parameters the cached geometry / operator tables were built for
+  bool geo_valid = false;
+  int geo_key_L = -1, geo_key_p = -1;
+  double geo_key_x0 = 0, geo_key_y0 = 0, geo_key_S = 0;
   std::vector<double> m2l_logz_host;
 };
 

@@ -1,0 +1,319 @@
+// serve.cu - a continuous-batching server for FMM solves (fmm2d_serve_*).
+//
+// Requests (points, strengths and output in host memory) are queued on
+// submit and admitted, oldest first, as soon as an execution slot is free and
+// the request's device-memory estimate fits in the HBM budget next to the
+// requests already running (a request that does not fit lets smaller,
+// later requests go first).  Each slot is a host thread with its own CUDA
+// stream and its own plans (one per tiling and precision, reused across
+// requests), so the work of several requests overlaps on the device.
+// Completion is reported through fmm2d_serve_poll / fmm2d_serve_wait.
+// The paper has no serving layer; the evaluation each request runs is the
+// FMM of fmm2d_build + fmm2d_evaluate.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "plan.h"
+
+namespace fmm2d {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Job {
+  uint64_t ticket = 0;
+  fmm2d_request req;
+  size_t est_bytes = 0;
+  Clock::time_point t_submit, t_start, t_end;
+  fmm2d_result res;
+  bool done = false;
+};
+
+struct SlotBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  cudaError_t reserve(size_t b) {
+    if (b <= bytes) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e == cudaSuccess) bytes = b;
+    return e;
+  }
+  ~SlotBuf() {
+    if (p) cudaFree(p);
+  }
+};
+
+struct Slot {
+  int id = 0;
+  cudaStream_t stream = nullptr;
+  // plans keyed by (tiling, flags, levels, p): a plan keeps its operator
+  // tables and device memory for requests with the same parameters
+  std::map<std::tuple<int, unsigned, int, int>, fmm2d_plan *> plans;
+  SlotBuf src, tgt, u, out;
+};
+
+// Device-memory estimate of one request: inputs and outputs, the plan's
+// per-point arrays, and its tree (about 1 KB per cell, cells <= points).
+size_t estimate_bytes(const fmm2d_request &r) {
+  const size_t esz = (r.flags & FMM2D_IN_F32) ? 4 : 8;
+  const size_t ns = (size_t)r.n_src, nt = r.tgt_xy ? (size_t)r.n_tgt : 0;
+  const size_t io = ns * 3 * esz + nt * 2 * esz + (r.tgt_xy ? nt : ns) * 8;
+  const size_t pts = (ns + nt) * 96;
+  const size_t tree = (ns + nt) * 1024 / 16 + (32u << 20);
+  return io + pts + tree;
+}
+
+unsigned precision_for(double eps, int p) {
+  // FP32 arithmetic cannot reach tolerances much below 1e-7: FP64 form there
+  if (eps < 1e-6) return FMM2D_PREC_FP64;
+  return p <= 31 ? FMM2D_PREC_MIXED_TC : FMM2D_PREC_MIXED;
+}
+
+}  // namespace
+}  // namespace fmm2d
+
+using namespace fmm2d;
+
+struct fmm2d_server {
+  size_t budget = 0;
+  int device = 0;
+  std::vector<std::unique_ptr<Slot>> slots;
+  std::vector<std::thread> workers;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Job *> queue;
+  std::unordered_map<uint64_t, Job *> jobs;
+  uint64_t next_ticket = 1;
+  size_t in_use = 0;
+  int running = 0;
+  uint64_t completed = 0;
+  bool stop = false;
+};
+
+namespace {
+
+// Pick the first queued job that fits the budget (mu held); nullptr if none.
+Job *admit(fmm2d_server *sv) {
+  for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
+    Job *j = *it;
+    if (sv->in_use + j->est_bytes <= sv->budget || sv->running == 0) {
+      sv->queue.erase(it);
+      sv->in_use += j->est_bytes;
+      ++sv->running;
+      return j;
+    }
+  }
+  return nullptr;
+}
+
+fmm2d_status run_job(Slot &sl, Job &j) {
+  const fmm2d_request &r = j.req;
+  const bool same = r.tgt_xy == nullptr;
+  const int64_t nt = same ? r.n_src : r.n_tgt;
+  const size_t esz = (r.flags & FMM2D_IN_F32) ? 4 : 8;
+  int p = r.p;
+  if (p == 0) fmm2d_default_params(r.tiling, std::max(r.n_src, nt), 64, r.eps, nullptr, &p, nullptr);
+  const unsigned prec = (r.flags & FMM2D_PREC_MASK) ? (r.flags & FMM2D_PREC_MASK) : precision_for(r.eps, p);
+  const unsigned flags = prec | (r.flags & FMM2D_IN_F32);
+  int L = r.levels;
+  if (L == 0) fmm2d_default_params(r.tiling, std::max(r.n_src, nt), 64, r.eps, &L, nullptr, nullptr);
+  auto key = std::make_tuple(r.tiling, flags, L, p);
+  fmm2d_plan *pl = sl.plans[key];
+  fmm2d_status st;
+  if (!pl) {
+    if (sl.plans.size() > 24) {   // bound the cache: drop the other plans of this slot
+      for (auto &kv : sl.plans)
+        if (kv.second) fmm2d_plan_destroy(kv.second);
+      sl.plans.clear();
+    }
+    st = fmm2d_plan_create(r.tiling, L, p, r.eps, flags, &pl);
+    if (st != FMM2D_OK) return st;
+    sl.plans[key] = pl;
+  }
+  const double *dom = r.domain;
+  st = fmm2d_plan_set_domain(pl, dom[2] > 0 ? dom[0] : 0.0, dom[2] > 0 ? dom[1] : 0.0,
+                             dom[2] > 0 ? dom[2] : 1.0);
+  if (st != FMM2D_OK) return st;
+  cudaStream_t s = sl.stream;
+  if (sl.src.reserve(std::max<size_t>(16, r.n_src * 2 * esz)) || sl.u.reserve(std::max<size_t>(16, r.n_src * esz)) ||
+      sl.out.reserve(std::max<size_t>(16, nt * 8)) || (!same && sl.tgt.reserve(std::max<size_t>(16, nt * 2 * esz))))
+    return FMM2D_ENOMEM;
+  if (r.n_src > 0) {
+    cudaMemcpyAsync(sl.src.p, r.src_xy, r.n_src * 2 * esz, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(sl.u.p, r.strengths, r.n_src * esz, cudaMemcpyHostToDevice, s);
+  }
+  if (!same && nt > 0) cudaMemcpyAsync(sl.tgt.p, r.tgt_xy, nt * 2 * esz, cudaMemcpyHostToDevice, s);
+  st = fmm2d_build(pl, sl.src.p, r.n_src, same ? sl.src.p : sl.tgt.p, nt, s);
+  if (st != FMM2D_OK) return st;
+  st = fmm2d_evaluate(pl, sl.u.p, (double *)sl.out.p, s);
+  if (st != FMM2D_OK) return st;
+  if (nt > 0) cudaMemcpyAsync(r.potentials, sl.out.p, nt * 8, cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return FMM2D_ECUDA;
+  fmm2d_info info;
+  fmm2d_plan_query(pl, &info);
+  j.res.levels = info.levels;
+  j.res.p = info.p;
+  j.res.flags = flags;
+  return info.device_error ? FMM2D_ETIMEOUT : FMM2D_OK;
+}
+
+void worker(fmm2d_server *sv, Slot *sl) {
+  cudaSetDevice(sv->device);
+  for (;;) {
+    Job *j = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      sv->cv_work.wait(lk, [&] { return sv->stop || (j = admit(sv)) != nullptr; });
+      if (!j) return;   // stopping
+      j->t_start = Clock::now();
+    }
+    std::memset(&j->res, 0, sizeof(j->res));
+    const fmm2d_status st = run_job(*sl, *j);
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      j->t_end = Clock::now();
+      j->res.status = st;
+      j->res.slot = sl->id;
+      j->res.queue_ms = std::chrono::duration<double, std::milli>(j->t_start - j->t_submit).count();
+      j->res.run_ms = std::chrono::duration<double, std::milli>(j->t_end - j->t_start).count();
+      j->res.latency_ms = std::chrono::duration<double, std::milli>(j->t_end - j->t_submit).count();
+      j->done = true;
+      sv->in_use -= j->est_bytes;
+      --sv->running;
+      ++sv->completed;
+    }
+    sv->cv_done.notify_all();
+    sv->cv_work.notify_all();
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+fmm2d_status fmm2d_serve_create(size_t hbm_budget_bytes, int max_slots, fmm2d_server **out) {
+  if (!out || max_slots < 1 || max_slots > 256 || hbm_budget_bytes == 0) return FMM2D_EINVAL;
+  *out = nullptr;
+  int dev = 0, ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0 || cudaGetDevice(&dev) != cudaSuccess)
+    return FMM2D_ECUDA;
+  fmm2d_server *sv = new (std::nothrow) fmm2d_server();
+  if (!sv) return FMM2D_ENOMEM;
+  sv->budget = hbm_budget_bytes;
+  sv->device = dev;
+  for (int i = 0; i < max_slots; ++i) {
+    auto sl = std::make_unique<Slot>();
+    sl->id = i;
+    if (cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      fmm2d_serve_destroy(sv);
+      return FMM2D_ECUDA;
+    }
+    sv->slots.push_back(std::move(sl));
+  }
+  for (auto &sl : sv->slots) sv->workers.emplace_back(worker, sv, sl.get());
+  *out = sv;
+  return FMM2D_OK;
+}
+
+fmm2d_status fmm2d_serve_submit(fmm2d_server *sv, const fmm2d_request *r, uint64_t *ticket) {
+  if (!sv || !r || !ticket) return FMM2D_EINVAL;
+  if (r->tiling < 0 || r->tiling > 2 || r->n_src < 0 || (r->tgt_xy && r->n_tgt < 0) ||
+      (r->n_src > 0 && (!r->src_xy || !r->strengths)) || !r->potentials ||
+      (r->p == 0 && !(r->eps > 0.0 && r->eps < 1.0)))
+    return FMM2D_EINVAL;
+  Job *j = new (std::nothrow) Job();
+  if (!j) return FMM2D_ENOMEM;
+  j->req = *r;
+  j->est_bytes = estimate_bytes(*r);
+  if (j->est_bytes > sv->budget) {
+    delete j;
+    return FMM2D_EBUSY;   // could never be admitted
+  }
+  j->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    j->ticket = sv->next_ticket++;
+    sv->jobs[j->ticket] = j;
+    sv->queue.push_back(j);
+    *ticket = j->ticket;
+  }
+  sv->cv_work.notify_one();
+  return FMM2D_OK;
+}
+
+fmm2d_status fmm2d_serve_poll(fmm2d_server *sv, uint64_t ticket, fmm2d_result *res) {
+  if (!sv) return FMM2D_EINVAL;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->jobs.find(ticket);
+  if (it == sv->jobs.end()) return FMM2D_EINVAL;
+  if (!it->second->done) return FMM2D_ENOTREADY;
+  if (res) *res = it->second->res;
+  delete it->second;
+  sv->jobs.erase(it);
+  return FMM2D_OK;
+}
+
+fmm2d_status fmm2d_serve_wait(fmm2d_server *sv, uint64_t ticket, double timeout_ms,
+                              fmm2d_result *res) {
+  if (!sv) return FMM2D_EINVAL;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->jobs.find(ticket);
+  if (it == sv->jobs.end()) return FMM2D_EINVAL;
+  Job *j = it->second;
+  const bool ok = sv->cv_done.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms),
+                                       [&] { return j->done; });
+  if (!ok) return FMM2D_ETIMEOUT;
+  if (res) *res = j->res;
+  delete j;
+  sv->jobs.erase(ticket);
+  return FMM2D_OK;
+}
+
+fmm2d_status fmm2d_serve_stats(fmm2d_server *sv, fmm2d_serve_info *info) {
+  if (!sv || !info) return FMM2D_EINVAL;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  info->queued = (int64_t)sv->queue.size();
+  info->running = sv->running;
+  info->completed = (int64_t)sv->completed;
+  info->bytes_in_use = sv->in_use;
+  info->budget_bytes = sv->budget;
+  info->slots = (int32_t)sv->slots.size();
+  return FMM2D_OK;
+}
+
+void fmm2d_serve_destroy(fmm2d_server *sv) {
+  if (!sv) return;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop = true;
+    for (Job *j : sv->queue) {
+      sv->jobs.erase(j->ticket);
+      delete j;
+    }
+    sv->queue.clear();
+  }
+  sv->cv_work.notify_all();
+  for (auto &t : sv->workers) t.join();
+  for (auto &kv : sv->jobs) delete kv.second;
+  for (auto &sl : sv->slots) {
+    for (auto &kv : sl->plans) fmm2d_plan_destroy(kv.second);
+    if (sl->stream) cudaStreamDestroy(sl->stream);
+  }
+  delete sv;
+}
+
+}  // extern "C"

@@ -30,7 +30,9 @@ EXPORTS = {"src_keys": 1, "src_perm": 2, "tgt_keys": 3, "tgt_perm": 4, "cells": 
 SYMBOLS = ["fmm2d_default_params", "fmm2d_plan_create", "fmm2d_plan_set_domain", "fmm2d_build",
            "fmm2d_evaluate", "fmm2d_plan_query", "fmm2d_debug_export", "fmm2d_plan_set_profiling",
            "fmm2d_stage_times", "fmm2d_plan_destroy", "fmm2d_last_error",
-           "fmm2d_keys_sort_noalloc", "fmm2d_autotune", "fmm2d_measure_alu_peaks"]
+           "fmm2d_keys_sort_noalloc", "fmm2d_autotune", "fmm2d_measure_alu_peaks",
+           "fmm2d_plan_set_params", "fmm2d_serve_create", "fmm2d_serve_submit", "fmm2d_serve_poll",
+           "fmm2d_serve_wait", "fmm2d_serve_stats", "fmm2d_serve_destroy"]
 
 
 class Info(ctypes.Structure):
@@ -42,6 +44,26 @@ class Info(ctypes.Structure):
                 ("n_m2l", ctypes.c_int64), ("n_p2p_pairs", ctypes.c_int64),
                 ("n_m2l_ops", ctypes.c_int32), ("max_far", ctypes.c_int32),
                 ("max_near", ctypes.c_int32), ("device_error", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("tiling", ctypes.c_int32), ("levels", ctypes.c_int32), ("p", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("eps", ctypes.c_double), ("domain", ctypes.c_double * 3),
+                ("src_xy", ctypes.c_void_p), ("n_src", ctypes.c_int64), ("tgt_xy", ctypes.c_void_p),
+                ("n_tgt", ctypes.c_int64), ("strengths", ctypes.c_void_p),
+                ("potentials", ctypes.c_void_p)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("levels", ctypes.c_int32), ("p", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("slot", ctypes.c_int32), ("queue_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+
+class ServeInfo(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int64), ("running", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t),
+                ("slots", ctypes.c_int32)]
 
 
 class FMM2DError(RuntimeError):
@@ -85,8 +107,16 @@ def lib():
                                  vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                                  ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
     L.fmm2d_measure_alu_peaks.argtypes = [ctypes.POINTER(dbl)]
+    L.fmm2d_plan_set_params.argtypes = [vp, c_int, c_int, dbl]
+    L.fmm2d_serve_create.argtypes = [ctypes.c_size_t, c_int, ctypes.POINTER(vp)]
+    L.fmm2d_serve_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+    L.fmm2d_serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(Result)]
+    L.fmm2d_serve_wait.argtypes = [vp, ctypes.c_uint64, dbl, ctypes.POINTER(Result)]
+    L.fmm2d_serve_stats.argtypes = [vp, ctypes.POINTER(ServeInfo)]
+    L.fmm2d_serve_destroy.argtypes = [vp]
+    L.fmm2d_serve_destroy.restype = None
     for name in SYMBOLS:
-        if name not in ("fmm2d_plan_destroy", "fmm2d_last_error"):
+        if name not in ("fmm2d_plan_destroy", "fmm2d_last_error", "fmm2d_serve_destroy"):
             getattr(L, name).restype = c_int
     _LIB = L
     return L
@@ -238,6 +268,92 @@ class Plan:
     def close(self):
         if self._h:
             self.lib.fmm2d_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _host_ptr(a):
+    """Address of a C-contiguous numpy array (host memory)."""
+    if a is None:
+        return None
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("host arrays must be C-contiguous")
+    return a.ctypes.data
+
+
+class Server:
+    """fmm2d_serve_* wrapper.  Inputs and outputs are host numpy arrays that
+    the caller keeps alive until the request completes."""
+
+    def __init__(self, hbm_budget_bytes, max_slots=8):
+        self.lib = lib()
+        self._h = ctypes.c_void_p()
+        st = self.lib.fmm2d_serve_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(self._h))
+        if st:
+            raise FMM2DError(st, "fmm2d_serve_create")
+        self._keep = {}
+
+    def fmm2d_serve_submit(self, tiling, src_xy, strengths, potentials, tgt_xy=None, eps=1e-6,
+                           levels=0, p=0, flags=0, domain=None):
+        f32 = src_xy.dtype == np.float32
+        r = Request()
+        r.tiling = TILINGS.get(tiling, tiling)
+        r.levels, r.p = int(levels), int(p)
+        r.flags = int(flags) | (IN_F32 if f32 else 0)
+        r.eps = float(eps)
+        r.domain[:] = list(domain) if domain is not None else [0.0, 0.0, 0.0]
+        r.src_xy, r.n_src = _host_ptr(src_xy), len(src_xy)
+        r.tgt_xy = _host_ptr(tgt_xy)
+        r.n_tgt = 0 if tgt_xy is None else len(tgt_xy)
+        r.strengths, r.potentials = _host_ptr(strengths), _host_ptr(potentials)
+        t = ctypes.c_uint64()
+        st = self.lib.fmm2d_serve_submit(self._h, ctypes.byref(r), ctypes.byref(t))
+        if st:
+            raise FMM2DError(st, "fmm2d_serve_submit")
+        self._keep[t.value] = (src_xy, strengths, potentials, tgt_xy)
+        return t.value
+
+    submit = fmm2d_serve_submit
+
+    def _result(self, t, res):
+        self._keep.pop(t, None)
+        return {f: getattr(res, f) for f, _ in Result._fields_}
+
+    def fmm2d_serve_poll(self, ticket):
+        res = Result()
+        st = self.lib.fmm2d_serve_poll(self._h, int(ticket), ctypes.byref(res))
+        if st == ENOTREADY:
+            return None
+        if st:
+            raise FMM2DError(st, "fmm2d_serve_poll")
+        return self._result(ticket, res)
+
+    poll = fmm2d_serve_poll
+
+    def fmm2d_serve_wait(self, ticket, timeout_ms=60000.0):
+        res = Result()
+        st = self.lib.fmm2d_serve_wait(self._h, int(ticket), float(timeout_ms), ctypes.byref(res))
+        if st:
+            raise FMM2DError(st, "fmm2d_serve_wait")
+        return self._result(ticket, res)
+
+    wait = fmm2d_serve_wait
+
+    def fmm2d_serve_stats(self):
+        info = ServeInfo()
+        self.lib.fmm2d_serve_stats(self._h, ctypes.byref(info))
+        return {f: getattr(info, f) for f, _ in ServeInfo._fields_}
+
+    stats = fmm2d_serve_stats
+
+    def close(self):
+        if self._h:
+            self.lib.fmm2d_serve_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

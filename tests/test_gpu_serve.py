@@ -1,0 +1,100 @@
+"""The continuous-batching server (fmm2d_serve_*): a request gives the same
+result alone and mixed with concurrent requests, results match the oracle's
+direct sum within the requested eps, and admission respects the HBM budget."""
+import time
+
+import numpy as np
+import pytest
+
+from oracle.direct import direct
+from paper_1204_3105_gb300.inputs import gaussian_mixture, rng, sample_targets, uniform_square
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1204_3105_gb300 import build, fmm2d
+    build.build()
+    fmm2d.lib()
+    return fmm2d
+
+
+def _mix(count, seed):
+    g = rng(seed)
+    reqs = []
+    for i in range(count):
+        n = int(np.exp(g.uniform(np.log(1e3), np.log(1.5e5))))
+        tiling = ("quad", "sept", "tri")[int(g.integers(0, 3))]
+        eps = (1e-4, 1e-8)[int(g.integers(0, 2))]
+        if g.random() < 0.5:
+            xy, u = uniform_square(n, seed=seed * 1000 + i)
+        else:
+            xy, u = gaussian_mixture(n, seed=seed * 1000 + i, k=8)
+        reqs.append((tiling, xy, u, eps))
+    return reqs
+
+
+def test_alone_equals_in_the_mix(fm):
+    sv = fm.Server(8 << 30, max_slots=6)
+    xy, u = uniform_square(60000, seed=21, dtype=np.float32)
+    alone = np.zeros(len(xy))
+    t = sv.submit("sept", xy, u, alone, eps=1e-6)
+    r = sv.wait(t)
+    assert r["status"] == 0
+    others = _mix(24, seed=5)
+    outs, tickets = [], []
+    for k, (tiling, pxy, pu, eps) in enumerate(others):
+        o = np.zeros(len(pxy))
+        outs.append(o)
+        tickets.append(sv.submit(tiling, pxy, pu, o, eps=eps))
+        if k == 12:
+            mixed = np.zeros(len(xy))
+            tm = sv.submit("sept", xy, u, mixed, eps=1e-6)
+    results = [sv.wait(t) for t in tickets]
+    rm = sv.wait(tm)
+    assert rm["status"] == 0 and all(r["status"] == 0 for r in results)
+    assert len({r["slot"] for r in results}) > 1          # the work was spread over slots
+    assert np.array_equal(alone, mixed)                   # bit for bit
+    # two of the mixed requests against the oracle's direct sum
+    for k in (0, 7):
+        tiling, pxy, pu, eps = others[k]
+        idx = sample_targets(len(pxy), 200, seed=k)
+        ref = direct(pxy, pu, pxy[idx])
+        err = np.max(np.abs(outs[k][idx] - ref)) / np.max(np.abs(ref))
+        assert err < max(eps, 1e-7) * 3, (tiling, eps, err)
+    sv.close()
+
+
+def test_budget_admission_and_busy(fm):
+    xy, u = uniform_square(200000, seed=3, dtype=np.float32)
+    est_one = 200000 * (3 * 4 + 2 * 0 + 8) + 200000 * 96 + 200000 * 1024 // 16 + (32 << 20)
+    sv = fm.Server(int(2.5 * est_one), max_slots=8)     # at most two of these at once
+    outs, tickets = [], []
+    for i in range(6):
+        o = np.zeros(len(xy))
+        outs.append(o)
+        tickets.append(sv.submit("quad", xy, u, o, eps=1e-6))
+    peak_running, peak_bytes = 0, 0
+    t0 = time.time()
+    while time.time() - t0 < 60:
+        st = sv.stats()
+        peak_running = max(peak_running, st["running"])
+        peak_bytes = max(peak_bytes, st["bytes_in_use"])
+        assert st["bytes_in_use"] <= st["budget_bytes"]
+        if st["completed"] == 6:
+            break
+        time.sleep(0.001)
+    assert peak_running <= 2
+    res = [sv.wait(t) for t in tickets]
+    assert all(r["status"] == 0 for r in res)
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    big, bu = uniform_square(4_000_000, seed=4, dtype=np.float32)
+    with pytest.raises(fm.FMM2DError) as e:
+        sv.submit("quad", big, bu, np.zeros(len(big)), eps=1e-6)
+    assert e.value.status == fm.EBUSY
+    sv.close()
