@@ -50,15 +50,20 @@ class Clocks:
         self.index = index
         self.rows = []
         self.proc = None
+        self.skip = 0
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()   # nvidia-smi takes a moment to start: wait for its first row
+            while not self.rows and time.time() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.skip = len(self.rows)
         except OSError:
             self.proc = None
         return self
@@ -76,6 +81,7 @@ class Clocks:
                 self.proc.kill()
 
     def summary(self):
+        self.rows = self.rows[self.skip:]   # rows taken before the timed region started
         if not self.rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
@@ -121,9 +127,12 @@ def run_reference(args):
     dist, rank, ws = dist_setup(args)
     if rank != 0:
         return
-    n = args.ref_points
+    # bounded sample: the whole run takes about --ref-seconds on the host
+    _, dt_cal = oracle_sample(n=2048)
+    per_step = args.ref_seconds / max(1, args.steps + args.warmup)
+    n = int(min(args.ref_points, max(512, 2048 * per_step / max(dt_cal, 1e-3))))
     for _ in range(args.warmup):
-        oracle_sample(n=max(1024, n // 8))
+        oracle_sample(n=n)
     times = []
     for _ in range(args.steps):
         _, dt = oracle_sample(n=n)
@@ -134,9 +143,10 @@ def run_reference(args):
             "value": value, "unit": "points/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "N=M=%d uniform unit square, quad+sept+tri, eps=1e-6 (oracle sample)" % n},
+            "config": {"workload": "N=M=%d uniform unit square, quad+sept+tri, eps=1e-6 (oracle sample "
+                                   "of the N=M=2^20 workload)" % n},
             "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle",
-                             "sample": "N=M=%d per tiling, 3 tilings, one evaluation per step" % n},
+                             "sample": "N=M=%d per tiling, 3 tilings, one FP64 evaluation per step" % n},
             "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -191,8 +201,6 @@ def run_ours(args):
     for _ in range(args.warmup):
         step(warm)
     torch.cuda.synchronize()
-    for t in args.tilings:
-        plans[t].set_profiling(not args.no_profile)
     per = {t: [] for t in args.tilings}
     if dist:
         dist.barrier()
@@ -204,7 +212,14 @@ def run_ours(args):
     if dist:
         dist.barrier()
     tt = {t: [a.elapsed_time(b) for a, b in per[t]] for t in args.tilings}
+    # one more step with per-stage events (kept out of the timed steps)
+    for t in args.tilings:
+        plans[t].set_profiling(not args.no_profile)
+    step({t: [] for t in args.tilings})
+    torch.cuda.synchronize()
     stage = {t: plans[t].stage_times() for t in args.tilings}
+    for t in args.tilings:
+        plans[t].set_profiling(False)
     info = {t: plans[t].query() for t in args.tilings}
     ms_step = sum(statistics.mean(tt[t]) for t in args.tilings)
     if dist:
@@ -212,6 +227,35 @@ def run_ours(args):
         dist.all_reduce(tm, op=dist.ReduceOp.MAX)
         ms_step = float(tm.item())
     value = ws * len(args.tilings) * N_POINTS / (ms_step / 1e3)
+
+    # the plain FP64 GPU form on the same points, (L, p) tuned for the same eps
+    fp64_form = None
+    if not args.no_fp64_form and args.prec != "fp64":
+        f64 = {}
+        for t in args.tilings:
+            L64, p64, e64, _ = fmm2d.fmm2d_autotune(t, EPS, fmm2d.PREC_FP64 | fmm2d.IN_F32, xy_d, N_POINTS,
+                                                    xy_d, N_POINTS, stream=stream)
+            pl64 = fmm2d.Plan(t, L64, p64, EPS, fmm2d.PREC_FP64 | fmm2d.IN_F32)
+            ts64 = []
+            for it in range(1 + args.fp64_steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pl64.build(xy_d, N_POINTS, xy_d, N_POINTS, stream)
+                pl64.evaluate(u_d, outs[t], stream)
+                e1.record(stream)
+                e1.synchronize()
+                if it > 0:
+                    ts64.append(e0.elapsed_time(e1))
+                flush.zero_()
+            pl64.close()
+            ms64 = statistics.mean(ts64)
+            f64[t] = {"points_per_s": N_POINTS / (ms64 / 1e3), "ms": ms64, "L": L64, "p": p64,
+                      "tune_probe_err": e64}
+        ms64_step = sum(v["ms"] for v in f64.values())
+        fp64_form = {"value": ws * len(args.tilings) * N_POINTS / (ms64_step / 1e3), "unit": "points/s",
+                     "ms_per_step": ms64_step, "steps": args.fp64_steps, "per_tiling": f64,
+                     "speedup_of_mixed": ms64_step / ms_step}
 
     # e2e: host buffers, copies inside the timed region, through the same ABI
     xy_h = torch.from_numpy(xy).pin_memory()
@@ -241,8 +285,8 @@ def run_ours(args):
     for t in args.tilings:
         for k, (ms, n) in stage[t].items():
             tot.setdefault(k, [0.0, 0])
-            tot[k][0] += ms / args.steps
-            tot[k][1] += n / args.steps
+            tot[k][0] += ms
+            tot[k][1] += n
     dom = max(tot, key=lambda k: tot[k][0])
     if tot[dom][0] <= 0.0:
         roof = None
@@ -285,12 +329,14 @@ def run_ours(args):
                                "ms": statistics.mean(tt[t]), "L": info[t]["levels"], "p": info[t]["p"],
                                "m2l": info[t]["n_m2l"], "p2p_pairs": info[t]["n_p2p_pairs"],
                                "tune_probe_err": tuned[t][2],
-                               "stages_ms": {k: v[0] / args.steps for k, v in stage[t].items()}}
+                               "stages_ms": {k: v[0] for k, v in stage[t].items()}}
                            for t in args.tilings},
+            "fp64_form": fp64_form,
             "roofline": roof,
             "peaks_source": src,
             "alu_peaks": alu,
             "stage_ms_total": {k: v[0] for k, v in tot.items()},
+            "stage_note": "per-stage CUDA events from one extra step after the timed steps",
             "cpu_baseline": None if cpu_v is None else {
                 "value": cpu_v, "unit": "points/s", "cores": 1, "kind": "oracle",
                 "sample": "N=M=%d per tiling, 3 tilings, one FP64 evaluation (%.1f s)" % (args.ref_points, cpu_dt)},
@@ -359,6 +405,14 @@ def run_server_workload(args):
     sv.close()
     lat = np.array([r["latency_ms"] for r in res])
     ok = sum(r["status"] == 0 for r in res)
+    by_eps = {}
+    for e in sorted(set(eps.tolist())):
+        m = eps == e
+        run = np.array([r["run_ms"] for r, k in zip(res, m) if k])
+        by_eps["%g" % e] = {"requests": int(m.sum()), "points": int(sizes[m].sum()),
+                            "run_ms_mean": float(run.mean()), "run_ms_sum": float(run.sum()),
+                            "latency_p50_ms": float(np.percentile(lat[m], 50)),
+                            "latency_p99_ms": float(np.percentile(lat[m], 99))}
     points = int(sizes.sum())
     line = {
         "metric": ("batched FMM points/s (4096-instance config)" if args.workload == "batch"
@@ -369,6 +423,7 @@ def run_server_workload(args):
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "max": float(lat.max())},
         "run_ms_mean": float(np.mean([r["run_ms"] for r in res])),
+        "by_eps": by_eps,
         "config": {"slots": args.slots, "hbm_budget_gb": args.budget_gb,
                    "sizes": "log-uniform [256, 65536]" if args.workload == "batch"
                    else "log-uniform [1e3, 2e6]",
@@ -383,15 +438,18 @@ def run_server_workload(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="tc", choices=["tc", "mixed", "fp64"])
     ap.add_argument("--tilings", default=",".join(TILINGS))
     ap.add_argument("--ref-points", type=int, default=16384)
+    ap.add_argument("--ref-seconds", type=float, default=150.0, help="reference arm: host time budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="a-priori L and p instead of fmm2d_autotune")
-    ap.add_argument("--no-profile", action="store_true", help="no per-stage events in the timed region")
+    ap.add_argument("--no-profile", action="store_true", help="no per-stage event pass")
+    ap.add_argument("--no-fp64-form", action="store_true", help="skip the plain FP64 GPU form")
+    ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 form")
     ap.add_argument("--params", default="", help="fixed L and p per tiling, e.g. quad:7:12,sept:5:13")
     ap.add_argument("--workload", default="fmm", choices=["fmm", "batch", "serve"])
     ap.add_argument("--instances", type=int, default=4096, help="batch: number of instances")

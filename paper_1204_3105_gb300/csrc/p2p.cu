@@ -261,6 +261,206 @@ k_p2p_block(int64_t leaf_first, const R *__restrict__ src4, const R *__restrict_
   }
 }
 
+// ---- FP32 form on packed f32x2 arithmetic ------------------------------
+// Four targets per thread held as two float2 pairs, so that one FADD2/FFMA2
+// serves two source-target pairs; sources are staged in the target leaf's
+// frame as (-x, -x, -y, -y) and (u, u) so that a staged record feeds the
+// packed operations directly.  Per source a thread issues 8 packed FP32
+// operations, 4 MUFU lg2 and 2 shared loads for 4 pairs, which leaves the
+// kernel bound by the MUFU unit (one lg2 per pair) instead of by issue.
+// A group of T threads (a warp, or 2 to 8 warps synchronised by a named
+// barrier) owns one target leaf; the block holds 256 / T groups.  Within a
+// group, thread (i, k) takes target quadruple i and every K-th staged source
+// starting at k; slice partials are combined in FP32 with compensation and
+// converted to FP64 once per target.
+constexpr int X2_CAP = 1536;   // staged sources per block
+
+template <int T>
+__device__ __forceinline__ void x2_sync(int grp) {
+  if constexpr (T == 32) __syncwarp();
+  else if constexpr (T == P2P_TH) __syncthreads();
+  else asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(T) : "memory");
+}
+
+__device__ __forceinline__ float x2_lg(float r2) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2));
+  return y;
+}
+
+// One staged source against the thread's four targets.  CHECK (the target's
+// own leaf): r^2 at the floor means the points coincide at FP32 resolution,
+// and the pair contributes nothing.
+template <bool CHECK>
+__device__ __forceinline__ void x2_source(const float4 &p, const float2 &u, const float2 &xab,
+                                          const float2 &xcd, const float2 &yab, const float2 &ycd,
+                                          float2 &acc_ab, float2 &acc_cd) {
+  constexpr float FL = 1e-30f;
+  const float2 px = make_float2(p.x, p.y), py = make_float2(p.z, p.w);
+  const float2 fl = make_float2(FL, FL);
+  const float2 dxab = __fadd2_rn(xab, px), dxcd = __fadd2_rn(xcd, px);
+  const float2 dyab = __fadd2_rn(yab, py), dycd = __fadd2_rn(ycd, py);
+  const float2 rab = __ffma2_rn(dxab, dxab, __ffma2_rn(dyab, dyab, fl));
+  const float2 rcd = __ffma2_rn(dxcd, dxcd, __ffma2_rn(dycd, dycd, fl));
+  float2 lab, lcd;
+  lab.x = x2_lg(rab.x);
+  lab.y = x2_lg(rab.y);
+  lcd.x = x2_lg(rcd.x);
+  lcd.y = x2_lg(rcd.y);
+  if (CHECK) {
+    lab.x = rab.x == FL ? 0.f : lab.x;
+    lab.y = rab.y == FL ? 0.f : lab.y;
+    lcd.x = rcd.x == FL ? 0.f : lcd.x;
+    lcd.y = rcd.y == FL ? 0.f : lcd.y;
+  }
+  acc_ab = __ffma2_rn(u, lab, acc_ab);
+  acc_cd = __ffma2_rn(u, lcd, acc_cd);
+}
+
+__device__ __forceinline__ void x2_kahan(float &s, float &c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// Staged sources q0, q0 + K, ... < q1; partial sums of at most 64 sources
+// are folded into the compensated running sums.
+template <bool CHECK>
+__device__ __forceinline__ void x2_slice(const float4 *sxy, const float2 *su, int q0, int q1, int K,
+                                         const float2 &xab, const float2 &xcd, const float2 &yab,
+                                         const float2 &ycd, float (&s)[4], float (&c)[4]) {
+  int q = q0;
+  while (q < q1) {
+    float2 acc_ab = make_float2(0.f, 0.f), acc_cd = make_float2(0.f, 0.f);
+    const int qe = min(q1, q + 64 * K);
+#pragma unroll 4
+    for (; q < qe; q += K) x2_source<CHECK>(sxy[q], su[q], xab, xcd, yab, ycd, acc_ab, acc_cd);
+    x2_kahan(s[0], c[0], acc_ab.x);
+    x2_kahan(s[1], c[1], acc_ab.y);
+    x2_kahan(s[2], c[2], acc_cd.x);
+    x2_kahan(s[3], c[3], acc_cd.y);
+  }
+}
+
+template <int T>
+__global__ void __launch_bounds__(P2P_TH, 4)
+k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const float *__restrict__ src4,
+         const float *__restrict__ tgt, int tstride, const int *__restrict__ sst,
+         const int *__restrict__ sen, const int *__restrict__ tst, const int *__restrict__ ten,
+         const int *__restrict__ near_cnt, const int *__restrict__ near_src,
+         const double2 *__restrict__ ctr, double *__restrict__ phi_near) {
+  constexpr int G = P2P_TH / T, CAP = X2_CAP / G;
+  __shared__ float4 s_xy[X2_CAP];
+  __shared__ float2 s_u[X2_CAP];
+  __shared__ float s_red[2][4][P2P_TH];
+  __shared__ int m_s0[G][NEAR_MAX], m_base[G][NEAR_MAX + 1];
+  __shared__ float m_dx[G][NEAR_MAX], m_dy[G][NEAR_MAX];
+  const int grp = threadIdx.x / T, tg = threadIdx.x % T;
+  const int64_t li = (int64_t)blockIdx.x * G + grp;
+  if (li >= n_leaves) return;                 // group-uniform exits only
+  const int64_t g = leaf_first + li;
+  const int ts = tst[g], te = ten[g];
+  if (ts >= te) return;
+  const int nn = near_cnt[li];
+  const int *nsrc = near_src + li * NEAR_MAX;
+  float4 *sxy = s_xy + grp * CAP;
+  float2 *su = s_u + grp * CAP;
+  if (tg < nn) {
+    const int s = nsrc[tg];
+    const double2 cg = ctr[g], cs = ctr[s];
+    m_s0[grp][tg] = sst[s];
+    m_base[grp][tg + 1] = sen[s] - sst[s];   // counts, prefix-summed below
+    m_dx[grp][tg] = (float)(cs.x - cg.x);
+    m_dy[grp][tg] = (float)(cs.y - cg.y);
+  }
+  x2_sync<T>(grp);
+  if (tg == 0) {
+    int b = 0;
+    m_base[grp][0] = 0;
+    for (int e = 0; e < nn; ++e) {
+      b += m_base[grp][e + 1];
+      m_base[grp][e + 1] = b;
+    }
+  }
+  x2_sync<T>(grp);
+  const int total = m_base[grp][nn];
+  // the Near stencils list the leaf itself first
+  const int n_self = (nn > 0 && nsrc[0] == (int)g) ? m_base[grp][1] : 0;
+  const float4 *src = reinterpret_cast<const float4 *>(src4);
+  auto stage = [&](int c0, int c1) {
+    for (int e = 0; e < nn; ++e) {
+      const int b = m_base[grp][e], lo = max(b, c0), hi = min(m_base[grp][e + 1], c1);
+      const int s0 = m_s0[grp][e] - b;
+      const float dcx = m_dx[grp][e], dcy = m_dy[grp][e];
+      for (int q = lo + tg; q < hi; q += T) {
+        const float4 v = src[s0 + q];
+        const float x = -(v.x + dcx), y = -(v.y + dcy);
+        sxy[q - c0] = make_float4(x, x, y, y);
+        su[q - c0] = make_float2(v.z, v.z);
+      }
+    }
+  };
+  const bool once = total <= CAP;   // all Near sources fit: stage them once
+  if (once) {
+    stage(0, total);
+    x2_sync<T>(grp);
+  }
+  for (int t0 = ts; t0 < te; t0 += 4 * T) {
+    const int ntc = min(4 * T, te - t0);
+    const int ng = (ntc + 3) / 4;          // target quadruples
+    const int K = T / ng;                  // source slices per quadruple
+    const int i = tg % ng, k = tg / ng;
+    const bool act = k < K;
+    float2 xab, xcd, yab, ycd;
+    {
+      int j[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) j[r] = t0 + (i + r * ng < ntc ? i + r * ng : i);
+      xab = make_float2(tgt[(int64_t)j[0] * tstride], tgt[(int64_t)j[1] * tstride]);
+      yab = make_float2(tgt[(int64_t)j[0] * tstride + 1], tgt[(int64_t)j[1] * tstride + 1]);
+      xcd = make_float2(tgt[(int64_t)j[2] * tstride], tgt[(int64_t)j[3] * tstride]);
+      ycd = make_float2(tgt[(int64_t)j[2] * tstride + 1], tgt[(int64_t)j[3] * tstride + 1]);
+    }
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int c0 = 0; c0 < total; c0 += CAP) {
+      const int c1 = min(total, c0 + CAP);
+      if (!once) {
+        x2_sync<T>(grp);
+        stage(c0, c1);
+        x2_sync<T>(grp);
+      }
+      if (act) {
+        const int m = c1 - c0;
+        const int self_end = max(0, min(m, n_self - c0));
+        const int first_unchecked = self_end + ((k - self_end) % K + K) % K;
+        if (self_end > 0) x2_slice<true>(sxy, su, k, self_end, K, xab, xcd, yab, ycd, s, c);
+        x2_slice<false>(sxy, su, first_unchecked, m, K, xab, xcd, yab, ycd, s, c);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      s_red[0][r][threadIdx.x] = act ? s[r] : 0.f;
+      s_red[1][r][threadIdx.x] = act ? c[r] : 0.f;
+    }
+    x2_sync<T>(grp);
+    if (tg < ng) {
+      const int base = grp * T;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        if (i + r * ng >= ntc) continue;
+        float S = 0.f, C = 0.f, cs = 0.f;
+        for (int kk = 0; kk < K; ++kk) {
+          x2_kahan(S, C, s_red[0][r][base + kk * ng + i]);
+          cs += s_red[1][r][base + kk * ng + i];
+        }
+        phi_near[t0 + i + r * ng] = ((double)S - (double)(C + cs)) * 0.34657359027997264;  // ln2/2
+      }
+    }
+    x2_sync<T>(grp);
+  }
+}
+
 }  // namespace
 
 template <typename R>
@@ -270,11 +470,27 @@ cudaError_t launch_p2p(int64_t leaf_first, int64_t n_leaves, const R *src4, cons
                        const int *near_src, const double2 *ctr, double *phi_near,
                        double mean_targets, cudaStream_t s) {
   if (n_leaves <= 0) return cudaSuccess;
-  if (mean_targets >= 48.0) {   // large leaves: block-staged, sliced sources
+  if constexpr (sizeof(R) == 4) {
+    // group size: the smallest T for which a leaf of mean + 2 sigma (Poisson)
+    // targets still gets two source slices per target quadruple
+    const double want = 0.5 * (mean_targets + 2.0 * sqrt(mean_targets));
+    const int T = want <= 32 ? 32 : want <= 64 ? 64 : want <= 128 ? 128 : 256;
+    const int G = P2P_TH / T;
+    const unsigned blocks = (unsigned)((n_leaves + G - 1) / G);
+#define X2_LAUNCH(TT)                                                                             \
+  k_p2p_x2<TT><<<blocks, P2P_TH, 0, s>>>(leaf_first, n_leaves, src4, tgt, tstride, src_start,      \
+                                         src_end, tgt_start, tgt_end, near_cnt, near_src, ctr,    \
+                                         phi_near)
+    if (T == 32) X2_LAUNCH(32);
+    else if (T == 64) X2_LAUNCH(64);
+    else if (T == 128) X2_LAUNCH(128);
+    else X2_LAUNCH(256);
+#undef X2_LAUNCH
+  } else if (mean_targets >= 48.0) {   // FP64, large leaves: block-staged, sliced sources
     k_p2p_block<R><<<(unsigned)n_leaves, P2P_TH, 0, s>>>(leaf_first, src4, tgt, tstride, src_start,
                                                          src_end, tgt_start, tgt_end, near_cnt,
                                                          near_src, ctr, phi_near);
-  } else {                      // small leaves: one warp per leaf
+  } else {                             // FP64, small leaves: one warp per leaf
     const unsigned blocks = (unsigned)((n_leaves * 32 + P2P_TH - 1) / P2P_TH);
     k_p2p<R><<<blocks, P2P_TH, 0, s>>>(leaf_first, n_leaves, src4, tgt, tstride, src_start, src_end,
                                         tgt_start, tgt_end, near_cnt, near_src, ctr, phi_near);
