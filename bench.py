@@ -387,6 +387,8 @@ def run_server_workload(args):
         cluster = g.random(count) < 0.5
         n_max = int(sizes.max())
     (uxy, uu), (gxy, gu) = _pool(n_max, SEED + 41)
+    tree = args.tree if args.tree != "auto" else ("adaptive" if args.workload == "serve" else "uniform")
+    tree_flag = fmm2d.ADAPTIVE if tree == "adaptive" else 0
     names = ("quad", "sept", "tri")
     sv = fmm2d.Server(int(args.budget_gb * (1 << 30)), max_slots=args.slots)
     outs, tickets, t_sub = [], [], []
@@ -399,7 +401,7 @@ def run_server_workload(args):
         n = int(sizes[i])
         o = np.empty(n)
         outs.append(o)
-        tickets.append(sv.submit(names[tilings[i]], xy[:n], u[:n], o, eps=float(eps[i])))
+        tickets.append(sv.submit(names[tilings[i]], xy[:n], u[:n], o, eps=float(eps[i]), flags=tree_flag))
     res = [sv.wait(t, 600000.0) for t in tickets]
     t1 = time.perf_counter()
     sv.close()
@@ -430,6 +432,7 @@ def run_server_workload(args):
                    "eps": "1e-6" if args.workload == "batch" else "1e-4 / 1e-8 (FP64 form)",
                    "arrival_rate_per_s": None if args.workload == "batch" else args.rate,
                    "points": "uniform" if args.workload == "batch" else "uniform / 8-cluster mixture",
+                   "tree": tree + (" (leaf size 64)" if tree == "adaptive" else ""),
                    "io": "host numpy buffers, copies inside each request"},
     }
     print(json.dumps(line))
@@ -457,6 +460,8 @@ def main():
     ap.add_argument("--duration", type=float, default=1.0, help="serve: seconds of arrivals")
     ap.add_argument("--slots", type=int, default=16, help="batch/serve: server slots")
     ap.add_argument("--budget-gb", type=float, default=80.0, help="batch/serve: HBM budget")
+    ap.add_argument("--tree", default="auto", choices=["auto", "uniform", "adaptive"],
+                    help="batch/serve: tree of each request (auto: adaptive for serve)")
     args = ap.parse_args()
     args.tilings = tuple(args.tilings.split(","))
     if args.workload != "fmm" and args.impl != "reference":

@@ -67,6 +67,14 @@ typedef enum {
                                      (split hi/lo TF32 products, FP32 accumulation) */
 #define FMM2D_PREC_MASK     0x3u
 #define FMM2D_IN_F32        0x10u /* points and strengths are float32 (default float64) */
+#define FMM2D_ADAPTIVE      0x20u /* adaptive tree for clustered input: a cell is split
+                                     while it holds more than the leaf size (default 64,
+                                     fmm2d_plan_set_leaf_size) sources or targets, down
+                                     to `levels` (0 = 16 for the quadtree and triangle
+                                     quadtree, 9 for the septree); cells of different
+                                     levels interact by M2P and P2L (W and X lists).
+                                     The paper refines uniformly (Sec. 2); this is the
+                                     adaptive extension for non-uniform data (Sec. 9). */
 
 typedef struct fmm2d_plan fmm2d_plan;
 
@@ -133,6 +141,16 @@ fmm2d_status fmm2d_plan_create(int tiling, int levels, int p, double eps, unsign
 fmm2d_status fmm2d_plan_set_params(fmm2d_plan *plan, int levels, int p, double eps);
 
 /*
+ * fmm2d_plan_set_leaf_size - leaf size of an FMM2D_ADAPTIVE plan: a cell is
+ * split while it holds more than leaf_size sources or more than leaf_size
+ * targets and is above the finest level (leaf_size >= 0; 0 splits every
+ * occupied cell down to the finest level, which reproduces the uniform
+ * tree).  Ignored by uniform plans.  Invalidates a previous build.
+ * Errors: FMM2D_EINVAL (null plan, negative size).
+ */
+fmm2d_status fmm2d_plan_set_leaf_size(fmm2d_plan *plan, int leaf_size);
+
+/*
  * fmm2d_plan_set_domain - set the domain square [x0, x0+S) x [y0, y0+S)
  * (S > 0).  Every source and target must lie in it (else fmm2d_build returns
  * FMM2D_EDOMAIN).  Invalidates a previous build.
@@ -188,6 +206,11 @@ fmm2d_status fmm2d_plan_query(const fmm2d_plan *plan, fmm2d_info *info);
  *    10 near-field part of Phi (float64, input target order)
  *    11 far-field part of Phi (float64, input target order)
  *    12 cell centres of `level` (complex128, order of 5, original coordinates)
+ *   FMM2D_ADAPTIVE plans (int64 tuples; `level` ignored):
+ *    13 cells: (level, key, split) of every cell, ordered by (level, key)
+ *    14 U (P2P) pairs, 15 W (M2P) pairs, 16 X (P2L) pairs, 17 M2L pairs:
+ *       (target level, target key, source level, source key), grouped by
+ *       target in cell order
  *   host_buf / cap: destination and its size in bytes; with host_buf NULL only
  *   *written (required bytes) is set.
  * Errors: FMM2D_EINVAL (unknown what / level, cap too small),
@@ -299,9 +322,11 @@ typedef struct {
   int32_t tiling;          /* fmm2d_tiling */
   int32_t levels;          /* leaf level, 0 = planner */
   int32_t p;               /* expansion order, 0 = from eps */
-  uint32_t flags;          /* FMM2D_IN_F32 and optionally FMM2D_PREC_*; with no
-                              precision bit the server uses the tensor-core
-                              mixed form for eps >= 1e-6 and FP64 below */
+  uint32_t flags;          /* FMM2D_IN_F32, optionally FMM2D_PREC_* and
+                              FMM2D_ADAPTIVE (leaf size 64; levels = finest
+                              level, 0 = the default); with no precision bit
+                              the server uses the tensor-core mixed form for
+                              eps >= 1e-6 and FP64 below */
   double eps;
   double domain[3];        /* x0, y0, S; S <= 0 means the unit square */
   const void *src_xy;      /* n_src interleaved points */

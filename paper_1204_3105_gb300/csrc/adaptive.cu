@@ -1,0 +1,661 @@
+// adaptive.cu - the adaptive tree for clustered input: cells split while they
+// hold more than `cap` sources or targets, interaction lists by a
+// level-synchronous dual traversal, and the two cross-level operators.
+//
+// Tree.  Points are keyed and sorted on the finest level Lmax, so the points
+// of a level-l cell (a key prefix, Parent(n) = n div b, Sec. 4-6) are one
+// contiguous range.  Level by level, each cell that must split finds its
+// children's ranges by binary search on the sorted keys; occupied children
+// are compacted (flag, scan, emit) into the next level.  Cells of all levels
+// live in one array ordered by (level, key); children of a cell are
+// contiguous.
+//
+// Lists.  Per level, three kinds of items are expanded (count pass, one scan,
+// emit pass, so the output order is deterministic):
+//  * a cell a: its Near stencil cells m (Sec. 4-6) that exist - both leaves:
+//    P2P pair (U); a leaf and m split: m's children go to the W test; a split
+//    and m a leaf: a's children go to the X test; its NeighborsE4 cells (eq. 3)
+//    that exist: M2L list, in the uniform tree's format;
+//  * a W test (leaf a, finer cell c): c separated from a (no cell of Near(c)
+//    lies inside a) -> M2P (W); else c a leaf -> U; else c's children;
+//  * an X test (cell a, coarser leaf c): mirrored -> P2L (X), U, or a's
+//    children.
+// The U, W and X pairs are then grouped by target (stable sort).
+//
+// Operators (Greengard-Rokhlin series, scaled like the uniform expansions):
+//  * M2P: phi(y) += Q log|y - c| + Re sum_k a^_k (s_c / (y - c))^k
+//  * P2L: L_0 += sum u log|x - c|, b^_l += -(1/l) sum u (s_c / (x - c))^l
+#include "cells.cuh"
+#include "plan.h"
+
+namespace fmm2d {
+
+namespace {
+
+inline unsigned nblk(int64_t n, int th) { return (unsigned)((n + th - 1) / th); }
+
+__device__ __forceinline__ uint64_t level_span(int b, int up) {   // b^up
+  uint64_t v = 1;
+  for (int i = 0; i < up; ++i) v *= (uint64_t)b;
+  return v;
+}
+
+// first index in [lo, hi) with key >= x
+__device__ __forceinline__ int lower_bound_u32(const uint32_t *__restrict__ k, int lo, int hi, uint64_t x) {
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if ((uint64_t)k[mid] < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// cell of level-l key `key` in the sorted key range [first, first + count), or -1
+__device__ __forceinline__ int find_cell(const uint32_t *__restrict__ ckey, int64_t first, int64_t count,
+                                         uint32_t key) {
+  int64_t lo = first, hi = first + count;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (ckey[mid] < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return (lo < first + count && ckey[lo] == key) ? (int)lo : -1;
+}
+
+__global__ void k_ad_root(Geo g, int n_s, int n_t, AdCells c) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int4 crd;
+  double2 ctr;
+  uint8_t cls;
+  cell_geometry(g, 0, 0u, &crd, &ctr, &cls);
+  c.key[0] = 0u;
+  c.lev[0] = 0;
+  c.parent[0] = -1;
+  c.child_first[0] = 0;
+  c.child_cnt[0] = 0;
+  c.split[0] = 0;
+  c.ss[0] = 0;
+  c.se[0] = n_s;
+  c.ts[0] = 0;
+  c.te[0] = n_t;
+  c.crd[0] = crd;
+  c.ctr[0] = ctr;
+  c.cls[0] = cls;
+  c.hsrc[0] = n_s > 0;
+}
+
+// Split decision and children's point ranges of the cells of level l.
+__global__ void k_ad_split(Geo g, int l, int64_t first, int64_t count, int cap,
+                           const uint32_t *__restrict__ skey, const uint32_t *__restrict__ tkey,
+                           AdCells c, int *__restrict__ flag, int4 *__restrict__ crange) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int64_t cell = first + i;
+  const int ss = c.ss[cell], se = c.se[cell], ts = c.ts[cell], te = c.te[cell];
+  const bool split = l < g.L && max(se - ss, te - ts) > cap;
+  c.split[cell] = split ? 1 : 0;
+  const int b = g.b;
+  if (!split) {
+    for (int d = 0; d < b; ++d) flag[i * b + d] = 0;
+    return;
+  }
+  const uint64_t span = level_span(b, g.L - l - 1);
+  const uint64_t key = c.key[cell];
+  int s0 = ss, t0 = ts;
+  for (int d = 0; d < b; ++d) {
+    const uint64_t hi = (key * b + d + 1) * span;
+    const int s1 = lower_bound_u32(skey, s0, se, hi);
+    const int t1 = tkey ? lower_bound_u32(tkey, t0, te, hi) : s1;
+    crange[i * b + d] = make_int4(s0, s1, tkey ? t0 : s0, t1);
+    flag[i * b + d] = (s1 > s0 || t1 > (tkey ? t0 : s0)) ? 1 : 0;
+    s0 = s1;
+    t0 = t1;
+  }
+}
+
+// Occupied children of the split cells of level l -> cells of level l + 1.
+__global__ void k_ad_emit(Geo g, int l, int64_t first, int64_t count, int64_t next_first,
+                          const int *__restrict__ flag, const int *__restrict__ pos,
+                          const int4 *__restrict__ crange, AdCells c) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int64_t cell = first + i;
+  const int b = g.b;
+  int n = 0;
+  for (int d = 0; d < b; ++d) {
+    if (!flag[i * b + d]) continue;
+    const int64_t ch = next_first + pos[i * b + d];
+    if (n == 0) c.child_first[cell] = (int)ch;
+    ++n;
+    const uint32_t key = c.key[cell] * (uint32_t)b + (uint32_t)d;
+    int4 crd;
+    double2 ctr;
+    uint8_t cls;
+    cell_geometry(g, l + 1, key, &crd, &ctr, &cls);
+    const int4 r = crange[i * b + d];
+    c.key[ch] = key;
+    c.lev[ch] = (uint8_t)(l + 1);
+    c.parent[ch] = (int)cell;
+    c.child_first[ch] = 0;
+    c.child_cnt[ch] = 0;
+    c.split[ch] = 0;
+    c.ss[ch] = r.x;
+    c.se[ch] = r.y;
+    c.ts[ch] = r.z;
+    c.te[ch] = r.w;
+    c.crd[ch] = crd;
+    c.ctr[ch] = ctr;
+    c.cls[ch] = cls;
+    c.hsrc[ch] = r.y > r.x;
+  }
+  c.child_cnt[cell] = (uint8_t)n;
+  if (n == 0) c.child_first[cell] = 0;
+}
+
+__global__ void k_ad_level_total(int64_t count_b, const int *__restrict__ flag,
+                                 const int *__restrict__ pos, int *__restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0)
+    out[0] = count_b > 0 ? pos[count_b - 1] + flag[count_b - 1] : 0;
+}
+
+__global__ void k_ad_leaf_flags(int64_t n, const uint8_t *__restrict__ split, int *__restrict__ flag) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) flag[i] = split[i] ? 0 : 1;
+}
+
+__global__ void k_ad_leaf_ids(int64_t n, const int *__restrict__ flag, const int *__restrict__ pos,
+                              int *__restrict__ leaf_ids, int *__restrict__ leaf_pos) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (flag[i]) {
+    leaf_ids[pos[i]] = (int)i;
+    leaf_pos[i] = pos[i];
+  } else {
+    leaf_pos[i] = -1;
+  }
+}
+
+// Points of every leaf relative to the leaf centre (one warp per leaf).
+template <typename TI, typename TO>
+__global__ void k_ad_rel(const TI *__restrict__ xy, const uint32_t *__restrict__ perm,
+                         int64_t n_leaves, const int *__restrict__ leaf_ids,
+                         const int *__restrict__ start, const int *__restrict__ end,
+                         const double2 *__restrict__ ctr, TO *__restrict__ out, int stride) {
+  const int lane = threadIdx.x & 31;
+  const int64_t li = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (li >= n_leaves) return;
+  const int cell = leaf_ids[li];
+  const double2 c = ctr[cell];
+  for (int i = start[cell] + lane; i < end[cell]; i += 32) {
+    const uint32_t o = perm[i];
+    const double x = (double)xy[2 * (int64_t)o], y = (double)xy[2 * (int64_t)o + 1];
+    TO *dst = out + (int64_t)i * stride;
+    dst[0] = (TO)(x - c.x);
+    dst[1] = (TO)(y - c.y);
+    for (int q = 2; q < stride; ++q) dst[q] = (TO)0;
+  }
+}
+
+// ---- list traversal ---------------------------------------------------------
+enum { K_U = 0, K_W, K_X, K_T, K_S, K_KINDS };
+
+struct ListOut {
+  int *cnt;                           // count pass: [K_KINDS][n_items]
+  const int *off;                     // emit pass: exclusive scan of cnt
+  int64_t n_items;
+  int64_t base[K_KINDS];              // emit pass: global offset of this level's block
+  int *u_t, *u_s, *w_t, *w_s, *x_t, *x_s;
+  int *t_a, *t_c, *s_a, *s_c;         // next level's W and X tests
+};
+
+template <bool EMIT>
+struct Emitter {
+  const ListOut &o;
+  int64_t item;
+  int n[K_KINDS];
+  __device__ Emitter(const ListOut &out, int64_t it) : o(out), item(it) {
+    for (int k = 0; k < K_KINDS; ++k) n[k] = 0;
+  }
+  __device__ void put(int kind, int a, int c) {
+    if (EMIT) {
+      const int64_t at = o.base[kind] + (o.off[kind * o.n_items + item] - o.off[kind * o.n_items]) + n[kind];
+      int *A, *C;
+      switch (kind) {
+        case K_U: A = o.u_t; C = o.u_s; break;
+        case K_W: A = o.w_t; C = o.w_s; break;
+        case K_X: A = o.x_t; C = o.x_s; break;
+        case K_T: A = o.t_a; C = o.t_c; break;
+        default: A = o.s_a; C = o.s_c; break;
+      }
+      A[at] = a;
+      C[at] = c;
+    }
+    ++n[kind];
+  }
+  __device__ void done() {
+    if (!EMIT)
+      for (int k = 0; k < K_KINDS; ++k) o.cnt[k * o.n_items + item] = n[k];
+  }
+};
+
+// true when no cell of Near(fine, lf) lies inside the coarser cell `coarse`
+__device__ bool separated(const Geo &g, const Stencils &st, int lf, int4 fcrd, int lc, uint32_t coarse) {
+  const int o = (g.tiling == FMM2D_TRI && fcrd.w == 0) ? 1 : 0;
+  for (int e = 0; e < st.near_len[o]; ++e) {
+    const int4 q = make_int4(fcrd.x + st.near_d[o][e][0], fcrd.y + st.near_d[o][e][1],
+                             fcrd.z + st.near_d[o][e][2], 0);
+    uint32_t k;
+    if (!cell_at(g, lf, q, &k)) continue;
+    if (parent_key(g.tiling, k, lf - lc) == coarse) return false;
+  }
+  return true;
+}
+
+template <bool EMIT>
+__global__ void k_ad_lists(Geo g, const Stencils *__restrict__ stp, int l, int l_min,
+                           int64_t first, int64_t count, int64_t n_t, int64_t n_s,
+                           const int *__restrict__ t_a, const int *__restrict__ t_c,
+                           const int *__restrict__ s_a, const int *__restrict__ s_c, AdCells c,
+                           ListOut out, int64_t far_first, int *__restrict__ far_cnt,
+                           int *__restrict__ far_src, uint16_t *__restrict__ far_op,
+                           int *__restrict__ far_full, int *__restrict__ cls_cnt,
+                           int *__restrict__ cls_cells, int64_t cls_cap) {
+  const int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (it >= count + n_t + n_s) return;
+  const Stencils &st = *stp;
+  Emitter<EMIT> em(out, it);
+  if (it < count) {                                   // a cell of level l
+    const int a = (int)(first + it);
+    const bool a_tgt = c.te[a] > c.ts[a];
+    const int4 ca = c.crd[a];
+    if (a_tgt) {
+      const int o = (g.tiling == FMM2D_TRI && ca.w == 0) ? 1 : 0;
+      const bool a_leaf = !c.split[a];
+      for (int e = 0; e < st.near_len[o]; ++e) {
+        const int4 q = make_int4(ca.x + st.near_d[o][e][0], ca.y + st.near_d[o][e][1],
+                                 ca.z + st.near_d[o][e][2], 0);
+        uint32_t k;
+        if (!cell_at(g, l, q, &k)) continue;
+        const int m = find_cell(c.key, first, count, k);
+        if (m < 0 || !c.hsrc[m]) continue;
+        const bool m_leaf = !c.split[m];
+        if (a_leaf && m_leaf) {
+          em.put(K_U, a, m);
+        } else if (a_leaf) {
+          for (int d = 0; d < c.child_cnt[m]; ++d) {
+            const int ch = c.child_first[m] + d;
+            if (c.hsrc[ch]) em.put(K_T, a, ch);
+          }
+        } else if (m_leaf) {
+          for (int d = 0; d < c.child_cnt[a]; ++d) {
+            const int ch = c.child_first[a] + d;
+            if (c.te[ch] > c.ts[ch]) em.put(K_S, ch, m);
+          }
+        }
+      }
+    }
+    if (EMIT && l >= l_min) {                         // M2L list (uniform format)
+      const int cls = c.cls[a];
+      const int64_t fi = a - far_first;
+      int cnt = 0;
+      const int n_far = a_tgt ? st.far_len[cls] : 0;
+      for (int e = 0; e < st.far_len[cls]; ++e) {
+        int sidx = -1;
+        if (e < n_far) {
+          const int4 q = make_int4(ca.x + st.far_d[cls][e][0], ca.y + st.far_d[cls][e][1],
+                                   ca.z + st.far_d[cls][e][2], 0);
+          uint32_t k;
+          if (cell_at(g, l, q, &k)) {
+            sidx = find_cell(c.key, first, count, k);
+            if (sidx >= 0 && !c.hsrc[sidx]) sidx = -1;
+          }
+        }
+        if (far_full) far_full[fi * FAR_MAX + e] = sidx;
+        if (sidx < 0) continue;
+        far_src[fi * FAR_MAX + cnt] = sidx;
+        far_op[fi * FAR_MAX + cnt] = st.far_op[cls][e];
+        ++cnt;
+      }
+      far_cnt[fi] = cnt;
+      if (cls_cnt && st.far_len[cls] > 0) {
+        const int pos = atomicAdd(&cls_cnt[cls], 1);
+        cls_cells[(int64_t)cls * cls_cap + pos] = a;
+      }
+    }
+  } else if (it < count + n_t) {                      // W test: leaf a, finer cell cc
+    const int64_t j = it - count;
+    const int a = t_a[j], cc = t_c[j];
+    if (separated(g, st, l, c.crd[cc], c.lev[a], c.key[a])) em.put(K_W, a, cc);
+    else if (!c.split[cc]) em.put(K_U, a, cc);
+    else
+      for (int d = 0; d < c.child_cnt[cc]; ++d) {
+        const int ch = c.child_first[cc] + d;
+        if (c.hsrc[ch]) em.put(K_T, a, ch);
+      }
+  } else {                                            // X test: cell a, coarser leaf cc
+    const int64_t j = it - count - n_t;
+    const int a = s_a[j], cc = s_c[j];
+    if (separated(g, st, l, c.crd[a], c.lev[cc], c.key[cc])) em.put(K_X, a, cc);
+    else if (!c.split[a]) em.put(K_U, a, cc);
+    else
+      for (int d = 0; d < c.child_cnt[a]; ++d) {
+        const int ch = c.child_first[a] + d;
+        if (c.te[ch] > c.ts[ch]) em.put(K_S, ch, cc);
+      }
+  }
+  em.done();
+}
+
+__global__ void k_ad_kind_totals(const int *__restrict__ cnt, const int *__restrict__ off,
+                                 int64_t n_items, int *__restrict__ out) {
+  const int k = threadIdx.x;
+  if (k >= K_KINDS || blockIdx.x != 0) return;
+  const int64_t last = (int64_t)(k + 1) * n_items - 1;
+  out[k] = n_items > 0 ? off[last] + cnt[last] - off[(int64_t)k * n_items] : 0;
+}
+
+// ---- grouping by target -----------------------------------------------------
+// group of pair i; a target outside [0, n_groups) (never produced by the
+// traversal) goes to the spare group n_groups, past the last CSR offset
+__global__ void k_ad_keys_of(int64_t n, const int *__restrict__ tgt, const int *__restrict__ map,
+                             int n_groups, uint32_t *__restrict__ key, uint32_t *__restrict__ idx) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int v = map ? map[tgt[i]] : tgt[i];
+  key[i] = (uint32_t)((v < 0 || v >= n_groups) ? n_groups : v);
+  idx[i] = (uint32_t)i;
+}
+
+__global__ void k_ad_count(int64_t n, const uint32_t *__restrict__ key, int *__restrict__ cnt) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) atomicAdd(&cnt[key[i]], 1);
+}
+
+__global__ void k_ad_gather(int64_t n, const uint32_t *__restrict__ idx, const int *__restrict__ src,
+                            int *__restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = src[idx[i]];
+}
+
+// ---- M2P and P2L --------------------------------------------------------------
+constexpr int AWPB = 4;
+
+template <typename R>
+__device__ __forceinline__ R warp_sum_ad(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename R>
+__device__ __forceinline__ double log_abs(Cx<R> d) {
+  if constexpr (sizeof(R) == 4) {   // log|d| = (ln 2 / 2) log2|d|^2 on the MUFU unit
+    float y;
+    const float r2 = d.x * d.x + d.y * d.y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2));
+    return 0.34657359027997264 * (double)y;
+  } else {
+    return 0.5 * log(d.x * d.x + d.y * d.y);
+  }
+}
+
+// One warp per target leaf: phi_near[j] += sum over its W cells of the
+// cell's multipole evaluated at target j.
+template <typename R>
+__global__ void __launch_bounds__(32 * AWPB)
+k_ad_m2p(int64_t n_leaves, const int *__restrict__ leaf_ids, const int *__restrict__ w_off,
+         const int *__restrict__ w_src, const R *__restrict__ tgt, int tstride,
+         const int *__restrict__ ts_, const int *__restrict__ te_, const double2 *__restrict__ ctr,
+         const uint8_t *__restrict__ lev, const double2 *__restrict__ scale, int p, int P,
+         const double *__restrict__ mQ, const Cx<R> *__restrict__ ma, double *__restrict__ phi) {
+  __shared__ Cx<R> sh[AWPB][MAXP + 1];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t li = blockIdx.x * (int64_t)AWPB + w;
+  if (li >= n_leaves) return;
+  const int a = leaf_ids[li];
+  const int e0 = w_off[li], e1 = w_off[li + 1];
+  if (e0 == e1) return;
+  const int ts = ts_[a], te = te_[a];
+  const double2 ca = ctr[a];
+  for (int j0 = ts; j0 < te; j0 += 32) {
+    const int j = j0 + lane;
+    const bool act = j < te;
+    const R tx = act ? tgt[(int64_t)j * tstride] : (R)0, ty = act ? tgt[(int64_t)j * tstride + 1] : (R)0;
+    double acc = 0.0;
+    for (int e = e0; e < e1; ++e) {
+      const int cc = w_src[e];
+      __syncwarp();
+      for (int k = lane; k < p; k += 32) sh[w][k + 1] = ma[(int64_t)cc * P + k];
+      __syncwarp();
+      const double2 c2 = ctr[cc];
+      const double2 sc = scale[lev[cc]];
+      const Cx<R> d = {(R)(ca.x - c2.x) + tx, (R)(ca.y - c2.y) + ty};
+      const Cx<R> s = {(R)sc.x, (R)sc.y};
+      const R den = d.x * d.x + d.y * d.y;
+      const Cx<R> id = {d.x / den, -d.y / den};
+      const Cx<R> z = s * id;                       // s_c / (y - c)
+      Cx<R> h = sh[w][p];
+      for (int k = p - 1; k >= 1; --k) h = h * z + sh[w][k];
+      h = h * z;
+      acc += mQ[cc] * log_abs(d) + (double)h.x;
+    }
+    if (act) phi[j] += acc;
+  }
+}
+
+// One warp per target cell: adds the local expansion of the sources of its X
+// leaves (coefficients in chunks of KC, as the P2M kernel).
+template <typename R, int KC>
+__global__ void __launch_bounds__(32 * AWPB)
+k_ad_p2l(int64_t n_cells, const int *__restrict__ x_off, const int *__restrict__ x_src,
+         const R *__restrict__ src4, const int *__restrict__ ss_, const int *__restrict__ se_,
+         const double2 *__restrict__ ctr, const uint8_t *__restrict__ lev,
+         const double2 *__restrict__ inv_scale, int p, int P, double *__restrict__ lL0,
+         Cx<R> *__restrict__ lb) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t a = blockIdx.x * (int64_t)AWPB + w;
+  if (a >= n_cells) return;
+  const int e0 = x_off[a], e1 = x_off[a + 1];
+  if (e0 == e1) return;
+  const double2 ca = ctr[a];
+  const double2 is2 = inv_scale[lev[a]];
+  const Cx<R> is = {(R)is2.x, (R)is2.y};
+  // L_0: sum u log|x - c_a|
+  double q = 0.0;
+  for (int e = e0; e < e1; ++e) {
+    const int cc = x_src[e];
+    const double2 c2 = ctr[cc];
+    const R dcx = (R)(c2.x - ca.x), dcy = (R)(c2.y - ca.y);
+    for (int i = ss_[cc] + lane; i < se_[cc]; i += 32) {
+      const R *pt = src4 + 4 * (int64_t)i;
+      const Cx<R> d = {pt[0] + dcx, pt[1] + dcy};
+      q += (double)pt[2] * log_abs(d);
+    }
+  }
+  q = warp_sum_ad(q);
+  if (lane == 0) lL0[a] += q;
+  for (int k0 = 1; k0 <= p; k0 += KC) {
+    Cx<R> acc[KC];
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) acc[kk] = {(R)0, (R)0};
+    for (int e = e0; e < e1; ++e) {
+      const int cc = x_src[e];
+      const double2 c2 = ctr[cc];
+      const R dcx = (R)(c2.x - ca.x), dcy = (R)(c2.y - ca.y);
+      for (int i = ss_[cc] + lane; i < se_[cc]; i += 32) {
+        const R *pt = src4 + 4 * (int64_t)i;
+        const Cx<R> zeta = Cx<R>{pt[0] + dcx, pt[1] + dcy} * is;   // (x - c_a) / s_a
+        const R den = zeta.x * zeta.x + zeta.y * zeta.y;
+        const Cx<R> z = {zeta.x / den, -zeta.y / den};              // s_a / (x - c_a)
+        Cx<R> v = {pt[2], (R)0};
+        for (int t = 0; t < k0; ++t) v = v * z;
+#pragma unroll
+        for (int kk = 0; kk < KC; ++kk) {
+          acc[kk] = acc[kk] + v;
+          v = v * z;
+        }
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+      const R re = warp_sum_ad(acc[kk].x), im = warp_sum_ad(acc[kk].y);
+      const int k = k0 + kk;
+      if (lane == 0 && k <= p) {
+        const R inv = (R)(-1.0) / (R)k;
+        Cx<R> cur = lb[a * P + k - 1];
+        lb[a * P + k - 1] = {cur.x + re * inv, cur.y + im * inv};
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t ad_launch_root(const Geo &g, int64_t n_s, int64_t n_t, const AdCells &c, cudaStream_t s) {
+  k_ad_root<<<1, 32, 0, s>>>(g, (int)n_s, (int)n_t, c);
+  return cudaGetLastError();
+}
+
+cudaError_t ad_launch_split(const Geo &g, int l, int64_t first, int64_t count, int cap,
+                            const uint32_t *skey, const uint32_t *tkey, const AdCells &c, int *flag,
+                            int4 *crange, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_ad_split<<<nblk(count, 128), 128, 0, s>>>(g, l, first, count, cap, skey, tkey, c, flag, crange);
+  return cudaGetLastError();
+}
+
+cudaError_t ad_launch_level_total(int64_t count_b, const int *flag, const int *pos, int *total_out,
+                                  cudaStream_t s) {
+  k_ad_level_total<<<1, 32, 0, s>>>(count_b, flag, pos, total_out);
+  return cudaGetLastError();
+}
+
+cudaError_t ad_launch_emit(const Geo &g, int l, int64_t first, int64_t count, int64_t next_first,
+                           const int *flag, const int *pos, const int4 *crange, const AdCells &c,
+                           cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_ad_emit<<<nblk(count, 128), 128, 0, s>>>(g, l, first, count, next_first, flag, pos, crange, c);
+  return cudaGetLastError();
+}
+
+cudaError_t ad_launch_leaves(int64_t n_cells, const uint8_t *split, int *flag, int *pos,
+                             void *scan_scratch, int *leaf_ids, int *leaf_pos, int *n_leaves_out,
+                             cudaStream_t s) {
+  if (n_cells <= 0) return cudaSuccess;
+  k_ad_leaf_flags<<<nblk(n_cells, 256), 256, 0, s>>>(n_cells, split, flag);
+  cudaError_t e = exclusive_scan(flag, pos, n_cells, scan_scratch, s);
+  if (e != cudaSuccess) return e;
+  k_ad_leaf_ids<<<nblk(n_cells, 256), 256, 0, s>>>(n_cells, flag, pos, leaf_ids, leaf_pos);
+  k_ad_level_total<<<1, 32, 0, s>>>(n_cells, flag, pos, n_leaves_out);
+  return cudaGetLastError();
+}
+
+cudaError_t ad_launch_rel(bool f32_in, bool f32_out, const void *xy, const uint32_t *perm,
+                          int64_t n_leaves, const int *leaf_ids, const int *start, const int *end,
+                          const double2 *ctr, void *out, int stride, cudaStream_t s) {
+  if (n_leaves <= 0) return cudaSuccess;
+  const unsigned b = nblk(n_leaves * 32, 256);
+  if (f32_in && f32_out)
+    k_ad_rel<float, float><<<b, 256, 0, s>>>((const float *)xy, perm, n_leaves, leaf_ids, start, end, ctr, (float *)out, stride);
+  else if (f32_in)
+    k_ad_rel<float, double><<<b, 256, 0, s>>>((const float *)xy, perm, n_leaves, leaf_ids, start, end, ctr, (double *)out, stride);
+  else if (f32_out)
+    k_ad_rel<double, float><<<b, 256, 0, s>>>((const double *)xy, perm, n_leaves, leaf_ids, start, end, ctr, (float *)out, stride);
+  else
+    k_ad_rel<double, double><<<b, 256, 0, s>>>((const double *)xy, perm, n_leaves, leaf_ids, start, end, ctr, (double *)out, stride);
+  return cudaGetLastError();
+}
+
+cudaError_t ad_launch_lists(const Geo &g, const Stencils *d_sten, int l, int l_min, int64_t first,
+                            int64_t count, int64_t n_t, int64_t n_s, const int *t_a, const int *t_c,
+                            const int *s_a, const int *s_c, const AdCells &c, int *cnt,
+                            int *off, void *scan_scratch, int *totals, cudaStream_t s) {
+  const int64_t n_items = count + n_t + n_s;
+  if (n_items <= 0) return cudaSuccess;
+  ListOut o{};
+  o.cnt = cnt;
+  o.n_items = n_items;
+  k_ad_lists<false><<<nblk(n_items, 128), 128, 0, s>>>(g, d_sten, l, l_min, first, count, n_t, n_s,
+                                                      t_a, t_c, s_a, s_c, c, o, 0, nullptr, nullptr,
+                                                      nullptr, nullptr, nullptr, nullptr, 0);
+  cudaError_t e = exclusive_scan(cnt, off, n_items * K_KINDS, scan_scratch, s);
+  if (e != cudaSuccess) return e;
+  k_ad_kind_totals<<<1, 32, 0, s>>>(cnt, off, n_items, totals);
+  return cudaGetLastError();
+}
+
+cudaError_t ad_launch_lists_emit(const Geo &g, const Stencils *d_sten, int l, int l_min,
+                                 int64_t first, int64_t count, int64_t n_t, int64_t n_s,
+                                 const int *t_a, const int *t_c, const int *s_a, const int *s_c,
+                                 const AdCells &c, const int *off, const int64_t base[5],
+                                 int *u_t, int *u_s, int *w_t, int *w_s, int *x_t, int *x_s,
+                                 int *nt_a, int *nt_c, int *ns_a, int *ns_c, int64_t far_first,
+                                 int *far_cnt, int *far_src, uint16_t *far_op, int *far_full,
+                                 int *cls_cnt, int *cls_cells, int64_t cls_cap, cudaStream_t s) {
+  const int64_t n_items = count + n_t + n_s;
+  if (n_items <= 0) return cudaSuccess;
+  ListOut o{};
+  o.off = off;
+  o.n_items = n_items;
+  for (int k = 0; k < K_KINDS; ++k) o.base[k] = base[k];
+  o.u_t = u_t; o.u_s = u_s; o.w_t = w_t; o.w_s = w_s; o.x_t = x_t; o.x_s = x_s;
+  o.t_a = nt_a; o.t_c = nt_c; o.s_a = ns_a; o.s_c = ns_c;
+  k_ad_lists<true><<<nblk(n_items, 128), 128, 0, s>>>(g, d_sten, l, l_min, first, count, n_t, n_s,
+                                                     t_a, t_c, s_a, s_c, c, o, far_first, far_cnt,
+                                                     far_src, far_op, far_full, cls_cnt, cls_cells,
+                                                     cls_cap);
+  return cudaGetLastError();
+}
+
+cudaError_t ad_group(int64_t n, const int *tgt, const int *src, const int *map, int n_groups,
+                     uint32_t *key, uint32_t *idx, uint32_t *tmp_k, uint32_t *tmp_v, void *scratch,
+                     int *cnt, int *off, int *out_src, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)(n_groups + 1) * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  if (n > 0) {
+    k_ad_keys_of<<<nblk(n, 256), 256, 0, s>>>(n, tgt, map, n_groups, key, idx);
+    int bits = 1;
+    while ((1ll << bits) <= (int64_t)n_groups) ++bits;
+    e = radix_sort_pairs(key, idx, tmp_k, tmp_v, n, bits, scratch, s);
+    if (e != cudaSuccess) return e;
+    k_ad_count<<<nblk(n, 256), 256, 0, s>>>(n, key, cnt);
+    k_ad_gather<<<nblk(n, 256), 256, 0, s>>>(n, idx, src, out_src);
+  }
+  return exclusive_scan(cnt, off, (int64_t)n_groups + 1, scratch, s);
+}
+
+template <typename R>
+cudaError_t ad_launch_m2p(int64_t n_leaves, const int *leaf_ids, const int *w_off, const int *w_src,
+                          const R *tgt, int tstride, const int *ts, const int *te,
+                          const double2 *ctr, const uint8_t *lev, const double2 *scale, int p,
+                          int P, const double *mQ, const Cx<R> *ma, double *phi, cudaStream_t s) {
+  if (n_leaves <= 0) return cudaSuccess;
+  k_ad_m2p<R><<<nblk(n_leaves, AWPB), 32 * AWPB, 0, s>>>(n_leaves, leaf_ids, w_off, w_src, tgt,
+                                                          tstride, ts, te, ctr, lev, scale, p, P,
+                                                          mQ, ma, phi);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t ad_launch_p2l(int64_t n_cells, const int *x_off, const int *x_src, const R *src4,
+                          const int *ss, const int *se, const double2 *ctr, const uint8_t *lev,
+                          const double2 *inv_scale, int p, int P, double *lL0, Cx<R> *lb,
+                          cudaStream_t s) {
+  if (n_cells <= 0) return cudaSuccess;
+  k_ad_p2l<R, 8><<<nblk(n_cells, AWPB), 32 * AWPB, 0, s>>>(n_cells, x_off, x_src, src4, ss, se, ctr,
+                                                            lev, inv_scale, p, P, lL0, lb);
+  return cudaGetLastError();
+}
+
+#define AD_INST(R)                                                                                \
+  template cudaError_t ad_launch_m2p<R>(int64_t, const int *, const int *, const int *, const R *, \
+                                        int, const int *, const int *, const double2 *,           \
+                                        const uint8_t *, const double2 *, int, int,               \
+                                        const double *, const Cx<R> *, double *, cudaStream_t);   \
+  template cudaError_t ad_launch_p2l<R>(int64_t, const int *, const int *, const R *, const int *, \
+                                        const int *, const double2 *, const uint8_t *,            \
+                                        const double2 *, int, int, double *, Cx<R> *, cudaStream_t);
+AD_INST(float)
+AD_INST(double)
+
+}  // namespace fmm2d

@@ -41,6 +41,28 @@ void dbuf_free(DBuf &b) {
   b.bytes = 0;
 }
 
+// Grow a buffer to at least `bytes`, keeping its first `keep` bytes.
+static cudaError_t dbuf_grow_keep(DBuf &b, size_t bytes, size_t keep, cudaStream_t s) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return cudaSuccess;
+  const size_t nb = std::max(bytes, b.bytes + b.bytes / 2);
+  void *np = nullptr;
+  cudaError_t e = cudaMalloc(&np, nb);
+  if (e != cudaSuccess) return e;
+  if (b.p && keep > 0) {
+    e = cudaMemcpyAsync(np, b.p, std::min(keep, b.bytes), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      cudaFree(np);
+      return e;
+    }
+  }
+  if (b.p) cudaFree(b.p);
+  b.p = np;
+  b.bytes = nb;
+  return cudaSuccess;
+}
+
 // ------------------------------------------------------------ planner rules
 static int64_t sept_min_outside_norm(int L) {
   static std::mutex mu;
@@ -81,6 +103,12 @@ static double kappa(int tiling) {
 }
 
 static int max_levels(int tiling) { return tiling == FMM2D_SEPT ? 9 : 12; }
+// adaptive trees: keys of the finest level fit 32 bits (quadtree and triangle
+// quadtree: 2 bits a level; septree: the cached leaf-radius enumeration)
+static int ad_max_levels(int tiling) { return tiling == FMM2D_SEPT ? 9 : 16; }
+static int max_levels_for(int tiling, unsigned flags) {
+  return (flags & FMM2D_ADAPTIVE) ? ad_max_levels(tiling) : max_levels(tiling);
+}
 
 static double leaf_area(int tiling, int L) {
   if (tiling == FMM2D_QUAD) return std::pow(4.0, -L);
@@ -567,9 +595,10 @@ fmm2d_status evaluate_t(fmm2d_plan *pl, const void *u, double *out, cudaStream_t
   }
   {
     StageScope sc(pl, ST_P2P, s, 1);
-    CK(launch_p2p<R>(a.leaf_first, a.n_leaves, src4, tgt, tstride, (const int *)pl->d_src_start.p,
-                     (const int *)pl->d_src_end.p, tst, ten, (const int *)pl->d_near_cnt.p,
-                     (const int *)pl->d_near_src.p, (const double2 *)pl->d_cell_ctr.p,
+    CK(launch_p2p<R>(a.leaf_first, a.n_leaves, nullptr, src4, tgt, tstride,
+                     (const int *)pl->d_src_start.p, (const int *)pl->d_src_end.p, tst, ten,
+                     (const int *)pl->d_near_cnt.p, nullptr, (const int *)pl->d_near_src.p,
+                     (const double2 *)pl->d_cell_ctr.p,
                      (double *)pl->d_phi_near.p,
                      a.n_leaves > 0 ? (double)pl->n_tgt / (double)a.n_leaves : 0.0, s),
        "p2p");
@@ -586,6 +615,414 @@ fmm2d_status evaluate_t(fmm2d_plan *pl, const void *u, double *out, cudaStream_t
 }  // namespace
 
 // ------------------------------------------------------------ C ABI
+// ------------------------------------------------------------ adaptive tree
+static AdCells ad_cells(fmm2d_plan *pl) {
+  AdCells c;
+  c.key = (uint32_t *)pl->d_cell_key.p;
+  c.lev = (uint8_t *)pl->d_cell_lev.p;
+  c.parent = (int *)pl->d_parent.p;
+  c.child_first = (int *)pl->d_child_first.p;
+  c.child_cnt = (uint8_t *)pl->d_child_cnt.p;
+  c.split = (uint8_t *)pl->d_split.p;
+  c.ss = (int *)pl->d_src_start.p;
+  c.se = (int *)pl->d_src_end.p;
+  c.ts = pl->same_sets ? c.ss : (int *)pl->d_tgt_start.p;
+  c.te = pl->same_sets ? c.se : (int *)pl->d_tgt_end.p;
+  c.crd = (int4 *)pl->d_cell_crd.p;
+  c.ctr = (double2 *)pl->d_cell_ctr.p;
+  c.cls = (uint8_t *)pl->d_cell_cls.p;
+  c.hsrc = (uint8_t *)pl->d_cell_hsrc.p;
+  return c;
+}
+
+// Keys and sort on the finest level, the tree level by level (one read-back
+// of each level's cell count), the leaves, and the U / W / X / M2L lists by
+// the level-synchronous traversal (one read-back of each level's list sizes).
+static fmm2d_status build_adaptive(fmm2d_plan *pl, const void *src, int64_t n_src, const void *tgt,
+                                   int64_t n_tgt, cudaStream_t s) {
+  const bool f32 = (pl->flags & FMM2D_IN_F32) != 0;
+  const bool f64 = is_fp64(pl);
+  const int L = pl->levels_req ? pl->levels_req : ad_max_levels(pl->tiling);
+  const int p = pl->p_req ? pl->p_req : p_from_eps(pl->tiling, pl->eps);
+  const bool tc = (pl->flags & FMM2D_PREC_MASK) == FMM2D_PREC_MIXED_TC;
+  if (tc && !tc_shape(p, &pl->tc_K, &pl->tc_N))
+    return fail(pl, FMM2D_EINVAL, "tensor-core M2L supports p <= 31");
+  pl->L = L;
+  pl->p = p;
+  pl->P = (p + 1) & ~1;
+  fmm2d_status st = setup_geometry(pl);
+  if (st != FMM2D_OK) return st;
+  const Geo &g = pl->geo;
+  const int b = pl->b;
+  const int64_t nmax = std::max<int64_t>(1, std::max(n_src, n_tgt));
+  CK(dbuf_reserve(pl->d_key_s, nmax * 4), "alloc");
+  CK(dbuf_reserve(pl->d_perm_s, nmax * 4), "alloc");
+  CK(dbuf_reserve(pl->d_key_t, nmax * 4), "alloc");
+  CK(dbuf_reserve(pl->d_perm_t, nmax * 4), "alloc");
+  CK(dbuf_reserve(pl->d_tmp_k, nmax * 4), "alloc");
+  CK(dbuf_reserve(pl->d_tmp_v, nmax * 4), "alloc");
+  CK(dbuf_reserve(pl->d_sort_scratch, radix_sort_scratch_bytes(nmax)), "alloc");
+  const size_t rsz = f64 ? sizeof(double) : sizeof(float);
+  CK(dbuf_reserve(pl->d_src4, std::max<int64_t>(1, n_src) * 4 * rsz), "alloc");
+  CK(dbuf_reserve(pl->d_tgt2, std::max<int64_t>(1, n_tgt) * 2 * rsz), "alloc");
+  CK(dbuf_reserve(pl->d_phi_near, std::max<int64_t>(1, n_tgt) * 8), "alloc");
+  CK(dbuf_reserve(pl->d_phi_far, std::max<int64_t>(1, n_tgt) * 8), "alloc");
+  CK(dbuf_reserve(pl->d_err, 16), "alloc");
+  CK(dbuf_reserve(pl->d_dev_err, 16), "alloc");
+  CK(dbuf_reserve(pl->d_lev_first, (MAXLEV + 2) * 8), "alloc");
+  CK(dbuf_reserve(pl->d_ad_tot, 64), "alloc");
+  CK(cudaMemsetAsync(pl->d_err.p, 0, 16, s), "memset");
+  CK(cudaMemsetAsync(pl->d_dev_err.p, 0, 16, s), "memset");
+  const int bits = key_bits(pl->tiling, L);
+  uint32_t *ks = (uint32_t *)pl->d_key_s.p, *ps = (uint32_t *)pl->d_perm_s.p;
+  uint32_t *kt = (uint32_t *)pl->d_key_t.p, *pt = (uint32_t *)pl->d_perm_t.p;
+  {
+    StageScope sc(pl, ST_KEYS, s, pl->same_sets ? 1 : 2);
+    CK(launch_keys(g, src, f32, n_src, ks, ps, (int *)pl->d_err.p, s), "keys");
+    if (!pl->same_sets) CK(launch_keys(g, tgt, f32, n_tgt, kt, pt, (int *)pl->d_err.p, s), "keys");
+  }
+  {
+    StageScope sc(pl, ST_SORT, s, 1);
+    CK(radix_sort_pairs(ks, ps, (uint32_t *)pl->d_tmp_k.p, (uint32_t *)pl->d_tmp_v.p, n_src, bits,
+                        pl->d_sort_scratch.p, s), "sort");
+    if (!pl->same_sets)
+      CK(radix_sort_pairs(kt, pt, (uint32_t *)pl->d_tmp_k.p, (uint32_t *)pl->d_tmp_v.p, n_tgt, bits,
+                          pl->d_sort_scratch.p, s), "sort");
+  }
+  int err_h = 0;
+  CK(cudaMemcpyAsync(&err_h, pl->d_err.p, 4, cudaMemcpyDeviceToHost, s), "readback");
+  CK(cudaStreamSynchronize(s), "keys sync");
+  if (err_h) return fail(pl, FMM2D_EDOMAIN, "a point lies outside the domain square or root cell");
+
+  // ---- cell capacity: a split cell holds more than leaf_cap sources or
+  // targets, so a level has at most n_src/(cap+1) + n_tgt/(cap+1) of them
+  const int cap = pl->leaf_cap;
+  const int64_t nsplit = pl->same_sets ? n_src / (cap + 1) : n_src / (cap + 1) + n_tgt / (cap + 1);
+  int64_t cap_cells = 1, pw = 1;
+  for (int l = 0; l < L; ++l) {
+    pw = pw > ((int64_t)1 << 40) ? pw : pw * b;
+    cap_cells += std::min<int64_t>(pw, (int64_t)b * std::max<int64_t>(1, std::min<int64_t>(nsplit, pw / b)));
+  }
+  CK(dbuf_reserve(pl->d_cell_key, cap_cells * 4), "alloc");
+  CK(dbuf_reserve(pl->d_cell_lev, cap_cells), "alloc");
+  CK(dbuf_reserve(pl->d_parent, cap_cells * 4), "alloc");
+  CK(dbuf_reserve(pl->d_child_first, cap_cells * 4), "alloc");
+  CK(dbuf_reserve(pl->d_child_cnt, cap_cells), "alloc");
+  CK(dbuf_reserve(pl->d_split, cap_cells), "alloc");
+  CK(dbuf_reserve(pl->d_src_start, cap_cells * 4), "alloc");
+  CK(dbuf_reserve(pl->d_src_end, cap_cells * 4), "alloc");
+  if (!pl->same_sets) {
+    CK(dbuf_reserve(pl->d_tgt_start, cap_cells * 4), "alloc");
+    CK(dbuf_reserve(pl->d_tgt_end, cap_cells * 4), "alloc");
+  }
+  CK(dbuf_reserve(pl->d_cell_crd, cap_cells * sizeof(int4)), "alloc");
+  CK(dbuf_reserve(pl->d_cell_ctr, cap_cells * sizeof(double2)), "alloc");
+  CK(dbuf_reserve(pl->d_cell_cls, cap_cells), "alloc");
+  CK(dbuf_reserve(pl->d_cell_hsrc, cap_cells), "alloc");
+  AdCells c = ad_cells(pl);
+  int64_t lf[MAXLEV + 2];
+  for (int l = 0; l <= MAXLEV + 1; ++l) lf[l] = 0;
+  lf[1] = 1;
+  int depth = 0;
+  {
+    StageScope sc(pl, ST_TREE, s, 1);
+    CK(ad_launch_root(g, n_src, pl->same_sets ? n_src : n_tgt, c, s), "root");
+    for (int l = 0; l <= L; ++l) {
+      const int64_t count = lf[l + 1] - lf[l];
+      CK(dbuf_reserve(pl->d_ad_flag, std::max<int64_t>(1, count * b) * 4), "alloc");
+      CK(dbuf_reserve(pl->d_ad_pos, std::max<int64_t>(1, count * b) * 4), "alloc");
+      CK(dbuf_reserve(pl->d_ad_crange, std::max<int64_t>(1, count * b) * sizeof(int4)), "alloc");
+      CK(dbuf_reserve(pl->d_sort_scratch, std::max(radix_sort_scratch_bytes(nmax),
+                                                   scan_scratch_bytes(count * b + 1))), "alloc");
+      CK(ad_launch_split(g, l, lf[l], count, cap, ks, pl->same_sets ? nullptr : kt, c,
+                         (int *)pl->d_ad_flag.p, (int4 *)pl->d_ad_crange.p, s), "split");
+      depth = l;
+      if (l == L) break;
+      CK(exclusive_scan((const int *)pl->d_ad_flag.p, (int *)pl->d_ad_pos.p, count * b,
+                        pl->d_sort_scratch.p, s), "scan");
+      CK(ad_launch_level_total(count * b, (const int *)pl->d_ad_flag.p, (const int *)pl->d_ad_pos.p,
+                               (int *)pl->d_ad_tot.p, s), "total");
+      int tot = 0;
+      CK(cudaMemcpyAsync(&tot, pl->d_ad_tot.p, 4, cudaMemcpyDeviceToHost, s), "readback");
+      CK(cudaStreamSynchronize(s), "tree sync");
+      if (lf[l + 1] + tot > cap_cells) return fail(pl, FMM2D_ECUDA, "adaptive tree capacity exceeded");
+      CK(ad_launch_emit(g, l, lf[l], count, lf[l + 1], (const int *)pl->d_ad_flag.p,
+                        (const int *)pl->d_ad_pos.p, (const int4 *)pl->d_ad_crange.p, c, s), "emit");
+      lf[l + 2] = lf[l + 1] + tot;
+      if (tot == 0) break;
+    }
+  }
+  const int64_t n_cells = lf[depth + 1];
+  for (int l = depth + 2; l <= MAXLEV + 1; ++l) lf[l] = n_cells;
+  for (int l = 0; l <= MAXLEV + 1; ++l) pl->lev_first[l] = lf[l];
+  for (int l = 0; l <= MAXLEV; ++l) pl->lev_count[l] = lf[l + 1] - lf[l];
+  pl->n_cells = n_cells;
+  CK(cudaMemcpyAsync(pl->d_lev_first.p, lf, (MAXLEV + 2) * 8, cudaMemcpyHostToDevice, s), "upload");
+  // ---- leaves, and points relative to their leaf centre
+  CK(dbuf_reserve(pl->d_ad_flag, n_cells * 4), "alloc");
+  CK(dbuf_reserve(pl->d_ad_pos, n_cells * 4), "alloc");
+  CK(dbuf_reserve(pl->d_leaf_ids, n_cells * 4), "alloc");
+  CK(dbuf_reserve(pl->d_leaf_pos, n_cells * 4), "alloc");
+  CK(dbuf_reserve(pl->d_sort_scratch, std::max(radix_sort_scratch_bytes(nmax),
+                                               scan_scratch_bytes(n_cells + 1))), "alloc");
+  int n_leaves = 0;
+  {
+    StageScope sc(pl, ST_TREE, s, 4);
+    CK(ad_launch_leaves(n_cells, c.split, (int *)pl->d_ad_flag.p, (int *)pl->d_ad_pos.p,
+                        pl->d_sort_scratch.p, (int *)pl->d_leaf_ids.p, (int *)pl->d_leaf_pos.p,
+                        (int *)pl->d_ad_tot.p, s), "leaves");
+    CK(cudaMemcpyAsync(&n_leaves, pl->d_ad_tot.p, 4, cudaMemcpyDeviceToHost, s), "readback");
+    CK(cudaStreamSynchronize(s), "leaves sync");
+    pl->n_leaves_ad = n_leaves;
+    CK(ad_launch_rel(f32, !f64, src, ps, n_leaves, (const int *)pl->d_leaf_ids.p, c.ss, c.se, c.ctr,
+                     pl->d_src4.p, 4, s), "rel");
+    if (!pl->same_sets)
+      CK(ad_launch_rel(f32, !f64, tgt, pt, n_leaves, (const int *)pl->d_leaf_ids.p, c.ts, c.te, c.ctr,
+                       pl->d_tgt2.p, 2, s), "rel");
+  }
+  // ---- lists
+  const int64_t far_first = depth >= pl->l_min ? lf[pl->l_min] : n_cells;
+  pl->n_far_cells = n_cells - far_first;
+  const int64_t nfc = std::max<int64_t>(1, pl->n_far_cells);
+  CK(dbuf_reserve(pl->d_far_cnt, nfc * 4), "alloc");
+  CK(dbuf_reserve(pl->d_far_src, nfc * FAR_MAX * 4), "alloc");
+  CK(dbuf_reserve(pl->d_far_op, nfc * FAR_MAX * 2), "alloc");
+  if (tc) {
+    CK(dbuf_reserve(pl->d_far_full, nfc * FAR_MAX * 4), "alloc");
+    CK(dbuf_reserve(pl->d_cls_cnt, MAX_CLASSES * 4), "alloc");
+    CK(dbuf_reserve(pl->d_cls_cells, (size_t)MAX_CLASSES * nfc * 4), "alloc");
+    CK(cudaMemsetAsync(pl->d_cls_cnt.p, 0, MAX_CLASSES * 4, s), "memset");
+  }
+  pl->cls_cap = nfc;
+  int64_t n_u = 0, n_w = 0, n_x = 0, n_t = 0, n_s = 0;
+  {
+    StageScope sc(pl, ST_LISTS, s, 4 * (depth + 1));
+    for (int l = 0; l <= depth; ++l) {
+      const int64_t count = lf[l + 1] - lf[l];
+      const int64_t items = count + n_t + n_s;
+      if (items == 0) continue;
+      CK(dbuf_reserve(pl->d_ad_cnt, items * 5 * 4), "alloc");
+      CK(dbuf_reserve(pl->d_ad_off, items * 5 * 4), "alloc");
+      CK(dbuf_reserve(pl->d_sort_scratch, std::max(radix_sort_scratch_bytes(nmax),
+                                                   scan_scratch_bytes(items * 5))), "alloc");
+      CK(ad_launch_lists(g, (const Stencils *)pl->d_sten.p, l, pl->l_min, lf[l], count, n_t, n_s,
+                         (const int *)pl->d_ad_ta.p, (const int *)pl->d_ad_tc.p,
+                         (const int *)pl->d_ad_sa.p, (const int *)pl->d_ad_sc.p, c,
+                         (int *)pl->d_ad_cnt.p, (int *)pl->d_ad_off.p, pl->d_sort_scratch.p,
+                         (int *)pl->d_ad_tot.p, s), "lists");
+      int tot[5];
+      CK(cudaMemcpyAsync(tot, pl->d_ad_tot.p, 20, cudaMemcpyDeviceToHost, s), "readback");
+      CK(cudaStreamSynchronize(s), "lists sync");
+      CK(dbuf_grow_keep(pl->d_ad_ut, (n_u + tot[0]) * 4, n_u * 4, s), "alloc");
+      CK(dbuf_grow_keep(pl->d_ad_us, (n_u + tot[0]) * 4, n_u * 4, s), "alloc");
+      CK(dbuf_grow_keep(pl->d_ad_wt, (n_w + tot[1]) * 4, n_w * 4, s), "alloc");
+      CK(dbuf_grow_keep(pl->d_ad_ws, (n_w + tot[1]) * 4, n_w * 4, s), "alloc");
+      CK(dbuf_grow_keep(pl->d_ad_xt, (n_x + tot[2]) * 4, n_x * 4, s), "alloc");
+      CK(dbuf_grow_keep(pl->d_ad_xs, (n_x + tot[2]) * 4, n_x * 4, s), "alloc");
+      CK(dbuf_reserve(pl->d_ad_ta2, std::max(1, tot[3]) * 4), "alloc");
+      CK(dbuf_reserve(pl->d_ad_tc2, std::max(1, tot[3]) * 4), "alloc");
+      CK(dbuf_reserve(pl->d_ad_sa2, std::max(1, tot[4]) * 4), "alloc");
+      CK(dbuf_reserve(pl->d_ad_sc2, std::max(1, tot[4]) * 4), "alloc");
+      const int64_t base[5] = {n_u, n_w, n_x, 0, 0};
+      CK(ad_launch_lists_emit(g, (const Stencils *)pl->d_sten.p, l, pl->l_min, lf[l], count, n_t, n_s,
+                              (const int *)pl->d_ad_ta.p, (const int *)pl->d_ad_tc.p,
+                              (const int *)pl->d_ad_sa.p, (const int *)pl->d_ad_sc.p, c,
+                              (const int *)pl->d_ad_off.p, base, (int *)pl->d_ad_ut.p,
+                              (int *)pl->d_ad_us.p, (int *)pl->d_ad_wt.p, (int *)pl->d_ad_ws.p,
+                              (int *)pl->d_ad_xt.p, (int *)pl->d_ad_xs.p, (int *)pl->d_ad_ta2.p,
+                              (int *)pl->d_ad_tc2.p, (int *)pl->d_ad_sa2.p, (int *)pl->d_ad_sc2.p,
+                              far_first, (int *)pl->d_far_cnt.p, (int *)pl->d_far_src.p,
+                              (uint16_t *)pl->d_far_op.p, tc ? (int *)pl->d_far_full.p : nullptr,
+                              tc ? (int *)pl->d_cls_cnt.p : nullptr,
+                              tc ? (int *)pl->d_cls_cells.p : nullptr, nfc, s), "lists");
+      std::swap(pl->d_ad_ta, pl->d_ad_ta2);
+      std::swap(pl->d_ad_tc, pl->d_ad_tc2);
+      std::swap(pl->d_ad_sa, pl->d_ad_sa2);
+      std::swap(pl->d_ad_sc, pl->d_ad_sc2);
+      n_u += tot[0];
+      n_w += tot[1];
+      n_x += tot[2];
+      n_t = tot[3];
+      n_s = tot[4];
+    }
+    if (n_t || n_s) return fail(pl, FMM2D_ECUDA, "adaptive traversal did not terminate");
+    pl->n_u = n_u;
+    pl->n_w = n_w;
+    pl->n_x = n_x;
+    // group U and W by target leaf, X by target cell
+    const int64_t ng = std::max<int64_t>({n_u, n_w, n_x, 1});
+    CK(dbuf_reserve(pl->d_tmp_k, std::max<int64_t>(nmax, ng) * 4), "alloc");
+    CK(dbuf_reserve(pl->d_tmp_v, std::max<int64_t>(nmax, ng) * 4), "alloc");
+    CK(dbuf_reserve(pl->d_ad_cnt, std::max<int64_t>(ng, n_cells + 1) * 4), "alloc");
+    CK(dbuf_reserve(pl->d_ad_off, std::max<int64_t>(ng, n_cells + 1) * 4), "alloc");
+    CK(dbuf_reserve(pl->d_ad_flag, ng * 4), "alloc");
+    CK(dbuf_reserve(pl->d_ad_pos, ng * 4), "alloc");
+    CK(dbuf_reserve(pl->d_sort_scratch, std::max(radix_sort_scratch_bytes(ng),
+                                                 scan_scratch_bytes(n_cells + 1))), "alloc");
+    CK(dbuf_reserve(pl->d_u_off, (n_leaves + 1) * 4), "alloc");
+    CK(dbuf_reserve(pl->d_w_off, (n_leaves + 1) * 4), "alloc");
+    CK(dbuf_reserve(pl->d_x_off, (n_cells + 1) * 4), "alloc");
+    CK(dbuf_reserve(pl->d_u_src, std::max<int64_t>(1, n_u) * 4), "alloc");
+    CK(dbuf_reserve(pl->d_w_src, std::max<int64_t>(1, n_w) * 4), "alloc");
+    CK(dbuf_reserve(pl->d_x_src, std::max<int64_t>(1, n_x) * 4), "alloc");
+    auto group = [&](int64_t n, DBuf &t, DBuf &sr, const int *map, int ngroups, DBuf &off, DBuf &out) {
+      return ad_group(n, (const int *)t.p, (const int *)sr.p, map, ngroups, (uint32_t *)pl->d_ad_flag.p,
+                      (uint32_t *)pl->d_ad_pos.p, (uint32_t *)pl->d_tmp_k.p, (uint32_t *)pl->d_tmp_v.p,
+                      pl->d_sort_scratch.p, (int *)pl->d_ad_cnt.p, (int *)off.p, (int *)out.p, s);
+    };
+    CK(group(n_u, pl->d_ad_ut, pl->d_ad_us, (const int *)pl->d_leaf_pos.p, n_leaves, pl->d_u_off, pl->d_u_src), "group U");
+    CK(group(n_w, pl->d_ad_wt, pl->d_ad_ws, (const int *)pl->d_leaf_pos.p, n_leaves, pl->d_w_off, pl->d_w_src), "group W");
+    CK(group(n_x, pl->d_ad_xt, pl->d_ad_xs, nullptr, (int)n_cells, pl->d_x_off, pl->d_x_src), "group X");
+  }
+  // per-level scales for the kernels
+  std::vector<double2> sc(MAXLEV + 1), isc(MAXLEV + 1);
+  for (int l = 0; l <= MAXLEV; ++l) {
+    const cd v = l <= L ? cd(pl->scale_re[l], pl->scale_im[l]) : cd(1.0, 0.0);
+    const cd iv = 1.0 / v;
+    sc[l] = make_double2(v.real(), v.imag());
+    isc[l] = make_double2(iv.real(), iv.imag());
+  }
+  CK(dbuf_reserve(pl->d_ad_scale, (MAXLEV + 1) * sizeof(double2)), "alloc");
+  CK(dbuf_reserve(pl->d_ad_inv_scale, (MAXLEV + 1) * sizeof(double2)), "alloc");
+  CK(cudaMemcpyAsync(pl->d_ad_scale.p, sc.data(), (MAXLEV + 1) * sizeof(double2), cudaMemcpyHostToDevice, s), "upload");
+  CK(cudaMemcpyAsync(pl->d_ad_inv_scale.p, isc.data(), (MAXLEV + 1) * sizeof(double2), cudaMemcpyHostToDevice, s), "upload");
+  const int64_t need_exp = n_cells * pl->P;
+  const size_t csz = f64 ? sizeof(double2) : sizeof(float2);
+  CK(dbuf_reserve(pl->d_mQ, n_cells * 8), "alloc");
+  CK(dbuf_reserve(pl->d_lL0, n_cells * 8), "alloc");
+  CK(dbuf_reserve(pl->d_ma, need_exp * csz), "alloc");
+  CK(dbuf_reserve(pl->d_lb, need_exp * csz), "alloc");
+  CK(cudaStreamSynchronize(s), "build sync");
+  CK(cudaGetLastError(), "build");
+  pl->n_m2l = -1;
+  pl->n_p2p_pairs = -1;
+  pl->built = true;
+  return FMM2D_OK;
+}
+
+template <typename R>
+fmm2d_status evaluate_adaptive_t(fmm2d_plan *pl, const void *u, double *out, cudaStream_t s) {
+  const bool f32_in = (pl->flags & FMM2D_IN_F32) != 0;
+  const int L = pl->L;
+  R *src4 = (R *)pl->d_src4.p;
+  const R *tgt = pl->same_sets ? src4 : (const R *)pl->d_tgt2.p;
+  const int tstride = pl->same_sets ? 4 : 2;
+  const uint32_t *tperm = (const uint32_t *)(pl->same_sets ? pl->d_perm_s.p : pl->d_perm_t.p);
+  AdCells c = ad_cells(pl);
+  Cx<R> *ma = (Cx<R> *)pl->d_ma.p, *lb = (Cx<R> *)pl->d_lb.p;
+  double *mQ = (double *)pl->d_mQ.p, *lL0 = (double *)pl->d_lL0.p;
+  int depth = 0;
+  while (depth < L && pl->lev_count[depth + 1] > 0) ++depth;
+  ExpandArgs a;
+  a.p = pl->p;
+  a.P = pl->P;
+  a.L = L;
+  a.l_min = pl->l_min;
+  a.b = pl->b;
+  a.leaf_first = 0;
+  a.n_leaves = pl->n_leaves_ad;
+  a.inv_s_re = 1.0;
+  a.inv_s_im = 0.0;
+  a.leaf_ids = (const int *)pl->d_leaf_ids.p;
+  a.cell_lev = c.lev;
+  a.inv_scale = (const double2 *)pl->d_ad_inv_scale.p;
+  a.child_first = c.child_first;
+  a.child_cnt = c.child_cnt;
+  a.parent = c.parent;
+  {
+    StageScope sc(pl, ST_OTHER, s, 1);
+    CK(launch_gather_u<R>(u, f32_in, (const uint32_t *)pl->d_perm_s.p, pl->n_src, src4, s), "gather");
+  }
+  {
+    StageScope sc(pl, ST_P2M, s, 1);
+    CK(launch_p2m<R>(a, src4, c.ss, c.se, mQ, ma, s), "p2m");
+  }
+  {
+    StageScope sc(pl, ST_M2M, s, std::max(0, depth - 1));
+    for (int l = depth - 1; l >= 1; --l)
+      CK(launch_m2m<R>(a, pl->geo, l, pl->lev_first[l], pl->lev_count[l], nullptr, c.key, c.cls,
+                       c.hsrc, (const Cx<R> *)pl->d_m2m_ops.p, mQ, ma, s), "m2m");
+  }
+  if (pl->n_far_cells == 0) {
+    CK(cudaMemsetAsync(lL0, 0, pl->n_cells * sizeof(double), s), "zero locals");
+    CK(cudaMemsetAsync(lb, 0, pl->n_cells * pl->P * sizeof(Cx<R>), s), "zero locals");
+  } else if constexpr (sizeof(R) == 4) {
+    if ((pl->flags & FMM2D_PREC_MASK) == FMM2D_PREC_MIXED_TC) {
+      StageScope sc(pl, ST_M2L, s, 1);
+      TcArgs t;
+      t.p = pl->p;
+      t.P = pl->P;
+      t.n_classes = pl->sten.n_classes;
+      t.sms = pl->n_sms;
+      t.far_first = pl->n_cells - pl->n_far_cells;
+      t.cls_cap = pl->cls_cap;
+      t.cls_cnt = (const int *)pl->d_cls_cnt.p;
+      t.cls_cells = (const int *)pl->d_cls_cells.p;
+      t.far_full = (const int *)pl->d_far_full.p;
+      t.sten_ops = (const uint16_t *)((const char *)pl->d_sten.p + offsetof(Stencils, far_op));
+      t.sten_len = (const int *)((const char *)pl->d_sten.p + offsetof(Stencils, far_len));
+      t.btab = (const unsigned char *)pl->d_tc_ops.p;
+      t.logz = (const double *)pl->d_m2l_logz.p;
+      t.log_abs_scale = (const double *)pl->d_geo_scale.p;
+      t.lev_first = (const int64_t *)pl->d_lev_first.p;
+      t.l_min = pl->l_min;
+      t.L = L;
+      t.mQ = mQ;
+      t.ma = (const float2 *)ma;
+      t.lL0 = lL0;
+      t.lb = (float2 *)lb;
+      t.err = (int *)pl->d_dev_err.p;
+      CK(launch_m2l_tc(t, pl->tc_K, pl->tc_N, pl->n_far_cells, s), "m2l_tc");
+    } else {
+      StageScope sc(pl, ST_M2L, s, 1);
+      const int64_t ff = pl->n_cells - pl->n_far_cells;
+      CK(launch_m2l<R>(a, ff, pl->n_far_cells, (const int64_t *)pl->d_lev_first.p,
+                       (const double *)pl->d_geo_scale.p, 0, (const int *)pl->d_far_cnt.p,
+                       (const int *)pl->d_far_src.p, (const uint16_t *)pl->d_far_op.p,
+                       (const Cx<R> *)pl->d_m2l_ops.p, (const double *)pl->d_m2l_logz.p, mQ, ma,
+                       lL0, lb, s), "m2l");
+    }
+  } else {
+    StageScope sc(pl, ST_M2L, s, 1);
+    const int64_t ff = pl->n_cells - pl->n_far_cells;
+    CK(launch_m2l<R>(a, ff, pl->n_far_cells, (const int64_t *)pl->d_lev_first.p,
+                     (const double *)pl->d_geo_scale.p, 0, (const int *)pl->d_far_cnt.p,
+                     (const int *)pl->d_far_src.p, (const uint16_t *)pl->d_far_op.p,
+                     (const Cx<R> *)pl->d_m2l_ops.p, (const double *)pl->d_m2l_logz.p, mQ, ma, lL0,
+                     lb, s), "m2l");
+  }
+  {
+    StageScope sc(pl, ST_M2L, s, 1);   // P2L (X lists) completes the locals before L2L
+    CK(ad_launch_p2l<R>(pl->n_cells, (const int *)pl->d_x_off.p, (const int *)pl->d_x_src.p, src4,
+                        c.ss, c.se, c.ctr, c.lev, (const double2 *)pl->d_ad_inv_scale.p, pl->p,
+                        pl->P, lL0, lb, s), "p2l");
+  }
+  {
+    StageScope sc(pl, ST_L2L, s, std::max(0, depth - pl->l_min));
+    for (int l = pl->l_min + 1; l <= depth; ++l)
+      CK(launch_l2l<R>(a, pl->geo, l, pl->lev_first[l], pl->lev_count[l], nullptr, c.key, c.cls,
+                       (const Cx<R> *)pl->d_l2l_ops.p, lL0, lb, s), "l2l");
+  }
+  {
+    StageScope sc(pl, ST_P2P, s, 2);
+    CK(launch_p2p<R>(0, pl->n_leaves_ad, (const int *)pl->d_leaf_ids.p, src4, tgt, tstride, c.ss,
+                     c.se, c.ts, c.te, nullptr, (const int *)pl->d_u_off.p,
+                     (const int *)pl->d_u_src.p, c.ctr, (double *)pl->d_phi_near.p,
+                     pl->n_leaves_ad > 0 ? (double)pl->n_tgt / (double)pl->n_leaves_ad : 0.0, s),
+       "p2p");
+    CK(ad_launch_m2p<R>(pl->n_leaves_ad, (const int *)pl->d_leaf_ids.p, (const int *)pl->d_w_off.p,
+                        (const int *)pl->d_w_src.p, tgt, tstride, c.ts, c.te, c.ctr, c.lev,
+                        (const double2 *)pl->d_ad_scale.p, pl->p, pl->P, mQ, ma,
+                        (double *)pl->d_phi_near.p, s), "m2p");
+  }
+  {
+    StageScope sc(pl, ST_L2P, s, 1);
+    CK(launch_l2p<R>(a, tgt, tstride, c.ts, c.te, tperm, lL0, lb, (const double *)pl->d_phi_near.p,
+                     (double *)pl->d_phi_far.p, out, s), "l2p");
+  }
+  return FMM2D_OK;
+}
+
 extern "C" {
 
 fmm2d_status fmm2d_default_params(int tiling, int64_t n_points, int leaf_target, double eps,
@@ -608,10 +1045,10 @@ fmm2d_status fmm2d_plan_create(int tiling, int levels, int p, double eps, unsign
   if (!out) return FMM2D_EINVAL;
   *out = nullptr;
   if (tiling < 0 || tiling > 2) { g_create_err = "unknown tiling"; return FMM2D_EINVAL; }
-  if (levels < 0 || levels > max_levels(tiling)) { g_create_err = "levels out of range"; return FMM2D_EINVAL; }
+  if (levels < 0 || levels > max_levels_for(tiling, flags)) { g_create_err = "levels out of range"; return FMM2D_EINVAL; }
   if (p < 0 || p > MAXP) { g_create_err = "p out of range (0..48)"; return FMM2D_EINVAL; }
   if (p == 0 && !(eps > 0.0 && eps < 1.0)) { g_create_err = "eps must be in (0, 1)"; return FMM2D_EINVAL; }
-  if ((flags & FMM2D_PREC_MASK) == 3u || (flags & ~(FMM2D_PREC_MASK | FMM2D_IN_F32)) != 0) {
+  if ((flags & FMM2D_PREC_MASK) == 3u || (flags & ~(FMM2D_PREC_MASK | FMM2D_IN_F32 | FMM2D_ADAPTIVE)) != 0) {
     g_create_err = "unknown flags";
     return FMM2D_EINVAL;
   }
@@ -630,12 +1067,21 @@ fmm2d_status fmm2d_plan_create(int tiling, int levels, int p, double eps, unsign
 
 fmm2d_status fmm2d_plan_set_params(fmm2d_plan *pl, int levels, int p, double eps) {
   if (!pl) return FMM2D_EINVAL;
-  if (levels < 0 || levels > max_levels(pl->tiling)) return fail(pl, FMM2D_EINVAL, "levels out of range");
+  if (levels < 0 || levels > max_levels_for(pl->tiling, pl->flags))
+    return fail(pl, FMM2D_EINVAL, "levels out of range");
   if (p < 0 || p > MAXP) return fail(pl, FMM2D_EINVAL, "p out of range (0..48)");
   if (p == 0 && !(eps > 0.0 && eps < 1.0)) return fail(pl, FMM2D_EINVAL, "eps must be in (0, 1)");
   pl->levels_req = levels;
   pl->p_req = p;
   pl->eps = eps;
+  pl->built = false;
+  return FMM2D_OK;
+}
+
+fmm2d_status fmm2d_plan_set_leaf_size(fmm2d_plan *pl, int leaf_size) {
+  if (!pl) return FMM2D_EINVAL;
+  if (leaf_size < 0) return fail(pl, FMM2D_EINVAL, "leaf size must be >= 0");
+  pl->leaf_cap = leaf_size;
   pl->built = false;
   return FMM2D_OK;
 }
@@ -665,6 +1111,7 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
   pl->same_sets = (src == tgt && n_src == n_tgt);
   pl->n_src = n_src;
   pl->n_tgt = n_tgt;
+  if (pl->flags & FMM2D_ADAPTIVE) return build_adaptive(pl, src, n_src, tgt, n_tgt, s);
   int L = pl->levels_req, p = pl->p_req;
   if (L == 0) L = auto_levels(pl->tiling, std::max(n_src, n_tgt), 64);
   if (p == 0) p = p_from_eps(pl->tiling, pl->eps);
@@ -833,6 +1280,10 @@ fmm2d_status fmm2d_evaluate(fmm2d_plan *pl, const void *u, double *out, void *st
   cudaStream_t s = (cudaStream_t)stream;
   pl->last_stream = s;
   if (pl->n_tgt == 0) return FMM2D_OK;
+  if (pl->flags & FMM2D_ADAPTIVE) {
+    if (is_fp64(pl)) return evaluate_adaptive_t<double>(pl, u, out, s);
+    return evaluate_adaptive_t<float>(pl, u, out, s);
+  }
   if (is_fp64(pl)) return evaluate_t<double>(pl, u, out, s);
   return evaluate_t<float>(pl, u, out, s);
 }
@@ -859,6 +1310,32 @@ fmm2d_status fmm2d_plan_query(const fmm2d_plan *cpl, fmm2d_info *info) {
   info->n_m2l_ops = pl->n_ops;
   info->max_far = pl->max_far;
   info->max_near = pl->max_near;
+  if (pl->n_m2l < 0 && (pl->flags & FMM2D_ADAPTIVE)) {
+    cudaStreamSynchronize(pl->last_stream);
+    std::vector<int> fc(std::max<int64_t>(1, pl->n_far_cells));
+    int64_t tot = 0;
+    if (pl->n_far_cells > 0) {
+      cudaMemcpy(fc.data(), pl->d_far_cnt.p, pl->n_far_cells * 4, cudaMemcpyDeviceToHost);
+      for (int64_t i = 0; i < pl->n_far_cells; ++i) tot += fc[i];
+    }
+    pl->n_m2l = tot;
+    const int64_t nl = pl->n_leaves_ad, nc = pl->n_cells;
+    std::vector<int> off(nl + 1), us(std::max<int64_t>(1, pl->n_u)), ids(std::max<int64_t>(1, nl));
+    std::vector<int> ss(nc), se(nc), ts(nc), te(nc);
+    cudaMemcpy(off.data(), pl->d_u_off.p, (nl + 1) * 4, cudaMemcpyDeviceToHost);
+    if (pl->n_u) cudaMemcpy(us.data(), pl->d_u_src.p, pl->n_u * 4, cudaMemcpyDeviceToHost);
+    if (nl) cudaMemcpy(ids.data(), pl->d_leaf_ids.p, nl * 4, cudaMemcpyDeviceToHost);
+    cudaMemcpy(ss.data(), pl->d_src_start.p, nc * 4, cudaMemcpyDeviceToHost);
+    cudaMemcpy(se.data(), pl->d_src_end.p, nc * 4, cudaMemcpyDeviceToHost);
+    cudaMemcpy(ts.data(), pl->same_sets ? pl->d_src_start.p : pl->d_tgt_start.p, nc * 4, cudaMemcpyDeviceToHost);
+    cudaMemcpy(te.data(), pl->same_sets ? pl->d_src_end.p : pl->d_tgt_end.p, nc * 4, cudaMemcpyDeviceToHost);
+    int64_t pairs = 0;
+    for (int64_t i = 0; i < nl; ++i) {
+      const int a = ids[i];
+      for (int e = off[i]; e < off[i + 1]; ++e) pairs += (int64_t)(te[a] - ts[a]) * (se[us[e]] - ss[us[e]]);
+    }
+    pl->n_p2p_pairs = pairs;
+  }
   if (pl->n_m2l < 0) {
     cudaStreamSynchronize(pl->last_stream);
     std::vector<int> fc(std::max<int64_t>(1, pl->n_far_cells));
@@ -1018,6 +1495,47 @@ fmm2d_status fmm2d_debug_export(fmm2d_plan *pl, int what, int level, void *host_
       std::vector<double> o(n);
       for (int64_t i = 0; i < n; ++i) o[pm[i]] = v[i];
       for (int64_t i = 0; i < n; ++i) putd(o[i]);
+      break;
+    }
+    case 13: case 14: case 15: case 16: case 17: {
+      if (!(pl->flags & FMM2D_ADAPTIVE)) return fail(pl, FMM2D_EINVAL, "not an adaptive plan");
+      const int64_t nc = pl->n_cells;
+      std::vector<uint8_t> lev(nc), spl(nc);
+      CK(cudaMemcpy(lev.data(), pl->d_cell_lev.p, nc, cudaMemcpyDeviceToHost), "copy");
+      CK(cudaMemcpy(spl.data(), pl->d_split.p, nc, cudaMemcpyDeviceToHost), "copy");
+      if (what == 13) {
+        for (int64_t i = 0; i < nc; ++i) { put64(lev[i]); put64(ckey[i]); put64(spl[i]); }
+        break;
+      }
+      if (what == 17) {
+        const int64_t ff = nc - pl->n_far_cells;
+        std::vector<int> cnt(std::max<int64_t>(1, pl->n_far_cells)), src(std::max<int64_t>(1, pl->n_far_cells * FAR_MAX));
+        if (pl->n_far_cells) {
+          CK(cudaMemcpy(cnt.data(), pl->d_far_cnt.p, pl->n_far_cells * 4, cudaMemcpyDeviceToHost), "copy");
+          CK(cudaMemcpy(src.data(), pl->d_far_src.p, pl->n_far_cells * FAR_MAX * 4, cudaMemcpyDeviceToHost), "copy");
+        }
+        for (int64_t i = 0; i < pl->n_far_cells; ++i)
+          for (int e = 0; e < cnt[i]; ++e) {
+            const int sc = src[i * FAR_MAX + e];
+            put64(lev[ff + i]); put64(ckey[ff + i]); put64(lev[sc]); put64(ckey[sc]);
+          }
+        break;
+      }
+      const bool by_leaf = what != 16;
+      const int64_t ng = by_leaf ? pl->n_leaves_ad : nc;
+      const int64_t n = what == 14 ? pl->n_u : what == 15 ? pl->n_w : pl->n_x;
+      const DBuf &ob = what == 14 ? pl->d_u_off : what == 15 ? pl->d_w_off : pl->d_x_off;
+      const DBuf &sb = what == 14 ? pl->d_u_src : what == 15 ? pl->d_w_src : pl->d_x_src;
+      std::vector<int> off(ng + 1), src(std::max<int64_t>(1, n)), ids(std::max<int64_t>(1, ng));
+      CK(cudaMemcpy(off.data(), ob.p, (ng + 1) * 4, cudaMemcpyDeviceToHost), "copy");
+      if (n) CK(cudaMemcpy(src.data(), sb.p, n * 4, cudaMemcpyDeviceToHost), "copy");
+      if (by_leaf && ng) CK(cudaMemcpy(ids.data(), pl->d_leaf_ids.p, ng * 4, cudaMemcpyDeviceToHost), "copy");
+      for (int64_t i = 0; i < ng; ++i) {
+        const int a = by_leaf ? ids[i] : (int)i;
+        for (int e = off[i]; e < off[i + 1]; ++e) {
+          put64(lev[a]); put64(ckey[a]); put64(lev[src[e]]); put64(ckey[src[e]]);
+        }
+      }
       break;
     }
     default:

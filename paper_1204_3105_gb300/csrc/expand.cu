@@ -45,9 +45,13 @@ k_p2m(ExpandArgs a, const R *__restrict__ src4, const int *__restrict__ start,
   const int lane = threadIdx.x & 31;
   const int64_t li = blockIdx.x * (int64_t)WPB + (threadIdx.x >> 5);
   if (li >= a.n_leaves) return;
-  const int64_t g = a.leaf_first + li;
+  const int64_t g = a.leaf_ids ? (int64_t)a.leaf_ids[li] : a.leaf_first + li;
   const int s = start[g], e = end[g];
-  const Cx<R> is = {(R)a.inv_s_re, (R)a.inv_s_im};
+  Cx<R> is = {(R)a.inv_s_re, (R)a.inv_s_im};
+  if (a.leaf_ids) {
+    const double2 v = a.inv_scale[a.cell_lev[g]];
+    is = {(R)v.x, (R)v.y};
+  }
   double q = 0.0;
   for (int i = s + lane; i < e; i += 32) q += (double)src4[4 * (int64_t)i + 2];
   q = warp_sum(q);
@@ -91,13 +95,16 @@ k_m2m(ExpandArgs a, Geo g, int level, int64_t first, int64_t count, const int *_
   const int64_t ci = blockIdx.x * (int64_t)WPB + w;
   if (ci >= count) return;
   const int64_t gp = first + ci;
+  if (a.child_first && a.child_cnt[gp] == 0) return;   // adaptive leaf: keeps its P2M
   const int p = a.p, P1 = p + 1;
   Cx<R> acc0 = {(R)0, (R)0}, acc1 = {(R)0, (R)0};
   double Q = 0.0;
   if (cell_hsrc[gp]) {
     const uint32_t key = cell_key[gp];
-    for (int d = 0; d < g.b; ++d) {
-      int cs = map[g.map_off[level + 1] + (int64_t)key * g.b + d];
+    const int nch = a.child_first ? (int)a.child_cnt[gp] : g.b;
+    for (int d = 0; d < nch; ++d) {
+      int cs = a.child_first ? a.child_first[gp] + d
+                             : map[g.map_off[level + 1] + (int64_t)key * g.b + d];
       if (cs < 0 || !cell_hsrc[cs]) continue;
       const double Qc = mQ[cs];
       for (int k = lane; k < p; k += 32) sh[w][k + 1] = ma[(int64_t)cs * a.P + k];
@@ -178,9 +185,14 @@ k_l2l(ExpandArgs a, Geo g, int level, int64_t first, int64_t count, const int *_
   const int64_t ci = blockIdx.x * (int64_t)WPB + w;
   if (ci >= count) return;
   const int64_t gc = first + ci;
-  const uint32_t key = cell_key[gc];
-  const uint32_t pkey = (g.tiling == FMM2D_SEPT) ? key / 7u : key >> 2;
-  const int ps = map[g.map_off[level - 1] + pkey];
+  int ps;
+  if (a.parent) {
+    ps = a.parent[gc];
+  } else {
+    const uint32_t key = cell_key[gc];
+    const uint32_t pkey = (g.tiling == FMM2D_SEPT) ? key / 7u : key >> 2;
+    ps = map[g.map_off[level - 1] + pkey];
+  }
   const int p = a.p, P1 = p + 1;
   for (int k = lane; k < p; k += 32) sh[w][k + 1] = lb[(int64_t)ps * a.P + k];
   __syncwarp();
@@ -213,14 +225,18 @@ k_l2p(ExpandArgs a, const R *__restrict__ tgt, int tstride, const int *__restric
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t li = blockIdx.x * (int64_t)WPB + w;
   if (li >= a.n_leaves) return;
-  const int64_t g = a.leaf_first + li;
+  const int64_t g = a.leaf_ids ? (int64_t)a.leaf_ids[li] : a.leaf_first + li;
   const int s = start[g], e = end[g];
   if (s >= e) return;
   const int p = a.p;
   for (int k = lane; k < p; k += 32) sh[w][k + 1] = lb[g * a.P + k];
   __syncwarp();
   const double L0 = lL0[g];
-  const Cx<R> is = {(R)a.inv_s_re, (R)a.inv_s_im};
+  Cx<R> is = {(R)a.inv_s_re, (R)a.inv_s_im};
+  if (a.leaf_ids) {
+    const double2 v = a.inv_scale[a.cell_lev[g]];
+    is = {(R)v.x, (R)v.y};
+  }
   for (int j = s + lane; j < e; j += 32) {
     const R *pt = tgt + (int64_t)j * tstride;
     Cx<R> z = Cx<R>{pt[0], pt[1]} * is;

@@ -94,20 +94,21 @@ __device__ __forceinline__ void p2p_leaf(const typename P2PTraits<R>::V4 *__rest
 
 template <typename R>
 __global__ void __launch_bounds__(P2P_TH)
-k_p2p(int64_t leaf_first, int64_t n_leaves, const R *__restrict__ src4, const R *__restrict__ tgt,
-      int tstride, const int *__restrict__ sst, const int *__restrict__ sen,
-      const int *__restrict__ tst, const int *__restrict__ ten, const int *__restrict__ near_cnt,
-      const int *__restrict__ near_src, const double2 *__restrict__ ctr,
-      double *__restrict__ phi_near) {
+k_p2p(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_ids,
+      const R *__restrict__ src4, const R *__restrict__ tgt, int tstride,
+      const int *__restrict__ sst, const int *__restrict__ sen, const int *__restrict__ tst,
+      const int *__restrict__ ten, const int *__restrict__ near_cnt,
+      const int *__restrict__ near_off, const int *__restrict__ near_src,
+      const double2 *__restrict__ ctr, double *__restrict__ phi_near) {
   using T = P2PTraits<R>;
   const int lane = threadIdx.x & 31;
   const int64_t li = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (li >= n_leaves) return;
-  const int64_t g = leaf_first + li;
+  const int64_t g = leaf_ids ? (int64_t)leaf_ids[li] : leaf_first + li;
   const int ts = tst[g], te = ten[g];
   if (ts >= te) return;
-  const int nn = near_cnt[li];
-  const int *nsrc = near_src + li * NEAR_MAX;
+  const int nn = near_off ? near_off[li + 1] - near_off[li] : near_cnt[li];
+  const int *nsrc = near_off ? near_src + near_off[li] : near_src + li * NEAR_MAX;
   const double2 cg = ctr[g];
   const typename T::V4 *src = reinterpret_cast<const typename T::V4 *>(src4);
   for (int t0 = ts; t0 < te; t0 += 64) {
@@ -345,10 +346,11 @@ __device__ __forceinline__ void x2_slice(const float4 *sxy, const float2 *su, in
 
 template <int T>
 __global__ void __launch_bounds__(P2P_TH, 4)
-k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const float *__restrict__ src4,
-         const float *__restrict__ tgt, int tstride, const int *__restrict__ sst,
-         const int *__restrict__ sen, const int *__restrict__ tst, const int *__restrict__ ten,
-         const int *__restrict__ near_cnt, const int *__restrict__ near_src,
+k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_ids,
+         const float *__restrict__ src4, const float *__restrict__ tgt, int tstride,
+         const int *__restrict__ sst, const int *__restrict__ sen, const int *__restrict__ tst,
+         const int *__restrict__ ten, const int *__restrict__ near_cnt,
+         const int *__restrict__ near_off, const int *__restrict__ near_src,
          const double2 *__restrict__ ctr, double *__restrict__ phi_near) {
   constexpr int G = P2P_TH / T, CAP = X2_CAP / G;
   __shared__ float4 s_xy[X2_CAP];
@@ -359,35 +361,42 @@ k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const float *__restrict__ src4,
   const int grp = threadIdx.x / T, tg = threadIdx.x % T;
   const int64_t li = (int64_t)blockIdx.x * G + grp;
   if (li >= n_leaves) return;                 // group-uniform exits only
-  const int64_t g = leaf_first + li;
+  const int64_t g = leaf_ids ? (int64_t)leaf_ids[li] : leaf_first + li;
   const int ts = tst[g], te = ten[g];
   if (ts >= te) return;
-  const int nn = near_cnt[li];
-  const int *nsrc = near_src + li * NEAR_MAX;
+  // source leaves: a fixed-stride Near list (uniform tree) or a CSR list of
+  // any length (adaptive tree), taken in batches of at most NEAR_MAX leaves;
+  // the target's own leaf, when it holds sources, comes first
+  const int n_all = near_off ? near_off[li + 1] - near_off[li] : near_cnt[li];
+  const int *nall = near_off ? near_src + near_off[li] : near_src + li * NEAR_MAX;
+  const bool single = n_all <= NEAR_MAX;
   float4 *sxy = s_xy + grp * CAP;
   float2 *su = s_u + grp * CAP;
-  if (tg < nn) {
-    const int s = nsrc[tg];
-    const double2 cg = ctr[g], cs = ctr[s];
-    m_s0[grp][tg] = sst[s];
-    m_base[grp][tg + 1] = sen[s] - sst[s];   // counts, prefix-summed below
-    m_dx[grp][tg] = (float)(cs.x - cg.x);
-    m_dy[grp][tg] = (float)(cs.y - cg.y);
-  }
-  x2_sync<T>(grp);
-  if (tg == 0) {
-    int b = 0;
-    m_base[grp][0] = 0;
-    for (int e = 0; e < nn; ++e) {
-      b += m_base[grp][e + 1];
-      m_base[grp][e + 1] = b;
-    }
-  }
-  x2_sync<T>(grp);
-  const int total = m_base[grp][nn];
-  // the Near stencils list the leaf itself first
-  const int n_self = (nn > 0 && nsrc[0] == (int)g) ? m_base[grp][1] : 0;
   const float4 *src = reinterpret_cast<const float4 *>(src4);
+  const double2 cg = ctr[g];
+  int nn = 0, total = 0;
+  auto setup = [&](int b0) {   // shift and prefix table of one batch (group-synchronous)
+    nn = min(NEAR_MAX, n_all - b0);
+    if (tg < nn) {
+      const int sl = nall[b0 + tg];
+      const double2 cs = ctr[sl];
+      m_s0[grp][tg] = sst[sl];
+      m_base[grp][tg + 1] = sen[sl] - sst[sl];   // counts, prefix-summed below
+      m_dx[grp][tg] = (float)(cs.x - cg.x);
+      m_dy[grp][tg] = (float)(cs.y - cg.y);
+    }
+    x2_sync<T>(grp);
+    if (tg == 0) {
+      int b = 0;
+      m_base[grp][0] = 0;
+      for (int e = 0; e < nn; ++e) {
+        b += m_base[grp][e + 1];
+        m_base[grp][e + 1] = b;
+      }
+    }
+    x2_sync<T>(grp);
+    total = m_base[grp][nn];
+  };
   auto stage = [&](int c0, int c1) {
     for (int e = 0; e < nn; ++e) {
       const int b = m_base[grp][e], lo = max(b, c0), hi = min(m_base[grp][e + 1], c1);
@@ -401,10 +410,14 @@ k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const float *__restrict__ src4,
       }
     }
   };
-  const bool once = total <= CAP;   // all Near sources fit: stage them once
-  if (once) {
-    stage(0, total);
-    x2_sync<T>(grp);
+  bool once = false;
+  if (single) {
+    setup(0);
+    once = total <= CAP;   // all Near sources fit: stage them once
+    if (once) {
+      stage(0, total);
+      x2_sync<T>(grp);
+    }
   }
   for (int t0 = ts; t0 < te; t0 += 4 * T) {
     const int ntc = min(4 * T, te - t0);
@@ -423,19 +436,26 @@ k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const float *__restrict__ src4,
       ycd = make_float2(tgt[(int64_t)j[2] * tstride + 1], tgt[(int64_t)j[3] * tstride + 1]);
     }
     float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int c0 = 0; c0 < total; c0 += CAP) {
-      const int c1 = min(total, c0 + CAP);
-      if (!once) {
-        x2_sync<T>(grp);
-        stage(c0, c1);
-        x2_sync<T>(grp);
+    for (int b0 = 0; b0 < n_all; b0 += NEAR_MAX) {
+      if (!single) {
+        x2_sync<T>(grp);   // the previous batch's table and staging are no longer read
+        setup(b0);
       }
-      if (act) {
-        const int m = c1 - c0;
-        const int self_end = max(0, min(m, n_self - c0));
-        const int first_unchecked = self_end + ((k - self_end) % K + K) % K;
-        if (self_end > 0) x2_slice<true>(sxy, su, k, self_end, K, xab, xcd, yab, ycd, s, c);
-        x2_slice<false>(sxy, su, first_unchecked, m, K, xab, xcd, yab, ycd, s, c);
+      const int n_self = (b0 == 0 && nn > 0 && nall[0] == (int)g) ? m_base[grp][1] : 0;
+      for (int c0 = 0; c0 < total; c0 += CAP) {
+        const int c1 = min(total, c0 + CAP);
+        if (!once) {
+          x2_sync<T>(grp);
+          stage(c0, c1);
+          x2_sync<T>(grp);
+        }
+        if (act) {
+          const int m = c1 - c0;
+          const int self_end = max(0, min(m, n_self - c0));
+          const int first_unchecked = self_end + ((k - self_end) % K + K) % K;
+          if (self_end > 0) x2_slice<true>(sxy, su, k, self_end, K, xab, xcd, yab, ycd, s, c);
+          x2_slice<false>(sxy, su, first_unchecked, m, K, xab, xcd, yab, ycd, s, c);
+        }
       }
     }
 #pragma unroll
@@ -464,11 +484,11 @@ k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const float *__restrict__ src4,
 }  // namespace
 
 template <typename R>
-cudaError_t launch_p2p(int64_t leaf_first, int64_t n_leaves, const R *src4, const R *tgt,
-                       int tstride, const int *src_start, const int *src_end,
+cudaError_t launch_p2p(int64_t leaf_first, int64_t n_leaves, const int *leaf_ids, const R *src4,
+                       const R *tgt, int tstride, const int *src_start, const int *src_end,
                        const int *tgt_start, const int *tgt_end, const int *near_cnt,
-                       const int *near_src, const double2 *ctr, double *phi_near,
-                       double mean_targets, cudaStream_t s) {
+                       const int *near_off, const int *near_src, const double2 *ctr,
+                       double *phi_near, double mean_targets, cudaStream_t s) {
   if (n_leaves <= 0) return cudaSuccess;
   if constexpr (sizeof(R) == 4) {
     // group size: the smallest T for which a leaf of mean + 2 sigma (Poisson)
@@ -478,33 +498,34 @@ cudaError_t launch_p2p(int64_t leaf_first, int64_t n_leaves, const R *src4, cons
     const int G = P2P_TH / T;
     const unsigned blocks = (unsigned)((n_leaves + G - 1) / G);
 #define X2_LAUNCH(TT)                                                                             \
-  k_p2p_x2<TT><<<blocks, P2P_TH, 0, s>>>(leaf_first, n_leaves, src4, tgt, tstride, src_start,      \
-                                         src_end, tgt_start, tgt_end, near_cnt, near_src, ctr,    \
-                                         phi_near)
+  k_p2p_x2<TT><<<blocks, P2P_TH, 0, s>>>(leaf_first, n_leaves, leaf_ids, src4, tgt, tstride,       \
+                                         src_start, src_end, tgt_start, tgt_end, near_cnt,        \
+                                         near_off, near_src, ctr, phi_near)
     if (T == 32) X2_LAUNCH(32);
     else if (T == 64) X2_LAUNCH(64);
     else if (T == 128) X2_LAUNCH(128);
     else X2_LAUNCH(256);
 #undef X2_LAUNCH
-  } else if (mean_targets >= 48.0) {   // FP64, large leaves: block-staged, sliced sources
+  } else if (mean_targets >= 48.0 && !near_off) {   // FP64, large leaves: block-staged
     k_p2p_block<R><<<(unsigned)n_leaves, P2P_TH, 0, s>>>(leaf_first, src4, tgt, tstride, src_start,
                                                          src_end, tgt_start, tgt_end, near_cnt,
                                                          near_src, ctr, phi_near);
-  } else {                             // FP64, small leaves: one warp per leaf
+  } else {                             // FP64, small leaves or CSR lists: one warp per leaf
     const unsigned blocks = (unsigned)((n_leaves * 32 + P2P_TH - 1) / P2P_TH);
-    k_p2p<R><<<blocks, P2P_TH, 0, s>>>(leaf_first, n_leaves, src4, tgt, tstride, src_start, src_end,
-                                        tgt_start, tgt_end, near_cnt, near_src, ctr, phi_near);
+    k_p2p<R><<<blocks, P2P_TH, 0, s>>>(leaf_first, n_leaves, leaf_ids, src4, tgt, tstride,
+                                        src_start, src_end, tgt_start, tgt_end, near_cnt, near_off,
+                                        near_src, ctr, phi_near);
   }
   return cudaGetLastError();
 }
 
-template cudaError_t launch_p2p<float>(int64_t, int64_t, const float *, const float *, int,
+template cudaError_t launch_p2p<float>(int64_t, int64_t, const int *, const float *,
+                                       const float *, int, const int *, const int *, const int *,
                                        const int *, const int *, const int *, const int *,
-                                       const int *, const int *, const double2 *, double *,
-                                       double, cudaStream_t);
-template cudaError_t launch_p2p<double>(int64_t, int64_t, const double *, const double *, int,
+                                       const double2 *, double *, double, cudaStream_t);
+template cudaError_t launch_p2p<double>(int64_t, int64_t, const int *, const double *,
+                                        const double *, int, const int *, const int *, const int *,
                                         const int *, const int *, const int *, const int *,
-                                        const int *, const int *, const double2 *, double *,
-                                        double, cudaStream_t);
+                                        const double2 *, double *, double, cudaStream_t);
 
 }  // namespace fmm2d

@@ -92,6 +92,16 @@ struct Plan {
   DBuf d_far_full, d_cls_cnt, d_cls_cells, d_tc_ops, d_dev_err;
   int tc_K = 0, tc_N = 0, n_sms = 148;
   int64_t cls_cap = 1;
+  // adaptive tree (FMM2D_ADAPTIVE): cells split while they hold more than
+  // leaf_cap sources or targets; U / W / X lists in CSR form by target
+  int leaf_cap = 64;
+  int64_t n_leaves_ad = 0, n_u = 0, n_w = 0, n_x = 0;
+  DBuf d_cell_lev, d_parent, d_child_first, d_child_cnt, d_split;
+  DBuf d_leaf_ids, d_leaf_pos, d_ad_scale, d_ad_inv_scale;
+  DBuf d_u_off, d_u_src, d_w_off, d_w_src, d_x_off, d_x_src;
+  DBuf d_ad_flag, d_ad_pos, d_ad_crange, d_ad_cnt, d_ad_off, d_ad_tot;
+  DBuf d_ad_ta, d_ad_tc, d_ad_sa, d_ad_sc, d_ad_ta2, d_ad_tc2, d_ad_sa2, d_ad_sc2;
+  DBuf d_ad_ut, d_ad_us, d_ad_wt, d_ad_ws, d_ad_xt, d_ad_xs;
   // parameters the cached geometry / operator tables were built for
   bool geo_valid = false;
   int geo_key_L = -1, geo_key_p = -1;
@@ -141,11 +151,77 @@ cudaError_t launch_lists(const Geo &g, const Stencils *d_sten, int lo_level, int
                          int *far_full, int *cls_cnt, int *cls_cells, int64_t cls_cap,
                          cudaStream_t s);
 
+// ---------------------------------------------------------------- adaptive.cu
+// Cell arrays of the adaptive tree (one array over all levels, ordered by
+// (level, key)); ts/te alias ss/se when sources and targets are one set.
+struct AdCells {
+  uint32_t *key;
+  uint8_t *lev;
+  int *parent, *child_first;
+  uint8_t *child_cnt, *split;
+  int *ss, *se, *ts, *te;
+  int4 *crd;
+  double2 *ctr;
+  uint8_t *cls, *hsrc;
+};
+cudaError_t ad_launch_root(const Geo &g, int64_t n_s, int64_t n_t, const AdCells &c, cudaStream_t s);
+cudaError_t ad_launch_split(const Geo &g, int l, int64_t first, int64_t count, int cap,
+                            const uint32_t *skey, const uint32_t *tkey, const AdCells &c, int *flag,
+                            int4 *crange, cudaStream_t s);
+cudaError_t ad_launch_level_total(int64_t count_b, const int *flag, const int *pos, int *total_out,
+                                  cudaStream_t s);
+cudaError_t ad_launch_emit(const Geo &g, int l, int64_t first, int64_t count, int64_t next_first,
+                           const int *flag, const int *pos, const int4 *crange, const AdCells &c,
+                           cudaStream_t s);
+cudaError_t ad_launch_leaves(int64_t n_cells, const uint8_t *split, int *flag, int *pos,
+                             void *scan_scratch, int *leaf_ids, int *leaf_pos, int *n_leaves_out,
+                             cudaStream_t s);
+cudaError_t ad_launch_rel(bool f32_in, bool f32_out, const void *xy, const uint32_t *perm,
+                          int64_t n_leaves, const int *leaf_ids, const int *start, const int *end,
+                          const double2 *ctr, void *out, int stride, cudaStream_t s);
+// count pass of one level's traversal; totals[5] = U, W, X, next W tests, next X tests
+cudaError_t ad_launch_lists(const Geo &g, const Stencils *d_sten, int l, int l_min, int64_t first,
+                            int64_t count, int64_t n_t, int64_t n_s, const int *t_a, const int *t_c,
+                            const int *s_a, const int *s_c, const AdCells &c, int *cnt,
+                            int *off, void *scan_scratch, int *totals, cudaStream_t s);
+cudaError_t ad_launch_lists_emit(const Geo &g, const Stencils *d_sten, int l, int l_min,
+                                 int64_t first, int64_t count, int64_t n_t, int64_t n_s,
+                                 const int *t_a, const int *t_c, const int *s_a, const int *s_c,
+                                 const AdCells &c, const int *off, const int64_t base[5],
+                                 int *u_t, int *u_s, int *w_t, int *w_s, int *x_t, int *x_s,
+                                 int *nt_a, int *nt_c, int *ns_a, int *ns_c, int64_t far_first,
+                                 int *far_cnt, int *far_src, uint16_t *far_op, int *far_full,
+                                 int *cls_cnt, int *cls_cells, int64_t cls_cap, cudaStream_t s);
+// Stable grouping of n (target, source) pairs by target (map[target] when map
+// is given): CSR offsets off[0..n_groups] and the sources in group order.
+cudaError_t ad_group(int64_t n, const int *tgt, const int *src, const int *map, int n_groups,
+                     uint32_t *key, uint32_t *idx, uint32_t *tmp_k, uint32_t *tmp_v, void *scratch,
+                     int *cnt, int *off, int *out_src, cudaStream_t s);
+template <typename R>
+cudaError_t ad_launch_m2p(int64_t n_leaves, const int *leaf_ids, const int *w_off, const int *w_src,
+                          const R *tgt, int tstride, const int *ts, const int *te,
+                          const double2 *ctr, const uint8_t *lev, const double2 *scale, int p,
+                          int P, const double *mQ, const Cx<R> *ma, double *phi, cudaStream_t s);
+template <typename R>
+cudaError_t ad_launch_p2l(int64_t n_cells, const int *x_off, const int *x_src, const R *src4,
+                          const int *ss, const int *se, const double2 *ctr, const uint8_t *lev,
+                          const double2 *inv_scale, int p, int P, double *lL0, Cx<R> *lb,
+                          cudaStream_t s);
+
 // ---------------------------------------------------------------- expand.cu
 struct ExpandArgs {
   int p, P, L, l_min, b;
   int64_t leaf_first, n_leaves;
   double inv_s_re, inv_s_im;          // 1 / s_L
+  // adaptive tree (null for the uniform one): leaf li is cell leaf_ids[li],
+  // of level cell_lev[...], whose inverse scale is inv_scale[level]
+  const int *leaf_ids = nullptr;
+  const uint8_t *cell_lev = nullptr;
+  const double2 *inv_scale = nullptr;
+  // adaptive tree: children of a split cell are contiguous, parents explicit
+  const int *child_first = nullptr;
+  const uint8_t *child_cnt = nullptr;
+  const int *parent = nullptr;
 };
 template <typename R>
 cudaError_t launch_gather_u(const void *u, bool f32_in, const uint32_t *perm, int64_t n, R *src4,
@@ -198,11 +274,14 @@ void tc_build_tables(const std::vector<double> &m2l_re, const std::vector<double
 cudaError_t launch_m2l_tc(const TcArgs &a, int K, int N, int64_t n_far_cells, cudaStream_t s);
 
 // ---------------------------------------------------------------- p2p.cu
+// leaf_ids: null (leaves leaf_first + li) or the cell of leaf li; near lists
+// fixed-stride (near_off null: near_cnt[li], near_src[li * NEAR_MAX + e]) or
+// CSR (near_src[near_off[li] .. near_off[li + 1])).
 template <typename R>
-cudaError_t launch_p2p(int64_t leaf_first, int64_t n_leaves, const R *src4, const R *tgt,
-                       int tstride, const int *src_start, const int *src_end,
+cudaError_t launch_p2p(int64_t leaf_first, int64_t n_leaves, const int *leaf_ids, const R *src4,
+                       const R *tgt, int tstride, const int *src_start, const int *src_end,
                        const int *tgt_start, const int *tgt_end, const int *near_cnt,
-                       const int *near_src, const double2 *ctr, double *phi_near,
-                       double mean_targets, cudaStream_t s);
+                       const int *near_off, const int *near_src, const double2 *ctr,
+                       double *phi_near, double mean_targets, cudaStream_t s);
 
 }  // namespace fmm2d

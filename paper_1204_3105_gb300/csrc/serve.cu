@@ -128,9 +128,10 @@ fmm2d_status run_job(Slot &sl, Job &j) {
   int p = r.p;
   if (p == 0) fmm2d_default_params(r.tiling, std::max(r.n_src, nt), 64, r.eps, nullptr, &p, nullptr);
   const unsigned prec = (r.flags & FMM2D_PREC_MASK) ? (r.flags & FMM2D_PREC_MASK) : precision_for(r.eps, p);
-  const unsigned flags = prec | (r.flags & FMM2D_IN_F32);
+  const unsigned flags = prec | (r.flags & (FMM2D_IN_F32 | FMM2D_ADAPTIVE));
   int L = r.levels;
-  if (L == 0) fmm2d_default_params(r.tiling, std::max(r.n_src, nt), 64, r.eps, &L, nullptr, nullptr);
+  if (L == 0 && !(flags & FMM2D_ADAPTIVE))
+    fmm2d_default_params(r.tiling, std::max(r.n_src, nt), 64, r.eps, &L, nullptr, nullptr);
   auto key = std::make_tuple(r.tiling, flags, L, p);
   fmm2d_plan *pl = sl.plans[key];
   fmm2d_status st;

@@ -8,19 +8,12 @@
 // offsets (the offsets of Neighbors and of NeighborsE4 = Children[Parent(n)
 // u Neighbors(Parent(n))] minus {n} u Neighbors(n), eq. 3), looked up in the
 // map; only cells holding sources enter a list.
+#include "cells.cuh"
 #include "plan.h"
 
 namespace fmm2d {
 
 namespace {
-
-__device__ __forceinline__ uint32_t parent_key(int tiling, uint32_t key, int up_levels) {
-  if (tiling == FMM2D_SEPT) {
-    for (int i = 0; i < up_levels; ++i) key /= 7u;
-    return key;
-  }
-  return key >> (2 * up_levels);
-}
 
 __global__ void k_mark(Geo g, const uint32_t *__restrict__ key, int64_t n, int *__restrict__ occ,
                        int *__restrict__ hsrc) {
@@ -62,44 +55,12 @@ __global__ void k_compact(Geo g, const int *__restrict__ occ, const int *__restr
   src_start[slot] = src_end[slot] = 0;   // leaf ranges are filled in later
   if (tgt_start) tgt_start[slot] = tgt_end[slot] = 0;
   cell_hsrc[slot] = (uint8_t)(hsrc[m] != 0);
-  int4 crd = make_int4(0, 0, 0, 0);
-  double X, Y;    // centre in the tiling frame
-  uint8_t cls = 0;
-  if (g.tiling == FMM2D_QUAD) {
-    int i = (int)compact_bits(key), j = (int)compact_bits(key >> 1);
-    crd = make_int4(i, j, 0, 0);
-    double h = ldexp(1.0, -l);
-    X = (i + 0.5) * h;
-    Y = (j + 0.5) * h;
-    cls = (uint8_t)(key & 3u);
-  } else if (g.tiling == FMM2D_SEPT) {
-    int64_t a, b;
-    key_to_eis(key, l, &a, &b);
-    crd = make_int4((int)a, (int)b, 0, 0);
-    // frame centre g_l (a + b w), w = e^{i pi/3}
-    double er = (double)a + 0.5 * (double)b, ei = 0.8660254037844386 * (double)b;
-    X = g.unit_re[l] * er - g.unit_im[l] * ei;
-    Y = g.unit_re[l] * ei + g.unit_im[l] * er;
-    cls = (uint8_t)(key % 7u);
-  } else {
-    int i, j, k;
-    tri_key_to_coords(key, l, &i, &j, &k);
-    bool up = tri_up(i, j, k, l);
-    crd = make_int4(i, j, k, up ? 1 : 0);
-    double o = up ? 1.0 : 2.0, rho0 = g.leaf_scale, inv = ldexp(1.0, -l);
-    Y = rho0 * (3.0 * i + o) * inv - rho0;
-    X = 1.7320508075688772 * rho0 * (double)(k - j) * inv;
-    if (l > 0) {
-      bool pup = tri_up(i >> 1, j >> 1, k >> 1, l - 1);
-      cls = (uint8_t)((key & 3u) + (pup ? 0u : 4u));
-    }
-  }
-  if (g.tiling != FMM2D_QUAD) {
-    X += 0.5;
-    Y += 0.5;
-  }
+  int4 crd;
+  double2 ctr;
+  uint8_t cls;
+  cell_geometry(g, l, key, &crd, &ctr, &cls);
   cell_crd[slot] = crd;
-  cell_ctr[slot] = make_double2(g.x0 + g.S * X, g.y0 + g.S * Y);
+  cell_ctr[slot] = ctr;
   cell_cls[slot] = cls;
 }
 
@@ -135,18 +96,6 @@ __global__ void k_rel(Geo g, const TI *__restrict__ xy, const uint32_t *__restri
   dst[0] = (TO)(x - c.x);
   dst[1] = (TO)(y - c.y);
   for (int q = 2; q < stride; ++q) dst[q] = (TO)0;
-}
-
-// Key of the level-l cell at lattice coordinates c, or false if none.
-__device__ __forceinline__ bool cell_at(const Geo &g, int l, int4 c, uint32_t *key) {
-  if (g.tiling == FMM2D_QUAD) {
-    int n = 1 << l;
-    if (c.x < 0 || c.y < 0 || c.x >= n || c.y >= n) return false;
-    *key = morton((uint32_t)c.x, (uint32_t)c.y);
-    return true;
-  }
-  if (g.tiling == FMM2D_SEPT) return eis_to_key(c.x, c.y, l, key);
-  return tri_coords_to_key(c.x, c.y, c.z, l, key);
 }
 
 __global__ void k_lists(Geo g, const Stencils *__restrict__ st, int lo_level, int l_min,

@@ -19,20 +19,23 @@ QUAD, SEPT, TRI = 0, 1, 2
 TILINGS = {"quad": QUAD, "sept": SEPT, "tri": TRI}
 PREC_FP64, PREC_MIXED, PREC_MIXED_TC = 0x0, 0x1, 0x2
 IN_F32 = 0x10
+ADAPTIVE = 0x20
 
 OK, EINVAL, ENOMEM, EDOMAIN, ECUDA, EBUSY, ETIMEOUT, ENOTREADY = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "EDOMAIN", "ECUDA", "EBUSY", "ETIMEOUT", "ENOTREADY"]
 STAGES = ["keys", "sort", "tree", "lists", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "other"]
 
 EXPORTS = {"src_keys": 1, "src_perm": 2, "tgt_keys": 3, "tgt_perm": 4, "cells": 5, "near": 6,
-           "far": 7, "multipoles": 8, "locals": 9, "phi_near": 10, "phi_far": 11, "centers": 12}
+           "far": 7, "multipoles": 8, "locals": 9, "phi_near": 10, "phi_far": 11, "centers": 12,
+           "ad_cells": 13, "ad_u": 14, "ad_w": 15, "ad_x": 16, "ad_v": 17}
 
 SYMBOLS = ["fmm2d_default_params", "fmm2d_plan_create", "fmm2d_plan_set_domain", "fmm2d_build",
            "fmm2d_evaluate", "fmm2d_plan_query", "fmm2d_debug_export", "fmm2d_plan_set_profiling",
            "fmm2d_stage_times", "fmm2d_plan_destroy", "fmm2d_last_error",
            "fmm2d_keys_sort_noalloc", "fmm2d_autotune", "fmm2d_measure_alu_peaks",
            "fmm2d_plan_set_params", "fmm2d_serve_create", "fmm2d_serve_submit", "fmm2d_serve_poll",
-           "fmm2d_serve_wait", "fmm2d_serve_stats", "fmm2d_serve_destroy"]
+           "fmm2d_serve_wait", "fmm2d_serve_stats", "fmm2d_serve_destroy",
+           "fmm2d_plan_set_leaf_size"]
 
 
 class Info(ctypes.Structure):
@@ -108,6 +111,7 @@ def lib():
                                  ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
     L.fmm2d_measure_alu_peaks.argtypes = [ctypes.POINTER(dbl)]
     L.fmm2d_plan_set_params.argtypes = [vp, c_int, c_int, dbl]
+    L.fmm2d_plan_set_leaf_size.argtypes = [vp, c_int]
     L.fmm2d_serve_create.argtypes = [ctypes.c_size_t, c_int, ctypes.POINTER(vp)]
     L.fmm2d_serve_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
     L.fmm2d_serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(Result)]
@@ -201,6 +205,11 @@ class Plan:
         if st:
             raise FMM2DError(st, "%s: %s" % (what, self.lib.fmm2d_last_error(self._h).decode()))
 
+    def fmm2d_plan_set_leaf_size(self, leaf_size):
+        self._check(self.lib.fmm2d_plan_set_leaf_size(self._h, int(leaf_size)), "set_leaf_size")
+
+    set_leaf_size = fmm2d_plan_set_leaf_size
+
     def fmm2d_plan_set_domain(self, x0, y0, size):
         self._check(self.lib.fmm2d_plan_set_domain(self._h, float(x0), float(y0), float(size)),
                     "set_domain")
@@ -247,6 +256,10 @@ class Plan:
             return buf.view(np.complex128).reshape(-1, p + 1)
         if w == 12:
             return buf.view(np.complex128)
+        if w == 13:
+            return buf.view(np.int64).reshape(-1, 3)
+        if w in (14, 15, 16, 17):
+            return buf.view(np.int64).reshape(-1, 4)
         return buf.view(np.float64)
 
     export = fmm2d_debug_export

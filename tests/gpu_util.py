@@ -13,7 +13,7 @@ def _torch():
 
 
 def run_gpu(tiling, src, u, tgt=None, levels=0, p=0, eps=1e-6, prec="mixed", f32=False,
-            domain=None, keep=False):
+            domain=None, keep=False, leaf_size=None):
     """Build + evaluate through the C ABI on cuda:0; returns (phi, plan)."""
     from paper_1204_3105_gb300 import fmm2d
 
@@ -23,7 +23,11 @@ def run_gpu(tiling, src, u, tgt=None, levels=0, p=0, eps=1e-6, prec="mixed", f32
     dt = np.float32 if f32 else np.float64
     if f32:
         flags |= fmm2d.IN_F32
+    if leaf_size is not None:      # adaptive tree
+        flags |= fmm2d.ADAPTIVE
     plan = fmm2d.Plan(tiling, levels=levels, p=p, eps=eps, flags=flags)
+    if leaf_size is not None:
+        plan.set_leaf_size(leaf_size)
     if domain is not None:
         plan.set_domain(*domain)
     s_d = t.from_numpy(np.ascontiguousarray(src, dt)).to(dev)
