@@ -394,6 +394,23 @@ void flush_events(fmm2d_plan *pl) {
   pl->ev_used = 0;
 }
 
+// The plan's far-field stream (highest priority) and its fork / join events.
+static cudaError_t far_stream(fmm2d_plan *pl, cudaStream_t *out) {
+  if (!pl->far_stream) {
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamCreateWithPriority(&pl->far_stream, cudaStreamNonBlocking, hi);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  *out = pl->far_stream;
+  return cudaSuccess;
+}
+
 // Geometry, stencils and operator tables for the current (tiling, L, p).
 // Skipped when the plan already holds them for the same parameters.
 fmm2d_status setup_geometry(fmm2d_plan *pl) {
@@ -535,23 +552,28 @@ fmm2d_status evaluate_t(fmm2d_plan *pl, const void *u, double *out, cudaStream_t
     StageScope sc(pl, ST_OTHER, s, 1);
     CK(launch_gather_u<R>(u, f32_in, (const uint32_t *)pl->d_perm_s.p, pl->n_src, src4, s), "gather");
   }
+  // fork: the far-field chain on the plan's high-priority stream f, P2P on s
+  cudaStream_t f;
+  CK(far_stream(pl, &f), "far stream");
+  CK(cudaEventRecord(pl->ev_fork, s), "fork");
+  CK(cudaStreamWaitEvent(f, pl->ev_fork, 0), "fork");
   {
-    StageScope sc(pl, ST_P2M, s, 1);
-    CK(launch_p2m<R>(a, src4, (const int *)pl->d_src_start.p, (const int *)pl->d_src_end.p, mQ, ma, s), "p2m");
+    StageScope sc(pl, ST_P2M, f, 1);
+    CK(launch_p2m<R>(a, src4, (const int *)pl->d_src_start.p, (const int *)pl->d_src_end.p, mQ, ma, f), "p2m");
   }
   {
-    StageScope sc(pl, ST_M2M, s, std::max(0, L - pl->l_min));
+    StageScope sc(pl, ST_M2M, f, std::max(0, L - pl->l_min));
     for (int l = L - 1; l >= pl->l_min; --l)
       CK(launch_m2m<R>(a, pl->geo, l, pl->lev_first[l], pl->lev_count[l], (const int *)pl->d_map.p,
                        (const uint32_t *)pl->d_cell_key.p, (const uint8_t *)pl->d_cell_cls.p,
-                       (const uint8_t *)pl->d_cell_hsrc.p, (const Cx<R> *)pl->d_m2m_ops.p, mQ, ma, s),
+                       (const uint8_t *)pl->d_cell_hsrc.p, (const Cx<R> *)pl->d_m2m_ops.p, mQ, ma, f),
          "m2m");
   }
   if (L < pl->l_min) {
-    CK(cudaMemsetAsync(lL0, 0, pl->n_cells * sizeof(double), s), "zero locals");
-    CK(cudaMemsetAsync(lb, 0, pl->n_cells * pl->P * sizeof(Cx<R>), s), "zero locals");
+    CK(cudaMemsetAsync(lL0, 0, pl->n_cells * sizeof(double), f), "zero locals");
+    CK(cudaMemsetAsync(lb, 0, pl->n_cells * pl->P * sizeof(Cx<R>), f), "zero locals");
   } else if ((pl->flags & FMM2D_PREC_MASK) == FMM2D_PREC_MIXED_TC) {
-    StageScope sc(pl, ST_M2L, s, 1);
+    StageScope sc(pl, ST_M2L, f, 1);
     TcArgs t;
     t.p = pl->p;
     t.P = pl->P;
@@ -575,22 +597,22 @@ fmm2d_status evaluate_t(fmm2d_plan *pl, const void *u, double *out, cudaStream_t
     t.lL0 = lL0;
     t.lb = (float2 *)lb;
     t.err = (int *)pl->d_dev_err.p;
-    CK(launch_m2l_tc(t, pl->tc_K, pl->tc_N, pl->n_far_cells, s), "m2l_tc");
+    CK(launch_m2l_tc(t, pl->tc_K, pl->tc_N, pl->n_far_cells, f), "m2l_tc");
   } else {
-    StageScope sc(pl, ST_M2L, s, 1);
+    StageScope sc(pl, ST_M2L, f, 1);
     CK(launch_m2l<R>(a, pl->lev_first[pl->l_min], pl->n_far_cells, (const int64_t *)pl->d_lev_first.p,
                      (const double *)pl->d_geo_scale.p, 0, (const int *)pl->d_far_cnt.p,
                      (const int *)pl->d_far_src.p, (const uint16_t *)pl->d_far_op.p,
                      (const Cx<R> *)pl->d_m2l_ops.p, (const double *)pl->d_m2l_logz.p, mQ, ma, lL0,
-                     lb, s),
+                     lb, f),
        "m2l");
   }
   {
-    StageScope sc(pl, ST_L2L, s, std::max(0, L - pl->l_min));
+    StageScope sc(pl, ST_L2L, f, std::max(0, L - pl->l_min));
     for (int l = pl->l_min + 1; l <= L; ++l)
       CK(launch_l2l<R>(a, pl->geo, l, pl->lev_first[l], pl->lev_count[l], (const int *)pl->d_map.p,
                        (const uint32_t *)pl->d_cell_key.p, (const uint8_t *)pl->d_cell_cls.p,
-                       (const Cx<R> *)pl->d_l2l_ops.p, lL0, lb, s),
+                       (const Cx<R> *)pl->d_l2l_ops.p, lL0, lb, f),
          "l2l");
   }
   {
@@ -603,6 +625,8 @@ fmm2d_status evaluate_t(fmm2d_plan *pl, const void *u, double *out, cudaStream_t
                      a.n_leaves > 0 ? (double)pl->n_tgt / (double)a.n_leaves : 0.0, s),
        "p2p");
   }
+  CK(cudaEventRecord(pl->ev_join, f), "join");   // join: L2P needs the locals
+  CK(cudaStreamWaitEvent(s, pl->ev_join, 0), "join");
   {
     StageScope sc(pl, ST_L2P, s, 1);
     CK(launch_l2p<R>(a, tgt, tstride, tst, ten, tperm, lL0, lb, (const double *)pl->d_phi_near.p,
@@ -678,8 +702,11 @@ static fmm2d_status build_adaptive(fmm2d_plan *pl, const void *src, int64_t n_sr
   uint32_t *kt = (uint32_t *)pl->d_key_t.p, *pt = (uint32_t *)pl->d_perm_t.p;
   {
     StageScope sc(pl, ST_KEYS, s, pl->same_sets ? 1 : 2);
-    CK(launch_keys(g, src, f32, n_src, ks, ps, (int *)pl->d_err.p, s), "keys");
-    if (!pl->same_sets) CK(launch_keys(g, tgt, f32, n_tgt, kt, pt, (int *)pl->d_err.p, s), "keys");
+    CK(launch_keys(g, src, f32, n_src, ks, ps, (int *)pl->d_err.p, s, (uint32_t *)pl->d_tmp_v.p,
+                   (int *)pl->d_err.p + 2), "keys");
+    if (!pl->same_sets)
+      CK(launch_keys(g, tgt, f32, n_tgt, kt, pt, (int *)pl->d_err.p, s, (uint32_t *)pl->d_tmp_v.p,
+                     (int *)pl->d_err.p + 2), "keys");
   }
   {
     StageScope sc(pl, ST_SORT, s, 1);
@@ -933,22 +960,26 @@ fmm2d_status evaluate_adaptive_t(fmm2d_plan *pl, const void *u, double *out, cud
     StageScope sc(pl, ST_OTHER, s, 1);
     CK(launch_gather_u<R>(u, f32_in, (const uint32_t *)pl->d_perm_s.p, pl->n_src, src4, s), "gather");
   }
+  cudaStream_t f;   // far-field chain on the plan's stream, P2P on s
+  CK(far_stream(pl, &f), "far stream");
+  CK(cudaEventRecord(pl->ev_fork, s), "fork");
+  CK(cudaStreamWaitEvent(f, pl->ev_fork, 0), "fork");
   {
-    StageScope sc(pl, ST_P2M, s, 1);
-    CK(launch_p2m<R>(a, src4, c.ss, c.se, mQ, ma, s), "p2m");
+    StageScope sc(pl, ST_P2M, f, 1);
+    CK(launch_p2m<R>(a, src4, c.ss, c.se, mQ, ma, f), "p2m");
   }
   {
-    StageScope sc(pl, ST_M2M, s, std::max(0, depth - 1));
+    StageScope sc(pl, ST_M2M, f, std::max(0, depth - 1));
     for (int l = depth - 1; l >= 1; --l)
       CK(launch_m2m<R>(a, pl->geo, l, pl->lev_first[l], pl->lev_count[l], nullptr, c.key, c.cls,
-                       c.hsrc, (const Cx<R> *)pl->d_m2m_ops.p, mQ, ma, s), "m2m");
+                       c.hsrc, (const Cx<R> *)pl->d_m2m_ops.p, mQ, ma, f), "m2m");
   }
   if (pl->n_far_cells == 0) {
-    CK(cudaMemsetAsync(lL0, 0, pl->n_cells * sizeof(double), s), "zero locals");
-    CK(cudaMemsetAsync(lb, 0, pl->n_cells * pl->P * sizeof(Cx<R>), s), "zero locals");
+    CK(cudaMemsetAsync(lL0, 0, pl->n_cells * sizeof(double), f), "zero locals");
+    CK(cudaMemsetAsync(lb, 0, pl->n_cells * pl->P * sizeof(Cx<R>), f), "zero locals");
   } else if constexpr (sizeof(R) == 4) {
     if ((pl->flags & FMM2D_PREC_MASK) == FMM2D_PREC_MIXED_TC) {
-      StageScope sc(pl, ST_M2L, s, 1);
+      StageScope sc(pl, ST_M2L, f, 1);
       TcArgs t;
       t.p = pl->p;
       t.P = pl->P;
@@ -972,44 +1003,49 @@ fmm2d_status evaluate_adaptive_t(fmm2d_plan *pl, const void *u, double *out, cud
       t.lL0 = lL0;
       t.lb = (float2 *)lb;
       t.err = (int *)pl->d_dev_err.p;
-      CK(launch_m2l_tc(t, pl->tc_K, pl->tc_N, pl->n_far_cells, s), "m2l_tc");
+      CK(launch_m2l_tc(t, pl->tc_K, pl->tc_N, pl->n_far_cells, f), "m2l_tc");
     } else {
-      StageScope sc(pl, ST_M2L, s, 1);
+      StageScope sc(pl, ST_M2L, f, 1);
       const int64_t ff = pl->n_cells - pl->n_far_cells;
       CK(launch_m2l<R>(a, ff, pl->n_far_cells, (const int64_t *)pl->d_lev_first.p,
                        (const double *)pl->d_geo_scale.p, 0, (const int *)pl->d_far_cnt.p,
                        (const int *)pl->d_far_src.p, (const uint16_t *)pl->d_far_op.p,
                        (const Cx<R> *)pl->d_m2l_ops.p, (const double *)pl->d_m2l_logz.p, mQ, ma,
-                       lL0, lb, s), "m2l");
+                       lL0, lb, f), "m2l");
     }
   } else {
-    StageScope sc(pl, ST_M2L, s, 1);
+    StageScope sc(pl, ST_M2L, f, 1);
     const int64_t ff = pl->n_cells - pl->n_far_cells;
     CK(launch_m2l<R>(a, ff, pl->n_far_cells, (const int64_t *)pl->d_lev_first.p,
                      (const double *)pl->d_geo_scale.p, 0, (const int *)pl->d_far_cnt.p,
                      (const int *)pl->d_far_src.p, (const uint16_t *)pl->d_far_op.p,
                      (const Cx<R> *)pl->d_m2l_ops.p, (const double *)pl->d_m2l_logz.p, mQ, ma, lL0,
-                     lb, s), "m2l");
+                     lb, f), "m2l");
   }
   {
-    StageScope sc(pl, ST_M2L, s, 1);   // P2L (X lists) completes the locals before L2L
+    StageScope sc(pl, ST_M2L, f, 1);   // P2L (X lists) completes the locals before L2L
     CK(ad_launch_p2l<R>(pl->n_cells, (const int *)pl->d_x_off.p, (const int *)pl->d_x_src.p, src4,
                         c.ss, c.se, c.ctr, c.lev, (const double2 *)pl->d_ad_inv_scale.p, pl->p,
-                        pl->P, lL0, lb, s), "p2l");
+                        pl->P, lL0, lb, f), "p2l");
   }
   {
-    StageScope sc(pl, ST_L2L, s, std::max(0, depth - pl->l_min));
+    StageScope sc(pl, ST_L2L, f, std::max(0, depth - pl->l_min));
     for (int l = pl->l_min + 1; l <= depth; ++l)
       CK(launch_l2l<R>(a, pl->geo, l, pl->lev_first[l], pl->lev_count[l], nullptr, c.key, c.cls,
-                       (const Cx<R> *)pl->d_l2l_ops.p, lL0, lb, s), "l2l");
+                       (const Cx<R> *)pl->d_l2l_ops.p, lL0, lb, f), "l2l");
   }
   {
-    StageScope sc(pl, ST_P2P, s, 2);
+    StageScope sc(pl, ST_P2P, s, 1);
     CK(launch_p2p<R>(0, pl->n_leaves_ad, (const int *)pl->d_leaf_ids.p, src4, tgt, tstride, c.ss,
                      c.se, c.ts, c.te, nullptr, (const int *)pl->d_u_off.p,
                      (const int *)pl->d_u_src.p, c.ctr, (double *)pl->d_phi_near.p,
                      pl->n_leaves_ad > 0 ? (double)pl->n_tgt / (double)pl->n_leaves_ad : 0.0, s),
        "p2p");
+  }
+  CK(cudaEventRecord(pl->ev_join, f), "join");   // join: M2P and L2P need the expansions
+  CK(cudaStreamWaitEvent(s, pl->ev_join, 0), "join");
+  {
+    StageScope sc(pl, ST_P2P, s, 1);
     CK(ad_launch_m2p<R>(pl->n_leaves_ad, (const int *)pl->d_leaf_ids.p, (const int *)pl->d_w_off.p,
                         (const int *)pl->d_w_src.p, tgt, tstride, c.ts, c.te, c.ctr, c.lev,
                         (const double2 *)pl->d_ad_scale.p, pl->p, pl->P, mQ, ma,
@@ -1161,8 +1197,11 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
   uint32_t *kt = (uint32_t *)pl->d_key_t.p, *pt = (uint32_t *)pl->d_perm_t.p;
   {
     StageScope sc(pl, ST_KEYS, s, pl->same_sets ? 1 : 2);
-    CK(launch_keys(g, src, f32, n_src, ks, ps, (int *)pl->d_err.p, s), "keys");
-    if (!pl->same_sets) CK(launch_keys(g, tgt, f32, n_tgt, kt, pt, (int *)pl->d_err.p, s), "keys");
+    CK(launch_keys(g, src, f32, n_src, ks, ps, (int *)pl->d_err.p, s, (uint32_t *)pl->d_tmp_v.p,
+                   (int *)pl->d_err.p + 2), "keys");
+    if (!pl->same_sets)
+      CK(launch_keys(g, tgt, f32, n_tgt, kt, pt, (int *)pl->d_err.p, s, (uint32_t *)pl->d_tmp_v.p,
+                     (int *)pl->d_err.p + 2), "keys");
   }
   {
     const int per_pass = (int64_t)256 * ((std::max<int64_t>(1, nmax) + 4095) / 4096) <= 8192 ? 3 : 5;
@@ -1583,8 +1622,22 @@ void fmm2d_plan_destroy(fmm2d_plan *pl) {
                   &pl->d_tgt2, &pl->d_mQ, &pl->d_ma, &pl->d_lL0, &pl->d_lb, &pl->d_phi_near,
                   &pl->d_phi_far, &pl->d_sten, &pl->d_geo_scale, &pl->d_m2l_ops, &pl->d_m2l_logz,
                   &pl->d_m2m_ops, &pl->d_l2l_ops, &pl->d_counts, &pl->d_far_full,
-                  &pl->d_cls_cnt, &pl->d_cls_cells, &pl->d_tc_ops, &pl->d_dev_err};
+                  &pl->d_cls_cnt, &pl->d_cls_cells, &pl->d_tc_ops, &pl->d_dev_err,
+                  &pl->d_cell_lev, &pl->d_parent, &pl->d_child_first, &pl->d_child_cnt,
+                  &pl->d_split, &pl->d_leaf_ids, &pl->d_leaf_pos, &pl->d_ad_scale,
+                  &pl->d_ad_inv_scale, &pl->d_u_off, &pl->d_u_src, &pl->d_w_off, &pl->d_w_src,
+                  &pl->d_x_off, &pl->d_x_src, &pl->d_ad_flag, &pl->d_ad_pos, &pl->d_ad_crange,
+                  &pl->d_ad_cnt, &pl->d_ad_off, &pl->d_ad_tot, &pl->d_ad_ta, &pl->d_ad_tc,
+                  &pl->d_ad_sa, &pl->d_ad_sc, &pl->d_ad_ta2, &pl->d_ad_tc2, &pl->d_ad_sa2,
+                  &pl->d_ad_sc2, &pl->d_ad_ut, &pl->d_ad_us, &pl->d_ad_wt, &pl->d_ad_ws,
+                  &pl->d_ad_xt, &pl->d_ad_xs};
   for (DBuf *b : bufs) dbuf_free(*b);
+  if (pl->far_stream) {
+    cudaStreamSynchronize(pl->far_stream);
+    cudaStreamDestroy(pl->far_stream);
+  }
+  if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
+  if (pl->ev_join) cudaEventDestroy(pl->ev_join);
   delete pl;
 }
 

@@ -333,10 +333,21 @@ __device__ __forceinline__ void x2_slice(const float4 *sxy, const float2 *su, in
                                          const float2 &ycd, float (&s)[4], float (&c)[4]) {
   int q = q0;
   while (q < q1) {
+    // two accumulator sets (even / odd sources) halve the loop-carried FFMA chain
     float2 acc_ab = make_float2(0.f, 0.f), acc_cd = make_float2(0.f, 0.f);
+    float2 acc_ab1 = make_float2(0.f, 0.f), acc_cd1 = make_float2(0.f, 0.f);
     const int qe = min(q1, q + 64 * K);
-#pragma unroll 4
-    for (; q < qe; q += K) x2_source<CHECK>(sxy[q], su[q], xab, xcd, yab, ycd, acc_ab, acc_cd);
+#pragma unroll 2
+    for (; q + K < qe; q += 2 * K) {
+      x2_source<CHECK>(sxy[q], su[q], xab, xcd, yab, ycd, acc_ab, acc_cd);
+      x2_source<CHECK>(sxy[q + K], su[q + K], xab, xcd, yab, ycd, acc_ab1, acc_cd1);
+    }
+    if (q < qe) {
+      x2_source<CHECK>(sxy[q], su[q], xab, xcd, yab, ycd, acc_ab, acc_cd);
+      q += K;
+    }
+    acc_ab = __fadd2_rn(acc_ab, acc_ab1);
+    acc_cd = __fadd2_rn(acc_cd, acc_cd1);
     x2_kahan(s[0], c[0], acc_ab.x);
     x2_kahan(s[1], c[1], acc_ab.y);
     x2_kahan(s[2], c[2], acc_cd.x);
@@ -344,8 +355,8 @@ __device__ __forceinline__ void x2_slice(const float4 *sxy, const float2 *su, in
   }
 }
 
-template <int T>
-__global__ void __launch_bounds__(P2P_TH, 4)
+template <int T, bool CSR>
+__global__ void __launch_bounds__(P2P_TH, CSR ? 3 : 4)
 k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_ids,
          const float *__restrict__ src4, const float *__restrict__ tgt, int tstride,
          const int *__restrict__ sst, const int *__restrict__ sen, const int *__restrict__ tst,
@@ -367,9 +378,9 @@ k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_ids,
   // source leaves: a fixed-stride Near list (uniform tree) or a CSR list of
   // any length (adaptive tree), taken in batches of at most NEAR_MAX leaves;
   // the target's own leaf, when it holds sources, comes first
-  const int n_all = near_off ? near_off[li + 1] - near_off[li] : near_cnt[li];
-  const int *nall = near_off ? near_src + near_off[li] : near_src + li * NEAR_MAX;
-  const bool single = n_all <= NEAR_MAX;
+  const int n_all = CSR ? near_off[li + 1] - near_off[li] : near_cnt[li];
+  const int *nall = CSR ? near_src + near_off[li] : near_src + li * NEAR_MAX;
+  const bool single = !CSR || n_all <= NEAR_MAX;
   float4 *sxy = s_xy + grp * CAP;
   float2 *su = s_u + grp * CAP;
   const float4 *src = reinterpret_cast<const float4 *>(src4);
@@ -498,9 +509,18 @@ cudaError_t launch_p2p(int64_t leaf_first, int64_t n_leaves, const int *leaf_ids
     const int G = P2P_TH / T;
     const unsigned blocks = (unsigned)((n_leaves + G - 1) / G);
 #define X2_LAUNCH(TT)                                                                             \
-  k_p2p_x2<TT><<<blocks, P2P_TH, 0, s>>>(leaf_first, n_leaves, leaf_ids, src4, tgt, tstride,       \
-                                         src_start, src_end, tgt_start, tgt_end, near_cnt,        \
-                                         near_off, near_src, ctr, phi_near)
+  do {                                                                                            \
+    if (near_off)                                                                                 \
+      k_p2p_x2<TT, true><<<blocks, P2P_TH, 0, s>>>(leaf_first, n_leaves, leaf_ids, src4, tgt,     \
+                                                   tstride, src_start, src_end, tgt_start,        \
+                                                   tgt_end, near_cnt, near_off, near_src, ctr,    \
+                                                   phi_near);                                     \
+    else                                                                                          \
+      k_p2p_x2<TT, false><<<blocks, P2P_TH, 0, s>>>(leaf_first, n_leaves, leaf_ids, src4, tgt,    \
+                                                    tstride, src_start, src_end, tgt_start,       \
+                                                    tgt_end, near_cnt, near_off, near_src, ctr,   \
+                                                    phi_near);                                    \
+  } while (0)
     if (T == 32) X2_LAUNCH(32);
     else if (T == 64) X2_LAUNCH(64);
     else if (T == 128) X2_LAUNCH(128);

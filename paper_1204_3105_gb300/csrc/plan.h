@@ -102,6 +102,10 @@ struct Plan {
   DBuf d_ad_flag, d_ad_pos, d_ad_crange, d_ad_cnt, d_ad_off, d_ad_tot;
   DBuf d_ad_ta, d_ad_tc, d_ad_sa, d_ad_sc, d_ad_ta2, d_ad_tc2, d_ad_sa2, d_ad_sc2;
   DBuf d_ad_ut, d_ad_us, d_ad_wt, d_ad_ws, d_ad_xt, d_ad_xs;
+  // the far-field chain (P2M ... L2L) runs on a high-priority plan stream
+  // while P2P runs on the caller's stream; two events fork and join them
+  cudaStream_t far_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // parameters the cached geometry / operator tables were built for
   bool geo_valid = false;
   int geo_key_L = -1, geo_key_p = -1;
@@ -114,8 +118,11 @@ cudaError_t dbuf_reserve(DBuf &b, size_t bytes);
 void dbuf_free(DBuf &b);
 
 // ---------------------------------------------------------------- keys.cu
+// list / list_n (optional, n entries + one counter): scratch for the FP32
+// filter; without them every point takes the exact FP64 front end.
 cudaError_t launch_keys(const Geo &g, const void *xy, bool f32, int64_t n, uint32_t *key,
-                        uint32_t *perm_iota, int *err, cudaStream_t s);
+                        uint32_t *perm_iota, int *err, cudaStream_t s, uint32_t *list = nullptr,
+                        int *list_n = nullptr);
 
 // ---------------------------------------------------------------- sort.cu
 size_t radix_sort_scratch_bytes(int64_t n);

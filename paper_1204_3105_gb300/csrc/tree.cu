@@ -98,6 +98,9 @@ __global__ void k_rel(Geo g, const TI *__restrict__ xy, const uint32_t *__restri
   for (int q = 2; q < stride; ++q) dst[q] = (TO)0;
 }
 
+// One warp per cell: lane e looks up stencil entry e (and e + 32), and a
+// ballot compacts the hits in stencil order, so the list is the same as a
+// sequential scan of the stencil would give.
 __global__ void k_lists(Geo g, const Stencils *__restrict__ st, int lo_level, int l_min,
                         const int *__restrict__ map, const uint8_t *__restrict__ cell_cls,
                         const int4 *__restrict__ cell_crd, const uint8_t *__restrict__ cell_hsrc,
@@ -106,9 +109,11 @@ __global__ void k_lists(Geo g, const Stencils *__restrict__ st, int lo_level, in
                         int *__restrict__ near_src, const int64_t *__restrict__ lev_first,
                         int *__restrict__ far_full, int *__restrict__ cls_cnt,
                         int *__restrict__ cls_cells, int64_t cls_cap) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
   const int64_t first = lev_first[lo_level];
-  const int64_t gslot = first + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (gslot >= lev_first[g.L + 1]) return;
+  const int64_t gslot = first + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  if (gslot >= lev_first[g.L + 1]) return;   // warp-uniform
   int l = lo_level;
   while (l < g.L && gslot >= lev_first[l + 1]) ++l;
   const int4 c = cell_crd[gslot];
@@ -116,42 +121,51 @@ __global__ void k_lists(Geo g, const Stencils *__restrict__ st, int lo_level, in
   const int64_t fi = gslot - first;
   const int n_far = l >= l_min ? st->far_len[cls] : 0;
   int cnt = 0;
-  for (int e = 0; e < n_far; ++e) {
-    int4 q = make_int4(c.x + st->far_d[cls][e][0], c.y + st->far_d[cls][e][1],
-                       c.z + st->far_d[cls][e][2], 0);
-    uint32_t k;
+  for (int e0 = 0; e0 < n_far; e0 += 32) {
+    const int e = e0 + lane;
     int s = -1;
-    if (cell_at(g, l, q, &k)) {
-      s = map[g.map_off[l] + k];
-      if (s >= 0 && !cell_hsrc[s]) s = -1;
+    if (e < n_far) {
+      const int4 q = make_int4(c.x + st->far_d[cls][e][0], c.y + st->far_d[cls][e][1],
+                               c.z + st->far_d[cls][e][2], 0);
+      uint32_t k;
+      if (cell_at(g, l, q, &k)) {
+        s = map[g.map_off[l] + k];
+        if (s >= 0 && !cell_hsrc[s]) s = -1;
+      }
+      if (far_full) far_full[fi * FAR_MAX + e] = s;
     }
-    if (far_full) far_full[fi * FAR_MAX + e] = s;
-    if (s < 0) continue;
-    far_src[fi * FAR_MAX + cnt] = s;
-    far_op[fi * FAR_MAX + cnt] = st->far_op[cls][e];
-    ++cnt;
+    const unsigned hit = __ballot_sync(0xffffffffu, s >= 0);
+    if (s >= 0) {
+      const int at = cnt + __popc(hit & lt);
+      far_src[fi * FAR_MAX + at] = s;
+      far_op[fi * FAR_MAX + at] = st->far_op[cls][e];
+    }
+    cnt += __popc(hit);
   }
-  far_cnt[fi] = cnt;
-  if (cls_cnt && n_far > 0) {
-    // group the M2L targets by stencil class for the tensor-core M2L
-    int pos = atomicAdd(&cls_cnt[cls], 1);
-    cls_cells[(int64_t)cls * cls_cap + pos] = (int)gslot;
+  if (lane == 0) {
+    far_cnt[fi] = cnt;
+    if (cls_cnt && n_far > 0) {
+      // group the M2L targets by stencil class for the tensor-core M2L
+      const int pos = atomicAdd(&cls_cnt[cls], 1);
+      cls_cells[(int64_t)cls * cls_cap + pos] = (int)gslot;
+    }
   }
   if (l == g.L) {
     const int o = (g.tiling == FMM2D_TRI && c.w == 0) ? 1 : 0;
     const int64_t ni = gslot - lev_first[g.L];
-    int nc = 0;
-    for (int e = 0; e < st->near_len[o]; ++e) {
-      int4 q = make_int4(c.x + st->near_d[o][e][0], c.y + st->near_d[o][e][1],
-                         c.z + st->near_d[o][e][2], 0);
+    int s = -1;
+    if (lane < st->near_len[o]) {
+      const int4 q = make_int4(c.x + st->near_d[o][lane][0], c.y + st->near_d[o][lane][1],
+                               c.z + st->near_d[o][lane][2], 0);
       uint32_t k;
-      if (!cell_at(g, l, q, &k)) continue;
-      int s = map[g.map_off[l] + k];
-      if (s < 0 || !cell_hsrc[s]) continue;
-      near_src[ni * NEAR_MAX + nc] = s;
-      ++nc;
+      if (cell_at(g, l, q, &k)) {
+        s = map[g.map_off[l] + k];
+        if (s >= 0 && !cell_hsrc[s]) s = -1;
+      }
     }
-    near_cnt[ni] = nc;
+    const unsigned hit = __ballot_sync(0xffffffffu, s >= 0);
+    if (s >= 0) near_src[ni * NEAR_MAX + __popc(hit & lt)] = s;
+    if (lane == 0) near_cnt[ni] = __popc(hit);
   }
 }
 
@@ -214,7 +228,7 @@ cudaError_t launch_lists(const Geo &g, const Stencils *d_sten, int lo_level, int
                          int *far_full, int *cls_cnt, int *cls_cells, int64_t cls_cap,
                          cudaStream_t s) {
   if (cap <= 0) return cudaSuccess;
-  k_lists<<<nblk(cap, 128), 128, 0, s>>>(g, d_sten, lo_level, l_min, map, cell_cls, cell_crd,
+  k_lists<<<nblk(cap * 32, 256), 256, 0, s>>>(g, d_sten, lo_level, l_min, map, cell_cls, cell_crd,
                                           cell_hsrc, far_cnt, far_src, far_op, near_cnt, near_src,
                                           lev_first_dev, far_full, cls_cnt, cls_cells, cls_cap);
   return cudaGetLastError();
