@@ -29,6 +29,11 @@ EPS = 1e-6
 TILINGS = ("quad", "sept", "tri")
 SEED = 2
 MUFU_PER_CLK_SM = 16      # lg2 results per clock per SM (MUFU pipe)
+# DRAM bytes (read + write) of one P2P launch on the 2^20-point quadtree
+# workload, from the ncu capture summarised in profiles/p2p_x2_quad_2p20.md
+# (the three tilings' launches each read the 2^20 sorted sources once:
+# 18.3-19.3 MB); set to None when the kernel changes after that capture
+P2P_TRAFFIC = 18315520     # bytes: dram__bytes_read.sum + dram__bytes_write.sum of one launch
 FP32_LANES_SM = 128       # FP32 FMA lanes per SM
 
 
@@ -123,6 +128,18 @@ def dist_setup(args):
     return None, rank, ws
 
 
+def replica_aggregate(dist, ms_local, units_per_rank, ws, device=None):
+    """Whole-job throughput of N replicas: the slowest rank's time (max over
+    ranks, one all_reduce) and units = every rank's units."""
+    ms = float(ms_local)
+    if dist is not None and ws > 1:
+        import torch
+        tm = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ms = float(tm.item())
+    return ms, ws * units_per_rank / (ms / 1e3)
+
+
 def run_reference(args):
     dist, rank, ws = dist_setup(args)
     if rank != 0:
@@ -212,21 +229,28 @@ def run_ours(args):
     if dist:
         dist.barrier()
     tt = {t: [a.elapsed_time(b) for a, b in per[t]] for t in args.tilings}
-    # one more step with per-stage events (kept out of the timed steps)
+    # stage split: a few more steps with per-stage CUDA events on the stream of
+    # each stage (far-field stages concurrent with P2P, as in the timed steps;
+    # kept out of the timed steps, whose host enqueue they would slow)
+    n_prof = 0 if args.no_profile else 5
     for t in args.tilings:
-        plans[t].set_profiling(not args.no_profile)
+        plans[t].set_profiling(0 if args.no_profile else 1)
+    for _ in range(n_prof):
+        step({t: [] for t in args.tilings})
+    torch.cuda.synchronize()
+    stage = {t: {k: (v[0] / max(1, n_prof), v[1] / max(1, n_prof))
+                 for k, v in plans[t].stage_times().items()} for t in args.tilings}
+    # one more step with the stages serialised: each stage's own time
+    for t in args.tilings:
+        plans[t].set_profiling(0 if args.no_profile else 2)
     step({t: [] for t in args.tilings})
     torch.cuda.synchronize()
-    stage = {t: plans[t].stage_times() for t in args.tilings}
+    stage_iso = {t: plans[t].stage_times() for t in args.tilings}
     for t in args.tilings:
-        plans[t].set_profiling(False)
+        plans[t].set_profiling(0)
     info = {t: plans[t].query() for t in args.tilings}
     ms_step = sum(statistics.mean(tt[t]) for t in args.tilings)
-    if dist:
-        tm = torch.tensor([ms_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        ms_step = float(tm.item())
-    value = ws * len(args.tilings) * N_POINTS / (ms_step / 1e3)
+    ms_step, value = replica_aggregate(dist, ms_step, len(args.tilings) * N_POINTS, ws, dev)
 
     # the plain FP64 GPU form on the same points, (L, p) tuned for the same eps
     fp64_form = None
@@ -287,32 +311,43 @@ def run_ours(args):
             tot.setdefault(k, [0.0, 0])
             tot[k][0] += ms
             tot[k][1] += n
-    dom = max(tot, key=lambda k: tot[k][0])
-    if tot[dom][0] <= 0.0:
-        roof = None
-    elif dom == "p2p":
-        # one MUFU log2 per pair; peak = measured lg2 throughput
-        pairs = sum(info[t]["n_p2p_pairs"] for t in args.tilings)
-        peak = alu["lg2_gops"]
-        ach = pairs / (tot[dom][0] / 1e3) / 1e9
-        roof = {"kernel": "p2p", "bound": "alu", "achieved": ach, "peak": peak, "unit": "Gpair/s",
-                "frac": ach / peak, "traffic": None,
-                "peak_source": "measured MUFU lg2 rate (fmm2d_measure_alu_peaks), one lg2 per pair"}
-    else:
+    tot_iso = {}
+    for t in args.tilings:
+        for k, (ms, n) in stage_iso[t].items():
+            tot_iso.setdefault(k, [0.0, 0])
+            tot_iso[k][0] += ms
+            tot_iso[k][1] += n
+
+    def roofline(tt_, note):
+        dom = max(tt_, key=lambda k: tt_[k][0])
+        if tt_[dom][0] <= 0.0:
+            return None
+        if dom == "p2p":
+            # one MUFU log2 per pair; peak = measured lg2 throughput
+            pairs = sum(info[t]["n_p2p_pairs"] for t in args.tilings)
+            peak = alu["lg2_gops"]
+            ach = pairs / (tt_[dom][0] / 1e3) / 1e9
+            return {"kernel": "k_p2p_x2 (P2P)", "bound": "alu", "achieved": ach, "peak": peak,
+                    "unit": "Gpair/s", "frac": ach / peak, "traffic": P2P_TRAFFIC,
+                    "peak_source": "measured MUFU lg2 rate (fmm2d_measure_alu_peaks), one lg2 per pair",
+                    "timing": note}
         fl = 0.0
         for t in args.tilings:
             p = info[t]["p"]
             fl += info[t]["n_m2l"] * 8.0 * p * (p + 1)
         peak = alu["fp32_tflops"]
-        ach = fl / (tot[dom][0] / 1e3) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+        ach = fl / (tt_[dom][0] / 1e3) / 1e12
+        return {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": None,
-                "peak_source": "measured FP32 FMA rate (fmm2d_measure_alu_peaks)"}
+                "peak_source": "measured FP32 FMA rate (fmm2d_measure_alu_peaks)", "timing": note}
+
+    roof = roofline(tot, "CUDA events around the stage, 5 steps after the timed ones (far field concurrent)")
+    roof_iso = roofline(tot_iso, "CUDA events, one extra step with the stages serialised")
 
     cpu_v, cpu_dt = (None, None)
     if rank == 0 and not args.no_cpu_baseline:
         cpu_v, cpu_dt = oracle_sample(n=args.ref_points)
-    launches = int(sum(tot[k][1] for k in tot))
+    launches = int(sum(tot_iso[k][1] for k in tot_iso))
     if rank == 0:
         line = {
             "metric": "FMM eval points/s at eps=1e-6 (3 tilings)", "value": value, "unit": "points/s",
@@ -329,14 +364,18 @@ def run_ours(args):
                                "ms": statistics.mean(tt[t]), "L": info[t]["levels"], "p": info[t]["p"],
                                "m2l": info[t]["n_m2l"], "p2p_pairs": info[t]["n_p2p_pairs"],
                                "tune_probe_err": tuned[t][2],
-                               "stages_ms": {k: v[0] for k, v in stage[t].items()}}
+                               "stages_ms": {k: v[0] for k, v in stage[t].items()},
+                               "stages_ms_isolated": {k: v[0] for k, v in stage_iso[t].items()}}
                            for t in args.tilings},
             "fp64_form": fp64_form,
             "roofline": roof,
+            "roofline_isolated": roof_iso,
             "peaks_source": src,
             "alu_peaks": alu,
             "stage_ms_total": {k: v[0] for k, v in tot.items()},
-            "stage_note": "per-stage CUDA events from one extra step after the timed steps",
+            "stage_ms_total_isolated": {k: v[0] for k, v in tot_iso.items()},
+            "stage_note": "stage_ms: mean of 5 steps after the timed ones, far field concurrent "
+                          "with P2P; isolated: one extra step with the stages serialised",
             "cpu_baseline": None if cpu_v is None else {
                 "value": cpu_v, "unit": "points/s", "cores": 1, "kind": "oracle",
                 "sample": "N=M=%d per tiling, 3 tilings, one FP64 evaluation (%.1f s)" % (args.ref_points, cpu_dt)},
@@ -360,6 +399,105 @@ def _pool(n_max, seed):
     uxy, uu = uniform_square(n_max, seed=seed, dtype=np.float32)
     gxy, gu = gaussian_mixture(n_max, seed=seed + 1, k=8, dtype=np.float32)
     return (uxy, uu), (gxy, gu.astype(np.float32))
+
+
+def run_forest_batch(args):
+    """The 4096-instance batch as three forests (one per tiling): each forest is
+    one fmm2d_build_forest + fmm2d_evaluate over all its instances.  Device
+    time with CUDA events (inputs resident), and end to end from pinned host
+    buffers with the copies inside the timed region."""
+    import torch
+    from paper_1204_3105_gb300 import fmm2d
+    from paper_1204_3105_gb300.inputs import rng, uniform_square
+    fmm2d.lib()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    g = rng(SEED + 40)
+    count = args.instances
+    sizes = np.exp(g.uniform(np.log(256), np.log(65536), count)).astype(np.int64)
+    tilings = g.integers(0, 3, count)
+    names = ("quad", "sept", "tri")
+    forests = {}
+    for ti, name in enumerate(names):
+        idx = np.nonzero(tilings == ti)[0]
+        pts = [uniform_square(int(sizes[i]), seed=1000 + int(i), dtype=np.float32) for i in idx]
+        off = np.concatenate([[0], np.cumsum(sizes[idx])]).astype(np.int64)
+        xy = np.concatenate([q[0] for q in pts])
+        u = np.concatenate([q[1] for q in pts])
+        # p from fmm2d_autotune on the forest's largest instance (eps, seeded probe)
+        big = int(np.argmax(sizes[idx]))
+        bxy = torch.from_numpy(pts[big][0]).to(dev)
+        _, p_t, e_t, _ = fmm2d.fmm2d_autotune(name, 1e-6, fmm2d.PREC_MIXED_TC | fmm2d.IN_F32, bxy,
+                                             len(pts[big][0]), bxy, len(pts[big][0]), stream=stream)
+        plan = fmm2d.Plan(name, 0, p_t, 1e-6, fmm2d.PREC_MIXED_TC | fmm2d.IN_F32 | fmm2d.ADAPTIVE)
+        plan.set_leaf_size(args.leaf_size)
+        forests[name] = dict(off=off, xy=xy, u=u, plan=plan, p=p_t, tune_err=e_t, n=len(idx),
+                             xy_d=torch.from_numpy(xy).to(dev), u_d=torch.from_numpy(u).to(dev),
+                             out=torch.empty(len(xy), dtype=torch.float64, device=dev),
+                             xy_h=torch.from_numpy(xy).pin_memory(), u_h=torch.from_numpy(u).pin_memory(),
+                             res_h=torch.empty(len(xy), dtype=torch.float64).pin_memory())
+    flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device=dev)
+    total = int(sizes.sum())
+
+    def step(times):
+        for name in names:
+            f = forests[name]
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            f["plan"].build_forest(f["xy_d"], f["off"], stream)
+            f["plan"].evaluate(f["u_d"], f["out"], stream)
+            e1.record(stream)
+            times.append((name, e0, e1))
+            flush.zero_()
+
+    for _ in range(args.warmup):
+        step([])
+    torch.cuda.synchronize()
+    times = []
+    with Clocks(0) as clk:
+        for _ in range(args.steps):
+            step(times)
+        torch.cuda.synchronize()
+    per = {n: [] for n in names}
+    for name, a, b in times:
+        per[name].append(a.elapsed_time(b))
+    ms = sum(statistics.mean(v) for v in per.values())
+    e2e = []
+    for it in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for name in names:
+            f = forests[name]
+            xd = f["xy_h"].to(dev, non_blocking=True)
+            ud = f["u_h"].to(dev, non_blocking=True)
+            f["plan"].build_forest(xd, f["off"], stream)
+            f["plan"].evaluate(ud, f["out"], stream)
+            f["res_h"].copy_(f["out"], non_blocking=True)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            e2e.append(time.perf_counter() - t0)
+    line = {
+        "metric": "batched FMM points/s (4096 instances, eps=1e-6)", "value": total / (ms / 1e3),
+        "unit": "points/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "tf32x3+f32+f64", "data": "synthetic",
+        "config": {"workload": "4096 instances, N log-uniform [256, 65536], uniform unit square, tiling "
+                               "uniform over 3, eps=1e-6, FP32; one forest per tiling "
+                               "(fmm2d_build_forest + fmm2d_evaluate), leaf size %d" % args.leaf_size,
+                   "instances": count, "points": total, "l2": "flushed between forests (256 MB write)"},
+        "per_tiling": {n: {"instances": forests[n]["n"], "points": int(forests[n]["off"][-1]),
+                           "ms": statistics.mean(per[n]), "p": forests[n]["p"],
+                           "levels": forests[n]["plan"].query()["levels"],
+                           "tune_probe_err": forests[n]["tune_err"]} for n in names},
+        "e2e": {"value": total / statistics.mean(e2e), "unit": "points/s",
+                "h2d_bytes_per_step": int(sum(f["xy"].nbytes + f["u"].nbytes for f in forests.values())),
+                "d2h_bytes_per_step": int(8 * total)},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    for f in forests.values():
+        f["plan"].close()
 
 
 def run_server_workload(args):
@@ -460,10 +598,16 @@ def main():
     ap.add_argument("--duration", type=float, default=1.0, help="serve: seconds of arrivals")
     ap.add_argument("--slots", type=int, default=16, help="batch/serve: server slots")
     ap.add_argument("--budget-gb", type=float, default=80.0, help="batch/serve: HBM budget")
+    ap.add_argument("--batch-mode", default="forest", choices=["forest", "server"],
+                    help="batch: one forest per tiling, or one server request per instance")
+    ap.add_argument("--leaf-size", type=int, default=64, help="batch/serve: adaptive leaf size")
     ap.add_argument("--tree", default="auto", choices=["auto", "uniform", "adaptive"],
                     help="batch/serve: tree of each request (auto: adaptive for serve)")
     args = ap.parse_args()
     args.tilings = tuple(args.tilings.split(","))
+    if args.workload == "batch" and args.batch_mode == "forest" and args.impl != "reference":
+        run_forest_batch(args)
+        return
     if args.workload != "fmm" and args.impl != "reference":
         run_server_workload(args)
         return

@@ -173,6 +173,23 @@ fmm2d_status fmm2d_build(fmm2d_plan *plan, const void *src_xy_dev, int64_t n_src
                          const void *tgt_xy_dev, int64_t n_tgt, void *stream);
 
 /*
+ * fmm2d_build_forest - build many independent instances at once (batched
+ * solves): instance i holds the points [offsets[i], offsets[i+1]) of xy_dev
+ * (sources = targets); all instances share the plan's tiling, domain, p and
+ * leaf size, and never interact.  The instances form one adaptive tree with
+ * one level-0 cell per instance, so one fmm2d_evaluate (strengths and
+ * potentials concatenated in the same order) runs every instance with the
+ * launches of a single solve.  Needs an FMM2D_ADAPTIVE plan; its `levels`
+ * (0 = the largest level for which n_inst * b^levels < 2^32) is the finest
+ * level.  offsets: HOST array of n_inst + 1 non-decreasing int64, offsets[0]
+ * = 0.  The paper has no batched form; each instance is the FMM of Sec. 2.
+ * Errors: FMM2D_EINVAL (not adaptive, bad offsets, too many instances for the
+ * finest level), FMM2D_ENOMEM, FMM2D_EDOMAIN, FMM2D_ECUDA.
+ */
+fmm2d_status fmm2d_build_forest(fmm2d_plan *plan, const void *xy_dev, const int64_t *offsets,
+                                int n_inst, void *stream);
+
+/*
  * fmm2d_evaluate - one FMM evaluation on the built geometry (Sec. 2):
  * P2M, M2M, M2L, L2L, L2P and P2P, then the potentials are written in the
  * caller's original target order.
@@ -220,11 +237,15 @@ fmm2d_status fmm2d_debug_export(fmm2d_plan *plan, int what, int level, void *hos
                                 size_t cap, size_t *written);
 
 /*
- * fmm2d_plan_set_profiling - when on (1), fmm2d_build / fmm2d_evaluate
- * record CUDA events around every stage on the launching stream, and
+ * fmm2d_plan_set_profiling - when on (1 or 2), fmm2d_build / fmm2d_evaluate
+ * record CUDA events around every stage on the stream that runs it, and
  * fmm2d_stage_times returns the accumulated milliseconds per stage
  * (keys, sort, tree, lists, p2m, m2m, m2l, l2l, l2p, p2p, other) and the
- * number of launches of each.  Resets the accumulators.
+ * number of launches of each.  With 1 the evaluation runs as usual: the
+ * far-field stages (P2M ... L2L) run on a plan stream concurrently with P2P
+ * on the caller's stream, so their times overlap.  With 2 every stage runs
+ * on the caller's stream, one after the other, so that each time is the
+ * stage's own.  Resets the accumulators.
  */
 fmm2d_status fmm2d_plan_set_profiling(fmm2d_plan *plan, int on);
 fmm2d_status fmm2d_stage_times(fmm2d_plan *plan, double *ms_host, int64_t *launches_host,

@@ -22,6 +22,11 @@
 //    children.
 // The U, W and X pairs are then grouped by target (stable sort).
 //
+// Forest.  Many independent instances (same tiling and domain) form one tree
+// with one level-0 cell per instance: a level-l key is inst * b^l + the
+// instance-local key, so every key arithmetic below works on the local part
+// and lookups re-attach the instance.  Instances never interact.
+//
 // Operators (Greengard-Rokhlin series, scaled like the uniform expansions):
 //  * M2P: phi(y) += Q log|y - c| + Re sum_k a^_k (s_c / (y - c))^k
 //  * P2L: L_0 += sum u log|x - c|, b^_l += -(1/l) sum u (s_c / (x - c))^l
@@ -38,6 +43,13 @@ __device__ __forceinline__ uint64_t level_span(int b, int up) {   // b^up
   uint64_t v = 1;
   for (int i = 0; i < up; ++i) v *= (uint64_t)b;
   return v;
+}
+
+// split a level-l key into instance and local key
+__device__ __forceinline__ uint32_t local_key(int b, int l, uint32_t key, uint32_t *inst) {
+  const uint64_t pw = level_span(b, l);
+  *inst = (uint32_t)(key / pw);
+  return (uint32_t)(key % pw);
 }
 
 // first index in [lo, hi) with key >= x
@@ -62,26 +74,47 @@ __device__ __forceinline__ int find_cell(const uint32_t *__restrict__ ckey, int6
   return (lo < first + count && ckey[lo] == key) ? (int)lo : -1;
 }
 
-__global__ void k_ad_root(Geo g, int n_s, int n_t, AdCells c) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// One level-0 cell per instance: instance i owns sources [soff[i], soff[i+1])
+// and targets [toff[i], toff[i+1]) (one instance: the whole sets).
+__global__ void k_ad_roots(Geo g, int n_inst, const int64_t *__restrict__ soff,
+                           const int64_t *__restrict__ toff, int64_t n_s, int64_t n_t, AdCells c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_inst) return;
   int4 crd;
   double2 ctr;
   uint8_t cls;
   cell_geometry(g, 0, 0u, &crd, &ctr, &cls);
-  c.key[0] = 0u;
-  c.lev[0] = 0;
-  c.parent[0] = -1;
-  c.child_first[0] = 0;
-  c.child_cnt[0] = 0;
-  c.split[0] = 0;
-  c.ss[0] = 0;
-  c.se[0] = n_s;
-  c.ts[0] = 0;
-  c.te[0] = n_t;
-  c.crd[0] = crd;
-  c.ctr[0] = ctr;
-  c.cls[0] = cls;
-  c.hsrc[0] = n_s > 0;
+  const int s0 = soff ? (int)soff[i] : 0, s1 = soff ? (int)soff[i + 1] : (int)n_s;
+  const int t0 = toff ? (int)toff[i] : 0, t1 = toff ? (int)toff[i + 1] : (int)n_t;
+  c.key[i] = (uint32_t)i;
+  c.lev[i] = 0;
+  c.parent[i] = -1;
+  c.child_first[i] = 0;
+  c.child_cnt[i] = 0;
+  c.split[i] = 0;
+  c.ss[i] = s0;
+  c.se[i] = s1;
+  c.ts[i] = t0;
+  c.te[i] = t1;
+  c.crd[i] = crd;
+  c.ctr[i] = ctr;
+  c.cls[i] = cls;
+  c.hsrc[i] = s1 > s0;
+}
+
+// Instance prefix of the finest-level keys: key += inst * b^L, the instance
+// found by binary search in the offsets.
+__global__ void k_ad_prefix(int64_t n, uint32_t *__restrict__ key, const int64_t *__restrict__ off,
+                            int n_inst, uint64_t span) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int lo = 0, hi = n_inst;   // last instance with off[inst] <= i
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= i) lo = mid;
+    else hi = mid;
+  }
+  key[i] = (uint32_t)((uint64_t)key[i] + (uint64_t)lo * span);
 }
 
 // Split decision and children's point ranges of the cells of level l.
@@ -131,7 +164,8 @@ __global__ void k_ad_emit(Geo g, int l, int64_t first, int64_t count, int64_t ne
     int4 crd;
     double2 ctr;
     uint8_t cls;
-    cell_geometry(g, l + 1, key, &crd, &ctr, &cls);
+    uint32_t inst;
+    cell_geometry(g, l + 1, local_key(b, l + 1, key, &inst), &crd, &ctr, &cls);
     const int4 r = crange[i * b + d];
     c.key[ch] = key;
     c.lev[ch] = (uint8_t)(l + 1);
@@ -268,6 +302,9 @@ __global__ void k_ad_lists(Geo g, const Stencils *__restrict__ stp, int l, int l
     const int a = (int)(first + it);
     const bool a_tgt = c.te[a] > c.ts[a];
     const int4 ca = c.crd[a];
+    uint32_t inst;
+    local_key(g.b, l, c.key[a], &inst);
+    const uint32_t ibase = (uint32_t)((uint64_t)inst * level_span(g.b, l));
     if (a_tgt) {
       const int o = (g.tiling == FMM2D_TRI && ca.w == 0) ? 1 : 0;
       const bool a_leaf = !c.split[a];
@@ -276,7 +313,7 @@ __global__ void k_ad_lists(Geo g, const Stencils *__restrict__ stp, int l, int l
                                  ca.z + st.near_d[o][e][2], 0);
         uint32_t k;
         if (!cell_at(g, l, q, &k)) continue;
-        const int m = find_cell(c.key, first, count, k);
+        const int m = find_cell(c.key, first, count, ibase + k);
         if (m < 0 || !c.hsrc[m]) continue;
         const bool m_leaf = !c.split[m];
         if (a_leaf && m_leaf) {
@@ -306,7 +343,7 @@ __global__ void k_ad_lists(Geo g, const Stencils *__restrict__ stp, int l, int l
                                    ca.z + st.far_d[cls][e][2], 0);
           uint32_t k;
           if (cell_at(g, l, q, &k)) {
-            sidx = find_cell(c.key, first, count, k);
+            sidx = find_cell(c.key, first, count, ibase + k);
             if (sidx >= 0 && !c.hsrc[sidx]) sidx = -1;
           }
         }
@@ -325,7 +362,9 @@ __global__ void k_ad_lists(Geo g, const Stencils *__restrict__ stp, int l, int l
   } else if (it < count + n_t) {                      // W test: leaf a, finer cell cc
     const int64_t j = it - count;
     const int a = t_a[j], cc = t_c[j];
-    if (separated(g, st, l, c.crd[cc], c.lev[a], c.key[a])) em.put(K_W, a, cc);
+    uint32_t inst;
+    if (separated(g, st, l, c.crd[cc], c.lev[a], local_key(g.b, c.lev[a], c.key[a], &inst)))
+      em.put(K_W, a, cc);
     else if (!c.split[cc]) em.put(K_U, a, cc);
     else
       for (int d = 0; d < c.child_cnt[cc]; ++d) {
@@ -335,7 +374,9 @@ __global__ void k_ad_lists(Geo g, const Stencils *__restrict__ stp, int l, int l
   } else {                                            // X test: cell a, coarser leaf cc
     const int64_t j = it - count - n_t;
     const int a = s_a[j], cc = s_c[j];
-    if (separated(g, st, l, c.crd[a], c.lev[cc], c.key[cc])) em.put(K_X, a, cc);
+    uint32_t inst;
+    if (separated(g, st, l, c.crd[a], c.lev[cc], local_key(g.b, c.lev[cc], c.key[cc], &inst)))
+      em.put(K_X, a, cc);
     else if (!c.split[a]) em.put(K_U, a, cc);
     else
       for (int d = 0; d < c.child_cnt[a]; ++d) {
@@ -511,8 +552,17 @@ k_ad_p2l(int64_t n_cells, const int *__restrict__ x_off, const int *__restrict__
 
 }  // namespace
 
-cudaError_t ad_launch_root(const Geo &g, int64_t n_s, int64_t n_t, const AdCells &c, cudaStream_t s) {
-  k_ad_root<<<1, 32, 0, s>>>(g, (int)n_s, (int)n_t, c);
+cudaError_t ad_launch_roots(const Geo &g, int n_inst, const int64_t *soff, const int64_t *toff,
+                            int64_t n_s, int64_t n_t, const AdCells &c, cudaStream_t s) {
+  if (n_inst <= 0) return cudaSuccess;
+  k_ad_roots<<<nblk(n_inst, 128), 128, 0, s>>>(g, n_inst, soff, toff, n_s, n_t, c);
+  return cudaGetLastError();
+}
+
+cudaError_t ad_launch_prefix(int64_t n, uint32_t *key, const int64_t *off, int n_inst, uint64_t span,
+                             cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_ad_prefix<<<nblk(n, 256), 256, 0, s>>>(n, key, off, n_inst, span);
   return cudaGetLastError();
 }
 

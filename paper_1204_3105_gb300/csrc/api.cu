@@ -394,8 +394,13 @@ void flush_events(fmm2d_plan *pl) {
   pl->ev_used = 0;
 }
 
-// The plan's far-field stream (highest priority) and its fork / join events.
+// The plan's far-field stream (highest priority) and its fork / join events;
+// with serialised profiling, the caller's stream itself.
 static cudaError_t far_stream(fmm2d_plan *pl, cudaStream_t *out) {
+  if (pl->profiling == 2) {
+    *out = pl->last_stream;
+    return cudaSuccess;
+  }
   if (!pl->far_stream) {
     int lo = 0, hi = 0;
     cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
@@ -555,8 +560,10 @@ fmm2d_status evaluate_t(fmm2d_plan *pl, const void *u, double *out, cudaStream_t
   // fork: the far-field chain on the plan's high-priority stream f, P2P on s
   cudaStream_t f;
   CK(far_stream(pl, &f), "far stream");
-  CK(cudaEventRecord(pl->ev_fork, s), "fork");
-  CK(cudaStreamWaitEvent(f, pl->ev_fork, 0), "fork");
+  if (f != s) {
+    CK(cudaEventRecord(pl->ev_fork, s), "fork");
+    CK(cudaStreamWaitEvent(f, pl->ev_fork, 0), "fork");
+  }
   {
     StageScope sc(pl, ST_P2M, f, 1);
     CK(launch_p2m<R>(a, src4, (const int *)pl->d_src_start.p, (const int *)pl->d_src_end.p, mQ, ma, f), "p2m");
@@ -625,8 +632,10 @@ fmm2d_status evaluate_t(fmm2d_plan *pl, const void *u, double *out, cudaStream_t
                      a.n_leaves > 0 ? (double)pl->n_tgt / (double)a.n_leaves : 0.0, s),
        "p2p");
   }
-  CK(cudaEventRecord(pl->ev_join, f), "join");   // join: L2P needs the locals
-  CK(cudaStreamWaitEvent(s, pl->ev_join, 0), "join");
+  if (f != s) {   // join: L2P needs the locals
+    CK(cudaEventRecord(pl->ev_join, f), "join");
+    CK(cudaStreamWaitEvent(s, pl->ev_join, 0), "join");
+  }
   {
     StageScope sc(pl, ST_L2P, s, 1);
     CK(launch_l2p<R>(a, tgt, tstride, tst, ten, tperm, lL0, lb, (const double *)pl->d_phi_near.p,
@@ -663,10 +672,23 @@ static AdCells ad_cells(fmm2d_plan *pl) {
 // of each level's cell count), the leaves, and the U / W / X / M2L lists by
 // the level-synchronous traversal (one read-back of each level's list sizes).
 static fmm2d_status build_adaptive(fmm2d_plan *pl, const void *src, int64_t n_src, const void *tgt,
-                                   int64_t n_tgt, cudaStream_t s) {
+                                   int64_t n_tgt, cudaStream_t s, int n_inst = 1,
+                                   const int64_t *inst_off = nullptr) {
   const bool f32 = (pl->flags & FMM2D_IN_F32) != 0;
   const bool f64 = is_fp64(pl);
-  const int L = pl->levels_req ? pl->levels_req : ad_max_levels(pl->tiling);
+  // a forest's level-L keys carry the instance: n_inst b^L must fit 32 bits
+  auto fits = [&](int Lc) {
+    double v = (double)n_inst;
+    for (int i = 0; i < Lc; ++i) v *= pl->b;
+    return v <= 4294967296.0;   // keys up to n_inst b^L - 1 < 2^32
+  };
+  int L = pl->levels_req;
+  if (L == 0) {
+    L = ad_max_levels(pl->tiling);
+    while (L > 1 && !fits(L)) --L;
+  }
+  if (!fits(L)) return fail(pl, FMM2D_EINVAL, "too many instances for this finest level");
+  pl->n_inst = n_inst;
   const int p = pl->p_req ? pl->p_req : p_from_eps(pl->tiling, pl->eps);
   const bool tc = (pl->flags & FMM2D_PREC_MASK) == FMM2D_PREC_MIXED_TC;
   if (tc && !tc_shape(p, &pl->tc_K, &pl->tc_N))
@@ -708,12 +730,22 @@ static fmm2d_status build_adaptive(fmm2d_plan *pl, const void *src, int64_t n_sr
       CK(launch_keys(g, tgt, f32, n_tgt, kt, pt, (int *)pl->d_err.p, s, (uint32_t *)pl->d_tmp_v.p,
                      (int *)pl->d_err.p + 2), "keys");
   }
+  int sbits = bits;
+  if (inst_off) {   // forest: prefix the keys with the instance
+    CK(dbuf_reserve(pl->d_inst_off, (n_inst + 1) * 8), "alloc");
+    CK(cudaMemcpyAsync(pl->d_inst_off.p, inst_off, (n_inst + 1) * 8, cudaMemcpyHostToDevice, s), "upload");
+    uint64_t span = 1;
+    for (int i = 0; i < L; ++i) span *= (uint64_t)pl->b;
+    CK(ad_launch_prefix(n_src, ks, (const int64_t *)pl->d_inst_off.p, n_inst, span, s), "prefix");
+    sbits = 0;
+    while (sbits < 32 && ((uint64_t)1 << sbits) < span * (uint64_t)n_inst) ++sbits;
+  }
   {
     StageScope sc(pl, ST_SORT, s, 1);
-    CK(radix_sort_pairs(ks, ps, (uint32_t *)pl->d_tmp_k.p, (uint32_t *)pl->d_tmp_v.p, n_src, bits,
+    CK(radix_sort_pairs(ks, ps, (uint32_t *)pl->d_tmp_k.p, (uint32_t *)pl->d_tmp_v.p, n_src, sbits,
                         pl->d_sort_scratch.p, s), "sort");
     if (!pl->same_sets)
-      CK(radix_sort_pairs(kt, pt, (uint32_t *)pl->d_tmp_k.p, (uint32_t *)pl->d_tmp_v.p, n_tgt, bits,
+      CK(radix_sort_pairs(kt, pt, (uint32_t *)pl->d_tmp_k.p, (uint32_t *)pl->d_tmp_v.p, n_tgt, sbits,
                           pl->d_sort_scratch.p, s), "sort");
   }
   int err_h = 0;
@@ -725,10 +757,11 @@ static fmm2d_status build_adaptive(fmm2d_plan *pl, const void *src, int64_t n_sr
   // targets, so a level has at most n_src/(cap+1) + n_tgt/(cap+1) of them
   const int cap = pl->leaf_cap;
   const int64_t nsplit = pl->same_sets ? n_src / (cap + 1) : n_src / (cap + 1) + n_tgt / (cap + 1);
-  int64_t cap_cells = 1, pw = 1;
+  int64_t cap_cells = n_inst, pw = n_inst;   // pw: cells a level can hold
   for (int l = 0; l < L; ++l) {
+    const int64_t prev = pw;
     pw = pw > ((int64_t)1 << 40) ? pw : pw * b;
-    cap_cells += std::min<int64_t>(pw, (int64_t)b * std::max<int64_t>(1, std::min<int64_t>(nsplit, pw / b)));
+    cap_cells += std::min<int64_t>(pw, (int64_t)b * std::max<int64_t>(1, std::min<int64_t>(nsplit, prev)));
   }
   CK(dbuf_reserve(pl->d_cell_key, cap_cells * 4), "alloc");
   CK(dbuf_reserve(pl->d_cell_lev, cap_cells), "alloc");
@@ -749,11 +782,12 @@ static fmm2d_status build_adaptive(fmm2d_plan *pl, const void *src, int64_t n_sr
   AdCells c = ad_cells(pl);
   int64_t lf[MAXLEV + 2];
   for (int l = 0; l <= MAXLEV + 1; ++l) lf[l] = 0;
-  lf[1] = 1;
+  lf[1] = n_inst;
   int depth = 0;
   {
     StageScope sc(pl, ST_TREE, s, 1);
-    CK(ad_launch_root(g, n_src, pl->same_sets ? n_src : n_tgt, c, s), "root");
+    const int64_t *doff = inst_off ? (const int64_t *)pl->d_inst_off.p : nullptr;
+    CK(ad_launch_roots(g, n_inst, doff, doff, n_src, pl->same_sets ? n_src : n_tgt, c, s), "roots");
     for (int l = 0; l <= L; ++l) {
       const int64_t count = lf[l + 1] - lf[l];
       CK(dbuf_reserve(pl->d_ad_flag, std::max<int64_t>(1, count * b) * 4), "alloc");
@@ -962,8 +996,10 @@ fmm2d_status evaluate_adaptive_t(fmm2d_plan *pl, const void *u, double *out, cud
   }
   cudaStream_t f;   // far-field chain on the plan's stream, P2P on s
   CK(far_stream(pl, &f), "far stream");
-  CK(cudaEventRecord(pl->ev_fork, s), "fork");
-  CK(cudaStreamWaitEvent(f, pl->ev_fork, 0), "fork");
+  if (f != s) {
+    CK(cudaEventRecord(pl->ev_fork, s), "fork");
+    CK(cudaStreamWaitEvent(f, pl->ev_fork, 0), "fork");
+  }
   {
     StageScope sc(pl, ST_P2M, f, 1);
     CK(launch_p2m<R>(a, src4, c.ss, c.se, mQ, ma, f), "p2m");
@@ -974,9 +1010,16 @@ fmm2d_status evaluate_adaptive_t(fmm2d_plan *pl, const void *u, double *out, cud
       CK(launch_m2m<R>(a, pl->geo, l, pl->lev_first[l], pl->lev_count[l], nullptr, c.key, c.cls,
                        c.hsrc, (const Cx<R> *)pl->d_m2m_ops.p, mQ, ma, f), "m2m");
   }
+  {
+    // cells above the first M2L level get no M2L write: their locals (read by
+    // L2P when such a cell is a leaf) start at zero
+    const int64_t ff = pl->n_cells - pl->n_far_cells;
+    if (ff > 0) {
+      CK(cudaMemsetAsync(lL0, 0, ff * sizeof(double), f), "zero locals");
+      CK(cudaMemsetAsync(lb, 0, ff * pl->P * sizeof(Cx<R>), f), "zero locals");
+    }
+  }
   if (pl->n_far_cells == 0) {
-    CK(cudaMemsetAsync(lL0, 0, pl->n_cells * sizeof(double), f), "zero locals");
-    CK(cudaMemsetAsync(lb, 0, pl->n_cells * pl->P * sizeof(Cx<R>), f), "zero locals");
   } else if constexpr (sizeof(R) == 4) {
     if ((pl->flags & FMM2D_PREC_MASK) == FMM2D_PREC_MIXED_TC) {
       StageScope sc(pl, ST_M2L, f, 1);
@@ -1042,8 +1085,10 @@ fmm2d_status evaluate_adaptive_t(fmm2d_plan *pl, const void *u, double *out, cud
                      pl->n_leaves_ad > 0 ? (double)pl->n_tgt / (double)pl->n_leaves_ad : 0.0, s),
        "p2p");
   }
-  CK(cudaEventRecord(pl->ev_join, f), "join");   // join: M2P and L2P need the expansions
-  CK(cudaStreamWaitEvent(s, pl->ev_join, 0), "join");
+  if (f != s) {   // join: M2P and L2P need the expansions
+    CK(cudaEventRecord(pl->ev_join, f), "join");
+    CK(cudaStreamWaitEvent(s, pl->ev_join, 0), "join");
+  }
   {
     StageScope sc(pl, ST_P2P, s, 1);
     CK(ad_launch_m2p<R>(pl->n_leaves_ad, (const int *)pl->d_leaf_ids.p, (const int *)pl->d_w_off.p,
@@ -1250,7 +1295,7 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
   CK(dbuf_reserve(pl->d_near_src, cap_leaf * NEAR_MAX * 4), "alloc");
   pl->cls_cap = cap_list;
   {
-    StageScope sc(pl, ST_TREE, s, (pl->same_sets ? 1 : 2) + (ms <= 8192 ? 1 : 3) + 1 + 1);
+    StageScope sc(pl, ST_TREE, s, (pl->same_sets ? 1 : 2) + (ms <= 8192 ? 1 : 3) + 1);
     CK(cudaMemsetAsync(pl->d_occ.p, 0, ms * 4, s), "memset");
     CK(cudaMemsetAsync(pl->d_hsrc.p, 0, ms * 4, s), "memset");
     CK(launch_mark(g, ks, n_src, (int *)pl->d_occ.p, (int *)pl->d_hsrc.p, s), "mark");
@@ -1261,22 +1306,18 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
                       (double2 *)pl->d_cell_ctr.p, (uint8_t *)pl->d_cell_cls.p,
                       (uint8_t *)pl->d_cell_hsrc.p, (int *)pl->d_src_start.p, (int *)pl->d_src_end.p,
                       pl->same_sets ? nullptr : (int *)pl->d_tgt_start.p,
-                      pl->same_sets ? nullptr : (int *)pl->d_tgt_end.p, s), "compact");
-    CK(launch_level_first(g, (const int *)pl->d_scan.p, (const int *)pl->d_occ.p, ms,
-                          (int64_t *)pl->d_lev_first.p, s), "levels");
+                      pl->same_sets ? nullptr : (int *)pl->d_tgt_end.p, (int64_t *)pl->d_lev_first.p,
+                      s), "compact");
   }
   {
-    StageScope sc(pl, ST_TREE, s, pl->same_sets ? 2 : 4);
-    CK(launch_leaf_ranges(g, ks, n_src, (const int *)pl->d_map.p, (int *)pl->d_src_start.p,
-                          (int *)pl->d_src_end.p, s), "ranges");
-    if (!pl->same_sets)
-      CK(launch_leaf_ranges(g, kt, n_tgt, (const int *)pl->d_map.p, (int *)pl->d_tgt_start.p,
-                            (int *)pl->d_tgt_end.p, s), "ranges");
+    StageScope sc(pl, ST_TREE, s, pl->same_sets ? 1 : 2);
     CK(launch_rel_coords(g, f32, !f64, src, ps, ks, n_src, (const int *)pl->d_map.p,
-                         (const double2 *)pl->d_cell_ctr.p, pl->d_src4.p, 4, s), "rel");
+                         (const double2 *)pl->d_cell_ctr.p, pl->d_src4.p, 4, (int *)pl->d_src_start.p,
+                         (int *)pl->d_src_end.p, s), "rel");
     if (!pl->same_sets)
       CK(launch_rel_coords(g, f32, !f64, tgt, pt, kt, n_tgt, (const int *)pl->d_map.p,
-                           (const double2 *)pl->d_cell_ctr.p, pl->d_tgt2.p, 2, s), "rel");
+                           (const double2 *)pl->d_cell_ctr.p, pl->d_tgt2.p, 2,
+                           (int *)pl->d_tgt_start.p, (int *)pl->d_tgt_end.p, s), "rel");
   }
   {
     StageScope sc(pl, ST_LISTS, s, 1);
@@ -1310,6 +1351,26 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
   pl->n_p2p_pairs = -1;
   pl->built = true;
   return FMM2D_OK;
+}
+
+fmm2d_status fmm2d_build_forest(fmm2d_plan *pl, const void *xy, const int64_t *offsets, int n_inst,
+                                void *stream) {
+  if (!pl) return FMM2D_EINVAL;
+  pl->built = false;
+  if (!(pl->flags & FMM2D_ADAPTIVE)) return fail(pl, FMM2D_EINVAL, "forest builds need an FMM2D_ADAPTIVE plan");
+  if (n_inst < 1 || !offsets) return fail(pl, FMM2D_EINVAL, "need n_inst >= 1 and offsets");
+  if (offsets[0] != 0) return fail(pl, FMM2D_EINVAL, "offsets[0] must be 0");
+  for (int i = 0; i < n_inst; ++i)
+    if (offsets[i + 1] < offsets[i]) return fail(pl, FMM2D_EINVAL, "offsets must not decrease");
+  const int64_t n = offsets[n_inst];
+  if (n > 0 && !xy) return fail(pl, FMM2D_EINVAL, "null point pointer");
+  if (n >= (int64_t)INT_MAX) return fail(pl, FMM2D_EINVAL, "too many points");
+  cudaStream_t s = (cudaStream_t)stream;
+  pl->last_stream = s;
+  pl->same_sets = true;
+  pl->n_src = n;
+  pl->n_tgt = n;
+  return build_adaptive(pl, xy, n, xy, n, s, n_inst, offsets);
 }
 
 fmm2d_status fmm2d_evaluate(fmm2d_plan *pl, const void *u, double *out, void *stream) {
@@ -1590,7 +1651,7 @@ fmm2d_status fmm2d_debug_export(fmm2d_plan *pl, int what, int level, void *host_
 fmm2d_status fmm2d_plan_set_profiling(fmm2d_plan *pl, int on) {
   if (!pl) return FMM2D_EINVAL;
   flush_events(pl);
-  pl->profiling = on != 0;
+  pl->profiling = on == 2 ? 2 : (on != 0 ? 1 : 0);
   for (int i = 0; i < ST_COUNT; ++i) {
     pl->stage_ms[i] = 0;
     pl->stage_launches[i] = 0;
@@ -1630,7 +1691,7 @@ void fmm2d_plan_destroy(fmm2d_plan *pl) {
                   &pl->d_ad_cnt, &pl->d_ad_off, &pl->d_ad_tot, &pl->d_ad_ta, &pl->d_ad_tc,
                   &pl->d_ad_sa, &pl->d_ad_sc, &pl->d_ad_ta2, &pl->d_ad_tc2, &pl->d_ad_sa2,
                   &pl->d_ad_sc2, &pl->d_ad_ut, &pl->d_ad_us, &pl->d_ad_wt, &pl->d_ad_ws,
-                  &pl->d_ad_xt, &pl->d_ad_xs};
+                  &pl->d_ad_xt, &pl->d_ad_xs, &pl->d_inst_off};
   for (DBuf *b : bufs) dbuf_free(*b);
   if (pl->far_stream) {
     cudaStreamSynchronize(pl->far_stream);

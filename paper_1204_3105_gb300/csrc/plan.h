@@ -69,7 +69,7 @@ struct Plan {
   std::string err;
   cudaStream_t last_stream = nullptr;
   // profiling
-  bool profiling = false;
+  int profiling = 0;                  // 0 off, 1 stage events, 2 stage events, stages serialised
   double stage_ms[ST_COUNT] = {0};
   int64_t stage_launches[ST_COUNT] = {0};
   std::vector<cudaEvent_t> ev_pool;
@@ -102,6 +102,8 @@ struct Plan {
   DBuf d_ad_flag, d_ad_pos, d_ad_crange, d_ad_cnt, d_ad_off, d_ad_tot;
   DBuf d_ad_ta, d_ad_tc, d_ad_sa, d_ad_sc, d_ad_ta2, d_ad_tc2, d_ad_sa2, d_ad_sc2;
   DBuf d_ad_ut, d_ad_us, d_ad_wt, d_ad_ws, d_ad_xt, d_ad_xs;
+  int n_inst = 1;                     // instances of a forest build
+  DBuf d_inst_off;
   // the far-field chain (P2M ... L2L) runs on a high-priority plan stream
   // while P2P runs on the caller's stream; two events fork and join them
   cudaStream_t far_stream = nullptr;
@@ -136,19 +138,18 @@ cudaError_t exclusive_scan(const int *in, int *out, int64_t n, void *scratch, cu
 // ---------------------------------------------------------------- tree.cu
 cudaError_t launch_mark(const Geo &g, const uint32_t *key_sorted, int64_t n, int *occ, int *hsrc,
                         cudaStream_t s);
+// Cells of every level from the occupancy scan; also the first slot of every
+// level and the total in lev_first[0 .. L+1].
 cudaError_t launch_compact(const Geo &g, const int *occ, const int *scan, const int *hsrc,
                            int64_t map_size, int *map, uint32_t *cell_key, int4 *cell_crd,
                            double2 *cell_ctr, uint8_t *cell_cls, uint8_t *cell_hsrc,
                            int *src_start, int *src_end, int *tgt_start, int *tgt_end,
-                           cudaStream_t s);
-cudaError_t launch_leaf_ranges(const Geo &g, const uint32_t *key_sorted, int64_t n, const int *map,
-                               int *start, int *end, cudaStream_t s);
+                           int64_t *lev_first, cudaStream_t s);
+// Sorted points relative to their leaf centre, and the leaves' point ranges.
 cudaError_t launch_rel_coords(const Geo &g, bool f32_in, bool f32_out, const void *xy,
                               const uint32_t *perm, const uint32_t *key_sorted, int64_t n,
                               const int *map, const double2 *ctr, void *out, int out_stride,
-                              cudaStream_t s);
-cudaError_t launch_level_first(const Geo &g, const int *scan, const int *occ, int64_t map_size,
-                               int64_t *out, cudaStream_t s);
+                              int *start, int *end, cudaStream_t s);
 // Near lists of the leaves and M2L lists of levels >= l_min, for the cells
 // of levels lo_level..L (count read on the device; cap = launch bound).
 cudaError_t launch_lists(const Geo &g, const Stencils *d_sten, int lo_level, int l_min, int64_t cap,
@@ -171,7 +172,13 @@ struct AdCells {
   double2 *ctr;
   uint8_t *cls, *hsrc;
 };
-cudaError_t ad_launch_root(const Geo &g, int64_t n_s, int64_t n_t, const AdCells &c, cudaStream_t s);
+// level-0 cells: one per instance (soff / toff: n_inst + 1 device offsets),
+// or one cell holding everything (null offsets, n_inst = 1)
+cudaError_t ad_launch_roots(const Geo &g, int n_inst, const int64_t *soff, const int64_t *toff,
+                            int64_t n_s, int64_t n_t, const AdCells &c, cudaStream_t s);
+// add the instance prefix inst * span to sorted-order-independent keys
+cudaError_t ad_launch_prefix(int64_t n, uint32_t *key, const int64_t *off, int n_inst, uint64_t span,
+                             cudaStream_t s);
 cudaError_t ad_launch_split(const Geo &g, int l, int64_t first, int64_t count, int cap,
                             const uint32_t *skey, const uint32_t *tkey, const AdCells &c, int *flag,
                             int4 *crange, cudaStream_t s);

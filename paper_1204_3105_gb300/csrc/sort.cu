@@ -148,17 +148,24 @@ __global__ void k_radix_hist(const uint32_t *__restrict__ keys, int64_t n, int s
   counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
+// Stable scatter of one tile: every element's rank inside the tile in
+// (digit, input order) order, the tile reordered in shared memory by that
+// rank, then written out run by run so that consecutive threads store to
+// consecutive addresses of each digit's destination range.
 __global__ void __launch_bounds__(RS_TH)
 k_radix_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
                 uint32_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int shift,
                 const int *__restrict__ offs, int nblocks) {
   __shared__ int wcnt[RS_WARPS][257];
-  __shared__ int goff[256];
+  __shared__ int goff[256], dstart[256];
+  __shared__ int sm_scan[33];
+  __shared__ uint32_t tk[RS_TILE], tv[RS_TILE];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < RS_WARPS * 257; i += RS_TH) (&wcnt[0][0])[i] = 0;
   goff[threadIdx.x] = offs[(int64_t)threadIdx.x * nblocks + blockIdx.x];
   __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)w * (32 * RS_IPT);
+  const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
+  const int64_t base = tile0 + (int64_t)w * (32 * RS_IPT);
   const unsigned lt = (1u << lane) - 1u;
   uint32_t key[RS_IPT], val[RS_IPT];
   int loc[RS_IPT];
@@ -177,13 +184,17 @@ k_radix_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ v
     __syncwarp();
   }
   __syncthreads();
-  {  // exclusive scan over warps, per digit
+  int tot;
+  {  // exclusive scan over warps, per digit; then over digits
     int d = threadIdx.x, run = 0;
     for (int ww = 0; ww < RS_WARPS; ++ww) {
       int t = wcnt[ww][d];
       wcnt[ww][d] = run;
       run += t;
     }
+    int ex;
+    tot = block_excl_scan(run, ex, sm_scan);
+    dstart[d] = ex;
   }
   __syncthreads();
 #pragma unroll
@@ -191,10 +202,18 @@ k_radix_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ v
     int64_t idx = base + r * 32 + lane;
     if (idx < n) {
       int d = (int)((key[r] >> shift) & 255u);
-      int64_t pos = (int64_t)goff[d] + wcnt[w][d] + loc[r];
-      kout[pos] = key[r];
-      vout[pos] = val[r];
+      int tp = dstart[d] + wcnt[w][d] + loc[r];   // rank inside the tile
+      tk[tp] = key[r];
+      tv[tp] = val[r];
     }
+  }
+  __syncthreads();
+  for (int tp = threadIdx.x; tp < tot; tp += RS_TH) {
+    const uint32_t k = tk[tp];
+    const int d = (int)((k >> shift) & 255u);
+    const int64_t pos = (int64_t)goff[d] + (tp - dstart[d]);
+    kout[pos] = k;
+    vout[pos] = tv[tp];
   }
 }
 

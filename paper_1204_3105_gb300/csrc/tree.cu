@@ -40,14 +40,18 @@ __global__ void k_compact(Geo g, const int *__restrict__ occ, const int *__restr
                           double2 *__restrict__ cell_ctr, uint8_t *__restrict__ cell_cls,
                           uint8_t *__restrict__ cell_hsrc, int *__restrict__ src_start,
                           int *__restrict__ src_end, int *__restrict__ tgt_start,
-                          int *__restrict__ tgt_end) {
+                          int *__restrict__ tgt_end, int64_t *__restrict__ lev_first) {
   int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (m >= map_size) return;
+  const int l = level_of_map(g, m);
+  if (lev_first) {   // first slot of every level, and the total
+    if (m == g.map_off[l]) lev_first[l] = scan[m];
+    if (m == map_size - 1) lev_first[g.L + 1] = (int64_t)scan[m] + occ[m];
+  }
   if (!occ[m]) {
     map[m] = -1;
     return;
   }
-  const int l = level_of_map(g, m);
   const uint32_t key = (uint32_t)(m - g.map_off[l]);
   const int slot = scan[m];
   map[m] = slot;
@@ -64,32 +68,20 @@ __global__ void k_compact(Geo g, const int *__restrict__ occ, const int *__restr
   cell_cls[slot] = cls;
 }
 
-__global__ void k_level_first(Geo g, const int *__restrict__ scan, const int *__restrict__ occ,
-                              int64_t map_size, int64_t *__restrict__ out) {
-  int l = threadIdx.x;
-  if (l <= g.L) out[l] = scan[g.map_off[l]];
-  if (l == g.L + 1) out[l] = (int64_t)scan[map_size - 1] + occ[map_size - 1];
-}
-
-__global__ void k_leaf_ranges(Geo g, const uint32_t *__restrict__ key, int64_t n,
-                              const int *__restrict__ map, int *__restrict__ start,
-                              int *__restrict__ end) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint32_t k = key[i];
-  int slot = map[g.map_off[g.L] + k];
-  if (i == 0 || key[i - 1] != k) start[slot] = (int)i;
-  if (i == n - 1 || key[i + 1] != k) end[slot] = (int)(i + 1);
-}
-
+// Per sorted point: the leaf's [start, end) at run boundaries, and the point
+// relative to its leaf centre.
 template <typename TI, typename TO>
 __global__ void k_rel(Geo g, const TI *__restrict__ xy, const uint32_t *__restrict__ perm,
                       const uint32_t *__restrict__ key, int64_t n, const int *__restrict__ map,
-                      const double2 *__restrict__ ctr, TO *__restrict__ out, int stride) {
+                      const double2 *__restrict__ ctr, TO *__restrict__ out, int stride,
+                      int *__restrict__ start, int *__restrict__ end) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t o = perm[i];
-  int slot = map[g.map_off[g.L] + key[i]];
+  const uint32_t k = key[i];
+  int slot = map[g.map_off[g.L] + k];
+  if (i == 0 || key[i - 1] != k) start[slot] = (int)i;
+  if (i == n - 1 || key[i + 1] != k) end[slot] = (int)(i + 1);
   double2 c = ctr[slot];
   double x = (double)xy[2 * (int64_t)o], y = (double)xy[2 * (int64_t)o + 1];
   TO *dst = out + i * stride;
@@ -184,40 +176,27 @@ cudaError_t launch_compact(const Geo &g, const int *occ, const int *scan, const 
                            int64_t map_size, int *map, uint32_t *cell_key, int4 *cell_crd,
                            double2 *cell_ctr, uint8_t *cell_cls, uint8_t *cell_hsrc,
                            int *src_start, int *src_end, int *tgt_start, int *tgt_end,
-                           cudaStream_t s) {
+                           int64_t *lev_first, cudaStream_t s) {
   k_compact<<<nblk(map_size, 256), 256, 0, s>>>(g, occ, scan, hsrc, map_size, map, cell_key,
                                                  cell_crd, cell_ctr, cell_cls, cell_hsrc, src_start,
-                                                 src_end, tgt_start, tgt_end);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_level_first(const Geo &g, const int *scan, const int *occ, int64_t map_size,
-                               int64_t *out, cudaStream_t s) {
-  k_level_first<<<1, 64, 0, s>>>(g, scan, occ, map_size, out);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_leaf_ranges(const Geo &g, const uint32_t *key_sorted, int64_t n, const int *map,
-                               int *start, int *end, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  k_leaf_ranges<<<nblk(n, 256), 256, 0, s>>>(g, key_sorted, n, map, start, end);
+                                                 src_end, tgt_start, tgt_end, lev_first);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rel_coords(const Geo &g, bool f32_in, bool f32_out, const void *xy,
                               const uint32_t *perm, const uint32_t *key_sorted, int64_t n,
                               const int *map, const double2 *ctr, void *out, int out_stride,
-                              cudaStream_t s) {
+                              int *start, int *end, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   unsigned b = nblk(n, 256);
   if (f32_in && f32_out)
-    k_rel<float, float><<<b, 256, 0, s>>>(g, (const float *)xy, perm, key_sorted, n, map, ctr, (float *)out, out_stride);
+    k_rel<float, float><<<b, 256, 0, s>>>(g, (const float *)xy, perm, key_sorted, n, map, ctr, (float *)out, out_stride, start, end);
   else if (f32_in)
-    k_rel<float, double><<<b, 256, 0, s>>>(g, (const float *)xy, perm, key_sorted, n, map, ctr, (double *)out, out_stride);
+    k_rel<float, double><<<b, 256, 0, s>>>(g, (const float *)xy, perm, key_sorted, n, map, ctr, (double *)out, out_stride, start, end);
   else if (f32_out)
-    k_rel<double, float><<<b, 256, 0, s>>>(g, (const double *)xy, perm, key_sorted, n, map, ctr, (float *)out, out_stride);
+    k_rel<double, float><<<b, 256, 0, s>>>(g, (const double *)xy, perm, key_sorted, n, map, ctr, (float *)out, out_stride, start, end);
   else
-    k_rel<double, double><<<b, 256, 0, s>>>(g, (const double *)xy, perm, key_sorted, n, map, ctr, (double *)out, out_stride);
+    k_rel<double, double><<<b, 256, 0, s>>>(g, (const double *)xy, perm, key_sorted, n, map, ctr, (double *)out, out_stride, start, end);
   return cudaGetLastError();
 }
 

@@ -35,7 +35,7 @@ SYMBOLS = ["fmm2d_default_params", "fmm2d_plan_create", "fmm2d_plan_set_domain",
            "fmm2d_keys_sort_noalloc", "fmm2d_autotune", "fmm2d_measure_alu_peaks",
            "fmm2d_plan_set_params", "fmm2d_serve_create", "fmm2d_serve_submit", "fmm2d_serve_poll",
            "fmm2d_serve_wait", "fmm2d_serve_stats", "fmm2d_serve_destroy",
-           "fmm2d_plan_set_leaf_size"]
+           "fmm2d_plan_set_leaf_size", "fmm2d_build_forest"]
 
 
 class Info(ctypes.Structure):
@@ -112,6 +112,7 @@ def lib():
     L.fmm2d_measure_alu_peaks.argtypes = [ctypes.POINTER(dbl)]
     L.fmm2d_plan_set_params.argtypes = [vp, c_int, c_int, dbl]
     L.fmm2d_plan_set_leaf_size.argtypes = [vp, c_int]
+    L.fmm2d_build_forest.argtypes = [vp, vp, ctypes.POINTER(i64), c_int, vp]
     L.fmm2d_serve_create.argtypes = [ctypes.c_size_t, c_int, ctypes.POINTER(vp)]
     L.fmm2d_serve_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
     L.fmm2d_serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(Result)]
@@ -222,6 +223,15 @@ class Plan:
 
     build = fmm2d_build
 
+    def fmm2d_build_forest(self, xy, offsets, stream=None):
+        """xy: device points of all instances; offsets: host int64 array, n_inst + 1 entries."""
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        self._check(self.lib.fmm2d_build_forest(
+            self._h, _ptr(xy), off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(off) - 1,
+            _stream(stream)), "build_forest")
+
+    build_forest = fmm2d_build_forest
+
     def fmm2d_evaluate(self, strengths, potentials, stream=None):
         self._check(self.lib.fmm2d_evaluate(self._h, _ptr(strengths), _ptr(potentials),
                                             _stream(stream)), "evaluate")
@@ -265,7 +275,8 @@ class Plan:
     export = fmm2d_debug_export
 
     def fmm2d_plan_set_profiling(self, on=True):
-        self._check(self.lib.fmm2d_plan_set_profiling(self._h, 1 if on else 0), "profiling")
+        """on: False/0 off, True/1 stage events, 2 stage events with the stages serialised."""
+        self._check(self.lib.fmm2d_plan_set_profiling(self._h, int(on)), "profiling")
 
     set_profiling = fmm2d_plan_set_profiling
 

@@ -19,6 +19,8 @@ def uniform_square(n, seed, dtype=np.float64):
     """(xy[n, 2], u[n]) with xy uniform in [0, 1)^2 and u uniform in [-1, 1]."""
     g = rng(seed)
     xy = g.random((n, 2)).astype(dtype)
+    # rounding to a narrower type can turn a value just below 1 into 1.0
+    xy = np.minimum(xy, np.nextafter(dtype(1.0), dtype(0.0)))
     u = g.uniform(-1.0, 1.0, n).astype(dtype)
     return xy, u
 
@@ -36,7 +38,10 @@ def gaussian_mixture(n, seed, k=32, sigma=(1e-3, 1e-1), dtype=np.float64, clip=T
         xy = np.mod(xy, 1.0)
         xy[xy >= 1.0] = np.nextafter(1.0, 0.0)
     u = g.standard_normal(n)
-    return xy.astype(dtype), u.astype(dtype)
+    xy = xy.astype(dtype)
+    if clip:   # rounding to a narrower type can turn a value just below 1 into 1.0
+        xy = np.minimum(xy, np.nextafter(dtype(1.0), dtype(0.0)))
+    return xy, u.astype(dtype)
 
 
 def sample_targets(m, count, seed):

@@ -90,6 +90,23 @@ def test_leaf_size_zero_is_the_uniform_tree(tiling, L):
     assert rel_inf_error(a, b) < 1e-12
 
 
+@pytest.mark.parametrize("tiling,L", [("quad", 10), ("sept", 6), ("tri", 10)])
+def test_shallow_leaf_beside_a_deep_cluster(tiling, L):
+    """A leaf on level 1 (a sparse corner) next to a cluster refined many
+    levels deep: the leaf's local expansion gets no M2L and must start at 0."""
+    g = np.random.default_rng(35)
+    sparse = 0.05 + 0.1 * g.random((12, 2))
+    dense = 0.7 + 2e-3 * g.standard_normal((4000, 2))
+    xy = np.concatenate([sparse, dense])
+    u = g.uniform(-1, 1, len(xy))
+    phi, plan = run_gpu(tiling, xy, u, levels=L, p=14, prec="fp64", leaf_size=32, keep=True)
+    cells = plan.export("ad_cells")
+    plan.close()
+    assert any(l == 1 and not sp for l, _, sp in cells.tolist())      # a level-1 leaf exists
+    ref = adaptive_fmm(make_tiling(tiling, L), xy, u, xy, 14, s=32).phi
+    assert rel_inf_error(phi, ref) < 1e-11
+
+
 def test_edge_cases():
     from paper_1204_3105_gb300 import fmm2d
     # a single point, all points in one cell, and fewer points than the leaf size
