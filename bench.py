@@ -401,6 +401,77 @@ def _pool(n_max, seed):
     return (uxy, uu), (gxy, gu.astype(np.float32))
 
 
+def run_clustered(args):
+    """The clustered workload: N = M = 4,194,304 points from a 32-component
+    Gaussian mixture, strengths N(0, 1), FP64, eps = 1e-10, quadtree and
+    septree on adaptive trees (leaf size 64).  One step = build + evaluate of
+    both tilings; device time with CUDA events, inputs resident."""
+    import torch
+    from paper_1204_3105_gb300 import fmm2d
+    from paper_1204_3105_gb300.inputs import gaussian_mixture
+    fmm2d.lib()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    n = 4194304
+    xy, u = gaussian_mixture(n, seed=3, k=32)
+    xy_d = torch.from_numpy(xy).to(dev)
+    u_d = torch.from_numpy(u).to(dev)
+    out = torch.empty(n, dtype=torch.float64, device=dev)
+    names = ("quad", "sept")
+    plans = {}
+    for t in names:
+        plans[t] = fmm2d.Plan(t, 0, 0, 1e-10, fmm2d.PREC_FP64 | fmm2d.ADAPTIVE)
+        plans[t].set_leaf_size(args.leaf_size)
+    flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device=dev)
+
+    def step(times):
+        for t in names:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plans[t].build(xy_d, n, xy_d, n, stream)
+            plans[t].evaluate(u_d, out, stream)
+            e1.record(stream)
+            times.append((t, e0, e1))
+            flush.zero_()
+
+    for _ in range(args.warmup):
+        step([])
+    torch.cuda.synchronize()
+    times = []
+    with Clocks(0) as clk:
+        for _ in range(args.steps):
+            step(times)
+        torch.cuda.synchronize()
+    per = {t: [] for t in names}
+    for t, a, b in times:
+        per[t].append(a.elapsed_time(b))
+    for t in names:
+        plans[t].set_profiling(2)
+    step([])
+    torch.cuda.synchronize()
+    info = {t: plans[t].query() for t in names}
+    stages = {t: {k: v[0] for k, v in plans[t].stage_times().items()} for t in names}
+    ms = sum(statistics.mean(v) for v in per.values())
+    line = {
+        "metric": "clustered FMM points/s (4,194,304 points, 32-cluster mixture, eps=1e-10, FP64)",
+        "value": len(names) * n / (ms / 1e3), "unit": "points/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "N=M=4194304 Gaussian mixture (32 components, sigma log-uniform "
+                               "[1e-3, 1e-1]), strengths N(0,1) FP64, quad + sept, eps=1e-10, adaptive "
+                               "trees, leaf size %d" % args.leaf_size, "l2": "flushed between tilings"},
+        "per_tiling": {t: {"points_per_s": n / (statistics.mean(per[t]) / 1e3), "ms": statistics.mean(per[t]),
+                           "levels": info[t]["levels"], "p": info[t]["p"], "m2l": info[t]["n_m2l"],
+                           "p2p_pairs": info[t]["n_p2p_pairs"], "stages_ms_isolated": stages[t]}
+                       for t in names},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    for pl in plans.values():
+        pl.close()
+
+
 def run_forest_batch(args):
     """The 4096-instance batch as three forests (one per tiling): each forest is
     one fmm2d_build_forest + fmm2d_evaluate over all its instances.  Device
@@ -592,7 +663,7 @@ def main():
     ap.add_argument("--no-fp64-form", action="store_true", help="skip the plain FP64 GPU form")
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 form")
     ap.add_argument("--params", default="", help="fixed L and p per tiling, e.g. quad:7:12,sept:5:13")
-    ap.add_argument("--workload", default="fmm", choices=["fmm", "batch", "serve"])
+    ap.add_argument("--workload", default="fmm", choices=["fmm", "batch", "serve", "clustered"])
     ap.add_argument("--instances", type=int, default=4096, help="batch: number of instances")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: arrivals per second")
     ap.add_argument("--duration", type=float, default=1.0, help="serve: seconds of arrivals")
@@ -605,6 +676,9 @@ def main():
                     help="batch/serve: tree of each request (auto: adaptive for serve)")
     args = ap.parse_args()
     args.tilings = tuple(args.tilings.split(","))
+    if args.workload == "clustered" and args.impl != "reference":
+        run_clustered(args)
+        return
     if args.workload == "batch" and args.batch_mode == "forest" and args.impl != "reference":
         run_forest_batch(args)
         return

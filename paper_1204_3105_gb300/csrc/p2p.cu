@@ -1,11 +1,12 @@
 // p2p.cu - near-field direct sum (Sec. 2; the M(P2 s) term of App. A-C):
 //   phi_near(y_j) = sum over the sources x_i of {leaf(y_j)} u Neighbors(leaf)
 //                   of u_i log|y_j - x_i|,  skipping x_i == y_j.
-// Two forms: one warp per target leaf (k_p2p) for small leaves, and a
-// block-staged form (k_p2p_block) for large ones.  Points are stored relative to
-// their leaf centre, so differences keep full precision.  The FP32 form takes
-// log2(r^2) on the MUFU unit and scales by ln2/2 once per target; partial
-// sums are kept in a compensated (Kahan) running sum.
+// FP32 form (k_p2p_x2): packed f32x2 arithmetic, log2(r^2) on the MUFU unit,
+// scaled by ln2/2 once per target, compensated (Kahan) partial sums.  FP64
+// form: one warp per target leaf (k_p2p) for small leaves or CSR lists, and a
+// block-staged form (k_p2p_block) for large ones, with a table-driven log.
+// Points are stored relative to their leaf centre, so differences keep full
+// precision.
 #include "plan.h"
 
 namespace fmm2d {
@@ -15,23 +16,53 @@ namespace {
 constexpr int P2P_TH = 256;
 
 template <typename R> struct P2PTraits;
-template <> struct P2PTraits<float> {
-  using V4 = float4;
-  static constexpr double scale = 0.34657359027997264;   // ln2 / 2
-  // log2(r^2); r^2 = 0 (a coincident pair) contributes nothing
-  static __device__ __forceinline__ float lg(float r2) {
-    float y;   // MUFU lg2; r^2 is never subnormal here (zero or >= the floor)
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2));
-    return y;
+// FP64 natural logarithm, table driven (Tang, "Table-driven implementation of
+// the logarithm function in IEEE floating-point arithmetic", ACM TOMS 1990):
+// x = 2^k m with m in [1, 2); c = 1 + j/128 with j the top seven fraction bits
+// of m; log x = k ln2 + log c + log1p(t), t = (m - c)/c in [0, 1/128), and
+// log1p by its Taylor series to t^9 (truncation below 1e-22).  m - c is
+// exact; the table holds log c and 1/c, filled per block with the library's
+// log.  The result is within a few ulp of log x for every normal x > 0.
+__shared__ double2 s_logtab[128];
+
+__device__ __forceinline__ void logtab_init() {
+  for (int j = threadIdx.x; j < 128; j += blockDim.x) {
+    const double c = 1.0 + j * 0.0078125;
+    s_logtab[j] = make_double2(log(c), 1.0 / c);
   }
-  static __device__ __forceinline__ float lg_checked(float r2) { return r2 > 0.f ? lg(r2) : 0.f; }
-  static constexpr float floor_r2 = 1e-30f;
-};
+  __syncthreads();
+}
+
+__device__ __forceinline__ double log_tab(double x) {
+  // ln 2 split into its leading 32 significant bits (so k * LN2_HI is exact)
+  // and the rest, from ln 2 = sum 1/(i 2^i) evaluated to 60 digits
+  constexpr double LN2_HI = 0x1.62e42fee00000p-1;
+  constexpr double LN2_LO = 0x1.a39ef35793c76p-33;
+  const int hi = __double2hiint(x), lo = __double2loint(x);
+  const int k = (hi >> 20) - 1023;
+  const int j = (hi >> 13) & 127;
+  const double m = __hiloint2double((hi & 0x000FFFFF) | 0x3FF00000, lo);
+  const double c = __hiloint2double(0x3FF00000 | (j << 13), 0);
+  const double2 e = s_logtab[j];
+  const double t = (m - c) * e.y;
+  double s = 1.0 / 9.0;
+  s = fma(s, t, -1.0 / 8.0);
+  s = fma(s, t, 1.0 / 7.0);
+  s = fma(s, t, -1.0 / 6.0);
+  s = fma(s, t, 1.0 / 5.0);
+  s = fma(s, t, -1.0 / 4.0);
+  s = fma(s, t, 1.0 / 3.0);
+  s = fma(s, t, -1.0 / 2.0);
+  s = fma(s, t, 1.0);
+  const double dk = (double)k;
+  return fma(dk, LN2_HI, e.x) + fma(dk, LN2_LO, s * t);
+}
+
 template <> struct P2PTraits<double> {
   using V4 = double4_32a;
   static constexpr double scale = 0.5;
-  static __device__ __forceinline__ double lg_checked(double r2) { return r2 > 0.0 ? log(r2) : 0.0; }
-  static __device__ __forceinline__ double lg(double r2) { return log(r2); }
+  static __device__ __forceinline__ double lg_checked(double r2) { return r2 > 0.0 ? log_tab(r2) : 0.0; }
+  static __device__ __forceinline__ double lg(double r2) { return log_tab(r2); }
   static constexpr double floor_r2 = 1e-300;
 };
 
@@ -101,6 +132,7 @@ k_p2p(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_ids,
       const int *__restrict__ near_off, const int *__restrict__ near_src,
       const double2 *__restrict__ ctr, double *__restrict__ phi_near) {
   using T = P2PTraits<R>;
+  if constexpr (sizeof(R) == 8) logtab_init();   // before any thread leaves
   const int lane = threadIdx.x & 31;
   const int64_t li = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (li >= n_leaves) return;
@@ -174,6 +206,7 @@ k_p2p_block(int64_t leaf_first, const R *__restrict__ src4, const R *__restrict_
   __shared__ int m_s0[NEAR_MAX], m_cnt[NEAR_MAX], m_base[NEAR_MAX + 1];
   __shared__ R m_dx[NEAR_MAX], m_dy[NEAR_MAX];
   const int tid = threadIdx.x;
+  if constexpr (sizeof(R) == 8) logtab_init();   // before any thread leaves
   const int64_t li = blockIdx.x;
   const int64_t g = leaf_first + li;
   const int ts = tst[g], te = ten[g];
@@ -503,8 +536,9 @@ cudaError_t launch_p2p(int64_t leaf_first, int64_t n_leaves, const int *leaf_ids
   if (n_leaves <= 0) return cudaSuccess;
   if constexpr (sizeof(R) == 4) {
     // group size: the smallest T for which a leaf of mean + 2 sigma (Poisson)
-    // targets still gets two source slices per target quadruple
-    const double want = 0.5 * (mean_targets + 2.0 * sqrt(mean_targets));
+    // targets still gets about three source slices per target quadruple (so
+    // that a group's lanes stay busy whatever the leaf's exact size)
+    const double want = 0.75 * (mean_targets + 2.0 * sqrt(mean_targets));
     const int T = want <= 32 ? 32 : want <= 64 ? 64 : want <= 128 ? 128 : 256;
     const int G = P2P_TH / T;
     const unsigned blocks = (unsigned)((n_leaves + G - 1) / G);
