@@ -1082,7 +1082,9 @@ fmm2d_status evaluate_adaptive_t(fmm2d_plan *pl, const void *u, double *out, cud
     CK(launch_p2p<R>(0, pl->n_leaves_ad, (const int *)pl->d_leaf_ids.p, src4, tgt, tstride, c.ss,
                      c.se, c.ts, c.te, nullptr, (const int *)pl->d_u_off.p,
                      (const int *)pl->d_u_src.p, c.ctr, (double *)pl->d_phi_near.p,
-                     pl->n_leaves_ad > 0 ? (double)pl->n_tgt / (double)pl->n_leaves_ad : 0.0, s),
+                     // the group size follows the leaf size, not the data, so that a
+                     // leaf's sum does not depend on the other leaves (or instances)
+                     (double)std::max(1, pl->leaf_cap), s),
        "p2p");
   }
   if (f != s) {   // join: M2P and L2P need the expansions

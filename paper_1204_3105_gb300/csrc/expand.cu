@@ -83,16 +83,20 @@ k_p2m(ExpandArgs a, const R *__restrict__ src4, const int *__restrict__ start,
   }
 }
 
-// One warp per parent cell; lane owns output coefficients lane+1, lane+33.
-template <typename R>
+// H lanes per parent cell (a warp, or half a warp when p < 16 so that no lane
+// idles); lane i of the group owns output coefficients i+1 and i+1+H.
+template <typename R, int H>
 __global__ void __launch_bounds__(32 * WPB)
 k_m2m(ExpandArgs a, Geo g, int level, int64_t first, int64_t count, const int *__restrict__ map,
       const uint32_t *__restrict__ cell_key, const uint8_t *__restrict__ cell_cls,
       const uint8_t *__restrict__ cell_hsrc, const Cx<R> *__restrict__ ops,
       double *__restrict__ mQ, Cx<R> *__restrict__ ma) {
-  __shared__ Cx<R> sh[WPB][MAXP + 1];
+  constexpr int CPW = 32 / H;
+  __shared__ Cx<R> sh[WPB * CPW][MAXP + 1];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t ci = blockIdx.x * (int64_t)WPB + w;
+  const int li = lane % H, sub = lane / H, slot = w * CPW + sub;
+  const unsigned mask = H == 32 ? 0xffffffffu : (0xffffu << (16 * sub));
+  const int64_t ci = (blockIdx.x * (int64_t)WPB + w) * CPW + sub;
   if (ci >= count) return;
   const int64_t gp = first + ci;
   if (a.child_first && a.child_cnt[gp] == 0) return;   // adaptive leaf: keeps its P2M
@@ -107,39 +111,43 @@ k_m2m(ExpandArgs a, Geo g, int level, int64_t first, int64_t count, const int *_
                              : map[g.map_off[level + 1] + (int64_t)key * g.b + d];
       if (cs < 0 || !cell_hsrc[cs]) continue;
       const double Qc = mQ[cs];
-      for (int k = lane; k < p; k += 32) sh[w][k + 1] = ma[(int64_t)cs * a.P + k];
-      __syncwarp();
+      for (int k = li; k < p; k += H) sh[slot][k + 1] = ma[(int64_t)cs * a.P + k];
+      __syncwarp(mask);
       const Cx<R> *op = ops + (int64_t)cell_cls[cs] * P1 * P1;
       const R qc = (R)Qc;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int l = lane + 1 + 32 * h;
+      for (int h = 0; h < 64 / H; ++h) {
+        const int l = li + 1 + H * h;
         if (l > p) break;
         const Cx<R> *row = op + (int64_t)l * P1;
         Cx<R> s = qc * row[0];
-        for (int k = 1; k <= l; ++k) cfma(s, row[k], sh[w][k]);
+        for (int k = 1; k <= l; ++k) cfma(s, row[k], sh[slot][k]);
         if (h == 0) acc0 = acc0 + s; else acc1 = acc1 + s;
       }
       Q += Qc;
-      __syncwarp();
+      __syncwarp(mask);
     }
   }
-  if (lane == 0) mQ[gp] = Q;
-  if (lane + 1 <= p) ma[gp * a.P + lane] = acc0;
-  if (lane + 33 <= p) ma[gp * a.P + lane + 32] = acc1;
+  if (li == 0) mQ[gp] = Q;
+  if (li + 1 <= p) ma[gp * a.P + li] = acc0;
+  if (li + 1 + H <= p) ma[gp * a.P + li + H] = acc1;
 }
 
-// One warp per target cell; lane owns local coefficients lane and lane+32.
-template <typename R>
+// H lanes per target cell (half a warp when p < 16); lane i of the group owns
+// local coefficients i and i+H.
+template <typename R, int H>
 __global__ void __launch_bounds__(32 * WPB)
 k_m2l(ExpandArgs a, int64_t first, int64_t count, const int64_t *__restrict__ lev_first,
       const double *__restrict__ log_abs_scale, const int *__restrict__ far_cnt,
       const int *__restrict__ far_src, const uint16_t *__restrict__ far_op,
       const Cx<R> *__restrict__ ops, const double *__restrict__ logz, const double *__restrict__ mQ,
       const Cx<R> *__restrict__ ma, double *__restrict__ lL0, Cx<R> *__restrict__ lb) {
-  __shared__ Cx<R> sh[WPB][MAXP + 1];
+  constexpr int CPW = 32 / H;
+  __shared__ Cx<R> sh[WPB * CPW][MAXP + 1];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t fi = blockIdx.x * (int64_t)WPB + w;
+  const int li = lane % H, sub = lane / H, slot = w * CPW + sub;
+  const unsigned mask = H == 32 ? 0xffffffffu : (0xffffu << (16 * sub));
+  const int64_t fi = (blockIdx.x * (int64_t)WPB + w) * CPW + sub;
   if (fi >= count) return;
   const int64_t gt = first + fi;
   int l = a.l_min;
@@ -153,36 +161,40 @@ k_m2l(ExpandArgs a, int64_t first, int64_t count, const int64_t *__restrict__ le
     const int s = far_src[fi * FAR_MAX + e];
     const int op = far_op[fi * FAR_MAX + e];
     const double Qs = mQ[s];
-    for (int k = lane; k < p; k += 32) sh[w][k + 1] = ma[(int64_t)s * a.P + k];
-    __syncwarp();
+    for (int k = li; k < p; k += H) sh[slot][k + 1] = ma[(int64_t)s * a.P + k];
+    __syncwarp(mask);
     const Cx<R> *T = ops + (int64_t)op * P1 * P1;
     const R qs = (R)Qs;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int ll = lane + 32 * h;
+    for (int h = 0; h < 64 / H; ++h) {
+      const int ll = li + H * h;
       if (ll > p) break;
       const Cx<R> *row = T + (int64_t)ll * P1;
       Cx<R> t = qs * row[0];
-      for (int k = 1; k <= p; ++k) cfma(t, row[k], sh[w][k]);
+      for (int k = 1; k <= p; ++k) cfma(t, row[k], sh[slot][k]);
       if (h == 0) acc0 = acc0 + t; else acc1 = acc1 + t;
     }
-    if (lane == 0) L0 += Qs * (ls + logz[op]);
-    __syncwarp();
+    if (li == 0) L0 += Qs * (ls + logz[op]);
+    __syncwarp(mask);
   }
-  if (lane == 0) lL0[gt] = L0 + (double)acc0.x;
-  if (lane >= 1 && lane <= p) lb[gt * a.P + lane - 1] = acc0;
-  if (lane + 32 <= p) lb[gt * a.P + lane + 31] = acc1;
+  if (li == 0) lL0[gt] = L0 + (double)acc0.x;
+  if (li >= 1 && li <= p) lb[gt * a.P + li - 1] = acc0;
+  if (li + H <= p) lb[gt * a.P + li + H - 1] = acc1;
 }
 
-// One warp per child cell of `level`; adds the shifted parent local.
-template <typename R>
+// H lanes per child cell (half a warp when p < 16); adds the shifted parent
+// local; lane i of the group owns coefficients i and i+H.
+template <typename R, int H>
 __global__ void __launch_bounds__(32 * WPB)
 k_l2l(ExpandArgs a, Geo g, int level, int64_t first, int64_t count, const int *__restrict__ map,
       const uint32_t *__restrict__ cell_key, const uint8_t *__restrict__ cell_cls,
       const Cx<R> *__restrict__ ops, double *__restrict__ lL0, Cx<R> *__restrict__ lb) {
-  __shared__ Cx<R> sh[WPB][MAXP + 1];
+  constexpr int CPW = 32 / H;
+  __shared__ Cx<R> sh[WPB * CPW][MAXP + 1];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t ci = blockIdx.x * (int64_t)WPB + w;
+  const int li = lane % H, sub = lane / H, slot = w * CPW + sub;
+  const unsigned mask = H == 32 ? 0xffffffffu : (0xffffu << (16 * sub));
+  const int64_t ci = (blockIdx.x * (int64_t)WPB + w) * CPW + sub;
   if (ci >= count) return;
   const int64_t gc = first + ci;
   int ps;
@@ -194,16 +206,16 @@ k_l2l(ExpandArgs a, Geo g, int level, int64_t first, int64_t count, const int *_
     ps = map[g.map_off[level - 1] + pkey];
   }
   const int p = a.p, P1 = p + 1;
-  for (int k = lane; k < p; k += 32) sh[w][k + 1] = lb[(int64_t)ps * a.P + k];
-  __syncwarp();
+  for (int k = li; k < p; k += H) sh[slot][k + 1] = lb[(int64_t)ps * a.P + k];
+  __syncwarp(mask);
   const Cx<R> *U = ops + (int64_t)cell_cls[gc] * P1 * P1;
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int k = lane + 32 * h;
+  for (int h = 0; h < 64 / H; ++h) {
+    const int k = li + H * h;
     if (k > p) break;
     const Cx<R> *row = U + (int64_t)k * P1;
     Cx<R> s = {(R)0, (R)0};
-    for (int l = (k > 1 ? k : 1); l <= p; ++l) cfma(s, row[l], sh[w][l]);
+    for (int l = (k > 1 ? k : 1); l <= p; ++l) cfma(s, row[l], sh[slot][l]);
     if (k == 0) {
       lL0[gc] += lL0[ps] + (double)s.x;
     } else {
@@ -250,6 +262,7 @@ k_l2p(ExpandArgs a, const R *__restrict__ tgt, int tstride, const int *__restric
 }
 
 inline unsigned wblocks(int64_t n) { return (unsigned)((n + WPB - 1) / WPB); }
+inline unsigned hblocks(int64_t n) { return (unsigned)((n + 2 * WPB - 1) / (2 * WPB)); }
 
 }  // namespace
 
@@ -275,8 +288,12 @@ cudaError_t launch_m2m(const ExpandArgs &a, const Geo &g, int level, int64_t fir
                        const uint8_t *cell_hsrc, const Cx<R> *ops, double *mQ, Cx<R> *ma,
                        cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  k_m2m<R><<<wblocks(count), 32 * WPB, 0, s>>>(a, g, level, first, count, map, cell_key, cell_cls,
-                                                 cell_hsrc, ops, mQ, ma);
+  if (a.p < 16)
+    k_m2m<R, 16><<<hblocks(count), 32 * WPB, 0, s>>>(a, g, level, first, count, map, cell_key,
+                                                      cell_cls, cell_hsrc, ops, mQ, ma);
+  else
+    k_m2m<R, 32><<<wblocks(count), 32 * WPB, 0, s>>>(a, g, level, first, count, map, cell_key,
+                                                      cell_cls, cell_hsrc, ops, mQ, ma);
   return cudaGetLastError();
 }
 
@@ -286,8 +303,14 @@ cudaError_t launch_m2l(const ExpandArgs &a, int64_t first, int64_t count, const 
                        const uint16_t *far_op, const Cx<R> *ops, const double *logz,
                        const double *mQ, const Cx<R> *ma, double *lL0, Cx<R> *lb, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  k_m2l<R><<<wblocks(count), 32 * WPB, 0, s>>>(a, first, count, lev_first, log_abs_scale, far_cnt,
-                                                 far_src, far_op, ops, logz, mQ, ma, lL0, lb);
+  if (a.p < 16)
+    k_m2l<R, 16><<<hblocks(count), 32 * WPB, 0, s>>>(a, first, count, lev_first, log_abs_scale,
+                                                      far_cnt, far_src, far_op, ops, logz, mQ, ma,
+                                                      lL0, lb);
+  else
+    k_m2l<R, 32><<<wblocks(count), 32 * WPB, 0, s>>>(a, first, count, lev_first, log_abs_scale,
+                                                      far_cnt, far_src, far_op, ops, logz, mQ, ma,
+                                                      lL0, lb);
   return cudaGetLastError();
 }
 
@@ -296,8 +319,12 @@ cudaError_t launch_l2l(const ExpandArgs &a, const Geo &g, int level, int64_t fir
                        const int *map, const uint32_t *cell_key, const uint8_t *cell_cls,
                        const Cx<R> *ops, double *lL0, Cx<R> *lb, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  k_l2l<R><<<wblocks(count), 32 * WPB, 0, s>>>(a, g, level, first, count, map, cell_key, cell_cls,
-                                                 ops, lL0, lb);
+  if (a.p < 16)
+    k_l2l<R, 16><<<hblocks(count), 32 * WPB, 0, s>>>(a, g, level, first, count, map, cell_key,
+                                                      cell_cls, ops, lL0, lb);
+  else
+    k_l2l<R, 32><<<wblocks(count), 32 * WPB, 0, s>>>(a, g, level, first, count, map, cell_key,
+                                                      cell_cls, ops, lL0, lb);
   return cudaGetLastError();
 }
 

@@ -109,6 +109,24 @@ def test_forest_mixed_forms_within_eps(tiling, prec):
         assert rel_inf_error(phi[a:e], ref) < 1e-6, (i, e - a)
 
 
+@pytest.mark.parametrize("tiling", ["quad", "tri"])
+def test_forest_fp32_forms_equal_instances_alone(tiling):
+    """In the FP32 forms too, an instance in the forest gives bit for bit its
+    result alone (every per-leaf and per-cell sum depends on that leaf or
+    cell only)."""
+    xy, u, off = _batch(12, seed=43, lo=200, hi=4000)
+    x32, u32 = xy.astype(np.float32), u.astype(np.float32)
+    for prec in ("mixed", "tc"):
+        phi, plan = _forest(tiling, x32, u32, off, 12, prec=prec, cap=64, f32=True)
+        L = plan.query()["levels"]
+        plan.close()
+        for i in (0, 4, 9):
+            a, e = int(off[i]), int(off[i + 1])
+            alone, _ = run_gpu(tiling, x32[a:e], u32[a:e], levels=L, p=12, prec=prec, f32=True,
+                               leaf_size=64)
+            assert np.array_equal(phi[a:e], alone), (prec, i)
+
+
 def test_forest_argument_errors():
     from paper_1204_3105_gb300 import fmm2d
     t = _torch()
