@@ -65,6 +65,9 @@ typedef enum {
                                      leading Q log term, L_0 and the final sums in FP64 */
 #define FMM2D_PREC_MIXED_TC 0x2u  /* as MIXED, with M2L on the tensor cores
                                      (split hi/lo TF32 products, FP32 accumulation) */
+#define FMM2D_PREC_HYBRID   0x3u  /* FP64 expansions and translations (P2M ... L2P),
+                                     FP32 P2P with compensated sums: for tolerances
+                                     between about 1e-9 and 1e-6 */
 #define FMM2D_PREC_MASK     0x3u
 #define FMM2D_IN_F32        0x10u /* points and strengths are float32 (default float64) */
 #define FMM2D_ADAPTIVE      0x20u /* adaptive tree for clustered input: a cell is split
@@ -347,7 +350,8 @@ typedef struct {
                               FMM2D_ADAPTIVE (leaf size 64; levels = finest
                               level, 0 = the default); with no precision bit
                               the server uses the tensor-core mixed form for
-                              eps >= 1e-6 and FP64 below */
+                              eps >= 1e-6, the hybrid form down to 1e-9 and
+                              the FP64 form below */
   double eps;
   double domain[3];        /* x0, y0, S; S <= 0 means the unit square */
   const void *src_xy;      /* n_src interleaved points */

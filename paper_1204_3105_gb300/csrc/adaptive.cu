@@ -214,7 +214,8 @@ template <typename TI, typename TO>
 __global__ void k_ad_rel(const TI *__restrict__ xy, const uint32_t *__restrict__ perm,
                          int64_t n_leaves, const int *__restrict__ leaf_ids,
                          const int *__restrict__ start, const int *__restrict__ end,
-                         const double2 *__restrict__ ctr, TO *__restrict__ out, int stride) {
+                         const double2 *__restrict__ ctr, TO *__restrict__ out, int stride,
+                         float2 *__restrict__ lo) {
   const int lane = threadIdx.x & 31;
   const int64_t li = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (li >= n_leaves) return;
@@ -224,9 +225,11 @@ __global__ void k_ad_rel(const TI *__restrict__ xy, const uint32_t *__restrict__
     const uint32_t o = perm[i];
     const double x = (double)xy[2 * (int64_t)o], y = (double)xy[2 * (int64_t)o + 1];
     TO *dst = out + (int64_t)i * stride;
-    dst[0] = (TO)(x - c.x);
-    dst[1] = (TO)(y - c.y);
+    const double dx = x - c.x, dy = y - c.y;
+    dst[0] = (TO)dx;
+    dst[1] = (TO)dy;
     for (int q = 2; q < stride; ++q) dst[q] = (TO)0;
+    if (lo) lo[i] = make_float2((float)(dx - (double)(float)dx), (float)(dy - (double)(float)dy));
   }
 }
 
@@ -602,17 +605,17 @@ cudaError_t ad_launch_leaves(int64_t n_cells, const uint8_t *split, int *flag, i
 
 cudaError_t ad_launch_rel(bool f32_in, bool f32_out, const void *xy, const uint32_t *perm,
                           int64_t n_leaves, const int *leaf_ids, const int *start, const int *end,
-                          const double2 *ctr, void *out, int stride, cudaStream_t s) {
+                          const double2 *ctr, void *out, int stride, cudaStream_t s, float2 *lo) {
   if (n_leaves <= 0) return cudaSuccess;
   const unsigned b = nblk(n_leaves * 32, 256);
   if (f32_in && f32_out)
-    k_ad_rel<float, float><<<b, 256, 0, s>>>((const float *)xy, perm, n_leaves, leaf_ids, start, end, ctr, (float *)out, stride);
+    k_ad_rel<float, float><<<b, 256, 0, s>>>((const float *)xy, perm, n_leaves, leaf_ids, start, end, ctr, (float *)out, stride, lo);
   else if (f32_in)
-    k_ad_rel<float, double><<<b, 256, 0, s>>>((const float *)xy, perm, n_leaves, leaf_ids, start, end, ctr, (double *)out, stride);
+    k_ad_rel<float, double><<<b, 256, 0, s>>>((const float *)xy, perm, n_leaves, leaf_ids, start, end, ctr, (double *)out, stride, lo);
   else if (f32_out)
-    k_ad_rel<double, float><<<b, 256, 0, s>>>((const double *)xy, perm, n_leaves, leaf_ids, start, end, ctr, (float *)out, stride);
+    k_ad_rel<double, float><<<b, 256, 0, s>>>((const double *)xy, perm, n_leaves, leaf_ids, start, end, ctr, (float *)out, stride, lo);
   else
-    k_ad_rel<double, double><<<b, 256, 0, s>>>((const double *)xy, perm, n_leaves, leaf_ids, start, end, ctr, (double *)out, stride);
+    k_ad_rel<double, double><<<b, 256, 0, s>>>((const double *)xy, perm, n_leaves, leaf_ids, start, end, ctr, (double *)out, stride, lo);
   return cudaGetLastError();
 }
 

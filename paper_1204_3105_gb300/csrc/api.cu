@@ -354,7 +354,12 @@ fmm2d_status cuda_fail(fmm2d_plan *pl, cudaError_t e, const char *where) {
     if (_e != cudaSuccess) return cuda_fail(pl, _e, where); \
   } while (0)
 
-bool is_fp64(const fmm2d_plan *pl) { return (pl->flags & FMM2D_PREC_MASK) == FMM2D_PREC_FP64; }
+// FP64 expansions (the FP64 form and the hybrid form)
+bool is_fp64(const fmm2d_plan *pl) {
+  const unsigned pr = pl->flags & FMM2D_PREC_MASK;
+  return pr == FMM2D_PREC_FP64 || pr == FMM2D_PREC_HYBRID;
+}
+bool is_hybrid(const fmm2d_plan *pl) { return (pl->flags & FMM2D_PREC_MASK) == FMM2D_PREC_HYBRID; }
 
 struct StageScope {
   fmm2d_plan *pl;
@@ -556,6 +561,9 @@ fmm2d_status evaluate_t(fmm2d_plan *pl, const void *u, double *out, cudaStream_t
   {
     StageScope sc(pl, ST_OTHER, s, 1);
     CK(launch_gather_u<R>(u, f32_in, (const uint32_t *)pl->d_perm_s.p, pl->n_src, src4, s), "gather");
+    if (is_hybrid(pl))
+      CK(launch_gather_u<float>(u, f32_in, (const uint32_t *)pl->d_perm_s.p, pl->n_src,
+                                (float *)pl->d_src4f.p, s, true), "gather");
   }
   // fork: the far-field chain on the plan's high-priority stream f, P2P on s
   cudaStream_t f;
@@ -624,6 +632,18 @@ fmm2d_status evaluate_t(fmm2d_plan *pl, const void *u, double *out, cudaStream_t
   }
   {
     StageScope sc(pl, ST_P2P, s, 1);
+    if (is_hybrid(pl)) {   // FP32 P2P on the FP32 copies
+      const float *s4 = (const float *)pl->d_src4f.p;
+      CK(launch_p2p<float>(a.leaf_first, a.n_leaves, nullptr, s4,
+                           pl->same_sets ? s4 : (const float *)pl->d_tgt2f.p, tstride,
+                           (const int *)pl->d_src_start.p, (const int *)pl->d_src_end.p, tst, ten,
+                           (const int *)pl->d_near_cnt.p, nullptr, (const int *)pl->d_near_src.p,
+                           (const double2 *)pl->d_cell_ctr.p, (double *)pl->d_phi_near.p,
+                           a.n_leaves > 0 ? (double)pl->n_tgt / (double)a.n_leaves : 0.0, s,
+                           (const float2 *)pl->d_srclo.p,
+                           (const float2 *)(pl->same_sets ? pl->d_srclo.p : pl->d_tgtlo.p)),
+         "p2p");
+    } else
     CK(launch_p2p<R>(a.leaf_first, a.n_leaves, nullptr, src4, tgt, tstride,
                      (const int *)pl->d_src_start.p, (const int *)pl->d_src_end.p, tst, ten,
                      (const int *)pl->d_near_cnt.p, nullptr, (const int *)pl->d_near_src.p,
@@ -840,6 +860,18 @@ static fmm2d_status build_adaptive(fmm2d_plan *pl, const void *src, int64_t n_sr
     if (!pl->same_sets)
       CK(ad_launch_rel(f32, !f64, tgt, pt, n_leaves, (const int *)pl->d_leaf_ids.p, c.ts, c.te, c.ctr,
                        pl->d_tgt2.p, 2, s), "rel");
+    if (is_hybrid(pl)) {   // FP32 hi + lo copies for the P2P
+      CK(dbuf_reserve(pl->d_src4f, std::max<int64_t>(1, n_src) * 16), "alloc");
+      CK(dbuf_reserve(pl->d_srclo, std::max<int64_t>(1, n_src) * 8), "alloc");
+      CK(ad_launch_rel(f32, true, src, ps, n_leaves, (const int *)pl->d_leaf_ids.p, c.ss, c.se, c.ctr,
+                       pl->d_src4f.p, 4, s, (float2 *)pl->d_srclo.p), "rel");
+      if (!pl->same_sets) {
+        CK(dbuf_reserve(pl->d_tgt2f, std::max<int64_t>(1, n_tgt) * 8), "alloc");
+        CK(dbuf_reserve(pl->d_tgtlo, std::max<int64_t>(1, n_tgt) * 8), "alloc");
+        CK(ad_launch_rel(f32, true, tgt, pt, n_leaves, (const int *)pl->d_leaf_ids.p, c.ts, c.te,
+                         c.ctr, pl->d_tgt2f.p, 2, s, (float2 *)pl->d_tgtlo.p), "rel");
+      }
+    }
   }
   // ---- lists
   const int64_t far_first = depth >= pl->l_min ? lf[pl->l_min] : n_cells;
@@ -993,6 +1025,9 @@ fmm2d_status evaluate_adaptive_t(fmm2d_plan *pl, const void *u, double *out, cud
   {
     StageScope sc(pl, ST_OTHER, s, 1);
     CK(launch_gather_u<R>(u, f32_in, (const uint32_t *)pl->d_perm_s.p, pl->n_src, src4, s), "gather");
+    if (is_hybrid(pl))
+      CK(launch_gather_u<float>(u, f32_in, (const uint32_t *)pl->d_perm_s.p, pl->n_src,
+                                (float *)pl->d_src4f.p, s, true), "gather");
   }
   cudaStream_t f;   // far-field chain on the plan's stream, P2P on s
   CK(far_stream(pl, &f), "far stream");
@@ -1079,6 +1114,16 @@ fmm2d_status evaluate_adaptive_t(fmm2d_plan *pl, const void *u, double *out, cud
   }
   {
     StageScope sc(pl, ST_P2P, s, 1);
+    if (is_hybrid(pl)) {   // FP32 P2P on the FP32 copies
+      const float *s4 = (const float *)pl->d_src4f.p;
+      CK(launch_p2p<float>(0, pl->n_leaves_ad, (const int *)pl->d_leaf_ids.p, s4,
+                           pl->same_sets ? s4 : (const float *)pl->d_tgt2f.p, tstride, c.ss, c.se,
+                           c.ts, c.te, nullptr, (const int *)pl->d_u_off.p,
+                           (const int *)pl->d_u_src.p, c.ctr, (double *)pl->d_phi_near.p,
+                           (double)std::max(1, pl->leaf_cap), s, (const float2 *)pl->d_srclo.p,
+                           (const float2 *)(pl->same_sets ? pl->d_srclo.p : pl->d_tgtlo.p)),
+         "p2p");
+    } else
     CK(launch_p2p<R>(0, pl->n_leaves_ad, (const int *)pl->d_leaf_ids.p, src4, tgt, tstride, c.ss,
                      c.se, c.ts, c.te, nullptr, (const int *)pl->d_u_off.p,
                      (const int *)pl->d_u_src.p, c.ctr, (double *)pl->d_phi_near.p,
@@ -1131,7 +1176,7 @@ fmm2d_status fmm2d_plan_create(int tiling, int levels, int p, double eps, unsign
   if (levels < 0 || levels > max_levels_for(tiling, flags)) { g_create_err = "levels out of range"; return FMM2D_EINVAL; }
   if (p < 0 || p > MAXP) { g_create_err = "p out of range (0..48)"; return FMM2D_EINVAL; }
   if (p == 0 && !(eps > 0.0 && eps < 1.0)) { g_create_err = "eps must be in (0, 1)"; return FMM2D_EINVAL; }
-  if ((flags & FMM2D_PREC_MASK) == 3u || (flags & ~(FMM2D_PREC_MASK | FMM2D_IN_F32 | FMM2D_ADAPTIVE)) != 0) {
+  if ((flags & ~(FMM2D_PREC_MASK | FMM2D_IN_F32 | FMM2D_ADAPTIVE)) != 0) {
     g_create_err = "unknown flags";
     return FMM2D_EINVAL;
   }
@@ -1320,6 +1365,22 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
       CK(launch_rel_coords(g, f32, !f64, tgt, pt, kt, n_tgt, (const int *)pl->d_map.p,
                            (const double2 *)pl->d_cell_ctr.p, pl->d_tgt2.p, 2,
                            (int *)pl->d_tgt_start.p, (int *)pl->d_tgt_end.p, s), "rel");
+    if (is_hybrid(pl)) {   // FP32 hi + lo copies for the P2P
+      CK(dbuf_reserve(pl->d_src4f, std::max<int64_t>(1, n_src) * 16), "alloc");
+      CK(dbuf_reserve(pl->d_srclo, std::max<int64_t>(1, n_src) * 8), "alloc");
+      CK(launch_rel_coords(g, f32, true, src, ps, ks, n_src, (const int *)pl->d_map.p,
+                           (const double2 *)pl->d_cell_ctr.p, pl->d_src4f.p, 4,
+                           (int *)pl->d_src_start.p, (int *)pl->d_src_end.p, s,
+                           (float2 *)pl->d_srclo.p), "rel");
+      if (!pl->same_sets) {
+        CK(dbuf_reserve(pl->d_tgt2f, std::max<int64_t>(1, n_tgt) * 8), "alloc");
+        CK(dbuf_reserve(pl->d_tgtlo, std::max<int64_t>(1, n_tgt) * 8), "alloc");
+        CK(launch_rel_coords(g, f32, true, tgt, pt, kt, n_tgt, (const int *)pl->d_map.p,
+                             (const double2 *)pl->d_cell_ctr.p, pl->d_tgt2f.p, 2,
+                             (int *)pl->d_tgt_start.p, (int *)pl->d_tgt_end.p, s,
+                             (float2 *)pl->d_tgtlo.p), "rel");
+      }
+    }
   }
   {
     StageScope sc(pl, ST_LISTS, s, 1);
@@ -1693,7 +1754,8 @@ void fmm2d_plan_destroy(fmm2d_plan *pl) {
                   &pl->d_ad_cnt, &pl->d_ad_off, &pl->d_ad_tot, &pl->d_ad_ta, &pl->d_ad_tc,
                   &pl->d_ad_sa, &pl->d_ad_sc, &pl->d_ad_ta2, &pl->d_ad_tc2, &pl->d_ad_sa2,
                   &pl->d_ad_sc2, &pl->d_ad_ut, &pl->d_ad_us, &pl->d_ad_wt, &pl->d_ad_ws,
-                  &pl->d_ad_xt, &pl->d_ad_xs, &pl->d_inst_off};
+                  &pl->d_ad_xt, &pl->d_ad_xs, &pl->d_inst_off, &pl->d_src4f, &pl->d_tgt2f, &pl->d_srclo,
+                  &pl->d_tgtlo};
   for (DBuf *b : bufs) dbuf_free(*b);
   if (pl->far_stream) {
     cudaStreamSynchronize(pl->far_stream);

@@ -28,14 +28,17 @@ __device__ __forceinline__ R warp_sum(R v) {
   return v;
 }
 
+// Strength of every sorted source into component 2 of its record; with lo,
+// the rounding residual u - (R)u goes to component 3 (hybrid P2P).
 template <typename R>
 __global__ void k_gather_u(const void *__restrict__ u, int f32_in, const uint32_t *__restrict__ perm,
-                           int64_t n, R *__restrict__ src4) {
+                           int64_t n, R *__restrict__ src4, int lo) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t o = perm[i];
   double v = f32_in ? (double)((const float *)u)[o] : ((const double *)u)[o];
   src4[4 * i + 2] = (R)v;
+  if (lo) src4[4 * i + 3] = (R)(v - (double)(R)v);
 }
 
 template <typename R, int KC>
@@ -83,8 +86,8 @@ k_p2m(ExpandArgs a, const R *__restrict__ src4, const int *__restrict__ start,
   }
 }
 
-// H lanes per parent cell (a warp, or half a warp when p < 16 so that no lane
-// idles); lane i of the group owns output coefficients i+1 and i+1+H.
+// H lanes per parent cell (the launcher uses a whole warp, H = 32); lane i of
+// the group owns output coefficients i+1 and i+1+H.
 template <typename R, int H>
 __global__ void __launch_bounds__(32 * WPB)
 k_m2m(ExpandArgs a, Geo g, int level, int64_t first, int64_t count, const int *__restrict__ map,
@@ -133,7 +136,7 @@ k_m2m(ExpandArgs a, Geo g, int level, int64_t first, int64_t count, const int *_
   if (li + 1 + H <= p) ma[gp * a.P + li + H] = acc1;
 }
 
-// H lanes per target cell (half a warp when p < 16); lane i of the group owns
+// H lanes per target cell (the launcher uses H = 32); lane i of the group owns
 // local coefficients i and i+H.
 template <typename R, int H>
 __global__ void __launch_bounds__(32 * WPB)
@@ -182,7 +185,7 @@ k_m2l(ExpandArgs a, int64_t first, int64_t count, const int64_t *__restrict__ le
   if (li + H <= p) lb[gt * a.P + li + H - 1] = acc1;
 }
 
-// H lanes per child cell (half a warp when p < 16); adds the shifted parent
+// H lanes per child cell (the launcher uses H = 32); adds the shifted parent
 // local; lane i of the group owns coefficients i and i+H.
 template <typename R, int H>
 __global__ void __launch_bounds__(32 * WPB)
@@ -262,15 +265,15 @@ k_l2p(ExpandArgs a, const R *__restrict__ tgt, int tstride, const int *__restric
 }
 
 inline unsigned wblocks(int64_t n) { return (unsigned)((n + WPB - 1) / WPB); }
-inline unsigned hblocks(int64_t n) { return (unsigned)((n + 2 * WPB - 1) / (2 * WPB)); }
 
 }  // namespace
 
 template <typename R>
 cudaError_t launch_gather_u(const void *u, bool f32_in, const uint32_t *perm, int64_t n, R *src4,
-                            cudaStream_t s) {
+                            cudaStream_t s, bool lo) {
   if (n <= 0) return cudaSuccess;
-  k_gather_u<R><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(u, f32_in ? 1 : 0, perm, n, src4);
+  k_gather_u<R><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(u, f32_in ? 1 : 0, perm, n, src4,
+                                                            lo ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -288,12 +291,10 @@ cudaError_t launch_m2m(const ExpandArgs &a, const Geo &g, int level, int64_t fir
                        const uint8_t *cell_hsrc, const Cx<R> *ops, double *mQ, Cx<R> *ma,
                        cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  if (a.p < 16)
-    k_m2m<R, 16><<<hblocks(count), 32 * WPB, 0, s>>>(a, g, level, first, count, map, cell_key,
-                                                      cell_cls, cell_hsrc, ops, mQ, ma);
-  else
-    k_m2m<R, 32><<<wblocks(count), 32 * WPB, 0, s>>>(a, g, level, first, count, map, cell_key,
-                                                      cell_cls, cell_hsrc, ops, mQ, ma);
+  // a whole warp per cell: measured faster than two cells per warp (H = 16)
+  // even when half the lanes idle (p < 16)
+  k_m2m<R, 32><<<wblocks(count), 32 * WPB, 0, s>>>(a, g, level, first, count, map, cell_key,
+                                                    cell_cls, cell_hsrc, ops, mQ, ma);
   return cudaGetLastError();
 }
 
@@ -303,14 +304,9 @@ cudaError_t launch_m2l(const ExpandArgs &a, int64_t first, int64_t count, const 
                        const uint16_t *far_op, const Cx<R> *ops, const double *logz,
                        const double *mQ, const Cx<R> *ma, double *lL0, Cx<R> *lb, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  if (a.p < 16)
-    k_m2l<R, 16><<<hblocks(count), 32 * WPB, 0, s>>>(a, first, count, lev_first, log_abs_scale,
-                                                      far_cnt, far_src, far_op, ops, logz, mQ, ma,
-                                                      lL0, lb);
-  else
-    k_m2l<R, 32><<<wblocks(count), 32 * WPB, 0, s>>>(a, first, count, lev_first, log_abs_scale,
-                                                      far_cnt, far_src, far_op, ops, logz, mQ, ma,
-                                                      lL0, lb);
+  k_m2l<R, 32><<<wblocks(count), 32 * WPB, 0, s>>>(a, first, count, lev_first, log_abs_scale,
+                                                    far_cnt, far_src, far_op, ops, logz, mQ, ma,
+                                                    lL0, lb);
   return cudaGetLastError();
 }
 
@@ -319,12 +315,8 @@ cudaError_t launch_l2l(const ExpandArgs &a, const Geo &g, int level, int64_t fir
                        const int *map, const uint32_t *cell_key, const uint8_t *cell_cls,
                        const Cx<R> *ops, double *lL0, Cx<R> *lb, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  if (a.p < 16)
-    k_l2l<R, 16><<<hblocks(count), 32 * WPB, 0, s>>>(a, g, level, first, count, map, cell_key,
-                                                      cell_cls, ops, lL0, lb);
-  else
-    k_l2l<R, 32><<<wblocks(count), 32 * WPB, 0, s>>>(a, g, level, first, count, map, cell_key,
-                                                      cell_cls, ops, lL0, lb);
+  k_l2l<R, 32><<<wblocks(count), 32 * WPB, 0, s>>>(a, g, level, first, count, map, cell_key,
+                                                    cell_cls, ops, lL0, lb);
   return cudaGetLastError();
 }
 
@@ -340,7 +332,7 @@ cudaError_t launch_l2p(const ExpandArgs &a, const R *tgt, int tstride, const int
 
 #define INST(R)                                                                                   \
   template cudaError_t launch_gather_u<R>(const void *, bool, const uint32_t *, int64_t, R *,      \
-                                          cudaStream_t);                                          \
+                                          cudaStream_t, bool);                                    \
   template cudaError_t launch_p2m<R>(const ExpandArgs &, const R *, const int *, const int *,      \
                                      double *, Cx<R> *, cudaStream_t);                            \
   template cudaError_t launch_m2m<R>(const ExpandArgs &, const Geo &, int, int64_t, int64_t,       \

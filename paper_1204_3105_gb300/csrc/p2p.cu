@@ -2,7 +2,7 @@
 //   phi_near(y_j) = sum over the sources x_i of {leaf(y_j)} u Neighbors(leaf)
 //                   of u_i log|y_j - x_i|,  skipping x_i == y_j.
 // FP32 form (k_p2p_x2): packed f32x2 arithmetic, log2(r^2) on the MUFU unit,
-// scaled by ln2/2 once per target, compensated (Kahan) partial sums.  FP64
+// scaled by ln2/2 once per target, partial sums folded without error.  FP64
 // form: one warp per target leaf (k_p2p) for small leaves or CSR lists, and a
 // block-staged form (k_p2p_block) for large ones, with a table-driven log.
 // Points are stored relative to their leaf centre, so differences keep full
@@ -307,7 +307,8 @@ k_p2p_block(int64_t leaf_first, const R *__restrict__ src4, const R *__restrict_
 // group, thread (i, k) takes target quadruple i and every K-th staged source
 // starting at k; slice partials are combined in FP32 with compensation and
 // converted to FP64 once per target.
-constexpr int X2_CAP = 1536;   // staged sources per block
+constexpr int X2_CAP = 1536;        // staged sources per block
+constexpr int X2_CAP_COMP = 640;    // hybrid form: hi and lo coordinates, split strengths
 
 template <int T>
 __device__ __forceinline__ void x2_sync(int grp) {
@@ -322,13 +323,13 @@ __device__ __forceinline__ float x2_lg(float r2) {
   return y;
 }
 
-// One staged source against the thread's four targets.  CHECK (the target's
-// own leaf): r^2 at the floor means the points coincide at FP32 resolution,
-// and the pair contributes nothing.
+// One staged source against the thread's four targets: log2 r^2 of the four
+// pairs.  CHECK (the target's own leaf): r^2 at the floor means the points
+// coincide at FP32 resolution, and the pair contributes nothing.
 template <bool CHECK>
-__device__ __forceinline__ void x2_source(const float4 &p, const float2 &u, const float2 &xab,
-                                          const float2 &xcd, const float2 &yab, const float2 &ycd,
-                                          float2 &acc_ab, float2 &acc_cd) {
+__device__ __forceinline__ void x2_logs(const float4 &p, const float2 &xab, const float2 &xcd,
+                                        const float2 &yab, const float2 &ycd, float2 &lab,
+                                        float2 &lcd) {
   constexpr float FL = 1e-30f;
   const float2 px = make_float2(p.x, p.y), py = make_float2(p.z, p.w);
   const float2 fl = make_float2(FL, FL);
@@ -336,7 +337,6 @@ __device__ __forceinline__ void x2_source(const float4 &p, const float2 &u, cons
   const float2 dyab = __fadd2_rn(yab, py), dycd = __fadd2_rn(ycd, py);
   const float2 rab = __ffma2_rn(dxab, dxab, __ffma2_rn(dyab, dyab, fl));
   const float2 rcd = __ffma2_rn(dxcd, dxcd, __ffma2_rn(dycd, dycd, fl));
-  float2 lab, lcd;
   lab.x = x2_lg(rab.x);
   lab.y = x2_lg(rab.y);
   lcd.x = x2_lg(rcd.x);
@@ -347,23 +347,145 @@ __device__ __forceinline__ void x2_source(const float4 &p, const float2 &u, cons
     lcd.x = rcd.x == FL ? 0.f : lcd.x;
     lcd.y = rcd.y == FL ? 0.f : lcd.y;
   }
+}
+
+// log2 of a mantissa m in [sqrt(1/2), sqrt(2)) in FP32 to a few ulp, from
+// ln m = 2 atanh(s) = 2 (s + s^3/3 + s^5/5 + ...), s = (m - 1)/(m + 1),
+// |s| < 0.172 (series truncated after s^11: below 2e-9 relative).
+__device__ __forceinline__ float x2_log2_mant(float m) {
+  const float s = __fdividef(m - 1.f, m + 1.f);
+  const float s2 = s * s;
+  float q = 1.f / 11.f;
+  q = fmaf(q, s2, 1.f / 9.f);
+  q = fmaf(q, s2, 1.f / 7.f);
+  q = fmaf(q, s2, 1.f / 5.f);
+  q = fmaf(q, s2, 1.f / 3.f);
+  q = fmaf(q, s2, 1.f);
+  return (2.f * 1.4426950408889634f) * (s * q);   // 2 s q / ln 2
+}
+
+// As x2_logs, with log2 r^2 split into its exact exponent e and the log2 of
+// the mantissa (reduced to [sqrt(1/2), sqrt(2))), computed in FP32 to a few
+// ulp instead of by the MUFU approximation; the two parts are accumulated
+// separately, so the FP32 rounding of e + log2 m never happens.
+template <bool CHECK>
+__device__ __forceinline__ void x2_logs_split(const float4 &p, const float4 &pl, const float2 &xab,
+                                              const float2 &xcd, const float2 &yab,
+                                              const float2 &ycd, const float2 &xlab,
+                                              const float2 &xlcd, const float2 &ylab,
+                                              const float2 &ylcd, float2 &eab, float2 &ecd,
+                                              float2 &lab, float2 &lcd) {
+  constexpr float FL = 1e-30f;
+  // coordinates as hi + lo floats: the differences keep ~48 bits
+  const float2 px = make_float2(p.x, p.y), py = make_float2(p.z, p.w);
+  const float2 pxl = make_float2(pl.x, pl.y), pyl = make_float2(pl.z, pl.w);
+  const float2 fl = make_float2(FL, FL);
+  const float2 dxab = __fadd2_rn(__fadd2_rn(xab, px), __fadd2_rn(xlab, pxl));
+  const float2 dxcd = __fadd2_rn(__fadd2_rn(xcd, px), __fadd2_rn(xlcd, pxl));
+  const float2 dyab = __fadd2_rn(__fadd2_rn(yab, py), __fadd2_rn(ylab, pyl));
+  const float2 dycd = __fadd2_rn(__fadd2_rn(ycd, py), __fadd2_rn(ylcd, pyl));
+  const float2 rab = __ffma2_rn(dxab, dxab, __ffma2_rn(dyab, dyab, fl));
+  const float2 rcd = __ffma2_rn(dxcd, dxcd, __ffma2_rn(dycd, dycd, fl));
+  const float r[4] = {rab.x, rab.y, rcd.x, rcd.y};
+  float e[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {   // r >= 1e-30: a normal number
+    const int b = __float_as_int(r[i]);
+    // mantissa in [sqrt(1/2), sqrt(2)): fraction bits above 0x3504F3 move to [1/2, 1)
+    const int hi = (b & 0x007FFFFF) > 0x003504F3;
+    e[i] = (float)((b >> 23) - 127 + hi);
+    l[i] = x2_log2_mant(__int_as_float((b & 0x007FFFFF) | (hi ? 0x3F000000 : 0x3F800000)));
+    if (CHECK && r[i] == FL) {
+      e[i] = 0.f;
+      l[i] = 0.f;
+    }
+  }
+  eab = make_float2(e[0], e[1]);
+  ecd = make_float2(e[2], e[3]);
+  lab = make_float2(l[0], l[1]);
+  lcd = make_float2(l[2], l[3]);
+}
+
+template <bool CHECK>
+__device__ __forceinline__ void x2_source(const float4 &p, const float2 &u, const float2 &xab,
+                                          const float2 &xcd, const float2 &yab, const float2 &ycd,
+                                          float2 &acc_ab, float2 &acc_cd) {
+  float2 lab, lcd;
+  x2_logs<CHECK>(p, xab, xcd, yab, ycd, lab, lcd);
   acc_ab = __ffma2_rn(u, lab, acc_ab);
   acc_cd = __ffma2_rn(u, lcd, acc_cd);
 }
 
-__device__ __forceinline__ void x2_kahan(float &s, float &c, float x) {
-  const float y = x - c;
-  const float t = s + y;
-  c = (t - s) - y;
+// Error-free accumulation (Knuth's TwoSum, exact whatever the magnitudes):
+// t = s + x, err = (s - (t - (t - s))) + (x - (t - s)); the errors are summed
+// in e.  The sum is s + e.
+__device__ __forceinline__ void x2_twosum(float2 &s, float2 &e, const float2 &x) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 t = __fadd2_rn(s, x);
+  const float2 bp = __ffma2_rn(s, m1, t);    // t - s
+  const float2 ap = __ffma2_rn(bp, m1, t);   // t - bp
+  const float2 da = __ffma2_rn(ap, m1, s);   // s - ap
+  const float2 db = __ffma2_rn(bp, m1, x);   // x - bp
+  e = __fadd2_rn(e, __fadd2_rn(da, db));
   s = t;
 }
 
-// Staged sources q0, q0 + K, ... < q1; partial sums of at most 64 sources
-// are folded into the compensated running sums.
-template <bool CHECK>
-__device__ __forceinline__ void x2_slice(const float4 *sxy, const float2 *su, int q0, int q1, int K,
-                                         const float2 &xab, const float2 &xcd, const float2 &yab,
-                                         const float2 &ycd, float (&s)[4], float (&c)[4]) {
+// Fold x into the running sum s + e without error (TwoSum; e collects the
+// rounding errors).  Used once per partial sum, so its cost does not matter.
+__device__ __forceinline__ void x2_kahan(float &s, float &e, float x) {
+  const float t = s + x;
+  const float bp = t - s;
+  const float ap = t - bp;
+  e += (s - ap) + (x - bp);
+  s = t;
+}
+
+// Staged sources q0, q0 + K, ... < q1.  Plain form: partial sums of at most
+// 64 sources are folded into the compensated running sums.  COMP (the hybrid
+// precision form): float-float differences, log2 r^2 split into exponent and
+// mantissa log, the exponent products made exact by splitting u, and every
+// term added error-free (TwoSum), which leaves the mantissa log (a few ulp)
+// as the only FP32 error: ~1e-9 relative instead of ~5e-8.
+template <bool CHECK, bool COMP>
+__device__ __forceinline__ void x2_slice(const float4 *sxy, const float4 *slo, const float2 *su,
+                                         const float4 *su4, int q0, int q1, int K, const float2 &xab,
+                                         const float2 &xcd, const float2 &yab, const float2 &ycd,
+                                         const float2 &xlab, const float2 &xlcd,
+                                         const float2 &ylab, const float2 &ylcd, float (&s)[4],
+                                         float (&c)[4]) {
+  if constexpr (COMP) {
+    float2 acc_ab = make_float2(0.f, 0.f), acc_cd = make_float2(0.f, 0.f);
+    float2 nc_ab = make_float2(0.f, 0.f), nc_cd = make_float2(0.f, 0.f);
+#pragma unroll 2
+    for (int q = q0; q < q1; q += K) {
+      float2 eab, ecd, lab, lcd;
+      x2_logs_split<CHECK>(sxy[q], slo[q], xab, xcd, yab, ycd, xlab, xlcd, ylab, ylcd, eab, ecd,
+                           lab, lcd);
+      // u = uh + um + ul with uh of 16 and um of 8 significant bits: uh e and
+      // um e are exact products, so the exponent part enters the sum unrounded;
+      // the residual ul (below 2^-24 u) multiplies the whole log
+      const float4 uu = su4[q];
+      const float2 uh = make_float2(uu.x, uu.y), um = make_float2(uu.z, uu.w), ul = su[q];
+      const float2 u = __fadd2_rn(uh, um);
+      x2_twosum(acc_ab, nc_ab, __fmul2_rn(uh, eab));
+      x2_twosum(acc_ab, nc_ab, __fmul2_rn(um, eab));
+      x2_twosum(acc_ab, nc_ab, __fmul2_rn(u, lab));
+      x2_twosum(acc_ab, nc_ab, __fmul2_rn(ul, __fadd2_rn(eab, lab)));
+      x2_twosum(acc_cd, nc_cd, __fmul2_rn(uh, ecd));
+      x2_twosum(acc_cd, nc_cd, __fmul2_rn(um, ecd));
+      x2_twosum(acc_cd, nc_cd, __fmul2_rn(u, lcd));
+      x2_twosum(acc_cd, nc_cd, __fmul2_rn(ul, __fadd2_rn(ecd, lcd)));
+    }
+    x2_kahan(s[0], c[0], acc_ab.x);
+    x2_kahan(s[1], c[1], acc_ab.y);
+    x2_kahan(s[2], c[2], acc_cd.x);
+    x2_kahan(s[3], c[3], acc_cd.y);
+    x2_kahan(s[0], c[0], nc_ab.x);
+    x2_kahan(s[1], c[1], nc_ab.y);
+    x2_kahan(s[2], c[2], nc_cd.x);
+    x2_kahan(s[3], c[3], nc_cd.y);
+    return;
+  }
   int q = q0;
   while (q < q1) {
     // two accumulator sets (even / odd sources) halve the loop-carried FFMA chain
@@ -388,20 +510,25 @@ __device__ __forceinline__ void x2_slice(const float4 *sxy, const float2 *su, in
   }
 }
 
-template <int T, bool CSR>
-__global__ void __launch_bounds__(P2P_TH, CSR ? 3 : 4)
+template <int T, bool CSR, bool COMP>
+__global__ void __launch_bounds__(P2P_TH, COMP ? 2 : (CSR ? 3 : 4))
 k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_ids,
          const float *__restrict__ src4, const float *__restrict__ tgt, int tstride,
+         const float2 *__restrict__ src_lo, const float2 *__restrict__ tgt_lo,
          const int *__restrict__ sst, const int *__restrict__ sen, const int *__restrict__ tst,
          const int *__restrict__ ten, const int *__restrict__ near_cnt,
          const int *__restrict__ near_off, const int *__restrict__ near_src,
          const double2 *__restrict__ ctr, double *__restrict__ phi_near) {
-  constexpr int G = P2P_TH / T, CAP = X2_CAP / G;
-  __shared__ float4 s_xy[X2_CAP];
-  __shared__ float2 s_u[X2_CAP];
+  constexpr int CAPB = COMP ? X2_CAP_COMP : X2_CAP;
+  constexpr int G = P2P_TH / T, CAP = CAPB / G;
+  __shared__ float4 s_xy[CAPB];
+  __shared__ float4 s_lo[COMP ? CAPB : 1];
+  __shared__ float2 s_u[CAPB];
+  __shared__ float4 s_u4[COMP ? CAPB : 1];   // (uh, uh, ul, ul): strength split in two
   __shared__ float s_red[2][4][P2P_TH];
   __shared__ int m_s0[G][NEAR_MAX], m_base[G][NEAR_MAX + 1];
   __shared__ float m_dx[G][NEAR_MAX], m_dy[G][NEAR_MAX];
+  __shared__ double m_dxd[COMP ? G : 1][NEAR_MAX], m_dyd[COMP ? G : 1][NEAR_MAX];
   const int grp = threadIdx.x / T, tg = threadIdx.x % T;
   const int64_t li = (int64_t)blockIdx.x * G + grp;
   if (li >= n_leaves) return;                 // group-uniform exits only
@@ -415,7 +542,9 @@ k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_ids,
   const int *nall = CSR ? near_src + near_off[li] : near_src + li * NEAR_MAX;
   const bool single = !CSR || n_all <= NEAR_MAX;
   float4 *sxy = s_xy + grp * CAP;
-  float2 *su = s_u + grp * CAP;
+  float4 *slo = COMP ? s_lo + grp * CAP : s_lo;
+  float2 *su = s_u + grp * CAP;   // (u, u); hybrid form: the residuals (ul, ul)
+  float4 *su4 = COMP ? s_u4 + grp * CAP : s_u4;
   const float4 *src = reinterpret_cast<const float4 *>(src4);
   const double2 cg = ctr[g];
   int nn = 0, total = 0;
@@ -428,6 +557,10 @@ k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_ids,
       m_base[grp][tg + 1] = sen[sl] - sst[sl];   // counts, prefix-summed below
       m_dx[grp][tg] = (float)(cs.x - cg.x);
       m_dy[grp][tg] = (float)(cs.y - cg.y);
+      if constexpr (COMP) {
+        m_dxd[grp][tg] = cs.x - cg.x;
+        m_dyd[grp][tg] = cs.y - cg.y;
+      }
     }
     x2_sync<T>(grp);
     if (tg == 0) {
@@ -448,9 +581,24 @@ k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_ids,
       const float dcx = m_dx[grp][e], dcy = m_dy[grp][e];
       for (int q = lo + tg; q < hi; q += T) {
         const float4 v = src[s0 + q];
-        const float x = -(v.x + dcx), y = -(v.y + dcy);
-        sxy[q - c0] = make_float4(x, x, y, y);
-        su[q - c0] = make_float2(v.z, v.z);
+        if constexpr (COMP) {   // the source in the target leaf's frame, as hi + lo
+          const float2 vl = src_lo[s0 + q];
+          const double X = ((double)v.x + (double)vl.x) + m_dxd[grp][e];
+          const double Y = ((double)v.y + (double)vl.y) + m_dyd[grp][e];
+          const float xh = (float)X, yh = (float)Y;
+          const float xl = (float)(X - (double)xh), yl = (float)(Y - (double)yh);
+          sxy[q - c0] = make_float4(-xh, -xh, -yh, -yh);
+          slo[q - c0] = make_float4(-xl, -xl, -yl, -yl);
+          // u = uh + um + ul: uh keeps 16 significant bits of the FP32 value,
+          // um its other 8, ul (component 3) the FP32 rounding residual
+          const float uh = __int_as_float(__float_as_int(v.z) & (int)0xFFFFFF00u), um = v.z - uh;
+          su4[q - c0] = make_float4(uh, uh, um, um);
+          su[q - c0] = make_float2(v.w, v.w);
+        } else {
+          const float x = -(v.x + dcx), y = -(v.y + dcy);
+          sxy[q - c0] = make_float4(x, x, y, y);
+          su[q - c0] = make_float2(v.z, v.z);
+        }
       }
     }
   };
@@ -470,6 +618,7 @@ k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_ids,
     const int i = tg % ng, k = tg / ng;
     const bool act = k < K;
     float2 xab, xcd, yab, ycd;
+    float2 xlab = make_float2(0.f, 0.f), xlcd = xlab, ylab = xlab, ylcd = xlab;
     {
       int j[4];
 #pragma unroll
@@ -478,6 +627,13 @@ k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_ids,
       yab = make_float2(tgt[(int64_t)j[0] * tstride + 1], tgt[(int64_t)j[1] * tstride + 1]);
       xcd = make_float2(tgt[(int64_t)j[2] * tstride], tgt[(int64_t)j[3] * tstride]);
       ycd = make_float2(tgt[(int64_t)j[2] * tstride + 1], tgt[(int64_t)j[3] * tstride + 1]);
+      if constexpr (COMP) {
+        const float2 l0 = tgt_lo[j[0]], l1 = tgt_lo[j[1]], l2 = tgt_lo[j[2]], l3 = tgt_lo[j[3]];
+        xlab = make_float2(l0.x, l1.x);
+        ylab = make_float2(l0.y, l1.y);
+        xlcd = make_float2(l2.x, l3.x);
+        ylcd = make_float2(l2.y, l3.y);
+      }
     }
     float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
     for (int b0 = 0; b0 < n_all; b0 += NEAR_MAX) {
@@ -497,8 +653,11 @@ k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_ids,
           const int m = c1 - c0;
           const int self_end = max(0, min(m, n_self - c0));
           const int first_unchecked = self_end + ((k - self_end) % K + K) % K;
-          if (self_end > 0) x2_slice<true>(sxy, su, k, self_end, K, xab, xcd, yab, ycd, s, c);
-          x2_slice<false>(sxy, su, first_unchecked, m, K, xab, xcd, yab, ycd, s, c);
+          if (self_end > 0)
+            x2_slice<true, COMP>(sxy, slo, su, su4, k, self_end, K, xab, xcd, yab, ycd, xlab, xlcd,
+                                 ylab, ylcd, s, c);
+          x2_slice<false, COMP>(sxy, slo, su, su4, first_unchecked, m, K, xab, xcd, yab, ycd, xlab,
+                                xlcd, ylab, ylcd, s, c);
         }
       }
     }
@@ -513,12 +672,12 @@ k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_ids,
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         if (i + r * ng >= ntc) continue;
-        float S = 0.f, C = 0.f, cs = 0.f;
+        float S = 0.f, E = 0.f, es = 0.f;
         for (int kk = 0; kk < K; ++kk) {
-          x2_kahan(S, C, s_red[0][r][base + kk * ng + i]);
-          cs += s_red[1][r][base + kk * ng + i];
+          x2_kahan(S, E, s_red[0][r][base + kk * ng + i]);
+          es += s_red[1][r][base + kk * ng + i];
         }
-        phi_near[t0 + i + r * ng] = ((double)S - (double)(C + cs)) * 0.34657359027997264;  // ln2/2
+        phi_near[t0 + i + r * ng] = ((double)S + ((double)E + (double)es)) * 0.34657359027997264;  // ln2/2
       }
     }
     x2_sync<T>(grp);
@@ -532,8 +691,10 @@ cudaError_t launch_p2p(int64_t leaf_first, int64_t n_leaves, const int *leaf_ids
                        const R *tgt, int tstride, const int *src_start, const int *src_end,
                        const int *tgt_start, const int *tgt_end, const int *near_cnt,
                        const int *near_off, const int *near_src, const double2 *ctr,
-                       double *phi_near, double mean_targets, cudaStream_t s) {
+                       double *phi_near, double mean_targets, cudaStream_t s, const float2 *src_lo,
+                       const float2 *tgt_lo) {
   if (n_leaves <= 0) return cudaSuccess;
+  const bool comp = src_lo != nullptr;
   if constexpr (sizeof(R) == 4) {
     // group size: the smallest T for which a leaf of mean + 2 sigma (Poisson)
     // targets still gets about three source slices per target quadruple (so
@@ -542,24 +703,24 @@ cudaError_t launch_p2p(int64_t leaf_first, int64_t n_leaves, const int *leaf_ids
     const int T = want <= 32 ? 32 : want <= 64 ? 64 : want <= 128 ? 128 : 256;
     const int G = P2P_TH / T;
     const unsigned blocks = (unsigned)((n_leaves + G - 1) / G);
+#define X2_LAUNCH_3(TT, CS, CP)                                                                   \
+  k_p2p_x2<TT, CS, CP><<<blocks, P2P_TH, 0, s>>>(leaf_first, n_leaves, leaf_ids, src4, tgt,         \
+                                                 tstride, src_lo, tgt_lo, src_start, src_end,      \
+                                                 tgt_start, tgt_end, near_cnt, near_off, near_src, \
+                                                 ctr, phi_near)
 #define X2_LAUNCH(TT)                                                                             \
   do {                                                                                            \
-    if (near_off)                                                                                 \
-      k_p2p_x2<TT, true><<<blocks, P2P_TH, 0, s>>>(leaf_first, n_leaves, leaf_ids, src4, tgt,     \
-                                                   tstride, src_start, src_end, tgt_start,        \
-                                                   tgt_end, near_cnt, near_off, near_src, ctr,    \
-                                                   phi_near);                                     \
-    else                                                                                          \
-      k_p2p_x2<TT, false><<<blocks, P2P_TH, 0, s>>>(leaf_first, n_leaves, leaf_ids, src4, tgt,    \
-                                                    tstride, src_start, src_end, tgt_start,       \
-                                                    tgt_end, near_cnt, near_off, near_src, ctr,   \
-                                                    phi_near);                                    \
+    if (near_off && comp) X2_LAUNCH_3(TT, true, true);                                            \
+    else if (near_off) X2_LAUNCH_3(TT, true, false);                                              \
+    else if (comp) X2_LAUNCH_3(TT, false, true);                                                  \
+    else X2_LAUNCH_3(TT, false, false);                                                           \
   } while (0)
     if (T == 32) X2_LAUNCH(32);
     else if (T == 64) X2_LAUNCH(64);
     else if (T == 128) X2_LAUNCH(128);
     else X2_LAUNCH(256);
 #undef X2_LAUNCH
+#undef X2_LAUNCH_3
   } else if (mean_targets >= 48.0 && !near_off) {   // FP64, large leaves: block-staged
     k_p2p_block<R><<<(unsigned)n_leaves, P2P_TH, 0, s>>>(leaf_first, src4, tgt, tstride, src_start,
                                                          src_end, tgt_start, tgt_end, near_cnt,
@@ -576,10 +737,12 @@ cudaError_t launch_p2p(int64_t leaf_first, int64_t n_leaves, const int *leaf_ids
 template cudaError_t launch_p2p<float>(int64_t, int64_t, const int *, const float *,
                                        const float *, int, const int *, const int *, const int *,
                                        const int *, const int *, const int *, const int *,
-                                       const double2 *, double *, double, cudaStream_t);
+                                       const double2 *, double *, double, cudaStream_t,
+                                       const float2 *, const float2 *);
 template cudaError_t launch_p2p<double>(int64_t, int64_t, const int *, const double *,
                                         const double *, int, const int *, const int *, const int *,
                                         const int *, const int *, const int *, const int *,
-                                        const double2 *, double *, double, cudaStream_t);
+                                        const double2 *, double *, double, cudaStream_t,
+                                        const float2 *, const float2 *);
 
 }  // namespace fmm2d

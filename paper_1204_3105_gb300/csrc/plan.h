@@ -84,6 +84,8 @@ struct Plan {
   DBuf d_src_start, d_src_end, d_tgt_start, d_tgt_end, d_lev_first;
   DBuf d_far_cnt, d_far_src, d_far_op, d_near_cnt, d_near_src;
   DBuf d_src4, d_tgt2;
+  DBuf d_src4f, d_tgt2f;               // FP32 copies (high parts) for the P2P of FMM2D_PREC_HYBRID
+  DBuf d_srclo, d_tgtlo;               // their low parts (float2 per point)
   DBuf d_mQ, d_ma, d_lL0, d_lb;
   DBuf d_phi_near, d_phi_far;
   DBuf d_sten, d_geo_scale;
@@ -146,10 +148,11 @@ cudaError_t launch_compact(const Geo &g, const int *occ, const int *scan, const 
                            int *src_start, int *src_end, int *tgt_start, int *tgt_end,
                            int64_t *lev_first, cudaStream_t s);
 // Sorted points relative to their leaf centre, and the leaves' point ranges.
+// lo (optional): the low parts (leaf-relative coordinate minus its FP32 value).
 cudaError_t launch_rel_coords(const Geo &g, bool f32_in, bool f32_out, const void *xy,
                               const uint32_t *perm, const uint32_t *key_sorted, int64_t n,
                               const int *map, const double2 *ctr, void *out, int out_stride,
-                              int *start, int *end, cudaStream_t s);
+                              int *start, int *end, cudaStream_t s, float2 *lo = nullptr);
 // Near lists of the leaves and M2L lists of levels >= l_min, for the cells
 // of levels lo_level..L (count read on the device; cap = launch bound).
 cudaError_t launch_lists(const Geo &g, const Stencils *d_sten, int lo_level, int l_min, int64_t cap,
@@ -192,7 +195,8 @@ cudaError_t ad_launch_leaves(int64_t n_cells, const uint8_t *split, int *flag, i
                              cudaStream_t s);
 cudaError_t ad_launch_rel(bool f32_in, bool f32_out, const void *xy, const uint32_t *perm,
                           int64_t n_leaves, const int *leaf_ids, const int *start, const int *end,
-                          const double2 *ctr, void *out, int stride, cudaStream_t s);
+                          const double2 *ctr, void *out, int stride, cudaStream_t s,
+                          float2 *lo = nullptr);
 // count pass of one level's traversal; totals[5] = U, W, X, next W tests, next X tests
 cudaError_t ad_launch_lists(const Geo &g, const Stencils *d_sten, int l, int l_min, int64_t first,
                             int64_t count, int64_t n_t, int64_t n_s, const int *t_a, const int *t_c,
@@ -239,7 +243,7 @@ struct ExpandArgs {
 };
 template <typename R>
 cudaError_t launch_gather_u(const void *u, bool f32_in, const uint32_t *perm, int64_t n, R *src4,
-                            cudaStream_t s);
+                            cudaStream_t s, bool lo = false);
 template <typename R>
 cudaError_t launch_p2m(const ExpandArgs &a, const R *src4, const int *start, const int *end,
                        double *mQ, Cx<R> *ma, cudaStream_t s);
@@ -288,6 +292,9 @@ void tc_build_tables(const std::vector<double> &m2l_re, const std::vector<double
 cudaError_t launch_m2l_tc(const TcArgs &a, int K, int N, int64_t n_far_cells, cudaStream_t s);
 
 // ---------------------------------------------------------------- p2p.cu
+// src_lo / tgt_lo (FP32 form, hybrid precision): low parts of the points'
+// leaf-relative coordinates (hi + lo floats); with them every term is also
+// accumulated with compensation.
 // leaf_ids: null (leaves leaf_first + li) or the cell of leaf li; near lists
 // fixed-stride (near_off null: near_cnt[li], near_src[li * NEAR_MAX + e]) or
 // CSR (near_src[near_off[li] .. near_off[li + 1])).
@@ -296,6 +303,7 @@ cudaError_t launch_p2p(int64_t leaf_first, int64_t n_leaves, const int *leaf_ids
                        const R *tgt, int tstride, const int *src_start, const int *src_end,
                        const int *tgt_start, const int *tgt_end, const int *near_cnt,
                        const int *near_off, const int *near_src, const double2 *ctr,
-                       double *phi_near, double mean_targets, cudaStream_t s);
+                       double *phi_near, double mean_targets, cudaStream_t s,
+                       const float2 *src_lo = nullptr, const float2 *tgt_lo = nullptr);
 
 }  // namespace fmm2d

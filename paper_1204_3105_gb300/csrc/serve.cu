@@ -78,8 +78,10 @@ size_t estimate_bytes(const fmm2d_request &r) {
 }
 
 unsigned precision_for(double eps, int p) {
-  // FP32 arithmetic cannot reach tolerances much below 1e-7: FP64 form there
-  if (eps < 1e-6) return FMM2D_PREC_FP64;
+  // FP32 expansions cannot reach tolerances much below 1e-7: FP64 expansions
+  // with the FP32 P2P down to 1e-9, the FP64 form below
+  if (eps < 1e-9) return FMM2D_PREC_FP64;
+  if (eps < 1e-6) return FMM2D_PREC_HYBRID;
   return p <= 31 ? FMM2D_PREC_MIXED_TC : FMM2D_PREC_MIXED;
 }
 

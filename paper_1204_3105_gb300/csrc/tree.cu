@@ -74,7 +74,7 @@ template <typename TI, typename TO>
 __global__ void k_rel(Geo g, const TI *__restrict__ xy, const uint32_t *__restrict__ perm,
                       const uint32_t *__restrict__ key, int64_t n, const int *__restrict__ map,
                       const double2 *__restrict__ ctr, TO *__restrict__ out, int stride,
-                      int *__restrict__ start, int *__restrict__ end) {
+                      int *__restrict__ start, int *__restrict__ end, float2 *__restrict__ lo) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t o = perm[i];
@@ -85,9 +85,11 @@ __global__ void k_rel(Geo g, const TI *__restrict__ xy, const uint32_t *__restri
   double2 c = ctr[slot];
   double x = (double)xy[2 * (int64_t)o], y = (double)xy[2 * (int64_t)o + 1];
   TO *dst = out + i * stride;
-  dst[0] = (TO)(x - c.x);
-  dst[1] = (TO)(y - c.y);
+  const double dx = x - c.x, dy = y - c.y;
+  dst[0] = (TO)dx;
+  dst[1] = (TO)dy;
   for (int q = 2; q < stride; ++q) dst[q] = (TO)0;
+  if (lo) lo[i] = make_float2((float)(dx - (double)(float)dx), (float)(dy - (double)(float)dy));
 }
 
 // One warp per cell: lane e looks up stencil entry e (and e + 32), and a
@@ -186,17 +188,17 @@ cudaError_t launch_compact(const Geo &g, const int *occ, const int *scan, const 
 cudaError_t launch_rel_coords(const Geo &g, bool f32_in, bool f32_out, const void *xy,
                               const uint32_t *perm, const uint32_t *key_sorted, int64_t n,
                               const int *map, const double2 *ctr, void *out, int out_stride,
-                              int *start, int *end, cudaStream_t s) {
+                              int *start, int *end, cudaStream_t s, float2 *lo) {
   if (n <= 0) return cudaSuccess;
   unsigned b = nblk(n, 256);
   if (f32_in && f32_out)
-    k_rel<float, float><<<b, 256, 0, s>>>(g, (const float *)xy, perm, key_sorted, n, map, ctr, (float *)out, out_stride, start, end);
+    k_rel<float, float><<<b, 256, 0, s>>>(g, (const float *)xy, perm, key_sorted, n, map, ctr, (float *)out, out_stride, start, end, lo);
   else if (f32_in)
-    k_rel<float, double><<<b, 256, 0, s>>>(g, (const float *)xy, perm, key_sorted, n, map, ctr, (double *)out, out_stride, start, end);
+    k_rel<float, double><<<b, 256, 0, s>>>(g, (const float *)xy, perm, key_sorted, n, map, ctr, (double *)out, out_stride, start, end, lo);
   else if (f32_out)
-    k_rel<double, float><<<b, 256, 0, s>>>(g, (const double *)xy, perm, key_sorted, n, map, ctr, (float *)out, out_stride, start, end);
+    k_rel<double, float><<<b, 256, 0, s>>>(g, (const double *)xy, perm, key_sorted, n, map, ctr, (float *)out, out_stride, start, end, lo);
   else
-    k_rel<double, double><<<b, 256, 0, s>>>(g, (const double *)xy, perm, key_sorted, n, map, ctr, (double *)out, out_stride, start, end);
+    k_rel<double, double><<<b, 256, 0, s>>>(g, (const double *)xy, perm, key_sorted, n, map, ctr, (double *)out, out_stride, start, end, lo);
   return cudaGetLastError();
 }
 

@@ -127,6 +127,33 @@ def test_forest_fp32_forms_equal_instances_alone(tiling):
             assert np.array_equal(phi[a:e], alone), (prec, i)
 
 
+def test_batch_workload_full_size_sampled():
+    """The 4096-instance batch exactly as bench.py runs it (same instance
+    sizes, tilings, seeds, leaf size 64, tensor-core form), on sampled
+    instances and targets against the direct sum over each instance."""
+    from paper_1204_3105_gb300.inputs import rng, uniform_square as us
+    g = rng(2 + 40)
+    count = 4096
+    sizes = np.exp(g.uniform(np.log(256), np.log(65536), count)).astype(np.int64)
+    tilings = g.integers(0, 3, count)
+    for ti, name in enumerate(("quad", "sept", "tri")):
+        idx = np.nonzero(tilings == ti)[0]
+        pts = [us(int(sizes[i]), seed=1000 + int(i), dtype=np.float32) for i in idx]
+        off = np.concatenate([[0], np.cumsum(sizes[idx])]).astype(np.int64)
+        xy = np.concatenate([q[0] for q in pts])
+        u = np.concatenate([q[1] for q in pts])
+        phi, plan = _forest(name, xy, u, off, {"quad": 12, "sept": 14, "tri": 14}[name], prec="tc",
+                            cap=64, f32=True)
+        plan.close()
+        sel = np.random.default_rng(ti).choice(len(idx), 6, replace=False)
+        for k in sel:
+            a, e = int(off[k]), int(off[k + 1])
+            x64, u64 = xy[a:e].astype(np.float64), u[a:e].astype(np.float64)
+            t = np.random.default_rng(int(k)).choice(e - a, min(64, e - a), replace=False)
+            ref = direct(x64, u64, x64[t])
+            assert rel_inf_error(phi[a:e][t], ref) < 1e-6, (name, int(k), e - a)
+
+
 def test_forest_argument_errors():
     from paper_1204_3105_gb300 import fmm2d
     t = _torch()

@@ -200,3 +200,39 @@ def test_autotuned_benchmark_configuration(tiling):
     idx = sample_targets(n, 384, seed=7)
     ref = direct(x64, u.astype(np.float64), x64[idx])
     assert np.max(np.abs(phi[idx] - ref)) / np.max(np.abs(ref)) < 1e-6
+
+
+@pytest.mark.parametrize("tiling", ["quad", "sept", "tri"])
+def test_hybrid_form_eps_1e8(tiling):
+    """FMM2D_PREC_HYBRID (FP64 expansions, FP32 P2P): within 1e-8 of the
+    direct sum at the a-priori p for eps = 1e-8, on uniform FP32 points (the
+    P2P differences are then exact) and on a clustered set."""
+    from oracle.params import p_from_eps
+    p = p_from_eps(tiling, 1e-8)
+    xy, u = uniform_square(30000, seed=61, dtype=np.float32)
+    phi, _ = run_gpu(tiling, xy, u, p=p, eps=1e-8, prec="hybrid", f32=True)
+    idx = sample_targets(len(xy), 300, seed=1)
+    x64, u64 = xy.astype(np.float64), u.astype(np.float64)
+    ref = direct(x64, u64, x64[idx])
+    assert rel_inf_error(phi[idx], ref) < 1e-8
+    cxy, cu = gaussian_mixture(20000, seed=62, k=8)
+    phi, _ = run_gpu(tiling, cxy, cu, p=p, eps=1e-8, prec="hybrid", leaf_size=64)
+    cidx = sample_targets(len(cxy), 300, seed=2)
+    ref = direct(cxy, cu, cxy[cidx])
+    assert rel_inf_error(phi[cidx], ref) < 1e-8
+
+
+def test_plain_fp64_quadtree_8192():
+    """The plain FP64 quadtree configuration: N = M = 8192 uniform points,
+    strengths U[-1, 1], p = 16, 4 levels (leaf <= 64 on average): against the
+    oracle FMM of the same (L, p) to 1e-11 and the full direct sum within the
+    p = 16 truncation (reading of eq. 15: kappa^(p+1) ~ 4e-5 before the
+    cancellation of the far field)."""
+    xy, u = uniform_square(8192, seed=1)
+    phi, _ = run_gpu("quad", xy, u, levels=4, p=16, prec="fp64")
+    r, _ = _oracle("quad", 4, xy, u, None, 16)
+    assert rel_inf_error(phi, r.phi) < 1e-11
+    ref = direct(xy, u, xy)
+    err = rel_inf_error(phi, ref)
+    assert err < 1e-6
+    assert abs(err - rel_inf_error(r.phi, ref)) < 1e-9
