@@ -5,7 +5,10 @@ one full FMM - fmm2d_build (keys, sort, cells, lists) + fmm2d_evaluate
 (P2M, M2M, M2L, L2L, L2P, P2P) - over N = M = 2^20 seeded points uniform in
 the unit square (sources = targets), FP32 points and strengths uniform in
 [-1, 1], p and L from the planner for eps = 1e-6, mixed precision.
-value = 3 * M / (device time of one step), all ranks summed.
+The three FMMs of a step are independent and run on three streams (one
+tiling's build overlaps the evaluation of the one before it); --serial runs
+them one after another on one stream.  value = 3 * M / (device time of one
+step), all ranks summed.
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
 build) on a bounded sample of the same workload.
@@ -214,20 +217,50 @@ def run_ours(args):
             per[t].append((e0, e1))
             flush.zero_()
 
+    # the three tilings are independent problems: each runs on a stream of
+    # its own, so one tiling's build (latency-bound small kernels and one
+    # host read-back) overlaps the evaluation of the one before it
+    tstreams = {t: torch.cuda.Stream(device=dev) for t in args.tilings}
+
+    def step_concurrent(evs):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for t in args.tilings:
+            ts = tstreams[t]
+            ts.wait_event(e0)
+            plans[t].build(xy_d, N_POINTS, xy_d, N_POINTS, ts)
+            plans[t].evaluate(u_d, outs[t], ts)
+            d = torch.cuda.Event()
+            d.record(ts)
+            stream.wait_event(d)
+        e1.record(stream)
+        evs.append((e0, e1))
+        flush.zero_()
+
     warm = {t: [] for t in args.tilings}
     for _ in range(args.warmup):
         step(warm)
+        step_concurrent([])
     torch.cuda.synchronize()
     per = {t: [] for t in args.tilings}
+    whole = []
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
         for _ in range(args.steps):
-            step(per)
+            if args.serial:
+                step(per)
+            else:
+                step_concurrent(whole)
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    if not args.serial:   # per-tiling times: the same steps, one tiling after another
+        for _ in range(min(args.steps, 20)):
+            step(per)
+        torch.cuda.synchronize()
     tt = {t: [a.elapsed_time(b) for a, b in per[t]] for t in args.tilings}
     # stage split: a few more steps with per-stage CUDA events on the stream of
     # each stage (far-field stages concurrent with P2P, as in the timed steps;
@@ -249,7 +282,8 @@ def run_ours(args):
     for t in args.tilings:
         plans[t].set_profiling(0)
     info = {t: plans[t].query() for t in args.tilings}
-    ms_step = sum(statistics.mean(tt[t]) for t in args.tilings)
+    ms_serial = sum(statistics.mean(tt[t]) for t in args.tilings)
+    ms_step = ms_serial if args.serial else statistics.mean(a.elapsed_time(b) for a, b in whole)
     ms_step, value = replica_aggregate(dist, ms_step, len(args.tilings) * N_POINTS, ws, dev)
 
     # the plain FP64 GPU form on the same points, (L, p) tuned for the same eps
@@ -292,11 +326,15 @@ def run_ours(args):
         t0 = time.perf_counter()
         xd = xy_h.to(dev, non_blocking=True)
         ud = u_h.to(dev, non_blocking=True)
+        ready = torch.cuda.Event()
+        ready.record(stream)
         for t in args.tilings:
-            plans[t].build(xd, N_POINTS, xd, N_POINTS, stream)
-            plans[t].evaluate(ud, outs[t], stream)
+            ts = stream if args.serial else tstreams[t]
+            ts.wait_event(ready)
+            plans[t].build(xd, N_POINTS, xd, N_POINTS, ts)
+            plans[t].evaluate(ud, outs[t], ts)
             done = torch.cuda.Event()
-            done.record(stream)
+            done.record(ts)
             copy_stream.wait_event(done)
             with torch.cuda.stream(copy_stream):
                 res_h[t].copy_(outs[t], non_blocking=True)
@@ -363,8 +401,13 @@ def run_ours(args):
                                    "strengths, quad+sept+tri, eps=1e-6, %s L/p, %s form" % (
                                    "fixed" if args.params else "planner" if args.no_tune else "autotuned",
                                    args.prec),
-                       "global_batch": N_POINTS, "l2": "flushed between tilings (256 MB write)",
+                       "global_batch": N_POINTS,
+                       "l2": "flushed between tilings (256 MB write)" if args.serial else
+                             "flushed between steps (256 MB write)",
+                       "streams": "one tiling after another on one stream" if args.serial else
+                                  "the three tilings on three streams, joined at the end of the step",
                        "parallelism": "replicas" if ws > 1 else "single"},
+            "ms_per_step_serial": ms_serial,
             "per_tiling": {t: {"points_per_s": N_POINTS / (statistics.mean(tt[t]) / 1e3),
                                "ms": statistics.mean(tt[t]), "L": info[t]["levels"], "p": info[t]["p"],
                                "m2l": info[t]["n_m2l"], "p2p_pairs": info[t]["n_p2p_pairs"],
@@ -666,6 +709,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="a-priori L and p instead of fmm2d_autotune")
     ap.add_argument("--no-profile", action="store_true", help="no per-stage event pass")
     ap.add_argument("--no-fp64-form", action="store_true", help="skip the plain FP64 GPU form")
+    ap.add_argument("--serial", action="store_true",
+                    help="time the tilings one after another on one stream")
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 form")
     ap.add_argument("--params", default="", help="fixed L and p per tiling, e.g. quad:7:12,sept:5:13")
     ap.add_argument("--workload", default="fmm", choices=["fmm", "batch", "serve", "clustered"])

@@ -399,6 +399,34 @@ void flush_events(fmm2d_plan *pl) {
   pl->ev_used = 0;
 }
 
+// The hybrid form's M2L: float-float on the FP32 pipes over the class lists.
+static cudaError_t run_m2l_ff(fmm2d_plan *pl, int L, int64_t far_first, const double *mQ,
+                              const void *ma, double *lL0, void *lb, cudaStream_t f) {
+  FfArgs t;
+  t.p = pl->p;
+  t.P = pl->P;
+  t.n_classes = pl->sten.n_classes;
+  t.sms = pl->n_sms;
+  t.far_first = far_first;
+  t.cls_cap = pl->cls_cap;
+  t.cls_cnt = (const int *)pl->d_cls_cnt.p;
+  t.cls_cells = (const int *)pl->d_cls_cells.p;
+  t.far_full = (const int *)pl->d_far_full.p;
+  t.sten_ops = (const uint16_t *)((const char *)pl->d_sten.p + offsetof(Stencils, far_op));
+  t.sten_len = (const int *)((const char *)pl->d_sten.p + offsetof(Stencils, far_len));
+  t.ops = (const float4 *)pl->d_ff_ops.p;
+  t.logz = (const double *)pl->d_m2l_logz.p;
+  t.log_abs_scale = (const double *)pl->d_geo_scale.p;
+  t.lev_first = (const int64_t *)pl->d_lev_first.p;
+  t.l_min = pl->l_min;
+  t.L = L;
+  t.mQ = mQ;
+  t.ma = (const double2 *)ma;
+  t.lL0 = lL0;
+  t.lb = (double2 *)lb;
+  return launch_m2l_ff(t, pl->n_far_cells, f);
+}
+
 // The plan's far-field stream (highest priority) and its fork / join events;
 // with serialised profiling, the caller's stream itself.
 static cudaError_t far_stream(fmm2d_plan *pl, cudaStream_t *out) {
@@ -516,6 +544,20 @@ fmm2d_status setup_geometry(fmm2d_plan *pl) {
     cudaGetDevice(&dev);
     CK(cudaDeviceGetAttribute(&pl->n_sms, cudaDevAttrMultiProcessorCount, dev), "sm count");
   }
+  if (is_hybrid(pl)) {   // float-float operators for the FP32-pipe M2L
+    std::vector<double> re(m2l.size()), im(m2l.size());
+    for (size_t i = 0; i < m2l.size(); ++i) {
+      re[i] = m2l[i].real();
+      im[i] = m2l[i].imag();
+    }
+    std::vector<float> tab;
+    ff_build_table(re, im, pl->n_ops, p, tab);
+    CK(dbuf_reserve(pl->d_ff_ops, tab.size() * 4), "alloc ff ops");
+    CK(cudaMemcpy(pl->d_ff_ops.p, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice), "upload ff ops");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    CK(cudaDeviceGetAttribute(&pl->n_sms, cudaDevAttrMultiProcessorCount, dev), "sm count");
+  }
   CK(upload(pl->d_m2m_ops, m2m), "upload m2m");
   CK(upload(pl->d_l2l_ops, l2l), "upload l2l");
   CK(dbuf_reserve(pl->d_m2l_logz, pl->n_ops * sizeof(double)), "alloc logz");
@@ -587,6 +629,9 @@ fmm2d_status evaluate_t(fmm2d_plan *pl, const void *u, double *out, cudaStream_t
   if (L < pl->l_min) {
     CK(cudaMemsetAsync(lL0, 0, pl->n_cells * sizeof(double), f), "zero locals");
     CK(cudaMemsetAsync(lb, 0, pl->n_cells * pl->P * sizeof(Cx<R>), f), "zero locals");
+  } else if (is_hybrid(pl)) {
+    StageScope sc(pl, ST_M2L, f, 1);
+    CK(run_m2l_ff(pl, L, pl->lev_first[pl->l_min], mQ, ma, lL0, lb, f), "m2l_ff");
   } else if ((pl->flags & FMM2D_PREC_MASK) == FMM2D_PREC_MIXED_TC) {
     StageScope sc(pl, ST_M2L, f, 1);
     TcArgs t;
@@ -710,9 +755,10 @@ static fmm2d_status build_adaptive(fmm2d_plan *pl, const void *src, int64_t n_sr
   if (!fits(L)) return fail(pl, FMM2D_EINVAL, "too many instances for this finest level");
   pl->n_inst = n_inst;
   const int p = pl->p_req ? pl->p_req : p_from_eps(pl->tiling, pl->eps);
-  const bool tc = (pl->flags & FMM2D_PREC_MASK) == FMM2D_PREC_MIXED_TC;
-  if (tc && !tc_shape(p, &pl->tc_K, &pl->tc_N))
+  const bool tc_form = (pl->flags & FMM2D_PREC_MASK) == FMM2D_PREC_MIXED_TC;
+  if (tc_form && !tc_shape(p, &pl->tc_K, &pl->tc_N))
     return fail(pl, FMM2D_EINVAL, "tensor-core M2L supports p <= 31");
+  const bool tc = tc_form || is_hybrid(pl);   // class lists: tensor-core and float-float M2L
   pl->L = L;
   pl->p = p;
   pl->P = (p + 1) & ~1;
@@ -1091,6 +1137,9 @@ fmm2d_status evaluate_adaptive_t(fmm2d_plan *pl, const void *u, double *out, cud
                        (const Cx<R> *)pl->d_m2l_ops.p, (const double *)pl->d_m2l_logz.p, mQ, ma,
                        lL0, lb, f), "m2l");
     }
+  } else if (is_hybrid(pl)) {
+    StageScope sc(pl, ST_M2L, f, 1);
+    CK(run_m2l_ff(pl, L, pl->n_cells - pl->n_far_cells, mQ, ma, lL0, lb, f), "m2l_ff");
   } else {
     StageScope sc(pl, ST_M2L, f, 1);
     const int64_t ff = pl->n_cells - pl->n_far_cells;
@@ -1244,9 +1293,10 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
   if (L == 0) L = auto_levels(pl->tiling, std::max(n_src, n_tgt), 64);
   if (p == 0) p = p_from_eps(pl->tiling, pl->eps);
   if (L < 1 || L > max_levels(pl->tiling)) return fail(pl, FMM2D_EINVAL, "levels out of range");
-  const bool tc = (pl->flags & FMM2D_PREC_MASK) == FMM2D_PREC_MIXED_TC;
-  if (tc && !tc_shape(p, &pl->tc_K, &pl->tc_N))
+  const bool tc_form = (pl->flags & FMM2D_PREC_MASK) == FMM2D_PREC_MIXED_TC;
+  if (tc_form && !tc_shape(p, &pl->tc_K, &pl->tc_N))
     return fail(pl, FMM2D_EINVAL, "tensor-core M2L supports p <= 31");
+  const bool tc = tc_form || is_hybrid(pl);   // class lists: tensor-core and float-float M2L
   pl->L = L;
   pl->p = p;
   pl->P = (p + 1) & ~1;   // even stride: rows of complex values stay 16-byte aligned
@@ -1746,7 +1796,7 @@ void fmm2d_plan_destroy(fmm2d_plan *pl) {
                   &pl->d_tgt2, &pl->d_mQ, &pl->d_ma, &pl->d_lL0, &pl->d_lb, &pl->d_phi_near,
                   &pl->d_phi_far, &pl->d_sten, &pl->d_geo_scale, &pl->d_m2l_ops, &pl->d_m2l_logz,
                   &pl->d_m2m_ops, &pl->d_l2l_ops, &pl->d_counts, &pl->d_far_full,
-                  &pl->d_cls_cnt, &pl->d_cls_cells, &pl->d_tc_ops, &pl->d_dev_err,
+                  &pl->d_cls_cnt, &pl->d_cls_cells, &pl->d_tc_ops, &pl->d_ff_ops, &pl->d_dev_err,
                   &pl->d_cell_lev, &pl->d_parent, &pl->d_child_first, &pl->d_child_cnt,
                   &pl->d_split, &pl->d_leaf_ids, &pl->d_leaf_pos, &pl->d_ad_scale,
                   &pl->d_ad_inv_scale, &pl->d_u_off, &pl->d_u_src, &pl->d_w_off, &pl->d_w_src,

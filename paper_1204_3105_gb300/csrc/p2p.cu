@@ -349,61 +349,74 @@ __device__ __forceinline__ void x2_logs(const float4 &p, const float2 &xab, cons
   }
 }
 
-// log2 of a mantissa m in [sqrt(1/2), sqrt(2)) in FP32 to a few ulp, from
-// ln m = 2 atanh(s) = 2 (s + s^3/3 + s^5/5 + ...), s = (m - 1)/(m + 1),
-// |s| < 0.172 (series truncated after s^11: below 2e-9 relative).
-__device__ __forceinline__ float x2_log2_mant(float m) {
-  const float s = __fdividef(m - 1.f, m + 1.f);
-  const float s2 = s * s;
-  float q = 1.f / 11.f;
-  q = fmaf(q, s2, 1.f / 9.f);
-  q = fmaf(q, s2, 1.f / 7.f);
-  q = fmaf(q, s2, 1.f / 5.f);
-  q = fmaf(q, s2, 1.f / 3.f);
-  q = fmaf(q, s2, 1.f);
-  return (2.f * 1.4426950408889634f) * (s * q);   // 2 s q / ln 2
+// a + b = s + err exactly (Knuth's TwoSum), two lanes at a time
+__device__ __forceinline__ void x2_two_sum2(const float2 a, const float2 b, float2 &s, float2 &err) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  s = __fadd2_rn(a, b);
+  const float2 bp = __ffma2_rn(a, m1, s);    // s - a
+  const float2 ap = __ffma2_rn(bp, m1, s);   // s - bp
+  err = __fadd2_rn(__ffma2_rn(ap, m1, a), __ffma2_rn(bp, m1, b));   // (a - ap) + (b - bp)
 }
 
-// As x2_logs, with log2 r^2 split into its exact exponent e and the log2 of
-// the mantissa (reduced to [sqrt(1/2), sqrt(2))), computed in FP32 to a few
-// ulp instead of by the MUFU approximation; the two parts are accumulated
-// separately, so the FP32 rounding of e + log2 m never happens.
-template <bool CHECK>
-__device__ __forceinline__ void x2_logs_split(const float4 &p, const float4 &pl, const float2 &xab,
-                                              const float2 &xcd, const float2 &yab,
-                                              const float2 &ycd, const float2 &xlab,
-                                              const float2 &xlcd, const float2 &ylab,
-                                              const float2 &ylcd, float2 &eab, float2 &ecd,
-                                              float2 &lab, float2 &lcd) {
+// r^2 of two target-source pairs as rh + rl (float-float): the coordinate
+// differences are formed without error (TwoSum of the hi parts, lo parts
+// added to the error), squared with exact products (FMA), summed by TwoSum
+// and renormalised; rh is floored at FL > 0 (a normal number)
+__device__ __forceinline__ void x2_r2_ff(const float2 &xt, const float2 &xs, const float2 &xtl,
+                                         const float2 &xsl, const float2 &yt, const float2 &ys,
+                                         const float2 &ytl, const float2 &ysl, float2 &rh,
+                                         float2 &rl) {
   constexpr float FL = 1e-30f;
-  // coordinates as hi + lo floats: the differences keep ~48 bits
-  const float2 px = make_float2(p.x, p.y), py = make_float2(p.z, p.w);
-  const float2 pxl = make_float2(pl.x, pl.y), pyl = make_float2(pl.z, pl.w);
-  const float2 fl = make_float2(FL, FL);
-  const float2 dxab = __fadd2_rn(__fadd2_rn(xab, px), __fadd2_rn(xlab, pxl));
-  const float2 dxcd = __fadd2_rn(__fadd2_rn(xcd, px), __fadd2_rn(xlcd, pxl));
-  const float2 dyab = __fadd2_rn(__fadd2_rn(yab, py), __fadd2_rn(ylab, pyl));
-  const float2 dycd = __fadd2_rn(__fadd2_rn(ycd, py), __fadd2_rn(ylcd, pyl));
-  const float2 rab = __ffma2_rn(dxab, dxab, __ffma2_rn(dyab, dyab, fl));
-  const float2 rcd = __ffma2_rn(dxcd, dxcd, __ffma2_rn(dycd, dycd, fl));
-  const float r[4] = {rab.x, rab.y, rcd.x, rcd.y};
-  float e[4], l[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {   // r >= 1e-30: a normal number
-    const int b = __float_as_int(r[i]);
-    // mantissa in [sqrt(1/2), sqrt(2)): fraction bits above 0x3504F3 move to [1/2, 1)
-    const int hi = (b & 0x007FFFFF) > 0x003504F3;
-    e[i] = (float)((b >> 23) - 127 + hi);
-    l[i] = x2_log2_mant(__int_as_float((b & 0x007FFFFF) | (hi ? 0x3F000000 : 0x3F800000)));
-    if (CHECK && r[i] == FL) {
-      e[i] = 0.f;
-      l[i] = 0.f;
-    }
+  float2 dxh, ex, dyh, ey;
+  x2_two_sum2(xt, xs, dxh, ex);
+  x2_two_sum2(yt, ys, dyh, ey);
+  const float2 dxl = __fadd2_rn(__fadd2_rn(xtl, xsl), ex);
+  const float2 dyl = __fadd2_rn(__fadd2_rn(ytl, ysl), ey);
+  const float2 qx = __fmul2_rn(dxh, dxh), qy = __fmul2_rn(dyh, dyh);
+  const float2 qxe = __ffma2_rn(dxh, dxh, make_float2(-qx.x, -qx.y));
+  const float2 qye = __ffma2_rn(dyh, dyh, make_float2(-qy.x, -qy.y));
+  float2 h, he;
+  x2_two_sum2(qx, qy, h, he);
+  const float2 two = make_float2(2.f, 2.f);
+  float2 l = __fadd2_rn(__fadd2_rn(qxe, qye), he);
+  l = __ffma2_rn(__fmul2_rn(two, dxh), dxl, l);
+  l = __ffma2_rn(__fmul2_rn(two, dyh), dyl, l);
+  l = __ffma2_rn(dxl, dxl, __ffma2_rn(dyl, dyl, l));
+  const float2 t = __fadd2_rn(h, l);                              // renormalise (h >= |l| or h = 0)
+  rl = __fadd2_rn(l, __ffma2_rn(t, make_float2(-1.f, -1.f), h)); // l - (t - h)
+  rh = make_float2(fmaxf(t.x, FL), fmaxf(t.y, FL));
+}
+
+// log2 r^2 = e + lh + ll for r^2 = rh + rl (rh normal): e the exponent of
+// rh, lh + ll the log2 of its mantissa m in [1, 2) by Tang's table method
+// (m r_j = 1 + f with r_j ~ 1/m from a 128-entry table, |f| <= 2^-8;
+// lh + ll = -log2 r_j + log2(1 + f) + rl / (rh ln 2)); table entry j holds
+// (r_j, hi and lo of -log2 r_j).  |ll| < 2^-7, accurate to about 2^-31.
+__device__ __forceinline__ void x2_log2_ff(float rh, float rl, const float4 *tab, float &e,
+                                           float &lh, float &ll) {
+  const int b = __float_as_int(rh);
+  const float4 tb = tab[(b >> 16) & 127];
+  const float m = __int_as_float((b & 0x007FFFFF) | 0x3F800000);
+  e = (float)((b >> 23) - 127);
+  const float f = fmaf(m, tb.x, -1.f);
+  // ln(1 + f) = f - f^2/2 + f^3/3 - f^4/4 (next term below 2^-42)
+  float q = fmaf(f, -0.25f, 1.f / 3.f);
+  q = fmaf(q, f, -0.5f);
+  q = fmaf(q, f, 1.f);
+  q *= f;
+  lh = tb.y;
+  ll = fmaf(q + __fdividef(rl, rh), 1.4426950408889634f, tb.z);
+}
+
+// Table of x2_log2_ff, one entry per thread j < 128 of the block.
+__device__ __forceinline__ void x2_log2_table(float4 *tab) {
+  const int j = threadIdx.x;
+  if (j < 128) {
+    const float r = __frcp_rn(1.f + (2.f * (float)j + 1.f) * (1.f / 256.f));
+    const double lg = -log2((double)r);
+    const float hi = (float)lg;
+    tab[j] = make_float4(r, hi, (float)(lg - (double)hi), 0.f);
   }
-  eab = make_float2(e[0], e[1]);
-  ecd = make_float2(e[2], e[3]);
-  lab = make_float2(l[0], l[1]);
-  lcd = make_float2(l[2], l[3]);
 }
 
 template <bool CHECK>
@@ -442,13 +455,14 @@ __device__ __forceinline__ void x2_kahan(float &s, float &e, float x) {
 
 // Staged sources q0, q0 + K, ... < q1.  Plain form: partial sums of at most
 // 64 sources are folded into the compensated running sums.  COMP (the hybrid
-// precision form): float-float differences, log2 r^2 split into exponent and
-// mantissa log, the exponent products made exact by splitting u, and every
-// term added error-free (TwoSum), which leaves the mantissa log (a few ulp)
-// as the only FP32 error: ~1e-9 relative instead of ~5e-8.
+// precision form): r^2 in float-float from hi + lo coordinates, log2 r^2 as
+// its exact exponent plus a table-driven float-float log2 of the mantissa,
+// exact products with the strength and error-free sums (TwoSum): each term
+// is accurate to about 2^-31 of |u| instead of ~2^-23.
 template <bool CHECK, bool COMP>
 __device__ __forceinline__ void x2_slice(const float4 *sxy, const float4 *slo, const float2 *su,
-                                         const float4 *su4, int q0, int q1, int K, const float2 &xab,
+                                         const float4 *su4, const float4 *tab, int q0, int q1, int K,
+                                         const float2 &xab,
                                          const float2 &xcd, const float2 &yab, const float2 &ycd,
                                          const float2 &xlab, const float2 &xlcd,
                                          const float2 &ylab, const float2 &ylcd, float (&s)[4],
@@ -456,25 +470,51 @@ __device__ __forceinline__ void x2_slice(const float4 *sxy, const float4 *slo, c
   if constexpr (COMP) {
     float2 acc_ab = make_float2(0.f, 0.f), acc_cd = make_float2(0.f, 0.f);
     float2 nc_ab = make_float2(0.f, 0.f), nc_cd = make_float2(0.f, 0.f);
-#pragma unroll 2
     for (int q = q0; q < q1; q += K) {
-      float2 eab, ecd, lab, lcd;
-      x2_logs_split<CHECK>(sxy[q], slo[q], xab, xcd, yab, ycd, xlab, xlcd, ylab, ylcd, eab, ecd,
-                           lab, lcd);
-      // u = uh + um + ul with uh of 16 and um of 8 significant bits: uh e and
-      // um e are exact products, so the exponent part enters the sum unrounded;
-      // the residual ul (below 2^-24 u) multiplies the whole log
+      const float4 p = sxy[q], pl = slo[q];
+      const float2 px = make_float2(p.x, p.y), py = make_float2(p.z, p.w);
+      const float2 pxl = make_float2(pl.x, pl.y), pyl = make_float2(pl.z, pl.w);
+      float2 rh_ab, rl_ab, rh_cd, rl_cd;
+      x2_r2_ff(xab, px, xlab, pxl, yab, py, ylab, pyl, rh_ab, rl_ab);
+      x2_r2_ff(xcd, px, xlcd, pxl, ycd, py, ylcd, pyl, rh_cd, rl_cd);
+      float e[4], lh[4], ll[4];
+      x2_log2_ff(rh_ab.x, rl_ab.x, tab, e[0], lh[0], ll[0]);
+      x2_log2_ff(rh_ab.y, rl_ab.y, tab, e[1], lh[1], ll[1]);
+      x2_log2_ff(rh_cd.x, rl_cd.x, tab, e[2], lh[2], ll[2]);
+      x2_log2_ff(rh_cd.y, rl_cd.y, tab, e[3], lh[3], ll[3]);
+      if (CHECK) {   // a source on the target: no term
+        const bool z[4] = {rh_ab.x == 1e-30f && rl_ab.x == 0.f, rh_ab.y == 1e-30f && rl_ab.y == 0.f,
+                           rh_cd.x == 1e-30f && rl_cd.x == 0.f, rh_cd.y == 1e-30f && rl_cd.y == 0.f};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (z[i]) e[i] = lh[i] = ll[i] = 0.f;
+      }
+      // u (e + lh + ll) with u = uh + ul: uh e and uh lh as exact products
+      // (TwoProd), both added error-free (TwoSum); the small rest uh ll +
+      // ul (e + lh) goes to the compensation
       const float4 uu = su4[q];
-      const float2 uh = make_float2(uu.x, uu.y), um = make_float2(uu.z, uu.w), ul = su[q];
-      const float2 u = __fadd2_rn(uh, um);
-      x2_twosum(acc_ab, nc_ab, __fmul2_rn(uh, eab));
-      x2_twosum(acc_ab, nc_ab, __fmul2_rn(um, eab));
-      x2_twosum(acc_ab, nc_ab, __fmul2_rn(u, lab));
-      x2_twosum(acc_ab, nc_ab, __fmul2_rn(ul, __fadd2_rn(eab, lab)));
-      x2_twosum(acc_cd, nc_cd, __fmul2_rn(uh, ecd));
-      x2_twosum(acc_cd, nc_cd, __fmul2_rn(um, ecd));
-      x2_twosum(acc_cd, nc_cd, __fmul2_rn(u, lcd));
-      x2_twosum(acc_cd, nc_cd, __fmul2_rn(ul, __fadd2_rn(ecd, lcd)));
+      const float2 uh = make_float2(uu.x, uu.y), ul = make_float2(uu.z, uu.w);
+      const float2 eab = make_float2(e[0], e[1]), ecd = make_float2(e[2], e[3]);
+      const float2 hab = make_float2(lh[0], lh[1]), hcd = make_float2(lh[2], lh[3]);
+      const float2 lab = make_float2(ll[0], ll[1]), lcd = make_float2(ll[2], ll[3]);
+      {
+        const float2 p1 = __fmul2_rn(uh, eab), p2 = __fmul2_rn(uh, hab);
+        const float2 r1 = __ffma2_rn(uh, eab, make_float2(-p1.x, -p1.y));
+        const float2 r2 = __ffma2_rn(uh, hab, make_float2(-p2.x, -p2.y));
+        x2_twosum(acc_ab, nc_ab, p1);
+        x2_twosum(acc_ab, nc_ab, p2);
+        const float2 rest = __ffma2_rn(uh, lab, __fmul2_rn(ul, __fadd2_rn(eab, hab)));
+        nc_ab = __fadd2_rn(nc_ab, __fadd2_rn(__fadd2_rn(r1, r2), rest));
+      }
+      {
+        const float2 p1 = __fmul2_rn(uh, ecd), p2 = __fmul2_rn(uh, hcd);
+        const float2 r1 = __ffma2_rn(uh, ecd, make_float2(-p1.x, -p1.y));
+        const float2 r2 = __ffma2_rn(uh, hcd, make_float2(-p2.x, -p2.y));
+        x2_twosum(acc_cd, nc_cd, p1);
+        x2_twosum(acc_cd, nc_cd, p2);
+        const float2 rest = __ffma2_rn(uh, lcd, __fmul2_rn(ul, __fadd2_rn(ecd, hcd)));
+        nc_cd = __fadd2_rn(nc_cd, __fadd2_rn(__fadd2_rn(r1, r2), rest));
+      }
     }
     x2_kahan(s[0], c[0], acc_ab.x);
     x2_kahan(s[1], c[1], acc_ab.y);
@@ -523,13 +563,18 @@ k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_ids,
   constexpr int G = P2P_TH / T, CAP = CAPB / G;
   __shared__ float4 s_xy[CAPB];
   __shared__ float4 s_lo[COMP ? CAPB : 1];
-  __shared__ float2 s_u[CAPB];
+  __shared__ float2 s_u[COMP ? 1 : CAPB];
   __shared__ float4 s_u4[COMP ? CAPB : 1];   // (uh, uh, ul, ul): strength split in two
+  __shared__ float4 s_lg[COMP ? 128 : 1];    // log2 table of the hybrid form
   __shared__ float s_red[2][4][P2P_TH];
   __shared__ int m_s0[G][NEAR_MAX], m_base[G][NEAR_MAX + 1];
   __shared__ float m_dx[G][NEAR_MAX], m_dy[G][NEAR_MAX];
   __shared__ double m_dxd[COMP ? G : 1][NEAR_MAX], m_dyd[COMP ? G : 1][NEAR_MAX];
   const int grp = threadIdx.x / T, tg = threadIdx.x % T;
+  if constexpr (COMP) {
+    x2_log2_table(s_lg);
+    __syncthreads();
+  }
   const int64_t li = (int64_t)blockIdx.x * G + grp;
   if (li >= n_leaves) return;                 // group-uniform exits only
   const int64_t g = leaf_ids ? (int64_t)leaf_ids[li] : leaf_first + li;
@@ -543,7 +588,7 @@ k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_ids,
   const bool single = !CSR || n_all <= NEAR_MAX;
   float4 *sxy = s_xy + grp * CAP;
   float4 *slo = COMP ? s_lo + grp * CAP : s_lo;
-  float2 *su = s_u + grp * CAP;   // (u, u); hybrid form: the residuals (ul, ul)
+  float2 *su = COMP ? s_u : s_u + grp * CAP;   // (u, u); the hybrid form uses su4
   float4 *su4 = COMP ? s_u4 + grp * CAP : s_u4;
   const float4 *src = reinterpret_cast<const float4 *>(src4);
   const double2 cg = ctr[g];
@@ -589,11 +634,8 @@ k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_ids,
           const float xl = (float)(X - (double)xh), yl = (float)(Y - (double)yh);
           sxy[q - c0] = make_float4(-xh, -xh, -yh, -yh);
           slo[q - c0] = make_float4(-xl, -xl, -yl, -yl);
-          // u = uh + um + ul: uh keeps 16 significant bits of the FP32 value,
-          // um its other 8, ul (component 3) the FP32 rounding residual
-          const float uh = __int_as_float(__float_as_int(v.z) & (int)0xFFFFFF00u), um = v.z - uh;
-          su4[q - c0] = make_float4(uh, uh, um, um);
-          su[q - c0] = make_float2(v.w, v.w);
+          // u = uh + ul: the FP32 value and (component 3) its rounding residual
+          su4[q - c0] = make_float4(v.z, v.z, v.w, v.w);
         } else {
           const float x = -(v.x + dcx), y = -(v.y + dcy);
           sxy[q - c0] = make_float4(x, x, y, y);
@@ -654,9 +696,9 @@ k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_ids,
           const int self_end = max(0, min(m, n_self - c0));
           const int first_unchecked = self_end + ((k - self_end) % K + K) % K;
           if (self_end > 0)
-            x2_slice<true, COMP>(sxy, slo, su, su4, k, self_end, K, xab, xcd, yab, ycd, xlab, xlcd,
+            x2_slice<true, COMP>(sxy, slo, su, su4, s_lg, k, self_end, K, xab, xcd, yab, ycd, xlab, xlcd,
                                  ylab, ylcd, s, c);
-          x2_slice<false, COMP>(sxy, slo, su, su4, first_unchecked, m, K, xab, xcd, yab, ycd, xlab,
+          x2_slice<false, COMP>(sxy, slo, su, su4, s_lg, first_unchecked, m, K, xab, xcd, yab, ycd, xlab,
                                 xlcd, ylab, ylcd, s, c);
         }
       }

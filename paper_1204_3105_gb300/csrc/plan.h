@@ -91,7 +91,7 @@ struct Plan {
   DBuf d_sten, d_geo_scale;
   DBuf d_m2l_ops, d_m2l_logz, d_m2m_ops, d_l2l_ops;   // element type per precision
   DBuf d_counts;
-  DBuf d_far_full, d_cls_cnt, d_cls_cells, d_tc_ops, d_dev_err;
+  DBuf d_far_full, d_cls_cnt, d_cls_cells, d_tc_ops, d_ff_ops, d_dev_err;
   int tc_K = 0, tc_N = 0, n_sms = 148;
   int64_t cls_cap = 1;
   // adaptive tree (FMM2D_ADAPTIVE): cells split while they hold more than
@@ -290,6 +290,31 @@ bool tc_shape(int p, int *K, int *N);
 void tc_build_tables(const std::vector<double> &m2l_re, const std::vector<double> &m2l_im,
                      int n_ops, int p, int K, int N, std::vector<uint32_t> &out);
 cudaError_t launch_m2l_tc(const TcArgs &a, int K, int N, int64_t n_far_cells, cudaStream_t s);
+
+// ---------------------------------------------------------------- m2l_ff.cu
+// M2L of the hybrid form: float-float arithmetic on the FP32 pipes, one CTA
+// per 64 targets of a class (the class lists of the tensor-core form).
+struct FfArgs {
+  int p, P, n_classes, sms;
+  int64_t far_first, cls_cap;
+  const int *cls_cnt, *cls_cells, *far_full;
+  const uint16_t *sten_ops;           // [MAX_CLASSES][FAR_MAX] operator id per stencil entry
+  const int *sten_len;                // [MAX_CLASSES]
+  const float4 *ops;                  // per operator [k][l]: hi.re, hi.im, lo.re, lo.im
+  const double *logz, *log_abs_scale;
+  const int64_t *lev_first;
+  int l_min, L;
+  const double *mQ;
+  const double2 *ma;
+  double *lL0;
+  double2 *lb;
+};
+size_t m2l_ff_smem_bytes(int p);
+// The FP64 operators ([op][l][k] real and imaginary parts) as float-float
+// pairs in the kernel's [op][k][l] layout.
+void ff_build_table(const std::vector<double> &re, const std::vector<double> &im, int n_ops, int p,
+                    std::vector<float> &out);
+cudaError_t launch_m2l_ff(const FfArgs &a, int64_t n_far_cells, cudaStream_t s);
 
 // ---------------------------------------------------------------- p2p.cu
 // src_lo / tgt_lo (FP32 form, hybrid precision): low parts of the points'

@@ -82,6 +82,20 @@ def test_mixed_forms_within_eps(tiling, L, cap, prec):
     assert rel_inf_error(r.phi, direct(xy, u, xy)) < 1e-6
 
 
+@pytest.mark.parametrize("tiling,L,cap", CASES)
+def test_hybrid_form_adaptive(tiling, L, cap):
+    """Hybrid form on an adaptive tree (float-float M2L over the class
+    lists, FP64 M2P / P2L, FP32 P2P): against the FP64 oracle's adaptive FMM
+    of the same tree and p, within 1e-8 (the FP32 near field's level)."""
+    xy, u = _clustered(6000, seed=35)
+    p = p_from_eps(tiling, 1e-8)
+    r = adaptive_fmm(make_tiling(tiling, L), xy, u, xy, p, s=cap)
+    phi, plan = run_gpu(tiling, xy, u, levels=L, p=p, prec="hybrid", leaf_size=cap, keep=True)
+    assert plan.query()["device_error"] == 0
+    plan.close()
+    assert rel_inf_error(phi, r.phi) < 1e-8
+
+
 @pytest.mark.parametrize("tiling,L", [("quad", 5), ("sept", 4), ("tri", 5)])
 def test_leaf_size_zero_is_the_uniform_tree(tiling, L):
     xy, u = uniform_square(20000, seed=34)

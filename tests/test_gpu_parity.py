@@ -222,6 +222,34 @@ def test_hybrid_form_eps_1e8(tiling):
     assert rel_inf_error(phi[cidx], ref) < 1e-8
 
 
+@pytest.mark.parametrize("tiling,L,p", CASES + [("quad", 4, 30), ("sept", 3, 28), ("tri", 4, 36)])
+def test_hybrid_far_field_matches_oracle(tiling, L, p):
+    """Hybrid form: multipoles (FP64 P2M, M2M) and locals (float-float M2L,
+    FP64 L2L) per level against the FP64 oracle to the tolerances of the FP64
+    form, and the far-field potential to 1e-11 of the potential scale; only
+    the near field (FP32 P2P) is approximate."""
+    n = 6007
+    xy, u = uniform_square(n, seed=5)
+    phi, plan = run_gpu(tiling, xy, u, levels=L, p=p, prec="hybrid", keep=True)
+    r, T = _oracle(tiling, L, xy, u, None, p)
+    for l in range(T.l_min, L + 1):
+        mg = plan.export("multipoles", l)
+        lg = plan.export("locals", l)
+        for i, key in enumerate(r.cells[l]):
+            if (l, key) in r.mult:
+                Q, a = r.mult[(l, key)]
+                assert abs(mg[i, 0].real - Q) <= 1e-12 * max(1.0, abs(Q))
+                assert np.max(np.abs(mg[i, 1:] - a)) <= 1e-10 * (np.abs(a).max() + 1e-300)
+            b = r.loc[(l, key)]
+            assert abs(lg[i, 0].real - b[0].real) <= 1e-10 * max(1.0, np.abs(b).max())
+            assert np.max(np.abs(lg[i, 1:] - b[1:])) <= 1e-9 * (np.abs(b[1:]).max() + 1e-300)
+    far = plan.export("phi_far")
+    plan.close()
+    scale = np.max(np.abs(r.phi))
+    assert np.max(np.abs(far - r.phi_far)) / scale < 1e-11
+    assert rel_inf_error(phi, r.phi) < 1e-8
+
+
 def test_plain_fp64_quadtree_8192():
     """The plain FP64 quadtree configuration: N = M = 8192 uniform points,
     strengths U[-1, 1], p = 16, 4 levels (leaf <= 64 on average): against the
