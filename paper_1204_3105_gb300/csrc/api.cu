@@ -11,6 +11,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -71,14 +72,26 @@ static int64_t sept_min_outside_norm(int L) {
   auto it = cache.find(L);
   if (it != cache.end()) return it->second;
   const int R = (int)(0.6 * std::pow(7.0, L / 2.0)) + 4;
-  int64_t best = INT64_MAX;
-  for (int a = -R; a <= R; ++a)
-    for (int b = -R; b <= R; ++b) {
-      int64_t n = (int64_t)a * a + (int64_t)a * b + (int64_t)b * b;
-      if (n >= best) continue;
-      uint32_t k;
-      if (!eis_to_key(a, b, L, &k)) best = n;
-    }
+  // rows a of the (2R+1)^2 window split over host threads (the window holds
+  // ~6e7 points at L = 9); each thread keeps its own minimum
+  const int nth = R > 64 ? (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency())) : 1;
+  std::vector<int64_t> part(nth, INT64_MAX);
+  auto scan = [&](int t) {
+    int64_t best = INT64_MAX;
+    for (int a = -R + t; a <= R; a += nth)
+      for (int b = -R; b <= R; ++b) {
+        const int64_t n = (int64_t)a * a + (int64_t)a * b + (int64_t)b * b;
+        if (n >= best) continue;
+        uint32_t k;
+        if (!eis_to_key(a, b, L, &k)) best = n;
+      }
+    part[t] = best;
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < nth; ++t) th.emplace_back(scan, t);
+  scan(0);
+  for (auto &x : th) x.join();
+  const int64_t best = *std::min_element(part.begin(), part.end());
   cache[L] = best;
   return best;
 }
@@ -90,6 +103,12 @@ static double sept_leaf_r(int L) {
   double m = std::sqrt((double)sept_min_outside_norm(L));
   double raw = std::sqrt(0.5) / (kSqrt3 * m - 1.0);
   return std::ceil(raw * 1099511627776.0) / 1099511627776.0;   // 2^40
+}
+
+// The septree leaf radii of every level an adaptive tree may reach (a few
+// tenths of a second of host work at the deepest level, then cached).
+void planner_precompute() {
+  for (int L = 1; L <= 9; ++L) sept_leaf_r(L);
 }
 
 // Triangle root inradius: the upright triangle centred at the origin that
@@ -414,7 +433,8 @@ static cudaError_t run_m2l_ff(fmm2d_plan *pl, int L, int64_t far_first, const do
   t.far_full = (const int *)pl->d_far_full.p;
   t.sten_ops = (const uint16_t *)((const char *)pl->d_sten.p + offsetof(Stencils, far_op));
   t.sten_len = (const int *)((const char *)pl->d_sten.p + offsetof(Stencils, far_len));
-  t.ops = (const float4 *)pl->d_ff_ops.p;
+  t.opA = (const float2 *)pl->d_ff_ops.p;
+  t.oph = (const float4 *)pl->d_ff_ph.p;
   t.logz = (const double *)pl->d_m2l_logz.p;
   t.log_abs_scale = (const double *)pl->d_geo_scale.p;
   t.lev_first = (const int64_t *)pl->d_lev_first.p;
@@ -545,15 +565,12 @@ fmm2d_status setup_geometry(fmm2d_plan *pl) {
     CK(cudaDeviceGetAttribute(&pl->n_sms, cudaDevAttrMultiProcessorCount, dev), "sm count");
   }
   if (is_hybrid(pl)) {   // float-float operators for the FP32-pipe M2L
-    std::vector<double> re(m2l.size()), im(m2l.size());
-    for (size_t i = 0; i < m2l.size(); ++i) {
-      re[i] = m2l[i].real();
-      im[i] = m2l[i].imag();
-    }
-    std::vector<float> tab;
-    ff_build_table(re, im, pl->n_ops, p, tab);
-    CK(dbuf_reserve(pl->d_ff_ops, tab.size() * 4), "alloc ff ops");
-    CK(cudaMemcpy(pl->d_ff_ops.p, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice), "upload ff ops");
+    std::vector<float> A, ph;
+    ff_build_table(T.zeta, m2l, p, A, ph);
+    CK(dbuf_reserve(pl->d_ff_ops, A.size() * 4), "alloc ff ops");
+    CK(cudaMemcpy(pl->d_ff_ops.p, A.data(), A.size() * 4, cudaMemcpyHostToDevice), "upload ff ops");
+    CK(dbuf_reserve(pl->d_ff_ph, ph.size() * 4), "alloc ff phases");
+    CK(cudaMemcpy(pl->d_ff_ph.p, ph.data(), ph.size() * 4, cudaMemcpyHostToDevice), "upload ff phases");
     int dev = 0;
     cudaGetDevice(&dev);
     CK(cudaDeviceGetAttribute(&pl->n_sms, cudaDevAttrMultiProcessorCount, dev), "sm count");
@@ -933,6 +950,18 @@ static fmm2d_status build_adaptive(fmm2d_plan *pl, const void *src, int64_t n_sr
     CK(cudaMemsetAsync(pl->d_cls_cnt.p, 0, MAX_CLASSES * 4, s), "memset");
   }
   pl->cls_cap = nfc;
+  {   // (level, key) -> cell table for the traversal, at most half full
+    int hb = 1;
+    while (((int64_t)1 << hb) < 2 * n_cells) ++hb;
+    CK(dbuf_reserve(pl->d_ad_hkey, ((size_t)1 << hb) * 8), "alloc");
+    CK(dbuf_reserve(pl->d_ad_hval, ((size_t)1 << hb) * 4), "alloc");
+    CK(cudaMemsetAsync(pl->d_ad_hkey.p, 0xFF, ((size_t)1 << hb) * 8, s), "memset");
+    c.hkey = (const unsigned long long *)pl->d_ad_hkey.p;
+    c.hval = (const int *)pl->d_ad_hval.p;
+    c.hbits = hb;
+    CK(ad_launch_hash(n_cells, c, (unsigned long long *)pl->d_ad_hkey.p, (int *)pl->d_ad_hval.p, hb, s),
+       "hash");
+  }
   int64_t n_u = 0, n_w = 0, n_x = 0, n_t = 0, n_s = 0;
   {
     StageScope sc(pl, ST_LISTS, s, 4 * (depth + 1));
@@ -1796,7 +1825,8 @@ void fmm2d_plan_destroy(fmm2d_plan *pl) {
                   &pl->d_tgt2, &pl->d_mQ, &pl->d_ma, &pl->d_lL0, &pl->d_lb, &pl->d_phi_near,
                   &pl->d_phi_far, &pl->d_sten, &pl->d_geo_scale, &pl->d_m2l_ops, &pl->d_m2l_logz,
                   &pl->d_m2m_ops, &pl->d_l2l_ops, &pl->d_counts, &pl->d_far_full,
-                  &pl->d_cls_cnt, &pl->d_cls_cells, &pl->d_tc_ops, &pl->d_ff_ops, &pl->d_dev_err,
+                  &pl->d_cls_cnt, &pl->d_cls_cells, &pl->d_tc_ops, &pl->d_ff_ops, &pl->d_ff_ph, &pl->d_dev_err,
+                  &pl->d_ad_hkey, &pl->d_ad_hval,
                   &pl->d_cell_lev, &pl->d_parent, &pl->d_child_first, &pl->d_child_cnt,
                   &pl->d_split, &pl->d_leaf_ids, &pl->d_leaf_pos, &pl->d_ad_scale,
                   &pl->d_ad_inv_scale, &pl->d_u_off, &pl->d_u_src, &pl->d_w_off, &pl->d_w_src,

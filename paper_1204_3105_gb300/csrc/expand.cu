@@ -86,6 +86,74 @@ k_p2m(ExpandArgs a, const R *__restrict__ src4, const int *__restrict__ start,
   }
 }
 
+// P2M by powers kept per point: lane i of the warp takes source i of every
+// group of 32 and forms u z^k for k = 1, 2, ... by one complex product each;
+// 16 powers at a time go through shared memory, where lane (r, h) sums row
+// r over the 16 points of half h.  The FP64 work per source is p complex
+// products and p / 16 partial sums (the form above repeats the powers below
+// each chunk of 8 and reduces every coefficient with shuffles).
+template <typename R>
+__global__ void __launch_bounds__(32 * WPB)
+k_p2m_t(ExpandArgs a, const R *__restrict__ src4, const int *__restrict__ start,
+        const int *__restrict__ end, double *__restrict__ mQ, Cx<R> *__restrict__ ma) {
+  constexpr int KC = 16, NCH = (MAXP + KC - 1) / KC;
+  __shared__ Cx<R> sw[WPB][KC][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t li = blockIdx.x * (int64_t)WPB + w;
+  if (li >= a.n_leaves) return;
+  const int64_t g = a.leaf_ids ? (int64_t)a.leaf_ids[li] : a.leaf_first + li;
+  const int s = start[g], e = end[g];
+  Cx<R> is = {(R)a.inv_s_re, (R)a.inv_s_im};
+  if (a.leaf_ids) {
+    const double2 v = a.inv_scale[a.cell_lev[g]];
+    is = {(R)v.x, (R)v.y};
+  }
+  const int p = a.p, r = lane & (KC - 1), h = lane >> 4;
+  double q = 0.0;
+  Cx<R> acc[NCH];
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) acc[c] = {(R)0, (R)0};
+  for (int i0 = s; i0 < e; i0 += 32) {
+    const int i = i0 + lane;
+    Cx<R> z = {(R)0, (R)0}, wk = {(R)0, (R)0};
+    if (i < e) {
+      const R *pt = src4 + 4 * (int64_t)i;
+      z = Cx<R>{pt[0], pt[1]} * is;
+      wk = {pt[2], (R)0};
+      q += (double)pt[2];
+    }
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      const int nk = min(KC, p - c * KC);   // warp-uniform
+      if (nk <= 0) break;
+      for (int kk = 0; kk < nk; ++kk) {
+        wk = wk * z;
+        sw[w][kk][lane] = wk;
+      }
+      __syncwarp();
+      if (r < nk) {
+        Cx<R> t = {(R)0, (R)0};
+#pragma unroll
+        for (int j = 0; j < 16; ++j) t = t + sw[w][r][16 * h + j];
+        acc[c] = acc[c] + t;
+      }
+      __syncwarp();
+    }
+  }
+  q = warp_sum(q);
+  if (lane == 0) mQ[g] = q;
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    const R re = acc[c].x + __shfl_xor_sync(0xffffffffu, acc[c].x, 16);
+    const R im = acc[c].y + __shfl_xor_sync(0xffffffffu, acc[c].y, 16);
+    const int k = 1 + c * KC + lane;
+    if (lane < KC && k <= p) {
+      const R inv = (R)(-1.0) / (R)k;
+      ma[g * a.P + (k - 1)] = {re * inv, im * inv};
+    }
+  }
+}
+
 // H lanes per parent cell (the launcher uses a whole warp, H = 32); lane i of
 // the group owns output coefficients i+1 and i+1+H.
 template <typename R, int H>
@@ -281,7 +349,11 @@ template <typename R>
 cudaError_t launch_p2m(const ExpandArgs &a, const R *src4, const int *start, const int *end,
                        double *mQ, Cx<R> *ma, cudaStream_t s) {
   if (a.n_leaves <= 0) return cudaSuccess;
-  k_p2m<R, 8><<<wblocks(a.n_leaves), 32 * WPB, 0, s>>>(a, src4, start, end, mQ, ma);
+  if constexpr (sizeof(R) == 8) {   // FP64: the powers-per-point form
+    k_p2m_t<R><<<wblocks(a.n_leaves), 32 * WPB, 0, s>>>(a, src4, start, end, mQ, ma);
+  } else {
+    k_p2m<R, 8><<<wblocks(a.n_leaves), 32 * WPB, 0, s>>>(a, src4, start, end, mQ, ma);
+  }
   return cudaGetLastError();
 }
 

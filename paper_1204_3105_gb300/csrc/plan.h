@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <complex>
 #include <vector>
 
 #include "common.cuh"
@@ -91,7 +92,8 @@ struct Plan {
   DBuf d_sten, d_geo_scale;
   DBuf d_m2l_ops, d_m2l_logz, d_m2m_ops, d_l2l_ops;   // element type per precision
   DBuf d_counts;
-  DBuf d_far_full, d_cls_cnt, d_cls_cells, d_tc_ops, d_ff_ops, d_dev_err;
+  DBuf d_far_full, d_cls_cnt, d_cls_cells, d_tc_ops, d_ff_ops, d_ff_ph, d_dev_err;
+  DBuf d_ad_hkey, d_ad_hval;          // adaptive tree: (level, key) -> cell table
   int tc_K = 0, tc_N = 0, n_sms = 148;
   int64_t cls_cap = 1;
   // adaptive tree (FMM2D_ADAPTIVE): cells split while they hold more than
@@ -118,6 +120,10 @@ struct Plan {
 };
 
 // ---------------------------------------------------------------- helpers
+// Host-side planner constants that take a moment to compute (septree leaf
+// radii), computed ahead of the first plan that needs them.
+void planner_precompute();
+
 cudaError_t dbuf_reserve(DBuf &b, size_t bytes);
 void dbuf_free(DBuf &b);
 
@@ -174,7 +180,15 @@ struct AdCells {
   int4 *crd;
   double2 *ctr;
   uint8_t *cls, *hsrc;
+  // (level, key) -> cell: open-addressing table of 2^hbits slots (null: the
+  // list traversal falls back to a binary search of the level's keys)
+  const unsigned long long *hkey = nullptr;
+  const int *hval = nullptr;
+  int hbits = 0;
 };
+// Fill the (level, key) -> cell table of cells [0, n_cells) (slots preset to ~0).
+cudaError_t ad_launch_hash(int64_t n_cells, const AdCells &c, unsigned long long *hkey, int *hval,
+                           int hbits, cudaStream_t s);
 // level-0 cells: one per instance (soff / toff: n_inst + 1 device offsets),
 // or one cell holding everything (null offsets, n_inst = 1)
 cudaError_t ad_launch_roots(const Geo &g, int n_inst, const int64_t *soff, const int64_t *toff,
@@ -300,7 +314,8 @@ struct FfArgs {
   const int *cls_cnt, *cls_cells, *far_full;
   const uint16_t *sten_ops;           // [MAX_CLASSES][FAR_MAX] operator id per stencil entry
   const int *sten_len;                // [MAX_CLASSES]
-  const float4 *ops;                  // per operator [k][l]: hi.re, hi.im, lo.re, lo.im
+  const float2 *opA;                  // per operator the real factor A [k][l]: hi, lo
+  const float4 *oph;                  // per operator the phases u^-m, m = 0..p
   const double *logz, *log_abs_scale;
   const int64_t *lev_first;
   int l_min, L;
@@ -310,10 +325,11 @@ struct FfArgs {
   double2 *lb;
 };
 size_t m2l_ff_smem_bytes(int p);
-// The FP64 operators ([op][l][k] real and imaginary parts) as float-float
-// pairs in the kernel's [op][k][l] layout.
-void ff_build_table(const std::vector<double> &re, const std::vector<double> &im, int n_ops, int p,
-                    std::vector<float> &out);
+// From the offsets zeta and the FP64 operators ([op][l][k]): the real
+// factors A (float-float, [op][k][l]) and the phases u^-m of the kernel.
+void ff_build_table(const std::vector<std::complex<double>> &zeta,
+                    const std::vector<std::complex<double>> &ops, int p, std::vector<float> &A,
+                    std::vector<float> &ph);
 cudaError_t launch_m2l_ff(const FfArgs &a, int64_t n_far_cells, cudaStream_t s);
 
 // ---------------------------------------------------------------- p2p.cu

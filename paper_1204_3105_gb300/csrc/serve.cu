@@ -216,6 +216,7 @@ fmm2d_status fmm2d_serve_create(size_t hbm_budget_bytes, int max_slots, fmm2d_se
     return FMM2D_ECUDA;
   fmm2d_server *sv = new (std::nothrow) fmm2d_server();
   if (!sv) return FMM2D_ENOMEM;
+  planner_precompute();   // not on the first request's clock
   sv->budget = hbm_budget_bytes;
   sv->device = dev;
   for (int i = 0; i < max_slots; ++i) {
