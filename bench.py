@@ -102,7 +102,7 @@ class Clocks:
                 "samples": len(self.rows)}
 
 
-def oracle_sample(tilings=TILINGS, n=16384, seed=SEED):
+def oracle_sample(tilings=TILINGS, n=16384, seed=SEED, eps=EPS):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
     N = M = n uniform points per tiling, the planner's L and p for eps."""
     from oracle.fmm import fmm, make_tiling
@@ -114,7 +114,7 @@ def oracle_sample(tilings=TILINGS, n=16384, seed=SEED):
     t0 = time.perf_counter()
     for t in tilings:
         T = make_tiling(t, auto_levels(t, n))
-        fmm(T, xy, u, xy, p_from_eps(t, EPS))
+        fmm(T, xy, u, xy, p_from_eps(t, eps))
     dt = time.perf_counter() - t0
     return len(tilings) * n / dt, dt
 
@@ -188,7 +188,8 @@ def run_ours(args):
     xy_d = torch.from_numpy(xy).to(dev)
     u_d = torch.from_numpy(u).to(dev)
     outs = {t: torch.empty(N_POINTS, dtype=torch.float64, device=dev) for t in args.tilings}
-    prec = {"tc": fmm2d.PREC_MIXED_TC, "mixed": fmm2d.PREC_MIXED, "fp64": fmm2d.PREC_FP64}[args.prec]
+    prec = {"tc": fmm2d.PREC_MIXED_TC, "mixed": fmm2d.PREC_MIXED, "fp64": fmm2d.PREC_FP64,
+            "hybrid": fmm2d.PREC_HYBRID}[args.prec]
     tuned = {}
     fixed = {}
     for item in filter(None, args.params.split(",")):
@@ -200,9 +201,9 @@ def run_ours(args):
         elif args.no_tune:
             tuned[t] = (0, 0, None, None)
         else:   # measured (L, p) for eps on this point set (seeded probe strengths)
-            tuned[t] = fmm2d.fmm2d_autotune(t, EPS, prec | fmm2d.IN_F32, xy_d, N_POINTS, xy_d,
+            tuned[t] = fmm2d.fmm2d_autotune(t, args.eps, prec | fmm2d.IN_F32, xy_d, N_POINTS, xy_d,
                                             N_POINTS, stream=stream)
-    plans = {t: fmm2d.Plan(t, tuned[t][0], tuned[t][1], EPS, prec | fmm2d.IN_F32)
+    plans = {t: fmm2d.Plan(t, tuned[t][0], tuned[t][1], args.eps, prec | fmm2d.IN_F32)
              for t in args.tilings}
     flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device=dev)   # 256 MB > L2
 
@@ -291,9 +292,9 @@ def run_ours(args):
     if not args.no_fp64_form and args.prec != "fp64":
         f64 = {}
         for t in args.tilings:
-            L64, p64, e64, _ = fmm2d.fmm2d_autotune(t, EPS, fmm2d.PREC_FP64 | fmm2d.IN_F32, xy_d, N_POINTS,
+            L64, p64, e64, _ = fmm2d.fmm2d_autotune(t, args.eps, fmm2d.PREC_FP64 | fmm2d.IN_F32, xy_d, N_POINTS,
                                                     xy_d, N_POINTS, stream=stream)
-            pl64 = fmm2d.Plan(t, L64, p64, EPS, fmm2d.PREC_FP64 | fmm2d.IN_F32)
+            pl64 = fmm2d.Plan(t, L64, p64, args.eps, fmm2d.PREC_FP64 | fmm2d.IN_F32)
             ts64 = []
             for it in range(1 + args.fp64_steps):
                 e0 = torch.cuda.Event(enable_timing=True)
@@ -384,21 +385,24 @@ def run_ours(args):
                 "frac": ach / peak, "traffic": None,
                 "peak_source": "measured FP32 FMA rate (fmm2d_measure_alu_peaks)", "timing": note}
 
-    roof = roofline(tot, "CUDA events around the stage, 5 steps after the timed ones (far field concurrent)")
-    roof_iso = roofline(tot_iso, "CUDA events, one extra step with the stages serialised")
+    lg2_p2p = args.prec in ("tc", "mixed")   # the P2P roofline counts one MUFU lg2 per pair
+    roof = roofline(tot, "CUDA events around the stage, 5 steps after the timed ones (far field concurrent)") \
+        if lg2_p2p else None
+    roof_iso = roofline(tot_iso, "CUDA events, one extra step with the stages serialised") if lg2_p2p else None
 
     cpu_v, cpu_dt = (None, None)
     if rank == 0 and not args.no_cpu_baseline:
-        cpu_v, cpu_dt = oracle_sample(n=args.ref_points)
+        cpu_v, cpu_dt = oracle_sample(n=args.ref_points, eps=args.eps)
     launches = int(sum(tot_iso[k][1] for k in tot_iso))
     if rank == 0:
         line = {
-            "metric": "FMM eval points/s at eps=1e-6 (3 tilings)", "value": value, "unit": "points/s",
+            "metric": "FMM eval points/s at eps=%g (3 tilings)" % args.eps, "value": value, "unit": "points/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.prec == "fp64" else "tf32x3+f32+f64", "data": "synthetic",
+            "dtype": {"fp64": "f64", "hybrid": "f64 + float-float M2L + f32 pairs P2P"}.get(
+                args.prec, "tf32x3+f32+f64"), "data": "synthetic",
             "config": {"workload": "N=M=2^20 uniform unit square (sources=targets), FP32 points and "
-                                   "strengths, quad+sept+tri, eps=1e-6, %s L/p, %s form" % (
+                                   "strengths, quad+sept+tri, eps=%g, %s L/p, %s form" % (args.eps,
                                    "fixed" if args.params else "planner" if args.no_tune else "autotuned",
                                    args.prec),
                        "global_batch": N_POINTS,
@@ -680,7 +684,7 @@ def run_server_workload(args):
             for i, r in enumerate(res):
                 f.write(json.dumps({"i": i, "tiling": names[tilings[i]], "n": int(sizes[i]),
                                     "eps": float(eps[i]), "cluster": bool(cluster[i]),
-                                    "slot": r["slot"], "queue_ms": r["queue_ms"],
+                                    "slot": r["slot"], "batched": r["batched"], "queue_ms": r["queue_ms"],
                                     "run_ms": r["run_ms"], "p": r["p"], "levels": r["levels"]}) + "\n")
     by_eps = {}
     for e in sorted(set(eps.tolist())):
@@ -720,7 +724,8 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="tc", choices=["tc", "mixed", "fp64"])
+    ap.add_argument("--prec", default="tc", choices=["tc", "mixed", "fp64", "hybrid"])
+    ap.add_argument("--eps", type=float, default=EPS, help="fmm workload: requested tolerance")
     ap.add_argument("--tilings", default=",".join(TILINGS))
     ap.add_argument("--ref-points", type=int, default=16384)
     ap.add_argument("--ref-seconds", type=float, default=150.0, help="reference arm: host time budget")

@@ -367,6 +367,10 @@ typedef struct {
   int32_t levels, p;       /* parameters used */
   uint32_t flags;          /* precision used */
   int32_t slot;            /* execution slot that ran it */
+  int32_t batched;         /* requests solved together with it as one forest
+                              (1: alone); small adaptive requests with equal
+                              tiling, eps, flags and domain that wait together
+                              are merged (fmm2d_build_forest) */
   double queue_ms;         /* submit -> start */
   double run_ms;           /* start -> potentials in host memory */
   double latency_ms;       /* submit -> completion */

@@ -317,111 +317,50 @@ struct Emitter {
   }
 };
 
-// true when no cell of Near(fine, lf) lies inside the coarser cell `coarse`
-__device__ bool separated(const Geo &g, const Stencils &st, int lf, int4 fcrd, int lc, uint32_t coarse) {
-  const int o = (g.tiling == FMM2D_TRI && fcrd.w == 0) ? 1 : 0;
-  for (int e = 0; e < st.near_len[o]; ++e) {
-    const int4 q = make_int4(fcrd.x + st.near_d[o][e][0], fcrd.y + st.near_d[o][e][1],
-                             fcrd.z + st.near_d[o][e][2], 0);
-    uint32_t k;
-    if (!cell_at(g, lf, q, &k)) continue;
-    if (parent_key(g.tiling, k, lf - lc) == coarse) return false;
-  }
-  return true;
-}
-
+// The W and X tests of level l, items it0 = count, count + 1, ...: half a
+// warp per test, lane e of the half checking Near stencil entry e of the
+// finer cell (does it lie inside the coarser one?); lane 0 of the half then
+// writes the outcome as one thread would.
 template <bool EMIT>
-__global__ void k_ad_lists(Geo g, const Stencils *__restrict__ stp, int l, int l_min,
-                           int64_t first, int64_t count, int64_t n_t, int64_t n_s,
-                           const int *__restrict__ t_a, const int *__restrict__ t_c,
-                           const int *__restrict__ s_a, const int *__restrict__ s_c, AdCells c,
-                           ListOut out, int64_t far_first, int *__restrict__ far_cnt,
-                           int *__restrict__ far_src, uint16_t *__restrict__ far_op,
-                           int *__restrict__ far_full, int *__restrict__ cls_cnt,
-                           int *__restrict__ cls_cells, int64_t cls_cap) {
-  const int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (it >= count + n_t + n_s) return;
+__global__ void k_ad_lists(Geo g, const Stencils *__restrict__ stp, int l, int64_t count,
+                           int64_t n_t, int64_t n_s, const int *__restrict__ t_a,
+                           const int *__restrict__ t_c, const int *__restrict__ s_a,
+                           const int *__restrict__ s_c, AdCells c, ListOut out, int64_t it0) {
+  const int lane = threadIdx.x & 31, sub = lane & 15;
+  const unsigned hmask = 0xFFFFu << (lane & 16);
+  const int64_t it = it0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 4);
+  if (it >= count + n_t + n_s) return;              // uniform within the half warp
   const Stencils &st = *stp;
+  const bool w_test = it < count + n_t;
+  const int64_t j = w_test ? it - count : it - count - n_t;
+  const int a = w_test ? t_a[j] : s_a[j], cc = w_test ? t_c[j] : s_c[j];
+  // W: fine cell cc (level l) against the leaf a; X: fine cell a against the leaf cc
+  const int fine = w_test ? cc : a, coarse = w_test ? a : cc;
+  const int lc = c.lev[coarse];
+  uint32_t inst;
+  const uint32_t ckey = local_key(g.b, lc, c.key[coarse], &inst);
+  const int4 fcrd = c.crd[fine];
+  const int o = (g.tiling == FMM2D_TRI && fcrd.w == 0) ? 1 : 0;
+  bool inside = false;
+  if (sub < st.near_len[o]) {
+    const int4 q = make_int4(fcrd.x + st.near_d[o][sub][0], fcrd.y + st.near_d[o][sub][1],
+                             fcrd.z + st.near_d[o][sub][2], 0);
+    uint32_t k;
+    if (cell_at(g, l, q, &k)) inside = parent_key(g.tiling, k, l - lc) == ckey;
+  }
+  const bool sep = __ballot_sync(hmask, inside) == 0u;
+  if (sub != 0) return;
   Emitter<EMIT> em(out, it);
-  if (it < count) {                                   // a cell of level l
-    const int a = (int)(first + it);
-    const bool a_tgt = c.te[a] > c.ts[a];
-    const int4 ca = c.crd[a];
-    uint32_t inst;
-    local_key(g.b, l, c.key[a], &inst);
-    const uint32_t ibase = (uint32_t)((uint64_t)inst * level_span(g.b, l));
-    if (a_tgt) {
-      const int o = (g.tiling == FMM2D_TRI && ca.w == 0) ? 1 : 0;
-      const bool a_leaf = !c.split[a];
-      for (int e = 0; e < st.near_len[o]; ++e) {
-        const int4 q = make_int4(ca.x + st.near_d[o][e][0], ca.y + st.near_d[o][e][1],
-                                 ca.z + st.near_d[o][e][2], 0);
-        uint32_t k;
-        if (!cell_at(g, l, q, &k)) continue;
-        const int m = find_cell_at(c, l, first, count, ibase + k);
-        if (m < 0 || !c.hsrc[m]) continue;
-        const bool m_leaf = !c.split[m];
-        if (a_leaf && m_leaf) {
-          em.put(K_U, a, m);
-        } else if (a_leaf) {
-          for (int d = 0; d < c.child_cnt[m]; ++d) {
-            const int ch = c.child_first[m] + d;
-            if (c.hsrc[ch]) em.put(K_T, a, ch);
-          }
-        } else if (m_leaf) {
-          for (int d = 0; d < c.child_cnt[a]; ++d) {
-            const int ch = c.child_first[a] + d;
-            if (c.te[ch] > c.ts[ch]) em.put(K_S, ch, m);
-          }
-        }
-      }
-    }
-    if (EMIT && l >= l_min) {                         // M2L list (uniform format)
-      const int cls = c.cls[a];
-      const int64_t fi = a - far_first;
-      int cnt = 0;
-      const int n_far = a_tgt ? st.far_len[cls] : 0;
-      for (int e = 0; e < st.far_len[cls]; ++e) {
-        int sidx = -1;
-        if (e < n_far) {
-          const int4 q = make_int4(ca.x + st.far_d[cls][e][0], ca.y + st.far_d[cls][e][1],
-                                   ca.z + st.far_d[cls][e][2], 0);
-          uint32_t k;
-          if (cell_at(g, l, q, &k)) {
-            sidx = find_cell_at(c, l, first, count, ibase + k);
-            if (sidx >= 0 && !c.hsrc[sidx]) sidx = -1;
-          }
-        }
-        if (far_full) far_full[fi * FAR_MAX + e] = sidx;
-        if (sidx < 0) continue;
-        far_src[fi * FAR_MAX + cnt] = sidx;
-        far_op[fi * FAR_MAX + cnt] = st.far_op[cls][e];
-        ++cnt;
-      }
-      far_cnt[fi] = cnt;
-      if (cls_cnt && st.far_len[cls] > 0) {
-        const int pos = atomicAdd(&cls_cnt[cls], 1);
-        cls_cells[(int64_t)cls * cls_cap + pos] = a;
-      }
-    }
-  } else if (it < count + n_t) {                      // W test: leaf a, finer cell cc
-    const int64_t j = it - count;
-    const int a = t_a[j], cc = t_c[j];
-    uint32_t inst;
-    if (separated(g, st, l, c.crd[cc], c.lev[a], local_key(g.b, c.lev[a], c.key[a], &inst)))
-      em.put(K_W, a, cc);
+  if (w_test) {
+    if (sep) em.put(K_W, a, cc);
     else if (!c.split[cc]) em.put(K_U, a, cc);
     else
       for (int d = 0; d < c.child_cnt[cc]; ++d) {
         const int ch = c.child_first[cc] + d;
         if (c.hsrc[ch]) em.put(K_T, a, ch);
       }
-  } else {                                            // X test: cell a, coarser leaf cc
-    const int64_t j = it - count - n_t;
-    const int a = s_a[j], cc = s_c[j];
-    uint32_t inst;
-    if (separated(g, st, l, c.crd[a], c.lev[cc], local_key(g.b, c.lev[cc], c.key[cc], &inst)))
-      em.put(K_X, a, cc);
+  } else {
+    if (sep) em.put(K_X, a, cc);
     else if (!c.split[a]) em.put(K_U, a, cc);
     else
       for (int d = 0; d < c.child_cnt[a]; ++d) {
@@ -430,6 +369,143 @@ __global__ void k_ad_lists(Geo g, const Stencils *__restrict__ stp, int l, int l
       }
   }
   em.done();
+}
+
+// The cell items of a level's traversal, a warp per cell: lane e takes
+// Near stencil entry e (and far stencil entries e, e + 32), so the ~50
+// lookups of a cell run side by side; per-kind warp scans (near part) and
+// ballots (far part) keep the output in stencil order, as one thread would
+// write it.
+template <bool EMIT>
+__global__ void k_ad_cell_lists(Geo g, const Stencils *__restrict__ stp, int l, int l_min,
+                                int64_t first, int64_t count, AdCells c, ListOut out,
+                                int64_t far_first, int *__restrict__ far_cnt,
+                                int *__restrict__ far_src, uint16_t *__restrict__ far_op,
+                                int *__restrict__ far_full, int *__restrict__ cls_cnt,
+                                int *__restrict__ cls_cells, int64_t cls_cap) {
+  const int lane = threadIdx.x & 31;
+  const int64_t it = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (it >= count) return;                          // warp-uniform
+  const Stencils &st = *stp;
+  const int a = (int)(first + it);
+  const bool a_tgt = c.te[a] > c.ts[a];
+  const int4 ca = c.crd[a];
+  uint32_t inst;
+  local_key(g.b, l, c.key[a], &inst);
+  const uint32_t ibase = (uint32_t)((uint64_t)inst * level_span(g.b, l));
+  // near stencil entry `lane`: U (a, m), T (a, child of m) or S (child of a, m)
+  int m = -1, mode = 0, nk = 0;
+  if (a_tgt) {
+    const int o = (g.tiling == FMM2D_TRI && ca.w == 0) ? 1 : 0;
+    if (lane < st.near_len[o]) {
+      const int4 q = make_int4(ca.x + st.near_d[o][lane][0], ca.y + st.near_d[o][lane][1],
+                               ca.z + st.near_d[o][lane][2], 0);
+      uint32_t k;
+      if (cell_at(g, l, q, &k)) {
+        m = find_cell_at(c, l, first, count, ibase + k);
+        if (m >= 0 && !c.hsrc[m]) m = -1;
+      }
+      if (m >= 0) {
+        const bool a_leaf = !c.split[a], m_leaf = !c.split[m];
+        if (a_leaf && m_leaf) {
+          mode = 1;
+          nk = 1;
+        } else if (a_leaf) {
+          mode = 2;
+          for (int d = 0; d < c.child_cnt[m]; ++d) nk += c.hsrc[c.child_first[m] + d] ? 1 : 0;
+        } else if (m_leaf) {
+          mode = 3;
+          for (int d = 0; d < c.child_cnt[a]; ++d) {
+            const int ch = c.child_first[a] + d;
+            nk += c.te[ch] > c.ts[ch] ? 1 : 0;
+          }
+        }
+      }
+    }
+  }
+  // exclusive scans of the three kinds' counts over the lanes
+  const int kind = mode == 1 ? K_U : (mode == 2 ? K_T : K_S);
+  int ex[3], tot[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int my = (mode == q + 1) ? nk : 0;
+    int v = my;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, v, d);
+      if (lane >= d) v += y;
+    }
+    tot[q] = __shfl_sync(0xffffffffu, v, 31);
+    ex[q] = v - my;
+  }
+  if (!EMIT) {
+    if (lane < K_KINDS) {
+      const int v = lane == K_U ? tot[0] : (lane == K_T ? tot[1] : (lane == K_S ? tot[2] : 0));
+      out.cnt[lane * out.n_items + it] = v;
+    }
+  } else if (mode != 0) {
+    const int64_t at0 = out.base[kind] + (out.off[kind * out.n_items + it] - out.off[kind * out.n_items]) +
+                        ex[mode - 1];
+    int *A = kind == K_U ? out.u_t : (kind == K_T ? out.t_a : out.s_a);
+    int *C = kind == K_U ? out.u_s : (kind == K_T ? out.t_c : out.s_c);
+    if (mode == 1) {
+      A[at0] = a;
+      C[at0] = m;
+    } else if (mode == 2) {
+      int j = 0;
+      for (int d = 0; d < c.child_cnt[m]; ++d) {
+        const int ch = c.child_first[m] + d;
+        if (!c.hsrc[ch]) continue;
+        A[at0 + j] = a;
+        C[at0 + j] = ch;
+        ++j;
+      }
+    } else {
+      int j = 0;
+      for (int d = 0; d < c.child_cnt[a]; ++d) {
+        const int ch = c.child_first[a] + d;
+        if (c.te[ch] <= c.ts[ch]) continue;
+        A[at0 + j] = ch;
+        C[at0 + j] = m;
+        ++j;
+      }
+    }
+  }
+  if (EMIT && l >= l_min) {                         // M2L list (uniform format)
+    const int cls = c.cls[a];
+    const int64_t fi = a - far_first;
+    const int fl = st.far_len[cls];
+    const int n_far = a_tgt ? fl : 0;
+    int cnt = 0;
+    for (int e0 = 0; e0 < fl; e0 += 32) {
+      const int e = e0 + lane;
+      int sidx = -1;
+      if (e < n_far) {
+        const int4 q = make_int4(ca.x + st.far_d[cls][e][0], ca.y + st.far_d[cls][e][1],
+                                 ca.z + st.far_d[cls][e][2], 0);
+        uint32_t k;
+        if (cell_at(g, l, q, &k)) {
+          sidx = find_cell_at(c, l, first, count, ibase + k);
+          if (sidx >= 0 && !c.hsrc[sidx]) sidx = -1;
+        }
+      }
+      if (far_full && e < fl) far_full[fi * FAR_MAX + e] = sidx;
+      const unsigned bal = __ballot_sync(0xffffffffu, sidx >= 0);
+      if (sidx >= 0) {
+        const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+        far_src[fi * FAR_MAX + pos] = sidx;
+        far_op[fi * FAR_MAX + pos] = st.far_op[cls][e];
+      }
+      cnt += __popc(bal);
+    }
+    if (lane == 0) {
+      far_cnt[fi] = cnt;
+      if (cls_cnt && fl > 0) {
+        const int pos = atomicAdd(&cls_cnt[cls], 1);
+        cls_cells[(int64_t)cls * cls_cap + pos] = a;
+      }
+    }
+  }
 }
 
 __global__ void k_ad_kind_totals(const int *__restrict__ cnt, const int *__restrict__ off,
@@ -677,9 +753,13 @@ cudaError_t ad_launch_lists(const Geo &g, const Stencils *d_sten, int l, int l_m
   ListOut o{};
   o.cnt = cnt;
   o.n_items = n_items;
-  k_ad_lists<false><<<nblk(n_items, 128), 128, 0, s>>>(g, d_sten, l, l_min, first, count, n_t, n_s,
-                                                      t_a, t_c, s_a, s_c, c, o, 0, nullptr, nullptr,
-                                                      nullptr, nullptr, nullptr, nullptr, 0);
+  if (count > 0)
+    k_ad_cell_lists<false><<<nblk(count * 32, 128), 128, 0, s>>>(g, d_sten, l, l_min, first, count, c, o,
+                                                                 0, nullptr, nullptr, nullptr, nullptr,
+                                                                 nullptr, nullptr, 0);
+  if (n_t + n_s > 0)
+    k_ad_lists<false><<<nblk((n_t + n_s) * 16, 128), 128, 0, s>>>(g, d_sten, l, count, n_t, n_s, t_a, t_c,
+                                                                 s_a, s_c, c, o, count);
   cudaError_t e = exclusive_scan(cnt, off, n_items * K_KINDS, scan_scratch, s);
   if (e != cudaSuccess) return e;
   k_ad_kind_totals<<<1, 32, 0, s>>>(cnt, off, n_items, totals);
@@ -702,10 +782,13 @@ cudaError_t ad_launch_lists_emit(const Geo &g, const Stencils *d_sten, int l, in
   for (int k = 0; k < K_KINDS; ++k) o.base[k] = base[k];
   o.u_t = u_t; o.u_s = u_s; o.w_t = w_t; o.w_s = w_s; o.x_t = x_t; o.x_s = x_s;
   o.t_a = nt_a; o.t_c = nt_c; o.s_a = ns_a; o.s_c = ns_c;
-  k_ad_lists<true><<<nblk(n_items, 128), 128, 0, s>>>(g, d_sten, l, l_min, first, count, n_t, n_s,
-                                                     t_a, t_c, s_a, s_c, c, o, far_first, far_cnt,
-                                                     far_src, far_op, far_full, cls_cnt, cls_cells,
-                                                     cls_cap);
+  if (count > 0)
+    k_ad_cell_lists<true><<<nblk(count * 32, 128), 128, 0, s>>>(g, d_sten, l, l_min, first, count, c, o,
+                                                                far_first, far_cnt, far_src, far_op,
+                                                                far_full, cls_cnt, cls_cells, cls_cap);
+  if (n_t + n_s > 0)
+    k_ad_lists<true><<<nblk((n_t + n_s) * 16, 128), 128, 0, s>>>(g, d_sten, l, count, n_t, n_s, t_a, t_c,
+                                                                s_a, s_c, c, o, count);
   return cudaGetLastError();
 }
 

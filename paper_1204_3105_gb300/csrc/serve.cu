@@ -77,6 +77,24 @@ size_t estimate_bytes(const fmm2d_request &r) {
   return io + pts + tree;
 }
 
+// Continuous batching: small adaptive requests with targets = sources that
+// wait together with equal tiling, eps, p, flags and domain are solved as one
+// forest (fmm2d_build_forest), so the launches and level read-backs of one
+// solve serve them all.
+constexpr int64_t MERGE_MAX_POINTS = (int64_t)1 << 17;     // requests up to this size merge
+constexpr int64_t MERGE_BATCH_POINTS = (int64_t)1 << 21;   // points per forest at most
+constexpr int MERGE_MAX = 256;                              // requests per forest at most
+
+bool mergeable(const fmm2d_request &r) {
+  return (r.flags & FMM2D_ADAPTIVE) && r.tgt_xy == nullptr && r.levels == 0 && r.n_src > 0 &&
+         r.n_src <= MERGE_MAX_POINTS;
+}
+
+bool same_solve(const fmm2d_request &a, const fmm2d_request &b) {
+  return a.tiling == b.tiling && a.flags == b.flags && a.eps == b.eps && a.p == b.p &&
+         a.domain[0] == b.domain[0] && a.domain[1] == b.domain[1] && a.domain[2] == b.domain[2];
+}
+
 unsigned precision_for(double eps, int p) {
   // FP32 expansions cannot reach tolerances much below 1e-7: FP64 expansions
   // with the FP32 P2P down to 1e-9, the FP64 form below
@@ -122,18 +140,17 @@ Job *admit(fmm2d_server *sv) {
   return nullptr;
 }
 
-fmm2d_status run_job(Slot &sl, Job &j) {
-  const fmm2d_request &r = j.req;
-  const bool same = r.tgt_xy == nullptr;
-  const int64_t nt = same ? r.n_src : r.n_tgt;
-  const size_t esz = (r.flags & FMM2D_IN_F32) ? 4 : 8;
+// The slot's plan for request r's parameters (created on first use), with
+// the request's domain set; *flags_out: the precision and input flags used.
+fmm2d_status slot_plan(Slot &sl, const fmm2d_request &r, int64_t n_points, fmm2d_plan **out,
+                       unsigned *flags_out) {
   int p = r.p;
-  if (p == 0) fmm2d_default_params(r.tiling, std::max(r.n_src, nt), 64, r.eps, nullptr, &p, nullptr);
+  if (p == 0) fmm2d_default_params(r.tiling, n_points, 64, r.eps, nullptr, &p, nullptr);
   const unsigned prec = (r.flags & FMM2D_PREC_MASK) ? (r.flags & FMM2D_PREC_MASK) : precision_for(r.eps, p);
   const unsigned flags = prec | (r.flags & (FMM2D_IN_F32 | FMM2D_ADAPTIVE));
   int L = r.levels;
   if (L == 0 && !(flags & FMM2D_ADAPTIVE))
-    fmm2d_default_params(r.tiling, std::max(r.n_src, nt), 64, r.eps, &L, nullptr, nullptr);
+    fmm2d_default_params(r.tiling, n_points, 64, r.eps, &L, nullptr, nullptr);
   auto key = std::make_tuple(r.tiling, flags, L, p);
   fmm2d_plan *pl = sl.plans[key];
   fmm2d_status st;
@@ -150,6 +167,19 @@ fmm2d_status run_job(Slot &sl, Job &j) {
   const double *dom = r.domain;
   st = fmm2d_plan_set_domain(pl, dom[2] > 0 ? dom[0] : 0.0, dom[2] > 0 ? dom[1] : 0.0,
                              dom[2] > 0 ? dom[2] : 1.0);
+  *out = pl;
+  *flags_out = flags;
+  return st;
+}
+
+fmm2d_status run_job(Slot &sl, Job &j) {
+  const fmm2d_request &r = j.req;
+  const bool same = r.tgt_xy == nullptr;
+  const int64_t nt = same ? r.n_src : r.n_tgt;
+  const size_t esz = (r.flags & FMM2D_IN_F32) ? 4 : 8;
+  fmm2d_plan *pl = nullptr;
+  unsigned flags = 0;
+  fmm2d_status st = slot_plan(sl, r, std::max(r.n_src, nt), &pl, &flags);
   if (st != FMM2D_OK) return st;
   cudaStream_t s = sl.stream;
   if (sl.src.reserve(std::max<size_t>(16, r.n_src * 2 * esz)) || sl.u.reserve(std::max<size_t>(16, r.n_src * esz)) ||
@@ -174,30 +204,106 @@ fmm2d_status run_job(Slot &sl, Job &j) {
   return info.device_error ? FMM2D_ETIMEOUT : FMM2D_OK;
 }
 
+// Requests jobs (mergeable, same solve) as one forest: inputs copied one
+// after another into the slot's buffers, one fmm2d_build_forest and one
+// fmm2d_evaluate, each output copied back to its request.
+fmm2d_status run_batch(Slot &sl, std::vector<Job *> &jobs) {
+  const fmm2d_request &r = jobs[0]->req;
+  const size_t esz = (r.flags & FMM2D_IN_F32) ? 4 : 8;
+  std::vector<int64_t> off(jobs.size() + 1, 0);
+  for (size_t i = 0; i < jobs.size(); ++i) off[i + 1] = off[i] + jobs[i]->req.n_src;
+  const int64_t n = off.back();
+  fmm2d_plan *pl = nullptr;
+  unsigned flags = 0;
+  fmm2d_status st = slot_plan(sl, r, n, &pl, &flags);
+  if (st != FMM2D_OK) return st;
+  cudaStream_t s = sl.stream;
+  if (sl.src.reserve(n * 2 * esz) || sl.u.reserve(n * esz) || sl.out.reserve(n * 8)) return FMM2D_ENOMEM;
+  for (size_t i = 0; i < jobs.size(); ++i) {
+    const fmm2d_request &q = jobs[i]->req;
+    cudaMemcpyAsync((char *)sl.src.p + off[i] * 2 * esz, q.src_xy, q.n_src * 2 * esz,
+                    cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync((char *)sl.u.p + off[i] * esz, q.strengths, q.n_src * esz, cudaMemcpyHostToDevice, s);
+  }
+  st = fmm2d_build_forest(pl, sl.src.p, off.data(), (int)jobs.size(), s);
+  if (st != FMM2D_OK) return st;
+  st = fmm2d_evaluate(pl, sl.u.p, (double *)sl.out.p, s);
+  if (st != FMM2D_OK) return st;
+  for (size_t i = 0; i < jobs.size(); ++i)
+    cudaMemcpyAsync(jobs[i]->req.potentials, (double *)sl.out.p + off[i], jobs[i]->req.n_src * 8,
+                    cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return FMM2D_ECUDA;
+  fmm2d_info info;
+  fmm2d_plan_query(pl, &info);
+  for (Job *j : jobs) {
+    j->res.levels = info.levels;
+    j->res.p = info.p;
+    j->res.flags = flags;
+  }
+  return info.device_error ? FMM2D_ETIMEOUT : FMM2D_OK;
+}
+
 void worker(fmm2d_server *sv, Slot *sl) {
   cudaSetDevice(sv->device);
   for (;;) {
-    Job *j = nullptr;
+    std::vector<Job *> batch;
     {
       std::unique_lock<std::mutex> lk(sv->mu);
+      Job *j = nullptr;
       sv->cv_work.wait(lk, [&] { return sv->stop || (j = admit(sv)) != nullptr; });
       if (!j) return;   // stopping
-      j->t_start = Clock::now();
+      batch.push_back(j);
+      if (mergeable(j->req)) {   // queued requests that can share this solve
+        int64_t pts = j->req.n_src;
+        for (auto it = sv->queue.begin(); it != sv->queue.end() && (int)batch.size() < MERGE_MAX;) {
+          Job *k = *it;
+          if (mergeable(k->req) && same_solve(k->req, j->req) && pts + k->req.n_src <= MERGE_BATCH_POINTS &&
+              sv->in_use + k->est_bytes <= sv->budget) {
+            pts += k->req.n_src;
+            sv->in_use += k->est_bytes;
+            ++sv->running;
+            batch.push_back(k);
+            it = sv->queue.erase(it);
+          } else {
+            ++it;
+          }
+        }
+      }
+      const Clock::time_point now = Clock::now();
+      for (Job *k : batch) k->t_start = now;
     }
-    std::memset(&j->res, 0, sizeof(j->res));
-    const fmm2d_status st = run_job(*sl, *j);
+    for (Job *k : batch) std::memset(&k->res, 0, sizeof(k->res));
+    std::vector<fmm2d_status> st(batch.size(), FMM2D_OK);
+    if (batch.size() == 1) {
+      st[0] = run_job(*sl, *batch[0]);
+    } else {
+      const fmm2d_status bs = run_batch(*sl, batch);
+      if (bs == FMM2D_OK) {
+        std::fill(st.begin(), st.end(), FMM2D_OK);
+      } else {   // one request may be at fault (e.g. a point outside the domain): run each alone
+        for (size_t i = 0; i < batch.size(); ++i) {
+          std::memset(&batch[i]->res, 0, sizeof(batch[i]->res));
+          st[i] = run_job(*sl, *batch[i]);
+        }
+      }
+    }
     {
       std::lock_guard<std::mutex> lk(sv->mu);
-      j->t_end = Clock::now();
-      j->res.status = st;
-      j->res.slot = sl->id;
-      j->res.queue_ms = std::chrono::duration<double, std::milli>(j->t_start - j->t_submit).count();
-      j->res.run_ms = std::chrono::duration<double, std::milli>(j->t_end - j->t_start).count();
-      j->res.latency_ms = std::chrono::duration<double, std::milli>(j->t_end - j->t_submit).count();
-      j->done = true;
-      sv->in_use -= j->est_bytes;
-      --sv->running;
-      ++sv->completed;
+      const Clock::time_point now = Clock::now();
+      for (size_t i = 0; i < batch.size(); ++i) {
+        Job *k = batch[i];
+        k->t_end = now;
+        k->res.status = st[i];
+        k->res.slot = sl->id;
+        k->res.batched = (int32_t)batch.size();
+        k->res.queue_ms = std::chrono::duration<double, std::milli>(k->t_start - k->t_submit).count();
+        k->res.run_ms = std::chrono::duration<double, std::milli>(k->t_end - k->t_start).count();
+        k->res.latency_ms = std::chrono::duration<double, std::milli>(k->t_end - k->t_submit).count();
+        k->done = true;
+        sv->in_use -= k->est_bytes;
+        --sv->running;
+        ++sv->completed;
+      }
     }
     sv->cv_done.notify_all();
     sv->cv_work.notify_all();

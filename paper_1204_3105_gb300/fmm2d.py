@@ -59,7 +59,8 @@ class Request(ctypes.Structure):
 
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("levels", ctypes.c_int32), ("p", ctypes.c_int32),
-                ("flags", ctypes.c_uint32), ("slot", ctypes.c_int32), ("queue_ms", ctypes.c_double),
+                ("flags", ctypes.c_uint32), ("slot", ctypes.c_int32), ("batched", ctypes.c_int32),
+                ("queue_ms", ctypes.c_double),
                 ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
 
 

@@ -69,6 +69,42 @@ def test_alone_equals_in_the_mix(fm):
     sv.close()
 
 
+def test_small_requests_merge_into_one_forest(fm):
+    """Small adaptive requests that wait together with equal tiling, eps and
+    flags are solved as one forest; each result equals the same request
+    solved alone within eps, and the direct sum on samples."""
+    sv = fm.Server(8 << 30, max_slots=1)
+    bxy, bu = uniform_square(400000, seed=40, dtype=np.float32)
+    big = np.zeros(len(bxy))
+    tb = sv.submit("quad", bxy, bu, big, eps=1e-6, flags=fm.ADAPTIVE)   # holds the only slot
+    reqs = []
+    for i in range(20):
+        n = 500 + 173 * i
+        if i % 2:
+            xy, u = uniform_square(n, seed=300 + i, dtype=np.float32)
+        else:
+            xy, u = gaussian_mixture(n, seed=300 + i, k=8, dtype=np.float32)
+            u = u.astype(np.float32)
+        o = np.zeros(n)
+        reqs.append((xy, u, o, sv.submit("tri", xy, u, o, eps=1e-6, flags=fm.ADAPTIVE)))
+    res = [sv.wait(t) for (_, _, _, t) in reqs]
+    assert sv.wait(tb)["status"] == 0
+    assert all(r["status"] == 0 for r in res)
+    assert max(r["batched"] for r in res) > 1                       # merged into a forest
+    for (xy, u, o, _), r in zip(reqs, res):
+        a = np.zeros(len(xy))
+        ra = sv.wait(sv.submit("tri", xy, u, a, eps=1e-6, flags=fm.ADAPTIVE))
+        assert ra["status"] == 0 and ra["batched"] == 1             # alone
+        assert np.max(np.abs(a - o)) <= 1e-6 * np.max(np.abs(a))
+    for k in (3, 8):
+        xy, u, o, _ = reqs[k]
+        x64, u64 = xy.astype(np.float64), u.astype(np.float64)
+        idx = sample_targets(len(xy), 200, seed=k)
+        ref = direct(x64, u64, x64[idx])
+        assert np.max(np.abs(o[idx] - ref)) / np.max(np.abs(ref)) < 3e-6
+    sv.close()
+
+
 def test_budget_admission_and_busy(fm):
     xy, u = uniform_square(200000, seed=3, dtype=np.float32)
     est_one = 200000 * (3 * 4 + 2 * 0 + 8) + 200000 * 96 + 200000 * 1024 // 16 + (32 << 20)
