@@ -189,7 +189,7 @@ def run_ours(args):
     u_d = torch.from_numpy(u).to(dev)
     outs = {t: torch.empty(N_POINTS, dtype=torch.float64, device=dev) for t in args.tilings}
     prec = {"tc": fmm2d.PREC_MIXED_TC, "mixed": fmm2d.PREC_MIXED, "fp64": fmm2d.PREC_FP64,
-            "hybrid": fmm2d.PREC_HYBRID}[args.prec]
+            "hybrid": fmm2d.PREC_HYBRID, "split": fmm2d.PREC_SPLIT}[args.prec]
     tuned = {}
     fixed = {}
     for item in filter(None, args.params.split(",")):
@@ -399,7 +399,8 @@ def run_ours(args):
             "metric": "FMM eval points/s at eps=%g (3 tilings)" % args.eps, "value": value, "unit": "points/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "hybrid": "f64 + float-float M2L + f32 pairs P2P"}.get(
+            "dtype": {"fp64": "f64", "hybrid": "f64 + float-float M2L + f32 pairs P2P",
+                      "split": "f64 + float-float M2L"}.get(
                 args.prec, "tf32x3+f32+f64"), "data": "synthetic",
             "config": {"workload": "N=M=2^20 uniform unit square (sources=targets), FP32 points and "
                                    "strengths, quad+sept+tri, eps=%g, %s L/p, %s form" % (args.eps,
@@ -456,8 +457,10 @@ def _pool(n_max, seed):
 def run_clustered(args):
     """The clustered workload: N = M = 4,194,304 points from a 32-component
     Gaussian mixture, strengths N(0, 1), FP64, eps = 1e-10, quadtree and
-    septree on adaptive trees (leaf size 64).  One step = build + evaluate of
-    both tilings; device time with CUDA events, inputs resident."""
+    septree on adaptive trees (leaf size 64), FP64 leading terms with the
+    split-precision M2L (the plain FP64 form timed beside it).  One step =
+    build + evaluate of both tilings; device time with CUDA events, inputs
+    resident."""
     import torch
     from paper_1204_3105_gb300 import fmm2d
     from paper_1204_3105_gb300.inputs import gaussian_mixture
@@ -470,9 +473,12 @@ def run_clustered(args):
     u_d = torch.from_numpy(u).to(dev)
     out = torch.empty(n, dtype=torch.float64, device=dev)
     names = ("quad", "sept")
+    # FP64 leading terms with the split-precision (float-float) M2L; --prec
+    # fp64 runs the plain FP64 form
+    form = fmm2d.PREC_FP64 if args.prec == "fp64" else fmm2d.PREC_SPLIT
     plans = {}
     for t in names:
-        plans[t] = fmm2d.Plan(t, 0, 0, 1e-10, fmm2d.PREC_FP64 | fmm2d.ADAPTIVE)
+        plans[t] = fmm2d.Plan(t, 0, 0, 1e-10, form | fmm2d.ADAPTIVE)
         plans[t].set_leaf_size(args.leaf_size)
     flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device=dev)
 
@@ -505,11 +511,36 @@ def run_clustered(args):
     info = {t: plans[t].query() for t in names}
     stages = {t: {k: v[0] for k, v in plans[t].stage_times().items()} for t in names}
     ms = sum(statistics.mean(v) for v in per.values())
+    fp64_form = None
+    if form != fmm2d.PREC_FP64 and not args.no_fp64_form:   # the plain FP64 form on the same points
+        f64 = {}
+        for t in names:
+            pl = fmm2d.Plan(t, 0, 0, 1e-10, fmm2d.PREC_FP64 | fmm2d.ADAPTIVE)
+            pl.set_leaf_size(args.leaf_size)
+            ts = []
+            for it in range(3):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pl.build(xy_d, n, xy_d, n, stream)
+                pl.evaluate(u_d, out, stream)
+                e1.record(stream)
+                e1.synchronize()
+                if it > 0:
+                    ts.append(e0.elapsed_time(e1))
+                flush.zero_()
+            pl.close()
+            f64[t] = statistics.mean(ts)
+        fp64_form = {"value": len(names) * n / (sum(f64.values()) / 1e3), "unit": "points/s",
+                     "ms_per_step": sum(f64.values()), "per_tiling_ms": f64,
+                     "speedup_of_split": sum(f64.values()) / ms}
     line = {
-        "metric": "clustered FMM points/s (4,194,304 points, 32-cluster mixture, eps=1e-10, FP64)",
+        "metric": "clustered FMM points/s (4,194,304 points, 32-cluster mixture, eps=1e-10, %s)" % (
+            "FP64" if form == fmm2d.PREC_FP64 else "FP64 leading terms, split-precision M2L"),
         "value": len(names) * n / (ms / 1e3), "unit": "points/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if form == fmm2d.PREC_FP64 else "f64 + float-float M2L",
+        "data": "synthetic", "fp64_form": fp64_form,
         "config": {"workload": "N=M=4194304 Gaussian mixture (32 components, sigma log-uniform "
                                "[1e-3, 1e-1]), strengths N(0,1) FP64, quad + sept, eps=1e-10, adaptive "
                                "trees, leaf size %d" % args.leaf_size, "l2": "flushed between tilings"},
@@ -711,7 +742,8 @@ def run_server_workload(args):
                    "eps": "1e-6" if args.workload == "batch" else "1e-4 (mixed form) / 1e-8 (hybrid form)",
                    "arrival_rate_per_s": None if args.workload == "batch" else args.rate,
                    "points": "uniform" if args.workload == "batch" else "uniform / 8-cluster mixture",
-                   "tree": tree + (" (leaf size 64)" if tree == "adaptive" else ""),
+                   "tree": tree + (" (leaf size chosen by the server: quad 64, sept and tri 128)"
+                                   if tree == "adaptive" else ""),
                    "io": "host numpy buffers, copies inside each request",
                    "warmup": "untimed: one 2000-point request per (tiling, eps) per slot"},
     }
@@ -724,7 +756,8 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="tc", choices=["tc", "mixed", "fp64", "hybrid"])
+    ap.add_argument("--prec", default="tc", choices=["tc", "mixed", "fp64", "hybrid", "split"],
+                    help="fmm workload: precision form (clustered: split unless fp64)")
     ap.add_argument("--eps", type=float, default=EPS, help="fmm workload: requested tolerance")
     ap.add_argument("--tilings", default=",".join(TILINGS))
     ap.add_argument("--ref-points", type=int, default=16384)

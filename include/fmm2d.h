@@ -65,10 +65,17 @@ typedef enum {
                                      leading Q log term, L_0 and the final sums in FP64 */
 #define FMM2D_PREC_MIXED_TC 0x2u  /* as MIXED, with M2L on the tensor cores
                                      (split hi/lo TF32 products, FP32 accumulation) */
-#define FMM2D_PREC_HYBRID   0x3u  /* FP64 expansions and translations (P2M ... L2P),
-                                     FP32 P2P with compensated sums: for tolerances
-                                     between about 1e-9 and 1e-6 */
-#define FMM2D_PREC_MASK     0x3u
+#define FMM2D_PREC_HYBRID   0x3u  /* FP64 expansions, P2M, M2M, L2L and L2P, the M2L
+                                     of FMM2D_PREC_SPLIT, and a P2P in FP32 pairs
+                                     (float-float r^2 and log2, exact products,
+                                     error-free sums): for tolerances between about
+                                     1e-9 and 1e-6 */
+#define FMM2D_PREC_SPLIT    0x4u  /* as FP64, with the M2L sums in float-float
+                                     (hi + lo FP32 pairs, exact products,
+                                     error-free sums) on the FP32 pipes: the
+                                     FP64 leading terms and a split-precision
+                                     M2L, for tolerances down to about 1e-12 */
+#define FMM2D_PREC_MASK     0x7u
 #define FMM2D_IN_F32        0x10u /* points and strengths are float32 (default float64) */
 #define FMM2D_ADAPTIVE      0x20u /* adaptive tree for clustered input: a cell is split
                                      while it holds more than the leaf size (default 64,
@@ -347,11 +354,12 @@ typedef struct {
   int32_t levels;          /* leaf level, 0 = planner */
   int32_t p;               /* expansion order, 0 = from eps */
   uint32_t flags;          /* FMM2D_IN_F32, optionally FMM2D_PREC_* and
-                              FMM2D_ADAPTIVE (leaf size 64; levels = finest
-                              level, 0 = the default); with no precision bit
-                              the server uses the tensor-core mixed form for
-                              eps >= 1e-6, the hybrid form down to 1e-9 and
-                              the FP64 form below */
+                              FMM2D_ADAPTIVE (leaf size 64 for the quadtree,
+                              128 for the septree and the triangle tiling;
+                              levels = finest level, 0 = the default); with no
+                              precision bit the server uses the tensor-core
+                              mixed form for eps >= 1e-6, the hybrid form down
+                              to 1e-9 and the split form below */
   double eps;
   double domain[3];        /* x0, y0, S; S <= 0 means the unit square */
   const void *src_xy;      /* n_src interleaved points */

@@ -376,9 +376,14 @@ fmm2d_status cuda_fail(fmm2d_plan *pl, cudaError_t e, const char *where) {
 // FP64 expansions (the FP64 form and the hybrid form)
 bool is_fp64(const fmm2d_plan *pl) {
   const unsigned pr = pl->flags & FMM2D_PREC_MASK;
-  return pr == FMM2D_PREC_FP64 || pr == FMM2D_PREC_HYBRID;
+  return pr == FMM2D_PREC_FP64 || pr == FMM2D_PREC_HYBRID || pr == FMM2D_PREC_SPLIT;
 }
 bool is_hybrid(const fmm2d_plan *pl) { return (pl->flags & FMM2D_PREC_MASK) == FMM2D_PREC_HYBRID; }
+// forms whose M2L runs in float-float on the FP32 pipes (k_m2l_ff)
+static bool ff_m2l(const fmm2d_plan *pl) {
+  const unsigned pr = pl->flags & FMM2D_PREC_MASK;
+  return pr == FMM2D_PREC_HYBRID || pr == FMM2D_PREC_SPLIT;
+}
 
 struct StageScope {
   fmm2d_plan *pl;
@@ -564,7 +569,7 @@ fmm2d_status setup_geometry(fmm2d_plan *pl) {
     cudaGetDevice(&dev);
     CK(cudaDeviceGetAttribute(&pl->n_sms, cudaDevAttrMultiProcessorCount, dev), "sm count");
   }
-  if (is_hybrid(pl)) {   // float-float operators for the FP32-pipe M2L
+  if (ff_m2l(pl)) {   // float-float operators for the FP32-pipe M2L
     std::vector<float> A, ph;
     ff_build_table(T.zeta, m2l, p, A, ph);
     CK(dbuf_reserve(pl->d_ff_ops, A.size() * 4), "alloc ff ops");
@@ -646,7 +651,7 @@ fmm2d_status evaluate_t(fmm2d_plan *pl, const void *u, double *out, cudaStream_t
   if (L < pl->l_min) {
     CK(cudaMemsetAsync(lL0, 0, pl->n_cells * sizeof(double), f), "zero locals");
     CK(cudaMemsetAsync(lb, 0, pl->n_cells * pl->P * sizeof(Cx<R>), f), "zero locals");
-  } else if (is_hybrid(pl)) {
+  } else if (ff_m2l(pl)) {
     StageScope sc(pl, ST_M2L, f, 1);
     CK(run_m2l_ff(pl, L, pl->lev_first[pl->l_min], mQ, ma, lL0, lb, f), "m2l_ff");
   } else if ((pl->flags & FMM2D_PREC_MASK) == FMM2D_PREC_MIXED_TC) {
@@ -775,7 +780,7 @@ static fmm2d_status build_adaptive(fmm2d_plan *pl, const void *src, int64_t n_sr
   const bool tc_form = (pl->flags & FMM2D_PREC_MASK) == FMM2D_PREC_MIXED_TC;
   if (tc_form && !tc_shape(p, &pl->tc_K, &pl->tc_N))
     return fail(pl, FMM2D_EINVAL, "tensor-core M2L supports p <= 31");
-  const bool tc = tc_form || is_hybrid(pl);   // class lists: tensor-core and float-float M2L
+  const bool tc = tc_form || ff_m2l(pl);   // class lists: tensor-core and float-float M2L
   pl->L = L;
   pl->p = p;
   pl->P = (p + 1) & ~1;
@@ -1166,7 +1171,7 @@ fmm2d_status evaluate_adaptive_t(fmm2d_plan *pl, const void *u, double *out, cud
                        (const Cx<R> *)pl->d_m2l_ops.p, (const double *)pl->d_m2l_logz.p, mQ, ma,
                        lL0, lb, f), "m2l");
     }
-  } else if (is_hybrid(pl)) {
+  } else if (ff_m2l(pl)) {
     StageScope sc(pl, ST_M2L, f, 1);
     CK(run_m2l_ff(pl, L, pl->n_cells - pl->n_far_cells, mQ, ma, lL0, lb, f), "m2l_ff");
   } else {
@@ -1254,7 +1259,8 @@ fmm2d_status fmm2d_plan_create(int tiling, int levels, int p, double eps, unsign
   if (levels < 0 || levels > max_levels_for(tiling, flags)) { g_create_err = "levels out of range"; return FMM2D_EINVAL; }
   if (p < 0 || p > MAXP) { g_create_err = "p out of range (0..48)"; return FMM2D_EINVAL; }
   if (p == 0 && !(eps > 0.0 && eps < 1.0)) { g_create_err = "eps must be in (0, 1)"; return FMM2D_EINVAL; }
-  if ((flags & ~(FMM2D_PREC_MASK | FMM2D_IN_F32 | FMM2D_ADAPTIVE)) != 0) {
+  if ((flags & ~(FMM2D_PREC_MASK | FMM2D_IN_F32 | FMM2D_ADAPTIVE)) != 0 ||
+      (flags & FMM2D_PREC_MASK) > FMM2D_PREC_SPLIT) {
     g_create_err = "unknown flags";
     return FMM2D_EINVAL;
   }
@@ -1325,7 +1331,7 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
   const bool tc_form = (pl->flags & FMM2D_PREC_MASK) == FMM2D_PREC_MIXED_TC;
   if (tc_form && !tc_shape(p, &pl->tc_K, &pl->tc_N))
     return fail(pl, FMM2D_EINVAL, "tensor-core M2L supports p <= 31");
-  const bool tc = tc_form || is_hybrid(pl);   // class lists: tensor-core and float-float M2L
+  const bool tc = tc_form || ff_m2l(pl);   // class lists: tensor-core and float-float M2L
   pl->L = L;
   pl->p = p;
   pl->P = (p + 1) & ~1;   // even stride: rows of complex values stay 16-byte aligned

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libfmm2d.so")
 
 QUAD, SEPT, TRI = 0, 1, 2
 TILINGS = {"quad": QUAD, "sept": SEPT, "tri": TRI}
-PREC_FP64, PREC_MIXED, PREC_MIXED_TC, PREC_HYBRID = 0x0, 0x1, 0x2, 0x3
+PREC_FP64, PREC_MIXED, PREC_MIXED_TC, PREC_HYBRID, PREC_SPLIT = 0x0, 0x1, 0x2, 0x3, 0x4
 IN_F32 = 0x10
 ADAPTIVE = 0x20
 

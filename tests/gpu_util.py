@@ -20,7 +20,7 @@ def run_gpu(tiling, src, u, tgt=None, levels=0, p=0, eps=1e-6, prec="mixed", f32
     t = _torch()
     dev = t.device("cuda:0")
     flags = {"fp64": fmm2d.PREC_FP64, "mixed": fmm2d.PREC_MIXED, "tc": fmm2d.PREC_MIXED_TC,
-             "hybrid": fmm2d.PREC_HYBRID}[prec]
+             "hybrid": fmm2d.PREC_HYBRID, "split": fmm2d.PREC_SPLIT}[prec]
     dt = np.float32 if f32 else np.float64
     if f32:
         flags |= fmm2d.IN_F32

@@ -49,12 +49,12 @@ CASES = [("quad", 8, 24), ("sept", 5, 16), ("tri", 8, 24)]
 
 
 @pytest.mark.parametrize("tiling,L,cap", CASES)
-@pytest.mark.parametrize("separate", [False, True])
-def test_tree_and_lists_bit_exact(tiling, L, cap, separate):
+@pytest.mark.parametrize("separate,prec", [(False, "fp64"), (True, "fp64"), (False, "split")])
+def test_tree_and_lists_bit_exact(tiling, L, cap, separate, prec):
     xy, u = _clustered(3000, seed=31)
     txy = _clustered(2000, seed=32)[0] if separate else None
     p = 6
-    phi, plan = run_gpu(tiling, xy, u, txy, levels=L, p=p, prec="fp64", keep=True, leaf_size=cap)
+    phi, plan = run_gpu(tiling, xy, u, txy, levels=L, p=p, prec=prec, keep=True, leaf_size=cap)
     r = adaptive_fmm(make_tiling(tiling, L), xy, u, xy if txy is None else txy, p, s=cap, record=True)
     cells = plan.export("ad_cells")
     want = sorted((l, n, int((l, n) in r.split)) for l, cs in enumerate(r.cells) for n in cs)

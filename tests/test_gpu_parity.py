@@ -250,6 +250,26 @@ def test_hybrid_far_field_matches_oracle(tiling, L, p):
     assert rel_inf_error(phi, r.phi) < 1e-8
 
 
+@pytest.mark.parametrize("tiling,L,p", CASES + [("quad", 4, 30), ("sept", 3, 28), ("tri", 4, 36)])
+def test_split_form_matches_oracle(tiling, L, p):
+    """FMM2D_PREC_SPLIT (FP64 with the float-float M2L): potentials, near
+    field and per-level locals against the FP64 oracle to the FP64 form's
+    tolerances."""
+    n = 6007
+    xy, u = uniform_square(n, seed=5)
+    phi, plan = run_gpu(tiling, xy, u, levels=L, p=p, prec="split", keep=True)
+    r, T = _oracle(tiling, L, xy, u, None, p)
+    assert rel_inf_error(phi, r.phi) < 1e-11
+    assert rel_inf_error(plan.export("phi_near"), r.phi_near) < 1e-11
+    for l in range(T.l_min, L + 1):
+        lg = plan.export("locals", l)
+        for i, key in enumerate(r.cells[l]):
+            b = r.loc[(l, key)]
+            assert abs(lg[i, 0].real - b[0].real) <= 1e-10 * max(1.0, np.abs(b).max())
+            assert np.max(np.abs(lg[i, 1:] - b[1:])) <= 1e-9 * (np.abs(b[1:]).max() + 1e-300)
+    plan.close()
+
+
 def test_plain_fp64_quadtree_8192():
     """The plain FP64 quadtree configuration: N = M = 8192 uniform points,
     strengths U[-1, 1], p = 16, 4 levels (leaf <= 64 on average): against the
