@@ -475,7 +475,7 @@ def run_clustered(args):
     names = ("quad", "sept")
     # FP64 leading terms with the split-precision (float-float) M2L; --prec
     # fp64 runs the plain FP64 form
-    form = fmm2d.PREC_FP64 if args.prec == "fp64" else fmm2d.PREC_SPLIT
+    form = {"fp64": fmm2d.PREC_FP64, "hybrid": fmm2d.PREC_HYBRID}.get(args.prec, fmm2d.PREC_SPLIT)
     plans = {}
     for t in names:
         plans[t] = fmm2d.Plan(t, 0, 0, 1e-10, form | fmm2d.ADAPTIVE)
@@ -511,14 +511,13 @@ def run_clustered(args):
     info = {t: plans[t].query() for t in names}
     stages = {t: {k: v[0] for k, v in plans[t].stage_times().items()} for t in names}
     ms = sum(statistics.mean(v) for v in per.values())
-    fp64_form = None
-    if form != fmm2d.PREC_FP64 and not args.no_fp64_form:   # the plain FP64 form on the same points
-        f64 = {}
+    def leg(lform, steps=2):   # another precision form on the same points
+        ms_t = {}
         for t in names:
-            pl = fmm2d.Plan(t, 0, 0, 1e-10, fmm2d.PREC_FP64 | fmm2d.ADAPTIVE)
+            pl = fmm2d.Plan(t, 0, 0, 1e-10, lform | fmm2d.ADAPTIVE)
             pl.set_leaf_size(args.leaf_size)
             ts = []
-            for it in range(3):
+            for it in range(1 + steps):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
@@ -530,17 +529,26 @@ def run_clustered(args):
                     ts.append(e0.elapsed_time(e1))
                 flush.zero_()
             pl.close()
-            f64[t] = statistics.mean(ts)
-        fp64_form = {"value": len(names) * n / (sum(f64.values()) / 1e3), "unit": "points/s",
-                     "ms_per_step": sum(f64.values()), "per_tiling_ms": f64,
-                     "speedup_of_split": sum(f64.values()) / ms}
+            ms_t[t] = statistics.mean(ts)
+        tot = sum(ms_t.values())
+        return {"value": len(names) * n / (tot / 1e3), "unit": "points/s", "ms_per_step": tot,
+                "per_tiling_ms": ms_t, "time_vs_headline": tot / ms}
+
+    fp64_form = hybrid_form = None
+    if not args.no_fp64_form:
+        if form != fmm2d.PREC_FP64:
+            fp64_form = leg(fmm2d.PREC_FP64)
+        if form != fmm2d.PREC_HYBRID:   # FP32-pair P2P: within 1e-10 here (sampled test)
+            hybrid_form = leg(fmm2d.PREC_HYBRID)
     line = {
         "metric": "clustered FMM points/s (4,194,304 points, 32-cluster mixture, eps=1e-10, %s)" % (
-            "FP64" if form == fmm2d.PREC_FP64 else "FP64 leading terms, split-precision M2L"),
+            {fmm2d.PREC_FP64: "FP64", fmm2d.PREC_HYBRID: "hybrid form"}.get(
+                form, "FP64 leading terms, split-precision M2L")),
         "value": len(names) * n / (ms / 1e3), "unit": "points/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if form == fmm2d.PREC_FP64 else "f64 + float-float M2L",
-        "data": "synthetic", "fp64_form": fp64_form,
+        "vs_baseline": None, "dtype": {fmm2d.PREC_FP64: "f64", fmm2d.PREC_HYBRID: "f64 + float-float M2L + f32 pairs P2P"}.get(
+            form, "f64 + float-float M2L"),
+        "data": "synthetic", "fp64_form": fp64_form, "hybrid_form": hybrid_form,
         "config": {"workload": "N=M=4194304 Gaussian mixture (32 components, sigma log-uniform "
                                "[1e-3, 1e-1]), strengths N(0,1) FP64, quad + sept, eps=1e-10, adaptive "
                                "trees, leaf size %d" % args.leaf_size, "l2": "flushed between tilings"},

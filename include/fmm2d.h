@@ -343,7 +343,13 @@ fmm2d_status fmm2d_keys_sort_noalloc(int tiling, int levels, double leaf_scale,
 /* ------------------------------------------------------------------------
  * Serving: a continuous-batching server for FMM solves.  The paper has no
  * serving layer; each request runs the evaluation of fmm2d_build +
- * fmm2d_evaluate.
+ * fmm2d_evaluate.  Requests are admitted, oldest first, as execution slots
+ * and the HBM budget allow, and run concurrently on the slots' streams;
+ * small adaptive requests (targets = sources, at most 131072 points) that
+ * wait together with equal tiling, eps, p, flags and domain are solved as
+ * one forest (fmm2d_build_forest), their results equal to the requests
+ * solved alone within eps.  If such a merged solve fails, its requests are
+ * run one by one, so each gets its own status.
  * ---------------------------------------------------------------------- */
 typedef struct fmm2d_server fmm2d_server;
 

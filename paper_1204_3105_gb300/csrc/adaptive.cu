@@ -317,6 +317,124 @@ struct Emitter {
   }
 };
 
+// true when no cell of Near(fine, lf) lies inside the coarser cell `coarse`
+__device__ bool separated(const Geo &g, const Stencils &st, int lf, int4 fcrd, int lc, uint32_t coarse) {
+  const int o = (g.tiling == FMM2D_TRI && fcrd.w == 0) ? 1 : 0;
+  for (int e = 0; e < st.near_len[o]; ++e) {
+    const int4 q = make_int4(fcrd.x + st.near_d[o][e][0], fcrd.y + st.near_d[o][e][1],
+                             fcrd.z + st.near_d[o][e][2], 0);
+    uint32_t k;
+    if (!cell_at(g, lf, q, &k)) continue;
+    if (parent_key(g.tiling, k, lf - lc) == coarse) return false;
+  }
+  return true;
+}
+
+// One thread per item it0 .. it1 - 1 (cells of level l, then W tests, then X
+// tests): for levels with enough items to fill the GPU, where the cooperative
+// forms below would mostly idle lanes.
+template <bool EMIT>
+__global__ void k_ad_lists_1t(Geo g, const Stencils *__restrict__ stp, int l, int l_min,
+                           int64_t first, int64_t count, int64_t n_t, int64_t n_s,
+                           const int *__restrict__ t_a, const int *__restrict__ t_c,
+                           const int *__restrict__ s_a, const int *__restrict__ s_c, AdCells c,
+                           ListOut out, int64_t far_first, int *__restrict__ far_cnt,
+                           int *__restrict__ far_src, uint16_t *__restrict__ far_op,
+                           int *__restrict__ far_full, int *__restrict__ cls_cnt,
+                           int *__restrict__ cls_cells, int64_t cls_cap, int64_t it0, int64_t it1) {
+  const int64_t it = it0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (it >= it1) return;
+  const Stencils &st = *stp;
+  Emitter<EMIT> em(out, it);
+  if (it < count) {                                   // a cell of level l
+    const int a = (int)(first + it);
+    const bool a_tgt = c.te[a] > c.ts[a];
+    const int4 ca = c.crd[a];
+    uint32_t inst;
+    local_key(g.b, l, c.key[a], &inst);
+    const uint32_t ibase = (uint32_t)((uint64_t)inst * level_span(g.b, l));
+    if (a_tgt) {
+      const int o = (g.tiling == FMM2D_TRI && ca.w == 0) ? 1 : 0;
+      const bool a_leaf = !c.split[a];
+      for (int e = 0; e < st.near_len[o]; ++e) {
+        const int4 q = make_int4(ca.x + st.near_d[o][e][0], ca.y + st.near_d[o][e][1],
+                                 ca.z + st.near_d[o][e][2], 0);
+        uint32_t k;
+        if (!cell_at(g, l, q, &k)) continue;
+        const int m = find_cell_at(c, l, first, count, ibase + k);
+        if (m < 0 || !c.hsrc[m]) continue;
+        const bool m_leaf = !c.split[m];
+        if (a_leaf && m_leaf) {
+          em.put(K_U, a, m);
+        } else if (a_leaf) {
+          for (int d = 0; d < c.child_cnt[m]; ++d) {
+            const int ch = c.child_first[m] + d;
+            if (c.hsrc[ch]) em.put(K_T, a, ch);
+          }
+        } else if (m_leaf) {
+          for (int d = 0; d < c.child_cnt[a]; ++d) {
+            const int ch = c.child_first[a] + d;
+            if (c.te[ch] > c.ts[ch]) em.put(K_S, ch, m);
+          }
+        }
+      }
+    }
+    if (EMIT && l >= l_min) {                         // M2L list (uniform format)
+      const int cls = c.cls[a];
+      const int64_t fi = a - far_first;
+      int cnt = 0;
+      const int n_far = a_tgt ? st.far_len[cls] : 0;
+      for (int e = 0; e < st.far_len[cls]; ++e) {
+        int sidx = -1;
+        if (e < n_far) {
+          const int4 q = make_int4(ca.x + st.far_d[cls][e][0], ca.y + st.far_d[cls][e][1],
+                                   ca.z + st.far_d[cls][e][2], 0);
+          uint32_t k;
+          if (cell_at(g, l, q, &k)) {
+            sidx = find_cell_at(c, l, first, count, ibase + k);
+            if (sidx >= 0 && !c.hsrc[sidx]) sidx = -1;
+          }
+        }
+        if (far_full) far_full[fi * FAR_MAX + e] = sidx;
+        if (sidx < 0) continue;
+        far_src[fi * FAR_MAX + cnt] = sidx;
+        far_op[fi * FAR_MAX + cnt] = st.far_op[cls][e];
+        ++cnt;
+      }
+      far_cnt[fi] = cnt;
+      if (cls_cnt && st.far_len[cls] > 0) {
+        const int pos = atomicAdd(&cls_cnt[cls], 1);
+        cls_cells[(int64_t)cls * cls_cap + pos] = a;
+      }
+    }
+  } else if (it < count + n_t) {                      // W test: leaf a, finer cell cc
+    const int64_t j = it - count;
+    const int a = t_a[j], cc = t_c[j];
+    uint32_t inst;
+    if (separated(g, st, l, c.crd[cc], c.lev[a], local_key(g.b, c.lev[a], c.key[a], &inst)))
+      em.put(K_W, a, cc);
+    else if (!c.split[cc]) em.put(K_U, a, cc);
+    else
+      for (int d = 0; d < c.child_cnt[cc]; ++d) {
+        const int ch = c.child_first[cc] + d;
+        if (c.hsrc[ch]) em.put(K_T, a, ch);
+      }
+  } else {                                            // X test: cell a, coarser leaf cc
+    const int64_t j = it - count - n_t;
+    const int a = s_a[j], cc = s_c[j];
+    uint32_t inst;
+    if (separated(g, st, l, c.crd[a], c.lev[cc], local_key(g.b, c.lev[cc], c.key[cc], &inst)))
+      em.put(K_X, a, cc);
+    else if (!c.split[a]) em.put(K_U, a, cc);
+    else
+      for (int d = 0; d < c.child_cnt[a]; ++d) {
+        const int ch = c.child_first[a] + d;
+        if (c.te[ch] > c.ts[ch]) em.put(K_S, ch, cc);
+      }
+  }
+  em.done();
+}
+
 // The W and X tests of level l, items it0 = count, count + 1, ...: half a
 // warp per test, lane e of the half checking Near stencil entry e of the
 // finer cell (does it lie inside the coarser one?); lane 0 of the half then
@@ -737,6 +855,12 @@ cudaError_t ad_launch_rel(bool f32_in, bool f32_out, const void *xy, const uint3
   return cudaGetLastError();
 }
 
+// Above these item counts a level fills the GPU with one thread per item
+// (~52 dependent lookups per cell, 13 stencil checks per test) and the
+// cooperative forms (32 lanes per cell, 16 per test) would mostly idle lanes.
+constexpr int64_t COOP_MAX_CELLS = (int64_t)1 << 18;
+constexpr int64_t COOP_MAX_TESTS = (int64_t)1 << 19;
+
 cudaError_t ad_launch_hash(int64_t n_cells, const AdCells &c, unsigned long long *hkey, int *hval,
                            int hbits, cudaStream_t s) {
   if (n_cells <= 0) return cudaSuccess;
@@ -753,11 +877,20 @@ cudaError_t ad_launch_lists(const Geo &g, const Stencils *d_sten, int l, int l_m
   ListOut o{};
   o.cnt = cnt;
   o.n_items = n_items;
-  if (count > 0)
+  if (count > COOP_MAX_CELLS)
+    k_ad_lists_1t<false><<<nblk(count, 128), 128, 0, s>>>(g, d_sten, l, l_min, first, count, n_t, n_s, t_a,
+                                                         t_c, s_a, s_c, c, o, 0, nullptr, nullptr, nullptr,
+                                                         nullptr, nullptr, nullptr, 0, 0, count);
+  else if (count > 0)
     k_ad_cell_lists<false><<<nblk(count * 32, 128), 128, 0, s>>>(g, d_sten, l, l_min, first, count, c, o,
                                                                  0, nullptr, nullptr, nullptr, nullptr,
                                                                  nullptr, nullptr, 0);
-  if (n_t + n_s > 0)
+  if (n_t + n_s > COOP_MAX_TESTS)
+    k_ad_lists_1t<false><<<nblk(n_t + n_s, 128), 128, 0, s>>>(g, d_sten, l, l_min, first, count, n_t, n_s,
+                                                             t_a, t_c, s_a, s_c, c, o, 0, nullptr, nullptr,
+                                                             nullptr, nullptr, nullptr, nullptr, 0, count,
+                                                             n_items);
+  else if (n_t + n_s > 0)
     k_ad_lists<false><<<nblk((n_t + n_s) * 16, 128), 128, 0, s>>>(g, d_sten, l, count, n_t, n_s, t_a, t_c,
                                                                  s_a, s_c, c, o, count);
   cudaError_t e = exclusive_scan(cnt, off, n_items * K_KINDS, scan_scratch, s);
@@ -782,11 +915,21 @@ cudaError_t ad_launch_lists_emit(const Geo &g, const Stencils *d_sten, int l, in
   for (int k = 0; k < K_KINDS; ++k) o.base[k] = base[k];
   o.u_t = u_t; o.u_s = u_s; o.w_t = w_t; o.w_s = w_s; o.x_t = x_t; o.x_s = x_s;
   o.t_a = nt_a; o.t_c = nt_c; o.s_a = ns_a; o.s_c = ns_c;
-  if (count > 0)
+  if (count > COOP_MAX_CELLS)
+    k_ad_lists_1t<true><<<nblk(count, 128), 128, 0, s>>>(g, d_sten, l, l_min, first, count, n_t, n_s, t_a,
+                                                        t_c, s_a, s_c, c, o, far_first, far_cnt, far_src,
+                                                        far_op, far_full, cls_cnt, cls_cells, cls_cap, 0,
+                                                        count);
+  else if (count > 0)
     k_ad_cell_lists<true><<<nblk(count * 32, 128), 128, 0, s>>>(g, d_sten, l, l_min, first, count, c, o,
                                                                 far_first, far_cnt, far_src, far_op,
                                                                 far_full, cls_cnt, cls_cells, cls_cap);
-  if (n_t + n_s > 0)
+  if (n_t + n_s > COOP_MAX_TESTS)
+    k_ad_lists_1t<true><<<nblk(n_t + n_s, 128), 128, 0, s>>>(g, d_sten, l, l_min, first, count, n_t, n_s,
+                                                            t_a, t_c, s_a, s_c, c, o, far_first, far_cnt,
+                                                            far_src, far_op, far_full, cls_cnt, cls_cells,
+                                                            cls_cap, count, n_items);
+  else if (n_t + n_s > 0)
     k_ad_lists<true><<<nblk((n_t + n_s) * 16, 128), 128, 0, s>>>(g, d_sten, l, count, n_t, n_s, t_a, t_c,
                                                                 s_a, s_c, c, o, count);
   return cudaGetLastError();

@@ -449,6 +449,8 @@ static cudaError_t run_m2l_ff(fmm2d_plan *pl, int L, int64_t far_first, const do
   t.ma = (const double2 *)ma;
   t.lL0 = lL0;
   t.lb = (double2 *)lb;
+  t.ma_ff = (float4 *)pl->d_ma_ff.p;
+  t.n_cells = pl->n_cells;
   return launch_m2l_ff(t, pl->n_far_cells, f);
 }
 
@@ -1064,6 +1066,7 @@ static fmm2d_status build_adaptive(fmm2d_plan *pl, const void *src, int64_t n_sr
   CK(dbuf_reserve(pl->d_mQ, n_cells * 8), "alloc");
   CK(dbuf_reserve(pl->d_lL0, n_cells * 8), "alloc");
   CK(dbuf_reserve(pl->d_ma, need_exp * csz), "alloc");
+  if (ff_m2l(pl)) CK(dbuf_reserve(pl->d_ma_ff, n_cells * (pl->p + 1) * sizeof(float4)), "alloc");
   CK(dbuf_reserve(pl->d_lb, need_exp * csz), "alloc");
   CK(cudaStreamSynchronize(s), "build sync");
   CK(cudaGetLastError(), "build");
@@ -1413,6 +1416,7 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
   CK(dbuf_reserve(pl->d_mQ, cap_cells * 8), "alloc");
   CK(dbuf_reserve(pl->d_lL0, cap_cells * 8), "alloc");
   CK(dbuf_reserve(pl->d_ma, cap_cells * pl->P * csz), "alloc");
+  if (ff_m2l(pl)) CK(dbuf_reserve(pl->d_ma_ff, cap_cells * (pl->p + 1) * sizeof(float4)), "alloc");
   CK(dbuf_reserve(pl->d_lb, cap_cells * pl->P * csz), "alloc");
   CK(dbuf_reserve(pl->d_far_cnt, cap_list * 4), "alloc");
   CK(dbuf_reserve(pl->d_far_src, cap_list * FAR_MAX * 4), "alloc");
@@ -1828,7 +1832,7 @@ void fmm2d_plan_destroy(fmm2d_plan *pl) {
                   &pl->d_cell_cls, &pl->d_cell_hsrc, &pl->d_src_start, &pl->d_src_end,
                   &pl->d_tgt_start, &pl->d_tgt_end, &pl->d_lev_first, &pl->d_far_cnt,
                   &pl->d_far_src, &pl->d_far_op, &pl->d_near_cnt, &pl->d_near_src, &pl->d_src4,
-                  &pl->d_tgt2, &pl->d_mQ, &pl->d_ma, &pl->d_lL0, &pl->d_lb, &pl->d_phi_near,
+                  &pl->d_tgt2, &pl->d_mQ, &pl->d_ma, &pl->d_ma_ff, &pl->d_lL0, &pl->d_lb, &pl->d_phi_near,
                   &pl->d_phi_far, &pl->d_sten, &pl->d_geo_scale, &pl->d_m2l_ops, &pl->d_m2l_logz,
                   &pl->d_m2m_ops, &pl->d_l2l_ops, &pl->d_counts, &pl->d_far_full,
                   &pl->d_cls_cnt, &pl->d_cls_cells, &pl->d_tc_ops, &pl->d_ff_ops, &pl->d_ff_ph, &pl->d_dev_err,

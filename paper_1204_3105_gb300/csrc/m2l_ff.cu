@@ -94,6 +94,24 @@ __device__ __forceinline__ float4 ff_of(double re, double im) {
   return make_float4(hr, hi, __double2float_rn(re - (double)hr), __double2float_rn(im - (double)hi));
 }
 
+// Every cell's multipole (Q, a^_1 .. a^_p) as float-float, once, so that the
+// M2L gathers (each source row is read once per stencil entry that names it)
+// need no FP64 arithmetic.
+__global__ void k_ma_to_ff(int64_t n_cells, int p, int P, const double *__restrict__ mQ,
+                           const double2 *__restrict__ ma, float4 *__restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int P1 = p + 1;
+  if (i >= n_cells * P1) return;
+  const int64_t cell = i / P1;
+  const int k = (int)(i - cell * P1);
+  if (k == 0) {
+    out[i] = ff_of(mQ[cell], 0.0);
+  } else {
+    const double2 m = ma[cell * P + k - 1];
+    out[i] = ff_of(m.x, m.y);
+  }
+}
+
 // The scaled operator of an entry with zeta = |zeta| u is T_lk = A_lk u^-(l+k)
 // with A real (the binomial, sign and |zeta| powers), so
 //   b^_l = u^-l sum_k A_lk (u^-k a^_k):
@@ -155,12 +173,8 @@ k_m2l_ff(FfArgs a) {
         const int src = s_src[tt];
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (src >= 0) {
-          if (k == 0) {
-            v = ff_of(a.mQ[src], 0.0);   // u^0 = 1
-          } else {
-            const double2 m = a.ma[(int64_t)src * a.P + k - 1];
-            v = ff_cmul(sPh[k], ff_of(m.x, m.y));
-          }
+          v = a.ma_ff[(int64_t)src * P1 + k];
+          if (k > 0) v = ff_cmul(sPh[k], v);   // u^0 = 1
         }
         sC[tt * AS + k] = v;
       }
@@ -258,6 +272,8 @@ cudaError_t launch_m2l_ff(const FfArgs &a, int64_t n_far_cells, cudaStream_t s) 
   cudaError_t e = cudaFuncSetAttribute(k_m2l_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // tiles <= cells / 32 + classes; a persistent grid of three CTAs per SM
+  const int64_t nel = a.n_cells * (a.p + 1);
+  k_ma_to_ff<<<(unsigned)((nel + 255) / 256), 256, 0, s>>>(a.n_cells, a.p, a.P, a.mQ, a.ma, a.ma_ff);
   const int64_t tiles = n_far_cells / FF_TM + MAX_CLASSES;
   const int grid = (int)std::min<int64_t>(tiles, 3 * (int64_t)std::max(1, a.sms));
   k_m2l_ff<<<grid, FF_THREADS, smem, s>>>(a);

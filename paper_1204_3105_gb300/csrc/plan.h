@@ -92,7 +92,7 @@ struct Plan {
   DBuf d_sten, d_geo_scale;
   DBuf d_m2l_ops, d_m2l_logz, d_m2m_ops, d_l2l_ops;   // element type per precision
   DBuf d_counts;
-  DBuf d_far_full, d_cls_cnt, d_cls_cells, d_tc_ops, d_ff_ops, d_ff_ph, d_dev_err;
+  DBuf d_far_full, d_cls_cnt, d_cls_cells, d_tc_ops, d_ff_ops, d_ff_ph, d_ma_ff, d_dev_err;
   DBuf d_ad_hkey, d_ad_hval;          // adaptive tree: (level, key) -> cell table
   int tc_K = 0, tc_N = 0, n_sms = 148;
   int64_t cls_cap = 1;
@@ -323,6 +323,8 @@ struct FfArgs {
   const double2 *ma;
   double *lL0;
   double2 *lb;
+  float4 *ma_ff;                      // scratch: every cell's Q, a^_1..a^_p as float-float
+  int64_t n_cells;
 };
 size_t m2l_ff_smem_bytes(int p);
 // From the offsets zeta and the FP64 operators ([op][l][k]): the real

@@ -6,7 +6,10 @@
 // requests already running (a request that does not fit lets smaller,
 // later requests go first).  Each slot is a host thread with its own CUDA
 // stream and its own plans (one per tiling and precision, reused across
-// requests), so the work of several requests overlaps on the device.
+// requests), so the work of several requests overlaps on the device.  When a
+// slot takes a small adaptive request, the queued requests that can share its
+// solve (same tiling, eps, p, flags and domain) come along and the batch runs
+// as one forest: one build and one evaluation for all of them.
 // Completion is reported through fmm2d_serve_poll / fmm2d_serve_wait.
 // The paper has no serving layer; the evaluation each request runs is the
 // FMM of fmm2d_build + fmm2d_evaluate.

@@ -146,13 +146,15 @@ def test_edge_cases():
 
 
 @pytest.mark.parametrize("tiling", ["quad", "sept"])
-def test_clustered_4m_eps_1e10_sampled(tiling):
+@pytest.mark.parametrize("prec", ["fp64", "split", "hybrid"])
+def test_clustered_4m_eps_1e10_sampled(tiling, prec):
     """The clustered workload at full size: N = M = 4,194,304 points from a
-    32-component Gaussian mixture, strengths N(0, 1), FP64 form, eps = 1e-10,
-    leaf size 64; 96 sampled targets against the direct sum over all sources."""
+    32-component Gaussian mixture, strengths N(0, 1), eps = 1e-10, leaf size
+    64, in the FP64, split and hybrid forms; 96 sampled targets against the
+    direct sum over all sources."""
     n = 4194304
     xy, u = gaussian_mixture(n, seed=3, k=32)
-    phi, plan = run_gpu(tiling, xy, u, eps=1e-10, prec="fp64", leaf_size=64, keep=True)
+    phi, plan = run_gpu(tiling, xy, u, eps=1e-10, prec=prec, leaf_size=64, keep=True)
     info = plan.query()
     plan.close()
     idx = sample_targets(n, 96, seed=5)
