@@ -625,6 +625,14 @@ def run_forest_batch(args):
     for name, a, b in times:
         per[name].append(a.elapsed_time(b))
     ms = sum(statistics.mean(v) for v in per.values())
+    for name in names:   # one more step with the stages serialised: each stage's own time
+        forests[name]["plan"].set_profiling(2)
+    step([])
+    torch.cuda.synchronize()
+    stages = {}
+    for name in names:
+        stages[name] = {k: v[0] for k, v in forests[name]["plan"].stage_times().items()}
+        forests[name]["plan"].set_profiling(0)
     e2e = []
     for it in range(args.warmup + args.steps):
         torch.cuda.synchronize()
@@ -649,6 +657,7 @@ def run_forest_batch(args):
                                "(fmm2d_build_forest + fmm2d_evaluate), leaf size %d" % args.leaf_size,
                    "instances": count, "points": total, "l2": "flushed between forests (256 MB write)"},
         "per_tiling": {n: {"instances": forests[n]["n"], "points": int(forests[n]["off"][-1]),
+                           "stages_ms_isolated": stages[n],
                            "ms": statistics.mean(per[n]), "p": forests[n]["p"],
                            "levels": forests[n]["plan"].query()["levels"],
                            "tune_probe_err": forests[n]["tune_err"]} for n in names},

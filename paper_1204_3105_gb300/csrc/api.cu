@@ -943,6 +943,14 @@ static fmm2d_status build_adaptive(fmm2d_plan *pl, const void *src, int64_t n_sr
       }
     }
   }
+  // the FP32 P2P's leaf size classes (group size per leaf)
+  pl->p2p_binned = !f64 || is_hybrid(pl);
+  if (pl->p2p_binned) {
+    CK(dbuf_reserve(pl->d_p2p_order, std::max(1, n_leaves) * 4), "alloc");
+    CK(dbuf_reserve(pl->d_p2p_cnt, 8 * 4), "alloc");
+    CK(launch_p2p_bins(n_leaves, (const int *)pl->d_leaf_ids.p, c.ts, c.te, (int *)pl->d_p2p_cnt.p,
+                       (int *)pl->d_p2p_order.p, s), "p2p bins");
+  }
   // ---- lists
   const int64_t far_first = depth >= pl->l_min ? lf[pl->l_min] : n_cells;
   pl->n_far_cells = n_cells - far_first;
@@ -1068,7 +1076,11 @@ static fmm2d_status build_adaptive(fmm2d_plan *pl, const void *src, int64_t n_sr
   CK(dbuf_reserve(pl->d_ma, need_exp * csz), "alloc");
   if (ff_m2l(pl)) CK(dbuf_reserve(pl->d_ma_ff, n_cells * (pl->p + 1) * sizeof(float4)), "alloc");
   CK(dbuf_reserve(pl->d_lb, need_exp * csz), "alloc");
+  int bin_h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (pl->p2p_binned)
+    CK(cudaMemcpyAsync(bin_h, pl->d_p2p_cnt.p, sizeof(bin_h), cudaMemcpyDeviceToHost, s), "readback");
   CK(cudaStreamSynchronize(s), "build sync");
+  for (int k = 0; k < 4; ++k) pl->p2p_bin_count[k] = bin_h[k];
   CK(cudaGetLastError(), "build");
   pl->n_m2l = -1;
   pl->n_p2p_pairs = -1;
@@ -1207,15 +1219,19 @@ fmm2d_status evaluate_adaptive_t(fmm2d_plan *pl, const void *u, double *out, cud
                            c.ts, c.te, nullptr, (const int *)pl->d_u_off.p,
                            (const int *)pl->d_u_src.p, c.ctr, (double *)pl->d_phi_near.p,
                            (double)std::max(1, pl->leaf_cap), s, (const float2 *)pl->d_srclo.p,
-                           (const float2 *)(pl->same_sets ? pl->d_srclo.p : pl->d_tgtlo.p)),
+                           (const float2 *)(pl->same_sets ? pl->d_srclo.p : pl->d_tgtlo.p),
+                           (const int *)pl->d_p2p_order.p, pl->p2p_bin_count),
          "p2p");
     } else
     CK(launch_p2p<R>(0, pl->n_leaves_ad, (const int *)pl->d_leaf_ids.p, src4, tgt, tstride, c.ss,
                      c.se, c.ts, c.te, nullptr, (const int *)pl->d_u_off.p,
                      (const int *)pl->d_u_src.p, c.ctr, (double *)pl->d_phi_near.p,
-                     // the group size follows the leaf size, not the data, so that a
-                     // leaf's sum does not depend on the other leaves (or instances)
-                     (double)std::max(1, pl->leaf_cap), s),
+                     (double)std::max(1, pl->leaf_cap), s, nullptr, nullptr,
+                     // FP32: the group size of each leaf follows its own target
+                     // count, so that a leaf's sum does not depend on the other
+                     // leaves (or instances)
+                     pl->p2p_binned ? (const int *)pl->d_p2p_order.p : nullptr,
+                     pl->p2p_binned ? pl->p2p_bin_count : nullptr),
        "p2p");
   }
   if (f != s) {   // join: M2P and L2P need the expansions
@@ -1836,7 +1852,7 @@ void fmm2d_plan_destroy(fmm2d_plan *pl) {
                   &pl->d_phi_far, &pl->d_sten, &pl->d_geo_scale, &pl->d_m2l_ops, &pl->d_m2l_logz,
                   &pl->d_m2m_ops, &pl->d_l2l_ops, &pl->d_counts, &pl->d_far_full,
                   &pl->d_cls_cnt, &pl->d_cls_cells, &pl->d_tc_ops, &pl->d_ff_ops, &pl->d_ff_ph, &pl->d_dev_err,
-                  &pl->d_ad_hkey, &pl->d_ad_hval,
+                  &pl->d_ad_hkey, &pl->d_ad_hval, &pl->d_p2p_order, &pl->d_p2p_cnt,
                   &pl->d_cell_lev, &pl->d_parent, &pl->d_child_first, &pl->d_child_cnt,
                   &pl->d_split, &pl->d_leaf_ids, &pl->d_leaf_pos, &pl->d_ad_scale,
                   &pl->d_ad_inv_scale, &pl->d_u_off, &pl->d_u_src, &pl->d_w_off, &pl->d_w_src,

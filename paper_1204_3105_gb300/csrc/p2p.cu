@@ -558,7 +558,8 @@ k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_ids,
          const int *__restrict__ sst, const int *__restrict__ sen, const int *__restrict__ tst,
          const int *__restrict__ ten, const int *__restrict__ near_cnt,
          const int *__restrict__ near_off, const int *__restrict__ near_src,
-         const double2 *__restrict__ ctr, double *__restrict__ phi_near) {
+         const double2 *__restrict__ ctr, double *__restrict__ phi_near,
+         const int *__restrict__ order) {
   constexpr int CAPB = COMP ? X2_CAP_COMP : X2_CAP;
   constexpr int G = P2P_TH / T, CAP = CAPB / G;
   __shared__ float4 s_xy[CAPB];
@@ -575,8 +576,9 @@ k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_ids,
     x2_log2_table(s_lg);
     __syncthreads();
   }
-  const int64_t li = (int64_t)blockIdx.x * G + grp;
+  int64_t li = (int64_t)blockIdx.x * G + grp;
   if (li >= n_leaves) return;                 // group-uniform exits only
+  if (order) li = order[li];                  // leaves of one size class
   const int64_t g = leaf_ids ? (int64_t)leaf_ids[li] : leaf_first + li;
   const int ts = tst[g], te = ten[g];
   if (ts >= te) return;
@@ -734,22 +736,15 @@ cudaError_t launch_p2p(int64_t leaf_first, int64_t n_leaves, const int *leaf_ids
                        const int *tgt_start, const int *tgt_end, const int *near_cnt,
                        const int *near_off, const int *near_src, const double2 *ctr,
                        double *phi_near, double mean_targets, cudaStream_t s, const float2 *src_lo,
-                       const float2 *tgt_lo) {
+                       const float2 *tgt_lo, const int *bin_order, const int64_t *bin_count) {
   if (n_leaves <= 0) return cudaSuccess;
   const bool comp = src_lo != nullptr;
   if constexpr (sizeof(R) == 4) {
-    // group size: the smallest T for which a leaf of mean + 2 sigma (Poisson)
-    // targets still gets about three source slices per target quadruple (so
-    // that a group's lanes stay busy whatever the leaf's exact size)
-    const double want = 0.75 * (mean_targets + 2.0 * sqrt(mean_targets));
-    const int T = want <= 32 ? 32 : want <= 64 ? 64 : want <= 128 ? 128 : 256;
-    const int G = P2P_TH / T;
-    const unsigned blocks = (unsigned)((n_leaves + G - 1) / G);
 #define X2_LAUNCH_3(TT, CS, CP)                                                                   \
-  k_p2p_x2<TT, CS, CP><<<blocks, P2P_TH, 0, s>>>(leaf_first, n_leaves, leaf_ids, src4, tgt,         \
-                                                 tstride, src_lo, tgt_lo, src_start, src_end,      \
-                                                 tgt_start, tgt_end, near_cnt, near_off, near_src, \
-                                                 ctr, phi_near)
+  k_p2p_x2<TT, CS, CP><<<blocks, P2P_TH, 0, s>>>(leaf_first, nl, leaf_ids, src4, tgt, tstride,      \
+                                                 src_lo, tgt_lo, src_start, src_end, tgt_start,    \
+                                                 tgt_end, near_cnt, near_off, near_src, ctr,       \
+                                                 phi_near, order)
 #define X2_LAUNCH(TT)                                                                             \
   do {                                                                                            \
     if (near_off && comp) X2_LAUNCH_3(TT, true, true);                                            \
@@ -757,12 +752,31 @@ cudaError_t launch_p2p(int64_t leaf_first, int64_t n_leaves, const int *leaf_ids
     else if (comp) X2_LAUNCH_3(TT, false, true);                                                  \
     else X2_LAUNCH_3(TT, false, false);                                                           \
   } while (0)
-    if (T == 32) X2_LAUNCH(32);
-    else if (T == 64) X2_LAUNCH(64);
-    else if (T == 128) X2_LAUNCH(128);
-    else X2_LAUNCH(256);
+    auto launch_T = [&](int T, int64_t nl, const int *order) {
+      const int G = P2P_TH / T;
+      const unsigned blocks = (unsigned)((nl + G - 1) / G);
+      if (T == 32) X2_LAUNCH(32);
+      else if (T == 64) X2_LAUNCH(64);
+      else if (T == 128) X2_LAUNCH(128);
+      else X2_LAUNCH(256);
+    };
 #undef X2_LAUNCH
 #undef X2_LAUNCH_3
+    if (bin_order && bin_count) {
+      // leaves binned by their own target count (p2p_size_class): one launch
+      // per class with that class's group size
+      int64_t off = 0;
+      for (int c = 0; c < 4; ++c) {
+        if (bin_count[c] > 0) launch_T(32 << c, bin_count[c], bin_order + off);
+        off += bin_count[c];
+      }
+    } else {
+      // group size: the smallest T for which a leaf of mean + 2 sigma (Poisson)
+      // targets still gets about three source slices per target quadruple (so
+      // that a group's lanes stay busy whatever the leaf's exact size)
+      const double want = 0.75 * (mean_targets + 2.0 * sqrt(mean_targets));
+      launch_T(want <= 32 ? 32 : want <= 64 ? 64 : want <= 128 ? 128 : 256, n_leaves, nullptr);
+    }
   } else if (mean_targets >= 48.0 && !near_off) {   // FP64, large leaves: block-staged
     k_p2p_block<R><<<(unsigned)n_leaves, P2P_TH, 0, s>>>(leaf_first, src4, tgt, tstride, src_start,
                                                          src_end, tgt_start, tgt_end, near_cnt,
@@ -776,15 +790,57 @@ cudaError_t launch_p2p(int64_t leaf_first, int64_t n_leaves, const int *leaf_ids
   return cudaGetLastError();
 }
 
+namespace {
+// Size class of a leaf with nt targets: the group size T = 32 << class is the
+// smallest of 32 ... 256 with T >= 3 nt / 4, so a target quadruple gets about
+// three source slices.  It depends on the leaf alone.
+__device__ __forceinline__ int p2p_size_class(int nt) {
+  return 3 * nt <= 128 ? 0 : (3 * nt <= 256 ? 1 : (3 * nt <= 512 ? 2 : 3));
+}
+
+__global__ void k_p2p_bin_count(int64_t n_leaves, const int *__restrict__ leaf_ids,
+                                const int *__restrict__ ts, const int *__restrict__ te,
+                                int *__restrict__ cnt) {
+  const int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (li >= n_leaves) return;
+  const int g = leaf_ids[li];
+  atomicAdd(&cnt[p2p_size_class(te[g] - ts[g])], 1);
+}
+
+// order[off_c + j] = leaf position li (the order inside a class does not
+// matter: every leaf's sum is computed on its own)
+__global__ void k_p2p_bin_scatter(int64_t n_leaves, const int *__restrict__ leaf_ids,
+                                  const int *__restrict__ ts, const int *__restrict__ te,
+                                  int *__restrict__ cnt, int *__restrict__ order) {
+  const int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (li >= n_leaves) return;
+  const int g = leaf_ids[li];
+  const int c = p2p_size_class(te[g] - ts[g]);
+  int off = 0;
+  for (int k = 0; k < c; ++k) off += cnt[k];
+  order[off + atomicAdd(&cnt[4 + c], 1)] = (int)li;
+}
+}  // namespace
+
+cudaError_t launch_p2p_bins(int64_t n_leaves, const int *leaf_ids, const int *ts, const int *te,
+                            int *cnt8, int *order, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(cnt8, 0, 8 * sizeof(int), s);
+  if (e != cudaSuccess || n_leaves <= 0) return e;
+  const unsigned blocks = (unsigned)((n_leaves + 255) / 256);
+  k_p2p_bin_count<<<blocks, 256, 0, s>>>(n_leaves, leaf_ids, ts, te, cnt8);
+  k_p2p_bin_scatter<<<blocks, 256, 0, s>>>(n_leaves, leaf_ids, ts, te, cnt8, order);
+  return cudaGetLastError();
+}
+
 template cudaError_t launch_p2p<float>(int64_t, int64_t, const int *, const float *,
                                        const float *, int, const int *, const int *, const int *,
                                        const int *, const int *, const int *, const int *,
                                        const double2 *, double *, double, cudaStream_t,
-                                       const float2 *, const float2 *);
+                                       const float2 *, const float2 *, const int *, const int64_t *);
 template cudaError_t launch_p2p<double>(int64_t, int64_t, const int *, const double *,
                                         const double *, int, const int *, const int *, const int *,
                                         const int *, const int *, const int *, const int *,
                                         const double2 *, double *, double, cudaStream_t,
-                                        const float2 *, const float2 *);
+                                        const float2 *, const float2 *, const int *, const int64_t *);
 
 }  // namespace fmm2d

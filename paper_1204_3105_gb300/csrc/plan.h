@@ -94,12 +94,16 @@ struct Plan {
   DBuf d_counts;
   DBuf d_far_full, d_cls_cnt, d_cls_cells, d_tc_ops, d_ff_ops, d_ff_ph, d_ma_ff, d_dev_err;
   DBuf d_ad_hkey, d_ad_hval;          // adaptive tree: (level, key) -> cell table
+  DBuf d_p2p_order, d_p2p_cnt;        // adaptive tree: P2P leaf size classes
   int tc_K = 0, tc_N = 0, n_sms = 148;
   int64_t cls_cap = 1;
   // adaptive tree (FMM2D_ADAPTIVE): cells split while they hold more than
   // leaf_cap sources or targets; U / W / X lists in CSR form by target
   int leaf_cap = 64;
   int64_t n_leaves_ad = 0, n_u = 0, n_w = 0, n_x = 0;
+  // adaptive FP32 P2P: leaves by size class (launch_p2p_bins), class counts
+  bool p2p_binned = false;
+  int64_t p2p_bin_count[4] = {0, 0, 0, 0};
   DBuf d_cell_lev, d_parent, d_child_first, d_child_cnt, d_split;
   DBuf d_leaf_ids, d_leaf_pos, d_ad_scale, d_ad_inv_scale;
   DBuf d_u_off, d_u_src, d_w_off, d_w_src, d_x_off, d_x_src;
@@ -347,6 +351,11 @@ cudaError_t launch_p2p(int64_t leaf_first, int64_t n_leaves, const int *leaf_ids
                        const int *tgt_start, const int *tgt_end, const int *near_cnt,
                        const int *near_off, const int *near_src, const double2 *ctr,
                        double *phi_near, double mean_targets, cudaStream_t s,
-                       const float2 *src_lo = nullptr, const float2 *tgt_lo = nullptr);
+                       const float2 *src_lo = nullptr, const float2 *tgt_lo = nullptr,
+                       const int *bin_order = nullptr, const int64_t *bin_count = nullptr);
+// Adaptive trees: the leaves (positions li of leaf_ids) by size class, for
+// launch_p2p's per-class group sizes; cnt8[0..3] the class counts.
+cudaError_t launch_p2p_bins(int64_t n_leaves, const int *leaf_ids, const int *ts, const int *te,
+                            int *cnt8, int *order, cudaStream_t s);
 
 }  // namespace fmm2d
