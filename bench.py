@@ -613,18 +613,46 @@ def run_forest_batch(args):
             times.append((name, e0, e1))
             flush.zero_()
 
+    # the three forests are independent: one stream each, joined per step
+    fstreams = {nm: torch.cuda.Stream(device=dev) for nm in names}
+
+    def step_concurrent(whole):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for name in names:
+            f, fs = forests[name], fstreams[name]
+            fs.wait_event(e0)
+            f["plan"].build_forest(f["xy_d"], f["off"], fs)
+            f["plan"].evaluate(f["u_d"], f["out"], fs)
+            d = torch.cuda.Event()
+            d.record(fs)
+            stream.wait_event(d)
+        e1.record(stream)
+        whole.append((e0, e1))
+        flush.zero_()
+
     for _ in range(args.warmup):
         step([])
+        step_concurrent([])
     torch.cuda.synchronize()
-    times = []
+    times, whole = [], []
     with Clocks(0) as clk:
         for _ in range(args.steps):
+            if args.serial:
+                step(times)
+            else:
+                step_concurrent(whole)
+        torch.cuda.synchronize()
+    if not args.serial:   # per-forest times: the same steps, one forest after another
+        for _ in range(min(args.steps, 10)):
             step(times)
         torch.cuda.synchronize()
     per = {n: [] for n in names}
     for name, a, b in times:
         per[name].append(a.elapsed_time(b))
-    ms = sum(statistics.mean(v) for v in per.values())
+    ms_serial = sum(statistics.mean(v) for v in per.values())
+    ms = ms_serial if args.serial else statistics.mean(a.elapsed_time(b) for a, b in whole)
     for name in names:   # one more step with the stages serialised: each stage's own time
         forests[name]["plan"].set_profiling(2)
     step([])
@@ -639,23 +667,30 @@ def run_forest_batch(args):
         t0 = time.perf_counter()
         for name in names:
             f = forests[name]
-            xd = f["xy_h"].to(dev, non_blocking=True)
-            ud = f["u_h"].to(dev, non_blocking=True)
-            f["plan"].build_forest(xd, f["off"], stream)
-            f["plan"].evaluate(ud, f["out"], stream)
-            f["res_h"].copy_(f["out"], non_blocking=True)
+            fs = stream if args.serial else fstreams[name]
+            with torch.cuda.stream(fs):   # copies, build and evaluation on the forest's stream
+                xd = f["xy_h"].to(dev, non_blocking=True)
+                ud = f["u_h"].to(dev, non_blocking=True)
+                f["plan"].build_forest(xd, f["off"], fs)
+                f["plan"].evaluate(ud, f["out"], fs)
+                f["res_h"].copy_(f["out"], non_blocking=True)
         torch.cuda.synchronize()
         if it >= args.warmup:
             e2e.append(time.perf_counter() - t0)
     line = {
         "metric": "batched FMM points/s (4096 instances, eps=1e-6)", "value": total / (ms / 1e3),
         "unit": "points/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": ms, "ms_per_step_serial": ms_serial, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
         "dtype": "tf32x3+f32+f64", "data": "synthetic",
         "config": {"workload": "4096 instances, N log-uniform [256, 65536], uniform unit square, tiling "
                                "uniform over 3, eps=1e-6, FP32; one forest per tiling "
                                "(fmm2d_build_forest + fmm2d_evaluate), leaf size %d" % args.leaf_size,
-                   "instances": count, "points": total, "l2": "flushed between forests (256 MB write)"},
+                   "instances": count, "points": total,
+                   "l2": "flushed between forests (256 MB write)" if args.serial else
+                         "flushed between steps (256 MB write)",
+                   "streams": "one forest after another" if args.serial else
+                              "the three forests on three streams, joined at the end of the step"},
         "per_tiling": {n: {"instances": forests[n]["n"], "points": int(forests[n]["off"][-1]),
                            "stages_ms_isolated": stages[n],
                            "ms": statistics.mean(per[n]), "p": forests[n]["p"],

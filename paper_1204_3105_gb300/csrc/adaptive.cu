@@ -74,48 +74,6 @@ __device__ __forceinline__ int find_cell(const uint32_t *__restrict__ ckey, int6
   return (lo < first + count && ckey[lo] == key) ? (int)lo : -1;
 }
 
-__device__ __forceinline__ unsigned long long cell_hkey(int l, uint32_t key) {
-  return ((unsigned long long)l << 32) | key;
-}
-__device__ __forceinline__ uint64_t cell_hslot(unsigned long long k, int bits) {
-  return (k * 0x9E3779B97F4A7C15ull) >> (64 - bits);   // Fibonacci hashing
-}
-
-// cell of level l with key `key`: the hash table when there is one (linear
-// probing; every probe sequence ends at the key or at an empty slot, the
-// table being at most half full), else the binary search of the level
-__device__ __forceinline__ int find_cell_at(const AdCells &c, int l, int64_t first, int64_t count,
-                                            uint32_t key) {
-  if (!c.hkey) return find_cell(c.key, first, count, key);
-  const unsigned long long k = cell_hkey(l, key);
-  const uint64_t mask = ((uint64_t)1 << c.hbits) - 1;
-  uint64_t h = cell_hslot(k, c.hbits);
-  for (uint64_t probe = 0; probe <= mask; ++probe) {
-    const unsigned long long v = c.hkey[h];
-    if (v == k) return c.hval[h];
-    if (v == ~0ull) return -1;
-    h = (h + 1) & mask;
-  }
-  return -1;
-}
-
-__global__ void k_ad_hash(int64_t n_cells, AdCells c, unsigned long long *__restrict__ hkey,
-                          int *__restrict__ hval, int bits) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n_cells) return;
-  const unsigned long long k = cell_hkey(c.lev[i], c.key[i]);
-  const uint64_t mask = ((uint64_t)1 << bits) - 1;
-  uint64_t h = cell_hslot(k, bits);
-  for (uint64_t probe = 0; probe <= mask; ++probe) {
-    const unsigned long long prev = atomicCAS(&hkey[h], ~0ull, k);
-    if (prev == ~0ull || prev == k) {
-      hval[h] = (int)i;
-      return;
-    }
-    h = (h + 1) & mask;
-  }
-}
-
 // One level-0 cell per instance: instance i owns sources [soff[i], soff[i+1])
 // and targets [toff[i], toff[i+1]) (one instance: the whole sets).
 __global__ void k_ad_roots(Geo g, int n_inst, const int64_t *__restrict__ soff,
@@ -361,7 +319,7 @@ __global__ void k_ad_lists_1t(Geo g, const Stencils *__restrict__ stp, int l, in
                                  ca.z + st.near_d[o][e][2], 0);
         uint32_t k;
         if (!cell_at(g, l, q, &k)) continue;
-        const int m = find_cell_at(c, l, first, count, ibase + k);
+        const int m = find_cell(c.key, first, count, ibase + k);
         if (m < 0 || !c.hsrc[m]) continue;
         const bool m_leaf = !c.split[m];
         if (a_leaf && m_leaf) {
@@ -391,7 +349,7 @@ __global__ void k_ad_lists_1t(Geo g, const Stencils *__restrict__ stp, int l, in
                                    ca.z + st.far_d[cls][e][2], 0);
           uint32_t k;
           if (cell_at(g, l, q, &k)) {
-            sidx = find_cell_at(c, l, first, count, ibase + k);
+            sidx = find_cell(c.key, first, count, ibase + k);
             if (sidx >= 0 && !c.hsrc[sidx]) sidx = -1;
           }
         }
@@ -520,7 +478,7 @@ __global__ void k_ad_cell_lists(Geo g, const Stencils *__restrict__ stp, int l, 
                                ca.z + st.near_d[o][lane][2], 0);
       uint32_t k;
       if (cell_at(g, l, q, &k)) {
-        m = find_cell_at(c, l, first, count, ibase + k);
+        m = find_cell(c.key, first, count, ibase + k);
         if (m >= 0 && !c.hsrc[m]) m = -1;
       }
       if (m >= 0) {
@@ -603,7 +561,7 @@ __global__ void k_ad_cell_lists(Geo g, const Stencils *__restrict__ stp, int l, 
                                  ca.z + st.far_d[cls][e][2], 0);
         uint32_t k;
         if (cell_at(g, l, q, &k)) {
-          sidx = find_cell_at(c, l, first, count, ibase + k);
+          sidx = find_cell(c.key, first, count, ibase + k);
           if (sidx >= 0 && !c.hsrc[sidx]) sidx = -1;
         }
       }
@@ -860,13 +818,6 @@ cudaError_t ad_launch_rel(bool f32_in, bool f32_out, const void *xy, const uint3
 // cooperative forms (32 lanes per cell, 16 per test) would mostly idle lanes.
 constexpr int64_t COOP_MAX_CELLS = (int64_t)1 << 18;
 constexpr int64_t COOP_MAX_TESTS = (int64_t)1 << 19;
-
-cudaError_t ad_launch_hash(int64_t n_cells, const AdCells &c, unsigned long long *hkey, int *hval,
-                           int hbits, cudaStream_t s) {
-  if (n_cells <= 0) return cudaSuccess;
-  k_ad_hash<<<nblk(n_cells, 256), 256, 0, s>>>(n_cells, c, hkey, hval, hbits);
-  return cudaGetLastError();
-}
 
 cudaError_t ad_launch_lists(const Geo &g, const Stencils *d_sten, int l, int l_min, int64_t first,
                             int64_t count, int64_t n_t, int64_t n_s, const int *t_a, const int *t_c,

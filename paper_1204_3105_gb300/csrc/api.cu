@@ -965,18 +965,6 @@ static fmm2d_status build_adaptive(fmm2d_plan *pl, const void *src, int64_t n_sr
     CK(cudaMemsetAsync(pl->d_cls_cnt.p, 0, MAX_CLASSES * 4, s), "memset");
   }
   pl->cls_cap = nfc;
-  {   // (level, key) -> cell table for the traversal, at most half full
-    int hb = 1;
-    while (((int64_t)1 << hb) < 2 * n_cells) ++hb;
-    CK(dbuf_reserve(pl->d_ad_hkey, ((size_t)1 << hb) * 8), "alloc");
-    CK(dbuf_reserve(pl->d_ad_hval, ((size_t)1 << hb) * 4), "alloc");
-    CK(cudaMemsetAsync(pl->d_ad_hkey.p, 0xFF, ((size_t)1 << hb) * 8, s), "memset");
-    c.hkey = (const unsigned long long *)pl->d_ad_hkey.p;
-    c.hval = (const int *)pl->d_ad_hval.p;
-    c.hbits = hb;
-    CK(ad_launch_hash(n_cells, c, (unsigned long long *)pl->d_ad_hkey.p, (int *)pl->d_ad_hval.p, hb, s),
-       "hash");
-  }
   int64_t n_u = 0, n_w = 0, n_x = 0, n_t = 0, n_s = 0;
   {
     StageScope sc(pl, ST_LISTS, s, 4 * (depth + 1));
@@ -1852,7 +1840,7 @@ void fmm2d_plan_destroy(fmm2d_plan *pl) {
                   &pl->d_phi_far, &pl->d_sten, &pl->d_geo_scale, &pl->d_m2l_ops, &pl->d_m2l_logz,
                   &pl->d_m2m_ops, &pl->d_l2l_ops, &pl->d_counts, &pl->d_far_full,
                   &pl->d_cls_cnt, &pl->d_cls_cells, &pl->d_tc_ops, &pl->d_ff_ops, &pl->d_ff_ph, &pl->d_dev_err,
-                  &pl->d_ad_hkey, &pl->d_ad_hval, &pl->d_p2p_order, &pl->d_p2p_cnt,
+                  &pl->d_p2p_order, &pl->d_p2p_cnt,
                   &pl->d_cell_lev, &pl->d_parent, &pl->d_child_first, &pl->d_child_cnt,
                   &pl->d_split, &pl->d_leaf_ids, &pl->d_leaf_pos, &pl->d_ad_scale,
                   &pl->d_ad_inv_scale, &pl->d_u_off, &pl->d_u_src, &pl->d_w_off, &pl->d_w_src,

@@ -93,7 +93,6 @@ struct Plan {
   DBuf d_m2l_ops, d_m2l_logz, d_m2m_ops, d_l2l_ops;   // element type per precision
   DBuf d_counts;
   DBuf d_far_full, d_cls_cnt, d_cls_cells, d_tc_ops, d_ff_ops, d_ff_ph, d_ma_ff, d_dev_err;
-  DBuf d_ad_hkey, d_ad_hval;          // adaptive tree: (level, key) -> cell table
   DBuf d_p2p_order, d_p2p_cnt;        // adaptive tree: P2P leaf size classes
   int tc_K = 0, tc_N = 0, n_sms = 148;
   int64_t cls_cap = 1;
@@ -184,15 +183,7 @@ struct AdCells {
   int4 *crd;
   double2 *ctr;
   uint8_t *cls, *hsrc;
-  // (level, key) -> cell: open-addressing table of 2^hbits slots (null: the
-  // list traversal falls back to a binary search of the level's keys)
-  const unsigned long long *hkey = nullptr;
-  const int *hval = nullptr;
-  int hbits = 0;
 };
-// Fill the (level, key) -> cell table of cells [0, n_cells) (slots preset to ~0).
-cudaError_t ad_launch_hash(int64_t n_cells, const AdCells &c, unsigned long long *hkey, int *hval,
-                           int hbits, cudaStream_t s);
 // level-0 cells: one per instance (soff / toff: n_inst + 1 device offsets),
 // or one cell holding everything (null offsets, n_inst = 1)
 cudaError_t ad_launch_roots(const Geo &g, int n_inst, const int64_t *soff, const int64_t *toff,
