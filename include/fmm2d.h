@@ -345,7 +345,7 @@ fmm2d_status fmm2d_keys_sort_noalloc(int tiling, int levels, double leaf_scale,
  * serving layer; each request runs the evaluation of fmm2d_build +
  * fmm2d_evaluate.  Requests are admitted, oldest first, as execution slots
  * and the HBM budget allow, and run concurrently on the slots' streams;
- * small adaptive requests (targets = sources, at most 131072 points) that
+ * small adaptive requests (targets = sources, at most 524288 points) that
  * wait together with equal tiling, eps, p, flags and domain are solved as
  * one forest (fmm2d_build_forest), their results equal to the requests
  * solved alone within eps.  If such a merged solve fails, its requests are

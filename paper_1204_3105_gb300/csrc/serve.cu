@@ -84,8 +84,8 @@ size_t estimate_bytes(const fmm2d_request &r) {
 // wait together with equal tiling, eps, p, flags and domain are solved as one
 // forest (fmm2d_build_forest), so the launches and level read-backs of one
 // solve serve them all.
-constexpr int64_t MERGE_MAX_POINTS = (int64_t)1 << 17;     // requests up to this size merge
-constexpr int64_t MERGE_BATCH_POINTS = (int64_t)1 << 21;   // points per forest at most
+constexpr int64_t MERGE_MAX_POINTS = (int64_t)1 << 19;     // requests up to this size merge
+constexpr int64_t MERGE_BATCH_POINTS = (int64_t)1 << 22;   // points per forest at most
 constexpr int MERGE_MAX = 256;                              // requests per forest at most
 
 bool mergeable(const fmm2d_request &r) {
