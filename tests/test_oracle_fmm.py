@@ -82,6 +82,34 @@ def test_m2l_within_bound_and_l2l_exact():
     assert np.max(np.abs(F.l2p(b2, y2, c2) - F.l2p(b, y2, ct))) < 1e-12 * np.max(np.abs(exact))
 
 
+def test_m2l_operator_is_real_factor_times_phase():
+    """The M2L operator of an offset z0 = |z0| u (the oracle's, i.e. the
+    translation of Sec. 2): every entry except the log term of b_0 is a real
+    number times u^-(l+k) (column 0 is the Q column, k = 0).  The float-float
+    M2L applies it as a rotation of the multipole by u^-k, a real matrix and a
+    rotation of the result by u^-l; a sign or index slip in the operator would
+    leave a complex factor."""
+    rs = np.random.default_rng(11)
+    p = 24
+    for _ in range(6):
+        z0 = complex(rs.uniform(-5, 5), rs.uniform(-5, 5))
+        if abs(z0) < 2.5:
+            z0 *= 3.0 / abs(z0)
+        u = z0 / abs(z0)
+        M = np.zeros((p + 1, p + 1), complex)
+        b = F.m2l(1.0, np.zeros(p, complex), z0, p)
+        b[0] -= np.log(-z0)                       # the log term of b_0 is not translated
+        M[:, 0] = b
+        for k in range(1, p + 1):
+            e = np.zeros(p, complex)
+            e[k - 1] = 1.0
+            M[:, k] = F.m2l(0.0, e, z0, p)
+        lk = np.add.outer(np.arange(p + 1), np.arange(p + 1))
+        A = M * u ** lk
+        assert np.all(np.abs(A.imag) <= 1e-12 * np.abs(A) + 1e-300)   # entry by entry
+        assert abs(M[0, 0]) == 0.0
+
+
 @pytest.mark.parametrize("name,L", [("quad", 3), ("sept", 3), ("tri", 4)])
 def test_fmm_converges_to_direct(name, L):
     rng = np.random.default_rng(4)
