@@ -33,10 +33,10 @@ TILINGS = ("quad", "sept", "tri")
 SEED = 2
 MUFU_PER_CLK_SM = 16      # lg2 results per clock per SM (MUFU pipe)
 # DRAM bytes (read + write) of one P2P launch on the 2^20-point quadtree
-# workload, from the ncu capture summarised in profiles/p2p_x2_quad_2p20.md
-# (the three tilings' launches each read the 2^20 sorted sources once:
-# 18.3-19.3 MB); set to None when the kernel changes after that capture
-P2P_TRAFFIC = 18315520     # bytes: dram__bytes_read.sum + dram__bytes_write.sum of one launch
+# workload from an ncu capture of the current kernel, or None: the capture
+# summarised in profiles/p2p_x2_quad_2p20.md (18.3 MB, the sorted sources
+# read once) predates the kernel's leaf size-class indirection
+P2P_TRAFFIC = None         # bytes: dram__bytes_read.sum + dram__bytes_write.sum of one launch
 FP32_LANES_SM = 128       # FP32 FMA lanes per SM
 
 
