@@ -62,3 +62,45 @@ def test_bad_arguments_rejected_without_gpu(fm):
         fm.Plan("quad", p=0, eps=2.0)
     with pytest.raises(fm.FMM2DError):
         fm.fmm2d_default_params("quad", 100, 64, 0.0)
+
+
+def _header():
+    txt = open(os.path.join(ROOT, "include", "fmm2d.h")).read()
+    return re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+
+
+def _struct_fields(txt, name):
+    """Field names, in order, of `typedef struct { ... } name;`."""
+    m = re.search(r"typedef struct\s*\{([^{}]*)\}\s*" + name + r"\s*;", txt, flags=re.S)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        for part in decl.split(","):
+            part = re.sub(r"\[.*?\]", "", part).strip()   # arrays: keep the name
+            fields.append(re.findall(r"\*?\s*([A-Za-z_][A-Za-z0-9_]*)\s*$", part)[0])
+    return fields
+
+
+def test_binding_matches_header(fm):
+    """The ctypes binding's flag values and struct layouts are the header's:
+    every flag macro, and the field order of the request, result, info and
+    server-statistics structs."""
+    txt = _header()
+    macros = dict(re.findall(r"#define\s+(FMM2D_[A-Z0-9_]+)\s+(0x[0-9a-fA-F]+)u", txt))
+    for name in ("PREC_FP64", "PREC_MIXED", "PREC_MIXED_TC", "PREC_HYBRID", "PREC_SPLIT",
+                 "IN_F32", "ADAPTIVE"):
+        assert getattr(fm, name) == int(macros["FMM2D_" + name], 16), name
+    for cname, py in (("fmm2d_request", fm.Request), ("fmm2d_result", fm.Result),
+                      ("fmm2d_info", fm.Info), ("fmm2d_serve_info", fm.ServeInfo)):
+        assert _struct_fields(txt, cname) == [f for f, _ in py._fields_], cname
+
+
+def test_unknown_precision_form_rejected(fm):
+    """Precision values past FMM2D_PREC_SPLIT are refused at plan creation."""
+    for bad in (0x5, 0x6, 0x7, 0x8):
+        with pytest.raises(fm.FMM2DError) as e:
+            fm.Plan("quad", levels=4, p=8, flags=bad)
+        assert e.value.status == fm.EINVAL
