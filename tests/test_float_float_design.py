@@ -129,12 +129,13 @@ def test_float_float_r2():
     """r^2 of a target and a source given as hi + lo coordinates (relative to
     the target leaf's centre): a TwoSum difference of the hi parts, lo parts
     into the error, FMA squares, a TwoSum of the squares and one
-    renormalisation.  The difference (hi, lo) is not renormalised before
-    squaring, so the cross and lo terms carry FP32 roundings of relative size
-    ~ ulp(coordinate) / distance, and their cancellation squares that ratio
-    when the points are a few ulps apart: with q = |coordinate| / distance the
-    error is below 2^-44 + 2^-44 q + 2^-69 q^2 relative to r^2, i.e. ~2^-44 for
-    points a leaf apart, 2^-28 at q = 1e6 and FP32-level only near q = 1e7."""
+    renormalisation.  The lo parts of the two points are subtracted in FP32
+    (their difference can need a bit or two more than a float holds), and the
+    unrenormalised (hi, lo) difference is squared with FP32 cross and lo
+    terms, so the error grows as the points approach each other: with
+    q = |coordinate| / distance it is below 2^-44 + 2^-44 q + 2^-69 q^2
+    relative to r^2, i.e. ~2^-44 for points a leaf apart, 2^-28 at q = 1e6
+    and FP32-level only near q = 1e7."""
     rs = np.random.default_rng(5)
     for case in range(600):
         far = case < 400
