@@ -367,11 +367,22 @@ __device__ __forceinline__ void x2_r2_ff(const float2 &xt, const float2 &xs, con
                                          const float2 &ytl, const float2 &ysl, float2 &rh,
                                          float2 &rl) {
   constexpr float FL = 1e-30f;
-  float2 dxh, ex, dyh, ey;
-  x2_two_sum2(xt, xs, dxh, ex);
-  x2_two_sum2(yt, ys, dyh, ey);
-  const float2 dxl = __fadd2_rn(__fadd2_rn(xtl, xsl), ex);
-  const float2 dyl = __fadd2_rn(__fadd2_rn(ytl, ysl), ey);
+  // accurate float-float differences: TwoSum of the hi parts and of the lo
+  // parts, the first lo error into the hi error, a TwoSum renormalisation,
+  // then the second lo error (|lo| stays near ulp(hi) / 2 however close the
+  // two points are)
+  float2 dxh, dyh, dxl, dyl;
+  {
+    float2 sx, ex, lx, lex, sy, ey, ly, ley, rx, ry;
+    x2_two_sum2(xt, xs, sx, ex);
+    x2_two_sum2(xtl, xsl, lx, lex);
+    x2_two_sum2(yt, ys, sy, ey);
+    x2_two_sum2(ytl, ysl, ly, ley);
+    x2_two_sum2(sx, __fadd2_rn(ex, lx), dxh, rx);
+    x2_two_sum2(sy, __fadd2_rn(ey, ly), dyh, ry);
+    dxl = __fadd2_rn(rx, lex);
+    dyl = __fadd2_rn(ry, ley);
+  }
   const float2 qx = __fmul2_rn(dxh, dxh), qy = __fmul2_rn(dyh, dyh);
   const float2 qxe = __ffma2_rn(dxh, dxh, make_float2(-qx.x, -qx.y));
   const float2 qye = __ffma2_rn(dyh, dyh, make_float2(-qy.x, -qy.y));

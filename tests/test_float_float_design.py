@@ -127,36 +127,29 @@ def _r2_case(rs, lo_exp, hi_exp):
 
 def test_float_float_r2():
     """r^2 of a target and a source given as hi + lo coordinates (relative to
-    the target leaf's centre): a TwoSum difference of the hi parts, lo parts
-    into the error, FMA squares, a TwoSum of the squares and one
-    renormalisation.  The lo parts of the two points are subtracted in FP32
-    (their difference can need a bit or two more than a float holds), and the
-    unrenormalised (hi, lo) difference is squared with FP32 cross and lo
-    terms, so the error grows as the points approach each other: with
-    q = |coordinate| / distance it is below 2^-44 + 2^-44 q + 2^-69 q^2
-    relative to r^2, i.e. ~2^-44 for points a leaf apart, 2^-28 at q = 1e6
-    and FP32-level only near q = 1e7."""
+    the target leaf's centre), as the hybrid P2P forms it: the accurate
+    float-float difference (TwoSum of the hi parts and of the lo parts, the
+    first lo error into the hi error, a TwoSum renormalisation, then the
+    second lo error), FMA squares, a TwoSum of the squares and one
+    renormalisation: within 2^-43 of the exact r^2 of the coordinates at every
+    separation, down to points 2^-34 of the coordinate scale apart.  (Without
+    the lo-part TwoSum the error grew like |coordinate| / distance and reached
+    FP32 level for points ~1e-7 of a leaf apart.)"""
     rs = np.random.default_rng(5)
     for case in range(600):
-        far = case < 400
-        t, s = _r2_case(rs, -20, 0) if far else _r2_case(rs, -30, -24)
+        t, s = _r2_case(rs, -20, 0) if case < 300 else _r2_case(rs, -34, -20)
         th = [split(v) for v in t]
         sh = [split(-v) for v in s]        # sources are staged negated
         dh, dl = [], []
         for k in range(2):
-            a, b = th[k][0], sh[k][0]
-            sm = F32(a + b)
-            bp = F32(sm - a)
-            ap = F32(sm - bp)
-            err = F32(F32(a - ap) + F32(b - bp))
-            dh.append(sm)
-            dl.append(F32(F32(th[k][1] + sh[k][1]) + err))
+            s1, s2 = two_sum_acc(th[k][0], F32(0.0), sh[k][0])
+            t1, t2 = two_sum_acc(th[k][1], F32(0.0), sh[k][1])
+            h, r = two_sum_acc(s1, F32(0.0), F32(s2 + t1))
+            dh.append(h)
+            dl.append(F32(r + t2))
         qx, qy = F32(dh[0] * dh[0]), F32(dh[1] * dh[1])
         qxe, qye = fmaf(dh[0], dh[0], -qx), fmaf(dh[1], dh[1], -qy)
-        h = F32(qx + qy)
-        bp = F32(h - qx)
-        ap = F32(h - bp)
-        he = F32(F32(qx - ap) + F32(qy - bp))
+        h, he = two_sum_acc(qx, F32(0.0), qy)
         lo = F32(F32(qxe + qye) + he)
         lo = fmaf(F32(2.0 * dh[0]), dl[0], lo)
         lo = fmaf(F32(2.0 * dh[1]), dl[1], lo)
@@ -165,8 +158,7 @@ def test_float_float_r2():
         rl = F32(lo - F32(tt - h))
         ex = sum((exact(th[k][0]) + exact(th[k][1]) + exact(sh[k][0]) + exact(sh[k][1])) ** 2
                  for k in range(2))
+        if ex == 0:
+            continue
         got = exact(tt) + exact(rl)
-        dist = float(np.hypot(*(t - s)))
-        q = float(np.max(np.abs(t))) / dist
-        bound = 2.0 ** -44 + 2.0 ** -44 * q + 2.0 ** -69 * q * q
-        assert abs(float(got - ex)) <= bound * float(ex)
+        assert abs(float(got - ex)) <= 2.0 ** -43 * float(ex)
