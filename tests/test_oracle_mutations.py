@@ -131,3 +131,35 @@ def test_adaptive_near_set_missing_a_neighbour_is_caught(monkeypatch):
     orig = Quadtree.near
     monkeypatch.setattr(Quadtree, "near", lambda self, n, l: orig(self, n, l)[:-1])
     _fails(pins_ad.test_every_pair_covered_exactly_once, "quad", 6)
+
+
+def test_m2p_conjugate_is_caught(monkeypatch):
+    """M2P summing the multipole tail on the conjugate coefficients."""
+    import test_oracle_adaptive as pins_ad
+    from oracle import adaptive as A
+    orig = A.m2p
+    monkeypatch.setattr(A, "m2p", lambda Q, a, c, zt: orig(Q, np.conj(a), c, zt))
+    _fails(pins_ad.test_m2p_single_source_within_series_tail)
+
+
+def test_p2l_without_1_over_l_is_caught(monkeypatch):
+    import test_oracle_adaptive as pins_ad
+    from oracle import adaptive as A
+    orig = A.p2l
+
+    def bad(xs, us, c, p):
+        b = orig(xs, us, c, p)
+        b[1:] *= np.arange(1, p + 1)
+        return b
+    monkeypatch.setattr(A, "p2l", bad)
+    _fails(pins_ad.test_p2l_single_source_within_series_tail)
+
+
+def test_morton_axes_swapped_is_caught(monkeypatch):
+    """The x and y bits of the Morton interleave exchanged."""
+    orig = Quadtree.keys
+
+    def bad(self, x, y, l=None):
+        return orig(self, y, x, l)
+    monkeypatch.setattr(Quadtree, "keys", bad)
+    _fails(pins_quad.test_morton_containment_and_prefix)
