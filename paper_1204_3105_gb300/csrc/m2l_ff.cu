@@ -1,17 +1,23 @@
-// m2l_ff.cu - M2L of the hybrid precision form on the FP32 pipes, in
-// float-float (hi + lo) arithmetic.
+// m2l_ff.cu - M2L of the hybrid and split precision forms on the FP32 pipes,
+// in float-float (hi + lo) arithmetic.
 //
-// The hybrid form keeps multipoles and locals in FP64 for tolerances below
-// the reach of FP32 expansions.  On this GPU the FP64 pipe runs at about
-// 1/70 of the FP32 rate, so the M2L sum (Sec. 2: every local coefficient is a
-// sum over the NeighborsE4 list of operator x multipole products, eq. 3) is
-// done here in float-float: every operator entry and every multipole
-// coefficient is an unevaluated sum hi + lo of two floats (48 significant
-// bits), each product is formed exactly with an FMA (TwoProd), the two cross
-// terms hi*lo are added to a running compensation, and the sum is kept as
-// s + c with an error-free TwoSum per term (the compensated dot product of
-// Ogita, Rump and Oishi, 2005).  The result is as accurate as an FP64
-// evaluation of the same sum to within a few units of 2^-48.
+// These forms keep multipoles and locals in FP64 for tolerances below the
+// reach of FP32 expansions.  On this GPU the FP64 pipe runs at about 1/70 of
+// the FP32 rate, so the M2L sum (Sec. 2: every local coefficient is a sum
+// over the NeighborsE4 list of operator x multipole products, eq. 3) is done
+// here in float-float: every operator value and every multipole coefficient
+// is an unevaluated sum hi + lo of two floats (48 significant bits), each
+// product is formed exactly with an FMA (TwoProd), the cross terms hi*lo are
+// added to a running compensation, and the sum is kept as s + c with an
+// error-free TwoSum per term (the compensated dot product of Ogita, Rump and
+// Oishi, 2005).  The result is as accurate as an FP64 evaluation of the same
+// sum to within a few units of 2^-48.
+//
+// The scaled operator of an offset zeta = |zeta| u is T_lk = A_lk u^-(l+k)
+// with A real, so an entry turns the gathered multipoles by u^-k, applies
+// the real A (two real products per entry instead of four) and turns the
+// sum by u^-l (k_m2l_ff below).  The multipoles are converted to float-float
+// once per cell (k_ma_to_ff) before the gathers.
 //
 // Work is laid out as the dense contraction the operator sharing allows: on
 // scaled coefficients the operator depends only on (child class, stencil

@@ -359,9 +359,9 @@ __device__ __forceinline__ void x2_two_sum2(const float2 a, const float2 b, floa
 }
 
 // r^2 of two target-source pairs as rh + rl (float-float): the coordinate
-// differences are formed without error (TwoSum of the hi parts, lo parts
-// added to the error), squared with exact products (FMA), summed by TwoSum
-// and renormalised; rh is floored at FL > 0 (a normal number)
+// differences by the accurate float-float subtraction (below), squared with
+// exact products (FMA), summed by TwoSum and renormalised (about 43 bits of
+// r^2 however close the points); rh is floored at FL > 0 (a normal number)
 __device__ __forceinline__ void x2_r2_ff(const float2 &xt, const float2 &xs, const float2 &xtl,
                                          const float2 &xsl, const float2 &yt, const float2 &ys,
                                          const float2 &ytl, const float2 &ysl, float2 &rh,
