@@ -48,39 +48,105 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-class Clocks:
-    """Sample SM clocks and throttle reasons with nvidia-smi while running."""
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+def eps_label(eps):
+    """eps as the metric strings print it: 1e-06 -> '1e-6' (one formatter for
+    both arms, so that their metric names are identical)."""
+    m, e = ("%.0e" % eps).split("e")
+    return "%se%d" % (m, int(e))
 
-    def __init__(self, index=0):
-        self.index = index
-        self.rows = []
+
+def metric_name(eps):
+    return "FMM eval points/s at eps=%s (3 tilings)" % eps_label(eps)
+
+
+# Clock sampler: a separate process polls NVML (read-only queries) every
+# 2 ms and appends "monotonic_time sm_mhz max_mhz power_mw reasons" lines to a
+# file, so that even a timed region of a few tens of milliseconds holds
+# samples and the benchmark process itself is not disturbed.
+_SAMPLER = r"""
+import ctypes, sys, time
+bus, out, period = sys.argv[1], sys.argv[2], float(sys.argv[3])
+f = open(out, "w", buffering=1)
+try:
+    nv = ctypes.CDLL("libnvidia-ml.so.1")
+    if nv.nvmlInit_v2() != 0:
+        raise OSError("nvmlInit")
+    h = ctypes.c_void_p()
+    if bus.startswith("pci:"):
+        r = nv.nvmlDeviceGetHandleByPciBusId_v2(bus[4:].encode(), ctypes.byref(h))
+    else:
+        r = nv.nvmlDeviceGetHandleByIndex_v2(int(bus[4:]), ctypes.byref(h))
+    if r != 0:
+        raise OSError("handle %d" % r)
+    get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or         nv.nvmlDeviceGetCurrentClocksThrottleReasons
+    sm, mx, pw, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+    nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))
+    while True:
+        nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(sm))
+        nv.nvmlDeviceGetPowerUsage(h, ctypes.byref(pw))
+        get_reasons(h, ctypes.byref(rs))
+        f.write("%.6f %d %d %d %d
+" % (time.monotonic(), sm.value, mx.value, pw.value, rs.value))
+        time.sleep(period)
+except Exception as e:
+    f.write("error %s
+" % e)
+"""
+_REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+            0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+
+class Clocks:
+    """SM clocks and throttle reasons of the benchmarked GPU, sampled by NVML
+    in a separate process; mark() the start and end of the timed region and
+    summary() reports the samples taken inside it."""
+
+    def __init__(self, device_index=0, period_s=0.002):
+        self.index = device_index
+        self.period = period_s
         self.proc = None
-        self.skip = 0
+        self.path = None
+        self.t0 = self.t1 = None
+
+    def _bus(self):
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(self.index)
+            if hasattr(pr, "pci_bus_id"):
+                return "pci:%08x:%02x:%02x.0" % (getattr(pr, "pci_domain_id", 0), pr.pci_bus_id,
+                                                 pr.pci_device_id)
+        except Exception:
+            pass
+        return "idx:%d" % self.index
 
     def __enter__(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".txt")
+        os.close(fd)
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "50"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
-            t0 = time.time()   # nvidia-smi takes a moment to start: wait for its first row
-            while not self.rows and time.time() - t0 < 5.0 and self.proc.poll() is None:
+            self.proc = subprocess.Popen([sys.executable, "-c", _SAMPLER, self._bus(), self.path,
+                                          str(self.period)], stdout=subprocess.DEVNULL,
+                                         stderr=subprocess.DEVNULL)
+            t = time.time()   # wait for the first sample (NVML initialised)
+            while time.time() - t < 10.0 and self.proc.poll() is None:
+                if os.path.getsize(self.path) > 0:
+                    break
                 time.sleep(0.01)
-            self.skip = len(self.rows)
         except OSError:
             self.proc = None
+        self.t0 = time.monotonic()
         return self
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
+    def start(self):
+        self.t0 = time.monotonic()
+
+    def stop(self):
+        self.t1 = time.monotonic()
 
     def __exit__(self, *a):
+        if self.t1 is None:
+            self.t1 = time.monotonic()
+        time.sleep(2 * self.period)
         if self.proc:
             self.proc.terminate()
             try:
@@ -89,34 +155,102 @@ class Clocks:
                 self.proc.kill()
 
     def summary(self):
-        self.rows = self.rows[self.skip:]   # rows taken before the timed region started
-        if not self.rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4)
-                          if len(r) > 3 + i and r[3 + i].lower().startswith("active")})
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.rows)}
+        rows, err = [], None
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    if line.startswith("error"):
+                        err = line.strip()
+                        continue
+                    v = line.split()
+                    if len(v) == 5:
+                        rows.append((float(v[0]), int(v[1]), int(v[2]), int(v[3]), int(v[4])))
+            os.unlink(self.path)
+        except OSError:
+            pass
+        inside = [r for r in rows if self.t0 <= r[0] <= self.t1]
+        if not inside:   # a region shorter than the period: the next sample after its start
+            inside = [r for r in rows if r[0] >= self.t0][:1]
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"],
+                    "note": err or "no NVML sample"}
+        reasons = sorted({name for r in inside for bit, name in _REASONS.items() if r[4] & bit})
+        return {"sm_mhz": statistics.median(r[1] for r in inside),
+                "sm_max_mhz": max(r[2] for r in inside), "reasons": reasons,
+                "power_w_median": statistics.median(r[3] for r in inside) / 1e3,
+                "samples": len(inside), "window_ms": 1e3 * (self.t1 - self.t0),
+                "source": "NVML, every %g ms" % (1e3 * self.period)}
 
 
 def oracle_sample(tilings=TILINGS, n=16384, seed=SEED, eps=EPS):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
     N = M = n uniform points per tiling, the planner's L and p for eps."""
+    t0 = time.perf_counter()
+    for t in tilings:
+        _oracle_task((t, n, seed, eps))
+    dt = time.perf_counter() - t0
+    return len(tilings) * n / dt, dt
+
+
+def _oracle_task(args):
+    """One oracle FMM (one tiling, N = M = n uniform points); returns seconds."""
     from oracle.fmm import fmm, make_tiling
     from oracle.params import auto_levels, p_from_eps
     from paper_1204_3105_gb300.inputs import uniform_square
+    tiling, n, seed, eps = args
     xy, u = uniform_square(n, seed=seed, dtype=np.float32)
     xy = xy.astype(np.float64)
     u = u.astype(np.float64)
     t0 = time.perf_counter()
-    for t in tilings:
-        T = make_tiling(t, auto_levels(t, n))
-        fmm(T, xy, u, xy, p_from_eps(t, eps))
-    dt = time.perf_counter() - t0
-    return len(tilings) * n / dt, dt
+    fmm(make_tiling(tiling, auto_levels(tiling, n)), xy, u, xy, p_from_eps(tiling, eps))
+    return time.perf_counter() - t0
+
+
+def _oracle_warm(_):
+    import oracle.fmm  # noqa: F401  (imports paid before the timed maps)
+    return os.getpid()
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class OraclePool:
+    """The oracle on every host core: one single-threaded process per core
+    (spawned, so that it holds no CUDA state), each running whole oracle
+    FMMs; throughput = points of all tasks / wall time of the batch."""
+
+    def __init__(self, cores=None):
+        import multiprocessing as mp
+        self.cores = cores or host_cores()
+        keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                              "MKL_NUM_THREADS")}
+        for k in keep:
+            os.environ[k] = "1"   # one thread per process: the pool supplies the parallelism
+        try:
+            self.pool = mp.get_context("spawn").Pool(self.cores)
+        finally:
+            for k, v in keep.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.pool.map(_oracle_warm, range(self.cores), chunksize=1)
+
+    def run(self, n, eps=EPS, tasks=None, seed0=SEED + 100):
+        tasks = tasks or self.cores * len(TILINGS)
+        work = [(TILINGS[i % len(TILINGS)], n, seed0 + i, eps) for i in range(tasks)]
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_task, work, chunksize=1)
+        dt = time.perf_counter() - t0
+        return tasks * n / dt, dt, tasks
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
 
 
 def dist_setup(args):
@@ -147,26 +281,31 @@ def run_reference(args):
     dist, rank, ws = dist_setup(args)
     if rank != 0:
         return
-    # bounded sample: the whole run takes about --ref-seconds on the host
-    _, dt_cal = oracle_sample(n=2048)
+    pool = OraclePool()
+    # bounded sample: the whole run takes about --ref-seconds on the host; a
+    # step is 3 oracle FMMs (one per tiling) on each core, N = M = n each
+    _, dt_cal, _ = pool.run(2048, tasks=pool.cores)
     per_step = args.ref_seconds / max(1, args.steps + args.warmup)
-    n = int(min(args.ref_points, max(512, 2048 * per_step / max(dt_cal, 1e-3))))
+    n = int(min(args.ref_points, max(512, 2048 * (per_step / 3) / max(dt_cal, 1e-3))))
     for _ in range(args.warmup):
-        oracle_sample(n=n)
-    times = []
+        pool.run(n)
+    times, tasks = [], 0
     for _ in range(args.steps):
-        _, dt = oracle_sample(n=n)
+        _, dt, tasks = pool.run(n)
         times.append(dt)
+    pool.close()
     ms = 1e3 * statistics.mean(times)
-    value = len(TILINGS) * n / (ms / 1e3)
-    line = {"impl": "reference", "metric": "FMM eval points/s at eps=1e-6 (3 tilings)",
+    value = tasks * n / (ms / 1e3)
+    sample = ("N=M=%d uniform points per FMM, %d FP64 oracle FMMs per step (the 3 tilings on each "
+              "of %d host cores, one process per core)" % (n, tasks, pool.cores))
+    line = {"impl": "reference", "metric": metric_name(EPS),
             "value": value, "unit": "points/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "N=M=%d uniform unit square, quad+sept+tri, eps=1e-6 (oracle sample "
-                                   "of the N=M=2^20 workload)" % n},
-            "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle",
-                             "sample": "N=M=%d per tiling, 3 tilings, one FP64 evaluation per step" % n},
+            "config": {"workload": "N=M=%d uniform unit square, quad+sept+tri, eps=%s (oracle sample "
+                                   "of the N=M=2^20 workload)" % (n, eps_label(EPS))},
+            "cpu_baseline": {"value": value, "unit": "points/s", "cores": pool.cores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -250,12 +389,14 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
+        clk.start()
         for _ in range(args.steps):
             if args.serial:
                 step(per)
             else:
                 step_concurrent(whole)
         torch.cuda.synchronize()
+        clk.stop()
     if dist:
         dist.barrier()
     if not args.serial:   # per-tiling times: the same steps, one tiling after another
@@ -390,20 +531,29 @@ def run_ours(args):
         if lg2_p2p else None
     roof_iso = roofline(tot_iso, "CUDA events, one extra step with the stages serialised") if lg2_p2p else None
 
-    cpu_v, cpu_dt = (None, None)
+    cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu_v, cpu_dt = oracle_sample(n=args.ref_points, eps=args.eps)
+        v1, dt1 = oracle_sample(n=args.ref_points, eps=args.eps)
+        pool = OraclePool()
+        vc, dtc, ntask = pool.run(args.ref_points, eps=args.eps)
+        pool.close()
+        cpu = {"value": vc, "unit": "points/s", "cores": pool.cores, "kind": "oracle",
+               "sample": "N=M=%d uniform points per FMM, eps=%s: %d FP64 oracle FMMs (the 3 tilings "
+                         "on each of %d host cores, one process per core) in %.1f s"
+                         % (args.ref_points, eps_label(args.eps), ntask, pool.cores, dtc),
+               "single_core": {"value": v1, "unit": "points/s", "cores": 1,
+                               "sample": "the 3 tilings one after another, %.1f s" % dt1}}
     launches = int(sum(tot_iso[k][1] for k in tot_iso))
     if rank == 0:
         line = {
-            "metric": "FMM eval points/s at eps=%g (3 tilings)" % args.eps, "value": value, "unit": "points/s",
+            "metric": metric_name(args.eps), "value": value, "unit": "points/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f64", "hybrid": "f64 + float-float M2L + f32 pairs P2P",
                       "split": "f64 + float-float M2L"}.get(
                 args.prec, "tf32x3+f32+f64"), "data": "synthetic",
             "config": {"workload": "N=M=2^20 uniform unit square (sources=targets), FP32 points and "
-                                   "strengths, quad+sept+tri, eps=%g, %s L/p, %s form" % (args.eps,
+                                   "strengths, quad+sept+tri, eps=%s, %s L/p, %s form" % (eps_label(args.eps),
                                    "fixed" if args.params else "planner" if args.no_tune else "autotuned",
                                    args.prec),
                        "global_batch": N_POINTS,
@@ -416,6 +566,9 @@ def run_ours(args):
             "per_tiling": {t: {"points_per_s": N_POINTS / (statistics.mean(tt[t]) / 1e3),
                                "ms": statistics.mean(tt[t]), "L": info[t]["levels"], "p": info[t]["p"],
                                "m2l": info[t]["n_m2l"], "p2p_pairs": info[t]["n_p2p_pairs"],
+                               "leaf_points": {"mean": N_POINTS / max(1, info[t]["n_leaves"]),
+                                               "max": info[t]["max_leaf_src"],
+                                               "occupied_leaves": info[t]["n_leaves"]},
                                "tune_probe_err": tuned[t][2],
                                "stages_ms": {k: v[0] for k, v in stage[t].items()},
                                "stages_ms_isolated": {k: v[0] for k, v in stage_iso[t].items()}}
@@ -429,9 +582,7 @@ def run_ours(args):
             "stage_ms_total_isolated": {k: v[0] for k, v in tot_iso.items()},
             "stage_note": "stage_ms: mean of 5 steps after the timed ones, far field concurrent "
                           "with P2P; isolated: one extra step with the stages serialised",
-            "cpu_baseline": None if cpu_v is None else {
-                "value": cpu_v, "unit": "points/s", "cores": 1, "kind": "oracle",
-                "sample": "N=M=%d per tiling, 3 tilings, one FP64 evaluation (%.1f s)" % (args.ref_points, cpu_dt)},
+            "cpu_baseline": cpu,
             "e2e": {"value": e2e_v, "unit": "points/s",
                     "h2d_bytes_per_step": int(xy.nbytes + u.nbytes),
                     "d2h_bytes_per_step": int(8 * N_POINTS * len(args.tilings))},

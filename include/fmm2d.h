@@ -109,6 +109,9 @@ typedef struct {
   int32_t max_near;        /* longest Near list (P2 of Table 2) */
   int32_t device_error;    /* nonzero if a kernel of the last evaluation gave up a
                               bounded wait (results of that evaluation invalid) */
+  int64_t n_leaves;        /* leaves holding points (adaptive: of every level) */
+  int64_t max_leaf_src;    /* most sources in one leaf */
+  int64_t max_leaf_tgt;    /* most targets in one leaf */
 } fmm2d_info;
 
 /*
@@ -130,7 +133,10 @@ fmm2d_status fmm2d_default_params(int tiling, int64_t n_points, int leaf_target,
                                   int *levels_out, int *p_out, double *leaf_scale_out);
 
 /*
- * fmm2d_plan_create - make an empty plan.
+ * fmm2d_plan_create - make an empty plan.  The expansion order follows the
+ * truncation error bounds of Sec. 8 (eqs. 14-15) with the ratios of Table 2:
+ * with p == 0 the plan keeps the smallest p with kappa^(p+1) <= eps (as
+ * fmm2d_default_params).
  *   tiling: FMM2D_QUAD, FMM2D_SEPT or FMM2D_TRI.
  *   levels: leaf level L (1..12 quadtree/triangle, 1..9 septree), or 0 to
  *     choose it at fmm2d_build time with fmm2d_default_params (leaf target 64).
@@ -318,8 +324,12 @@ fmm2d_status fmm2d_autotune(int tiling, double eps, unsigned flags, const double
  * about 8.5 MiB that every GPU loading the library keeps until the process
  * exits.
  *   tiling, levels: as fmm2d_plan_create (levels >= 1).
- *   leaf_scale: septree only - the leaf circumradius that
- *     fmm2d_default_params returns for `levels`; ignored otherwise.
+ *   leaf_scale: septree only - 0, and the library uses the leaf circumradius
+ *     of `levels` (the one fmm2d_build uses; the first call for a level
+ *     enumerates it on the host, up to a few tenths of a second at level 9,
+ *     then it is cached), or exactly that value (as fmm2d_plan_query reports
+ *     it); any other value gives FMM2D_EINVAL.  Ignored for the other
+ *     tilings.
  *   domain: NULL for the unit square, else {x0, y0, S}.
  *   xy_dev: n interleaved points (float64, or float32 with FMM2D_IN_F32 in
  *     flags), 0 <= n <= 1048576 (larger n: FMM2D_EINVAL, use fmm2d_build).
@@ -329,10 +339,10 @@ fmm2d_status fmm2d_autotune(int tiling, double eps, unsigned flags, const double
  *     fmm2d_debug_export reports for a plan built on these points.
  *   err_buf / err_cap: optional caller buffer that receives the error text.
  * The first call on a device looks up the array's device address with
- * cudaGetSymbolAddress; make that first call before any stream capture.
- * The call waits for its own work (it reads back the domain-error flag).
- * All calls share the array, so calls whose GPU work overlaps race and must
- * be serialised by the caller.  Errors: FMM2D_EINVAL, FMM2D_EDOMAIN,
+ * cudaGetSymbolAddress.  Every call synchronises `stream` (it reads back the
+ * domain-error flag into host memory), so it must not be made while a stream
+ * is being captured.  All calls share the array, so calls whose GPU work
+ * overlaps race and must be serialised by the caller.  Errors: FMM2D_EINVAL, FMM2D_EDOMAIN,
  * FMM2D_ECUDA.
  */
 fmm2d_status fmm2d_keys_sort_noalloc(int tiling, int levels, double leaf_scale,

@@ -86,8 +86,10 @@ def leaf_area(tiling, L):
 
 def auto_levels(tiling, n_points, leaf_target=64):
     """Smallest leaf level L whose expected mean points per occupied leaf of
-    a uniform input does not exceed ``leaf_target``."""
-    top = {"quad": 12, "tri": 12, "sept": 8}[tiling]
+    a uniform input does not exceed ``leaf_target`` (the paper fixes no
+    deepest level; 15 levels serve up to 64 * 4^15 points, the septree stops
+    at the 8 levels whose leaf radius the tests enumerate)."""
+    top = {"quad": 15, "tri": 15, "sept": 8}[tiling]
     for L in range(1, top + 1):
         if n_points * leaf_area(tiling, L) <= leaf_target:
             return L

@@ -99,7 +99,7 @@ static int64_t sept_min_outside_norm(int L) {
 // Septree leaf circumradius r_L: every point of the frame square (inside the
 // disc of radius sqrt(1/2)) has its nearest leaf-lattice point (spacing r
 // sqrt3, covering radius r) inside the L-digit GBT region.
-static double sept_leaf_r(int L) {
+double sept_leaf_r(int L) {
   double m = std::sqrt((double)sept_min_outside_norm(L));
   double raw = std::sqrt(0.5) / (kSqrt3 * m - 1.0);
   return std::ceil(raw * 1099511627776.0) / 1099511627776.0;   // 2^40
@@ -113,7 +113,7 @@ void planner_precompute() {
 
 // Triangle root inradius: the upright triangle centred at the origin that
 // contains the frame square [-1/2, 1/2)^2, widened by 2^-20.
-static double tri_rho0() { return (kSqrt3 + 1.0) / 4.0 * (1.0 + std::ldexp(1.0, -20)); }
+double tri_rho0() { return (kSqrt3 + 1.0) / 4.0 * (1.0 + std::ldexp(1.0, -20)); }
 
 static double kappa(int tiling) {
   if (tiling == FMM2D_QUAD) return 1.0 / (1.0 + 2.0 * (std::sqrt(2.0) - 1.0));
@@ -1585,12 +1585,18 @@ fmm2d_status fmm2d_plan_query(const fmm2d_plan *cpl, fmm2d_info *info) {
     cudaMemcpy(se.data(), pl->d_src_end.p, nc * 4, cudaMemcpyDeviceToHost);
     cudaMemcpy(ts.data(), pl->same_sets ? pl->d_src_start.p : pl->d_tgt_start.p, nc * 4, cudaMemcpyDeviceToHost);
     cudaMemcpy(te.data(), pl->same_sets ? pl->d_src_end.p : pl->d_tgt_end.p, nc * 4, cudaMemcpyDeviceToHost);
-    int64_t pairs = 0;
+    int64_t pairs = 0, ml_s = 0, ml_t = 0, occ = 0;
     for (int64_t i = 0; i < nl; ++i) {
       const int a = ids[i];
       for (int e = off[i]; e < off[i + 1]; ++e) pairs += (int64_t)(te[a] - ts[a]) * (se[us[e]] - ss[us[e]]);
+      ml_s = std::max<int64_t>(ml_s, se[a] - ss[a]);
+      ml_t = std::max<int64_t>(ml_t, te[a] - ts[a]);
+      occ += (se[a] > ss[a] || te[a] > ts[a]) ? 1 : 0;
     }
     pl->n_p2p_pairs = pairs;
+    pl->n_leaves_q = occ;
+    pl->max_leaf_src = ml_s;
+    pl->max_leaf_tgt = ml_t;
   }
   if (pl->n_m2l < 0) {
     cudaStreamSynchronize(pl->last_stream);
@@ -1614,15 +1620,21 @@ fmm2d_status fmm2d_plan_query(const fmm2d_plan *cpl, fmm2d_info *info) {
       const void *tep = pl->same_sets ? pl->d_src_end.p : pl->d_tgt_end.p;
       cudaMemcpy(ts.data(), tsp, pl->n_cells * 4, cudaMemcpyDeviceToHost);
       cudaMemcpy(te.data(), tep, pl->n_cells * 4, cudaMemcpyDeviceToHost);
+      int64_t ml_s = 0, ml_t = 0;
       for (int64_t i = 0; i < nl; ++i) {
         int64_t gt = pl->lev_first[pl->L] + i;
         int64_t nt = te[gt] - ts[gt];
+        ml_s = std::max<int64_t>(ml_s, se[gt] - ss[gt]);
+        ml_t = std::max<int64_t>(ml_t, nt);
         for (int e = 0; e < nc[i]; ++e) {
           int sl = ns[i * NEAR_MAX + e];
           pairs += nt * (int64_t)(se[sl] - ss[sl]);
         }
       }
+      pl->max_leaf_src = ml_s;
+      pl->max_leaf_tgt = ml_t;
     }
+    pl->n_leaves_q = nl;
     pl->n_p2p_pairs = pairs;
   }
   {
@@ -1635,6 +1647,9 @@ fmm2d_status fmm2d_plan_query(const fmm2d_plan *cpl, fmm2d_info *info) {
   }
   info->n_m2l = pl->n_m2l;
   info->n_p2p_pairs = pl->n_p2p_pairs;
+  info->n_leaves = pl->n_leaves_q;
+  info->max_leaf_src = pl->max_leaf_src;
+  info->max_leaf_tgt = pl->max_leaf_tgt;
   return FMM2D_OK;
 }
 

@@ -74,8 +74,13 @@ extern "C" fmm2d_status fmm2d_keys_sort_noalloc(int tiling, int levels, double l
     set_msg(err_buf, err_cap, "null pointer");
     return FMM2D_EINVAL;
   }
-  if (tiling == FMM2D_SEPT && !(leaf_scale > 0.0)) {
-    set_msg(err_buf, err_cap, "septree needs leaf_scale (fmm2d_default_params)");
+  // The septree leaf radius belongs to the level count: it is computed here
+  // (host work, cached per level; no device memory), as fmm2d_build does.  A
+  // caller-given value must be that one, or the keys would silently differ.
+  const double sept_r = tiling == FMM2D_SEPT ? sept_leaf_r(levels) : 0.0;
+  if (tiling == FMM2D_SEPT && leaf_scale != 0.0 && leaf_scale != sept_r) {
+    set_msg(err_buf, err_cap,
+            "leaf_scale is not the septree leaf radius of this level count (pass 0)");
     return FMM2D_EINVAL;
   }
   const double S = domain ? domain[2] : 1.0;
@@ -120,8 +125,8 @@ extern "C" fmm2d_status fmm2d_keys_sort_noalloc(int tiling, int levels, double l
   g.y0 = domain ? domain[1] : 0.0;
   g.S = S;
   if (tiling == FMM2D_QUAD) g.leaf_scale = ldexp(1.0, -levels);
-  else if (tiling == FMM2D_TRI) g.leaf_scale = (sqrt(3.0) + 1.0) / 4.0 * (1.0 + ldexp(1.0, -20));
-  else g.leaf_scale = leaf_scale;
+  else if (tiling == FMM2D_TRI) g.leaf_scale = tri_rho0();
+  else g.leaf_scale = sept_r;
   int *err = (int *)(base + kErrOff);
   k_noalloc_clear_err<<<1, 32, 0, s>>>();
   e = cudaGetLastError();

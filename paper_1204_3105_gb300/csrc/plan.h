@@ -65,6 +65,7 @@ struct Plan {
   int64_t map_size = 0;
   int64_t lev_first[MAXLEV + 2] = {0}, lev_count[MAXLEV + 2] = {0};
   int64_t n_cells = 0, n_far_cells = 0, n_m2l = 0, n_p2p_pairs = 0;
+  int64_t n_leaves_q = 0, max_leaf_src = 0, max_leaf_tgt = 0;   // filled by fmm2d_plan_query
   int max_far = 0, max_near = 0;
   double scale_re[MAXLEV + 1], scale_im[MAXLEV + 1], log_abs_scale[MAXLEV + 1];
   std::string err;
@@ -126,6 +127,13 @@ struct Plan {
 // Host-side planner constants that take a moment to compute (septree leaf
 // radii), computed ahead of the first plan that needs them.
 void planner_precompute();
+// Septree leaf circumradius r_L of an L-level tree (frame units): the
+// smallest multiple of 2^-40 for which every point of the frame square has
+// its nearest leaf-lattice point inside the L-digit GBT region (Sec. 5).
+// Computed once per L by enumeration, then cached; host work only.
+double sept_leaf_r(int L);
+// Triangle quadtree root inradius rho0 (frame units, Sec. 6).
+double tri_rho0();
 
 cudaError_t dbuf_reserve(DBuf &b, size_t bytes);
 void dbuf_free(DBuf &b);

@@ -46,7 +46,9 @@ class Info(ctypes.Structure):
                 ("n_tgt", ctypes.c_int64), ("n_cells", ctypes.c_int64 * 24),
                 ("n_m2l", ctypes.c_int64), ("n_p2p_pairs", ctypes.c_int64),
                 ("n_m2l_ops", ctypes.c_int32), ("max_far", ctypes.c_int32),
-                ("max_near", ctypes.c_int32), ("device_error", ctypes.c_int32)]
+                ("max_near", ctypes.c_int32), ("device_error", ctypes.c_int32),
+                ("n_leaves", ctypes.c_int64), ("max_leaf_src", ctypes.c_int64),
+                ("max_leaf_tgt", ctypes.c_int64)]
 
 
 class Request(ctypes.Structure):

@@ -6,7 +6,7 @@ import time
 import numpy as np
 import pytest
 
-from oracle.direct import direct
+from oracle.direct import direct, rel_inf_error
 from paper_1204_3105_gb300.inputs import gaussian_mixture, rng, sample_targets, uniform_square
 
 pytestmark = pytest.mark.gpu
@@ -59,14 +59,47 @@ def test_alone_equals_in_the_mix(fm):
     assert rm["status"] == 0 and all(r["status"] == 0 for r in results)
     assert len({r["slot"] for r in results}) > 1          # the work was spread over slots
     assert np.array_equal(alone, mixed)                   # bit for bit
-    # two of the mixed requests against the oracle's direct sum
-    for k in (0, 7):
-        tiling, pxy, pu, eps = others[k]
+    # every mixed request against the oracle's direct sum, at its own eps
+    for k, (tiling, pxy, pu, eps) in enumerate(others):
         idx = sample_targets(len(pxy), 200, seed=k)
         ref = direct(pxy, pu, pxy[idx])
-        err = np.max(np.abs(outs[k][idx] - ref)) / np.max(np.abs(ref))
-        assert err < max(eps, 1e-7) * 3, (tiling, eps, err)
+        assert rel_inf_error(outs[k][idx], ref) <= eps, (k, tiling, eps, len(pxy))
     sv.close()
+
+
+SIZES = (1000, 10000, 100000)
+
+
+@pytest.mark.parametrize("tiling", ["quad", "sept", "tri"])
+@pytest.mark.parametrize("tree", ["adaptive", "uniform"])
+def test_served_results_meet_their_eps(fm, tiling, tree):
+    """Served requests of the serving workload's two tolerances (1e-4 and
+    1e-8), at N = 1e3, 1e4 and 1e5, uniform and 8-cluster points, each meet
+    their own eps: eps_rel_inf against the direct sum of eq. (2) on 256
+    sampled targets (the server picks the precision form from eps and N)."""
+    sv = fm.Server(16 << 30, max_slots=4)
+    flags = fm.ADAPTIVE if tree == "adaptive" else 0
+    reqs = []
+    for eps in (1e-8, 1e-4):
+        for n in SIZES:
+            for cl in (False, True):
+                seed = 7000 + n // 100 + (1 if cl else 0) + (2 if eps < 1e-6 else 0)
+                if cl:
+                    xy, u = gaussian_mixture(n, seed=seed, k=8)
+                else:
+                    xy, u = uniform_square(n, seed=seed)
+                o = np.full(n, np.nan)
+                reqs.append((eps, n, cl, xy, u, o, sv.submit(tiling, xy, u, o, eps=eps, flags=flags)))
+    bad = []
+    for eps, n, cl, xy, u, o, t in reqs:
+        r = sv.wait(t, 600000.0)
+        assert r["status"] == 0
+        idx = sample_targets(n, 256, seed=n)
+        err = rel_inf_error(o[idx], direct(xy, u, xy[idx]))
+        if not err <= eps:
+            bad.append((eps, n, "cluster" if cl else "uniform", r["flags"] & 7, r["p"], err))
+    sv.close()
+    assert not bad, bad
 
 
 def test_small_requests_merge_into_one_forest(fm):
@@ -101,7 +134,7 @@ def test_small_requests_merge_into_one_forest(fm):
         x64, u64 = xy.astype(np.float64), u.astype(np.float64)
         idx = sample_targets(len(xy), 200, seed=k)
         ref = direct(x64, u64, x64[idx])
-        assert np.max(np.abs(o[idx] - ref)) / np.max(np.abs(ref)) < 3e-6
+        assert rel_inf_error(o[idx], ref) <= 1e-6
     sv.close()
 
 

@@ -27,23 +27,32 @@ def fm():
     return fmm2d
 
 
-@pytest.mark.parametrize("tiling,levels", [("quad", 7), ("sept", 6), ("tri", 8)])
+@pytest.mark.parametrize("tiling,levels", [("quad", 7), ("sept", 6), ("tri", 8), ("sept", 9)])
 def test_noalloc_matches_build_two_calls(fm, tiling, levels):
     torch = _torch()
     dev = torch.device("cuda:0")
-    L_auto, _, leaf_scale = fm.fmm2d_default_params(tiling, 2 ** 20, 64, 1e-6)
-    assert L_auto == levels                  # leaf_scale belongs to this level count
     for call, (n, seed) in enumerate([(300007, 11), (1 << 20, 12)]):
         xy, _ = uniform_square(n, seed=seed, dtype=np.float32)
         x_d = torch.from_numpy(xy).to(dev)
         keys = torch.empty(n, dtype=torch.int32, device=dev)
         perm = torch.empty(n, dtype=torch.int32, device=dev)
-        fm.fmm2d_keys_sort_noalloc(tiling, levels, leaf_scale, None, x_d, n, fm.IN_F32, keys, perm)
+        # leaf_scale 0: the septree leaf radius of `levels` is the library's own
+        fm.fmm2d_keys_sort_noalloc(tiling, levels, 0.0, None, x_d, n, fm.IN_F32, keys, perm)
         plan = fm.Plan(tiling, levels=levels, p=4, flags=fm.PREC_MIXED | fm.IN_F32)
         plan.build(x_d, n, x_d, n)
         want_perm = plan.export("src_perm")
         want_keys = plan.export("src_keys")[want_perm]
+        leaf_scale = plan.query()["leaf_scale"]
         plan.close()
+        if tiling == "sept":   # the plan's own leaf radius is accepted, another one is not
+            k2 = torch.empty_like(keys)
+            p2 = torch.empty_like(perm)
+            fm.fmm2d_keys_sort_noalloc(tiling, levels, leaf_scale, None, x_d, n, fm.IN_F32, k2, p2)
+            assert torch.equal(k2, keys) and torch.equal(p2, perm)
+            with pytest.raises(fm.FMM2DError) as e:
+                fm.fmm2d_keys_sort_noalloc(tiling, levels, leaf_scale * 1.001, None, x_d, n,
+                                           fm.IN_F32, k2, p2)
+            assert e.value.status == fm.EINVAL
         got_perm = perm.cpu().numpy().astype(np.int64)
         got_keys = keys.cpu().numpy().view(np.uint32).astype(np.int64)
         assert np.array_equal(got_perm, want_perm), (tiling, call)
