@@ -35,13 +35,15 @@ Traversal (per level l, starting with the root):
   -> P2P; else repeat with the children of c.  The X test mirrors it.
 
 Every (target, source) pair is covered exactly once: the tests check that by
-brute force.  Only Re Phi is returned.
+brute force.  Re Phi is returned and, optionally, the field F = sum u / (y - x)
+from the differentiated operators (L2P' and P2P' as in ``fmm``, and
+M2P' = Q / (y - c) - sum_k k a_k (y - c)^-(k+1)).
 """
 from collections import defaultdict
 
 import numpy as np
 
-from .fmm import l2l, l2p, m2l, m2m, p2m, p2p
+from .fmm import l2l, l2p, l2p_field, m2l, m2m, p2m, p2p, p2p_field
 
 
 def m2p(Q, a, c, zt):
@@ -52,6 +54,17 @@ def m2p(Q, a, c, zt):
     for k in range(len(a), 0, -1):      # Horner in 1/d
         acc = (acc + a[k - 1]) * inv
     return Q * np.log(np.abs(d)) + acc.real
+
+
+def m2p_field(Q, a, c, zt):
+    """d/dy of Q log(y - c) + sum_k a_k (y - c)^-k at the complex targets zt:
+    Q / (y - c) - sum_k k a_k (y - c)^-(k+1)."""
+    d = zt - c
+    inv = 1.0 / d
+    acc = np.zeros(zt.shape, complex)
+    for k in range(len(a), 0, -1):      # Horner in 1/d: sum_k k a_k d^-k
+        acc = (acc + k * a[k - 1]) * inv
+    return inv * (Q - acc)
 
 
 def p2l(xs, us, c, p):
@@ -72,7 +85,7 @@ class AdaptiveResult:
     pass
 
 
-def adaptive_fmm(tiling, src_xy, u, tgt_xy, p, s=64, record=False):
+def adaptive_fmm(tiling, src_xy, u, tgt_xy, p, s=64, record=False, field=False):
     """Re Phi_j at every target with an adaptive p-term FMM over ``tiling``
     (its level L is the finest level a cell may be split to); a cell is split
     while it holds more than ``s`` sources or more than ``s`` targets."""
@@ -224,24 +237,35 @@ def adaptive_fmm(tiling, src_xy, u, tgt_xy, p, s=64, record=False):
 
     # target leaves: L2P + M2P (W) + P2P (U)
     phi_s = np.zeros(len(zt))
+    f_s = np.zeros(len(zt), complex)
     for l in range(Lmax + 1):
         for a in cells[l]:
             if (l, a) in split or not nt(l, a):
                 continue
             lo, hi = tgt_r[l][a]
             val = l2p(loc[(l, a)], zt[lo:hi], C(l, a))
+            fv = l2p_field(loc[(l, a)], zt[lo:hi], C(l, a)) if field else None
             for (lc, c) in W[(l, a)]:
                 Qs, a_s = mult[(lc, c)]
                 val = val + m2p(Qs, a_s, C(lc, c), zt[lo:hi])
+                if field:
+                    fv = fv + m2p_field(Qs, a_s, C(lc, c), zt[lo:hi])
             parts = [np.arange(*src_r[lc][c]) for (lc, c) in U[(l, a)]]
             if parts:
                 idx = np.concatenate(parts)
                 val = val + p2p(xs[idx], us[idx], ys[lo:hi])
+                if field:
+                    fv = fv + p2p_field(xs[idx], us[idx], ys[lo:hi])
             phi_s[lo:hi] = val
+            if field:
+                f_s[lo:hi] = fv
     phi = np.zeros(len(zt))
     phi[tperm] = phi_s
     res = AdaptiveResult()
     res.phi = phi
+    if field:
+        res.field = np.zeros(len(zt), complex)
+        res.field[tperm] = f_s
     if record:
         res.src_perm, res.tgt_perm = sperm, tperm
         res.src_keys, res.tgt_keys = skey, tkey

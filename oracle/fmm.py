@@ -21,6 +21,15 @@ series log(z - x) = log(z - c) - sum_k ((x - c)/(z - c))^k / k:
 * P2P      sum over the source points of {leaf} u Neighbors(leaf) of
            u_i log|y - x_i|, skipping a source equal to the target.
 
+Field (optional).  The complex potential of eq. 1 is analytic in y away from
+the sources and its derivative, F(y) = sum_i u_i / (y - x_i), is single
+valued (the branch of the logarithm only shifts the constant b_0).  The
+gradient of Re Phi is (Re F, -Im F).  The FMM gives it by differentiating the
+two expansions a target meets:
+* L2P'     sum_{l>=1} l b_l (y - c)^(l-1)
+* P2P'     sum over the same near sources of u_i / (y - x_i), coincident
+           pairs skipped.
+
 Algorithm order (Sec. 2 / App. A cost terms): key every point with the
 tiling's CellIndex, stable-sort by key, collect the occupied cells of every
 level, build Near (leaf level) and NeighborsE4 lists (eq. 3), upward pass
@@ -131,6 +140,25 @@ def l2p(b, ys, c):
     return acc.real
 
 
+def l2p_field(b, ys, c):
+    """d/dy of sum_l b_l (y - c)^l, i.e. sum_{l>=1} l b_l (y - c)^(l-1) (Horner)."""
+    d = ys - c
+    p = len(b) - 1
+    acc = np.zeros(ys.shape, complex) + p * b[p]
+    for l in range(p - 1, 0, -1):
+        acc = acc * d + l * b[l]
+    return acc
+
+
+def p2p_field(src_xy, us, tgt_xy):
+    """sum_i u_i / (y - x_i) over the given sources, coincident pairs skipped."""
+    dz = (tgt_xy[:, 0][:, None] - src_xy[:, 0][None, :]) + \
+        1j * (tgt_xy[:, 1][:, None] - src_xy[:, 1][None, :])
+    same = dz == 0
+    dz[same] = 1.0
+    return np.where(same, 0.0, us[None, :] / dz).sum(axis=1)
+
+
 def p2p(src_xy, us, tgt_xy):
     """sum_i u_i log|y - x_i| over the given sources, coincident pairs skipped."""
     dx = tgt_xy[:, 0][:, None] - src_xy[:, 0][None, :]
@@ -145,13 +173,15 @@ class FMMResult:
     pass
 
 
-def fmm(tiling, src_xy, u, tgt_xy, p, record=False):
+def fmm(tiling, src_xy, u, tgt_xy, p, record=False, field=False):
     """Evaluate Re Phi_j (eq. 2) at every target with a p-term FMM over
     ``tiling`` (a Quadtree, Septree or TriQuadtree with leaf level L).
 
     Returns an ``FMMResult`` with ``phi`` (original target order) and, when
     ``record`` is set, every intermediate: keys, sort permutations, cells per
-    level, lists, multipoles, locals and the near / far parts of phi."""
+    level, lists, multipoles, locals and the near / far parts of phi.  With
+    ``field`` it also holds ``field``, F_j = sum_i u_i / (y_j - x_i) from the
+    differentiated L2P and P2P (and, with ``record``, its near / far parts)."""
     src_xy = np.asarray(src_xy, np.float64).reshape(-1, 2)
     tgt_xy = np.asarray(tgt_xy, np.float64).reshape(-1, 2)
     u = np.asarray(u, np.float64)
@@ -234,17 +264,26 @@ def fmm(tiling, src_xy, u, tgt_xy, p, record=False):
     # 9-10. L2P and P2P at the leaves.
     phi_far = np.zeros(len(zt))
     phi_near = np.zeros(len(zt))
+    f_far = np.zeros(len(zt), complex)
+    f_near = np.zeros(len(zt), complex)
     for n, (lo, hi) in tgt_leaf.items():
         phi_far[lo:hi] = l2p(loc[(L, n)], zt[lo:hi], C(L, n))
+        if field:
+            f_far[lo:hi] = l2p_field(loc[(L, n)], zt[lo:hi], C(L, n))
         parts = [np.arange(*src_leaf[m]) for m in near[n]]
         if parts:
             idx = np.concatenate(parts)
             phi_near[lo:hi] = p2p(xs[idx], us[idx], ys[lo:hi])
+            if field:
+                f_near[lo:hi] = p2p_field(xs[idx], us[idx], ys[lo:hi])
 
     # 11. Undo the sort.
     phi = np.zeros(len(zt))
     phi[tperm] = phi_far + phi_near
     res.phi = phi
+    if field:
+        res.field = np.zeros(len(zt), complex)
+        res.field[tperm] = f_far + f_near
     if record:
         res.src_keys, res.tgt_keys = skey, tkey
         res.src_perm, res.tgt_perm = sperm, tperm
@@ -260,4 +299,9 @@ def fmm(tiling, src_xy, u, tgt_xy, p, record=False):
         far_o[tperm] = phi_far
         near_o[tperm] = phi_near
         res.phi_far, res.phi_near = far_o, near_o
+        if field:
+            res.field_far = np.zeros(len(zt), complex)
+            res.field_near = np.zeros(len(zt), complex)
+            res.field_far[tperm] = f_far
+            res.field_near[tperm] = f_near
     return res

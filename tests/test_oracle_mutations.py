@@ -163,3 +163,51 @@ def test_morton_axes_swapped_is_caught(monkeypatch):
         return orig(self, y, x, l)
     monkeypatch.setattr(Quadtree, "keys", bad)
     _fails(pins_quad.test_morton_containment_and_prefix)
+
+
+# ---- the field (derivative) operators ----------------------------------------
+import test_oracle_field as pins_field  # noqa: E402
+from oracle import adaptive as A  # noqa: E402
+
+
+def test_l2p_field_without_factor_l_is_caught(monkeypatch):
+    def bad(b, ys, c):           # sum b_l (y - c)^(l-1): the factor l dropped
+        d = ys - c
+        acc = np.zeros(ys.shape, complex) + b[-1]
+        for l in range(len(b) - 2, 0, -1):
+            acc = acc * d + b[l]
+        return acc
+    monkeypatch.setattr(F, "l2p_field", bad)
+    _fails(pins_field.test_l2p_field_is_derivative_of_l2p)
+    _fails(pins_field.test_fmm_field_converges_to_direct, "quad", 3)
+
+
+def test_p2p_field_conjugate_is_caught(monkeypatch):
+    orig = F.p2p_field
+    monkeypatch.setattr(F, "p2p_field", lambda s, u, t: np.conj(orig(s, u, t)))
+    _fails(pins_field.test_p2p_field_matches_direct)
+    _fails(pins_field.test_fmm_field_converges_to_direct, "tri", 3)
+
+
+def test_m2p_field_sign_is_caught(monkeypatch):
+    def bad(Q, a, c, zt):        # Q / (y - c) + sum k a_k (y - c)^-(k+1): wrong sign
+        d = zt - c
+        inv = 1.0 / d
+        acc = np.zeros(zt.shape, complex)
+        for k in range(len(a), 0, -1):
+            acc = (acc + k * a[k - 1]) * inv
+        return inv * (Q + acc)
+    monkeypatch.setattr(A, "m2p_field", bad)
+    _fails(pins_field.test_m2p_field_single_source_and_derivative)
+    _fails(pins_field.test_adaptive_field_matches_direct, "quad", 7)
+
+
+def test_direct_field_conjugate_is_caught(monkeypatch):
+    orig = pins_field.direct
+
+    def bad(src, u, tgt, block=2048, gradient=False):
+        out = orig(src, u, tgt, block=block, gradient=gradient)
+        return (out[0], np.conj(out[1])) if gradient else out
+    monkeypatch.setattr(pins_field, "direct", bad)
+    _fails(pins_field.test_direct_field_single_source_closed_form)
+    _fails(pins_field.test_direct_field_is_gradient_of_potential)
