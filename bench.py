@@ -85,12 +85,10 @@ try:
         nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(sm))
         nv.nvmlDeviceGetPowerUsage(h, ctypes.byref(pw))
         get_reasons(h, ctypes.byref(rs))
-        f.write("%.6f %d %d %d %d
-" % (time.monotonic(), sm.value, mx.value, pw.value, rs.value))
+        f.write("%.6f %d %d %d %d\n" % (time.monotonic(), sm.value, mx.value, pw.value, rs.value))
         time.sleep(period)
 except Exception as e:
-    f.write("error %s
-" % e)
+    f.write("error %s\n" % e)
 """
 _REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
             0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}

@@ -81,7 +81,7 @@ typedef enum {
                                      while it holds more than the leaf size (default 64,
                                      fmm2d_plan_set_leaf_size) sources or targets, down
                                      to `levels` (0 = 16 for the quadtree and triangle
-                                     quadtree, 9 for the septree); cells of different
+                                     quadtree, 11 for the septree); cells of different
                                      levels interact by M2P and P2L (W and X lists).
                                      The paper refines uniformly (Sec. 2); this is the
                                      adaptive extension for non-uniform data (Sec. 9). */
@@ -116,9 +116,12 @@ typedef struct {
 
 /*
  * fmm2d_default_params - the planner's rules, exposed for callers and tests.
- *   levels_out: smallest leaf level L whose expected mean points per occupied
- *     leaf of a uniform input of n_points points is <= leaf_target (the
- *     tiling's leaf area times n_points).
+ *   levels_out: with leaf_target >= 1, the smallest leaf level L whose
+ *     expected mean points per occupied leaf of a uniform input of n_points
+ *     points is <= leaf_target (the tiling's leaf area times n_points); with
+ *     leaf_target == 0, the level of S_opt (Table 2, App. A-C): the L whose
+ *     expected points per leaf s minimise the s-dependent cost
+ *     (N / s) b/(b-1) (P4 + 2) p^2 + M P2 s for N = M = n_points and p_out.
  *   p_out: smallest p with kappa^(p+1) <= eps, kappa = 1/(1 + rho/r) from
  *     Table 2 (Sec. 8; septree rho/r measured on the GBT aggregates, giving
  *     kappa = 0.525).
@@ -127,7 +130,7 @@ typedef struct {
  *     its nearest hexagon centre inside the L-digit GBT region), triangle root
  *     inradius, or 2^-L for the quadtree.
  * Any output pointer may be NULL.  Returns FMM2D_EINVAL for a bad tiling,
- * eps outside (0, 1) or n_points < 0.
+ * eps outside (0, 1), n_points < 0 or leaf_target < 0.
  */
 fmm2d_status fmm2d_default_params(int tiling, int64_t n_points, int leaf_target, double eps,
                                   int *levels_out, int *p_out, double *leaf_scale_out);
@@ -138,7 +141,8 @@ fmm2d_status fmm2d_default_params(int tiling, int64_t n_points, int leaf_target,
  * with p == 0 the plan keeps the smallest p with kappa^(p+1) <= eps (as
  * fmm2d_default_params).
  *   tiling: FMM2D_QUAD, FMM2D_SEPT or FMM2D_TRI.
- *   levels: leaf level L (1..12 quadtree/triangle, 1..9 septree), or 0 to
+ *   levels: leaf level L (1..12 quadtree/triangle, 1..9 septree; with
+ *     FMM2D_ADAPTIVE the finest level, 1..16 and 1..11), or 0 to
  *     choose it at fmm2d_build time with fmm2d_default_params (leaf target 64).
  *   p: highest expansion power 1..48, or 0 to derive it from eps.
  *   eps: requested relative tolerance (used when p == 0), 0 < eps < 1.
@@ -217,6 +221,26 @@ fmm2d_status fmm2d_build_forest(fmm2d_plan *plan, const void *xy_dev, const int6
 fmm2d_status fmm2d_evaluate(fmm2d_plan *plan, const void *strengths_dev, double *potentials_dev,
                             void *stream);
 
+/*
+ * fmm2d_evaluate_field - fmm2d_evaluate, and also the field
+ *     F_j = sum_{i : x_i != y_j} u_i / (y_j - x_i),
+ * the derivative of the complex potential of eq. 1 (Sec. 2).  Unlike the
+ * potential's imaginary part it is single valued; the gradient of Re Phi is
+ * (Re F_j, -Im F_j).  It is computed on the same tree, lists and expansions by
+ * the differentiated operators: sum u_i / (y - x_i) over the Near sources,
+ * sum_{l>=1} l b_l (y - c)^(l-1) of the leaf's local expansion, and on
+ * adaptive trees Q / (y - c) - sum_k k a_k (y - c)^-(k+1) of each W cell's
+ * multipole.  In the FP32 forms the field's near and far sums run in FP32
+ * (compensated partial sums), in the others in FP64.
+ *   strengths_dev, potentials_dev: as fmm2d_evaluate.
+ *   field_dev: 2 * n_tgt float64 outputs, (Re F_j, Im F_j) interleaved, in
+ *     the caller's target order.
+ * Asynchronous on `stream`.  Errors: as fmm2d_evaluate; FMM2D_EINVAL for a
+ * null field pointer.
+ */
+fmm2d_status fmm2d_evaluate_field(fmm2d_plan *plan, const void *strengths_dev,
+                                  double *potentials_dev, double *field_dev, void *stream);
+
 /* fmm2d_plan_query - fill *info (host struct) with the plan's parameters and
  * counts.  Errors: FMM2D_EINVAL. */
 fmm2d_status fmm2d_plan_query(const fmm2d_plan *plan, fmm2d_info *info);
@@ -256,7 +280,7 @@ fmm2d_status fmm2d_debug_export(fmm2d_plan *plan, int what, int level, void *hos
  * fmm2d_plan_set_profiling - when on (1 or 2), fmm2d_build / fmm2d_evaluate
  * record CUDA events around every stage on the stream that runs it, and
  * fmm2d_stage_times returns the accumulated milliseconds per stage
- * (keys, sort, tree, lists, p2m, m2m, m2l, l2l, l2p, p2p, other) and the
+ * (keys, sort, tree, lists, p2m, m2m, m2l, l2l, l2p, p2p, other, field) and the
  * number of launches of each.  With 1 the evaluation runs as usual: the
  * far-field stages (P2M ... L2L) run on a plan stream concurrently with P2P
  * on the caller's stream, so their times overlap.  With 2 every stage runs
@@ -294,7 +318,8 @@ fmm2d_status fmm2d_measure_alu_peaks(double *out_host);
  *   The caller's points are evaluated with seeded probe strengths (uniform in
  *   [-1, 1]); potentials at 1024 evenly spaced targets are compared with an
  *   FP64 direct sum of eq. (2) computed on the GPU.  For L in {L0-1, L0,
- *   L0+1} (L0 = fmm2d_default_params) the smallest p with
+ *   L0+1} (L0 the S_opt level of Table 2 for n_src, n_tgt and the a-priori
+ *   p, as fmm2d_default_params with leaf_target 0) the smallest p with
  *   eps_rel_inf <= eps/3 is found by bisection and build + evaluate is timed;
  *   the fastest (L, p) is returned.
  *   tiling, eps, flags, domain (NULL = unit square): as for a plan.

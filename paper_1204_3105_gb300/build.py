@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libfmm2d.so")
 
-SOURCES = ["api.cu", "keys.cu", "sort.cu", "tree.cu", "expand.cu", "p2p.cu", "noalloc.cu", "m2l_tc.cu", "m2l_ff.cu", "autotune.cu", "peaks.cu", "serve.cu", "adaptive.cu"]
+SOURCES = ["api.cu", "keys.cu", "sort.cu", "tree.cu", "expand.cu", "p2p.cu", "noalloc.cu", "m2l_tc.cu", "m2l_ff.cu", "autotune.cu", "peaks.cu", "serve.cu", "adaptive.cu", "field.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
          "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC]

@@ -96,19 +96,36 @@ static int64_t sept_min_outside_norm(int L) {
   return best;
 }
 
+// Deepest septree level whose minimal outside norm m_L is enumerated (about
+// 6e7 lattice points); deeper levels use the lower bound below.
+constexpr int SEPT_ENUM_LEVELS = 9;
+
+// sqrt(m_L), or for L > SEPT_ENUM_LEVELS a lower bound of it: a point z
+// outside the (L+1)-digit region, z = d (mod beta), has (z - unit_d) / beta
+// outside the L-digit region, so |z| >= sqrt7 sqrt(m_L) - 1.  The recursion
+// from the enumerated level, less 1e-9 per step for rounding, stays below the
+// true value, which only makes the leaf radius larger (still covering).
+static double sept_root_norm(int L) {
+  if (L <= SEPT_ENUM_LEVELS) return std::sqrt((double)sept_min_outside_norm(L));
+  double m = std::sqrt((double)sept_min_outside_norm(SEPT_ENUM_LEVELS));
+  for (int l = SEPT_ENUM_LEVELS; l < L; ++l) m = std::sqrt(7.0) * m - 1.0 - 1e-9;
+  return m;
+}
+
 // Septree leaf circumradius r_L: every point of the frame square (inside the
 // disc of radius sqrt(1/2)) has its nearest leaf-lattice point (spacing r
 // sqrt3, covering radius r) inside the L-digit GBT region.
 double sept_leaf_r(int L) {
-  double m = std::sqrt((double)sept_min_outside_norm(L));
+  const double m = sept_root_norm(L);
   double raw = std::sqrt(0.5) / (kSqrt3 * m - 1.0);
   return std::ceil(raw * 1099511627776.0) / 1099511627776.0;   // 2^40
 }
 
 // The septree leaf radii of every level an adaptive tree may reach (a few
-// tenths of a second of host work at the deepest level, then cached).
+// tenths of a second of host work at the deepest enumerated level, then
+// cached).
 void planner_precompute() {
-  for (int L = 1; L <= 9; ++L) sept_leaf_r(L);
+  for (int L = 1; L <= SEPT_ENUM_LEVELS; ++L) sept_leaf_r(L);
 }
 
 // Triangle root inradius: the upright triangle centred at the origin that
@@ -123,8 +140,8 @@ static double kappa(int tiling) {
 
 static int max_levels(int tiling) { return tiling == FMM2D_SEPT ? 9 : 12; }
 // adaptive trees: keys of the finest level fit 32 bits (quadtree and triangle
-// quadtree: 2 bits a level; septree: the cached leaf-radius enumeration)
-static int ad_max_levels(int tiling) { return tiling == FMM2D_SEPT ? 9 : 16; }
+// quadtree: 2 bits a level; septree: 7^11 < 2^32)
+static int ad_max_levels(int tiling) { return tiling == FMM2D_SEPT ? 11 : 16; }
 static int max_levels_for(int tiling, unsigned flags) {
   return (flags & FMM2D_ADAPTIVE) ? ad_max_levels(tiling) : max_levels(tiling);
 }
@@ -144,6 +161,30 @@ static int auto_levels(int tiling, int64_t n, int leaf_target) {
   for (int L = 1; L <= top; ++L)
     if ((double)n * leaf_area(tiling, L) <= (double)leaf_target) return L;
   return top;
+}
+
+// S_opt of Table 2 (App. A-C): the leaf level whose expected sources per
+// leaf s_L = N leaf_area(L) minimise the s-dependent FMM cost
+// (N / s) b/(b-1) (P4 + 2) p^2 + M P2 s (M2L work of N / s leaves against
+// the direct work of M targets), P4 = 27 / 42 / 39 and P2 = 9 / 7 / 13.
+int planner_sopt_levels(int tiling, int64_t n_src, int64_t n_tgt, int p) {
+  const double P4 = tiling == FMM2D_QUAD ? 27.0 : tiling == FMM2D_SEPT ? 42.0 : 39.0;
+  const double P2 = tiling == FMM2D_QUAD ? 9.0 : tiling == FMM2D_SEPT ? 7.0 : 13.0;
+  const double b = tiling == FMM2D_SEPT ? 7.0 : 4.0;
+  const double N = (double)std::max<int64_t>(1, n_src), M = (double)std::max<int64_t>(1, n_tgt);
+  const double m2l = b / (b - 1.0) * (P4 + 2.0) * (double)p * (double)p;
+  const int top = tiling == FMM2D_SEPT ? 8 : 12;
+  int best_l = 1;
+  double best = 0.0;
+  for (int L = 1; L <= top; ++L) {
+    const double sl = N * leaf_area(tiling, L);
+    const double c = N / sl * m2l + M * P2 * sl;
+    if (L == 1 || c < best) {
+      best = c;
+      best_l = L;
+    }
+  }
+  return best_l;
 }
 
 static int p_from_eps(int tiling, double eps) {
@@ -1241,15 +1282,86 @@ fmm2d_status evaluate_adaptive_t(fmm2d_plan *pl, const void *u, double *out, cud
   return FMM2D_OK;
 }
 
+// The field F = sum u / (y - x) after an evaluation on s (the strengths are
+// gathered and the locals final): P2P' (and M2P' on adaptive trees) into the
+// near part, then L2P' adds the far part and writes the caller's order.
+template <typename R>
+fmm2d_status field_t(fmm2d_plan *pl, double *field, cudaStream_t s) {
+  const bool ad = (pl->flags & FMM2D_ADAPTIVE) != 0;
+  const int L = pl->L;
+  const R *src4 = (const R *)pl->d_src4.p;
+  const R *tgt = pl->same_sets ? src4 : (const R *)pl->d_tgt2.p;
+  const int tstride = pl->same_sets ? 4 : 2;
+  const uint32_t *tperm = (const uint32_t *)(pl->same_sets ? pl->d_perm_s.p : pl->d_perm_t.p);
+  const int *ss = (const int *)pl->d_src_start.p, *se = (const int *)pl->d_src_end.p;
+  const int *ts = pl->same_sets ? ss : (const int *)pl->d_tgt_start.p;
+  const int *te = pl->same_sets ? se : (const int *)pl->d_tgt_end.p;
+  const double2 *ctr = (const double2 *)pl->d_cell_ctr.p;
+  CK(dbuf_reserve(pl->d_fnear, std::max<int64_t>(1, pl->n_tgt) * sizeof(double2)), "alloc");
+  double2 *fnear = (double2 *)pl->d_fnear.p;
+  ExpandArgs a;
+  a.p = pl->p;
+  a.P = pl->P;
+  a.L = L;
+  a.l_min = pl->l_min;
+  a.b = pl->b;
+  if (ad) {
+    a.leaf_first = 0;
+    a.n_leaves = pl->n_leaves_ad;
+    a.inv_s_re = 1.0;
+    a.inv_s_im = 0.0;
+    a.leaf_ids = (const int *)pl->d_leaf_ids.p;
+    a.cell_lev = (const uint8_t *)pl->d_cell_lev.p;
+    a.inv_scale = (const double2 *)pl->d_ad_inv_scale.p;
+  } else {
+    a.leaf_first = pl->lev_first[L];
+    a.n_leaves = pl->lev_count[L];
+    const cd inv_s = 1.0 / cd(pl->scale_re[L], pl->scale_im[L]);
+    a.inv_s_re = inv_s.real();
+    a.inv_s_im = inv_s.imag();
+  }
+  StageScope sc(pl, ST_FIELD, s, ad ? 3 : 2);
+  if (ad) {
+    CK(launch_p2p_field<R>(0, pl->n_leaves_ad, a.leaf_ids, src4, tgt, tstride, ss, se, ts, te,
+                           nullptr, (const int *)pl->d_u_off.p, (const int *)pl->d_u_src.p, ctr,
+                           fnear, s), "p2p field");
+    CK(launch_m2p_field<R>(pl->n_leaves_ad, a.leaf_ids, (const int *)pl->d_w_off.p,
+                           (const int *)pl->d_w_src.p, tgt, tstride, ts, te, ctr, a.cell_lev,
+                           (const double2 *)pl->d_ad_scale.p, pl->p, pl->P,
+                           (const double *)pl->d_mQ.p, (const Cx<R> *)pl->d_ma.p, fnear, s),
+       "m2p field");
+  } else {
+    CK(launch_p2p_field<R>(a.leaf_first, a.n_leaves, nullptr, src4, tgt, tstride, ss, se, ts, te,
+                           (const int *)pl->d_near_cnt.p, nullptr, (const int *)pl->d_near_src.p,
+                           ctr, fnear, s), "p2p field");
+  }
+  CK(launch_l2p_field<R>(a, tgt, tstride, ts, te, tperm, (const Cx<R> *)pl->d_lb.p, fnear,
+                         (double2 *)field, s), "l2p field");
+  return FMM2D_OK;
+}
+
 extern "C" {
+
+fmm2d_status fmm2d_evaluate_field(fmm2d_plan *pl, const void *u, double *out, double *field,
+                                  void *stream) {
+  if (!pl) return FMM2D_EINVAL;
+  if (pl->built && pl->n_tgt > 0 && !field) return fail(pl, FMM2D_EINVAL, "null field pointer");
+  const fmm2d_status st = fmm2d_evaluate(pl, u, out, stream);
+  if (st != FMM2D_OK || pl->n_tgt == 0) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (is_fp64(pl)) return field_t<double>(pl, field, s);
+  return field_t<float>(pl, field, s);
+}
 
 fmm2d_status fmm2d_default_params(int tiling, int64_t n_points, int leaf_target, double eps,
                                   int *levels_out, int *p_out, double *leaf_scale_out) {
-  if (tiling < 0 || tiling > 2 || n_points < 0 || !(eps > 0.0 && eps < 1.0) || leaf_target < 1)
+  if (tiling < 0 || tiling > 2 || n_points < 0 || !(eps > 0.0 && eps < 1.0) || leaf_target < 0)
     return FMM2D_EINVAL;
-  int L = auto_levels(tiling, n_points, leaf_target);
+  const int p = p_from_eps(tiling, eps);
+  int L = leaf_target > 0 ? auto_levels(tiling, n_points, leaf_target)
+                          : planner_sopt_levels(tiling, n_points, n_points, p);
   if (levels_out) *levels_out = L;
-  if (p_out) *p_out = p_from_eps(tiling, eps);
+  if (p_out) *p_out = p;
   if (leaf_scale_out) {
     if (tiling == FMM2D_QUAD) *leaf_scale_out = std::ldexp(1.0, -L);
     else if (tiling == FMM2D_TRI) *leaf_scale_out = tri_rho0();
@@ -1852,6 +1964,7 @@ void fmm2d_plan_destroy(fmm2d_plan *pl) {
                   &pl->d_tgt_start, &pl->d_tgt_end, &pl->d_lev_first, &pl->d_far_cnt,
                   &pl->d_far_src, &pl->d_far_op, &pl->d_near_cnt, &pl->d_near_src, &pl->d_src4,
                   &pl->d_tgt2, &pl->d_mQ, &pl->d_ma, &pl->d_ma_ff, &pl->d_lL0, &pl->d_lb, &pl->d_phi_near,
+                  &pl->d_fnear,
                   &pl->d_phi_far, &pl->d_sten, &pl->d_geo_scale, &pl->d_m2l_ops, &pl->d_m2l_logz,
                   &pl->d_m2m_ops, &pl->d_l2l_ops, &pl->d_counts, &pl->d_far_full,
                   &pl->d_cls_cnt, &pl->d_cls_cells, &pl->d_tc_ops, &pl->d_ff_ops, &pl->d_ff_ph, &pl->d_dev_err,

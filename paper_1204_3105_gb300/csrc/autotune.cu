@@ -7,7 +7,8 @@
 // potentials at sampled targets with an FP64 direct sum computed on the GPU
 // (k_direct_sample, eq. 2 summed exactly as written).  For each candidate L
 // it finds the smallest p whose eps_rel_inf is at most eps/3, times
-// build + evaluate, and returns the fastest (L, p).
+// build + evaluate, and returns the fastest (L, p).  The candidate levels
+// surround the level of S_opt (Table 2, App. A-C) for the a-priori p.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -59,9 +60,10 @@ extern "C" fmm2d_status fmm2d_autotune(int tiling, double eps, unsigned flags, c
   cudaStream_t s = (cudaStream_t)stream;
   const bool f32 = (flags & FMM2D_IN_F32) != 0;
   const size_t esz = f32 ? 4 : 8;
-  int L0 = 0, pmax = 0;
-  fmm2d_status st = fmm2d_default_params(tiling, std::max(n_src, n_tgt), 64, eps, &L0, &pmax, nullptr);
+  int pmax = 0;
+  fmm2d_status st = fmm2d_default_params(tiling, std::max(n_src, n_tgt), 64, eps, nullptr, &pmax, nullptr);
   if (st != FMM2D_OK) return st;
+  const int L0 = planner_sopt_levels(tiling, n_src, n_tgt, pmax);
   if ((flags & FMM2D_PREC_MASK) == FMM2D_PREC_MIXED_TC) pmax = std::min(pmax, 31);
   // seeded probe strengths (64-bit LCG, uniform in [-1, 1))
   std::vector<double> ud(n_src);

@@ -21,7 +21,7 @@ constexpr int FAR_MAX = 48;      // longest M2L stencil (septree: 42)
 constexpr int NEAR_MAX = 16;     // longest Near stencil (triangle: 13)
 
 enum Stage { ST_KEYS, ST_SORT, ST_TREE, ST_LISTS, ST_P2M, ST_M2M, ST_M2L, ST_L2L, ST_L2P, ST_P2P,
-             ST_OTHER, ST_COUNT };
+             ST_OTHER, ST_FIELD, ST_COUNT };
 
 // Grow-only device buffer owned by a plan.
 struct DBuf {
@@ -90,6 +90,7 @@ struct Plan {
   DBuf d_srclo, d_tgtlo;               // their low parts (float2 per point)
   DBuf d_mQ, d_ma, d_lL0, d_lb;
   DBuf d_phi_near, d_phi_far;
+  DBuf d_fnear;                        // near part of the field (fmm2d_evaluate_field)
   DBuf d_sten, d_geo_scale;
   DBuf d_m2l_ops, d_m2l_logz, d_m2m_ops, d_l2l_ops;   // element type per precision
   DBuf d_counts;
@@ -134,6 +135,9 @@ void planner_precompute();
 double sept_leaf_r(int L);
 // Triangle quadtree root inradius rho0 (frame units, Sec. 6).
 double tri_rho0();
+// Leaf level of the S_opt rule (Table 2, App. A-C) for N sources, M targets
+// and expansion order p.
+int planner_sopt_levels(int tiling, int64_t n_src, int64_t n_tgt, int p);
 
 cudaError_t dbuf_reserve(DBuf &b, size_t bytes);
 void dbuf_free(DBuf &b);
@@ -356,5 +360,25 @@ cudaError_t launch_p2p(int64_t leaf_first, int64_t n_leaves, const int *leaf_ids
 // launch_p2p's per-class group sizes; cnt8[0..3] the class counts.
 cudaError_t launch_p2p_bins(int64_t n_leaves, const int *leaf_ids, const int *ts, const int *te,
                             int *cnt8, int *order, cudaStream_t s);
+
+// ---------------------------------------------------------------- field.cu
+// The field F = sum u / (y - x) by the differentiated P2P, M2P and L2P
+// (fmm2d_evaluate_field); fnear: per target (sorted order) double2.
+template <typename R>
+cudaError_t launch_p2p_field(int64_t leaf_first, int64_t n_leaves, const int *leaf_ids,
+                             const R *src4, const R *tgt, int tstride, const int *src_start,
+                             const int *src_end, const int *tgt_start, const int *tgt_end,
+                             const int *near_cnt, const int *near_off, const int *near_src,
+                             const double2 *ctr, double2 *fnear, cudaStream_t s);
+template <typename R>
+cudaError_t launch_m2p_field(int64_t n_leaves, const int *leaf_ids, const int *w_off,
+                             const int *w_src, const R *tgt, int tstride, const int *ts,
+                             const int *te, const double2 *ctr, const uint8_t *lev,
+                             const double2 *scale, int p, int P, const double *mQ, const Cx<R> *ma,
+                             double2 *fnear, cudaStream_t s);
+template <typename R>
+cudaError_t launch_l2p_field(const ExpandArgs &a, const R *tgt, int tstride, const int *start,
+                             const int *end, const uint32_t *perm, const Cx<R> *lb,
+                             const double2 *fnear, double2 *out, cudaStream_t s);
 
 }  // namespace fmm2d

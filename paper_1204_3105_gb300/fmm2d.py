@@ -23,7 +23,8 @@ ADAPTIVE = 0x20
 
 OK, EINVAL, ENOMEM, EDOMAIN, ECUDA, EBUSY, ETIMEOUT, ENOTREADY = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "EDOMAIN", "ECUDA", "EBUSY", "ETIMEOUT", "ENOTREADY"]
-STAGES = ["keys", "sort", "tree", "lists", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "other"]
+STAGES = ["keys", "sort", "tree", "lists", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "other",
+          "field"]
 
 EXPORTS = {"src_keys": 1, "src_perm": 2, "tgt_keys": 3, "tgt_perm": 4, "cells": 5, "near": 6,
            "far": 7, "multipoles": 8, "locals": 9, "phi_near": 10, "phi_far": 11, "centers": 12,
@@ -35,7 +36,7 @@ SYMBOLS = ["fmm2d_default_params", "fmm2d_plan_create", "fmm2d_plan_set_domain",
            "fmm2d_keys_sort_noalloc", "fmm2d_autotune", "fmm2d_measure_alu_peaks",
            "fmm2d_plan_set_params", "fmm2d_serve_create", "fmm2d_serve_submit", "fmm2d_serve_poll",
            "fmm2d_serve_wait", "fmm2d_serve_stats", "fmm2d_serve_destroy",
-           "fmm2d_plan_set_leaf_size", "fmm2d_build_forest"]
+           "fmm2d_plan_set_leaf_size", "fmm2d_build_forest", "fmm2d_evaluate_field"]
 
 
 class Info(ctypes.Structure):
@@ -96,6 +97,7 @@ def lib():
     L.fmm2d_plan_set_domain.argtypes = [vp, dbl, dbl, dbl]
     L.fmm2d_build.argtypes = [vp, vp, i64, vp, i64, vp]
     L.fmm2d_evaluate.argtypes = [vp, vp, vp, vp]
+    L.fmm2d_evaluate_field.argtypes = [vp, vp, vp, vp, vp]
     L.fmm2d_plan_query.argtypes = [vp, ctypes.POINTER(Info)]
     L.fmm2d_debug_export.argtypes = [vp, c_int, c_int, vp, ctypes.c_size_t,
                                      ctypes.POINTER(ctypes.c_size_t)]
@@ -240,6 +242,13 @@ class Plan:
                                             _stream(stream)), "evaluate")
 
     evaluate = fmm2d_evaluate
+
+    def fmm2d_evaluate_field(self, strengths, potentials, field, stream=None):
+        """field: 2 * n_tgt float64 device values (Re F, Im F) per target."""
+        self._check(self.lib.fmm2d_evaluate_field(self._h, _ptr(strengths), _ptr(potentials),
+                                                  _ptr(field), _stream(stream)), "evaluate_field")
+
+    evaluate_field = fmm2d_evaluate_field
 
     def fmm2d_plan_query(self):
         info = Info()

@@ -50,6 +50,11 @@ def test_planner_rules_match_oracle(fm, tiling):
             assert r == op.tri_root_inradius()
     for eps in (1e-3, 1e-4, 1e-8, 1e-10):
         assert fm.fmm2d_default_params(tiling, 1000, 64, eps)[1] == op.p_from_eps(tiling, eps)
+    # leaf target 0: the S_opt level of Table 2 / App. A-C
+    for n in (1000, 5120, 100000, 2 ** 20, 4 * 10 ** 6):
+        for eps in (1e-4, 1e-6, 1e-10):
+            L, p, _ = fm.fmm2d_default_params(tiling, n, 0, eps)
+            assert L == op.sopt_levels(tiling, n, n, p), (n, eps)
 
 
 def test_bad_arguments_rejected_without_gpu(fm):

@@ -143,6 +143,8 @@ def test_edge_cases():
     assert rel_inf_error(phi, direct(xy, u, xy)) < 1e-5      # p = 8 truncation
     with pytest.raises(fmm2d.FMM2DError):
         fmm2d.Plan("quad", levels=17, p=8, flags=fmm2d.ADAPTIVE)
+    with pytest.raises(fmm2d.FMM2DError):   # septree keys of 12 levels exceed 32 bits
+        fmm2d.Plan("sept", levels=12, p=8, flags=fmm2d.ADAPTIVE)
 
 
 @pytest.mark.parametrize("tiling", ["quad", "sept"])
@@ -160,4 +162,27 @@ def test_clustered_4m_eps_1e10_sampled(tiling, prec):
     idx = sample_targets(n, 96, seed=5)
     ref = direct(xy, u, xy[idx])
     assert rel_inf_error(phi[idx], ref) < 1e-10
-    assert info["levels"] == (16 if tiling == "quad" else 9)    # the default finest level
+    assert info["levels"] == (16 if tiling == "quad" else 11)   # the default finest level
+    # the configuration's "adaptive depth to leaf <= 64": no leaf holds more
+    assert info["max_leaf_src"] <= 64 and info["max_leaf_tgt"] <= 64, info
+
+
+def test_septree_eleven_levels_bit_exact():
+    """Two tight clusters on an 11-level septree (the deepest with 32-bit
+    keys; its leaf radius comes from the norm lower bound, not from an
+    enumeration): cells and U / W / X / M2L lists bit for bit with the
+    oracle, FP64 potentials within 1e-11, and the tree reaches level 11."""
+    xy, u = gaussian_mixture(3000, seed=35, k=2, sigma=(2e-5, 1e-4))
+    p = 6
+    phi, plan = run_gpu("sept", xy, u, levels=11, p=p, prec="fp64", keep=True, leaf_size=8)
+    r = adaptive_fmm(make_tiling("sept", 11), xy, u, xy, p, s=8, record=True)
+    cells = plan.export("ad_cells")
+    want = sorted((l, n, int((l, n) in r.split)) for l, cs in enumerate(r.cells) for n in cs)
+    assert sorted(map(tuple, cells.tolist())) == want
+    assert max(l for l, _, _ in want) == 11
+    for name, d, pairs in (("ad_u", r.U, True), ("ad_w", r.W, True), ("ad_x", r.X, True),
+                           ("ad_v", {k: v for k, v in r.V.items() if v}, False)):
+        got = sorted(map(tuple, plan.export(name).tolist()))
+        assert got == _tuples(d, pairs), name
+    plan.close()
+    assert rel_inf_error(phi, r.phi) < 1e-11

@@ -284,3 +284,25 @@ def test_plain_fp64_quadtree_8192():
     err = rel_inf_error(phi, ref)
     assert err < 1e-6
     assert abs(err - rel_inf_error(r.phi, ref)) < 1e-9
+
+
+@pytest.mark.parametrize("tiling", ["quad", "sept", "tri"])
+def test_separate_sets_full_size_autotuned(tiling):
+    """M != N at full size: N = 2^20 sources and M = 2^19 other targets (FP32,
+    uniform), (L, p) from fmm2d_autotune (levels around the S_opt level of
+    Table 2 for N and M) for eps = 1e-6, tensor-core form; 512 sampled
+    targets against the direct sum over all sources within eps."""
+    import torch
+    from paper_1204_3105_gb300 import fmm2d
+    n, m = 1 << 20, 1 << 19
+    src, u = uniform_square(n, seed=61, dtype=np.float32)
+    tgt, _ = uniform_square(m, seed=62, dtype=np.float32)
+    dev = torch.device("cuda:0")
+    s_d = torch.from_numpy(src).to(dev)
+    t_d = torch.from_numpy(tgt).to(dev)
+    L, p, err, ms = fmm2d.fmm2d_autotune(tiling, 1e-6, fmm2d.PREC_MIXED_TC | fmm2d.IN_F32, s_d, n, t_d, m)
+    assert 0 < err <= 1e-6 / 3 and ms > 0
+    phi, _ = run_gpu(tiling, src, u, tgt, levels=L, p=p, eps=1e-6, prec="tc", f32=True)
+    idx = sample_targets(m, 512, seed=7)
+    ref = direct(src.astype(np.float64), u.astype(np.float64), tgt[idx].astype(np.float64))
+    assert rel_inf_error(phi[idx], ref) <= 1e-6

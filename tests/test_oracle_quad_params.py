@@ -94,3 +94,29 @@ def test_auto_levels():
     assert auto_levels("quad", 2 ** 20) == 7
     assert auto_levels("tri", 2 ** 20) == 8
     assert auto_levels("sept", 2 ** 20) == 6
+
+
+
+def test_s_opt_is_table2_and_minimises_app_cost():
+    """S_opt (Table 2) from P4, P2 and the branching factor reproduces the
+    printed coefficients, and it is where the s-dependent cost of App. A-C
+    is smallest (checked against a numeric minimisation on a fine grid)."""
+    from oracle.params import app_cost, s_opt
+    rows = {f[0]: (int(f[1]), int(f[2])) for f in (l.split() for l in golden_lines("table2_sopt.txt"))}
+    for t, (num, den) in rows.items():
+        assert s_opt(t, 1.0, 1.0, 1.0) == pytest.approx(math.sqrt(num / den), rel=1e-12)
+        for p, N, M in ((12, 5120, 5120), (22, 2 ** 20, 2 ** 19), (8, 1000, 30000)):
+            grid = np.exp(np.linspace(np.log(0.1), np.log(1e4), 200001))
+            best = grid[np.argmin(app_cost(t, p, N, M, grid))]
+            assert best == pytest.approx(s_opt(t, p, N, M), rel=1e-3)
+
+
+def test_sopt_levels_balances_the_cost():
+    """The S_opt level rule picks the level whose per-leaf count is nearest
+    S_opt in the cost's sense: its cost is below both neighbours'."""
+    from oracle.params import app_cost, leaf_area, sopt_levels
+    for t in ("quad", "sept", "tri"):
+        for N, M, p in ((2 ** 20, 2 ** 20, 22), (5120, 5120, 12), (10 ** 6, 3 * 10 ** 5, 14)):
+            L = sopt_levels(t, N, M, p)
+            c = lambda l: app_cost(t, p, N, M, N * leaf_area(t, l))
+            assert c(L) <= c(L + 1) and (L == 1 or c(L) <= c(L - 1))

@@ -205,3 +205,41 @@ def test_leaf_radius_table_is_monotone():
     assert all(a > b for a, b in zip(rs, rs[1:]))
     for L, r in enumerate(rs, start=1):
         assert r * 2 ** 40 == int(r * 2 ** 40)
+
+
+def test_deep_level_norm_bound_holds_where_enumerated():
+    """Levels beyond the enumerated ones take the lower bound
+    sqrt(m_{L+1}) >= sqrt7 sqrt(m_L) - 1 on the smallest norm of a lattice
+    point outside the L-digit GBT region (its last base-beta digit removed,
+    such a point maps to one outside the shorter region, and |beta| = sqrt7).
+    Where m_L is enumerated the bound must lie below it, and a leaf radius
+    computed from the bound must be at least the enumerated one (so the
+    region still covers the domain square)."""
+    from oracle.params import sept_root_norm_bound
+    for L in range(1, 9):
+        lo = math.sqrt(7.0) * math.sqrt(sept_min_outside_norm(L)) - 1.0
+        assert lo < math.sqrt(sept_min_outside_norm(L + 1))
+        raw = math.sqrt(0.5) / (math.sqrt(3.0) * (lo - 1e-9) - 1.0)
+        assert math.ceil(raw * 2.0 ** 40) / 2.0 ** 40 >= sept_leaf_circumradius(L + 1)
+    assert sept_root_norm_bound(5) == math.sqrt(sept_min_outside_norm(5))
+    # beyond the enumerated levels: below sqrt7 times the previous level
+    for L in (10, 11):
+        assert sept_root_norm_bound(L) < math.sqrt(7.0) * sept_root_norm_bound(L - 1)
+        assert sept_leaf_circumradius(L) < sept_leaf_circumradius(L - 1)
+
+
+@pytest.mark.parametrize("L", [10, 11])
+def test_deep_levels_cover_the_domain(L):
+    """Septrees of 10 and 11 levels (keys below 7^11 < 2^32) key every point
+    of the domain square: the corners (farthest from the root centre), its
+    edges and random points all get an L-digit GBT key."""
+    T = ts.Septree(L)
+    rng = np.random.default_rng(L)
+    e = 1 - 1e-12
+    g = np.linspace(0, e, 2001)
+    edge = np.concatenate([np.column_stack([g, np.zeros_like(g)]), np.column_stack([g, np.full_like(g, e)]),
+                           np.column_stack([np.zeros_like(g), g]), np.column_stack([np.full_like(g, e), g])])
+    corners = np.array([[0, 0], [e, 0], [0, e], [e, e]]) + 1e-9 * rng.random((4, 2))
+    pts = np.vstack([edge, np.clip(corners, 0, e), rng.random((20000, 2))])
+    k = T.keys(pts[:, 0], pts[:, 1])        # raises DomainError if a point is not covered
+    assert k.min() >= 0 and k.max() < 7 ** L
