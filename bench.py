@@ -32,11 +32,10 @@ EPS = 1e-6
 TILINGS = ("quad", "sept", "tri")
 SEED = 2
 MUFU_PER_CLK_SM = 16      # lg2 results per clock per SM (MUFU pipe)
-# DRAM bytes (read + write) of one P2P launch on the 2^20-point quadtree
-# workload from an ncu capture of the current kernel, or None: the capture
-# summarised in profiles/p2p_x2_quad_2p20.md (18.3 MB, the sorted sources
-# read once) predates the kernel's leaf size-class indirection
-P2P_TRAFFIC = None         # bytes: dram__bytes_read.sum + dram__bytes_write.sum of one launch
+# DRAM bytes (read + write) of one P2P launch per tiling on the 2^20-point
+# workload, from an ncu capture of the current kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum; summarised in profiles/p2p_x2_traffic_2p20.md)
+P2P_TRAFFIC = {"quad": 18325760 + 256, "sept": 17503232 + 0, "tri": 19340544 + 0}
 FP32_LANES_SM = 128       # FP32 FMA lanes per SM
 
 
@@ -510,8 +509,14 @@ def run_ours(args):
             pairs = sum(info[t]["n_p2p_pairs"] for t in args.tilings)
             peak = alu["lg2_gops"]
             ach = pairs / (tt_[dom][0] / 1e3) / 1e9
+            traffic = None
+            if all(t in P2P_TRAFFIC for t in args.tilings):
+                traffic = sum(P2P_TRAFFIC[t] for t in args.tilings) / len(args.tilings)
             return {"kernel": "k_p2p_x2 (P2P)", "bound": "alu", "achieved": ach, "peak": peak,
-                    "unit": "Gpair/s", "frac": ach / peak, "traffic": P2P_TRAFFIC,
+                    "unit": "Gpair/s", "frac": ach / peak, "traffic": traffic,
+                    "traffic_note": "bytes per launch, mean of the tilings' launches (ncu): "
+                                    "the sorted sources read once (16 B each); algorithmic "
+                                    "16.8 MB per launch",
                     "peak_source": "measured MUFU lg2 rate (fmm2d_measure_alu_peaks), one lg2 per pair",
                     "timing": note}
         fl = 0.0
@@ -523,6 +528,20 @@ def run_ours(args):
         return {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": None,
                 "peak_source": "measured FP32 FMA rate (fmm2d_measure_alu_peaks)", "timing": note}
+
+    def roofline_m2l(tt_, note):
+        """The tensor-core M2L against the measured TF32 tensor rate: useful
+        flops 8 p (p + 1) per translation (a complex (p+1) x p product); the
+        split form issues five TF32 products for each."""
+        ms_ = tt_.get("m2l", (0.0, 0))[0]
+        if args.prec != "tc" or ms_ <= 0.0 or not alu.get("tf32_tflops"):
+            return None
+        fl = sum(info[t]["n_m2l"] * 8.0 * info[t]["p"] * (info[t]["p"] + 1) for t in args.tilings)
+        ach = fl / (ms_ / 1e3) / 1e12
+        return {"kernel": "k_m2l_tc (M2L, tcgen05 kind::tf32)", "bound": "tensor", "achieved": ach,
+                "issued": 5 * ach, "peak": alu["tf32_tflops"], "unit": "TFLOP/s",
+                "frac": ach / alu["tf32_tflops"], "frac_issued": 5 * ach / alu["tf32_tflops"],
+                "peak_source": "measured TF32 tcgen05 rate (fmm2d_measure_alu_peaks)", "timing": note}
 
     lg2_p2p = args.prec in ("tc", "mixed")   # the P2P roofline counts one MUFU lg2 per pair
     roof = roofline(tot, "CUDA events around the stage, 5 steps after the timed ones (far field concurrent)") \
@@ -574,6 +593,7 @@ def run_ours(args):
             "fp64_form": fp64_form,
             "roofline": roof,
             "roofline_isolated": roof_iso,
+            "roofline_m2l": roofline_m2l(tot_iso, "CUDA events, one extra step with the stages serialised"),
             "peaks_source": src,
             "alu_peaks": alu,
             "stage_ms_total": {k: v[0] for k, v in tot.items()},
@@ -826,6 +846,39 @@ def run_forest_batch(args):
         torch.cuda.synchronize()
         if it >= args.warmup:
             e2e.append(time.perf_counter() - t0)
+    # the plain FP64 GPU form on the same forests, p tuned for the same eps
+    fp64_form = None
+    if not args.no_fp64_form:
+        ms64 = 0.0
+        per64 = {}
+        for name in names:
+            f = forests[name]
+            idx = np.nonzero(tilings == names.index(name))[0]
+            big = int(np.argmax(sizes[idx]))
+            bxy = torch.from_numpy(uniform_square(int(sizes[idx][big]), seed=1000 + int(idx[big]),
+                                                  dtype=np.float32)[0]).to(dev)
+            _, p64, e64, _ = fmm2d.fmm2d_autotune(name, 1e-6, fmm2d.PREC_FP64 | fmm2d.IN_F32, bxy,
+                                                  len(bxy), bxy, len(bxy), stream=stream)
+            pl = fmm2d.Plan(name, 0, p64, 1e-6, fmm2d.PREC_FP64 | fmm2d.IN_F32 | fmm2d.ADAPTIVE)
+            pl.set_leaf_size(args.leaf_size)
+            ts = []
+            for it in range(3):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pl.build_forest(f["xy_d"], f["off"], stream)
+                pl.evaluate(f["u_d"], f["out"], stream)
+                e1.record(stream)
+                e1.synchronize()
+                if it > 0:
+                    ts.append(e0.elapsed_time(e1))
+                flush.zero_()
+            pl.close()
+            per64[name] = {"ms": statistics.mean(ts), "p": p64, "tune_probe_err": e64}
+            ms64 += per64[name]["ms"]
+        fp64_form = {"value": total / (ms64 / 1e3), "unit": "points/s", "ms_per_step": ms64,
+                     "per_tiling": per64, "speedup_of_mixed": ms64 / ms,
+                     "note": "forests one after another, 2 timed steps each"}
     line = {
         "metric": "batched FMM points/s (4096 instances, eps=1e-6)", "value": total / (ms / 1e3),
         "unit": "points/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -848,6 +901,7 @@ def run_forest_batch(args):
         "e2e": {"value": total / statistics.mean(e2e), "unit": "points/s",
                 "h2d_bytes_per_step": int(sum(f["xy"].nbytes + f["u"].nbytes for f in forests.values())),
                 "d2h_bytes_per_step": int(8 * total)},
+        "fp64_form": fp64_form,
         "clocks": clk.summary(),
     }
     print(json.dumps(line))
@@ -882,6 +936,8 @@ def run_server_workload(args):
     (uxy, uu), (gxy, gu) = _pool(n_max, SEED + 41)
     tree = args.tree if args.tree != "auto" else ("adaptive" if args.workload == "serve" else "uniform")
     tree_flag = fmm2d.ADAPTIVE if tree == "adaptive" else 0
+    if args.serve_prec == "fp64":   # the plain FP64 GPU form for every request
+        tree_flag |= fmm2d.SERVE_PREC_AS_GIVEN | fmm2d.PREC_FP64
     names = ("quad", "sept", "tri")
     sv = fmm2d.Server(int(args.budget_gb * (1 << 30)), max_slots=args.slots)
     # untimed warm-up: every (tiling, eps) once per slot, so that module
@@ -927,6 +983,15 @@ def run_server_workload(args):
                             "latency_p50_ms": float(np.percentile(lat[m], 50)),
                             "latency_p99_ms": float(np.percentile(lat[m], 99))}
     points = int(sizes.sum())
+    # steady state or not: latency of the first, middle and last third of the
+    # requests in arrival order (a queue that grows shows rising thirds), and
+    # how long after the last arrival the last result came
+    thirds = []
+    for part in np.array_split(np.arange(count), 3):
+        if len(part):
+            thirds.append({"p50": float(np.percentile(lat[part], 50)),
+                           "p99": float(np.percentile(lat[part], 99))})
+    drain_s = (t1 - t0) - float(arrivals[-1])
     line = {
         "metric": ("batched FMM points/s (4096-instance config)" if args.workload == "batch"
                    else "served FMM requests: p50/p99 latency and points/s"),
@@ -936,11 +1001,15 @@ def run_server_workload(args):
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "max": float(lat.max())},
         "run_ms_mean": float(np.mean([r["run_ms"] for r in res])),
+        "latency_by_third_ms": thirds, "drain_after_last_arrival_s": drain_s,
+        "offered_points_per_s": points / max(1e-9, float(arrivals[-1])) if count > 1 else None,
         "by_eps": by_eps,
         "config": {"slots": args.slots, "hbm_budget_gb": args.budget_gb,
                    "sizes": "log-uniform [256, 65536]" if args.workload == "batch"
                    else "log-uniform [1e3, 2e6]",
-                   "eps": "1e-6" if args.workload == "batch" else "1e-4 (mixed form) / 1e-8 (hybrid form)",
+                   "eps": "1e-6" if args.workload == "batch" else (
+                       "1e-4 / 1e-8, plain FP64 form for both" if args.serve_prec == "fp64" else
+                       "1e-4 (mixed form) / 1e-8 (hybrid form)"),
                    "arrival_rate_per_s": None if args.workload == "batch" else args.rate,
                    "points": "uniform" if args.workload == "batch" else "uniform / 8-cluster mixture",
                    "tree": tree + (" (leaf size chosen by the server: quad 64, sept and tri 128)"
@@ -981,6 +1050,8 @@ def main():
                     help="batch: one forest per tiling, or one server request per instance")
     ap.add_argument("--leaf-size", type=int, default=64, help="batch/serve: adaptive leaf size")
     ap.add_argument("--dump", default="", help="batch/serve: write one JSON line per request here")
+    ap.add_argument("--serve-prec", default="auto", choices=["auto", "fp64"],
+                    help="serve: precision form chosen by the server, or the plain FP64 form")
     ap.add_argument("--tree", default="auto", choices=["auto", "uniform", "adaptive"],
                     help="batch/serve: tree of each request (auto: adaptive for serve)")
     args = ap.parse_args()

@@ -86,6 +86,15 @@ typedef enum {
                                      The paper refines uniformly (Sec. 2); this is the
                                      adaptive extension for non-uniform data (Sec. 9). */
 
+#define FMM2D_FIELD         0x80u /* the plan will also be evaluated with
+                                     fmm2d_evaluate_field: the FP32 forms then
+                                     keep the low parts of the points'
+                                     leaf-relative coordinates (needed for the
+                                     field's accurate pair differences) */
+/* Server requests only: take the FMM2D_PREC_* bits as given, including
+ * FMM2D_PREC_FP64 (value 0), instead of letting the server choose. */
+#define FMM2D_SERVE_PREC_AS_GIVEN 0x40u
+
 typedef struct fmm2d_plan fmm2d_plan;
 
 /* Plan description returned by fmm2d_plan_query. */
@@ -146,7 +155,7 @@ fmm2d_status fmm2d_default_params(int tiling, int64_t n_points, int leaf_target,
  *     choose it at fmm2d_build time with fmm2d_default_params (leaf target 64).
  *   p: highest expansion power 1..48, or 0 to derive it from eps.
  *   eps: requested relative tolerance (used when p == 0), 0 < eps < 1.
- *   flags: FMM2D_PREC_* | FMM2D_IN_F32.
+ *   flags: FMM2D_PREC_* | FMM2D_IN_F32 | FMM2D_ADAPTIVE | FMM2D_FIELD.
  * The domain defaults to the unit square [0,1)^2.  On success *out owns all
  * plan memory until fmm2d_plan_destroy.  Errors: FMM2D_EINVAL, FMM2D_ENOMEM.
  */
@@ -235,8 +244,10 @@ fmm2d_status fmm2d_evaluate(fmm2d_plan *plan, const void *strengths_dev, double 
  *   strengths_dev, potentials_dev: as fmm2d_evaluate.
  *   field_dev: 2 * n_tgt float64 outputs, (Re F_j, Im F_j) interleaved, in
  *     the caller's target order.
- * Asynchronous on `stream`.  Errors: as fmm2d_evaluate; FMM2D_EINVAL for a
- * null field pointer.
+ * FP32 forms (FMM2D_PREC_MIXED, FMM2D_PREC_MIXED_TC) need a plan created with
+ * FMM2D_FIELD.  Asynchronous on `stream`.  Errors: as fmm2d_evaluate;
+ * FMM2D_EINVAL for a null field pointer or an FP32-form plan created without
+ * FMM2D_FIELD.
  */
 fmm2d_status fmm2d_evaluate_field(fmm2d_plan *plan, const void *strengths_dev,
                                   double *potentials_dev, double *field_dev, void *stream);
@@ -291,6 +302,19 @@ fmm2d_status fmm2d_plan_set_profiling(fmm2d_plan *plan, int on);
 fmm2d_status fmm2d_stage_times(fmm2d_plan *plan, double *ms_host, int64_t *launches_host,
                                int cap, int *n_stages);
 
+/*
+ * fmm2d_plan_set_debug_stall - test switch of the bounded device waits (the
+ * paper has no counterpart).  When on, every CTA of the tensor-core M2L
+ * (FMM2D_PREC_MIXED_TC) makes its first operator wait on an mbarrier that
+ * nothing arrives on, before it issues any MMA: the wait gives up after about
+ * a second, the CTA lets its operator copies in flight land, frees its tensor
+ * memory and returns, and the evaluation's device_error (fmm2d_plan_query)
+ * is set; its results are then invalid.  The next evaluation with the switch
+ * off is normal (device_error is cleared at the start of each one).  Errors:
+ * FMM2D_EINVAL (null plan).
+ */
+fmm2d_status fmm2d_plan_set_debug_stall(fmm2d_plan *plan, int on);
+
 /* fmm2d_plan_destroy - free all plan memory (device and host).  NULL is a no-op. */
 void fmm2d_plan_destroy(fmm2d_plan *plan);
 
@@ -306,8 +330,11 @@ const char *fmm2d_last_error(const fmm2d_plan *plan);
  *   out[1]: MUFU log2 throughput, 1e9 results/s
  *   out[2]: FP64 FMA throughput, TFLOP/s
  *   out[3]: number of SMs
- * Runs three short kernels on the current device (legacy default stream) and
- * synchronises.  Errors: FMM2D_EINVAL, FMM2D_ENOMEM, FMM2D_ECUDA.
+ *   out[4]: TF32 tensor-core throughput (tcgen05.mma kind::tf32, FP32
+ *     accumulation), TFLOP/s
+ * out_host must hold 5 values.  Runs four short kernels on the current
+ * device (legacy default stream) and synchronises.  Errors: FMM2D_EINVAL,
+ * FMM2D_ENOMEM, FMM2D_ECUDA.
  */
 fmm2d_status fmm2d_measure_alu_peaks(double *out_host);
 
@@ -400,7 +427,9 @@ typedef struct {
                               levels = finest level, 0 = the default); with no
                               precision bit the server uses the tensor-core
                               mixed form for eps >= 1e-6, the hybrid form down
-                              to 1e-9 and the split form below */
+                              to 1e-9 and the split form below, unless
+                              FMM2D_SERVE_PREC_AS_GIVEN asks for the bits as
+                              they are (FMM2D_PREC_FP64: the plain FP64 form) */
   double eps;
   double domain[3];        /* x0, y0, S; S <= 0 means the unit square */
   const void *src_xy;      /* n_src interleaved points */

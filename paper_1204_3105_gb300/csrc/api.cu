@@ -464,6 +464,21 @@ void flush_events(fmm2d_plan *pl) {
   pl->ev_used = 0;
 }
 
+// Tensor-core M2L: how many CTAs share a tile's stencil entries, and the
+// partial-sum buffers that needs (after the far-cell count is known).
+static cudaError_t tc_prepare_split(fmm2d_plan *pl) {
+  pl->tc_split_n = 1;
+  if ((pl->flags & FMM2D_PREC_MASK) != FMM2D_PREC_MIXED_TC || pl->n_far_cells <= 0) return cudaSuccess;
+  const int S = tc_split(pl->n_far_cells, pl->sten.n_classes, pl->n_sms, pl->tc_K, pl->tc_N);
+  if (S > 1) {
+    cudaError_t e = dbuf_reserve(pl->d_tc_part_lb, (size_t)S * pl->n_far_cells * pl->P * sizeof(float2));
+    if (e == cudaSuccess) e = dbuf_reserve(pl->d_tc_part_L0, (size_t)S * pl->n_far_cells * sizeof(double));
+    if (e != cudaSuccess) return e;
+  }
+  pl->tc_split_n = S;
+  return cudaSuccess;
+}
+
 // The hybrid form's M2L: float-float on the FP32 pipes over the class lists.
 static cudaError_t run_m2l_ff(fmm2d_plan *pl, int L, int64_t far_first, const double *mQ,
                               const void *ma, double *lL0, void *lb, cudaStream_t f) {
@@ -698,7 +713,7 @@ fmm2d_status evaluate_t(fmm2d_plan *pl, const void *u, double *out, cudaStream_t
     StageScope sc(pl, ST_M2L, f, 1);
     CK(run_m2l_ff(pl, L, pl->lev_first[pl->l_min], mQ, ma, lL0, lb, f), "m2l_ff");
   } else if ((pl->flags & FMM2D_PREC_MASK) == FMM2D_PREC_MIXED_TC) {
-    StageScope sc(pl, ST_M2L, f, 1);
+    StageScope sc(pl, ST_M2L, f, pl->tc_split_n > 1 ? 2 : 1);
     TcArgs t;
     t.p = pl->p;
     t.P = pl->P;
@@ -722,6 +737,12 @@ fmm2d_status evaluate_t(fmm2d_plan *pl, const void *u, double *out, cudaStream_t
     t.lL0 = lL0;
     t.lb = (float2 *)lb;
     t.err = (int *)pl->d_dev_err.p;
+    t.split = pl->tc_split_n;
+    t.part_lb = (float2 *)pl->d_tc_part_lb.p;
+    t.part_L0 = (double *)pl->d_tc_part_L0.p;
+    t.n_far = pl->n_far_cells;
+    t.debug_stall = pl->debug_stall;
+    CK(cudaMemsetAsync(pl->d_dev_err.p, 0, 4, f), "memset");
     CK(launch_m2l_tc(t, pl->tc_K, pl->tc_N, pl->n_far_cells, f), "m2l_tc");
   } else {
     StageScope sc(pl, ST_M2L, f, 1);
@@ -966,11 +987,18 @@ static fmm2d_status build_adaptive(fmm2d_plan *pl, const void *src, int64_t n_sr
     CK(cudaMemcpyAsync(&n_leaves, pl->d_ad_tot.p, 4, cudaMemcpyDeviceToHost, s), "readback");
     CK(cudaStreamSynchronize(s), "leaves sync");
     pl->n_leaves_ad = n_leaves;
+    // FP32 forms of a field plan: also the low parts of the leaf-relative
+    // coordinates (the accurate pair differences of the field's P2P)
+    const bool keep_lo = !f64 && (pl->flags & FMM2D_FIELD);
+    if (keep_lo) {
+      CK(dbuf_reserve(pl->d_srclo, std::max<int64_t>(1, n_src) * 8), "alloc");
+      if (!pl->same_sets) CK(dbuf_reserve(pl->d_tgtlo, std::max<int64_t>(1, n_tgt) * 8), "alloc");
+    }
     CK(ad_launch_rel(f32, !f64, src, ps, n_leaves, (const int *)pl->d_leaf_ids.p, c.ss, c.se, c.ctr,
-                     pl->d_src4.p, 4, s), "rel");
+                     pl->d_src4.p, 4, s, keep_lo ? (float2 *)pl->d_srclo.p : nullptr), "rel");
     if (!pl->same_sets)
       CK(ad_launch_rel(f32, !f64, tgt, pt, n_leaves, (const int *)pl->d_leaf_ids.p, c.ts, c.te, c.ctr,
-                       pl->d_tgt2.p, 2, s), "rel");
+                       pl->d_tgt2.p, 2, s, keep_lo ? (float2 *)pl->d_tgtlo.p : nullptr), "rel");
     if (is_hybrid(pl)) {   // FP32 hi + lo copies for the P2P
       CK(dbuf_reserve(pl->d_src4f, std::max<int64_t>(1, n_src) * 16), "alloc");
       CK(dbuf_reserve(pl->d_srclo, std::max<int64_t>(1, n_src) * 8), "alloc");
@@ -1110,6 +1138,7 @@ static fmm2d_status build_adaptive(fmm2d_plan *pl, const void *src, int64_t n_sr
     CK(cudaMemcpyAsync(bin_h, pl->d_p2p_cnt.p, sizeof(bin_h), cudaMemcpyDeviceToHost, s), "readback");
   CK(cudaStreamSynchronize(s), "build sync");
   for (int k = 0; k < 4; ++k) pl->p2p_bin_count[k] = bin_h[k];
+  CK(tc_prepare_split(pl), "alloc");
   CK(cudaGetLastError(), "build");
   pl->n_m2l = -1;
   pl->n_p2p_pairs = -1;
@@ -1181,7 +1210,7 @@ fmm2d_status evaluate_adaptive_t(fmm2d_plan *pl, const void *u, double *out, cud
   if (pl->n_far_cells == 0) {
   } else if constexpr (sizeof(R) == 4) {
     if ((pl->flags & FMM2D_PREC_MASK) == FMM2D_PREC_MIXED_TC) {
-      StageScope sc(pl, ST_M2L, f, 1);
+      StageScope sc(pl, ST_M2L, f, pl->tc_split_n > 1 ? 2 : 1);
       TcArgs t;
       t.p = pl->p;
       t.P = pl->P;
@@ -1205,6 +1234,12 @@ fmm2d_status evaluate_adaptive_t(fmm2d_plan *pl, const void *u, double *out, cud
       t.lL0 = lL0;
       t.lb = (float2 *)lb;
       t.err = (int *)pl->d_dev_err.p;
+      t.split = pl->tc_split_n;
+      t.part_lb = (float2 *)pl->d_tc_part_lb.p;
+      t.part_L0 = (double *)pl->d_tc_part_L0.p;
+      t.n_far = pl->n_far_cells;
+      t.debug_stall = pl->debug_stall;
+      CK(cudaMemsetAsync(pl->d_dev_err.p, 0, 4, f), "memset");
       CK(launch_m2l_tc(t, pl->tc_K, pl->tc_N, pl->n_far_cells, f), "m2l_tc");
     } else {
       StageScope sc(pl, ST_M2L, f, 1);
@@ -1321,10 +1356,14 @@ fmm2d_status field_t(fmm2d_plan *pl, double *field, cudaStream_t s) {
     a.inv_s_im = inv_s.imag();
   }
   StageScope sc(pl, ST_FIELD, s, ad ? 3 : 2);
+  // FP32 forms: the low parts of the coordinates give accurate differences
+  const float2 *slo = sizeof(R) == 4 ? (const float2 *)pl->d_srclo.p : nullptr;
+  const float2 *tlo = sizeof(R) == 4 ? (const float2 *)(pl->same_sets ? pl->d_srclo.p : pl->d_tgtlo.p)
+                                     : nullptr;
   if (ad) {
     CK(launch_p2p_field<R>(0, pl->n_leaves_ad, a.leaf_ids, src4, tgt, tstride, ss, se, ts, te,
                            nullptr, (const int *)pl->d_u_off.p, (const int *)pl->d_u_src.p, ctr,
-                           fnear, s), "p2p field");
+                           fnear, s, slo, tlo), "p2p field");
     CK(launch_m2p_field<R>(pl->n_leaves_ad, a.leaf_ids, (const int *)pl->d_w_off.p,
                            (const int *)pl->d_w_src.p, tgt, tstride, ts, te, ctr, a.cell_lev,
                            (const double2 *)pl->d_ad_scale.p, pl->p, pl->P,
@@ -1333,7 +1372,7 @@ fmm2d_status field_t(fmm2d_plan *pl, double *field, cudaStream_t s) {
   } else {
     CK(launch_p2p_field<R>(a.leaf_first, a.n_leaves, nullptr, src4, tgt, tstride, ss, se, ts, te,
                            (const int *)pl->d_near_cnt.p, nullptr, (const int *)pl->d_near_src.p,
-                           ctr, fnear, s), "p2p field");
+                           ctr, fnear, s, slo, tlo), "p2p field");
   }
   CK(launch_l2p_field<R>(a, tgt, tstride, ts, te, tperm, (const Cx<R> *)pl->d_lb.p, fnear,
                          (double2 *)field, s), "l2p field");
@@ -1346,6 +1385,8 @@ fmm2d_status fmm2d_evaluate_field(fmm2d_plan *pl, const void *u, double *out, do
                                   void *stream) {
   if (!pl) return FMM2D_EINVAL;
   if (pl->built && pl->n_tgt > 0 && !field) return fail(pl, FMM2D_EINVAL, "null field pointer");
+  if (!is_fp64(pl) && !(pl->flags & FMM2D_FIELD))
+    return fail(pl, FMM2D_EINVAL, "FP32 forms need a plan created with FMM2D_FIELD");
   const fmm2d_status st = fmm2d_evaluate(pl, u, out, stream);
   if (st != FMM2D_OK || pl->n_tgt == 0) return st;
   cudaStream_t s = (cudaStream_t)stream;
@@ -1378,7 +1419,7 @@ fmm2d_status fmm2d_plan_create(int tiling, int levels, int p, double eps, unsign
   if (levels < 0 || levels > max_levels_for(tiling, flags)) { g_create_err = "levels out of range"; return FMM2D_EINVAL; }
   if (p < 0 || p > MAXP) { g_create_err = "p out of range (0..48)"; return FMM2D_EINVAL; }
   if (p == 0 && !(eps > 0.0 && eps < 1.0)) { g_create_err = "eps must be in (0, 1)"; return FMM2D_EINVAL; }
-  if ((flags & ~(FMM2D_PREC_MASK | FMM2D_IN_F32 | FMM2D_ADAPTIVE)) != 0 ||
+  if ((flags & ~(FMM2D_PREC_MASK | FMM2D_IN_F32 | FMM2D_ADAPTIVE | FMM2D_FIELD)) != 0 ||
       (flags & FMM2D_PREC_MASK) > FMM2D_PREC_SPLIT) {
     g_create_err = "unknown flags";
     return FMM2D_EINVAL;
@@ -1563,13 +1604,21 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
   }
   {
     StageScope sc(pl, ST_TREE, s, pl->same_sets ? 1 : 2);
+    // FP32 forms of a field plan: also the low parts of the leaf-relative
+    // coordinates (the accurate pair differences of the field's P2P)
+    const bool keep_lo = !f64 && (pl->flags & FMM2D_FIELD);
+    if (keep_lo) {
+      CK(dbuf_reserve(pl->d_srclo, std::max<int64_t>(1, n_src) * 8), "alloc");
+      if (!pl->same_sets) CK(dbuf_reserve(pl->d_tgtlo, std::max<int64_t>(1, n_tgt) * 8), "alloc");
+    }
     CK(launch_rel_coords(g, f32, !f64, src, ps, ks, n_src, (const int *)pl->d_map.p,
                          (const double2 *)pl->d_cell_ctr.p, pl->d_src4.p, 4, (int *)pl->d_src_start.p,
-                         (int *)pl->d_src_end.p, s), "rel");
+                         (int *)pl->d_src_end.p, s, keep_lo ? (float2 *)pl->d_srclo.p : nullptr), "rel");
     if (!pl->same_sets)
       CK(launch_rel_coords(g, f32, !f64, tgt, pt, kt, n_tgt, (const int *)pl->d_map.p,
                            (const double2 *)pl->d_cell_ctr.p, pl->d_tgt2.p, 2,
-                           (int *)pl->d_tgt_start.p, (int *)pl->d_tgt_end.p, s), "rel");
+                           (int *)pl->d_tgt_start.p, (int *)pl->d_tgt_end.p, s,
+                           keep_lo ? (float2 *)pl->d_tgtlo.p : nullptr), "rel");
     if (is_hybrid(pl)) {   // FP32 hi + lo copies for the P2P
       CK(dbuf_reserve(pl->d_src4f, std::max<int64_t>(1, n_src) * 16), "alloc");
       CK(dbuf_reserve(pl->d_srclo, std::max<int64_t>(1, n_src) * 8), "alloc");
@@ -1614,6 +1663,7 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
   for (int l = L + 1; l <= MAXLEV + 1; ++l) pl->lev_first[l] = pl->n_cells;
   const int64_t lfirst = L >= pl->l_min ? pl->lev_first[pl->l_min] : pl->n_cells;
   pl->n_far_cells = pl->n_cells - lfirst;
+  CK(tc_prepare_split(pl), "alloc");
   CK(cudaGetLastError(), "build");
   pl->n_m2l = -1;
   pl->n_p2p_pairs = -1;
@@ -1931,6 +1981,12 @@ fmm2d_status fmm2d_debug_export(fmm2d_plan *pl, int what, int level, void *host_
   return FMM2D_OK;
 }
 
+fmm2d_status fmm2d_plan_set_debug_stall(fmm2d_plan *pl, int on) {
+  if (!pl) return FMM2D_EINVAL;
+  pl->debug_stall = on ? 1 : 0;
+  return FMM2D_OK;
+}
+
 fmm2d_status fmm2d_plan_set_profiling(fmm2d_plan *pl, int on) {
   if (!pl) return FMM2D_EINVAL;
   flush_events(pl);
@@ -1964,7 +2020,7 @@ void fmm2d_plan_destroy(fmm2d_plan *pl) {
                   &pl->d_tgt_start, &pl->d_tgt_end, &pl->d_lev_first, &pl->d_far_cnt,
                   &pl->d_far_src, &pl->d_far_op, &pl->d_near_cnt, &pl->d_near_src, &pl->d_src4,
                   &pl->d_tgt2, &pl->d_mQ, &pl->d_ma, &pl->d_ma_ff, &pl->d_lL0, &pl->d_lb, &pl->d_phi_near,
-                  &pl->d_fnear,
+                  &pl->d_fnear, &pl->d_tc_part_lb, &pl->d_tc_part_L0,
                   &pl->d_phi_far, &pl->d_sten, &pl->d_geo_scale, &pl->d_m2l_ops, &pl->d_m2l_logz,
                   &pl->d_m2m_ops, &pl->d_l2l_ops, &pl->d_counts, &pl->d_far_full,
                   &pl->d_cls_cnt, &pl->d_cls_cells, &pl->d_tc_ops, &pl->d_ff_ops, &pl->d_ff_ph, &pl->d_dev_err,

@@ -72,6 +72,51 @@ __device__ __forceinline__ void field_leaf(const typename FieldT<R>::V4 *__restr
   }
 }
 
+// FP32 forms with the low parts of the leaf-relative coordinates: the pair
+// differences are formed accurately.  A field term u / r has the absolute
+// sensitivity u / r^2 to a coordinate error, so an FP32 coordinate rounded
+// once (an error of half an ulp of the leaf size) would spoil close pairs.
+// The target, shifted into the source leaf's frame by TwoSum (A_hi + A_lo),
+// minus the source (s_hi + s_lo) is (A_hi - s_hi) + (A_lo - s_lo): the first
+// difference is exact for close points (Sterbenz), so dx is the FP32
+// rounding of the true difference and each term has FP32 relative accuracy.
+__device__ __forceinline__ void ff_shift(float t_hi, float t_lo, double d, float &a_hi, float &a_lo) {
+  const float dh = (float)d, dl = (float)(d - (double)dh);
+  const float s = t_hi - dh;
+  const float bp = s - t_hi;                    // TwoSum of t_hi and -dh
+  const float err = (t_hi - (s - bp)) + (-dh - bp);
+  a_hi = s;
+  a_lo = err + (t_lo - dl);
+}
+
+__device__ __forceinline__ void field_leaf_acc(const float4 *__restrict__ sp,
+                                               const float2 *__restrict__ sl, int n, float ax,
+                                               float axl, float ay, float ayl, float bx, float bxl,
+                                               float by, float byl, float (&fa)[4], float (&fb)[4]) {
+  using T = FieldT<float>;
+  for (int i = 0; i < n; i += 64) {
+    const int m = min(n - i, 64);
+    float xa = 0, ya = 0, xb = 0, yb = 0;
+#pragma unroll 2
+    for (int j = 0; j < m; ++j) {
+      const float4 v = sp[i + j];
+      const float2 w = sl[i + j];
+      const float dxa = (ax - v.x) + (axl - w.x), dya = (ay - v.y) + (ayl - w.y);
+      const float dxb = (bx - v.x) + (bxl - w.x), dyb = (by - v.y) + (byl - w.y);
+      const float ia = T::rcp(fmaf(dxa, dxa, fmaf(dya, dya, T::floor_r2)));
+      const float ib = T::rcp(fmaf(dxb, dxb, fmaf(dyb, dyb, T::floor_r2)));
+      xa = fmaf(v.z * dxa, ia, xa);
+      ya = fmaf(v.z * dya, ia, ya);
+      xb = fmaf(v.z * dxb, ib, xb);
+      yb = fmaf(v.z * dyb, ib, yb);
+    }
+    f_kahan(fa[0], fa[1], xa);
+    f_kahan(fa[2], fa[3], ya);
+    f_kahan(fb[0], fb[1], xb);
+    f_kahan(fb[2], fb[3], yb);
+  }
+}
+
 // P2P': one warp per target leaf, two targets per lane; the warp streams the
 // sources of every Near leaf with broadcast loads.  u / (y - x) =
 // u (dx - i dy) / r^2.  Writes fnear[j] (sorted target order).
@@ -82,7 +127,8 @@ k_p2p_field(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_i
             const int *__restrict__ sst, const int *__restrict__ sen, const int *__restrict__ tst,
             const int *__restrict__ ten, const int *__restrict__ near_cnt,
             const int *__restrict__ near_off, const int *__restrict__ near_src,
-            const double2 *__restrict__ ctr, double2 *__restrict__ fnear) {
+            const double2 *__restrict__ ctr, double2 *__restrict__ fnear,
+            const float2 *__restrict__ src_lo, const float2 *__restrict__ tgt_lo) {
   using T = FieldT<R>;
   const int lane = threadIdx.x & 31;
   const int64_t li = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -100,12 +146,30 @@ k_p2p_field(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_i
     const R ax0 = tgt[(int64_t)ja * tstride], ay0 = tgt[(int64_t)ja * tstride + 1];
     const R bx0 = tgt[(int64_t)jb * tstride], by0 = tgt[(int64_t)jb * tstride + 1];
     R fa[4] = {0, 0, 0, 0}, fb[4] = {0, 0, 0, 0};   // (x sum, comp, y sum, comp)
-    for (int e = 0; e < nn; ++e) {
-      const int s = nsrc[e];
-      const int s0 = sst[s], cnt = sen[s] - s0;
-      const double2 cs = ctr[s];
-      const R dcx = (R)(cs.x - cg.x), dcy = (R)(cs.y - cg.y);
-      field_leaf<R>(src + s0, cnt, ax0 - dcx, ay0 - dcy, bx0 - dcx, by0 - dcy, fa, fb);
+    if constexpr (sizeof(R) == 4) {
+      if (src_lo) {   // accurate differences from the hi + lo coordinates
+        const float2 la = tgt_lo[ja], lb = tgt_lo[jb];
+        for (int e = 0; e < nn; ++e) {
+          const int s = nsrc[e];
+          const int s0 = sst[s], cnt = sen[s] - s0;
+          const double2 cs = ctr[s];
+          float axh, axl, ayh, ayl, bxh, bxl, byh, byl;
+          ff_shift(ax0, la.x, cs.x - cg.x, axh, axl);
+          ff_shift(ay0, la.y, cs.y - cg.y, ayh, ayl);
+          ff_shift(bx0, lb.x, cs.x - cg.x, bxh, bxl);
+          ff_shift(by0, lb.y, cs.y - cg.y, byh, byl);
+          field_leaf_acc(src + s0, src_lo + s0, cnt, axh, axl, ayh, ayl, bxh, bxl, byh, byl, fa, fb);
+        }
+      }
+    }
+    if (sizeof(R) == 8 || !src_lo) {
+      for (int e = 0; e < nn; ++e) {
+        const int s = nsrc[e];
+        const int s0 = sst[s], cnt = sen[s] - s0;
+        const double2 cs = ctr[s];
+        const R dcx = (R)(cs.x - cg.x), dcy = (R)(cs.y - cg.y);
+        field_leaf<R>(src + s0, cnt, ax0 - dcx, ay0 - dcy, bx0 - dcx, by0 - dcy, fa, fb);
+      }
     }
     if (ia < te)
       fnear[ia] = make_double2((double)fa[0] - (double)fa[1], -((double)fa[2] - (double)fa[3]));
@@ -209,12 +273,13 @@ cudaError_t launch_p2p_field(int64_t leaf_first, int64_t n_leaves, const int *le
                              const R *src4, const R *tgt, int tstride, const int *src_start,
                              const int *src_end, const int *tgt_start, const int *tgt_end,
                              const int *near_cnt, const int *near_off, const int *near_src,
-                             const double2 *ctr, double2 *fnear, cudaStream_t s) {
+                             const double2 *ctr, double2 *fnear, cudaStream_t s,
+                             const float2 *src_lo, const float2 *tgt_lo) {
   if (n_leaves <= 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((n_leaves * 32 + FTH - 1) / FTH);
   k_p2p_field<R><<<blocks, FTH, 0, s>>>(leaf_first, n_leaves, leaf_ids, src4, tgt, tstride,
                                          src_start, src_end, tgt_start, tgt_end, near_cnt,
-                                         near_off, near_src, ctr, fnear);
+                                         near_off, near_src, ctr, fnear, src_lo, tgt_lo);
   return cudaGetLastError();
 }
 
@@ -244,7 +309,8 @@ cudaError_t launch_l2p_field(const ExpandArgs &a, const R *tgt, int tstride, con
   template cudaError_t launch_p2p_field<R>(int64_t, int64_t, const int *, const R *, const R *,    \
                                            int, const int *, const int *, const int *, const int *, \
                                            const int *, const int *, const int *, const double2 *, \
-                                           double2 *, cudaStream_t);                               \
+                                           double2 *, cudaStream_t, const float2 *,                \
+                                           const float2 *);                                        \
   template cudaError_t launch_m2p_field<R>(int64_t, const int *, const int *, const int *,         \
                                            const R *, int, const int *, const int *,               \
                                            const double2 *, const uint8_t *, const double2 *, int, \

@@ -171,11 +171,12 @@ __global__ void __launch_bounds__(TC_THREADS, (TcShape<K, N>::CTAS)) k_m2l_tc(Tc
   constexpr uint32_t ACC = SH::ACC, COLS = SH::COLS;
   constexpr int QH = K / 8;                 // 16-byte chunks of a row per half
   // layout: A stages [2] x (A0, A1), operator stages [NB] x (B0, B1, B2), then
-  // barriers: mma[2] (A stage released), full[NB] (operator landed)
+  // barriers: mma[2] (A stage released), full[NB] (operator landed), and one
+  // that nothing arrives on (the test switch a.debug_stall waits on it)
   unsigned char *const Bbase = smem + 2 * (2 * A_BYTES);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SH::SMEM);
-  uint64_t *mma_bar = bars, *full_bar = bars + 2;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 + NB);
+  uint64_t *mma_bar = bars, *full_bar = bars + 2, *never_bar = bars + 2 + NB;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 3 + NB);
   int *s_cnt = reinterpret_cast<int *>(tmem_slot + 2);               // [MAX_CLASSES]
   volatile int *s_abort = s_cnt + MAX_CLASSES;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(TC_THREADS, (TcShape<K, N>::CTAS)) k_m2l_tc(Tc
 
   if (warp == 0) tmem_alloc(tmem_slot, COLS);
   if (tid == 0) {
-    for (int i = 0; i < 2 + NB; ++i) mbar_init(&bars[i], 1);
+    for (int i = 0; i < 3 + NB; ++i) mbar_init(&bars[i], 1);
     fence_barrier_init();
     *s_abort = 0;
   }
@@ -194,9 +195,11 @@ __global__ void __launch_bounds__(TC_THREADS, (TcShape<K, N>::CTAS)) k_m2l_tc(Tc
   const uint32_t tmem = *tmem_slot;
   int total_tiles = 0;
   for (int c = 0; c < a.n_classes; ++c) total_tiles += (s_cnt[c] + TC_M - 1) / TC_M;
+  const int S = a.split;                    // work item = (tile, part of its entries)
 
   uint32_t it = 0;                          // entries processed so far (global over tiles)
   uint32_t issued = 0;                      // operator copies issued (thread 0)
+  uint32_t landed = 0;                      // operator copies waited for (thread 0)
   const int p = a.p;
   // thread 0: issue the operator copy of global entry u into stage u % NB
   auto issue_b = [&](uint32_t u, int op) {
@@ -206,7 +209,8 @@ __global__ void __launch_bounds__(TC_THREADS, (TcShape<K, N>::CTAS)) k_m2l_tc(Tc
     bulk_g2s(B0, a.btab + (size_t)op * 3 * B_BYTES, 3 * B_BYTES, &full_bar[st]);
     issued = u + 1;
   };
-  for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+  for (int item = blockIdx.x; item < total_tiles * S; item += gridDim.x) {
+    const int tile = item / S, sidx = item - tile * S;
     int c = 0, t0 = tile;
     while (t0 >= (s_cnt[c] + TC_M - 1) / TC_M) {
       t0 -= (s_cnt[c] + TC_M - 1) / TC_M;
@@ -223,9 +227,13 @@ __global__ void __launch_bounds__(TC_THREADS, (TcShape<K, N>::CTAS)) k_m2l_tc(Tc
       ls = a.log_abs_scale[l];
     }
     double L0 = 0.0;
-    const int E = a.sten_len[c];
-    const uint16_t *ops_c = a.sten_ops + c * FAR_MAX;
-    const int *srcs = a.far_full + fi * FAR_MAX;
+    // this item's stencil entries: [e_lo, e_lo + E) of the class's list
+    const int E_all = a.sten_len[c];
+    const int chunk = (E_all + S - 1) / S;
+    const int e_lo = min(E_all, sidx * chunk);
+    const int E = min(E_all, e_lo + chunk) - e_lo;
+    const uint16_t *ops_c = a.sten_ops + c * FAR_MAX + e_lo;
+    const int *srcs = a.far_full + fi * FAR_MAX + e_lo;
     // software pipeline of the gather: the rows of entry e+1 are loaded while
     // entry e is split, stored and multiplied; source indices two ahead
     auto load_row = [&](int src, float4 (&f)[QH], double &q) {
@@ -237,7 +245,7 @@ __global__ void __launch_bounds__(TC_THREADS, (TcShape<K, N>::CTAS)) k_m2l_tc(Tc
       }
       q = src >= 0 ? a.mQ[src] : 0.0;
     };
-    int src = g >= 0 ? srcs[0] : -1;
+    int src = (g >= 0 && E > 0) ? srcs[0] : -1;
     int src_n = (g >= 0 && E > 1) ? srcs[1] : -1;
     float4 fc[QH];
     double qc;
@@ -288,9 +296,13 @@ __global__ void __launch_bounds__(TC_THREADS, (TcShape<K, N>::CTAS)) k_m2l_tc(Tc
       if (*s_abort) break;
       if (tid == 0) {
         const int bs = it % NB;
-        if (!mbar_wait(&full_bar[bs], (it / NB) & 1)) {
+        // test switch: the CTA's first operator wait is on a barrier that
+        // nothing arrives on, so its bounded wait runs out before any MMA
+        const bool stall = a.debug_stall && it == 0;
+        if (stall ? !mbar_wait(never_bar, 0) : !mbar_wait(&full_bar[bs], (it / NB) & 1)) {
           *s_abort = 1;
         } else {
+          landed = it + 1;
           tc_fence_after();
           const uint32_t a0 = smem_u32(A0), a1 = a0 + A_BYTES;
           const uint32_t b0 = smem_u32(Bbase + bs * (3 * B_BYTES)), b1 = b0 + B_BYTES, b2 = b1 + B_BYTES;
@@ -317,7 +329,7 @@ __global__ void __launch_bounds__(TC_THREADS, (TcShape<K, N>::CTAS)) k_m2l_tc(Tc
     __syncthreads();
     if (*s_abort) break;
     // wait for the last commit of this tile, then read the accumulators
-    {
+    if (E > 0) {
       const uint32_t last = it - 1;
       if (!mbar_wait(&mma_bar[last & 1], (last >> 1) & 1)) *s_abort = 1;
     }
@@ -346,12 +358,20 @@ __global__ void __launch_bounds__(TC_THREADS, (TcShape<K, N>::CTAS)) k_m2l_tc(Tc
           d[i] = t;
         }
       }
-      if (g >= 0) {
+      if (g >= 0 && S == 1) {
         if (q == 0) a.lL0[g] = L0 + (double)d[0];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int l = 8 * q + i;
           if (l >= 1 && l <= p) a.lb[(int64_t)g * a.P + l - 1] = make_float2(d[2 * i], d[2 * i + 1]);
+        }
+      } else if (g >= 0) {   // this part's sums, added up by k_m2l_tc_reduce
+        const int64_t pr = (int64_t)sidx * a.n_far + fi;
+        if (q == 0) a.part_L0[pr] = L0 + (double)d[0];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int l = 8 * q + i;
+          if (l >= 1 && l <= p) a.part_lb[pr * a.P + l - 1] = make_float2(d[2 * i], d[2 * i + 1]);
         }
       }
     }
@@ -362,8 +382,8 @@ __global__ void __launch_bounds__(TC_THREADS, (TcShape<K, N>::CTAS)) k_m2l_tc(Tc
     if (tid == 0) {
       atomicOr(a.err, 1);
       // let the operator copies in flight land before the CTA exits: the
-      // copies of entries it .. issued-1 were not waited on
-      for (uint32_t u = it; u < issued; ++u) mbar_wait(&full_bar[u % NB], (u / NB) & 1);
+      // copies of entries landed .. issued-1 were not waited for
+      for (uint32_t u = landed; u < issued; ++u) mbar_wait(&full_bar[u % NB], (u / NB) & 1);
     }
   } else if (it > 0 && tid == 0) {
     const uint32_t last = it - 1;
@@ -375,17 +395,50 @@ __global__ void __launch_bounds__(TC_THREADS, (TcShape<K, N>::CTAS)) k_m2l_tc(Tc
   if (warp == 0) tmem_dealloc(tmem, COLS);
 }
 
+// Sum of the split parts of every far cell, in part order (FP64, rounded once).
+__global__ void k_m2l_tc_reduce(int split, int64_t n_far, int64_t far_first, int p, int P,
+                                const float2 *__restrict__ part_lb,
+                                const double *__restrict__ part_L0, double *__restrict__ lL0,
+                                float2 *__restrict__ lb) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // (cell, column)
+  const int64_t fi = i / (p + 1);
+  const int l = (int)(i - fi * (p + 1));
+  if (fi >= n_far) return;
+  const int64_t g = far_first + fi;
+  if (l == 0) {
+    double v = 0.0;
+    for (int sp = 0; sp < split; ++sp) v += part_L0[(int64_t)sp * n_far + fi];
+    lL0[g] = v;
+  } else {
+    double re = 0.0, im = 0.0;
+    for (int sp = 0; sp < split; ++sp) {
+      const float2 v = part_lb[((int64_t)sp * n_far + fi) * P + l - 1];
+      re += (double)v.x;
+      im += (double)v.y;
+    }
+    lb[g * P + l - 1] = make_float2((float)re, (float)im);
+  }
+}
+
 template <int K, int N>
 cudaError_t launch_tc(const TcArgs &a, int64_t n_far_cells, cudaStream_t s) {
   using SH = TcShape<K, N>;
-  const size_t smem = SH::SMEM + (2 + SH::NB) * 8 + 8 + (MAX_CLASSES + 1) * 4 + 16;
+  const size_t smem = SH::SMEM + (3 + SH::NB) * 8 + 8 + (MAX_CLASSES + 1) * 4 + 16;
   cudaError_t e = cudaFuncSetAttribute(k_m2l_tc<K, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  int64_t tiles = (n_far_cells + TC_M - 1) / TC_M + a.n_classes;
-  int grid = (int)std::min<int64_t>(tiles, (int64_t)a.sms * SH::CTAS);
+  const int S = a.split > 1 && a.part_lb && a.part_L0 ? a.split : 1;
+  TcArgs b = a;
+  b.split = S;
+  int64_t items = ((n_far_cells + TC_M - 1) / TC_M + a.n_classes) * S;
+  int grid = (int)std::min<int64_t>(items, (int64_t)a.sms * SH::CTAS);
   if (grid < 1) return cudaSuccess;
-  k_m2l_tc<K, N><<<grid, TC_THREADS, smem, s>>>(a);
+  k_m2l_tc<K, N><<<grid, TC_THREADS, smem, s>>>(b);
+  if (S > 1) {
+    const int64_t work = n_far_cells * (a.p + 1);
+    k_m2l_tc_reduce<<<(unsigned)((work + 255) / 256), 256, 0, s>>>(
+        S, a.n_far, a.far_first, a.p, a.P, a.part_lb, a.part_L0, a.lL0, a.lb);
+  }
   return cudaGetLastError();
 }
 
@@ -397,7 +450,94 @@ uint32_t tf32_round_host(float x) {
   return u;
 }
 
+// TF32 tensor-core throughput probe: one CTA per SM, one thread issuing
+// `reps` back-to-back tcgen05.mma of M = 128, N = 256, K = 8 (TF32 in, FP32
+// accumulate in TMEM) from fixed shared-memory operands; the commit of the
+// last one is waited on (bounded) before TMEM is freed.
+constexpr int PK_N = 256;
+__global__ void __launch_bounds__(128, 1) k_tf32_peak(int reps, int *err) {
+  __shared__ __align__(1024) unsigned char sm[TC_M * 32 + PK_N * 32];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t slot;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < (TC_M * 32 + PK_N * 32) / 4; i += blockDim.x)
+    reinterpret_cast<float *>(sm)[i] = 0.f;
+  if (tid < 32) tmem_alloc(&slot, PK_N);
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = slot;
+  if (tid == 0) {
+    constexpr uint32_t IDESC = idesc_tf32(TC_M, PK_N);
+    const uint32_t a = smem_u32(sm), b = a + TC_M * 32;
+    const uint64_t da = sdesc(a, 128, 256), db = sdesc(b, 128, 256);
+    for (int r = 0; r < reps; ++r) mma_tf32(tmem, da, db, IDESC, r > 0 ? 1u : 0u);
+    mma_commit(&bar);
+    if (!mbar_wait(&bar, 0)) atomicOr(err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (tid < 32) tmem_dealloc(tmem, PK_N);
+}
+
 }  // namespace
+
+cudaError_t tc_measure_tf32(double *tflops) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  int *err = nullptr;
+  if ((e = cudaMalloc(&err, sizeof(int))) != cudaSuccess) return e;
+  cudaMemset(err, 0, sizeof(int));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int reps = 8192;
+  // a large dynamic shared-memory request keeps it to one CTA per SM
+  const int pad = 150 * 1024;
+  e = cudaFuncSetAttribute(k_tf32_peak, cudaFuncAttributeMaxDynamicSharedMemorySize, pad);
+  if (e != cudaSuccess) {
+    cudaFree(err);
+    return e;
+  }
+  k_tf32_peak<<<sms, 128, pad>>>(64, err);   // warm-up
+  cudaEventRecord(e0);
+  k_tf32_peak<<<sms, 128, pad>>>(reps, err);
+  cudaEventRecord(e1);
+  e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  int err_h = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&err_h, err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(err);
+  if (e != cudaSuccess) return e;
+  if (err_h) return cudaErrorLaunchTimeout;
+  *tflops = 2.0 * TC_M * PK_N * 8 * (double)reps * sms / (ms * 1e-3) * 1e-12;
+  return cudaSuccess;
+}
+
+int tc_split(int64_t n_far_cells, int n_classes, int sms, int K, int N) {
+  // Split only a grid that would leave more than half the CTA slots idle
+  // (measured on 2^20 points: the septree's 76 tiles on 152 SMs ran 1.4x
+  // faster split four ways; the quadtree's 175 and the triangle tiling's 293
+  // tiles ran slower split, paying the extra epilogues and the reduction).
+  const int ctas = N <= 32 ? 2 : 1;                 // TcShape<K, N>::CTAS
+  const int64_t slots = (int64_t)sms * ctas;
+  const int64_t tiles = (n_far_cells + TC_M - 1) / TC_M + n_classes;
+  (void)K;
+  if (2 * tiles > slots) return 1;
+  return (int)std::min<int64_t>(4, (2 * slots + tiles - 1) / tiles);
+}
 
 bool tc_shape(int p, int *K, int *N) {
   if (p <= 15) { *K = 32; *N = 32; return true; }

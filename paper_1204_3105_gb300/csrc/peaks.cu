@@ -96,5 +96,9 @@ extern "C" fmm2d_status fmm2d_measure_alu_peaks(double *out) {
   out[1] = threads * PK_ITERS * 8 / t_lg2 * 1e-9;               // lg2 Gop/s
   out[2] = threads * (PK_ITERS / 8) * 4 * 2.0 / t_dfma * 1e-12; // FP64 TFLOP/s
   out[3] = (double)sms;
+  double tf32 = 0.0;
+  const cudaError_t te = tc_measure_tf32(&tf32);   // tcgen05 kind::tf32, FP32 accumulate
+  if (te != cudaSuccess) return FMM2D_ECUDA;
+  out[4] = tf32;
   return FMM2D_OK;
 }

@@ -95,6 +95,9 @@ struct Plan {
   DBuf d_m2l_ops, d_m2l_logz, d_m2m_ops, d_l2l_ops;   // element type per precision
   DBuf d_counts;
   DBuf d_far_full, d_cls_cnt, d_cls_cells, d_tc_ops, d_ff_ops, d_ff_ph, d_ma_ff, d_dev_err;
+  DBuf d_tc_part_lb, d_tc_part_L0;     // tensor-core M2L: partial locals of split tiles
+  int tc_split_n = 1;
+  int debug_stall = 0;                // test switch: M2L CTAs time out before their MMAs
   DBuf d_p2p_order, d_p2p_cnt;        // adaptive tree: P2P leaf size classes
   int tc_K = 0, tc_N = 0, n_sms = 148;
   int64_t cls_cap = 1;
@@ -305,8 +308,21 @@ struct TcArgs {
   double *lL0;
   float2 *lb;
   int *err;
+  // stencil entries of a tile split over `split` CTAs (split > 1): partial
+  // locals [split][far cell][P] and partial L_0 [split][far cell], summed in
+  // split order by a second kernel
+  int split = 1;
+  float2 *part_lb = nullptr;
+  double *part_L0 = nullptr;
+  int64_t n_far = 0;
+  int debug_stall = 0;                // test switch (fmm2d_plan_set_debug_stall)
 };
 bool tc_shape(int p, int *K, int *N);
+// CTAs over which the stencil entries of one tile are split, for a level
+// range with n_far_cells M2L targets (fills the SMs about twice).
+int tc_split(int64_t n_far_cells, int n_classes, int sms, int K, int N);
+// Measured TF32 tensor-core throughput (TFLOP/s) of this device.
+cudaError_t tc_measure_tf32(double *tflops);
 // B tables (hi/lo TF32 splits of the real-ified operators) for all operators.
 void tc_build_tables(const std::vector<double> &m2l_re, const std::vector<double> &m2l_im,
                      int n_ops, int p, int K, int N, std::vector<uint32_t> &out);
@@ -369,7 +385,8 @@ cudaError_t launch_p2p_field(int64_t leaf_first, int64_t n_leaves, const int *le
                              const R *src4, const R *tgt, int tstride, const int *src_start,
                              const int *src_end, const int *tgt_start, const int *tgt_end,
                              const int *near_cnt, const int *near_off, const int *near_src,
-                             const double2 *ctr, double2 *fnear, cudaStream_t s);
+                             const double2 *ctr, double2 *fnear, cudaStream_t s,
+                             const float2 *src_lo = nullptr, const float2 *tgt_lo = nullptr);
 template <typename R>
 cudaError_t launch_m2p_field(int64_t n_leaves, const int *leaf_ids, const int *w_off,
                              const int *w_src, const R *tgt, int tstride, const int *ts,

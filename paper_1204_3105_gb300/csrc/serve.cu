@@ -155,7 +155,9 @@ fmm2d_status slot_plan(Slot &sl, const fmm2d_request &r, int64_t n_points, fmm2d
                        unsigned *flags_out) {
   int p = r.p;
   if (p == 0) fmm2d_default_params(r.tiling, n_points, 64, r.eps, nullptr, &p, nullptr);
-  const unsigned prec = (r.flags & FMM2D_PREC_MASK) ? (r.flags & FMM2D_PREC_MASK) : precision_for(r.eps, p);
+  const unsigned prec = ((r.flags & FMM2D_PREC_MASK) || (r.flags & FMM2D_SERVE_PREC_AS_GIVEN))
+                            ? (r.flags & FMM2D_PREC_MASK)
+                            : precision_for(r.eps, p);
   const unsigned flags = prec | (r.flags & (FMM2D_IN_F32 | FMM2D_ADAPTIVE));
   int L = r.levels;
   if (L == 0 && !(flags & FMM2D_ADAPTIVE))

@@ -20,6 +20,8 @@ TILINGS = {"quad": QUAD, "sept": SEPT, "tri": TRI}
 PREC_FP64, PREC_MIXED, PREC_MIXED_TC, PREC_HYBRID, PREC_SPLIT = 0x0, 0x1, 0x2, 0x3, 0x4
 IN_F32 = 0x10
 ADAPTIVE = 0x20
+SERVE_PREC_AS_GIVEN = 0x40
+FIELD = 0x80
 
 OK, EINVAL, ENOMEM, EDOMAIN, ECUDA, EBUSY, ETIMEOUT, ENOTREADY = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "EDOMAIN", "ECUDA", "EBUSY", "ETIMEOUT", "ENOTREADY"]
@@ -36,7 +38,8 @@ SYMBOLS = ["fmm2d_default_params", "fmm2d_plan_create", "fmm2d_plan_set_domain",
            "fmm2d_keys_sort_noalloc", "fmm2d_autotune", "fmm2d_measure_alu_peaks",
            "fmm2d_plan_set_params", "fmm2d_serve_create", "fmm2d_serve_submit", "fmm2d_serve_poll",
            "fmm2d_serve_wait", "fmm2d_serve_stats", "fmm2d_serve_destroy",
-           "fmm2d_plan_set_leaf_size", "fmm2d_build_forest", "fmm2d_evaluate_field"]
+           "fmm2d_plan_set_leaf_size", "fmm2d_build_forest", "fmm2d_evaluate_field",
+           "fmm2d_plan_set_debug_stall"]
 
 
 class Info(ctypes.Structure):
@@ -102,6 +105,7 @@ def lib():
     L.fmm2d_debug_export.argtypes = [vp, c_int, c_int, vp, ctypes.c_size_t,
                                      ctypes.POINTER(ctypes.c_size_t)]
     L.fmm2d_plan_set_profiling.argtypes = [vp, c_int]
+    L.fmm2d_plan_set_debug_stall.argtypes = [vp, c_int]
     L.fmm2d_stage_times.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64), c_int,
                                     ctypes.POINTER(c_int)]
     L.fmm2d_plan_destroy.argtypes = [vp]
@@ -186,12 +190,14 @@ def fmm2d_autotune(tiling, eps, flags, src_xy, n_src, tgt_xy, n_tgt, domain=None
 
 
 def fmm2d_measure_alu_peaks():
-    """{"fp32_tflops", "lg2_gops", "fp64_tflops", "sms"} measured on the current device."""
-    out = (ctypes.c_double * 4)()
+    """{"fp32_tflops", "lg2_gops", "fp64_tflops", "sms", "tf32_tflops"} measured on the
+    current device."""
+    out = (ctypes.c_double * 5)()
     st = lib().fmm2d_measure_alu_peaks(out)
     if st:
         raise FMM2DError(st, "fmm2d_measure_alu_peaks")
-    return {"fp32_tflops": out[0], "lg2_gops": out[1], "fp64_tflops": out[2], "sms": int(out[3])}
+    return {"fp32_tflops": out[0], "lg2_gops": out[1], "fp64_tflops": out[2], "sms": int(out[3]),
+            "tf32_tflops": out[4]}
 
 
 class Plan:
@@ -291,6 +297,12 @@ class Plan:
         self._check(self.lib.fmm2d_plan_set_profiling(self._h, int(on)), "profiling")
 
     set_profiling = fmm2d_plan_set_profiling
+
+    def fmm2d_plan_set_debug_stall(self, on=True):
+        """Test switch: tensor-core M2L CTAs time out before their MMAs."""
+        self._check(self.lib.fmm2d_plan_set_debug_stall(self._h, int(on)), "debug_stall")
+
+    set_debug_stall = fmm2d_plan_set_debug_stall
 
     def fmm2d_stage_times(self):
         ms = (ctypes.c_double * 16)()

@@ -96,7 +96,7 @@ def test_binding_matches_header(fm):
     txt = _header()
     macros = dict(re.findall(r"#define\s+(FMM2D_[A-Z0-9_]+)\s+(0x[0-9a-fA-F]+)u", txt))
     for name in ("PREC_FP64", "PREC_MIXED", "PREC_MIXED_TC", "PREC_HYBRID", "PREC_SPLIT",
-                 "IN_F32", "ADAPTIVE"):
+                 "IN_F32", "ADAPTIVE", "SERVE_PREC_AS_GIVEN", "FIELD"):
         assert getattr(fm, name) == int(macros["FMM2D_" + name], 16), name
     for cname, py in (("fmm2d_request", fm.Request), ("fmm2d_result", fm.Result),
                       ("fmm2d_info", fm.Info), ("fmm2d_serve_info", fm.ServeInfo)):

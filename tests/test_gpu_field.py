@@ -44,7 +44,7 @@ def run_field(fm, tiling, src, u, tgt=None, levels=0, p=0, eps=1e-6, prec="fp64"
               leaf_size=None, check_phi=True):
     torch = _torch()
     dev = torch.device("cuda:0")
-    flags = PREC[prec] | (fm.IN_F32 if f32 else 0) | (fm.ADAPTIVE if leaf_size is not None else 0)
+    flags = PREC[prec] | fm.FIELD | (fm.IN_F32 if f32 else 0) | (fm.ADAPTIVE if leaf_size is not None else 0)
     dt = np.float32 if f32 else np.float64
     plan = fm.Plan(tiling, levels=levels, p=p, eps=eps, flags=flags)
     if leaf_size is not None:
@@ -151,3 +151,10 @@ def test_field_edge_cases(fm):
     torch.cuda.synchronize()
     assert fld.cpu().numpy().tolist() == [0.0, 0.0]
     plan.close()
+    # an FP32-form plan made without FMM2D_FIELD refuses the field
+    p32 = fm.Plan("quad", levels=2, p=8, flags=PREC["mixed"])
+    p32.build(x_d, 100, x_d, 100)
+    with pytest.raises(fm.FMM2DError) as e:
+        p32.evaluate_field(u_d, phi, torch.empty(200, dtype=torch.float64, device=dev))
+    assert e.value.status == fm.EINVAL
+    p32.close()
