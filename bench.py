@@ -967,6 +967,10 @@ def run_server_workload(args):
     sv.close()
     lat = np.array([r["latency_ms"] for r in res])
     ok = sum(r["status"] == 0 for r in res)
+    failed = [{"i": i, "status": int(r["status"]), "tiling": names[tilings[i]], "n": int(sizes[i]),
+               "eps": float(eps[i]), "cluster": bool(cluster[i]), "batched": int(r["batched"]),
+               "slot": int(r["slot"]), "error": r.get("error", "")}
+              for i, r in enumerate(res) if r["status"] != 0]
     if args.dump:   # one line per request: what it was and how long it took
         with open(args.dump, "w") as f:
             for i, r in enumerate(res):
@@ -997,7 +1001,7 @@ def run_server_workload(args):
                    else "served FMM requests: p50/p99 latency and points/s"),
         "value": points / (t1 - t0), "unit": "points/s", "n_gpus": 1,
         "higher_is_better": True, "data": "synthetic", "workload": args.workload,
-        "requests": count, "completed_ok": int(ok), "wall_s": t1 - t0,
+        "requests": count, "completed_ok": int(ok), "failed": failed[:20], "wall_s": t1 - t0,
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "max": float(lat.max())},
         "run_ms_mean": float(np.mean([r["run_ms"] for r in res])),

@@ -452,6 +452,7 @@ typedef struct {
   double queue_ms;         /* submit -> start */
   double run_ms;           /* start -> potentials in host memory */
   double latency_ms;       /* submit -> completion */
+  char error[128];         /* text of the error of a failed request ("" if none) */
 } fmm2d_result;
 
 typedef struct {
@@ -463,7 +464,11 @@ typedef struct {
 /*
  * fmm2d_serve_create - start a server on the current device with `max_slots`
  * execution slots (host threads, each with its own stream and plans; 1..256)
- * and an HBM budget in bytes for the requests running at once.
+ * and an HBM budget in bytes for the requests running at once.  The plans a
+ * slot keeps between requests (their operator tables and buffers) hold at
+ * most budget / (2 max_slots) bytes per slot, least recently used dropped
+ * first; a request whose solve runs out of device memory frees its slot's
+ * plans and buffers and runs once more before it reports FMM2D_ENOMEM.
  * Errors: FMM2D_EINVAL, FMM2D_ENOMEM, FMM2D_ECUDA (no device).
  */
 fmm2d_status fmm2d_serve_create(size_t hbm_budget_bytes, int max_slots, fmm2d_server **out);

@@ -406,6 +406,12 @@ fmm2d_status fail(fmm2d_plan *pl, fmm2d_status st, const std::string &msg) {
   return st;
 }
 fmm2d_status cuda_fail(fmm2d_plan *pl, cudaError_t e, const char *where) {
+  // a failed device allocation is reported as such (the caller may free
+  // memory and retry); any other failed CUDA call as FMM2D_ECUDA
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();   // clear the (non-sticky) allocation error
+    return fail(pl, FMM2D_ENOMEM, std::string(where) + ": " + cudaGetErrorString(e));
+  }
   return fail(pl, FMM2D_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 #define CK(expr, where)                                  \
@@ -1379,6 +1385,41 @@ fmm2d_status field_t(fmm2d_plan *pl, double *field, cudaStream_t s) {
   return FMM2D_OK;
 }
 
+// Every device buffer a plan owns.
+template <typename F>
+static void for_each_dbuf(fmm2d_plan *pl, F f) {
+  DBuf *const bufs[] = {&pl->d_key_s, &pl->d_perm_s, &pl->d_key_t, &pl->d_perm_t, &pl->d_tmp_k,
+                  &pl->d_tmp_v, &pl->d_sort_scratch, &pl->d_err, &pl->d_occ, &pl->d_hsrc,
+                  &pl->d_scan, &pl->d_map, &pl->d_cell_key, &pl->d_cell_crd, &pl->d_cell_ctr,
+                  &pl->d_cell_cls, &pl->d_cell_hsrc, &pl->d_src_start, &pl->d_src_end,
+                  &pl->d_tgt_start, &pl->d_tgt_end, &pl->d_lev_first, &pl->d_far_cnt,
+                  &pl->d_far_src, &pl->d_far_op, &pl->d_near_cnt, &pl->d_near_src, &pl->d_src4,
+                  &pl->d_tgt2, &pl->d_mQ, &pl->d_ma, &pl->d_ma_ff, &pl->d_lL0, &pl->d_lb, &pl->d_phi_near,
+                  &pl->d_fnear, &pl->d_tc_part_lb, &pl->d_tc_part_L0,
+                  &pl->d_phi_far, &pl->d_sten, &pl->d_geo_scale, &pl->d_m2l_ops, &pl->d_m2l_logz,
+                  &pl->d_m2m_ops, &pl->d_l2l_ops, &pl->d_counts, &pl->d_far_full,
+                  &pl->d_cls_cnt, &pl->d_cls_cells, &pl->d_tc_ops, &pl->d_ff_ops, &pl->d_ff_ph, &pl->d_dev_err,
+                  &pl->d_p2p_order, &pl->d_p2p_cnt,
+                  &pl->d_cell_lev, &pl->d_parent, &pl->d_child_first, &pl->d_child_cnt,
+                  &pl->d_split, &pl->d_leaf_ids, &pl->d_leaf_pos, &pl->d_ad_scale,
+                  &pl->d_ad_inv_scale, &pl->d_u_off, &pl->d_u_src, &pl->d_w_off, &pl->d_w_src,
+                  &pl->d_x_off, &pl->d_x_src, &pl->d_ad_flag, &pl->d_ad_pos, &pl->d_ad_crange,
+                  &pl->d_ad_cnt, &pl->d_ad_off, &pl->d_ad_tot, &pl->d_ad_ta, &pl->d_ad_tc,
+                  &pl->d_ad_sa, &pl->d_ad_sc, &pl->d_ad_ta2, &pl->d_ad_tc2, &pl->d_ad_sa2,
+                  &pl->d_ad_sc2, &pl->d_ad_ut, &pl->d_ad_us, &pl->d_ad_wt, &pl->d_ad_ws,
+                  &pl->d_ad_xt, &pl->d_ad_xs, &pl->d_inst_off, &pl->d_src4f, &pl->d_tgt2f, &pl->d_srclo,
+                  &pl->d_tgtlo};
+  for (DBuf *b : bufs) f(*b);
+}
+
+namespace fmm2d {
+size_t plan_device_bytes(const fmm2d_plan *cpl) {
+  size_t tot = 0;
+  for_each_dbuf(const_cast<fmm2d_plan *>(cpl), [&](DBuf &b) { tot += b.bytes; });
+  return tot;
+}
+}  // namespace fmm2d
+
 extern "C" {
 
 fmm2d_status fmm2d_evaluate_field(fmm2d_plan *pl, const void *u, double *out, double *field,
@@ -2013,28 +2054,7 @@ void fmm2d_plan_destroy(fmm2d_plan *pl) {
   if (!pl) return;
   flush_events(pl);
   for (auto ev : pl->ev_pool) cudaEventDestroy(ev);
-  DBuf *bufs[] = {&pl->d_key_s, &pl->d_perm_s, &pl->d_key_t, &pl->d_perm_t, &pl->d_tmp_k,
-                  &pl->d_tmp_v, &pl->d_sort_scratch, &pl->d_err, &pl->d_occ, &pl->d_hsrc,
-                  &pl->d_scan, &pl->d_map, &pl->d_cell_key, &pl->d_cell_crd, &pl->d_cell_ctr,
-                  &pl->d_cell_cls, &pl->d_cell_hsrc, &pl->d_src_start, &pl->d_src_end,
-                  &pl->d_tgt_start, &pl->d_tgt_end, &pl->d_lev_first, &pl->d_far_cnt,
-                  &pl->d_far_src, &pl->d_far_op, &pl->d_near_cnt, &pl->d_near_src, &pl->d_src4,
-                  &pl->d_tgt2, &pl->d_mQ, &pl->d_ma, &pl->d_ma_ff, &pl->d_lL0, &pl->d_lb, &pl->d_phi_near,
-                  &pl->d_fnear, &pl->d_tc_part_lb, &pl->d_tc_part_L0,
-                  &pl->d_phi_far, &pl->d_sten, &pl->d_geo_scale, &pl->d_m2l_ops, &pl->d_m2l_logz,
-                  &pl->d_m2m_ops, &pl->d_l2l_ops, &pl->d_counts, &pl->d_far_full,
-                  &pl->d_cls_cnt, &pl->d_cls_cells, &pl->d_tc_ops, &pl->d_ff_ops, &pl->d_ff_ph, &pl->d_dev_err,
-                  &pl->d_p2p_order, &pl->d_p2p_cnt,
-                  &pl->d_cell_lev, &pl->d_parent, &pl->d_child_first, &pl->d_child_cnt,
-                  &pl->d_split, &pl->d_leaf_ids, &pl->d_leaf_pos, &pl->d_ad_scale,
-                  &pl->d_ad_inv_scale, &pl->d_u_off, &pl->d_u_src, &pl->d_w_off, &pl->d_w_src,
-                  &pl->d_x_off, &pl->d_x_src, &pl->d_ad_flag, &pl->d_ad_pos, &pl->d_ad_crange,
-                  &pl->d_ad_cnt, &pl->d_ad_off, &pl->d_ad_tot, &pl->d_ad_ta, &pl->d_ad_tc,
-                  &pl->d_ad_sa, &pl->d_ad_sc, &pl->d_ad_ta2, &pl->d_ad_tc2, &pl->d_ad_sa2,
-                  &pl->d_ad_sc2, &pl->d_ad_ut, &pl->d_ad_us, &pl->d_ad_wt, &pl->d_ad_ws,
-                  &pl->d_ad_xt, &pl->d_ad_xs, &pl->d_inst_off, &pl->d_src4f, &pl->d_tgt2f, &pl->d_srclo,
-                  &pl->d_tgtlo};
-  for (DBuf *b : bufs) dbuf_free(*b);
+  for_each_dbuf(pl, [](DBuf &b) { dbuf_free(b); });
   if (pl->far_stream) {
     cudaStreamSynchronize(pl->far_stream);
     cudaStreamDestroy(pl->far_stream);

@@ -384,6 +384,11 @@ __global__ void __launch_bounds__(TC_THREADS, (TcShape<K, N>::CTAS)) k_m2l_tc(Tc
       // let the operator copies in flight land before the CTA exits: the
       // copies of entries landed .. issued-1 were not waited for
       for (uint32_t u = landed; u < issued; ++u) mbar_wait(&full_bar[u % NB], (u / NB) & 1);
+      // and the MMAs committed before the abort, before their TMEM is freed
+      if (landed > 0) {
+        const uint32_t last = landed - 1;
+        mbar_wait(&mma_bar[last & 1], (last >> 1) & 1);
+      }
     }
   } else if (it > 0 && tid == 0) {
     const uint32_t last = it - 1;

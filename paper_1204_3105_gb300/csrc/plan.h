@@ -141,6 +141,11 @@ double tri_rho0();
 // Leaf level of the S_opt rule (Table 2, App. A-C) for N sources, M targets
 // and expansion order p.
 int planner_sopt_levels(int tiling, int64_t n_src, int64_t n_tgt, int p);
+}  // namespace fmm2d
+// Device memory (bytes) a plan holds in its buffers.
+struct fmm2d_plan;
+namespace fmm2d {
+size_t plan_device_bytes(const fmm2d_plan *pl);
 
 cudaError_t dbuf_reserve(DBuf &b, size_t bytes);
 void dbuf_free(DBuf &b);

@@ -55,19 +55,58 @@ struct SlotBuf {
     if (e == cudaSuccess) bytes = b;
     return e;
   }
-  ~SlotBuf() {
+  void release() {
     if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
   }
+  ~SlotBuf() { release(); }
 };
 
 struct Slot {
   int id = 0;
   cudaStream_t stream = nullptr;
   // plans keyed by (tiling, flags, levels, p): a plan keeps its operator
-  // tables and device memory for requests with the same parameters
+  // tables and device memory for requests with the same parameters; the
+  // cache is trimmed, least recently used first, to cache_bytes
   std::map<std::tuple<int, unsigned, int, int>, fmm2d_plan *> plans;
+  std::map<std::tuple<int, unsigned, int, int>, uint64_t> last_use;
+  uint64_t tick = 0;
+  size_t cache_bytes = 0;
   SlotBuf src, tgt, u, out;
 };
+
+// Drop the slot's cached plans, least recently used first, until the device
+// memory they hold is at most `cap` bytes.  cap = 0 drops every plan and
+// frees the slot's input and output buffers too.
+void trim_plans(Slot &sl, size_t cap) {
+  for (;;) {
+    size_t tot = 0;
+    bool found = false;
+    std::tuple<int, unsigned, int, int> victim;
+    uint64_t oldest = UINT64_MAX;
+    for (auto &kv : sl.plans) {
+      if (!kv.second) continue;
+      tot += plan_device_bytes(kv.second);
+      const uint64_t t = sl.last_use[kv.first];
+      if (t < oldest) {
+        oldest = t;
+        victim = kv.first;
+        found = true;
+      }
+    }
+    if (tot <= cap || !found) break;
+    fmm2d_plan_destroy(sl.plans[victim]);
+    sl.plans.erase(victim);
+    sl.last_use.erase(victim);
+  }
+  if (cap == 0) {
+    sl.src.release();
+    sl.tgt.release();
+    sl.u.release();
+    sl.out.release();
+  }
+}
 
 // Device-memory estimate of one request: inputs and outputs, the plan's
 // per-point arrays, and its tree (about 1 KB per cell, cells <= points).
@@ -166,22 +205,29 @@ fmm2d_status slot_plan(Slot &sl, const fmm2d_request &r, int64_t n_points, fmm2d
   fmm2d_plan *pl = sl.plans[key];
   fmm2d_status st;
   if (!pl) {
-    if (sl.plans.size() > 24) {   // bound the cache: drop the other plans of this slot
-      for (auto &kv : sl.plans)
-        if (kv.second) fmm2d_plan_destroy(kv.second);
-      sl.plans.clear();
-    }
     st = fmm2d_plan_create(r.tiling, L, p, r.eps, flags, &pl);
-    if (st != FMM2D_OK) return st;
+    if (st != FMM2D_OK) {
+      sl.plans.erase(key);
+      return st;
+    }
     if (flags & FMM2D_ADAPTIVE) fmm2d_plan_set_leaf_size(pl, serve_leaf_size(r.tiling));
     sl.plans[key] = pl;
   }
+  sl.last_use[key] = ++sl.tick;
   const double *dom = r.domain;
   st = fmm2d_plan_set_domain(pl, dom[2] > 0 ? dom[0] : 0.0, dom[2] > 0 ? dom[1] : 0.0,
                              dom[2] > 0 ? dom[2] : 1.0);
   *out = pl;
   *flags_out = flags;
   return st;
+}
+
+// The text of a failed request: the plan's last error, or `what`.
+void set_error(Job &j, const fmm2d_plan *pl, const char *what) {
+  const char *m = pl ? fmm2d_last_error(pl) : "";
+  if (!m || !*m) m = what;
+  std::strncpy(j.res.error, m, sizeof(j.res.error) - 1);
+  j.res.error[sizeof(j.res.error) - 1] = 0;
 }
 
 fmm2d_status run_job(Slot &sl, Job &j) {
@@ -192,27 +238,44 @@ fmm2d_status run_job(Slot &sl, Job &j) {
   fmm2d_plan *pl = nullptr;
   unsigned flags = 0;
   fmm2d_status st = slot_plan(sl, r, std::max(r.n_src, nt), &pl, &flags);
-  if (st != FMM2D_OK) return st;
+  if (st != FMM2D_OK) {
+    set_error(j, pl, "plan creation failed");
+    return st;
+  }
   cudaStream_t s = sl.stream;
   if (sl.src.reserve(std::max<size_t>(16, r.n_src * 2 * esz)) || sl.u.reserve(std::max<size_t>(16, r.n_src * esz)) ||
-      sl.out.reserve(std::max<size_t>(16, nt * 8)) || (!same && sl.tgt.reserve(std::max<size_t>(16, nt * 2 * esz))))
+      sl.out.reserve(std::max<size_t>(16, nt * 8)) || (!same && sl.tgt.reserve(std::max<size_t>(16, nt * 2 * esz)))) {
+    cudaGetLastError();
+    set_error(j, nullptr, "out of device memory for the request's buffers");
     return FMM2D_ENOMEM;
+  }
   if (r.n_src > 0) {
     cudaMemcpyAsync(sl.src.p, r.src_xy, r.n_src * 2 * esz, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(sl.u.p, r.strengths, r.n_src * esz, cudaMemcpyHostToDevice, s);
   }
   if (!same && nt > 0) cudaMemcpyAsync(sl.tgt.p, r.tgt_xy, nt * 2 * esz, cudaMemcpyHostToDevice, s);
   st = fmm2d_build(pl, sl.src.p, r.n_src, same ? sl.src.p : sl.tgt.p, nt, s);
-  if (st != FMM2D_OK) return st;
+  if (st != FMM2D_OK) {
+    set_error(j, pl, "build failed");
+    return st;
+  }
   st = fmm2d_evaluate(pl, sl.u.p, (double *)sl.out.p, s);
-  if (st != FMM2D_OK) return st;
+  if (st != FMM2D_OK) {
+    set_error(j, pl, "evaluate failed");
+    return st;
+  }
   if (nt > 0) cudaMemcpyAsync(r.potentials, sl.out.p, nt * 8, cudaMemcpyDeviceToHost, s);
-  if (cudaStreamSynchronize(s) != cudaSuccess) return FMM2D_ECUDA;
+  const cudaError_t ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) {
+    set_error(j, nullptr, cudaGetErrorString(ce));
+    return FMM2D_ECUDA;
+  }
   fmm2d_info info;
   fmm2d_plan_query(pl, &info);
   j.res.levels = info.levels;
   j.res.p = info.p;
   j.res.flags = flags;
+  if (info.device_error) set_error(j, nullptr, "a bounded device wait gave up");
   return info.device_error ? FMM2D_ETIMEOUT : FMM2D_OK;
 }
 
@@ -288,8 +351,19 @@ void worker(fmm2d_server *sv, Slot *sl) {
     std::vector<fmm2d_status> st(batch.size(), FMM2D_OK);
     if (batch.size() == 1) {
       st[0] = run_job(*sl, *batch[0]);
+      if (st[0] == FMM2D_ENOMEM) {   // free the slot's cache and try once more
+        cudaStreamSynchronize(sl->stream);
+        trim_plans(*sl, 0);
+        std::memset(&batch[0]->res, 0, sizeof(batch[0]->res));
+        st[0] = run_job(*sl, *batch[0]);
+      }
     } else {
-      const fmm2d_status bs = run_batch(*sl, batch);
+      fmm2d_status bs = run_batch(*sl, batch);
+      if (bs == FMM2D_ENOMEM) {
+        cudaStreamSynchronize(sl->stream);
+        trim_plans(*sl, 0);
+        bs = run_batch(*sl, batch);
+      }
       if (bs == FMM2D_OK) {
         std::fill(st.begin(), st.end(), FMM2D_OK);
       } else {   // one request may be at fault (e.g. a point outside the domain): run each alone
@@ -299,6 +373,7 @@ void worker(fmm2d_server *sv, Slot *sl) {
         }
       }
     }
+    trim_plans(*sl, sl->cache_bytes);   // the slot's cache back within its share
     {
       std::lock_guard<std::mutex> lk(sv->mu);
       const Clock::time_point now = Clock::now();
@@ -340,6 +415,8 @@ fmm2d_status fmm2d_serve_create(size_t hbm_budget_bytes, int max_slots, fmm2d_se
   for (int i = 0; i < max_slots; ++i) {
     auto sl = std::make_unique<Slot>();
     sl->id = i;
+    // cached plans of all slots together hold at most half the budget
+    sl->cache_bytes = hbm_budget_bytes / 2 / (size_t)max_slots;
     if (cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) != cudaSuccess) {
       fmm2d_serve_destroy(sv);
       return FMM2D_ECUDA;

@@ -67,7 +67,8 @@ class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("levels", ctypes.c_int32), ("p", ctypes.c_int32),
                 ("flags", ctypes.c_uint32), ("slot", ctypes.c_int32), ("batched", ctypes.c_int32),
                 ("queue_ms", ctypes.c_double),
-                ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+                ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
+                ("error", ctypes.c_char * 128)]
 
 
 class ServeInfo(ctypes.Structure):
@@ -370,7 +371,9 @@ class Server:
 
     def _result(self, t, res):
         self._keep.pop(t, None)
-        return {f: getattr(res, f) for f, _ in Result._fields_}
+        d = {f: getattr(res, f) for f, _ in Result._fields_}
+        d["error"] = res.error.decode(errors="replace")
+        return d
 
     def fmm2d_serve_poll(self, ticket):
         res = Result()
