@@ -27,6 +27,8 @@
 // lane t of every warp owns target t, warp w the output rows w, w + 8, ...
 #include <complex>
 
+#include <mutex>
+
 #include "plan.h"
 
 namespace fmm2d {
@@ -275,8 +277,20 @@ cudaError_t launch_m2l_ff(const FfArgs &a, int64_t n_far_cells, cudaStream_t s) 
   if (n_far_cells <= 0) return cudaSuccess;
   if (a.p < 1 || a.p > MAXP) return cudaErrorInvalidValue;
   const size_t smem = m2l_ff_smem_bytes(a.p);
-  cudaError_t e = cudaFuncSetAttribute(k_m2l_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  {
+    // The shared-memory limit is one setting of the kernel for the whole
+    // process, and plans of different p launch it from several host threads
+    // (server slots): only ever raise it, so that no launch finds it lowered
+    // by another thread between its own setting and its launch.
+    static std::mutex mu;
+    static size_t set_bytes = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (smem > set_bytes) {
+      cudaError_t e = cudaFuncSetAttribute(k_m2l_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      set_bytes = smem;
+    }
+  }
   // tiles <= cells / 32 + classes; a persistent grid of three CTAs per SM
   const int64_t nel = a.n_cells * (a.p + 1);
   k_ma_to_ff<<<(unsigned)((nel + 255) / 256), 256, 0, s>>>(a.n_cells, a.p, a.P, a.mQ, a.ma, a.ma_ff);

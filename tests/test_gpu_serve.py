@@ -167,3 +167,23 @@ def test_budget_admission_and_busy(fm):
         sv.submit("quad", big, bu, np.zeros(len(big)), eps=1e-6)
     assert e.value.status == fm.EBUSY
     sv.close()
+
+
+def test_concurrent_requests_of_different_p(fm):
+    """Requests of the float-float (hybrid) form with different expansion
+    orders p run at once on several slots.  The kernel's shared-memory size
+    depends on p and its limit is one setting for the whole process; every
+    request must still launch and succeed (a slot lowering the limit while
+    another launched used to fail that launch)."""
+    sv = fm.Server(16 << 30, max_slots=8)
+    reqs = []
+    for i in range(48):
+        n = 20000 + 997 * i
+        xy, u = gaussian_mixture(n, seed=900 + i, k=8)
+        o = np.zeros(n)
+        t = sv.submit(("quad", "sept", "tri")[i % 3], xy, u, o, eps=1e-8, p=14 + (i % 24),
+                      flags=fm.ADAPTIVE)
+        reqs.append(t)
+    res = [sv.wait(t, 600000.0) for t in reqs]
+    sv.close()
+    assert all(r["status"] == 0 for r in res), [(r["status"], r["error"]) for r in res if r["status"]]
