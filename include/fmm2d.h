@@ -464,11 +464,12 @@ typedef struct {
 /*
  * fmm2d_serve_create - start a server on the current device with `max_slots`
  * execution slots (host threads, each with its own stream and plans; 1..256)
- * and an HBM budget in bytes for the requests running at once.  The plans a
- * slot keeps between requests (their operator tables and buffers) hold at
- * most budget / (2 max_slots) bytes per slot, least recently used dropped
- * first; a request whose solve runs out of device memory frees its slot's
- * plans and buffers and runs once more before it reports FMM2D_ENOMEM.
+ * and an HBM budget in bytes for the requests running at once.  Each slot
+ * keeps the plans of its recent requests (operator tables and buffers); when
+ * less than a tenth of the device memory is free, a slot trims them to
+ * budget / (2 max_slots) bytes, least recently used first, and a request
+ * whose solve runs out of device memory frees its slot's plans and buffers
+ * and runs once more before it reports FMM2D_ENOMEM.
  * Errors: FMM2D_EINVAL, FMM2D_ENOMEM, FMM2D_ECUDA (no device).
  */
 fmm2d_status fmm2d_serve_create(size_t hbm_budget_bytes, int max_slots, fmm2d_server **out);

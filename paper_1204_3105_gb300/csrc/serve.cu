@@ -373,7 +373,13 @@ void worker(fmm2d_server *sv, Slot *sl) {
         }
       }
     }
-    trim_plans(*sl, sl->cache_bytes);   // the slot's cache back within its share
+    // under memory pressure (cudaFree synchronises the device, so not after
+    // every request) the slot's cache goes back within its share
+    {
+      size_t free_b = 0, total_b = 0;
+      if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && free_b < total_b / 10)
+        trim_plans(*sl, sl->cache_bytes);
+    }
     {
       std::lock_guard<std::mutex> lk(sv->mu);
       const Clock::time_point now = Clock::now();
@@ -415,7 +421,8 @@ fmm2d_status fmm2d_serve_create(size_t hbm_budget_bytes, int max_slots, fmm2d_se
   for (int i = 0; i < max_slots; ++i) {
     auto sl = std::make_unique<Slot>();
     sl->id = i;
-    // cached plans of all slots together hold at most half the budget
+    // when device memory runs low, the cached plans of all slots together
+    // are trimmed to half the budget
     sl->cache_bytes = hbm_budget_bytes / 2 / (size_t)max_slots;
     if (cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) != cudaSuccess) {
       fmm2d_serve_destroy(sv);
