@@ -359,17 +359,27 @@ def run_ours(args):
     # host read-back) overlaps the evaluation of the one before it
     tstreams = {t: torch.cuda.Stream(device=dev) for t in args.tilings}
 
+    # ... and each is issued from a host thread of its own: fmm2d_build waits
+    # for its own level counts, so from one thread the three builds (chains of
+    # small latency-bound kernels) would follow one another
+    from concurrent.futures import ThreadPoolExecutor
+    issuers = ThreadPoolExecutor(len(args.tilings), initializer=torch.cuda.set_device,
+                                 initargs=(local,))
+
+    def solve_on(t, start, xs, us):   # one tiling's build + evaluate on its stream
+        ts = tstreams[t]
+        ts.wait_event(start)
+        plans[t].build(xs, N_POINTS, xs, N_POINTS, ts)
+        plans[t].evaluate(us, outs[t], ts)
+        d = torch.cuda.Event()
+        d.record(ts)
+        return d
+
     def step_concurrent(evs):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for t in args.tilings:
-            ts = tstreams[t]
-            ts.wait_event(e0)
-            plans[t].build(xy_d, N_POINTS, xy_d, N_POINTS, ts)
-            plans[t].evaluate(u_d, outs[t], ts)
-            d = torch.cuda.Event()
-            d.record(ts)
+        for d in issuers.map(lambda t: solve_on(t, e0, xy_d, u_d), args.tilings):
             stream.wait_event(d)
         e1.record(stream)
         evs.append((e0, e1))
@@ -467,13 +477,18 @@ def run_ours(args):
         ud = u_h.to(dev, non_blocking=True)
         ready = torch.cuda.Event()
         ready.record(stream)
-        for t in args.tilings:
-            ts = stream if args.serial else tstreams[t]
-            ts.wait_event(ready)
-            plans[t].build(xd, N_POINTS, xd, N_POINTS, ts)
-            plans[t].evaluate(ud, outs[t], ts)
-            done = torch.cuda.Event()
-            done.record(ts)
+        if args.serial:
+            dones = []
+            for t in args.tilings:
+                stream.wait_event(ready)
+                plans[t].build(xd, N_POINTS, xd, N_POINTS, stream)
+                plans[t].evaluate(ud, outs[t], stream)
+                done = torch.cuda.Event()
+                done.record(stream)
+                dones.append(done)
+        else:
+            dones = list(issuers.map(lambda t: solve_on(t, ready, xd, ud), args.tilings))
+        for t, done in zip(args.tilings, dones):
             copy_stream.wait_event(done)
             with torch.cuda.stream(copy_stream):
                 res_h[t].copy_(outs[t], non_blocking=True)
@@ -577,7 +592,8 @@ def run_ours(args):
                        "l2": "flushed between tilings (256 MB write)" if args.serial else
                              "flushed between steps (256 MB write)",
                        "streams": "one tiling after another on one stream" if args.serial else
-                                  "the three tilings on three streams, joined at the end of the step",
+                                  "the three tilings on three streams, issued from three host "
+                                  "threads, joined at the end of the step",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "ms_per_step_serial": ms_serial,
             "per_tiling": {t: {"points_per_s": N_POINTS / (statistics.mean(tt[t]) / 1e3),
@@ -608,6 +624,7 @@ def run_ours(args):
             "clocks": clk.summary(),
         }
         print(json.dumps(line))
+    issuers.shutdown()
     for p_ in plans.values():
         p_.close()
     if dist:
@@ -782,20 +799,26 @@ def run_forest_batch(args):
             times.append((name, e0, e1))
             flush.zero_()
 
-    # the three forests are independent: one stream each, joined per step
+    # the three forests are independent: one stream and one issuing host
+    # thread each (a forest build waits for its level counts), joined per step
     fstreams = {nm: torch.cuda.Stream(device=dev) for nm in names}
+    from concurrent.futures import ThreadPoolExecutor
+    issuers = ThreadPoolExecutor(len(names), initializer=torch.cuda.set_device, initargs=(0,))
+
+    def forest_on(name, start):
+        f, fs = forests[name], fstreams[name]
+        fs.wait_event(start)
+        f["plan"].build_forest(f["xy_d"], f["off"], fs)
+        f["plan"].evaluate(f["u_d"], f["out"], fs)
+        d = torch.cuda.Event()
+        d.record(fs)
+        return d
 
     def step_concurrent(whole):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for name in names:
-            f, fs = forests[name], fstreams[name]
-            fs.wait_event(e0)
-            f["plan"].build_forest(f["xy_d"], f["off"], fs)
-            f["plan"].evaluate(f["u_d"], f["out"], fs)
-            d = torch.cuda.Event()
-            d.record(fs)
+        for d in issuers.map(lambda nm: forest_on(nm, e0), names):
             stream.wait_event(d)
         e1.record(stream)
         whole.append((e0, e1))
@@ -834,7 +857,7 @@ def run_forest_batch(args):
     for it in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for name in names:
+        def forest_e2e(name):
             f = forests[name]
             fs = stream if args.serial else fstreams[name]
             with torch.cuda.stream(fs):   # copies, build and evaluation on the forest's stream
@@ -843,6 +866,11 @@ def run_forest_batch(args):
                 f["plan"].build_forest(xd, f["off"], fs)
                 f["plan"].evaluate(ud, f["out"], fs)
                 f["res_h"].copy_(f["out"], non_blocking=True)
+        if args.serial:
+            for name in names:
+                forest_e2e(name)
+        else:
+            list(issuers.map(forest_e2e, names))
         torch.cuda.synchronize()
         if it >= args.warmup:
             e2e.append(time.perf_counter() - t0)
@@ -892,7 +920,8 @@ def run_forest_batch(args):
                    "l2": "flushed between forests (256 MB write)" if args.serial else
                          "flushed between steps (256 MB write)",
                    "streams": "one forest after another" if args.serial else
-                              "the three forests on three streams, joined at the end of the step"},
+                              "the three forests on three streams, issued from three host "
+                              "threads, joined at the end of the step"},
         "per_tiling": {n: {"instances": forests[n]["n"], "points": int(forests[n]["off"][-1]),
                            "stages_ms_isolated": stages[n],
                            "ms": statistics.mean(per[n]), "p": forests[n]["p"],
@@ -905,6 +934,7 @@ def run_forest_batch(args):
         "clocks": clk.summary(),
     }
     print(json.dumps(line))
+    issuers.shutdown()
     for f in forests.values():
         f["plan"].close()
 
