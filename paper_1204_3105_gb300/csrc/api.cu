@@ -681,6 +681,7 @@ fmm2d_status evaluate_t(fmm2d_plan *pl, const void *u, double *out, cudaStream_t
   a.L = L;
   a.l_min = pl->l_min;
   a.b = pl->b;
+  a.n_cls = pl->sten.n_classes;
   a.leaf_first = pl->lev_first[L];
   a.n_leaves = pl->lev_count[L];
   cd inv_s = 1.0 / cd(pl->scale_re[L], pl->scale_im[L]);
@@ -1171,6 +1172,7 @@ fmm2d_status evaluate_adaptive_t(fmm2d_plan *pl, const void *u, double *out, cud
   a.L = L;
   a.l_min = pl->l_min;
   a.b = pl->b;
+  a.n_cls = pl->sten.n_classes;
   a.leaf_first = 0;
   a.n_leaves = pl->n_leaves_ad;
   a.inv_s_re = 1.0;
@@ -1346,6 +1348,7 @@ fmm2d_status field_t(fmm2d_plan *pl, double *field, cudaStream_t s) {
   a.L = L;
   a.l_min = pl->l_min;
   a.b = pl->b;
+  a.n_cls = pl->sten.n_classes;
   if (ad) {
     a.leaf_first = 0;
     a.n_leaves = pl->n_leaves_ad;

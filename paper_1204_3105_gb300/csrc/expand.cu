@@ -154,54 +154,105 @@ k_p2m_t(ExpandArgs a, const R *__restrict__ src4, const int *__restrict__ start,
   }
 }
 
-// H lanes per parent cell (the launcher uses a whole warp, H = 32); lane i of
-// the group owns output coefficients i+1 and i+1+H.
-template <typename R, int H>
+// One warp per parent cell; lane i owns output coefficients i+1 and i+33.
+// Every child's slot, charge, class and multipole is fetched before any
+// arithmetic, so a level costs about three dependent loads (the parent's key,
+// the child slots, the child data) rather than three per child; the children
+// are then applied in child order.
+template <typename R>
 __global__ void __launch_bounds__(32 * WPB)
 k_m2m(ExpandArgs a, Geo g, int level, int64_t first, int64_t count, const int *__restrict__ map,
       const uint32_t *__restrict__ cell_key, const uint8_t *__restrict__ cell_cls,
-      const uint8_t *__restrict__ cell_hsrc, const Cx<R> *__restrict__ ops,
+      const uint8_t *__restrict__ cell_hsrc, const Cx<R> *__restrict__ ops, int n_staged,
       double *__restrict__ mQ, Cx<R> *__restrict__ ma) {
-  constexpr int CPW = 32 / H;
-  __shared__ Cx<R> sh[WPB * CPW][MAXP + 1];
+  constexpr int NB = 7;                        // children of a cell, at most
+  constexpr int NLD = (NB * MAXP + 31) / 32;   // multipole loads per lane, at most
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ Cx<R> sh[WPB][NB][MAXP + 1];
+  extern __shared__ __align__(16) unsigned char dyn_ops[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int li = lane % H, sub = lane / H, slot = w * CPW + sub;
-  const unsigned mask = H == 32 ? 0xffffffffu : (0xffffu << (16 * sub));
-  const int64_t ci = (blockIdx.x * (int64_t)WPB + w) * CPW + sub;
-  if (ci >= count) return;
-  const int64_t gp = first + ci;
-  if (a.child_first && a.child_cnt[gp] == 0) return;   // adaptive leaf: keeps its P2M
+  const int64_t ci = blockIdx.x * (int64_t)WPB + w;
+  const bool valid = ci < count;
+  const int64_t gp = first + (valid ? ci : 0);
   const int p = a.p, P1 = p + 1;
-  Cx<R> acc0 = {(R)0, (R)0}, acc1 = {(R)0, (R)0};
-  double Q = 0.0;
-  if (cell_hsrc[gp]) {
+  // the parent's own fields, fetched together (and with the operator table)
+  const bool hs = valid && cell_hsrc[gp];
+  int nch = 0, cs = -1, cf = 0;
+  if (a.child_first) {
+    cf = a.child_first[gp];
+    nch = a.child_cnt[gp];
+  } else {
     const uint32_t key = cell_key[gp];
-    const int nch = a.child_first ? (int)a.child_cnt[gp] : g.b;
-    for (int d = 0; d < nch; ++d) {
-      int cs = a.child_first ? a.child_first[gp] + d
-                             : map[g.map_off[level + 1] + (int64_t)key * g.b + d];
-      if (cs < 0 || !cell_hsrc[cs]) continue;
-      const double Qc = mQ[cs];
-      for (int k = li; k < p; k += H) sh[slot][k + 1] = ma[(int64_t)cs * a.P + k];
-      __syncwarp(mask);
-      const Cx<R> *op = ops + (int64_t)cell_cls[cs] * P1 * P1;
-      const R qc = (R)Qc;
+    nch = g.b;
+    if (valid && lane < nch) cs = map[g.map_off[level + 1] + (int64_t)key * g.b + lane];
+  }
+  const Cx<R> *op_tab = ops;
+  if (n_staged > 0) {   // the operators in shared memory: every child reads them
+    Cx<R> *so = reinterpret_cast<Cx<R> *>(dyn_ops);
+    for (int i = threadIdx.x; i < n_staged; i += blockDim.x) so[i] = ops[i];
+    __syncthreads();
+    op_tab = so;
+  }
+  if (!valid) return;
+  if (a.child_first) {
+    if (nch == 0) return;                      // adaptive leaf: keeps its P2M
+    if (!hs) nch = 0;
+    if (lane < nch) cs = cf + lane;
+  } else if (!hs) {
+    nch = 0;
+    cs = -1;
+  }
+  // lane d < nch: child d's flag, charge and class
+  int use = 0, cls = 0;
+  double Qc = 0.0;
+  if (cs >= 0) {
+    use = cell_hsrc[cs];
+    Qc = mQ[cs];
+    cls = cell_cls[cs];
+  }
+  // all lanes: the children's multipoles, entry idx = d p + k
+  Cx<R> v[NLD];
+  const int nv = nch * p;
 #pragma unroll
-      for (int h = 0; h < 64 / H; ++h) {
-        const int l = li + 1 + H * h;
-        if (l > p) break;
-        const Cx<R> *row = op + (int64_t)l * P1;
-        Cx<R> s = qc * row[0];
-        for (int k = 1; k <= l; ++k) cfma(s, row[k], sh[slot][k]);
-        if (h == 0) acc0 = acc0 + s; else acc1 = acc1 + s;
-      }
-      Q += Qc;
-      __syncwarp(mask);
+  for (int r = 0; r < NLD; ++r) {
+    const int idx = lane + 32 * r;
+    const int d = min(idx / max(p, 1), 31);
+    const int cd = __shfl_sync(FULL, cs, d);
+    v[r] = Cx<R>{(R)0, (R)0};
+    if (idx < nv && cd >= 0) v[r] = ma[(int64_t)cd * a.P + (idx - d * p)];
+  }
+#pragma unroll
+  for (int r = 0; r < NLD; ++r) {
+    const int idx = lane + 32 * r;
+    if (idx < nv) {
+      const int d = idx / p;
+      sh[w][d][idx - d * p + 1] = v[r];
     }
   }
-  if (li == 0) mQ[gp] = Q;
-  if (li + 1 <= p) ma[gp * a.P + li] = acc0;
-  if (li + 1 + H <= p) ma[gp * a.P + li + H] = acc1;
+  __syncwarp();
+  Cx<R> acc0 = {(R)0, (R)0}, acc1 = {(R)0, (R)0};
+  double Q = 0.0;
+  for (int d = 0; d < nch; ++d) {
+    const int ud = __shfl_sync(FULL, use, d);
+    const double qd = __shfl_sync(FULL, Qc, d);
+    const int kd = __shfl_sync(FULL, cls, d);
+    if (!ud) continue;                         // warp-uniform
+    const Cx<R> *op = op_tab + (int64_t)kd * P1 * P1;
+    const R q = (R)qd;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int l = lane + 1 + 32 * h;
+      if (l > p) break;
+      const Cx<R> *row = op + (int64_t)l * P1;
+      Cx<R> s = q * row[0];
+      for (int k = 1; k <= l; ++k) cfma(s, row[k], sh[w][d][k]);
+      if (h == 0) acc0 = acc0 + s; else acc1 = acc1 + s;
+    }
+    Q += qd;
+  }
+  if (lane == 0) mQ[gp] = Q;
+  if (lane + 1 <= p) ma[gp * a.P + lane] = acc0;
+  if (lane + 33 <= p) ma[gp * a.P + lane + 32] = acc1;
 }
 
 // H lanes per target cell (the launcher uses H = 32); lane i of the group owns
@@ -253,21 +304,32 @@ k_m2l(ExpandArgs a, int64_t first, int64_t count, const int64_t *__restrict__ le
   if (li + H <= p) lb[gt * a.P + li + H - 1] = acc1;
 }
 
-// H lanes per child cell (the launcher uses H = 32); adds the shifted parent
-// local; lane i of the group owns coefficients i and i+H.
-template <typename R, int H>
+// One warp per child cell; adds the shifted parent local in place; lane i
+// owns coefficients i and i+32.  The cell's own local, its class and its
+// parent slot are fetched together, then the parent's local.
+template <typename R>
 __global__ void __launch_bounds__(32 * WPB)
 k_l2l(ExpandArgs a, Geo g, int level, int64_t first, int64_t count, const int *__restrict__ map,
       const uint32_t *__restrict__ cell_key, const uint8_t *__restrict__ cell_cls,
-      const Cx<R> *__restrict__ ops, double *__restrict__ lL0, Cx<R> *__restrict__ lb) {
-  constexpr int CPW = 32 / H;
-  __shared__ Cx<R> sh[WPB * CPW][MAXP + 1];
+      const Cx<R> *__restrict__ ops, int n_staged, double *__restrict__ lL0,
+      Cx<R> *__restrict__ lb) {
+  __shared__ Cx<R> sh[WPB][MAXP + 1];
+  extern __shared__ __align__(16) unsigned char dyn_ops[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int li = lane % H, sub = lane / H, slot = w * CPW + sub;
-  const unsigned mask = H == 32 ? 0xffffffffu : (0xffffu << (16 * sub));
-  const int64_t ci = (blockIdx.x * (int64_t)WPB + w) * CPW + sub;
-  if (ci >= count) return;
-  const int64_t gc = first + ci;
+  const int64_t ci = blockIdx.x * (int64_t)WPB + w;
+  const bool valid = ci < count;
+  const int64_t gc = first + (valid ? ci : 0);
+  const int p = a.p, P1 = p + 1;
+  const int k0 = lane, k1 = lane + 32;
+  // the cell's own fields (fetched together with the operator table)
+  const int cls = cell_cls[gc];
+  Cx<R> own0 = {(R)0, (R)0}, own1 = {(R)0, (R)0};
+  double L0 = 0.0;
+  if (valid) {
+    if (k0 == 0) L0 = lL0[gc];
+    else if (k0 <= p) own0 = lb[gc * a.P + k0 - 1];
+    if (k1 <= p) own1 = lb[gc * a.P + k1 - 1];
+  }
   int ps;
   if (a.parent) {
     ps = a.parent[gc];
@@ -276,23 +338,29 @@ k_l2l(ExpandArgs a, Geo g, int level, int64_t first, int64_t count, const int *_
     const uint32_t pkey = (g.tiling == FMM2D_SEPT) ? key / 7u : key >> 2;
     ps = map[g.map_off[level - 1] + pkey];
   }
-  const int p = a.p, P1 = p + 1;
-  for (int k = li; k < p; k += H) sh[slot][k + 1] = lb[(int64_t)ps * a.P + k];
-  __syncwarp(mask);
-  const Cx<R> *U = ops + (int64_t)cell_cls[gc] * P1 * P1;
+  const Cx<R> *op_tab = ops;
+  if (n_staged > 0) {   // the operators in shared memory: every cell reads them
+    Cx<R> *so = reinterpret_cast<Cx<R> *>(dyn_ops);
+    for (int i = threadIdx.x; i < n_staged; i += blockDim.x) so[i] = ops[i];
+    __syncthreads();
+    op_tab = so;
+  }
+  if (!valid) return;
+  // the parent's local
+  double Lp = 0.0;
+  if (k0 == 0) Lp = lL0[ps];
+  for (int k = lane; k < p; k += 32) sh[w][k + 1] = lb[(int64_t)ps * a.P + k];
+  __syncwarp();
+  const Cx<R> *U = op_tab + (int64_t)cls * P1 * P1;
 #pragma unroll
-  for (int h = 0; h < 64 / H; ++h) {
-    const int k = li + H * h;
+  for (int h = 0; h < 2; ++h) {
+    const int k = h == 0 ? k0 : k1;
     if (k > p) break;
     const Cx<R> *row = U + (int64_t)k * P1;
     Cx<R> s = {(R)0, (R)0};
-    for (int l = (k > 1 ? k : 1); l <= p; ++l) cfma(s, row[l], sh[slot][l]);
-    if (k == 0) {
-      lL0[gc] += lL0[ps] + (double)s.x;
-    } else {
-      Cx<R> cur = lb[gc * a.P + k - 1];
-      lb[gc * a.P + k - 1] = cur + s;
-    }
+    for (int l = (k > 1 ? k : 1); l <= p; ++l) cfma(s, row[l], sh[w][l]);
+    if (k == 0) lL0[gc] = L0 + (Lp + (double)s.x);
+    else lb[gc * a.P + k - 1] = (h == 0 ? own0 : own1) + s;
   }
 }
 
@@ -334,6 +402,15 @@ k_l2p(ExpandArgs a, const R *__restrict__ tgt, int tstride, const int *__restric
 
 inline unsigned wblocks(int64_t n) { return (unsigned)((n + WPB - 1) / WPB); }
 
+// Entries of the M2M / L2L operator table a block stages in shared memory
+// (0: the table stays in global memory): all of it when it fits beside the
+// kernel's static shared memory within the 48 KB a launch gets by default.
+template <typename R>
+inline int staged_ops(const ExpandArgs &a, size_t static_bytes) {
+  const int64_t n = (int64_t)a.n_cls * (a.p + 1) * (a.p + 1);
+  return n > 0 && static_bytes + n * sizeof(Cx<R>) <= 48 * 1024 ? (int)n : 0;
+}
+
 }  // namespace
 
 template <typename R>
@@ -363,10 +440,9 @@ cudaError_t launch_m2m(const ExpandArgs &a, const Geo &g, int level, int64_t fir
                        const uint8_t *cell_hsrc, const Cx<R> *ops, double *mQ, Cx<R> *ma,
                        cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  // a whole warp per cell: measured faster than two cells per warp (H = 16)
-  // even when half the lanes idle (p < 16)
-  k_m2m<R, 32><<<wblocks(count), 32 * WPB, 0, s>>>(a, g, level, first, count, map, cell_key,
-                                                    cell_cls, cell_hsrc, ops, mQ, ma);
+  const int n_st = staged_ops<R>(a, sizeof(Cx<R>) * WPB * 7 * (MAXP + 1));
+  k_m2m<R><<<wblocks(count), 32 * WPB, n_st * sizeof(Cx<R>), s>>>(
+      a, g, level, first, count, map, cell_key, cell_cls, cell_hsrc, ops, n_st, mQ, ma);
   return cudaGetLastError();
 }
 
@@ -387,8 +463,9 @@ cudaError_t launch_l2l(const ExpandArgs &a, const Geo &g, int level, int64_t fir
                        const int *map, const uint32_t *cell_key, const uint8_t *cell_cls,
                        const Cx<R> *ops, double *lL0, Cx<R> *lb, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  k_l2l<R, 32><<<wblocks(count), 32 * WPB, 0, s>>>(a, g, level, first, count, map, cell_key,
-                                                    cell_cls, ops, lL0, lb);
+  const int n_st = staged_ops<R>(a, sizeof(Cx<R>) * WPB * (MAXP + 1));
+  k_l2l<R><<<wblocks(count), 32 * WPB, n_st * sizeof(Cx<R>), s>>>(
+      a, g, level, first, count, map, cell_key, cell_cls, ops, n_st, lL0, lb);
   return cudaGetLastError();
 }
 

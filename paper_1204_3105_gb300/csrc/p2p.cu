@@ -464,14 +464,64 @@ __device__ __forceinline__ void x2_kahan(float &s, float &e, float x) {
   s = t;
 }
 
-// Staged sources q0, q0 + K, ... < q1.  Plain form: partial sums of at most
-// 64 sources are folded into the compensated running sums.  COMP (the hybrid
-// precision form): r^2 in float-float from hi + lo coordinates, log2 r^2 as
+// Plain form: the staged sources of a group as pair records of 48 bytes,
+// rec[3j] = (-x, -x, -y, -y) of source 2j, rec[3j + 1] the same of source
+// 2j + 1 and rec[3j + 2] = (u, u) of both; a thread walks a contiguous run of
+// records with 32-bit shared addresses and immediate offsets, so a pair of
+// sources costs three 16-byte shared loads and no index arithmetic.
+constexpr uint32_t X2_REC = 48;
+
+__device__ __forceinline__ float4 x2_lds4(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(a));
+  return v;
+}
+
+// Records a, a + st, ... < e (shared byte addresses; st = K records for
+// source slice k) against the thread's four targets; partial sums of at most
+// 64 sources are folded into the compensated sums.
+template <bool CHECK>
+__device__ __forceinline__ void x2_pairs(uint32_t a, const uint32_t e, const uint32_t st,
+                                         const float2 &xab, const float2 &xcd, const float2 &yab,
+                                         const float2 &ycd, float (&s)[4], float (&c)[4]) {
+  while (a < e) {
+    const uint32_t be = min(e, a + 32 * st);
+    // two accumulator sets (even / odd sources) halve the loop-carried FFMA chain
+    float2 acc_ab = make_float2(0.f, 0.f), acc_cd = make_float2(0.f, 0.f);
+    float2 acc_ab1 = make_float2(0.f, 0.f), acc_cd1 = make_float2(0.f, 0.f);
+    for (; a + st < be; a += 2 * st) {
+      const uint32_t b = a + st;
+      const float4 x0 = x2_lds4(a), x1 = x2_lds4(a + 16), u01 = x2_lds4(a + 32);
+      const float4 x2 = x2_lds4(b), x3 = x2_lds4(b + 16), u23 = x2_lds4(b + 32);
+      x2_source<CHECK>(x0, make_float2(u01.x, u01.y), xab, xcd, yab, ycd, acc_ab, acc_cd);
+      x2_source<CHECK>(x1, make_float2(u01.z, u01.w), xab, xcd, yab, ycd, acc_ab1, acc_cd1);
+      x2_source<CHECK>(x2, make_float2(u23.x, u23.y), xab, xcd, yab, ycd, acc_ab, acc_cd);
+      x2_source<CHECK>(x3, make_float2(u23.z, u23.w), xab, xcd, yab, ycd, acc_ab1, acc_cd1);
+    }
+    if (a < be) {
+      const float4 x0 = x2_lds4(a), x1 = x2_lds4(a + 16), u01 = x2_lds4(a + 32);
+      x2_source<CHECK>(x0, make_float2(u01.x, u01.y), xab, xcd, yab, ycd, acc_ab, acc_cd);
+      x2_source<CHECK>(x1, make_float2(u01.z, u01.w), xab, xcd, yab, ycd, acc_ab1, acc_cd1);
+      a += st;
+    }
+    acc_ab = __fadd2_rn(acc_ab, acc_ab1);
+    acc_cd = __fadd2_rn(acc_cd, acc_cd1);
+    x2_kahan(s[0], c[0], acc_ab.x);
+    x2_kahan(s[1], c[1], acc_ab.y);
+    x2_kahan(s[2], c[2], acc_cd.x);
+    x2_kahan(s[3], c[3], acc_cd.y);
+  }
+}
+
+// Hybrid precision form (COMP), staged sources q0, q0 + K, ... < q1: r^2 in
+// float-float from hi + lo coordinates, log2 r^2 as
 // its exact exponent plus a table-driven float-float log2 of the mantissa,
 // exact products with the strength and error-free sums (TwoSum): each term
 // is accurate to about 2^-31 of |u| instead of ~2^-23.
 template <bool CHECK, bool COMP>
-__device__ __forceinline__ void x2_slice(const float4 *sxy, const float4 *slo, const float2 *su,
+__device__ __forceinline__ void x2_slice(const float4 *sxy, const float4 *slo,
                                          const float4 *su4, const float4 *tab, int q0, int q1, int K,
                                          const float2 &xab,
                                          const float2 &xcd, const float2 &yab, const float2 &ycd,
@@ -535,29 +585,6 @@ __device__ __forceinline__ void x2_slice(const float4 *sxy, const float4 *slo, c
     x2_kahan(s[1], c[1], nc_ab.y);
     x2_kahan(s[2], c[2], nc_cd.x);
     x2_kahan(s[3], c[3], nc_cd.y);
-    return;
-  }
-  int q = q0;
-  while (q < q1) {
-    // two accumulator sets (even / odd sources) halve the loop-carried FFMA chain
-    float2 acc_ab = make_float2(0.f, 0.f), acc_cd = make_float2(0.f, 0.f);
-    float2 acc_ab1 = make_float2(0.f, 0.f), acc_cd1 = make_float2(0.f, 0.f);
-    const int qe = min(q1, q + 64 * K);
-#pragma unroll 2
-    for (; q + K < qe; q += 2 * K) {
-      x2_source<CHECK>(sxy[q], su[q], xab, xcd, yab, ycd, acc_ab, acc_cd);
-      x2_source<CHECK>(sxy[q + K], su[q + K], xab, xcd, yab, ycd, acc_ab1, acc_cd1);
-    }
-    if (q < qe) {
-      x2_source<CHECK>(sxy[q], su[q], xab, xcd, yab, ycd, acc_ab, acc_cd);
-      q += K;
-    }
-    acc_ab = __fadd2_rn(acc_ab, acc_ab1);
-    acc_cd = __fadd2_rn(acc_cd, acc_cd1);
-    x2_kahan(s[0], c[0], acc_ab.x);
-    x2_kahan(s[1], c[1], acc_ab.y);
-    x2_kahan(s[2], c[2], acc_cd.x);
-    x2_kahan(s[3], c[3], acc_cd.y);
   }
 }
 
@@ -573,9 +600,9 @@ k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_ids,
          const int *__restrict__ order) {
   constexpr int CAPB = COMP ? X2_CAP_COMP : X2_CAP;
   constexpr int G = P2P_TH / T, CAP = CAPB / G;
-  __shared__ float4 s_xy[CAPB];
+  __shared__ float4 s_xy[COMP ? CAPB : 1];
   __shared__ float4 s_lo[COMP ? CAPB : 1];
-  __shared__ float2 s_u[COMP ? 1 : CAPB];
+  __shared__ float4 s_rec[COMP ? 1 : 3 * CAPB / 2];   // plain form: pair records
   __shared__ float4 s_u4[COMP ? CAPB : 1];   // (uh, uh, ul, ul): strength split in two
   __shared__ float4 s_lg[COMP ? 128 : 1];    // log2 table of the hybrid form
   __shared__ float s_red[2][4][P2P_TH];
@@ -599,9 +626,9 @@ k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_ids,
   const int n_all = CSR ? near_off[li + 1] - near_off[li] : near_cnt[li];
   const int *nall = CSR ? near_src + near_off[li] : near_src + li * NEAR_MAX;
   const bool single = !CSR || n_all <= NEAR_MAX;
-  float4 *sxy = s_xy + grp * CAP;
+  float4 *sxy = COMP ? s_xy + grp * CAP : s_xy;
   float4 *slo = COMP ? s_lo + grp * CAP : s_lo;
-  float2 *su = COMP ? s_u : s_u + grp * CAP;   // (u, u); the hybrid form uses su4
+  float4 *srec = COMP ? s_rec : s_rec + grp * (3 * CAP / 2);
   float4 *su4 = COMP ? s_u4 + grp * CAP : s_u4;
   const float4 *src = reinterpret_cast<const float4 *>(src4);
   const double2 cg = ctr[g];
@@ -651,9 +678,17 @@ k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_ids,
           su4[q - c0] = make_float4(v.z, v.z, v.w, v.w);
         } else {
           const float x = -(v.x + dcx), y = -(v.y + dcy);
-          sxy[q - c0] = make_float4(x, x, y, y);
-          su[q - c0] = make_float2(v.z, v.z);
+          const int j = (q - c0) >> 1, h = (q - c0) & 1;
+          srec[3 * j + h] = make_float4(x, x, y, y);
+          reinterpret_cast<float2 *>(&srec[3 * j + 2])[h] = make_float2(v.z, v.z);
         }
+      }
+    }
+    if constexpr (!COMP) {   // an odd count: the last record's second source has u = 0
+      if (tg == 0 && ((c1 - c0) & 1)) {
+        const int j = (c1 - c0) >> 1;
+        srec[3 * j + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        reinterpret_cast<float2 *>(&srec[3 * j + 2])[1] = make_float2(0.f, 0.f);
       }
     }
   };
@@ -707,12 +742,23 @@ k_p2p_x2(int64_t leaf_first, int64_t n_leaves, const int *__restrict__ leaf_ids,
         if (act) {
           const int m = c1 - c0;
           const int self_end = max(0, min(m, n_self - c0));
-          const int first_unchecked = self_end + ((k - self_end) % K + K) % K;
-          if (self_end > 0)
-            x2_slice<true, COMP>(sxy, slo, su, su4, s_lg, k, self_end, K, xab, xcd, yab, ycd, xlab, xlcd,
-                                 ylab, ylcd, s, c);
-          x2_slice<false, COMP>(sxy, slo, su, su4, s_lg, first_unchecked, m, K, xab, xcd, yab, ycd, xlab,
-                                xlcd, ylab, ylcd, s, c);
+          if constexpr (COMP) {
+            const int first_unchecked = self_end + ((k - self_end) % K + K) % K;
+            if (self_end > 0)
+              x2_slice<true, COMP>(sxy, slo, su4, s_lg, k, self_end, K, xab, xcd, yab, ycd, xlab,
+                                   xlcd, ylab, ylcd, s, c);
+            x2_slice<false, COMP>(sxy, slo, su4, s_lg, first_unchecked, m, K, xab, xcd, yab, ycd,
+                                  xlab, xlcd, ylab, ylcd, s, c);
+          } else {
+            // slice k: records k, k + K, ...; records holding a source of
+            // the target's own leaf take the coincidence check
+            const int nrec = (m + 1) >> 1, rself = (self_end + 1) >> 1;
+            const int ru = rself + ((k - rself) % K + K) % K;
+            const uint32_t base = (uint32_t)__cvta_generic_to_shared(srec), st = K * X2_REC;
+            if (k < rself)
+              x2_pairs<true>(base + k * X2_REC, base + rself * X2_REC, st, xab, xcd, yab, ycd, s, c);
+            x2_pairs<false>(base + ru * X2_REC, base + nrec * X2_REC, st, xab, xcd, yab, ycd, s, c);
+          }
         }
       }
     }

@@ -258,6 +258,7 @@ cudaError_t ad_launch_p2l(int64_t n_cells, const int *x_off, const int *x_src, c
 // ---------------------------------------------------------------- expand.cu
 struct ExpandArgs {
   int p, P, L, l_min, b;
+  int n_cls = 0;                      // M2M / L2L operators in the table (child classes)
   int64_t leaf_first, n_leaves;
   double inv_s_re, inv_s_im;          // 1 / s_L
   // adaptive tree (null for the uniform one): leaf li is cell leaf_ids[li],
