@@ -196,7 +196,8 @@ fmm2d_status fmm2d_plan_set_domain(fmm2d_plan *plan, double x0, double y0, doubl
  * memory; the caller may reuse its buffers after the call returns.  The call
  * synchronises `stream` once to read back the per-level cell counts.
  * Errors: FMM2D_EINVAL, FMM2D_ENOMEM, FMM2D_EDOMAIN (plan left unbuilt),
- * FMM2D_ECUDA.
+ * FMM2D_ETIMEOUT (a bounded wait between tiles of the radix sort gave up;
+ * plan left unbuilt), FMM2D_ECUDA.
  */
 fmm2d_status fmm2d_build(fmm2d_plan *plan, const void *src_xy_dev, int64_t n_src,
                          const void *tgt_xy_dev, int64_t n_tgt, void *stream);
@@ -213,7 +214,8 @@ fmm2d_status fmm2d_build(fmm2d_plan *plan, const void *src_xy_dev, int64_t n_src
  * level.  offsets: HOST array of n_inst + 1 non-decreasing int64, offsets[0]
  * = 0.  The paper has no batched form; each instance is the FMM of Sec. 2.
  * Errors: FMM2D_EINVAL (not adaptive, bad offsets, too many instances for the
- * finest level), FMM2D_ENOMEM, FMM2D_EDOMAIN, FMM2D_ECUDA.
+ * finest level), FMM2D_ENOMEM, FMM2D_EDOMAIN, FMM2D_ETIMEOUT (as fmm2d_build),
+ * FMM2D_ECUDA.
  */
 fmm2d_status fmm2d_build_forest(fmm2d_plan *plan, const void *xy_dev, const int64_t *offsets,
                                 int n_inst, void *stream);
@@ -395,7 +397,7 @@ fmm2d_status fmm2d_autotune(int tiling, double eps, unsigned flags, const double
  * domain-error flag into host memory), so it must not be made while a stream
  * is being captured.  All calls share the array, so calls whose GPU work
  * overlaps race and must be serialised by the caller.  Errors: FMM2D_EINVAL, FMM2D_EDOMAIN,
- * FMM2D_ECUDA.
+ * FMM2D_ETIMEOUT (a bounded wait of the radix sort gave up), FMM2D_ECUDA.
  */
 fmm2d_status fmm2d_keys_sort_noalloc(int tiling, int levels, double leaf_scale,
                                      const double *domain, const void *xy_dev, int64_t n,

@@ -888,14 +888,14 @@ cudaError_t ad_launch_lists_emit(const Geo &g, const Stencils *d_sten, int l, in
 
 cudaError_t ad_group(int64_t n, const int *tgt, const int *src, const int *map, int n_groups,
                      uint32_t *key, uint32_t *idx, uint32_t *tmp_k, uint32_t *tmp_v, void *scratch,
-                     int *cnt, int *off, int *out_src, cudaStream_t s) {
+                     int *cnt, int *off, int *out_src, cudaStream_t s, int *err) {
   cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)(n_groups + 1) * sizeof(int), s);
   if (e != cudaSuccess) return e;
   if (n > 0) {
     k_ad_keys_of<<<nblk(n, 256), 256, 0, s>>>(n, tgt, map, n_groups, key, idx);
     int bits = 1;
     while ((1ll << bits) <= (int64_t)n_groups) ++bits;
-    e = radix_sort_pairs(key, idx, tmp_k, tmp_v, n, bits, scratch, s);
+    e = radix_sort_pairs(key, idx, tmp_k, tmp_v, n, bits, scratch, s, err);
     if (e != cudaSuccess) return e;
     k_ad_count<<<nblk(n, 256), 256, 0, s>>>(n, key, cnt);
     k_ad_gather<<<nblk(n, 256), 256, 0, s>>>(n, idx, src, out_src);

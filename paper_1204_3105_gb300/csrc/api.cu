@@ -900,16 +900,18 @@ static fmm2d_status build_adaptive(fmm2d_plan *pl, const void *src, int64_t n_sr
     while (sbits < 32 && ((uint64_t)1 << sbits) < span * (uint64_t)n_inst) ++sbits;
   }
   {
-    StageScope sc(pl, ST_SORT, s, 1);
+    StageScope sc(pl, ST_SORT, s,
+                  radix_sort_launches(n_src, sbits) + (pl->same_sets ? 0 : radix_sort_launches(n_tgt, sbits)));
     CK(radix_sort_pairs(ks, ps, (uint32_t *)pl->d_tmp_k.p, (uint32_t *)pl->d_tmp_v.p, n_src, sbits,
-                        pl->d_sort_scratch.p, s), "sort");
+                        pl->d_sort_scratch.p, s, (int *)pl->d_err.p), "sort");
     if (!pl->same_sets)
       CK(radix_sort_pairs(kt, pt, (uint32_t *)pl->d_tmp_k.p, (uint32_t *)pl->d_tmp_v.p, n_tgt, sbits,
-                          pl->d_sort_scratch.p, s), "sort");
+                          pl->d_sort_scratch.p, s, (int *)pl->d_err.p), "sort");
   }
   int err_h = 0;
   CK(cudaMemcpyAsync(&err_h, pl->d_err.p, 4, cudaMemcpyDeviceToHost, s), "readback");
   CK(cudaStreamSynchronize(s), "keys sync");
+  if (err_h & 8) return fail(pl, FMM2D_ETIMEOUT, "a bounded wait of the radix sort gave up");
   if (err_h) return fail(pl, FMM2D_EDOMAIN, "a point lies outside the domain square or root cell");
 
   // ---- cell capacity: a split cell holds more than leaf_cap sources or
@@ -1115,7 +1117,8 @@ static fmm2d_status build_adaptive(fmm2d_plan *pl, const void *src, int64_t n_sr
     auto group = [&](int64_t n, DBuf &t, DBuf &sr, const int *map, int ngroups, DBuf &off, DBuf &out) {
       return ad_group(n, (const int *)t.p, (const int *)sr.p, map, ngroups, (uint32_t *)pl->d_ad_flag.p,
                       (uint32_t *)pl->d_ad_pos.p, (uint32_t *)pl->d_tmp_k.p, (uint32_t *)pl->d_tmp_v.p,
-                      pl->d_sort_scratch.p, (int *)pl->d_ad_cnt.p, (int *)off.p, (int *)out.p, s);
+                      pl->d_sort_scratch.p, (int *)pl->d_ad_cnt.p, (int *)off.p, (int *)out.p, s,
+                      (int *)pl->d_err.p);
     };
     CK(group(n_u, pl->d_ad_ut, pl->d_ad_us, (const int *)pl->d_leaf_pos.p, n_leaves, pl->d_u_off, pl->d_u_src), "group U");
     CK(group(n_w, pl->d_ad_wt, pl->d_ad_ws, (const int *)pl->d_leaf_pos.p, n_leaves, pl->d_w_off, pl->d_w_src), "group W");
@@ -1143,7 +1146,10 @@ static fmm2d_status build_adaptive(fmm2d_plan *pl, const void *src, int64_t n_sr
   int bin_h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   if (pl->p2p_binned)
     CK(cudaMemcpyAsync(bin_h, pl->d_p2p_cnt.p, sizeof(bin_h), cudaMemcpyDeviceToHost, s), "readback");
+  int err_g = 0;   // the sorts of the list grouping
+  CK(cudaMemcpyAsync(&err_g, pl->d_err.p, 4, cudaMemcpyDeviceToHost, s), "readback");
   CK(cudaStreamSynchronize(s), "build sync");
+  if (err_g & 8) return fail(pl, FMM2D_ETIMEOUT, "a bounded wait of the radix sort gave up");
   for (int k = 0; k < 4; ++k) pl->p2p_bin_count[k] = bin_h[k];
   CK(tc_prepare_split(pl), "alloc");
   CK(cudaGetLastError(), "build");
@@ -1585,15 +1591,13 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
                      (int *)pl->d_err.p + 2), "keys");
   }
   {
-    const int per_pass = (int64_t)256 * ((std::max<int64_t>(1, nmax) + 4095) / 4096) <= 8192 ? 3 : 5;
-    const int per_sort = n_src > 1 ? per_pass * ((bits + 7) / 8) : 0;
-    const int per_sort_t = n_tgt > 1 ? per_pass * ((bits + 7) / 8) : 0;
-    StageScope sc(pl, ST_SORT, s, per_sort + (pl->same_sets ? 0 : per_sort_t));
+    StageScope sc(pl, ST_SORT, s,
+                  radix_sort_launches(n_src, bits) + (pl->same_sets ? 0 : radix_sort_launches(n_tgt, bits)));
     CK(radix_sort_pairs(ks, ps, (uint32_t *)pl->d_tmp_k.p, (uint32_t *)pl->d_tmp_v.p, n_src, bits,
-                        pl->d_sort_scratch.p, s), "sort");
+                        pl->d_sort_scratch.p, s, (int *)pl->d_err.p), "sort");
     if (!pl->same_sets)
       CK(radix_sort_pairs(kt, pt, (uint32_t *)pl->d_tmp_k.p, (uint32_t *)pl->d_tmp_v.p, n_tgt, bits,
-                          pl->d_sort_scratch.p, s), "sort");
+                          pl->d_sort_scratch.p, s, (int *)pl->d_err.p), "sort");
   }
   // ---- capacities: a level holds at most min(b^l, points) occupied cells,
   // so every later buffer and launch can be sized before the counts are known
@@ -1632,7 +1636,7 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
   CK(dbuf_reserve(pl->d_near_src, cap_leaf * NEAR_MAX * 4), "alloc");
   pl->cls_cap = cap_list;
   {
-    StageScope sc(pl, ST_TREE, s, (pl->same_sets ? 1 : 2) + (ms <= 8192 ? 1 : 3) + 1);
+    StageScope sc(pl, ST_TREE, s, (pl->same_sets ? 1 : 2) + exclusive_scan_launches(ms) + 1);
     CK(cudaMemsetAsync(pl->d_occ.p, 0, ms * 4, s), "memset");
     CK(cudaMemsetAsync(pl->d_hsrc.p, 0, ms * 4, s), "memset");
     CK(launch_mark(g, ks, n_src, (int *)pl->d_occ.p, (int *)pl->d_hsrc.p, s), "mark");
@@ -1700,6 +1704,7 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
   CK(cudaMemcpyAsync(lev_first_h, pl->d_lev_first.p, (L + 2) * 8, cudaMemcpyDeviceToHost, s), "readback");
   CK(cudaMemcpyAsync(&err_h, pl->d_err.p, 4, cudaMemcpyDeviceToHost, s), "readback");
   CK(cudaStreamSynchronize(s), "build sync");
+  if (err_h & 8) return fail(pl, FMM2D_ETIMEOUT, "a bounded wait of the radix sort gave up");
   if (err_h) return fail(pl, FMM2D_EDOMAIN, "a point lies outside the domain square or root cell");
   for (int l = 0; l <= L + 1; ++l) pl->lev_first[l] = lev_first_h[l];
   pl->n_cells = lev_first_h[L + 1];

@@ -22,7 +22,7 @@ constexpr int64_t kMaxPoints = 1 << 20;
 constexpr size_t kTmpKeyOff = 0;
 constexpr size_t kTmpValOff = kTmpKeyOff + 4 * (size_t)kMaxPoints;
 constexpr size_t kSortOff = kTmpValOff + 4 * (size_t)kMaxPoints;
-constexpr size_t kSortBytes = 512 * 1024;
+constexpr size_t kSortBytes = 2304 * 1024;
 constexpr size_t kErrOff = kSortOff + kSortBytes;
 constexpr size_t kScratchBytes = kErrOff + 256;
 constexpr int kMaxDevices = 64;
@@ -134,13 +134,17 @@ extern "C" fmm2d_status fmm2d_keys_sort_noalloc(int tiling, int levels, double l
     e = launch_keys(g, xy_dev, (flags & FMM2D_IN_F32) != 0, n, keys_sorted_dev, perm_dev, err, s);
   if (e == cudaSuccess)
     e = radix_sort_pairs(keys_sorted_dev, perm_dev, (uint32_t *)(base + kTmpKeyOff),
-                         (uint32_t *)(base + kTmpValOff), n, bits, base + kSortOff, s);
+                         (uint32_t *)(base + kTmpValOff), n, bits, base + kSortOff, s, err);
   int err_h = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&err_h, err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     set_msg(err_buf, err_cap, cudaGetErrorString(e));
     return FMM2D_ECUDA;
+  }
+  if (err_h & 8) {
+    set_msg(err_buf, err_cap, "a bounded wait of the radix sort gave up");
+    return FMM2D_ETIMEOUT;
   }
   if (err_h) {
     set_msg(err_buf, err_cap, "a point lies outside the domain square or root cell");

@@ -159,9 +159,15 @@ cudaError_t launch_keys(const Geo &g, const void *xy, bool f32, int64_t n, uint3
 
 // ---------------------------------------------------------------- sort.cu
 size_t radix_sort_scratch_bytes(int64_t n);
-// Stable LSD sort of (key, val) pairs on the low `bits` bits; result in keys/vals.
+// Stable LSD sort of (key, val) pairs on the low `bits` bits; result in
+// keys/vals.  A look-back wait that gives up ORs 8 into *err (when err is
+// given; the output is then invalid but every write stays in bounds).
 cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *tmp_k, uint32_t *tmp_v,
-                             int64_t n, int bits, void *scratch, cudaStream_t s);
+                             int64_t n, int bits, void *scratch, cudaStream_t s,
+                             int *err = nullptr);
+// Kernel launches of one radix_sort_pairs / exclusive_scan call.
+int radix_sort_launches(int64_t n, int bits);
+int exclusive_scan_launches(int64_t n);
 size_t scan_scratch_bytes(int64_t n);
 // Exclusive prefix sum of int32 values; out may alias in.
 cudaError_t exclusive_scan(const int *in, int *out, int64_t n, void *scratch, cudaStream_t s);
@@ -243,7 +249,7 @@ cudaError_t ad_launch_lists_emit(const Geo &g, const Stencils *d_sten, int l, in
 // is given): CSR offsets off[0..n_groups] and the sources in group order.
 cudaError_t ad_group(int64_t n, const int *tgt, const int *src, const int *map, int n_groups,
                      uint32_t *key, uint32_t *idx, uint32_t *tmp_k, uint32_t *tmp_v, void *scratch,
-                     int *cnt, int *off, int *out_src, cudaStream_t s);
+                     int *cnt, int *off, int *out_src, cudaStream_t s, int *err = nullptr);
 template <typename R>
 cudaError_t ad_launch_m2p(int64_t n_leaves, const int *leaf_ids, const int *w_off, const int *w_src,
                           const R *tgt, int tstride, const int *ts, const int *te,

@@ -15,16 +15,27 @@ namespace fmm2d {
 
 namespace {
 
+// The first point (in sorted order) of every occupied cell of every level
+// marks that cell: the point whose leaf key starts a run marks its leaf and
+// then each ancestor up to the first one it shares with the point before it,
+// so every flag is written once (no write contention on the top levels).
 __global__ void k_mark(Geo g, const uint32_t *__restrict__ key, int64_t n, int *__restrict__ occ,
                        int *__restrict__ hsrc) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t k = key[i];
-  if (i > 0 && key[i - 1] == k) return;
+  const bool first = i == 0;
+  uint32_t kp = first ? 0u : key[i - 1];
+  if (!first && kp == k) return;
   for (int l = g.L; l >= 0; --l) {
-    uint32_t kl = parent_key(g.tiling, k, g.L - l);
-    occ[g.map_off[l] + kl] = 1;
-    if (hsrc) hsrc[g.map_off[l] + kl] = 1;
+    occ[g.map_off[l] + k] = 1;
+    if (hsrc) hsrc[g.map_off[l] + k] = 1;
+    if (l == 0) break;
+    k = parent_key(g.tiling, k, 1);
+    if (!first) {
+      kp = parent_key(g.tiling, kp, 1);
+      if (kp == k) break;   // this ancestor and all above it are marked by earlier points
+    }
   }
 }
 
