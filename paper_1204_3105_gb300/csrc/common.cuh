@@ -58,13 +58,19 @@ FMM_HD uint32_t morton(uint32_t i, uint32_t j) { return spread_bits(i) | (spread
 
 // ---------------------------------------------------------------- septree
 // digit d -> unit w^(d-1) = (A, B) meaning A + B w; index 0 is the zero digit.
-FMM_HD int unit_a(int d) { const int t[7] = {0, 1, 0, -1, -1, 0, 1}; return t[d]; }
-FMM_HD int unit_b(int d) { const int t[7] = {0, 0, 1, 1, 0, -1, -1}; return t[d]; }
-// residue (a + 3b) mod 7 -> digit, since w = 3 (mod beta) in Z[w]/(beta) = Z/7.
-FMM_HD int residue_digit(int r) { const int t[7] = {0, 1, 3, 2, 5, 6, 4}; return t[r]; }
+// (Tables packed into integer constants, 2 or 3 bits an entry, so that a
+// lookup is a shift and a mask rather than an indexed local array.)
+//   unit_a: 0, 1, 0, -1, -1, 0, 1      unit_b: 0, 0, 1, 1, 0, -1, -1
+FMM_HD int unit_a(int d) { return (int)((9241u >> (2 * d)) & 3u) - 1; }
+FMM_HD int unit_b(int d) { return (int)((421u >> (2 * d)) & 3u) - 1; }
+// residue (a + 3b) mod 7 -> digit, since w = 3 (mod beta) in Z[w]/(beta) = Z/7:
+//   0, 1, 3, 2, 5, 6, 4
+FMM_HD int residue_digit(int r) { return (int)((1266888u >> (3 * r)) & 7u); }
 
 FMM_HD int64_t floordiv7(int64_t v) { return v >= 0 ? v / 7 : -((-v + 6) / 7); }
 FMM_HD int mod7(int64_t v) { int r = (int)(v % 7); return r < 0 ? r + 7 : r; }
+FMM_HD int floordiv7_32(int v) { return v >= 0 ? v / 7 : -((-v + 6) / 7); }
+FMM_HD int mod7_32(int v) { int r = v % 7; return r < 0 ? r + 7 : r; }
 
 // Base-beta digits of a + b w; returns false if more than l digits are needed.
 FMM_HD bool eis_to_key(int64_t a, int64_t b, int l, uint32_t *key) {
@@ -76,6 +82,22 @@ FMM_HD bool eis_to_key(int64_t a, int64_t b, int l, uint32_t *key) {
     int64_t qa = 3 * a1 + 2 * b1, qb = b1 - 2 * a1;
     a = floordiv7(qa);
     b = floordiv7(qb);
+    k += (uint32_t)d * pw;
+    pw *= 7u;
+  }
+  *key = k;
+  return a == 0 && b == 0;
+}
+// The same in 32-bit arithmetic, for |a|, |b| < 2^27 (every lattice
+// coordinate of a tree of at most 16 levels).
+FMM_HD bool eis_to_key32(int a, int b, int l, uint32_t *key) {
+  uint32_t k = 0, pw = 1;
+  for (int i = 0; i < l; ++i) {
+    int d = residue_digit(mod7_32(a + 3 * b));
+    int a1 = a - unit_a(d), b1 = b - unit_b(d);
+    int qa = 3 * a1 + 2 * b1, qb = b1 - 2 * a1;
+    a = floordiv7_32(qa);
+    b = floordiv7_32(qb);
     k += (uint32_t)d * pw;
     pw *= 7u;
   }

@@ -230,8 +230,9 @@ __global__ void k_keys_fast(const T *__restrict__ xy, int64_t n, int tiling, int
       queue_exact(i, list, list_n);
       return;
     }
-    const int64_t bb = (int64_t)fb + (q_best & 1), bc = (int64_t)fc + (q_best >> 1);
-    if (!eis_to_key(bb, bc, L, &k)) {   // outside the root: the exact kernel reports it
+    // |fb|, |fc| <= 2.8 / (3 r) + 1, far below 2^27 for any supported depth
+    const int bb = (int)fb + (q_best & 1), bc = (int)fc + (q_best >> 1);
+    if (!eis_to_key32(bb, bc, L, &k)) {   // outside the root: the exact kernel reports it
       queue_exact(i, list, list_n);
       return;
     }

@@ -147,6 +147,7 @@ constexpr size_t RS_LB_OFF = RS_CTR_OFF + 256;          // uint64 [4][tiles][256
 // A look-back word: flag in the top two bits, a count below.
 constexpr uint64_t LB_LOCAL = 1ull << 62, LB_INCL = 2ull << 62, LB_COUNT = LB_LOCAL - 1;
 constexpr int LB_POLLS = 1 << 22;   // polls of one word before the wait gives up
+constexpr int LB_WIN = 8;           // look-back words read per round
 
 // Digit totals of every pass (atomics into the zeroed totals) and, for the
 // tile of this block, the look-back words of every pass set to "not yet".
@@ -234,27 +235,39 @@ k_radix_onesweep(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ 
   dstart[d] = ex;
   int dbase;
   block_excl_scan(hist[d], dbase, sm_scan);
-  // look-back: the counts of digit d in all earlier tiles
+  // look-back: the counts of digit d in all earlier tiles, LB_WIN words
+  // read at once per round (one memory latency per LB_WIN tiles walked)
   int64_t excl = 0;
   if (tile > 0) {
     int j = tile - 1, polls = 0;
-    while (j >= 0) {
-      const uint64_t v = lb_load(&lb[(int64_t)j * 256 + d]);
-      if (v & LB_INCL) {
-        excl += (int64_t)(v & LB_COUNT);
-        break;
+    bool done = false;
+    while (!done && j >= 0) {
+      uint64_t v[LB_WIN];
+#pragma unroll
+      for (int q = 0; q < LB_WIN; ++q) v[q] = j - q >= 0 ? lb_load(&lb[(int64_t)(j - q) * 256 + d]) : LB_INCL;
+      int used = 0;
+#pragma unroll
+      for (int q = 0; q < LB_WIN; ++q) {
+        if (done || used < q) continue;   // stop at the first word not yet published
+        if (v[q] & LB_INCL) {
+          excl += (int64_t)(v[q] & LB_COUNT);
+          done = true;
+        } else if (v[q] & LB_LOCAL) {
+          excl += (int64_t)(v[q] & LB_COUNT);
+          used = q + 1;
+        }
       }
-      if (v & LB_LOCAL) {
-        excl += (int64_t)(v & LB_COUNT);
-        --j;
+      j -= used;
+      if (done) break;
+      if (used > 0) {
         polls = 0;
-        continue;
+      } else {
+        if (++polls > LB_POLLS) {   // the earlier tile never published: give up
+          atomicOr(err, 8);
+          break;
+        }
+        if (polls > 32) __nanosleep(64);
       }
-      if (++polls > LB_POLLS) {   // the earlier tile never published: give up
-        atomicOr(err, 8);
-        break;
-      }
-      if (polls > 32) __nanosleep(64);
     }
     lb_store(&lb[(int64_t)tile * 256 + d], LB_INCL | (uint64_t)(excl + run));
   }
