@@ -36,7 +36,6 @@ namespace fmm2d {
 
 namespace {
 
-constexpr int TC_THREADS = 256;
 constexpr int TC_M = 128;
 constexpr int NACC = 8;                  // accumulators, entry e -> e % NACC
 constexpr long long WAIT_CYCLES = 2000000000ll;   // ~1 s at 2 GHz
@@ -63,12 +62,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait on one phase of an mbarrier; false on time-out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// Bounded wait on one phase of an mbarrier; false on time-out, or at once
+// when another thread of the CTA has set *abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          const volatile int *abort = nullptr) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (clock64() - t0 > WAIT_CYCLES) return false;
+    if (abort && *abort) return false;
   }
   return true;
 }
@@ -149,44 +154,71 @@ __host__ __device__ __forceinline__ uint32_t core_off(int row, int k, int K) {
   return (uint32_t)((row >> 3) * (K / 4) * 128 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
 }
 
-// Accumulator column stride and CTAs per SM for a shape.
+// Shape of one kernel instance: accumulator column stride, pipeline depths
+// and CTAs per SM.
 template <int K, int N> struct TcShape {
   static constexpr uint32_t ACC = N <= 32 ? 32 : 64;
   static constexpr uint32_t COLS = NACC * ACC;            // 256 or 512 TMEM columns
-  static constexpr int CTAS = N <= 32 ? 2 : 1;
-  static constexpr int NB = K <= 48 ? 4 : 2;              // operator stages
-  static constexpr int D = NB - 2;                        // operator prefetch distance
+  static constexpr int NA = K <= 32 ? 4 : 2;              // multipole (A) stages
+  static constexpr int NB = K <= 32 ? 4 : 2;              // operator (B) stages
   static constexpr uint32_t A_BYTES = 128 * K * 4, B_BYTES = N * K * 4;
-  static constexpr uint32_t SMEM = 2 * (2 * A_BYTES) + NB * (3 * B_BYTES);
+  static constexpr uint32_t SMEM = NA * (2 * A_BYTES) + NB * (3 * B_BYTES);
+  static constexpr int CTAS = (N <= 32 && SMEM <= 104 * 1024) ? 2 : 1;
+  static constexpr int PF = K <= 32 ? 2 : 1;              // gathered rows in flight per thread
 };
+
+// Warp roles of a CTA: warps 0-7 gather (two threads per target row, one
+// half of K each), split the rows into TF32 hi + lo and write the A stages,
+// then read the accumulators in the epilogue; warp 8 (one thread) issues the
+// MMAs; warp 9 (one thread) copies the operator tiles.  Hand-offs are
+// mbarriers only: a_full / b_full (stage written / landed), a_empty /
+// b_empty (stage read by the MMAs: tcgen05.commit), acc_full (a tile's MMAs
+// done) and acc_empty (its accumulators read).
+constexpr int TC_PROD = 256;                      // gathering threads
+constexpr int TC_THREADS = TC_PROD + 64;          // + MMA warp + operator warp
+constexpr int TC_MMA_WARP = 8, TC_LOAD_WARP = 9;
 
 template <int K, int N>
 __global__ void __launch_bounds__(TC_THREADS, (TcShape<K, N>::CTAS)) k_m2l_tc(TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   using SH = TcShape<K, N>;
   constexpr uint32_t A_BYTES = SH::A_BYTES, B_BYTES = SH::B_BYTES;
-  constexpr int NB = SH::NB, D = SH::D;
+  constexpr int NA = SH::NA, NB = SH::NB, PF = SH::PF;
   constexpr uint32_t SBO = (K / 4) * 128, LBO = 128;
   constexpr uint32_t IDESC = idesc_tf32(TC_M, N);
   constexpr uint32_t ACC = SH::ACC, COLS = SH::COLS;
   constexpr int QH = K / 8;                 // 16-byte chunks of a row per half
-  // layout: A stages [2] x (A0, A1), operator stages [NB] x (B0, B1, B2), then
-  // barriers: mma[2] (A stage released), full[NB] (operator landed), and one
-  // that nothing arrives on (the test switch a.debug_stall waits on it)
-  unsigned char *const Bbase = smem + 2 * (2 * A_BYTES);
+  // layout: A stages [NA] x (A0, A1), operator stages [NB] x (B0, B1, B2),
+  // then the barriers and a few words
+  unsigned char *const Bbase = smem + NA * (2 * A_BYTES);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SH::SMEM);
-  uint64_t *mma_bar = bars, *full_bar = bars + 2, *never_bar = bars + 2 + NB;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 3 + NB);
+  uint64_t *a_full = bars, *a_empty = bars + NA, *b_full = bars + 2 * NA,
+           *b_empty = bars + 2 * NA + NB, *acc_full = bars + 2 * NA + 2 * NB,
+           *acc_empty = acc_full + 1, *never_bar = acc_full + 2;
+  constexpr int NBARS = 2 * NA + 2 * NB + 3;
+  static_assert(NBARS * 8 + 8 + (MAX_CLASSES + 2) * 4 <= 1024, "barrier area");
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + NBARS);
   int *s_cnt = reinterpret_cast<int *>(tmem_slot + 2);               // [MAX_CLASSES]
   volatile int *s_abort = s_cnt + MAX_CLASSES;
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int row = tid & (TC_M - 1), half = tid >> 7;   // two threads per gathered row
+  volatile uint32_t *s_consumed = reinterpret_cast<volatile uint32_t *>(s_cnt + MAX_CLASSES + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  if (warp == 0) tmem_alloc(tmem_slot, COLS);
+  if (warp == TC_MMA_WARP) tmem_alloc(tmem_slot, COLS);
   if (tid == 0) {
-    for (int i = 0; i < 3 + NB; ++i) mbar_init(&bars[i], 1);
+    for (int i = 0; i < NA; ++i) {
+      mbar_init(&a_full[i], TC_PROD / 32);
+      mbar_init(&a_empty[i], 1);
+    }
+    for (int i = 0; i < NB; ++i) {
+      mbar_init(&b_full[i], 1);
+      mbar_init(&b_empty[i], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, TC_PROD / 32);
+    mbar_init(never_bar, 1);
     fence_barrier_init();
     *s_abort = 0;
+    *s_consumed = 0;
   }
   if (tid < MAX_CLASSES) s_cnt[tid] = tid < a.n_classes ? a.cls_cnt[tid] : 0;
   tc_fence_before();
@@ -196,116 +228,76 @@ __global__ void __launch_bounds__(TC_THREADS, (TcShape<K, N>::CTAS)) k_m2l_tc(Tc
   int total_tiles = 0;
   for (int c = 0; c < a.n_classes; ++c) total_tiles += (s_cnt[c] + TC_M - 1) / TC_M;
   const int S = a.split;                    // work item = (tile, part of its entries)
-
-  uint32_t it = 0;                          // entries processed so far (global over tiles)
-  uint32_t issued = 0;                      // operator copies issued (thread 0)
-  uint32_t landed = 0;                      // operator copies waited for (thread 0)
   const int p = a.p;
-  // thread 0: issue the operator copy of global entry u into stage u % NB
-  auto issue_b = [&](uint32_t u, int op) {
-    const int st = u % NB;
-    unsigned char *B0 = Bbase + st * (3 * B_BYTES);
-    mbar_expect_tx(&full_bar[st], 3 * B_BYTES);
-    bulk_g2s(B0, a.btab + (size_t)op * 3 * B_BYTES, 3 * B_BYTES, &full_bar[st]);
-    issued = u + 1;
-  };
-  for (int item = blockIdx.x; item < total_tiles * S; item += gridDim.x) {
+  // the work items of this CTA and their entry ranges (the same sequence for
+  // every role)
+  auto item_info = [&](int item, int &c, int &row0, int &nrows, int &e_lo, int &E) {
     const int tile = item / S, sidx = item - tile * S;
-    int c = 0, t0 = tile;
+    c = 0;
+    int t0 = tile;
     while (t0 >= (s_cnt[c] + TC_M - 1) / TC_M) {
       t0 -= (s_cnt[c] + TC_M - 1) / TC_M;
       ++c;
     }
-    const int row0 = t0 * TC_M;
-    const int nrows = min(TC_M, s_cnt[c] - row0);
-    const int g = row < nrows ? a.cls_cells[(int64_t)c * a.cls_cap + row0 + row] : -1;
-    const int64_t fi = g >= 0 ? (int64_t)g - a.far_first : 0;
-    double ls = 0.0;
-    if (g >= 0 && half == 0) {
-      int l = a.l_min;
-      while (l < a.L && (int64_t)g >= a.lev_first[l + 1]) ++l;
-      ls = a.log_abs_scale[l];
-    }
-    double L0 = 0.0;
-    // this item's stencil entries: [e_lo, e_lo + E) of the class's list
+    row0 = t0 * TC_M;
+    nrows = min(TC_M, s_cnt[c] - row0);
     const int E_all = a.sten_len[c];
     const int chunk = (E_all + S - 1) / S;
-    const int e_lo = min(E_all, sidx * chunk);
-    const int E = min(E_all, e_lo + chunk) - e_lo;
-    const uint16_t *ops_c = a.sten_ops + c * FAR_MAX + e_lo;
-    const int *srcs = a.far_full + fi * FAR_MAX + e_lo;
-    // software pipeline of the gather: the rows of entry e+1 are loaded while
-    // entry e is split, stored and multiplied; source indices two ahead
-    auto load_row = [&](int src, float4 (&f)[QH], double &q) {
-      const float4 *rowp = reinterpret_cast<const float4 *>(a.ma + (int64_t)(src >= 0 ? src : 0) * a.P);
-#pragma unroll
-      for (int qq = 0; qq < QH; ++qq) {
-        const int qi = half * QH + qq;
-        f[qq] = (src >= 0 && 4 * qi < 2 * p) ? rowp[qi] : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-      q = src >= 0 ? a.mQ[src] : 0.0;
-    };
-    int src = (g >= 0 && E > 0) ? srcs[0] : -1;
-    int src_n = (g >= 0 && E > 1) ? srcs[1] : -1;
-    float4 fc[QH];
-    double qc;
-    load_row(src, fc, qc);
-    for (int e = 0; e < E; ++e, ++it) {
-      const int s = it & 1;
-      const uint32_t use = it >> 1;
-      unsigned char *A0 = smem + s * (2 * A_BYTES), *A1 = A0 + A_BYTES;
-      // A stage s and operator stage (it + D) % NB were last read by the MMAs
-      // of entry it - 2
-      if (use >= 1) {
-        if (!mbar_wait(&mma_bar[s], (use - 1) & 1)) *s_abort = 1;
-      }
-      const int op = ops_c[e];
-      if (tid == 0 && !*s_abort) {
-        if (e == 0)
-          for (int d = 0; d < D && d < E; ++d) issue_b(it + d, ops_c[d]);
-        if (e + D < E) issue_b(it + D, ops_c[e + D]);
-      }
-      float4 fn[QH];
-      double qn = 0.0;
-      int src_nn = -1;
-      if (e + 1 < E) load_row(src_n, fn, qn);
-      if (g >= 0 && e + 2 < E) src_nn = srcs[e + 2];
-      // split the current row into TF32 A0 + A1 (Q sits at index 2p)
-      const float qf = (float)qc;
-#pragma unroll
-      for (int qq = 0; qq < QH; ++qq) {
-        const int q = half * QH + qq;
-        float v[4] = {fc[qq].x, fc[qq].y, fc[qq].z, fc[qq].w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int k = 4 * q + j;
-          v[j] = k < 2 * p ? v[j] : (k == 2 * p ? qf : 0.f);
+    e_lo = min(E_all, sidx * chunk);
+    E = min(E_all, e_lo + chunk) - e_lo;
+  };
+
+  if (warp == TC_LOAD_WARP) {
+    // ---- operator copies: entry it into stage it % NB once its previous
+    // use (entry it - NB) has been read by the MMAs
+    if (lane == 0) {
+      uint32_t it = 0;
+      for (int item = blockIdx.x; item < total_tiles * S && !*s_abort; item += gridDim.x) {
+        int c, row0, nrows, e_lo, E;
+        item_info(item, c, row0, nrows, e_lo, E);
+        const uint16_t *ops_c = a.sten_ops + c * FAR_MAX + e_lo;
+        for (int e = 0; e < E; ++e, ++it) {
+          const int st = it % NB;
+          if (it >= NB && !mbar_wait(&b_empty[st], ((it / NB) - 1) & 1, s_abort)) {
+            *s_abort = 1;
+            break;
+          }
+          mbar_expect_tx(&b_full[st], 3 * B_BYTES);
+          bulk_g2s(Bbase + st * (3 * B_BYTES), a.btab + (size_t)ops_c[e] * 3 * B_BYTES, 3 * B_BYTES,
+                   &b_full[st]);
         }
-        float4 h, l;
-        h.x = tf32_rna(v[0]); l.x = tf32_rna(v[0] - h.x);
-        h.y = tf32_rna(v[1]); l.y = tf32_rna(v[1] - h.y);
-        h.z = tf32_rna(v[2]); l.z = tf32_rna(v[2] - h.z);
-        h.w = tf32_rna(v[3]); l.w = tf32_rna(v[3] - h.w);
-        const uint32_t off = core_off(row, 4 * q, K);
-        *reinterpret_cast<float4 *>(A0 + off) = h;
-        *reinterpret_cast<float4 *>(A1 + off) = l;
       }
-      if (src >= 0 && half == 0) L0 += qc * (ls + a.logz[op]);
-      fence_proxy_async();
-      __syncthreads();
-      if (*s_abort) break;
-      if (tid == 0) {
-        const int bs = it % NB;
-        // test switch: the CTA's first operator wait is on a barrier that
-        // nothing arrives on, so its bounded wait runs out before any MMA
-        const bool stall = a.debug_stall && it == 0;
-        if (stall ? !mbar_wait(never_bar, 0) : !mbar_wait(&full_bar[bs], (it / NB) & 1)) {
-          *s_abort = 1;
-        } else {
-          landed = it + 1;
+      // let the copies in flight land before the CTA exits: those of the
+      // entries the MMA thread did not wait for
+      __syncwarp(1u);
+      const uint32_t issued = it, from = *s_consumed;
+      for (uint32_t u = from; u < issued; ++u) mbar_wait(&b_full[u % NB], (u / NB) & 1);
+    }
+  } else if (warp == TC_MMA_WARP) {
+    // ---- MMAs: entry it from A stage it % NA and operator stage it % NB,
+    // into accumulator e % NACC of the item
+    if (lane == 0) {
+      uint32_t it = 0, j = 0;
+      bool ok = true;
+      for (int item = blockIdx.x; item < total_tiles * S && ok; item += gridDim.x, ++j) {
+        int c, row0, nrows, e_lo, E;
+        item_info(item, c, row0, nrows, e_lo, E);
+        // the previous item's accumulators must have been read
+        if (j >= 1 && !mbar_wait(acc_empty, (j - 1) & 1, s_abort)) ok = false;
+        for (int e = 0; e < E && ok; ++e, ++it) {
+          const int sa = it % NA, sb = it % NB;
+          if (!mbar_wait(&a_full[sa], (it / NA) & 1, s_abort)) { ok = false; break; }
+          // test switch: the CTA's first operator wait is on a barrier that
+          // nothing arrives on, so its bounded wait runs out before any MMA
+          const bool stall = a.debug_stall && it == 0;
+          if (stall ? !mbar_wait(never_bar, 0) : !mbar_wait(&b_full[sb], (it / NB) & 1, s_abort)) {
+            ok = false;
+            break;
+          }
+          *s_consumed = it + 1;
           tc_fence_after();
-          const uint32_t a0 = smem_u32(A0), a1 = a0 + A_BYTES;
-          const uint32_t b0 = smem_u32(Bbase + bs * (3 * B_BYTES)), b1 = b0 + B_BYTES, b2 = b1 + B_BYTES;
+          const uint32_t a0 = smem_u32(smem + sa * (2 * A_BYTES)), a1 = a0 + A_BYTES;
+          const uint32_t b0 = smem_u32(Bbase + sb * (3 * B_BYTES)), b1 = b0 + B_BYTES, b2 = b1 + B_BYTES;
           const uint32_t acc = tmem + (uint32_t)(e % NACC) * ACC;
 #pragma unroll
           for (int ks = 0; ks < K / 8; ++ks) {
@@ -317,87 +309,158 @@ __global__ void __launch_bounds__(TC_THREADS, (TcShape<K, N>::CTAS)) k_m2l_tc(Tc
             mma_tf32(acc, da1, sdesc(b0 + o, LBO, SBO), IDESC, 1u);
             mma_tf32(acc, da1, sdesc(b1 + o, LBO, SBO), IDESC, 1u);
           }
-          mma_commit(&mma_bar[s]);
+          mma_commit(&a_empty[sa]);
+          mma_commit(&b_empty[sb]);
         }
+        if (ok) mma_commit(acc_full);   // the item's MMAs (none: at once)
       }
-#pragma unroll
-      for (int qq = 0; qq < QH; ++qq) fc[qq] = fn[qq];
-      qc = qn;
-      src = src_n;
-      src_n = src_nn;
-    }
-    __syncthreads();
-    if (*s_abort) break;
-    // wait for the last commit of this tile, then read the accumulators
-    if (E > 0) {
-      const uint32_t last = it - 1;
-      if (!mbar_wait(&mma_bar[last & 1], (last >> 1) & 1)) *s_abort = 1;
-    }
-    tc_fence_after();
-    __syncthreads();
-    if (*s_abort) break;
-    // sum the used accumulators in FP32 with Kahan compensation, 16 columns
-    // at a time; warps 0-3 take the even column chunks, warps 4-7 the odd
-    // ones (same TMEM lanes)
-    const int nacc = E < NACC ? E : NACC;
-    const uint32_t lane_base = ((uint32_t)((warp & 3) * 32)) << 16;
-#pragma unroll
-    for (int q = 0; q < N / 16; ++q) {
-      if ((q & 1) != half) continue;
-      float d[16], cmp[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) d[i] = cmp[i] = 0.f;
-      for (int ac = 0; ac < nacc; ++ac) {
-        float t16[16];
-        tmem_ld16(tmem + lane_base + (uint32_t)ac * ACC + q * 16, t16);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const float y = t16[i] - cmp[i];
-          const float t = d[i] + y;
-          cmp[i] = (t - d[i]) - y;
-          d[i] = t;
-        }
-      }
-      if (g >= 0 && S == 1) {
-        if (q == 0) a.lL0[g] = L0 + (double)d[0];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int l = 8 * q + i;
-          if (l >= 1 && l <= p) a.lb[(int64_t)g * a.P + l - 1] = make_float2(d[2 * i], d[2 * i + 1]);
-        }
-      } else if (g >= 0) {   // this part's sums, added up by k_m2l_tc_reduce
-        const int64_t pr = (int64_t)sidx * a.n_far + fi;
-        if (q == 0) a.part_L0[pr] = L0 + (double)d[0];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int l = 8 * q + i;
-          if (l >= 1 && l <= p) a.part_lb[pr * a.P + l - 1] = make_float2(d[2 * i], d[2 * i + 1]);
-        }
+      if (!ok) *s_abort = 1;
+      // the MMAs committed so far, before their TMEM is freed
+      if (*s_consumed > 0) {
+        const uint32_t last = *s_consumed - 1;
+        mbar_wait(&a_empty[last % NA], (last / NA) & 1);
       }
     }
-    tc_fence_before();
-    __syncthreads();
+  } else {
+    // ---- producers: warps 0-7, thread (row, half)
+    const int row = tid & (TC_M - 1), half = tid >> 7;
+    uint32_t it = 0, j = 0;
+    for (int item = blockIdx.x; item < total_tiles * S; item += gridDim.x, ++j) {
+      int c, row0, nrows, e_lo, E;
+      item_info(item, c, row0, nrows, e_lo, E);
+      const int sidx = item - (item / S) * S;
+      const int g = row < nrows ? a.cls_cells[(int64_t)c * a.cls_cap + row0 + row] : -1;
+      const int64_t fi = g >= 0 ? (int64_t)g - a.far_first : 0;
+      double ls = 0.0;
+      if (g >= 0 && half == 0) {
+        int l = a.l_min;
+        while (l < a.L && (int64_t)g >= a.lev_first[l + 1]) ++l;
+        ls = a.log_abs_scale[l];
+      }
+      double L0 = 0.0;
+      const uint16_t *ops_c = a.sten_ops + c * FAR_MAX + e_lo;
+      const int *srcs = a.far_full + fi * FAR_MAX + e_lo;
+      // the source slot of entry e is read one entry before its row, so that
+      // the row loads never wait for their own index
+      int src_next = (g >= 0 && PF < E) ? srcs[PF] : -1;
+      auto load_row = [&](int src_e, float4 (&f)[QH], double &q, int &src) {
+        src = src_e;
+        const float4 *rowp = reinterpret_cast<const float4 *>(a.ma + (int64_t)(src >= 0 ? src : 0) * a.P);
+#pragma unroll
+        for (int qq = 0; qq < QH; ++qq) {
+          const int qi = half * QH + qq;
+          f[qq] = (src >= 0 && 4 * qi < 2 * p) ? rowp[qi] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        q = src >= 0 ? a.mQ[src] : 0.0;
+      };
+      // rows of entries e .. e + PF - 1 in flight (a register ring)
+      float4 f[PF][QH];
+      double qv[PF];
+      int sv[PF];
+#pragma unroll
+      for (int d = 0; d < PF; ++d) load_row((g >= 0 && d < E) ? srcs[d] : -1, f[d], qv[d], sv[d]);
+      double lz = (half == 0 && E > 0) ? a.logz[ops_c[0]] : 0.0;   // log|zeta| of the entry's operator
+      for (int e = 0; e < E; ++e, ++it) {
+        const int sa = it % NA;
+        unsigned char *A0 = smem + sa * (2 * A_BYTES), *A1 = A0 + A_BYTES;
+        const double lz_next = (half == 0 && e + 1 < E) ? a.logz[ops_c[e + 1]] : 0.0;
+        // the stage's previous entry (it - NA) must have been read
+        if (it >= NA && !mbar_wait(&a_empty[sa], ((it / NA) - 1) & 1)) *s_abort = 1;
+        if (*s_abort) break;
+        // split the current row into TF32 A0 + A1 (Q sits at index 2p)
+        const float qf = (float)qv[0];
+#pragma unroll
+        for (int qq = 0; qq < QH; ++qq) {
+          const int q = half * QH + qq;
+          float v[4] = {f[0][qq].x, f[0][qq].y, f[0][qq].z, f[0][qq].w};
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const int k = 4 * q + jj;
+            v[jj] = k < 2 * p ? v[jj] : (k == 2 * p ? qf : 0.f);
+          }
+          float4 h, l;
+          h.x = tf32_rna(v[0]); l.x = tf32_rna(v[0] - h.x);
+          h.y = tf32_rna(v[1]); l.y = tf32_rna(v[1] - h.y);
+          h.z = tf32_rna(v[2]); l.z = tf32_rna(v[2] - h.z);
+          h.w = tf32_rna(v[3]); l.w = tf32_rna(v[3] - h.w);
+          const uint32_t off = core_off(row, 4 * q, K);
+          *reinterpret_cast<float4 *>(A0 + off) = h;
+          *reinterpret_cast<float4 *>(A1 + off) = l;
+        }
+        if (sv[0] >= 0 && half == 0) L0 += qv[0] * (ls + lz);
+        lz = lz_next;
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&a_full[sa]);
+        // advance the ring and fetch entry e + PF
+#pragma unroll
+        for (int d = 0; d + 1 < PF; ++d) {
+#pragma unroll
+          for (int qq = 0; qq < QH; ++qq) f[d][qq] = f[d + 1][qq];
+          qv[d] = qv[d + 1];
+          sv[d] = sv[d + 1];
+        }
+        load_row(src_next, f[PF - 1], qv[PF - 1], sv[PF - 1]);
+        src_next = (g >= 0 && e + PF + 1 < E) ? srcs[e + PF + 1] : -1;
+      }
+      if (*s_abort) break;
+      // the item's MMAs done: read and sum the accumulators
+      if (!mbar_wait(acc_full, j & 1)) {
+        *s_abort = 1;
+        break;
+      }
+      tc_fence_after();
+      // sum the used accumulators in FP32 with Kahan compensation, 16 columns
+      // at a time; warps 0-3 take the even column chunks, warps 4-7 the odd
+      // ones (same TMEM lanes)
+      const int nacc = E < NACC ? E : NACC;
+      const uint32_t lane_base = ((uint32_t)((warp & 3) * 32)) << 16;
+#pragma unroll
+      for (int q = 0; q < N / 16; ++q) {
+        if ((q & 1) != half) continue;
+        float d[16], cmp[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) d[i] = cmp[i] = 0.f;
+        for (int ac = 0; ac < nacc; ++ac) {
+          float t16[16];
+          tmem_ld16(tmem + lane_base + (uint32_t)ac * ACC + q * 16, t16);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const float y = t16[i] - cmp[i];
+            const float t = d[i] + y;
+            cmp[i] = (t - d[i]) - y;
+            d[i] = t;
+          }
+        }
+        if (g >= 0 && S == 1) {
+          if (q == 0) a.lL0[g] = L0 + (double)d[0];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int l = 8 * q + i;
+            if (l >= 1 && l <= p) a.lb[(int64_t)g * a.P + l - 1] = make_float2(d[2 * i], d[2 * i + 1]);
+          }
+        } else if (g >= 0) {   // this part's sums, added up by k_m2l_tc_reduce
+          const int64_t pr = (int64_t)sidx * a.n_far + fi;
+          if (q == 0) a.part_L0[pr] = L0 + (double)d[0];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int l = 8 * q + i;
+            if (l >= 1 && l <= p) a.part_lb[pr * a.P + l - 1] = make_float2(d[2 * i], d[2 * i + 1]);
+          }
+        }
+      }
+      // the accumulators may be overwritten by the next item's MMAs
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty);
+    }
   }
-  if (*s_abort) {
-    if (tid == 0) {
-      atomicOr(a.err, 1);
-      // let the operator copies in flight land before the CTA exits: the
-      // copies of entries landed .. issued-1 were not waited for
-      for (uint32_t u = landed; u < issued; ++u) mbar_wait(&full_bar[u % NB], (u / NB) & 1);
-      // and the MMAs committed before the abort, before their TMEM is freed
-      if (landed > 0) {
-        const uint32_t last = landed - 1;
-        mbar_wait(&mma_bar[last & 1], (last >> 1) & 1);
-      }
-    }
-  } else if (it > 0 && tid == 0) {
-    const uint32_t last = it - 1;
-    mbar_wait(&mma_bar[last & 1], (last >> 1) & 1);
-  }
+  __syncwarp();   // the single-thread roles rejoin their warps
+  if (*s_abort && tid == 0) atomicOr(a.err, 1);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, COLS);
+  if (warp == TC_MMA_WARP) tmem_dealloc(tmem, COLS);
 }
 
 // Sum of the split parts of every far cell, in part order (FP64, rounded once).
@@ -428,7 +491,7 @@ __global__ void k_m2l_tc_reduce(int split, int64_t n_far, int64_t far_first, int
 template <int K, int N>
 cudaError_t launch_tc(const TcArgs &a, int64_t n_far_cells, cudaStream_t s) {
   using SH = TcShape<K, N>;
-  const size_t smem = SH::SMEM + (3 + SH::NB) * 8 + 8 + (MAX_CLASSES + 1) * 4 + 16;
+  const size_t smem = SH::SMEM + 1024;   // + barriers and words (under 1 KB)
   cudaError_t e = cudaFuncSetAttribute(k_m2l_tc<K, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -531,17 +594,31 @@ cudaError_t tc_measure_tf32(double *tflops) {
   return cudaSuccess;
 }
 
+static int tc_ctas(int K, int N) {
+  if (K == 32 && N == 32) return TcShape<32, 32>::CTAS;
+  if (K == 48 && N == 48) return TcShape<48, 48>::CTAS;
+  if (K == 56 && N == 64) return TcShape<56, 64>::CTAS;
+  return TcShape<64, 64>::CTAS;
+}
+
 int tc_split(int64_t n_far_cells, int n_classes, int sms, int K, int N) {
-  // Split only a grid that would leave more than half the CTA slots idle
-  // (measured on 2^20 points: the septree's 76 tiles on 152 SMs ran 1.4x
-  // faster split four ways; the quadtree's 175 and the triangle tiling's 293
-  // tiles ran slower split, paying the extra epilogues and the reduction).
-  const int ctas = N <= 32 ? 2 : 1;                 // TcShape<K, N>::CTAS
-  const int64_t slots = (int64_t)sms * ctas;
+  // Items of a tile's stencil entries split S ways, chosen for load balance:
+  // the longest CTA runs ceil(tiles S / slots) items of 1/S of a tile; a
+  // split costs about a tenth of a tile more (partial writes and the
+  // reduction kernel).
+  const int64_t slots = (int64_t)sms * tc_ctas(K, N);
   const int64_t tiles = (n_far_cells + TC_M - 1) / TC_M + n_classes;
-  (void)K;
-  if (2 * tiles > slots) return 1;
-  return (int)std::min<int64_t>(4, (2 * slots + tiles - 1) / tiles);
+  int best = 1;
+  double best_cost = 1e30;
+  for (int S = 1; S <= 4; ++S) {
+    const double waves = (double)((tiles * S + slots - 1) / slots);
+    const double cost = waves / S * (S > 1 ? 1.1 : 1.0);
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = S;
+    }
+  }
+  return best;
 }
 
 bool tc_shape(int p, int *K, int *N) {

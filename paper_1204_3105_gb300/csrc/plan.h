@@ -331,7 +331,7 @@ struct TcArgs {
 };
 bool tc_shape(int p, int *K, int *N);
 // CTAs over which the stencil entries of one tile are split, for a level
-// range with n_far_cells M2L targets (fills the SMs about twice).
+// range with n_far_cells M2L targets (chosen for load balance over the SMs).
 int tc_split(int64_t n_far_cells, int n_classes, int sms, int K, int N);
 // Measured TF32 tensor-core throughput (TFLOP/s) of this device.
 cudaError_t tc_measure_tf32(double *tflops);
