@@ -35,7 +35,7 @@ MUFU_PER_CLK_SM = 16      # lg2 results per clock per SM (MUFU pipe)
 # DRAM bytes (read + write) of one P2P launch per tiling on the 2^20-point
 # workload, from an ncu capture of the current kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum; summarised in profiles/p2p_x2_traffic_2p20.md)
-P2P_TRAFFIC = {"quad": 18325760 + 256, "sept": 17503232 + 0, "tri": 19340544 + 0}
+P2P_TRAFFIC = {"quad": 18322688 + 0, "sept": 17506048 + 0, "tri": 19338240 + 0}
 FP32_LANES_SM = 128       # FP32 FMA lanes per SM
 
 
