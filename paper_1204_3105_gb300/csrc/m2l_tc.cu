@@ -143,10 +143,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+// x rounded to TF32 (10 fraction bits), to nearest with ties away from zero,
+// as integer operations on the bit pattern (finite x): adding half a unit of
+// the kept last place to the magnitude and clearing the 13 dropped bits
 __device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 // Byte offset of element (row, k) in a K-major no-swizzle operand tile.
@@ -164,7 +165,6 @@ template <int K, int N> struct TcShape {
   static constexpr uint32_t A_BYTES = 128 * K * 4, B_BYTES = N * K * 4;
   static constexpr uint32_t SMEM = NA * (2 * A_BYTES) + NB * (3 * B_BYTES);
   static constexpr int CTAS = (N <= 32 && SMEM <= 104 * 1024) ? 2 : 1;
-  static constexpr int PF = K <= 32 ? 2 : 1;              // gathered rows in flight per thread
 };
 
 // Warp roles of a CTA: warps 0-7 gather (two threads per target row, one
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(TC_THREADS, (TcShape<K, N>::CTAS)) k_m2l_tc(Tc
   extern __shared__ __align__(1024) unsigned char smem[];
   using SH = TcShape<K, N>;
   constexpr uint32_t A_BYTES = SH::A_BYTES, B_BYTES = SH::B_BYTES;
-  constexpr int NA = SH::NA, NB = SH::NB, PF = SH::PF;
+  constexpr int NA = SH::NA, NB = SH::NB;
   constexpr uint32_t SBO = (K / 4) * 128, LBO = 128;
   constexpr uint32_t IDESC = idesc_tf32(TC_M, N);
   constexpr uint32_t ACC = SH::ACC, COLS = SH::COLS;
@@ -296,18 +296,21 @@ __global__ void __launch_bounds__(TC_THREADS, (TcShape<K, N>::CTAS)) k_m2l_tc(Tc
           }
           *s_consumed = it + 1;
           tc_fence_after();
-          const uint32_t a0 = smem_u32(smem + sa * (2 * A_BYTES)), a1 = a0 + A_BYTES;
-          const uint32_t b0 = smem_u32(Bbase + sb * (3 * B_BYTES)), b1 = b0 + B_BYTES, b2 = b1 + B_BYTES;
+          // descriptors of the stage's operands; a K step advances the start
+          // address field (address / 16) by 2 LBO / 16
+          const uint64_t dA0 = sdesc(smem_u32(smem + sa * (2 * A_BYTES)), LBO, SBO);
+          const uint64_t dA1 = dA0 + (A_BYTES >> 4);
+          const uint64_t dB0 = sdesc(smem_u32(Bbase + sb * (3 * B_BYTES)), LBO, SBO);
+          const uint64_t dB1 = dB0 + (B_BYTES >> 4), dB2 = dB1 + (B_BYTES >> 4);
           const uint32_t acc = tmem + (uint32_t)(e % NACC) * ACC;
 #pragma unroll
           for (int ks = 0; ks < K / 8; ++ks) {
-            const uint32_t o = ks * 2 * LBO;
-            const uint64_t da0 = sdesc(a0 + o, LBO, SBO), da1 = sdesc(a1 + o, LBO, SBO);
-            mma_tf32(acc, da0, sdesc(b0 + o, LBO, SBO), IDESC, (e >= NACC || ks > 0) ? 1u : 0u);
-            mma_tf32(acc, da0, sdesc(b1 + o, LBO, SBO), IDESC, 1u);
-            mma_tf32(acc, da0, sdesc(b2 + o, LBO, SBO), IDESC, 1u);
-            mma_tf32(acc, da1, sdesc(b0 + o, LBO, SBO), IDESC, 1u);
-            mma_tf32(acc, da1, sdesc(b1 + o, LBO, SBO), IDESC, 1u);
+            const uint64_t o = (uint64_t)(ks * 2 * LBO) >> 4;
+            mma_tf32(acc, dA0 + o, dB0 + o, IDESC, (e >= NACC || ks > 0) ? 1u : 0u);
+            mma_tf32(acc, dA0 + o, dB1 + o, IDESC, 1u);
+            mma_tf32(acc, dA0 + o, dB2 + o, IDESC, 1u);
+            mma_tf32(acc, dA1 + o, dB0 + o, IDESC, 1u);
+            mma_tf32(acc, dA1 + o, dB1 + o, IDESC, 1u);
           }
           mma_commit(&a_empty[sa]);
           mma_commit(&b_empty[sb]);
@@ -340,9 +343,8 @@ __global__ void __launch_bounds__(TC_THREADS, (TcShape<K, N>::CTAS)) k_m2l_tc(Tc
       double L0 = 0.0;
       const uint16_t *ops_c = a.sten_ops + c * FAR_MAX + e_lo;
       const int *srcs = a.far_full + fi * FAR_MAX + e_lo;
-      // the source slot of entry e is read one entry before its row, so that
-      // the row loads never wait for their own index
-      int src_next = (g >= 0 && PF < E) ? srcs[PF] : -1;
+      auto src_of = [&](int e) { return (g >= 0 && e < E) ? srcs[e] : -1; };
+      auto lz_of = [&](int e) { return (half == 0 && e < E) ? a.logz[ops_c[e]] : 0.0; };
       auto load_row = [&](int src_e, float4 (&f)[QH], double &q, int &src) {
         src = src_e;
         const float4 *rowp = reinterpret_cast<const float4 *>(a.ma + (int64_t)(src >= 0 ? src : 0) * a.P);
@@ -353,29 +355,32 @@ __global__ void __launch_bounds__(TC_THREADS, (TcShape<K, N>::CTAS)) k_m2l_tc(Tc
         }
         q = src >= 0 ? a.mQ[src] : 0.0;
       };
-      // rows of entries e .. e + PF - 1 in flight (a register ring)
-      float4 f[PF][QH];
-      double qv[PF];
-      int sv[PF];
-#pragma unroll
-      for (int d = 0; d < PF; ++d) load_row((g >= 0 && d < E) ? srcs[d] : -1, f[d], qv[d], sv[d]);
-      double lz = (half == 0 && E > 0) ? a.logz[ops_c[0]] : 0.0;   // log|zeta| of the entry's operator
-      for (int e = 0; e < E; ++e, ++it) {
+      // Two slots, each holding one entry's row, Q, source slot and log|zeta|
+      // of its operator; after an entry is written out its slot is refilled
+      // with the entry two ahead, whose source slot was read one entry
+      // earlier still.  The loop body handles the two slots in turn, so no
+      // register is copied while its load is in flight.
+      float4 f0[QH], f1[QH];
+      double q0, q1, lz0 = lz_of(0), lz1 = lz_of(1);
+      int s0, s1;
+      load_row(src_of(0), f0, q0, s0);
+      load_row(src_of(1), f1, q1, s1);
+      int nx0 = src_of(2), nx1 = src_of(3);   // source slots of the next refills
+      auto step = [&](int e, float4 (&f)[QH], double &q, int &sv, double &lz, int &nx) {
         const int sa = it % NA;
         unsigned char *A0 = smem + sa * (2 * A_BYTES), *A1 = A0 + A_BYTES;
-        const double lz_next = (half == 0 && e + 1 < E) ? a.logz[ops_c[e + 1]] : 0.0;
         // the stage's previous entry (it - NA) must have been read
-        if (it >= NA && !mbar_wait(&a_empty[sa], ((it / NA) - 1) & 1)) *s_abort = 1;
-        if (*s_abort) break;
-        // split the current row into TF32 A0 + A1 (Q sits at index 2p)
-        const float qf = (float)qv[0];
+        if (it >= NA && !mbar_wait(&a_empty[sa], ((it / NA) - 1) & 1, s_abort)) *s_abort = 1;
+        if (*s_abort) return false;
+        // split the row into TF32 A0 + A1 (Q sits at index 2p)
+        const float qf = (float)q;
 #pragma unroll
         for (int qq = 0; qq < QH; ++qq) {
-          const int q = half * QH + qq;
-          float v[4] = {f[0][qq].x, f[0][qq].y, f[0][qq].z, f[0][qq].w};
+          const int qi = half * QH + qq;
+          float v[4] = {f[qq].x, f[qq].y, f[qq].z, f[qq].w};
 #pragma unroll
           for (int jj = 0; jj < 4; ++jj) {
-            const int k = 4 * q + jj;
+            const int k = 4 * qi + jj;
             v[jj] = k < 2 * p ? v[jj] : (k == 2 * p ? qf : 0.f);
           }
           float4 h, l;
@@ -383,29 +388,28 @@ __global__ void __launch_bounds__(TC_THREADS, (TcShape<K, N>::CTAS)) k_m2l_tc(Tc
           h.y = tf32_rna(v[1]); l.y = tf32_rna(v[1] - h.y);
           h.z = tf32_rna(v[2]); l.z = tf32_rna(v[2] - h.z);
           h.w = tf32_rna(v[3]); l.w = tf32_rna(v[3] - h.w);
-          const uint32_t off = core_off(row, 4 * q, K);
+          const uint32_t off = core_off(row, 4 * qi, K);
           *reinterpret_cast<float4 *>(A0 + off) = h;
           *reinterpret_cast<float4 *>(A1 + off) = l;
         }
-        if (sv[0] >= 0 && half == 0) L0 += qv[0] * (ls + lz);
-        lz = lz_next;
+        if (sv >= 0 && half == 0) L0 += q * (ls + lz);
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(&a_full[sa]);
-        // advance the ring and fetch entry e + PF
-#pragma unroll
-        for (int d = 0; d + 1 < PF; ++d) {
-#pragma unroll
-          for (int qq = 0; qq < QH; ++qq) f[d][qq] = f[d + 1][qq];
-          qv[d] = qv[d + 1];
-          sv[d] = sv[d + 1];
-        }
-        load_row(src_next, f[PF - 1], qv[PF - 1], sv[PF - 1]);
-        src_next = (g >= 0 && e + PF + 1 < E) ? srcs[e + PF + 1] : -1;
+        ++it;
+        // refill the slot with entry e + 2
+        load_row(nx, f, q, sv);
+        lz = lz_of(e + 2);
+        nx = src_of(e + 4);
+        return true;
+      };
+      for (int e = 0; e < E; e += 2) {
+        if (!step(e, f0, q0, s0, lz0, nx0)) break;
+        if (e + 1 < E && !step(e + 1, f1, q1, s1, lz1, nx1)) break;
       }
       if (*s_abort) break;
       // the item's MMAs done: read and sum the accumulators
-      if (!mbar_wait(acc_full, j & 1)) {
+      if (!mbar_wait(acc_full, j & 1, s_abort)) {
         *s_abort = 1;
         break;
       }
