@@ -701,17 +701,20 @@ fmm2d_status evaluate_t(fmm2d_plan *pl, const void *u, double *out, cudaStream_t
     CK(cudaEventRecord(pl->ev_fork, s), "fork");
     CK(cudaStreamWaitEvent(f, pl->ev_fork, 0), "fork");
   }
+  // the device error word of this evaluation (bounded waits report there)
+  CK(cudaMemsetAsync(pl->d_dev_err.p, 0, 4, f), "memset");
   {
     StageScope sc(pl, ST_P2M, f, 1);
     CK(launch_p2m<R>(a, src4, (const int *)pl->d_src_start.p, (const int *)pl->d_src_end.p, mQ, ma, f), "p2m");
   }
-  {
-    StageScope sc(pl, ST_M2M, f, std::max(0, L - pl->l_min));
-    for (int l = L - 1; l >= pl->l_min; --l)
-      CK(launch_m2m<R>(a, pl->geo, l, pl->lev_first[l], pl->lev_count[l], (const int *)pl->d_map.p,
-                       (const uint32_t *)pl->d_cell_key.p, (const uint8_t *)pl->d_cell_cls.p,
-                       (const uint8_t *)pl->d_cell_hsrc.p, (const Cx<R> *)pl->d_m2m_ops.p, mQ, ma, f),
-         "m2m");
+  if (L - 1 >= pl->l_min) {   // levels L-1 .. l_min in one launch
+    StageScope sc(pl, ST_M2M, f, 1);
+    CK(launch_m2m_up<R>(a, pl->geo, pl->l_min, pl->lev_first[L - 1], pl->lev_count[L - 1],
+                        (const int *)pl->d_map.p, (const uint32_t *)pl->d_cell_key.p,
+                        (const uint8_t *)pl->d_cell_cls.p, (const uint8_t *)pl->d_cell_hsrc.p,
+                        (const Cx<R> *)pl->d_m2m_ops.p, mQ, ma, (int *)pl->d_m2m_arrive.p,
+                        pl->n_cells, f),
+       "m2m");
   }
   if (L < pl->l_min) {
     CK(cudaMemsetAsync(lL0, 0, pl->n_cells * sizeof(double), f), "zero locals");
@@ -761,12 +764,17 @@ fmm2d_status evaluate_t(fmm2d_plan *pl, const void *u, double *out, cudaStream_t
        "m2l");
   }
   {
-    StageScope sc(pl, ST_L2L, f, std::max(0, L - pl->l_min));
-    for (int l = pl->l_min + 1; l <= L; ++l)
-      CK(launch_l2l<R>(a, pl->geo, l, pl->lev_first[l], pl->lev_count[l], (const int *)pl->d_map.p,
-                       (const uint32_t *)pl->d_cell_key.p, (const uint8_t *)pl->d_cell_cls.p,
-                       (const Cx<R> *)pl->d_l2l_ops.p, lL0, lb, f),
+    // levels l_min+1 .. L in one launch
+    StageScope sc(pl, ST_L2L, f, L > pl->l_min ? 1 : 0);
+    if (L > pl->l_min) {
+      const int64_t first = pl->lev_first[pl->l_min + 1];
+      CK(launch_l2l_down<R>(a, pl->geo, first, pl->n_cells - first, (const int64_t *)pl->d_lev_first.p,
+                            (const int *)pl->d_map.p, (const uint32_t *)pl->d_cell_key.p,
+                            (const uint8_t *)pl->d_cell_cls.p, (const Cx<R> *)pl->d_l2l_ops.p, lL0,
+                            lb, (int *)pl->d_l2l_ready.p, pl->n_cells, pl->n_sms,
+                            (int *)pl->d_dev_err.p, f),
          "l2l");
+    }
   }
   {
     StageScope sc(pl, ST_P2P, s, 1);
@@ -1404,7 +1412,7 @@ static void for_each_dbuf(fmm2d_plan *pl, F f) {
                   &pl->d_tgt_start, &pl->d_tgt_end, &pl->d_lev_first, &pl->d_far_cnt,
                   &pl->d_far_src, &pl->d_far_op, &pl->d_near_cnt, &pl->d_near_src, &pl->d_src4,
                   &pl->d_tgt2, &pl->d_mQ, &pl->d_ma, &pl->d_ma_ff, &pl->d_lL0, &pl->d_lb, &pl->d_phi_near,
-                  &pl->d_fnear, &pl->d_tc_part_lb, &pl->d_tc_part_L0,
+                  &pl->d_fnear, &pl->d_tc_part_lb, &pl->d_tc_part_L0, &pl->d_m2m_arrive, &pl->d_l2l_ready,
                   &pl->d_phi_far, &pl->d_sten, &pl->d_geo_scale, &pl->d_m2l_ops, &pl->d_m2l_logz,
                   &pl->d_m2m_ops, &pl->d_l2l_ops, &pl->d_counts, &pl->d_far_full,
                   &pl->d_cls_cnt, &pl->d_cls_cells, &pl->d_tc_ops, &pl->d_ff_ops, &pl->d_ff_ph, &pl->d_dev_err,
@@ -1619,6 +1627,8 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
   CK(dbuf_reserve(pl->d_tgt_start, cap_cells * 4), "alloc");
   CK(dbuf_reserve(pl->d_tgt_end, cap_cells * 4), "alloc");
   CK(dbuf_reserve(pl->d_mQ, cap_cells * 8), "alloc");
+  CK(dbuf_reserve(pl->d_m2m_arrive, cap_cells * 4), "alloc");
+  CK(dbuf_reserve(pl->d_l2l_ready, (cap_cells + 2) * 4), "alloc");
   CK(dbuf_reserve(pl->d_lL0, cap_cells * 8), "alloc");
   CK(dbuf_reserve(pl->d_ma, cap_cells * pl->P * csz), "alloc");
   if (ff_m2l(pl)) CK(dbuf_reserve(pl->d_ma_ff, cap_cells * (pl->p + 1) * sizeof(float4)), "alloc");

@@ -255,6 +255,208 @@ k_m2m(ExpandArgs a, Geo g, int level, int64_t first, int64_t count, const int *_
   if (lane + 33 <= p) ma[gp * a.P + lane + 32] = acc1;
 }
 
+// Uniform tree, the whole upward pass in one launch.  A warp takes a cell of
+// level L-1 (its children are leaves, done by the P2M), forms its multipole,
+// and then announces it to the parent: after a device-scope fence it adds
+// one to the parent's arrival counter, and the warp that brings the count to
+// the parent's number of occupied children goes on with the parent (whose
+// children are then all written), up to level l_min.  Each cell is computed
+// once, by one warp, with its children in child order, so the result is the
+// one of the level-by-level form; no warp waits for another.  Multipoles
+// written in this launch are read through L2 (ld.global.cg).
+template <typename R>
+__global__ void __launch_bounds__(32 * WPB)
+k_m2m_up(ExpandArgs a, Geo g, int l_min, int64_t first, int64_t count,
+         const int *__restrict__ map, const uint32_t *__restrict__ cell_key,
+         const uint8_t *__restrict__ cell_cls, const uint8_t *__restrict__ cell_hsrc,
+         const Cx<R> *__restrict__ ops, int n_staged, double *mQ, Cx<R> *ma,
+         int *__restrict__ arrive) {
+  constexpr int NB = 7;                        // children of a cell, at most
+  constexpr int NLD = (NB * MAXP + 31) / 32;   // multipole loads per lane, at most
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ Cx<R> sh[WPB][NB][MAXP + 1];
+  extern __shared__ __align__(16) unsigned char dyn_ops[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t ci = blockIdx.x * (int64_t)WPB + w;
+  const int p = a.p, P1 = p + 1;
+  const Cx<R> *op_tab = ops;
+  if (n_staged > 0) {   // the operators in shared memory: every cell reads them
+    Cx<R> *so = reinterpret_cast<Cx<R> *>(dyn_ops);
+    for (int i = threadIdx.x; i < n_staged; i += blockDim.x) so[i] = ops[i];
+    __syncthreads();
+    op_tab = so;
+  }
+  if (ci >= count) return;
+  int64_t gp = first + ci;
+  int level = a.L - 1;
+  for (;;) {
+    // the cell's fields and its children's slots
+    const bool hs = cell_hsrc[gp];
+    const uint32_t key = cell_key[gp];
+    int nch = hs ? g.b : 0, cs = -1;
+    if (lane < nch) cs = map[g.map_off[level + 1] + (int64_t)key * g.b + lane];
+    int use = 0, cls = 0;
+    double Qc = 0.0;
+    if (cs >= 0) {
+      use = cell_hsrc[cs];
+      Qc = __ldcg(&mQ[cs]);
+      cls = cell_cls[cs];
+    }
+    Cx<R> v[NLD];
+    const int nv = nch * p;
+#pragma unroll
+    for (int r = 0; r < NLD; ++r) {
+      const int idx = lane + 32 * r;
+      const int d = min(idx / max(p, 1), 31);
+      const int cd = __shfl_sync(FULL, cs, d);
+      v[r] = Cx<R>{(R)0, (R)0};
+      if (idx < nv && cd >= 0) {
+        const R *src = reinterpret_cast<const R *>(&ma[(int64_t)cd * a.P + (idx - d * p)]);
+        v[r] = Cx<R>{__ldcg(src), __ldcg(src + 1)};
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < NLD; ++r) {
+      const int idx = lane + 32 * r;
+      if (idx < nv) {
+        const int d = idx / p;
+        sh[w][d][idx - d * p + 1] = v[r];
+      }
+    }
+    __syncwarp();
+    Cx<R> acc0 = {(R)0, (R)0}, acc1 = {(R)0, (R)0};
+    double Q = 0.0;
+    for (int d = 0; d < nch; ++d) {
+      const int ud = __shfl_sync(FULL, use, d);
+      const double qd = __shfl_sync(FULL, Qc, d);
+      const int kd = __shfl_sync(FULL, cls, d);
+      if (!ud) continue;                         // warp-uniform
+      const Cx<R> *op = op_tab + (int64_t)kd * P1 * P1;
+      const R q = (R)qd;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int l = lane + 1 + 32 * h;
+        if (l > p) break;
+        const Cx<R> *row = op + (int64_t)l * P1;
+        Cx<R> s = q * row[0];
+        for (int k = 1; k <= l; ++k) cfma(s, row[k], sh[w][d][k]);
+        if (h == 0) acc0 = acc0 + s; else acc1 = acc1 + s;
+      }
+      Q += qd;
+    }
+    if (lane == 0) mQ[gp] = Q;
+    if (lane + 1 <= p) ma[gp * a.P + lane] = acc0;
+    if (lane + 33 <= p) ma[gp * a.P + lane + 32] = acc1;
+    if (level <= l_min) break;
+    // announce the cell to its parent; the last of the occupied siblings
+    // goes on with the parent
+    const uint32_t pkey = (g.tiling == FMM2D_SEPT) ? key / 7u : key >> 2;
+    const bool sib = lane < g.b && map[g.map_off[level] + (int64_t)pkey * g.b + lane] >= 0;
+    const int nsib = __popc(__ballot_sync(FULL, sib));
+    const int ps = map[g.map_off[level - 1] + pkey];
+    __threadfence();
+    __syncwarp();
+    int old = 0;
+    if (lane == 0) old = atomicAdd(&arrive[ps], 1);
+    old = __shfl_sync(FULL, old, 0);
+    if (old != nsib - 1) break;
+    __threadfence();   // the siblings' multipoles, announced before their arrivals
+    gp = ps;
+    --level;
+  }
+}
+
+// Uniform tree, the downward pass of levels l_min+1 .. L in one launch: a
+// persistent grid of warps takes the cells in slot order, i.e. by (level,
+// key), from a counter, so a cell's parent was taken earlier by a warp that
+// is running; the warp waits for the parent's ready word (bounded: after
+// about 2^22 polls it sets bit 2 of *err and goes on), adds the shifted
+// parent local to the cell's own (M2L) local, and sets the cell's ready word.
+// Each cell is computed once, as in the level-by-level form.  Locals written
+// in this launch are read through L2 (ld.global.cg).
+template <typename R>
+__global__ void __launch_bounds__(32 * WPB)
+k_l2l_down(ExpandArgs a, Geo g, int64_t first, int64_t total, int64_t fixed_end,
+           const int64_t *__restrict__ lev_first, const int *__restrict__ map,
+           const uint32_t *__restrict__ cell_key, const uint8_t *__restrict__ cell_cls,
+           const Cx<R> *__restrict__ ops, int n_staged, double *lL0, Cx<R> *lb, int *ready,
+           int *ctr, int *err) {
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ Cx<R> sh[WPB][MAXP + 1];
+  extern __shared__ __align__(16) unsigned char dyn_ops[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int p = a.p, P1 = p + 1;
+  const int k0 = lane, k1 = lane + 32;
+  const Cx<R> *op_tab = ops;
+  if (n_staged > 0) {   // the operators in shared memory: every cell reads them
+    Cx<R> *so = reinterpret_cast<Cx<R> *>(dyn_ops);
+    for (int i = threadIdx.x; i < n_staged; i += blockDim.x) so[i] = ops[i];
+    __syncthreads();
+    op_tab = so;
+  }
+  for (;;) {
+    int64_t idx = 0;
+    if (lane == 0) idx = atomicAdd(reinterpret_cast<unsigned long long *>(ctr), 1ull);
+    idx = __shfl_sync(FULL, idx, 0);
+    if (idx >= total) break;
+    const int64_t gc = first + idx;
+    int level = a.l_min + 1;
+    while (level < a.L && gc >= lev_first[level + 1]) ++level;
+    // the cell's own fields
+    const int cls = cell_cls[gc];
+    Cx<R> own0 = {(R)0, (R)0}, own1 = {(R)0, (R)0};
+    double L0 = 0.0;
+    if (k0 == 0) L0 = lL0[gc];
+    else if (k0 <= p) own0 = lb[gc * a.P + k0 - 1];
+    if (k1 <= p) own1 = lb[gc * a.P + k1 - 1];
+    const uint32_t key = cell_key[gc];
+    const uint32_t pkey = (g.tiling == FMM2D_SEPT) ? key / 7u : key >> 2;
+    const int ps = map[g.map_off[level - 1] + pkey];
+    // the parent's final local (level l_min: its M2L local, final already)
+    if (ps >= fixed_end) {
+      bool ok = true;
+      if (lane == 0) {
+        const volatile int *rw = ready + ps;
+        int polls = 0;
+        while (*rw == 0) {
+          if (++polls > (1 << 22)) {
+            ok = false;
+            break;
+          }
+          if (polls > 16) __nanosleep(64);
+        }
+        if (!ok) atomicOr(err, 2);
+      }
+      __syncwarp();
+      __threadfence();
+    }
+    double Lp = 0.0;
+    if (k0 == 0) Lp = __ldcg(&lL0[ps]);
+    for (int k = lane; k < p; k += 32) {
+      const R *src = reinterpret_cast<const R *>(&lb[(int64_t)ps * a.P + k]);
+      sh[w][k + 1] = Cx<R>{__ldcg(src), __ldcg(src + 1)};
+    }
+    __syncwarp();
+    const Cx<R> *U = op_tab + (int64_t)cls * P1 * P1;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = h == 0 ? k0 : k1;
+      if (k > p) break;
+      const Cx<R> *row = U + (int64_t)k * P1;
+      Cx<R> s = {(R)0, (R)0};
+      for (int l = (k > 1 ? k : 1); l <= p; ++l) cfma(s, row[l], sh[w][l]);
+      if (k == 0) lL0[gc] = L0 + (Lp + (double)s.x);
+      else lb[gc * a.P + k - 1] = (h == 0 ? own0 : own1) + s;
+    }
+    // the cell's local is final: publish it
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) *reinterpret_cast<volatile int *>(ready + gc) = 1;
+    __syncwarp();   // sh[w] is rewritten by the next cell
+  }
+}
+
 // H lanes per target cell (the launcher uses H = 32); lane i of the group owns
 // local coefficients i and i+H.
 template <typename R, int H>
@@ -413,6 +615,23 @@ inline int staged_ops(const ExpandArgs &a, size_t static_bytes) {
 
 }  // namespace
 
+// ready: 2 + n_cells ints (a 64-bit counter, then a word per cell), zeroed here.
+template <typename R>
+cudaError_t launch_l2l_down(const ExpandArgs &a, const Geo &g, int64_t first, int64_t total,
+                            const int64_t *lev_first_dev, const int *map, const uint32_t *cell_key,
+                            const uint8_t *cell_cls, const Cx<R> *ops, double *lL0, Cx<R> *lb,
+                            int *ready, int64_t n_cells, int sms, int *err, cudaStream_t s) {
+  if (total <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(ready, 0, (size_t)(n_cells + 2) * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  const int n_st = staged_ops<R>(a, sizeof(Cx<R>) * WPB * (MAXP + 1));
+  const unsigned blocks = (unsigned)std::min<int64_t>(wblocks(total), (int64_t)sms * 8);
+  k_l2l_down<R><<<blocks, 32 * WPB, n_st * sizeof(Cx<R>), s>>>(
+      a, g, first, total, first, lev_first_dev, map, cell_key, cell_cls, ops, n_st, lL0, lb,
+      ready + 2, ready, err);
+  return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_gather_u(const void *u, bool f32_in, const uint32_t *perm, int64_t n, R *src4,
                             cudaStream_t s, bool lo) {
@@ -443,6 +662,20 @@ cudaError_t launch_m2m(const ExpandArgs &a, const Geo &g, int level, int64_t fir
   const int n_st = staged_ops<R>(a, sizeof(Cx<R>) * WPB * 7 * (MAXP + 1));
   k_m2m<R><<<wblocks(count), 32 * WPB, n_st * sizeof(Cx<R>), s>>>(
       a, g, level, first, count, map, cell_key, cell_cls, cell_hsrc, ops, n_st, mQ, ma);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_m2m_up(const ExpandArgs &a, const Geo &g, int l_min, int64_t first, int64_t count,
+                          const int *map, const uint32_t *cell_key, const uint8_t *cell_cls,
+                          const uint8_t *cell_hsrc, const Cx<R> *ops, double *mQ, Cx<R> *ma,
+                          int *arrive, int64_t n_cells, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(arrive, 0, (size_t)n_cells * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  const int n_st = staged_ops<R>(a, sizeof(Cx<R>) * WPB * 7 * (MAXP + 1));
+  k_m2m_up<R><<<wblocks(count), 32 * WPB, n_st * sizeof(Cx<R>), s>>>(
+      a, g, l_min, first, count, map, cell_key, cell_cls, cell_hsrc, ops, n_st, mQ, ma, arrive);
   return cudaGetLastError();
 }
 
@@ -488,6 +721,14 @@ cudaError_t launch_l2p(const ExpandArgs &a, const R *tgt, int tstride, const int
                                      const int *, const uint32_t *, const uint8_t *,              \
                                      const uint8_t *, const Cx<R> *, double *, Cx<R> *,           \
                                      cudaStream_t);                                               \
+  template cudaError_t launch_l2l_down<R>(const ExpandArgs &, const Geo &, int64_t, int64_t,       \
+                                          const int64_t *, const int *, const uint32_t *,         \
+                                          const uint8_t *, const Cx<R> *, double *, Cx<R> *,      \
+                                          int *, int64_t, int, int *, cudaStream_t);              \
+  template cudaError_t launch_m2m_up<R>(const ExpandArgs &, const Geo &, int, int64_t, int64_t,    \
+                                        const int *, const uint32_t *, const uint8_t *,           \
+                                        const uint8_t *, const Cx<R> *, double *, Cx<R> *, int *, \
+                                        int64_t, cudaStream_t);                                   \
   template cudaError_t launch_m2l<R>(const ExpandArgs &, int64_t, int64_t, const int64_t *,        \
                                      const double *, int64_t, const int *, const int *,           \
                                      const uint16_t *, const Cx<R> *, const double *,             \

@@ -90,6 +90,8 @@ struct Plan {
   DBuf d_srclo, d_tgtlo;               // their low parts (float2 per point)
   DBuf d_mQ, d_ma, d_lL0, d_lb;
   DBuf d_phi_near, d_phi_far;
+  DBuf d_m2m_arrive;                // uniform upward pass: arrivals per cell
+  DBuf d_l2l_ready;                 // uniform downward pass: counter + ready word per cell
   DBuf d_fnear;                        // near part of the field (fmm2d_evaluate_field)
   DBuf d_sten, d_geo_scale;
   DBuf d_m2l_ops, d_m2l_logz, d_m2m_ops, d_l2l_ops;   // element type per precision
@@ -283,6 +285,22 @@ cudaError_t launch_gather_u(const void *u, bool f32_in, const uint32_t *perm, in
 template <typename R>
 cudaError_t launch_p2m(const ExpandArgs &a, const R *src4, const int *start, const int *end,
                        double *mQ, Cx<R> *ma, cudaStream_t s);
+// Uniform tree: the downward pass of levels l_min+1 .. L (cells first ..
+// first + total) in one persistent launch; ready: n_cells + 2 ints, zeroed
+// here; a bounded wait that gives up ORs 2 into *err.
+template <typename R>
+cudaError_t launch_l2l_down(const ExpandArgs &a, const Geo &g, int64_t first, int64_t total,
+                            const int64_t *lev_first_dev, const int *map, const uint32_t *cell_key,
+                            const uint8_t *cell_cls, const Cx<R> *ops, double *lL0, Cx<R> *lb,
+                            int *ready, int64_t n_cells, int sms, int *err, cudaStream_t s);
+// Uniform tree: the upward pass of levels L-1 .. l_min in one launch (cells
+// of level L-1 first at first .. first + count; arrive: n_cells ints, zeroed
+// here).
+template <typename R>
+cudaError_t launch_m2m_up(const ExpandArgs &a, const Geo &g, int l_min, int64_t first, int64_t count,
+                          const int *map, const uint32_t *cell_key, const uint8_t *cell_cls,
+                          const uint8_t *cell_hsrc, const Cx<R> *ops, double *mQ, Cx<R> *ma,
+                          int *arrive, int64_t n_cells, cudaStream_t s);
 template <typename R>
 cudaError_t launch_m2m(const ExpandArgs &a, const Geo &g, int level, int64_t first, int64_t count,
                        const int *map, const uint32_t *cell_key, const uint8_t *cell_cls,
