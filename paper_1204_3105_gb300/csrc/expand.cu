@@ -264,7 +264,7 @@ k_m2m(ExpandArgs a, Geo g, int level, int64_t first, int64_t count, const int *_
 // once, by one warp, with its children in child order, so the result is the
 // one of the level-by-level form; no warp waits for another.  Multipoles
 // written in this launch are read through L2 (ld.global.cg).
-template <typename R>
+template <typename R, bool STAGED>
 __global__ void __launch_bounds__(32 * WPB)
 k_m2m_up(ExpandArgs a, Geo g, int l_min, int64_t first, int64_t count,
          const int *__restrict__ map, const uint32_t *__restrict__ cell_key,
@@ -272,20 +272,18 @@ k_m2m_up(ExpandArgs a, Geo g, int l_min, int64_t first, int64_t count,
          const Cx<R> *__restrict__ ops, int n_staged, double *mQ, Cx<R> *ma,
          int *__restrict__ arrive) {
   constexpr int NB = 7;                        // children of a cell, at most
-  constexpr int NLD = (NB * MAXP + 31) / 32;   // multipole loads per lane, at most
   constexpr unsigned FULL = 0xffffffffu;
   __shared__ Cx<R> sh[WPB][NB][MAXP + 1];
   extern __shared__ __align__(16) unsigned char dyn_ops[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t ci = blockIdx.x * (int64_t)WPB + w;
   const int p = a.p, P1 = p + 1;
-  const Cx<R> *op_tab = ops;
-  if (n_staged > 0) {   // the operators in shared memory: every cell reads them
-    Cx<R> *so = reinterpret_cast<Cx<R> *>(dyn_ops);
+  Cx<R> *so = reinterpret_cast<Cx<R> *>(dyn_ops);
+  if (STAGED) {   // the operators in shared memory: every cell reads them
     for (int i = threadIdx.x; i < n_staged; i += blockDim.x) so[i] = ops[i];
     __syncthreads();
-    op_tab = so;
   }
+  const Cx<R> *op_tab = STAGED ? so : ops;
   if (ci >= count) return;
   int64_t gp = first + ci;
   int level = a.L - 1;
@@ -293,7 +291,8 @@ k_m2m_up(ExpandArgs a, Geo g, int l_min, int64_t first, int64_t count,
     // the cell's fields and its children's slots
     const bool hs = cell_hsrc[gp];
     const uint32_t key = cell_key[gp];
-    int nch = hs ? g.b : 0, cs = -1;
+    const int nch = hs ? g.b : 0;
+    int cs = -1;
     if (lane < nch) cs = map[g.map_off[level + 1] + (int64_t)key * g.b + lane];
     int use = 0, cls = 0;
     double Qc = 0.0;
@@ -302,26 +301,24 @@ k_m2m_up(ExpandArgs a, Geo g, int l_min, int64_t first, int64_t count,
       Qc = __ldcg(&mQ[cs]);
       cls = cell_cls[cs];
     }
-    Cx<R> v[NLD];
-    const int nv = nch * p;
+    // lane k: coefficient k (and k + 32) of every child, loaded together
+    Cx<R> v0[NB], v1[NB];
 #pragma unroll
-    for (int r = 0; r < NLD; ++r) {
-      const int idx = lane + 32 * r;
-      const int d = min(idx / max(p, 1), 31);
+    for (int d = 0; d < NB; ++d) {
       const int cd = __shfl_sync(FULL, cs, d);
-      v[r] = Cx<R>{(R)0, (R)0};
-      if (idx < nv && cd >= 0) {
-        const R *src = reinterpret_cast<const R *>(&ma[(int64_t)cd * a.P + (idx - d * p)]);
-        v[r] = Cx<R>{__ldcg(src), __ldcg(src + 1)};
+      v0[d] = v1[d] = Cx<R>{(R)0, (R)0};
+      if (d < nch && cd >= 0) {
+        const R *src = reinterpret_cast<const R *>(&ma[(int64_t)cd * a.P]);
+        if (lane < p) v0[d] = Cx<R>{__ldcg(src + 2 * lane), __ldcg(src + 2 * lane + 1)};
+        if (lane + 32 < p) v1[d] = Cx<R>{__ldcg(src + 2 * lane + 64), __ldcg(src + 2 * lane + 65)};
       }
     }
     __syncwarp();
 #pragma unroll
-    for (int r = 0; r < NLD; ++r) {
-      const int idx = lane + 32 * r;
-      if (idx < nv) {
-        const int d = idx / p;
-        sh[w][d][idx - d * p + 1] = v[r];
+    for (int d = 0; d < NB; ++d) {
+      if (d < nch) {
+        if (lane < p) sh[w][d][lane + 1] = v0[d];
+        if (lane + 32 < p) sh[w][d][lane + 33] = v1[d];
       }
     }
     __syncwarp();
@@ -340,6 +337,7 @@ k_m2m_up(ExpandArgs a, Geo g, int l_min, int64_t first, int64_t count,
         if (l > p) break;
         const Cx<R> *row = op + (int64_t)l * P1;
         Cx<R> s = q * row[0];
+#pragma unroll 4
         for (int k = 1; k <= l; ++k) cfma(s, row[k], sh[w][d][k]);
         if (h == 0) acc0 = acc0 + s; else acc1 = acc1 + s;
       }
@@ -375,7 +373,7 @@ k_m2m_up(ExpandArgs a, Geo g, int l_min, int64_t first, int64_t count,
 // parent local to the cell's own (M2L) local, and sets the cell's ready word.
 // Each cell is computed once, as in the level-by-level form.  Locals written
 // in this launch are read through L2 (ld.global.cg).
-template <typename R>
+template <typename R, bool STAGED>
 __global__ void __launch_bounds__(32 * WPB)
 k_l2l_down(ExpandArgs a, Geo g, int64_t first, int64_t total, int64_t fixed_end,
            const int64_t *__restrict__ lev_first, const int *__restrict__ map,
@@ -388,13 +386,12 @@ k_l2l_down(ExpandArgs a, Geo g, int64_t first, int64_t total, int64_t fixed_end,
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int p = a.p, P1 = p + 1;
   const int k0 = lane, k1 = lane + 32;
-  const Cx<R> *op_tab = ops;
-  if (n_staged > 0) {   // the operators in shared memory: every cell reads them
-    Cx<R> *so = reinterpret_cast<Cx<R> *>(dyn_ops);
+  Cx<R> *so = reinterpret_cast<Cx<R> *>(dyn_ops);
+  if (STAGED) {   // the operators in shared memory: every cell reads them
     for (int i = threadIdx.x; i < n_staged; i += blockDim.x) so[i] = ops[i];
     __syncthreads();
-    op_tab = so;
   }
+  const Cx<R> *op_tab = STAGED ? so : ops;
   for (;;) {
     int64_t idx = 0;
     if (lane == 0) idx = atomicAdd(reinterpret_cast<unsigned long long *>(ctr), 1ull);
@@ -445,6 +442,7 @@ k_l2l_down(ExpandArgs a, Geo g, int64_t first, int64_t total, int64_t fixed_end,
       if (k > p) break;
       const Cx<R> *row = U + (int64_t)k * P1;
       Cx<R> s = {(R)0, (R)0};
+#pragma unroll 4
       for (int l = (k > 1 ? k : 1); l <= p; ++l) cfma(s, row[l], sh[w][l]);
       if (k == 0) lL0[gc] = L0 + (Lp + (double)s.x);
       else lb[gc * a.P + k - 1] = (h == 0 ? own0 : own1) + s;
@@ -626,9 +624,14 @@ cudaError_t launch_l2l_down(const ExpandArgs &a, const Geo &g, int64_t first, in
   if (e != cudaSuccess) return e;
   const int n_st = staged_ops<R>(a, sizeof(Cx<R>) * WPB * (MAXP + 1));
   const unsigned blocks = (unsigned)std::min<int64_t>(wblocks(total), (int64_t)sms * 8);
-  k_l2l_down<R><<<blocks, 32 * WPB, n_st * sizeof(Cx<R>), s>>>(
-      a, g, first, total, first, lev_first_dev, map, cell_key, cell_cls, ops, n_st, lL0, lb,
-      ready + 2, ready, err);
+  if (n_st > 0)
+    k_l2l_down<R, true><<<blocks, 32 * WPB, n_st * sizeof(Cx<R>), s>>>(
+        a, g, first, total, first, lev_first_dev, map, cell_key, cell_cls, ops, n_st, lL0, lb,
+        ready + 2, ready, err);
+  else
+    k_l2l_down<R, false><<<blocks, 32 * WPB, 0, s>>>(
+        a, g, first, total, first, lev_first_dev, map, cell_key, cell_cls, ops, 0, lL0, lb,
+        ready + 2, ready, err);
   return cudaGetLastError();
 }
 
@@ -674,8 +677,12 @@ cudaError_t launch_m2m_up(const ExpandArgs &a, const Geo &g, int l_min, int64_t 
   cudaError_t e = cudaMemsetAsync(arrive, 0, (size_t)n_cells * sizeof(int), s);
   if (e != cudaSuccess) return e;
   const int n_st = staged_ops<R>(a, sizeof(Cx<R>) * WPB * 7 * (MAXP + 1));
-  k_m2m_up<R><<<wblocks(count), 32 * WPB, n_st * sizeof(Cx<R>), s>>>(
-      a, g, l_min, first, count, map, cell_key, cell_cls, cell_hsrc, ops, n_st, mQ, ma, arrive);
+  if (n_st > 0)
+    k_m2m_up<R, true><<<wblocks(count), 32 * WPB, n_st * sizeof(Cx<R>), s>>>(
+        a, g, l_min, first, count, map, cell_key, cell_cls, cell_hsrc, ops, n_st, mQ, ma, arrive);
+  else
+    k_m2m_up<R, false><<<wblocks(count), 32 * WPB, 0, s>>>(
+        a, g, l_min, first, count, map, cell_key, cell_cls, cell_hsrc, ops, 0, mQ, ma, arrive);
   return cudaGetLastError();
 }
 
