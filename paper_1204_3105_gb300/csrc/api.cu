@@ -764,11 +764,12 @@ fmm2d_status evaluate_t(fmm2d_plan *pl, const void *u, double *out, cudaStream_t
        "m2l");
   }
   {
-    // levels l_min+1 .. L in one launch
-    StageScope sc(pl, ST_L2L, f, L > pl->l_min ? 1 : 0);
-    if (L > pl->l_min) {
+    // levels l_min+1 .. L-1 in one launch; the leaf level's L2L is done by
+    // the L2P
+    StageScope sc(pl, ST_L2L, f, L - 1 > pl->l_min ? 1 : 0);
+    if (L - 1 > pl->l_min) {
       const int64_t first = pl->lev_first[pl->l_min + 1];
-      CK(launch_l2l_down<R>(a, pl->geo, first, pl->n_cells - first, (const int64_t *)pl->d_lev_first.p,
+      CK(launch_l2l_down<R>(a, pl->geo, first, pl->lev_first[L] - first, (const int64_t *)pl->d_lev_first.p,
                             (const int *)pl->d_map.p, (const uint32_t *)pl->d_cell_key.p,
                             (const uint8_t *)pl->d_cell_cls.p, (const Cx<R> *)pl->d_l2l_ops.p, lL0,
                             lb, (int *)pl->d_l2l_ready.p, pl->n_cells, pl->n_sms,
@@ -804,6 +805,14 @@ fmm2d_status evaluate_t(fmm2d_plan *pl, const void *u, double *out, cudaStream_t
   }
   {
     StageScope sc(pl, ST_L2P, s, 1);
+    if (L > pl->l_min) {   // the leaf level's L2L
+      a.l2l_map = (const int *)pl->d_map.p;
+      a.l2l_map_off = pl->geo.map_off[L - 1];
+      a.l2l_key = (const uint32_t *)pl->d_cell_key.p;
+      a.l2l_cls = (const uint8_t *)pl->d_cell_cls.p;
+      a.l2l_ops = pl->d_l2l_ops.p;
+      a.l2l_sept = pl->tiling == FMM2D_SEPT;
+    }
     CK(launch_l2p<R>(a, tgt, tstride, tst, ten, tperm, lL0, lb, (const double *)pl->d_phi_near.p,
                      (double *)pl->d_phi_far.p, out, s),
        "l2p");

@@ -92,6 +92,74 @@ k_p2m(ExpandArgs a, const R *__restrict__ src4, const int *__restrict__ start,
 // r over the 16 points of half h.  The FP64 work per source is p complex
 // products and p / 16 partial sums (the form above repeats the powers below
 // each chunk of 8 and reduces every coefficient with shuffles).
+// FP32 P2M for p <= PM: one warp per leaf; each lane sums u z^k for
+// k = 1 .. p over its points with the powers formed once per point, then a
+// butterfly reduce-scatter over the warp (16 + 8 + 4 + 2 + 1 shuffles of
+// halving vectors) leaves lane l with float slot l (PM = 16: Re / Im of
+// coefficient l / 2 + 1) or slots 2l, 2l + 1 (PM = 32: coefficient l + 1).
+template <int PM>
+__global__ void __launch_bounds__(32 * WPB)
+k_p2m_bf(ExpandArgs a, const float *__restrict__ src4, const int *__restrict__ start,
+         const int *__restrict__ end, double *__restrict__ mQ, Cx<float> *__restrict__ ma) {
+  constexpr int NV = 2 * PM;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t li = blockIdx.x * (int64_t)WPB + (threadIdx.x >> 5);
+  if (li >= a.n_leaves) return;
+  const int64_t g = a.leaf_ids ? (int64_t)a.leaf_ids[li] : a.leaf_first + li;
+  const int s = start[g], e = end[g];
+  Cx<float> is = {(float)a.inv_s_re, (float)a.inv_s_im};
+  if (a.leaf_ids) {
+    const double2 v = a.inv_scale[a.cell_lev[g]];
+    is = {(float)v.x, (float)v.y};
+  }
+  const int p = a.p;
+  float v[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = 0.f;
+  double q = 0.0;
+  for (int i = s + lane; i < e; i += 32) {
+    const float4 pt = reinterpret_cast<const float4 *>(src4)[i];
+    const Cx<float> z = Cx<float>{pt.x, pt.y} * is;
+    Cx<float> w = {pt.z, 0.f};
+    q += (double)pt.z;
+#pragma unroll
+    for (int k = 0; k < PM; ++k) {
+      if (k < p) {
+        w = w * z;
+        v[2 * k] += w.x;
+        v[2 * k + 1] += w.y;
+      }
+    }
+  }
+  q = warp_sum(q);
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    const int o = 16 >> r, m = NV >> r;   // partner distance, current length
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < m / 2; ++i) {
+      const float send = up ? v[i] : v[i + m / 2];
+      const float keep = up ? v[i + m / 2] : v[i];
+      v[i] = keep + __shfl_xor_sync(FULL, send, o);
+    }
+  }
+  if (lane == 0) mQ[g] = q;
+  if (PM == 16) {
+    const int k = lane >> 1;
+    if (k < p) {
+      const float inv = -1.f / (float)(k + 1);
+      reinterpret_cast<float *>(ma)[(g * a.P + k) * 2 + (lane & 1)] = v[0] * inv;
+    }
+  } else {
+    const int k = lane;
+    if (k < p) {
+      const float inv = -1.f / (float)(k + 1);
+      ma[g * a.P + k] = Cx<float>{v[0] * inv, v[1] * inv};
+    }
+  }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(32 * WPB)
 k_p2m_t(ExpandArgs a, const R *__restrict__ src4, const int *__restrict__ start,
@@ -569,20 +637,59 @@ k_l2l(ExpandArgs a, Geo g, int level, int64_t first, int64_t count, const int *_
 template <typename R>
 __global__ void __launch_bounds__(32 * WPB)
 k_l2p(ExpandArgs a, const R *__restrict__ tgt, int tstride, const int *__restrict__ start,
-      const int *__restrict__ end, const uint32_t *__restrict__ perm, const double *__restrict__ lL0,
-      const Cx<R> *__restrict__ lb, const double *__restrict__ phi_near,
+      const int *__restrict__ end, const uint32_t *__restrict__ perm, double *__restrict__ lL0,
+      Cx<R> *__restrict__ lb, const double *__restrict__ phi_near,
       double *__restrict__ phi_far, double *__restrict__ out) {
   __shared__ Cx<R> sh[WPB][MAXP + 1];
+  __shared__ Cx<R> shp[WPB][MAXP + 1];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t li = blockIdx.x * (int64_t)WPB + w;
   if (li >= a.n_leaves) return;
   const int64_t g = a.leaf_ids ? (int64_t)a.leaf_ids[li] : a.leaf_first + li;
   const int s = start[g], e = end[g];
-  if (s >= e) return;
   const int p = a.p;
-  for (int k = lane; k < p; k += 32) sh[w][k + 1] = lb[g * a.P + k];
-  __syncwarp();
-  const double L0 = lL0[g];
+  double L0;
+  if (a.l2l_map) {
+    // the leaf's L2L: own (M2L) local + the parent's shifted final local
+    const uint32_t key = a.l2l_key[g];
+    const int ps = a.l2l_map[a.l2l_map_off + (a.l2l_sept ? key / 7u : key >> 2)];
+    const int cls = a.l2l_cls[g];
+    const int P1 = p + 1;
+    for (int k = lane; k < p; k += 32) shp[w][k + 1] = lb[(int64_t)ps * a.P + k];
+    double Lp = 0.0, Lown = 0.0;
+    if (lane == 0) {
+      Lp = lL0[ps];
+      Lown = lL0[g];
+    }
+    __syncwarp();
+    const Cx<R> *U = reinterpret_cast<const Cx<R> *>(a.l2l_ops) + (int64_t)cls * P1 * P1;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = lane + 32 * h;
+      if (k > p) break;
+      const Cx<R> *row = U + (int64_t)k * P1;
+      Cx<R> sv = {(R)0, (R)0};
+#pragma unroll 4
+      for (int l = (k > 1 ? k : 1); l <= p; ++l) cfma(sv, row[l], shp[w][l]);
+      if (k == 0) {
+        const double L = Lown + (Lp + (double)sv.x);
+        lL0[g] = L;
+        Lown = L;
+      } else {
+        const Cx<R> fin = lb[g * a.P + k - 1] + sv;
+        lb[g * a.P + k - 1] = fin;
+        sh[w][k] = fin;
+      }
+    }
+    L0 = __shfl_sync(0xffffffffu, Lown, 0);
+    __syncwarp();
+  } else {
+    if (s >= e) return;
+    for (int k = lane; k < p; k += 32) sh[w][k + 1] = lb[g * a.P + k];
+    __syncwarp();
+    L0 = lL0[g];
+  }
+  if (s >= e) return;
   Cx<R> is = {(R)a.inv_s_re, (R)a.inv_s_im};
   if (a.leaf_ids) {
     const double2 v = a.inv_scale[a.cell_lev[g]];
@@ -650,6 +757,10 @@ cudaError_t launch_p2m(const ExpandArgs &a, const R *src4, const int *start, con
   if (a.n_leaves <= 0) return cudaSuccess;
   if constexpr (sizeof(R) == 8) {   // FP64: the powers-per-point form
     k_p2m_t<R><<<wblocks(a.n_leaves), 32 * WPB, 0, s>>>(a, src4, start, end, mQ, ma);
+  } else if (a.p <= 16) {
+    k_p2m_bf<16><<<wblocks(a.n_leaves), 32 * WPB, 0, s>>>(a, src4, start, end, mQ, ma);
+  } else if (a.p <= 32) {
+    k_p2m_bf<32><<<wblocks(a.n_leaves), 32 * WPB, 0, s>>>(a, src4, start, end, mQ, ma);
   } else {
     k_p2m<R, 8><<<wblocks(a.n_leaves), 32 * WPB, 0, s>>>(a, src4, start, end, mQ, ma);
   }
@@ -711,7 +822,7 @@ cudaError_t launch_l2l(const ExpandArgs &a, const Geo &g, int level, int64_t fir
 
 template <typename R>
 cudaError_t launch_l2p(const ExpandArgs &a, const R *tgt, int tstride, const int *start,
-                       const int *end, const uint32_t *perm, const double *lL0, const Cx<R> *lb,
+                       const int *end, const uint32_t *perm, double *lL0, Cx<R> *lb,
                        const double *phi_near, double *phi_far, double *out, cudaStream_t s) {
   if (a.n_leaves <= 0) return cudaSuccess;
   k_l2p<R><<<wblocks(a.n_leaves), 32 * WPB, 0, s>>>(a, tgt, tstride, start, end, perm, lL0, lb,
@@ -745,7 +856,7 @@ cudaError_t launch_l2p(const ExpandArgs &a, const R *tgt, int tstride, const int
                                      const int *, const uint32_t *, const uint8_t *,              \
                                      const Cx<R> *, double *, Cx<R> *, cudaStream_t);             \
   template cudaError_t launch_l2p<R>(const ExpandArgs &, const R *, int, const int *, const int *, \
-                                     const uint32_t *, const double *, const Cx<R> *,             \
+                                     const uint32_t *, double *, Cx<R> *,                         \
                                      const double *, double *, double *, cudaStream_t);
 INST(float)
 INST(double)

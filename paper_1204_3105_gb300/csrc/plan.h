@@ -278,6 +278,14 @@ struct ExpandArgs {
   const int *child_first = nullptr;
   const uint8_t *child_cnt = nullptr;
   const int *parent = nullptr;
+  // uniform tree: the L2L of the leaf level done by the L2P (the leaf's M2L
+  // local plus its parent's shifted final local, written back to lL0 / lb)
+  const int *l2l_map = nullptr;          // key -> slot map, level L-1 part at l2l_map_off
+  int64_t l2l_map_off = 0;
+  const uint32_t *l2l_key = nullptr;     // cell keys
+  const uint8_t *l2l_cls = nullptr;      // child classes
+  const void *l2l_ops = nullptr;         // L2L operator table (Cx<R>)
+  int l2l_sept = 0;                      // parent key = key / 7 (septree), else key >> 2
 };
 template <typename R>
 cudaError_t launch_gather_u(const void *u, bool f32_in, const uint32_t *perm, int64_t n, R *src4,
@@ -318,7 +326,7 @@ cudaError_t launch_l2l(const ExpandArgs &a, const Geo &g, int level, int64_t fir
                        const Cx<R> *ops, double *lL0, Cx<R> *lb, cudaStream_t s);
 template <typename R>
 cudaError_t launch_l2p(const ExpandArgs &a, const R *tgt, int tstride, const int *start,
-                       const int *end, const uint32_t *perm, const double *lL0, const Cx<R> *lb,
+                       const int *end, const uint32_t *perm, double *lL0, Cx<R> *lb,
                        const double *phi_near, double *phi_far, double *out, cudaStream_t s);
 
 // ---------------------------------------------------------------- m2l_tc.cu
