@@ -62,16 +62,79 @@ __device__ __forceinline__ int lower_bound_u32(const uint32_t *__restrict__ k, i
   return lo;
 }
 
-// cell of level-l key `key` in the sorted key range [first, first + count), or -1
-__device__ __forceinline__ int find_cell(const uint32_t *__restrict__ ckey, int64_t first, int64_t count,
-                                         uint32_t key) {
-  int64_t lo = first, hi = first + count;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (ckey[mid] < key) lo = mid + 1;
-    else hi = mid;
+__device__ __forceinline__ uint64_t ad_hash(uint64_t x) {   // a 64-bit mixer (splitmix64 finaliser)
+  x ^= x >> 30;
+  x *= 0xbf58476d1ce4e5b9ull;
+  x ^= x >> 27;
+  x *= 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
+
+// Table key of the level-l lattice position q of instance `inst`, or false
+// when q cannot be a cell of level l (so that it never aliases another):
+//  * quad and tri: inst * 4^l + x * 2^l + y, below 2^32 as the level's cell
+//    keys are; a tri position must also have x + y + z = 2^l - 1 (an up
+//    triangle, bit 58) or 2^l - 2, and z in range (Sec. 6);
+//  * septree: the Eisenstein coordinates (a, b) of every level-l cell obey
+//    |a|, |b| < 7^(l/2) (the cell is a sum of l units times powers of the
+//    base, whose modulus is sqrt 7), so each, biased, fits cb = (3l+1)/2 + 2
+//    bits, and inst * 2^(2 cb) < 2^40 for the instances a 32-bit key allows.
+// Level + 1 sits in bits 59-63, so no key is 0 (the empty slot).
+__device__ __forceinline__ bool crd_key(int tiling, int l, uint32_t inst, int4 q, uint64_t *out) {
+  uint64_t u;
+  if (tiling == FMM2D_SEPT) {
+    const int cb = (3 * l + 1) / 2 + 2;
+    const int half = 1 << (cb - 1);
+    if (q.x < -half || q.x >= half || q.y < -half || q.y >= half) return false;
+    u = ((uint64_t)inst << (2 * cb)) | ((uint64_t)(q.x + half) << cb) | (uint64_t)(q.y + half);
+  } else {
+    const int n = 1 << l;
+    if (q.x < 0 || q.y < 0 || q.x >= n || q.y >= n) return false;
+    u = ((uint64_t)inst << (2 * l)) | ((uint64_t)q.x << l) | (uint64_t)q.y;
+    if (tiling == FMM2D_TRI) {
+      const int sum = q.x + q.y + q.z;
+      if (q.z < 0 || q.z >= n || (sum != n - 1 && sum != n - 2)) return false;
+      if (sum == n - 1) u |= 1ull << 58;
+    }
   }
-  return (lo < first + count && ckey[lo] == key) ? (int)lo : -1;
+  *out = ((uint64_t)(l + 1) << 59) | u;
+  return true;
+}
+
+// The cell at level-l lattice position q of instance `inst`, or -1 (no such
+// cell in the tree): linear probing in the (level, instance, position) table.
+__device__ __forceinline__ int find_cell(const AdCells &c, int tiling, int l, uint32_t inst, int4 q) {
+  uint64_t k;
+  if (!crd_key(tiling, l, inst, q, &k)) return -1;
+  uint32_t h = (uint32_t)ad_hash(k) & c.hmask;
+  for (uint32_t probe = 0; probe <= c.hmask; ++probe) {
+    const uint64_t e = c.hkey[h];
+    if (e == k) return c.hval[h];
+    if (e == 0) return -1;
+    h = (h + 1) & c.hmask;
+  }
+  return -1;
+}
+
+// Does the level-lf lattice position q lie inside the coarser level-lc cell
+// (position ccrd, local key ckey)?  Quad and tri: the ancestor d levels up
+// of a position is the position shifted right by d (a key's digits are the
+// bits of the coordinates, Sec. 6), so no key is formed; septree: through
+// the key of q.
+__device__ __forceinline__ bool inside_coarse(const Geo &g, int lf, int4 q, int lc, int4 ccrd,
+                                              uint32_t ckey) {
+  if (g.tiling == FMM2D_SEPT) {
+    uint32_t k;
+    return cell_at(g, lf, q, &k) && parent_key(g.tiling, k, lf - lc) == ckey;
+  }
+  const int n = 1 << lf, d = lf - lc;
+  if (q.x < 0 || q.y < 0 || q.x >= n || q.y >= n) return false;
+  if (g.tiling == FMM2D_TRI) {
+    const int sum = q.x + q.y + q.z;
+    if (q.z < 0 || q.z >= n || (sum != n - 1 && sum != n - 2)) return false;
+    if ((q.z >> d) != ccrd.z) return false;
+  }
+  return (q.x >> d) == ccrd.x && (q.y >> d) == ccrd.y;
 }
 
 // One level-0 cell per instance: instance i owns sources [soff[i], soff[i+1])
@@ -275,15 +338,15 @@ struct Emitter {
   }
 };
 
-// true when no cell of Near(fine, lf) lies inside the coarser cell `coarse`
-__device__ bool separated(const Geo &g, const Stencils &st, int lf, int4 fcrd, int lc, uint32_t coarse) {
+// true when no cell of Near(fine, lf) lies inside the coarser cell
+// (level lc, position ccrd, local key ckey)
+__device__ bool separated(const Geo &g, const Stencils &st, int lf, int4 fcrd, int lc, int4 ccrd,
+                          uint32_t ckey) {
   const int o = (g.tiling == FMM2D_TRI && fcrd.w == 0) ? 1 : 0;
   for (int e = 0; e < st.near_len[o]; ++e) {
     const int4 q = make_int4(fcrd.x + st.near_d[o][e][0], fcrd.y + st.near_d[o][e][1],
                              fcrd.z + st.near_d[o][e][2], 0);
-    uint32_t k;
-    if (!cell_at(g, lf, q, &k)) continue;
-    if (parent_key(g.tiling, k, lf - lc) == coarse) return false;
+    if (inside_coarse(g, lf, q, lc, ccrd, ckey)) return false;
   }
   return true;
 }
@@ -310,16 +373,13 @@ __global__ void k_ad_lists_1t(Geo g, const Stencils *__restrict__ stp, int l, in
     const int4 ca = c.crd[a];
     uint32_t inst;
     local_key(g.b, l, c.key[a], &inst);
-    const uint32_t ibase = (uint32_t)((uint64_t)inst * level_span(g.b, l));
     if (a_tgt) {
       const int o = (g.tiling == FMM2D_TRI && ca.w == 0) ? 1 : 0;
       const bool a_leaf = !c.split[a];
       for (int e = 0; e < st.near_len[o]; ++e) {
         const int4 q = make_int4(ca.x + st.near_d[o][e][0], ca.y + st.near_d[o][e][1],
                                  ca.z + st.near_d[o][e][2], 0);
-        uint32_t k;
-        if (!cell_at(g, l, q, &k)) continue;
-        const int m = find_cell(c.key, first, count, ibase + k);
+        const int m = find_cell(c, g.tiling, l, inst, q);
         if (m < 0 || !c.hsrc[m]) continue;
         const bool m_leaf = !c.split[m];
         if (a_leaf && m_leaf) {
@@ -347,11 +407,8 @@ __global__ void k_ad_lists_1t(Geo g, const Stencils *__restrict__ stp, int l, in
         if (e < n_far) {
           const int4 q = make_int4(ca.x + st.far_d[cls][e][0], ca.y + st.far_d[cls][e][1],
                                    ca.z + st.far_d[cls][e][2], 0);
-          uint32_t k;
-          if (cell_at(g, l, q, &k)) {
-            sidx = find_cell(c.key, first, count, ibase + k);
-            if (sidx >= 0 && !c.hsrc[sidx]) sidx = -1;
-          }
+          sidx = find_cell(c, g.tiling, l, inst, q);
+          if (sidx >= 0 && !c.hsrc[sidx]) sidx = -1;
         }
         if (far_full) far_full[fi * FAR_MAX + e] = sidx;
         if (sidx < 0) continue;
@@ -369,7 +426,7 @@ __global__ void k_ad_lists_1t(Geo g, const Stencils *__restrict__ stp, int l, in
     const int64_t j = it - count;
     const int a = t_a[j], cc = t_c[j];
     uint32_t inst;
-    if (separated(g, st, l, c.crd[cc], c.lev[a], local_key(g.b, c.lev[a], c.key[a], &inst)))
+    if (separated(g, st, l, c.crd[cc], c.lev[a], c.crd[a], local_key(g.b, c.lev[a], c.key[a], &inst)))
       em.put(K_W, a, cc);
     else if (!c.split[cc]) em.put(K_U, a, cc);
     else
@@ -381,7 +438,7 @@ __global__ void k_ad_lists_1t(Geo g, const Stencils *__restrict__ stp, int l, in
     const int64_t j = it - count - n_t;
     const int a = s_a[j], cc = s_c[j];
     uint32_t inst;
-    if (separated(g, st, l, c.crd[a], c.lev[cc], local_key(g.b, c.lev[cc], c.key[cc], &inst)))
+    if (separated(g, st, l, c.crd[a], c.lev[cc], c.crd[cc], local_key(g.b, c.lev[cc], c.key[cc], &inst)))
       em.put(K_X, a, cc);
     else if (!c.split[a]) em.put(K_U, a, cc);
     else
@@ -421,8 +478,7 @@ __global__ void k_ad_lists(Geo g, const Stencils *__restrict__ stp, int l, int64
   if (sub < st.near_len[o]) {
     const int4 q = make_int4(fcrd.x + st.near_d[o][sub][0], fcrd.y + st.near_d[o][sub][1],
                              fcrd.z + st.near_d[o][sub][2], 0);
-    uint32_t k;
-    if (cell_at(g, l, q, &k)) inside = parent_key(g.tiling, k, l - lc) == ckey;
+    inside = inside_coarse(g, l, q, lc, c.crd[coarse], ckey);
   }
   const bool sep = __ballot_sync(hmask, inside) == 0u;
   if (sub != 0) return;
@@ -468,7 +524,6 @@ __global__ void k_ad_cell_lists(Geo g, const Stencils *__restrict__ stp, int l, 
   const int4 ca = c.crd[a];
   uint32_t inst;
   local_key(g.b, l, c.key[a], &inst);
-  const uint32_t ibase = (uint32_t)((uint64_t)inst * level_span(g.b, l));
   // near stencil entry `lane`: U (a, m), T (a, child of m) or S (child of a, m)
   int m = -1, mode = 0, nk = 0;
   if (a_tgt) {
@@ -476,11 +531,8 @@ __global__ void k_ad_cell_lists(Geo g, const Stencils *__restrict__ stp, int l, 
     if (lane < st.near_len[o]) {
       const int4 q = make_int4(ca.x + st.near_d[o][lane][0], ca.y + st.near_d[o][lane][1],
                                ca.z + st.near_d[o][lane][2], 0);
-      uint32_t k;
-      if (cell_at(g, l, q, &k)) {
-        m = find_cell(c.key, first, count, ibase + k);
-        if (m >= 0 && !c.hsrc[m]) m = -1;
-      }
+      m = find_cell(c, g.tiling, l, inst, q);
+      if (m >= 0 && !c.hsrc[m]) m = -1;
       if (m >= 0) {
         const bool a_leaf = !c.split[a], m_leaf = !c.split[m];
         if (a_leaf && m_leaf) {
@@ -559,11 +611,8 @@ __global__ void k_ad_cell_lists(Geo g, const Stencils *__restrict__ stp, int l, 
       if (e < n_far) {
         const int4 q = make_int4(ca.x + st.far_d[cls][e][0], ca.y + st.far_d[cls][e][1],
                                  ca.z + st.far_d[cls][e][2], 0);
-        uint32_t k;
-        if (cell_at(g, l, q, &k)) {
-          sidx = find_cell(c.key, first, count, ibase + k);
-          if (sidx >= 0 && !c.hsrc[sidx]) sidx = -1;
-        }
+        sidx = find_cell(c, g.tiling, l, inst, q);
+        if (sidx >= 0 && !c.hsrc[sidx]) sidx = -1;
       }
       if (far_full && e < fl) far_full[fi * FAR_MAX + e] = sidx;
       const unsigned bal = __ballot_sync(0xffffffffu, sidx >= 0);
@@ -818,6 +867,37 @@ cudaError_t ad_launch_rel(bool f32_in, bool f32_out, const void *xy, const uint3
 // cooperative forms (32 lanes per cell, 16 per test) would mostly idle lanes.
 constexpr int64_t COOP_MAX_CELLS = (int64_t)1 << 18;
 constexpr int64_t COOP_MAX_TESTS = (int64_t)1 << 19;
+
+namespace {
+__global__ void k_ad_hash(Geo g, int64_t n, AdCells c, unsigned long long *__restrict__ hkey,
+                          int *__restrict__ hval, uint32_t hmask) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int l = c.lev[i];
+  uint32_t inst;
+  local_key(g.b, l, c.key[i], &inst);
+  uint64_t k;
+  if (!crd_key(g.tiling, l, inst, c.crd[i], &k)) return;   // never for a cell of the tree
+  uint32_t h = (uint32_t)ad_hash(k) & hmask;
+  for (uint32_t probe = 0; probe <= hmask; ++probe) {
+    const unsigned long long prev = atomicCAS(&hkey[h], 0ull, (unsigned long long)k);
+    if (prev == 0ull || prev == k) {
+      hval[h] = (int)i;
+      return;
+    }
+    h = (h + 1) & hmask;
+  }
+}
+}  // namespace
+
+cudaError_t ad_launch_hash(const Geo &g, int64_t n_cells, const AdCells &c, uint64_t *hkey, int *hval,
+                           uint32_t hmask, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(hkey, 0, ((size_t)hmask + 1) * sizeof(uint64_t), s);
+  if (e != cudaSuccess || n_cells <= 0) return e;
+  k_ad_hash<<<nblk(n_cells, 256), 256, 0, s>>>(g, n_cells, c, reinterpret_cast<unsigned long long *>(hkey),
+                                               hval, hmask);
+  return cudaGetLastError();
+}
 
 cudaError_t ad_launch_lists(const Geo &g, const Stencils *d_sten, int l, int l_min, int64_t first,
                             int64_t count, int64_t n_t, int64_t n_s, const int *t_a, const int *t_c,

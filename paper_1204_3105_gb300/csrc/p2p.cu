@@ -855,27 +855,49 @@ __device__ __forceinline__ int p2p_size_class(int nt) {
   return 3 * nt <= 128 ? 0 : (3 * nt <= 256 ? 1 : (3 * nt <= 512 ? 2 : 3));
 }
 
+// One atomic per warp and class: the lanes of a class are counted by ballot
+// (all lanes of every warp take part; those past the end have no class).
 __global__ void k_p2p_bin_count(int64_t n_leaves, const int *__restrict__ leaf_ids,
                                 const int *__restrict__ ts, const int *__restrict__ te,
                                 int *__restrict__ cnt) {
   const int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (li >= n_leaves) return;
-  const int g = leaf_ids[li];
-  atomicAdd(&cnt[p2p_size_class(te[g] - ts[g])], 1);
+  const int lane = threadIdx.x & 31;
+  int c = -1;
+  if (li < n_leaves) {
+    const int g = leaf_ids[li];
+    c = p2p_size_class(te[g] - ts[g]);
+  }
+  for (int k = 0; k < 4; ++k) {
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, c == k);
+    if (m != 0u && lane == __ffs(m) - 1) atomicAdd(&cnt[k], __popc(m));
+  }
 }
 
 // order[off_c + j] = leaf position li (the order inside a class does not
-// matter: every leaf's sum is computed on its own)
+// matter: every leaf's sum is computed on its own); a warp reserves the
+// slots of its lanes of each class with one atomic
 __global__ void k_p2p_bin_scatter(int64_t n_leaves, const int *__restrict__ leaf_ids,
                                   const int *__restrict__ ts, const int *__restrict__ te,
                                   int *__restrict__ cnt, int *__restrict__ order) {
   const int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (li >= n_leaves) return;
-  const int g = leaf_ids[li];
-  const int c = p2p_size_class(te[g] - ts[g]);
+  const int lane = threadIdx.x & 31;
+  int c = -1;
+  if (li < n_leaves) {
+    const int g = leaf_ids[li];
+    c = p2p_size_class(te[g] - ts[g]);
+  }
   int off = 0;
-  for (int k = 0; k < c; ++k) off += cnt[k];
-  order[off + atomicAdd(&cnt[4 + c], 1)] = (int)li;
+  for (int k = 0; k < 4; ++k) {
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, c == k);
+    if (m != 0u) {   // warp-uniform
+      const int leader = __ffs(m) - 1;
+      int base = 0;
+      if (lane == leader) base = atomicAdd(&cnt[4 + k], __popc(m));
+      base = __shfl_sync(0xFFFFFFFFu, base, leader);
+      if (c == k) order[off + base + __popc(m & ((1u << lane) - 1u))] = (int)li;
+    }
+    off += cnt[k];
+  }
 }
 }  // namespace
 

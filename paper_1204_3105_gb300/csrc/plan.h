@@ -91,6 +91,7 @@ struct Plan {
   DBuf d_mQ, d_ma, d_lL0, d_lb;
   DBuf d_phi_near, d_phi_far;
   DBuf d_m2m_arrive;                // uniform upward pass: arrivals per cell
+  DBuf d_ad_hkey, d_ad_hval;        // adaptive tree: (level, key) -> cell table
   DBuf d_l2l_ready;                 // uniform downward pass: counter + ready word per cell
   DBuf d_fnear;                        // near part of the field (fmm2d_evaluate_field)
   DBuf d_sten, d_geo_scale;
@@ -211,7 +212,16 @@ struct AdCells {
   int4 *crd;
   double2 *ctr;
   uint8_t *cls, *hsrc;
+  // (level, instance, lattice position) -> cell: open addressing with
+  // linear probing, built once the cells exist (for the list traversal)
+  const uint64_t *hkey = nullptr;      // packed position, 0 = empty
+  const int *hval = nullptr;
+  uint32_t hmask = 0;                  // capacity - 1 (a power of two)
 };
+// Fill the (level, instance, lattice position) -> cell table of the n_cells
+// cells (hkey zeroed here; capacity hmask + 1, at least twice n_cells).
+cudaError_t ad_launch_hash(const Geo &g, int64_t n_cells, const AdCells &c, uint64_t *hkey, int *hval,
+                           uint32_t hmask, cudaStream_t s);
 // level-0 cells: one per instance (soff / toff: n_inst + 1 device offsets),
 // or one cell holding everything (null offsets, n_inst = 1)
 cudaError_t ad_launch_roots(const Geo &g, int n_inst, const int64_t *soff, const int64_t *toff,
