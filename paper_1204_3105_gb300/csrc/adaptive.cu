@@ -101,16 +101,17 @@ __device__ __forceinline__ bool crd_key(int tiling, int l, uint32_t inst, int4 q
   return true;
 }
 
-// The cell at level-l lattice position q of instance `inst`, or -1 (no such
-// cell in the tree): linear probing in the (level, instance, position) table.
+// The cell with sources at level-l lattice position q of instance `inst`, or
+// -1 (no such cell, or one without sources): linear probing in the
+// (level, instance, position) table.
 __device__ __forceinline__ int find_cell(const AdCells &c, int tiling, int l, uint32_t inst, int4 q) {
   uint64_t k;
   if (!crd_key(tiling, l, inst, q, &k)) return -1;
   uint32_t h = (uint32_t)ad_hash(k) & c.hmask;
   for (uint32_t probe = 0; probe <= c.hmask; ++probe) {
-    const uint64_t e = c.hkey[h];
-    if (e == k) return c.hval[h];
-    if (e == 0) return -1;
+    const ulonglong2 e = __ldg(&c.hslot[h]);
+    if (e.x == k) return (int)e.y;
+    if (e.x == 0) return -1;
     h = (h + 1) & c.hmask;
   }
   return -1;
@@ -380,7 +381,7 @@ __global__ void k_ad_lists_1t(Geo g, const Stencils *__restrict__ stp, int l, in
         const int4 q = make_int4(ca.x + st.near_d[o][e][0], ca.y + st.near_d[o][e][1],
                                  ca.z + st.near_d[o][e][2], 0);
         const int m = find_cell(c, g.tiling, l, inst, q);
-        if (m < 0 || !c.hsrc[m]) continue;
+        if (m < 0) continue;
         const bool m_leaf = !c.split[m];
         if (a_leaf && m_leaf) {
           em.put(K_U, a, m);
@@ -408,7 +409,6 @@ __global__ void k_ad_lists_1t(Geo g, const Stencils *__restrict__ stp, int l, in
           const int4 q = make_int4(ca.x + st.far_d[cls][e][0], ca.y + st.far_d[cls][e][1],
                                    ca.z + st.far_d[cls][e][2], 0);
           sidx = find_cell(c, g.tiling, l, inst, q);
-          if (sidx >= 0 && !c.hsrc[sidx]) sidx = -1;
         }
         if (far_full) far_full[fi * FAR_MAX + e] = sidx;
         if (sidx < 0) continue;
@@ -532,7 +532,6 @@ __global__ void k_ad_cell_lists(Geo g, const Stencils *__restrict__ stp, int l, 
       const int4 q = make_int4(ca.x + st.near_d[o][lane][0], ca.y + st.near_d[o][lane][1],
                                ca.z + st.near_d[o][lane][2], 0);
       m = find_cell(c, g.tiling, l, inst, q);
-      if (m >= 0 && !c.hsrc[m]) m = -1;
       if (m >= 0) {
         const bool a_leaf = !c.split[a], m_leaf = !c.split[m];
         if (a_leaf && m_leaf) {
@@ -612,7 +611,6 @@ __global__ void k_ad_cell_lists(Geo g, const Stencils *__restrict__ stp, int l, 
         const int4 q = make_int4(ca.x + st.far_d[cls][e][0], ca.y + st.far_d[cls][e][1],
                                  ca.z + st.far_d[cls][e][2], 0);
         sidx = find_cell(c, g.tiling, l, inst, q);
-        if (sidx >= 0 && !c.hsrc[sidx]) sidx = -1;
       }
       if (far_full && e < fl) far_full[fi * FAR_MAX + e] = sidx;
       const unsigned bal = __ballot_sync(0xffffffffu, sidx >= 0);
@@ -686,8 +684,31 @@ __device__ __forceinline__ double log_abs(Cx<R> d) {
   }
 }
 
+// Butterfly reduce-scatter of 32 values per lane over the warp: lane l ends
+// with the warp's total of value l (31 shuffles, against 32 x 5 for one
+// tree reduction per value).
+template <typename R>
+__device__ __forceinline__ R warp_reduce_scatter32(R (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const R send = up ? v[i] : v[i + o];
+      const R keep = up ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0];
+}
+
 // One warp per target leaf: phi_near[j] += sum over its W cells of the
-// cell's multipole evaluated at target j.
+// cell's multipole evaluated at target j (Horner in z = s_c / (y - c)).
+// The W cells' centres, scales and charges are fetched one per lane, 32 at
+// a time; the multipole of the next cell is loaded while the current one is
+// evaluated, and held one coefficient per lane (k and k + 32), so Horner's
+// rule takes its coefficients by shuffle.
 template <typename R>
 __global__ void __launch_bounds__(32 * AWPB)
 k_ad_m2p(int64_t n_leaves, const int *__restrict__ leaf_ids, const int *__restrict__ w_off,
@@ -695,7 +716,7 @@ k_ad_m2p(int64_t n_leaves, const int *__restrict__ leaf_ids, const int *__restri
          const int *__restrict__ ts_, const int *__restrict__ te_, const double2 *__restrict__ ctr,
          const uint8_t *__restrict__ lev, const double2 *__restrict__ scale, int p, int P,
          const double *__restrict__ mQ, const Cx<R> *__restrict__ ma, double *__restrict__ phi) {
-  __shared__ Cx<R> sh[AWPB][MAXP + 1];
+  constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t li = blockIdx.x * (int64_t)AWPB + w;
   if (li >= n_leaves) return;
@@ -704,34 +725,68 @@ k_ad_m2p(int64_t n_leaves, const int *__restrict__ leaf_ids, const int *__restri
   if (e0 == e1) return;
   const int ts = ts_[a], te = te_[a];
   const double2 ca = ctr[a];
+  auto coef = [&](const Cx<R> &c0, const Cx<R> &c1, int k) -> Cx<R> {   // k warp-uniform
+    const Cx<R> &c = k < 32 ? c0 : c1;
+    return Cx<R>{__shfl_sync(FULL, c.x, k & 31), __shfl_sync(FULL, c.y, k & 31)};
+  };
   for (int j0 = ts; j0 < te; j0 += 32) {
     const int j = j0 + lane;
     const bool act = j < te;
     const R tx = act ? tgt[(int64_t)j * tstride] : (R)0, ty = act ? tgt[(int64_t)j * tstride + 1] : (R)0;
     double acc = 0.0;
-    for (int e = e0; e < e1; ++e) {
-      const int cc = w_src[e];
-      __syncwarp();
-      for (int k = lane; k < p; k += 32) sh[w][k + 1] = ma[(int64_t)cc * P + k];
-      __syncwarp();
-      const double2 c2 = ctr[cc];
-      const double2 sc = scale[lev[cc]];
-      const Cx<R> d = {(R)(ca.x - c2.x) + tx, (R)(ca.y - c2.y) + ty};
-      const Cx<R> s = {(R)sc.x, (R)sc.y};
-      const R den = d.x * d.x + d.y * d.y;
-      const Cx<R> id = {d.x / den, -d.y / den};
-      const Cx<R> z = s * id;                       // s_c / (y - c)
-      Cx<R> h = sh[w][p];
-      for (int k = p - 1; k >= 1; --k) h = h * z + sh[w][k];
-      h = h * z;
-      acc += mQ[cc] * log_abs(d) + (double)h.x;
+    for (int eb = e0; eb < e1; eb += 32) {
+      const int nb = min(32, e1 - eb);
+      int cc = 0;
+      R dx = (R)0, dy = (R)0, sx = (R)0, sy = (R)0;
+      double qc = 0.0;
+      if (lane < nb) {
+        cc = w_src[eb + lane];
+        const double2 c2 = ctr[cc];
+        const double2 sc = scale[lev[cc]];
+        dx = (R)(ca.x - c2.x);
+        dy = (R)(ca.y - c2.y);
+        sx = (R)sc.x;
+        sy = (R)sc.y;
+        qc = mQ[cc];
+      }
+      Cx<R> cur0 = {(R)0, (R)0}, cur1 = {(R)0, (R)0};
+      {
+        const int c = __shfl_sync(FULL, cc, 0);
+        if (lane < p) cur0 = ma[(int64_t)c * P + lane];
+        if (lane + 32 < p) cur1 = ma[(int64_t)c * P + lane + 32];
+      }
+      for (int m = 0; m < nb; ++m) {
+        Cx<R> nxt0 = {(R)0, (R)0}, nxt1 = {(R)0, (R)0};
+        if (m + 1 < nb) {
+          const int c = __shfl_sync(FULL, cc, m + 1);
+          if (lane < p) nxt0 = ma[(int64_t)c * P + lane];
+          if (lane + 32 < p) nxt1 = ma[(int64_t)c * P + lane + 32];
+        }
+        const Cx<R> d = {__shfl_sync(FULL, dx, m) + tx, __shfl_sync(FULL, dy, m) + ty};
+        const Cx<R> sm = {__shfl_sync(FULL, sx, m), __shfl_sync(FULL, sy, m)};
+        const double qm = __shfl_sync(FULL, qc, m);
+        const R den = d.x * d.x + d.y * d.y;
+        const Cx<R> id = {d.x / den, -d.y / den};
+        const Cx<R> z = sm * id;                      // s_c / (y - c)
+        Cx<R> h = coef(cur0, cur1, p - 1);            // a^_p
+        for (int k = p - 2; k >= 0; --k) h = h * z + coef(cur0, cur1, k);
+        h = h * z;
+        acc += qm * log_abs(d) + (double)h.x;
+        cur0 = nxt0;
+        cur1 = nxt1;
+      }
     }
     if (act) phi[j] += acc;
   }
 }
 
 // One warp per target cell: adds the local expansion of the sources of its X
-// leaves (coefficients in chunks of KC, as the P2M kernel).
+// leaves.  The X leaves' ranges and centre offsets are fetched one per lane,
+// 32 at a time, and the lanes take the points of those leaves one each, in
+// order over the concatenated ranges (a lane finds its leaf by binary search
+// over the lanes' range starts), so every lane is busy whatever the leaf
+// sizes.  Coefficients come in chunks of KC (one chunk for p <= KC),
+// reduced over the warp by reduce-scatter; L_0 is formed in the first chunk.
 template <typename R, int KC>
 __global__ void __launch_bounds__(32 * AWPB)
 k_ad_p2l(int64_t n_cells, const int *__restrict__ x_off, const int *__restrict__ x_src,
@@ -739,6 +794,8 @@ k_ad_p2l(int64_t n_cells, const int *__restrict__ x_off, const int *__restrict__
          const double2 *__restrict__ ctr, const uint8_t *__restrict__ lev,
          const double2 *__restrict__ inv_scale, int p, int P, double *__restrict__ lL0,
          Cx<R> *__restrict__ lb) {
+  static_assert(2 * KC == 32, "one reduce-scatter value per lane");
+  constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t a = blockIdx.x * (int64_t)AWPB + w;
   if (a >= n_cells) return;
@@ -747,53 +804,76 @@ k_ad_p2l(int64_t n_cells, const int *__restrict__ x_off, const int *__restrict__
   const double2 ca = ctr[a];
   const double2 is2 = inv_scale[lev[a]];
   const Cx<R> is = {(R)is2.x, (R)is2.y};
-  // L_0: sum u log|x - c_a|
-  double q = 0.0;
-  for (int e = e0; e < e1; ++e) {
-    const int cc = x_src[e];
-    const double2 c2 = ctr[cc];
-    const R dcx = (R)(c2.x - ca.x), dcy = (R)(c2.y - ca.y);
-    for (int i = ss_[cc] + lane; i < se_[cc]; i += 32) {
-      const R *pt = src4 + 4 * (int64_t)i;
-      const Cx<R> d = {pt[0] + dcx, pt[1] + dcy};
-      q += (double)pt[2] * log_abs(d);
-    }
-  }
-  q = warp_sum_ad(q);
-  if (lane == 0) lL0[a] += q;
+  double q = 0.0;   // L_0: sum u log|x - c_a|
   for (int k0 = 1; k0 <= p; k0 += KC) {
     Cx<R> acc[KC];
 #pragma unroll
     for (int kk = 0; kk < KC; ++kk) acc[kk] = {(R)0, (R)0};
-    for (int e = e0; e < e1; ++e) {
-      const int cc = x_src[e];
-      const double2 c2 = ctr[cc];
-      const R dcx = (R)(c2.x - ca.x), dcy = (R)(c2.y - ca.y);
-      for (int i = ss_[cc] + lane; i < se_[cc]; i += 32) {
-        const R *pt = src4 + 4 * (int64_t)i;
-        const Cx<R> zeta = Cx<R>{pt[0] + dcx, pt[1] + dcy} * is;   // (x - c_a) / s_a
-        const R den = zeta.x * zeta.x + zeta.y * zeta.y;
-        const Cx<R> z = {zeta.x / den, -zeta.y / den};              // s_a / (x - c_a)
-        Cx<R> v = {pt[2], (R)0};
-        for (int t = 0; t < k0; ++t) v = v * z;
+    for (int eb = e0; eb < e1; eb += 32) {
+      const int nb = min(32, e1 - eb);
+      int st = 0, n = 0;
+      R dcx = (R)0, dcy = (R)0;
+      if (lane < nb) {
+        const int cc = x_src[eb + lane];
+        const double2 c2 = ctr[cc];
+        dcx = (R)(c2.x - ca.x);
+        dcy = (R)(c2.y - ca.y);
+        st = ss_[cc];
+        n = se_[cc] - st;
+      }
+      int incl = n;
 #pragma unroll
-        for (int kk = 0; kk < KC; ++kk) {
-          acc[kk] = acc[kk] + v;
-          v = v * z;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const int total = __shfl_sync(FULL, incl, 31);
+      const int excl = incl - n;
+      for (int i0 = 0; i0 < total; i0 += 32) {
+        const int idx = i0 + lane;
+        int m = 0;   // the last leaf m < nb whose range starts at or before idx
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+          const int cand = m + step;
+          const int ex = __shfl_sync(FULL, excl, cand & 31);
+          if (cand < nb && ex <= idx) m = cand;
+        }
+        const int sm = __shfl_sync(FULL, st, m), xm = __shfl_sync(FULL, excl, m);
+        const R ox = __shfl_sync(FULL, dcx, m), oy = __shfl_sync(FULL, dcy, m);
+        if (idx < total) {
+          const R *pt = src4 + 4 * (int64_t)(sm + idx - xm);
+          const Cx<R> d = {pt[0] + ox, pt[1] + oy};
+          if (k0 == 1) q += (double)pt[2] * log_abs(d);
+          const Cx<R> zeta = d * is;                                  // (x - c_a) / s_a
+          const R den = zeta.x * zeta.x + zeta.y * zeta.y;
+          const Cx<R> z = {zeta.x / den, -zeta.y / den};              // s_a / (x - c_a)
+          Cx<R> v = {pt[2], (R)0};
+          for (int t = 0; t < k0; ++t) v = v * z;
+#pragma unroll
+          for (int kk = 0; kk < KC; ++kk) {
+            acc[kk] = acc[kk] + v;
+            v = v * z;
+          }
         }
       }
     }
+    R vals[32];
 #pragma unroll
     for (int kk = 0; kk < KC; ++kk) {
-      const R re = warp_sum_ad(acc[kk].x), im = warp_sum_ad(acc[kk].y);
-      const int k = k0 + kk;
-      if (lane == 0 && k <= p) {
-        const R inv = (R)(-1.0) / (R)k;
-        Cx<R> cur = lb[a * P + k - 1];
-        lb[a * P + k - 1] = {cur.x + re * inv, cur.y + im * inv};
-      }
+      vals[2 * kk] = acc[kk].x;
+      vals[2 * kk + 1] = acc[kk].y;
+    }
+    const R re = warp_reduce_scatter32(vals);     // lane 2kk: Re, lane 2kk+1: Im of chunk entry kk
+    const R im = __shfl_down_sync(FULL, re, 1);
+    const int k = k0 + (lane >> 1);
+    if (!(lane & 1) && k <= p) {
+      const R inv = (R)(-1.0) / (R)k;
+      const Cx<R> cur = lb[a * P + k - 1];
+      lb[a * P + k - 1] = {cur.x + re * inv, cur.y + im * inv};
     }
   }
+  q = warp_sum_ad(q);
+  if (lane == 0) lL0[a] += q;
 }
 
 }  // namespace
@@ -869,10 +949,10 @@ constexpr int64_t COOP_MAX_CELLS = (int64_t)1 << 18;
 constexpr int64_t COOP_MAX_TESTS = (int64_t)1 << 19;
 
 namespace {
-__global__ void k_ad_hash(Geo g, int64_t n, AdCells c, unsigned long long *__restrict__ hkey,
-                          int *__restrict__ hval, uint32_t hmask) {
+__global__ void k_ad_hash(Geo g, int64_t n, AdCells c, unsigned long long *__restrict__ slots,
+                          uint32_t hmask) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || !c.hsrc[i]) return;
   const int l = c.lev[i];
   uint32_t inst;
   local_key(g.b, l, c.key[i], &inst);
@@ -880,9 +960,9 @@ __global__ void k_ad_hash(Geo g, int64_t n, AdCells c, unsigned long long *__res
   if (!crd_key(g.tiling, l, inst, c.crd[i], &k)) return;   // never for a cell of the tree
   uint32_t h = (uint32_t)ad_hash(k) & hmask;
   for (uint32_t probe = 0; probe <= hmask; ++probe) {
-    const unsigned long long prev = atomicCAS(&hkey[h], 0ull, (unsigned long long)k);
+    const unsigned long long prev = atomicCAS(&slots[2 * (size_t)h], 0ull, (unsigned long long)k);
     if (prev == 0ull || prev == k) {
-      hval[h] = (int)i;
+      slots[2 * (size_t)h + 1] = (unsigned long long)i;
       return;
     }
     h = (h + 1) & hmask;
@@ -890,12 +970,12 @@ __global__ void k_ad_hash(Geo g, int64_t n, AdCells c, unsigned long long *__res
 }
 }  // namespace
 
-cudaError_t ad_launch_hash(const Geo &g, int64_t n_cells, const AdCells &c, uint64_t *hkey, int *hval,
+cudaError_t ad_launch_hash(const Geo &g, int64_t n_cells, const AdCells &c, ulonglong2 *slots,
                            uint32_t hmask, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(hkey, 0, ((size_t)hmask + 1) * sizeof(uint64_t), s);
+  cudaError_t e = cudaMemsetAsync(slots, 0, ((size_t)hmask + 1) * sizeof(ulonglong2), s);
   if (e != cudaSuccess || n_cells <= 0) return e;
-  k_ad_hash<<<nblk(n_cells, 256), 256, 0, s>>>(g, n_cells, c, reinterpret_cast<unsigned long long *>(hkey),
-                                               hval, hmask);
+  k_ad_hash<<<nblk(n_cells, 256), 256, 0, s>>>(g, n_cells, c, reinterpret_cast<unsigned long long *>(slots),
+                                               hmask);
   return cudaGetLastError();
 }
 
@@ -1001,7 +1081,7 @@ cudaError_t ad_launch_p2l(int64_t n_cells, const int *x_off, const int *x_src, c
                           const double2 *inv_scale, int p, int P, double *lL0, Cx<R> *lb,
                           cudaStream_t s) {
   if (n_cells <= 0) return cudaSuccess;
-  k_ad_p2l<R, 8><<<nblk(n_cells, AWPB), 32 * AWPB, 0, s>>>(n_cells, x_off, x_src, src4, ss, se, ctr,
+  k_ad_p2l<R, 16><<<nblk(n_cells, AWPB), 32 * AWPB, 0, s>>>(n_cells, x_off, x_src, src4, ss, se, ctr,
                                                             lev, inv_scale, p, P, lL0, lb);
   return cudaGetLastError();
 }

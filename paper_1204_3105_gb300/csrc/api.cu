@@ -1064,16 +1064,14 @@ static fmm2d_status build_adaptive(fmm2d_plan *pl, const void *src, int64_t n_sr
   {
     StageScope sc(pl, ST_LISTS, s, 4 * (depth + 1) + 1);
     // the stencil lookups of the list kernels go through a (level, instance,
-    // lattice position) -> cell table, at most half full
+    // lattice position) -> cell table of the cells with sources, at most
+    // half full
     uint64_t hcap = 1024;
     while (hcap < 2 * (uint64_t)n_cells) hcap <<= 1;
-    CK(dbuf_reserve(pl->d_ad_hkey, hcap * 8), "alloc");
-    CK(dbuf_reserve(pl->d_ad_hval, hcap * 4), "alloc");
-    c.hkey = (const uint64_t *)pl->d_ad_hkey.p;
-    c.hval = (const int *)pl->d_ad_hval.p;
+    CK(dbuf_reserve(pl->d_ad_hash, hcap * sizeof(ulonglong2)), "alloc");
+    c.hslot = (const ulonglong2 *)pl->d_ad_hash.p;
     c.hmask = (uint32_t)(hcap - 1);
-    CK(ad_launch_hash(g, n_cells, c, (uint64_t *)pl->d_ad_hkey.p, (int *)pl->d_ad_hval.p, c.hmask, s),
-       "cell table");
+    CK(ad_launch_hash(g, n_cells, c, (ulonglong2 *)pl->d_ad_hash.p, c.hmask, s), "cell table");
     for (int l = 0; l <= depth; ++l) {
       const int64_t count = lf[l + 1] - lf[l];
       const int64_t items = count + n_t + n_s;
@@ -1238,7 +1236,7 @@ fmm2d_status evaluate_adaptive_t(fmm2d_plan *pl, const void *u, double *out, cud
     StageScope sc(pl, ST_M2M, f, std::max(0, depth - 1));
     for (int l = depth - 1; l >= 1; --l)
       CK(launch_m2m<R>(a, pl->geo, l, pl->lev_first[l], pl->lev_count[l], nullptr, c.key, c.cls,
-                       c.hsrc, (const Cx<R> *)pl->d_m2m_ops.p, mQ, ma, f), "m2m");
+                       c.hsrc, (const Cx<R> *)pl->d_m2m_ops.p, mQ, ma, pl->n_sms, f), "m2m");
   }
   {
     // cells above the first M2L level get no M2L write: their locals (read by
@@ -1314,7 +1312,7 @@ fmm2d_status evaluate_adaptive_t(fmm2d_plan *pl, const void *u, double *out, cud
     StageScope sc(pl, ST_L2L, f, std::max(0, depth - pl->l_min));
     for (int l = pl->l_min + 1; l <= depth; ++l)
       CK(launch_l2l<R>(a, pl->geo, l, pl->lev_first[l], pl->lev_count[l], nullptr, c.key, c.cls,
-                       (const Cx<R> *)pl->d_l2l_ops.p, lL0, lb, f), "l2l");
+                       (const Cx<R> *)pl->d_l2l_ops.p, lL0, lb, pl->n_sms, f), "l2l");
   }
   {
     StageScope sc(pl, ST_P2P, s, 1);
@@ -1433,7 +1431,7 @@ static void for_each_dbuf(fmm2d_plan *pl, F f) {
                   &pl->d_far_src, &pl->d_far_op, &pl->d_near_cnt, &pl->d_near_src, &pl->d_src4,
                   &pl->d_tgt2, &pl->d_mQ, &pl->d_ma, &pl->d_ma_ff, &pl->d_lL0, &pl->d_lb, &pl->d_phi_near,
                   &pl->d_fnear, &pl->d_tc_part_lb, &pl->d_tc_part_L0, &pl->d_m2m_arrive, &pl->d_l2l_ready,
-                  &pl->d_ad_hkey, &pl->d_ad_hval,
+                  &pl->d_ad_hash,
                   &pl->d_phi_far, &pl->d_sten, &pl->d_geo_scale, &pl->d_m2l_ops, &pl->d_m2l_logz,
                   &pl->d_m2m_ops, &pl->d_l2l_ops, &pl->d_counts, &pl->d_far_full,
                   &pl->d_cls_cnt, &pl->d_cls_cells, &pl->d_tc_ops, &pl->d_ff_ops, &pl->d_ff_ph, &pl->d_dev_err,

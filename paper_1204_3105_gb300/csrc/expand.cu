@@ -222,11 +222,12 @@ k_p2m_t(ExpandArgs a, const R *__restrict__ src4, const int *__restrict__ start,
   }
 }
 
-// One warp per parent cell; lane i owns output coefficients i+1 and i+33.
-// Every child's slot, charge, class and multipole is fetched before any
-// arithmetic, so a level costs about three dependent loads (the parent's key,
-// the child slots, the child data) rather than three per child; the children
-// are then applied in child order.
+// A warp per parent cell, the warps of the grid striding over the level
+// (the block stages the operator table once for all its cells); lane i owns
+// output coefficients i+1 and i+33.  Every child's slot, charge, class and
+// multipole is fetched before any arithmetic, so a cell costs about three
+// dependent loads (the parent's fields, the child slots, the child data)
+// rather than three per child; the children are then applied in child order.
 template <typename R>
 __global__ void __launch_bounds__(32 * WPB)
 k_m2m(ExpandArgs a, Geo g, int level, int64_t first, int64_t count, const int *__restrict__ map,
@@ -239,21 +240,7 @@ k_m2m(ExpandArgs a, Geo g, int level, int64_t first, int64_t count, const int *_
   __shared__ Cx<R> sh[WPB][NB][MAXP + 1];
   extern __shared__ __align__(16) unsigned char dyn_ops[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t ci = blockIdx.x * (int64_t)WPB + w;
-  const bool valid = ci < count;
-  const int64_t gp = first + (valid ? ci : 0);
   const int p = a.p, P1 = p + 1;
-  // the parent's own fields, fetched together (and with the operator table)
-  const bool hs = valid && cell_hsrc[gp];
-  int nch = 0, cs = -1, cf = 0;
-  if (a.child_first) {
-    cf = a.child_first[gp];
-    nch = a.child_cnt[gp];
-  } else {
-    const uint32_t key = cell_key[gp];
-    nch = g.b;
-    if (valid && lane < nch) cs = map[g.map_off[level + 1] + (int64_t)key * g.b + lane];
-  }
   const Cx<R> *op_tab = ops;
   if (n_staged > 0) {   // the operators in shared memory: every child reads them
     Cx<R> *so = reinterpret_cast<Cx<R> *>(dyn_ops);
@@ -261,66 +248,78 @@ k_m2m(ExpandArgs a, Geo g, int level, int64_t first, int64_t count, const int *_
     __syncthreads();
     op_tab = so;
   }
-  if (!valid) return;
-  if (a.child_first) {
-    if (nch == 0) return;                      // adaptive leaf: keeps its P2M
-    if (!hs) nch = 0;
-    if (lane < nch) cs = cf + lane;
-  } else if (!hs) {
-    nch = 0;
-    cs = -1;
-  }
-  // lane d < nch: child d's flag, charge and class
-  int use = 0, cls = 0;
-  double Qc = 0.0;
-  if (cs >= 0) {
-    use = cell_hsrc[cs];
-    Qc = mQ[cs];
-    cls = cell_cls[cs];
-  }
-  // all lanes: the children's multipoles, entry idx = d p + k
-  Cx<R> v[NLD];
-  const int nv = nch * p;
-#pragma unroll
-  for (int r = 0; r < NLD; ++r) {
-    const int idx = lane + 32 * r;
-    const int d = min(idx / max(p, 1), 31);
-    const int cd = __shfl_sync(FULL, cs, d);
-    v[r] = Cx<R>{(R)0, (R)0};
-    if (idx < nv && cd >= 0) v[r] = ma[(int64_t)cd * a.P + (idx - d * p)];
-  }
-#pragma unroll
-  for (int r = 0; r < NLD; ++r) {
-    const int idx = lane + 32 * r;
-    if (idx < nv) {
-      const int d = idx / p;
-      sh[w][d][idx - d * p + 1] = v[r];
+  const int64_t stride = (int64_t)gridDim.x * WPB;
+  for (int64_t ci = blockIdx.x * (int64_t)WPB + w; ci < count; ci += stride) {
+    const int64_t gp = first + ci;
+    const bool hs = cell_hsrc[gp];
+    int nch = 0, cs = -1;
+    if (a.child_first) {
+      nch = a.child_cnt[gp];
+      if (nch == 0) continue;                  // adaptive leaf: keeps its P2M (warp-uniform)
+      if (!hs) nch = 0;
+      if (lane < nch) cs = a.child_first[gp] + lane;
+    } else {
+      const uint32_t key = cell_key[gp];
+      nch = g.b;
+      if (lane < nch) cs = map[g.map_off[level + 1] + (int64_t)key * g.b + lane];
+      if (!hs) {
+        nch = 0;
+        cs = -1;
+      }
     }
-  }
-  __syncwarp();
-  Cx<R> acc0 = {(R)0, (R)0}, acc1 = {(R)0, (R)0};
-  double Q = 0.0;
-  for (int d = 0; d < nch; ++d) {
-    const int ud = __shfl_sync(FULL, use, d);
-    const double qd = __shfl_sync(FULL, Qc, d);
-    const int kd = __shfl_sync(FULL, cls, d);
-    if (!ud) continue;                         // warp-uniform
-    const Cx<R> *op = op_tab + (int64_t)kd * P1 * P1;
-    const R q = (R)qd;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int l = lane + 1 + 32 * h;
-      if (l > p) break;
-      const Cx<R> *row = op + (int64_t)l * P1;
-      Cx<R> s = q * row[0];
-      for (int k = 1; k <= l; ++k) cfma(s, row[k], sh[w][d][k]);
-      if (h == 0) acc0 = acc0 + s; else acc1 = acc1 + s;
+    // lane d < nch: child d's flag, charge and class
+    int use = 0, cls = 0;
+    double Qc = 0.0;
+    if (cs >= 0) {
+      use = cell_hsrc[cs];
+      Qc = mQ[cs];
+      cls = cell_cls[cs];
     }
-    Q += qd;
+    // all lanes: the children's multipoles, entry idx = d p + k
+    Cx<R> v[NLD];
+    const int nv = nch * p;
+#pragma unroll
+    for (int r = 0; r < NLD; ++r) {
+      const int idx = lane + 32 * r;
+      const int d = min(idx / max(p, 1), 31);
+      const int cd = __shfl_sync(FULL, cs, d);
+      v[r] = Cx<R>{(R)0, (R)0};
+      if (idx < nv && cd >= 0) v[r] = ma[(int64_t)cd * a.P + (idx - d * p)];
+    }
+#pragma unroll
+    for (int r = 0; r < NLD; ++r) {
+      const int idx = lane + 32 * r;
+      if (idx < nv) {
+        const int d = idx / p;
+        sh[w][d][idx - d * p + 1] = v[r];
+      }
+    }
+    __syncwarp();
+    Cx<R> acc0 = {(R)0, (R)0}, acc1 = {(R)0, (R)0};
+    double Q = 0.0;
+    for (int d = 0; d < nch; ++d) {
+      const int ud = __shfl_sync(FULL, use, d);
+      const double qd = __shfl_sync(FULL, Qc, d);
+      const int kd = __shfl_sync(FULL, cls, d);
+      if (!ud) continue;                       // warp-uniform
+      const Cx<R> *op = op_tab + (int64_t)kd * P1 * P1;
+      const R q = (R)qd;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int l = lane + 1 + 32 * h;
+        if (l > p) break;
+        const Cx<R> *row = op + (int64_t)l * P1;
+        Cx<R> s = q * row[0];
+        for (int k = 1; k <= l; ++k) cfma(s, row[k], sh[w][d][k]);
+        if (h == 0) acc0 = acc0 + s; else acc1 = acc1 + s;
+      }
+      Q += qd;
+    }
+    if (lane == 0) mQ[gp] = Q;
+    if (lane + 1 <= p) ma[gp * a.P + lane] = acc0;
+    if (lane + 33 <= p) ma[gp * a.P + lane + 32] = acc1;
+    __syncwarp();   // sh[w] is rewritten by the next cell
   }
-  if (lane == 0) mQ[gp] = Q;
-  if (lane + 1 <= p) ma[gp * a.P + lane] = acc0;
-  if (lane + 33 <= p) ma[gp * a.P + lane + 32] = acc1;
 }
 
 // Uniform tree, the whole upward pass in one launch.  A warp takes a cell of
@@ -572,9 +571,11 @@ k_m2l(ExpandArgs a, int64_t first, int64_t count, const int64_t *__restrict__ le
   if (li + H <= p) lb[gt * a.P + li + H - 1] = acc1;
 }
 
-// One warp per child cell; adds the shifted parent local in place; lane i
-// owns coefficients i and i+32.  The cell's own local, its class and its
-// parent slot are fetched together, then the parent's local.
+// A warp per child cell, the warps of the grid striding over the level (the
+// block stages the operator table once for all its cells); adds the shifted
+// parent local in place; lane i owns coefficients i and i+32.  The cell's
+// own local, its class and its parent slot are fetched together, then the
+// parent's local.
 template <typename R>
 __global__ void __launch_bounds__(32 * WPB)
 k_l2l(ExpandArgs a, Geo g, int level, int64_t first, int64_t count, const int *__restrict__ map,
@@ -584,28 +585,8 @@ k_l2l(ExpandArgs a, Geo g, int level, int64_t first, int64_t count, const int *_
   __shared__ Cx<R> sh[WPB][MAXP + 1];
   extern __shared__ __align__(16) unsigned char dyn_ops[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t ci = blockIdx.x * (int64_t)WPB + w;
-  const bool valid = ci < count;
-  const int64_t gc = first + (valid ? ci : 0);
   const int p = a.p, P1 = p + 1;
   const int k0 = lane, k1 = lane + 32;
-  // the cell's own fields (fetched together with the operator table)
-  const int cls = cell_cls[gc];
-  Cx<R> own0 = {(R)0, (R)0}, own1 = {(R)0, (R)0};
-  double L0 = 0.0;
-  if (valid) {
-    if (k0 == 0) L0 = lL0[gc];
-    else if (k0 <= p) own0 = lb[gc * a.P + k0 - 1];
-    if (k1 <= p) own1 = lb[gc * a.P + k1 - 1];
-  }
-  int ps;
-  if (a.parent) {
-    ps = a.parent[gc];
-  } else {
-    const uint32_t key = cell_key[gc];
-    const uint32_t pkey = (g.tiling == FMM2D_SEPT) ? key / 7u : key >> 2;
-    ps = map[g.map_off[level - 1] + pkey];
-  }
   const Cx<R> *op_tab = ops;
   if (n_staged > 0) {   // the operators in shared memory: every cell reads them
     Cx<R> *so = reinterpret_cast<Cx<R> *>(dyn_ops);
@@ -613,22 +594,41 @@ k_l2l(ExpandArgs a, Geo g, int level, int64_t first, int64_t count, const int *_
     __syncthreads();
     op_tab = so;
   }
-  if (!valid) return;
-  // the parent's local
-  double Lp = 0.0;
-  if (k0 == 0) Lp = lL0[ps];
-  for (int k = lane; k < p; k += 32) sh[w][k + 1] = lb[(int64_t)ps * a.P + k];
-  __syncwarp();
-  const Cx<R> *U = op_tab + (int64_t)cls * P1 * P1;
+  const int64_t stride = (int64_t)gridDim.x * WPB;
+  for (int64_t ci = blockIdx.x * (int64_t)WPB + w; ci < count; ci += stride) {
+    const int64_t gc = first + ci;
+    // the cell's own fields
+    const int cls = cell_cls[gc];
+    Cx<R> own0 = {(R)0, (R)0}, own1 = {(R)0, (R)0};
+    double L0 = 0.0;
+    if (k0 == 0) L0 = lL0[gc];
+    else if (k0 <= p) own0 = lb[gc * a.P + k0 - 1];
+    if (k1 <= p) own1 = lb[gc * a.P + k1 - 1];
+    int ps;
+    if (a.parent) {
+      ps = a.parent[gc];
+    } else {
+      const uint32_t key = cell_key[gc];
+      const uint32_t pkey = (g.tiling == FMM2D_SEPT) ? key / 7u : key >> 2;
+      ps = map[g.map_off[level - 1] + pkey];
+    }
+    // the parent's local
+    double Lp = 0.0;
+    if (k0 == 0) Lp = lL0[ps];
+    for (int k = lane; k < p; k += 32) sh[w][k + 1] = lb[(int64_t)ps * a.P + k];
+    __syncwarp();
+    const Cx<R> *U = op_tab + (int64_t)cls * P1 * P1;
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int k = h == 0 ? k0 : k1;
-    if (k > p) break;
-    const Cx<R> *row = U + (int64_t)k * P1;
-    Cx<R> s = {(R)0, (R)0};
-    for (int l = (k > 1 ? k : 1); l <= p; ++l) cfma(s, row[l], sh[w][l]);
-    if (k == 0) lL0[gc] = L0 + (Lp + (double)s.x);
-    else lb[gc * a.P + k - 1] = (h == 0 ? own0 : own1) + s;
+    for (int h = 0; h < 2; ++h) {
+      const int k = h == 0 ? k0 : k1;
+      if (k > p) break;
+      const Cx<R> *row = U + (int64_t)k * P1;
+      Cx<R> s = {(R)0, (R)0};
+      for (int l = (k > 1 ? k : 1); l <= p; ++l) cfma(s, row[l], sh[w][l]);
+      if (k == 0) lL0[gc] = L0 + (Lp + (double)s.x);
+      else lb[gc * a.P + k - 1] = (h == 0 ? own0 : own1) + s;
+    }
+    __syncwarp();   // sh[w] is rewritten by the next cell
   }
 }
 
@@ -770,11 +770,12 @@ cudaError_t launch_p2m(const ExpandArgs &a, const R *src4, const int *start, con
 template <typename R>
 cudaError_t launch_m2m(const ExpandArgs &a, const Geo &g, int level, int64_t first, int64_t count,
                        const int *map, const uint32_t *cell_key, const uint8_t *cell_cls,
-                       const uint8_t *cell_hsrc, const Cx<R> *ops, double *mQ, Cx<R> *ma,
+                       const uint8_t *cell_hsrc, const Cx<R> *ops, double *mQ, Cx<R> *ma, int sms,
                        cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   const int n_st = staged_ops<R>(a, sizeof(Cx<R>) * WPB * 7 * (MAXP + 1));
-  k_m2m<R><<<wblocks(count), 32 * WPB, n_st * sizeof(Cx<R>), s>>>(
+  const unsigned blocks = (unsigned)std::min<int64_t>(wblocks(count), (int64_t)std::max(sms, 1) * 8);
+  k_m2m<R><<<blocks, 32 * WPB, n_st * sizeof(Cx<R>), s>>>(
       a, g, level, first, count, map, cell_key, cell_cls, cell_hsrc, ops, n_st, mQ, ma);
   return cudaGetLastError();
 }
@@ -812,10 +813,11 @@ cudaError_t launch_m2l(const ExpandArgs &a, int64_t first, int64_t count, const 
 template <typename R>
 cudaError_t launch_l2l(const ExpandArgs &a, const Geo &g, int level, int64_t first, int64_t count,
                        const int *map, const uint32_t *cell_key, const uint8_t *cell_cls,
-                       const Cx<R> *ops, double *lL0, Cx<R> *lb, cudaStream_t s) {
+                       const Cx<R> *ops, double *lL0, Cx<R> *lb, int sms, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   const int n_st = staged_ops<R>(a, sizeof(Cx<R>) * WPB * (MAXP + 1));
-  k_l2l<R><<<wblocks(count), 32 * WPB, n_st * sizeof(Cx<R>), s>>>(
+  const unsigned blocks = (unsigned)std::min<int64_t>(wblocks(count), (int64_t)std::max(sms, 1) * 8);
+  k_l2l<R><<<blocks, 32 * WPB, n_st * sizeof(Cx<R>), s>>>(
       a, g, level, first, count, map, cell_key, cell_cls, ops, n_st, lL0, lb);
   return cudaGetLastError();
 }
@@ -837,7 +839,7 @@ cudaError_t launch_l2p(const ExpandArgs &a, const R *tgt, int tstride, const int
                                      double *, Cx<R> *, cudaStream_t);                            \
   template cudaError_t launch_m2m<R>(const ExpandArgs &, const Geo &, int, int64_t, int64_t,       \
                                      const int *, const uint32_t *, const uint8_t *,              \
-                                     const uint8_t *, const Cx<R> *, double *, Cx<R> *,           \
+                                     const uint8_t *, const Cx<R> *, double *, Cx<R> *, int,      \
                                      cudaStream_t);                                               \
   template cudaError_t launch_l2l_down<R>(const ExpandArgs &, const Geo &, int64_t, int64_t,       \
                                           const int64_t *, const int *, const uint32_t *,         \
@@ -854,7 +856,7 @@ cudaError_t launch_l2p(const ExpandArgs &a, const R *tgt, int tstride, const int
                                      cudaStream_t);                                               \
   template cudaError_t launch_l2l<R>(const ExpandArgs &, const Geo &, int, int64_t, int64_t,       \
                                      const int *, const uint32_t *, const uint8_t *,              \
-                                     const Cx<R> *, double *, Cx<R> *, cudaStream_t);             \
+                                     const Cx<R> *, double *, Cx<R> *, int, cudaStream_t);        \
   template cudaError_t launch_l2p<R>(const ExpandArgs &, const R *, int, const int *, const int *, \
                                      const uint32_t *, double *, Cx<R> *,                         \
                                      const double *, double *, double *, cudaStream_t);

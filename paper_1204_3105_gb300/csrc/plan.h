@@ -91,7 +91,7 @@ struct Plan {
   DBuf d_mQ, d_ma, d_lL0, d_lb;
   DBuf d_phi_near, d_phi_far;
   DBuf d_m2m_arrive;                // uniform upward pass: arrivals per cell
-  DBuf d_ad_hkey, d_ad_hval;        // adaptive tree: (level, key) -> cell table
+  DBuf d_ad_hash;                   // adaptive tree: (level, instance, position) -> cell table
   DBuf d_l2l_ready;                 // uniform downward pass: counter + ready word per cell
   DBuf d_fnear;                        // near part of the field (fmm2d_evaluate_field)
   DBuf d_sten, d_geo_scale;
@@ -212,15 +212,17 @@ struct AdCells {
   int4 *crd;
   double2 *ctr;
   uint8_t *cls, *hsrc;
-  // (level, instance, lattice position) -> cell: open addressing with
-  // linear probing, built once the cells exist (for the list traversal)
-  const uint64_t *hkey = nullptr;      // packed position, 0 = empty
-  const int *hval = nullptr;
+  // (level, instance, lattice position) -> cell, for the cells with
+  // sources: open addressing with linear probing, built once the cells
+  // exist (for the list traversal); slot = {packed position (0 = empty),
+  // cell}, one 16-byte read per probe
+  const ulonglong2 *hslot = nullptr;
   uint32_t hmask = 0;                  // capacity - 1 (a power of two)
 };
-// Fill the (level, instance, lattice position) -> cell table of the n_cells
-// cells (hkey zeroed here; capacity hmask + 1, at least twice n_cells).
-cudaError_t ad_launch_hash(const Geo &g, int64_t n_cells, const AdCells &c, uint64_t *hkey, int *hval,
+// Fill the (level, instance, lattice position) -> cell table with the
+// cells that hold sources, of the n_cells cells (slots zeroed here;
+// capacity hmask + 1, at least twice n_cells).
+cudaError_t ad_launch_hash(const Geo &g, int64_t n_cells, const AdCells &c, ulonglong2 *slots,
                            uint32_t hmask, cudaStream_t s);
 // level-0 cells: one per instance (soff / toff: n_inst + 1 device offsets),
 // or one cell holding everything (null offsets, n_inst = 1)
@@ -322,7 +324,7 @@ cudaError_t launch_m2m_up(const ExpandArgs &a, const Geo &g, int l_min, int64_t 
 template <typename R>
 cudaError_t launch_m2m(const ExpandArgs &a, const Geo &g, int level, int64_t first, int64_t count,
                        const int *map, const uint32_t *cell_key, const uint8_t *cell_cls,
-                       const uint8_t *cell_hsrc, const Cx<R> *ops, double *mQ, Cx<R> *ma,
+                       const uint8_t *cell_hsrc, const Cx<R> *ops, double *mQ, Cx<R> *ma, int sms,
                        cudaStream_t s);
 template <typename R>
 cudaError_t launch_m2l(const ExpandArgs &a, int64_t first, int64_t count, const int64_t *lev_of_cell_first,
@@ -333,7 +335,7 @@ cudaError_t launch_m2l(const ExpandArgs &a, int64_t first, int64_t count, const 
 template <typename R>
 cudaError_t launch_l2l(const ExpandArgs &a, const Geo &g, int level, int64_t first, int64_t count,
                        const int *map, const uint32_t *cell_key, const uint8_t *cell_cls,
-                       const Cx<R> *ops, double *lL0, Cx<R> *lb, cudaStream_t s);
+                       const Cx<R> *ops, double *lL0, Cx<R> *lb, int sms, cudaStream_t s);
 template <typename R>
 cudaError_t launch_l2p(const ExpandArgs &a, const R *tgt, int tstride, const int *start,
                        const int *end, const uint32_t *perm, double *lL0, Cx<R> *lb,
