@@ -1431,7 +1431,7 @@ static void for_each_dbuf(fmm2d_plan *pl, F f) {
                   &pl->d_far_src, &pl->d_far_op, &pl->d_near_cnt, &pl->d_near_src, &pl->d_src4,
                   &pl->d_tgt2, &pl->d_mQ, &pl->d_ma, &pl->d_ma_ff, &pl->d_lL0, &pl->d_lb, &pl->d_phi_near,
                   &pl->d_fnear, &pl->d_tc_part_lb, &pl->d_tc_part_L0, &pl->d_m2m_arrive, &pl->d_l2l_ready,
-                  &pl->d_ad_hash,
+                  &pl->d_ad_hash, &pl->d_pmap,
                   &pl->d_phi_far, &pl->d_sten, &pl->d_geo_scale, &pl->d_m2l_ops, &pl->d_m2l_logz,
                   &pl->d_m2m_ops, &pl->d_l2l_ops, &pl->d_counts, &pl->d_far_full,
                   &pl->d_cls_cnt, &pl->d_cls_cells, &pl->d_tc_ops, &pl->d_ff_ops, &pl->d_ff_ph, &pl->d_dev_err,
@@ -1598,6 +1598,8 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
   CK(dbuf_reserve(pl->d_hsrc, ms * 4), "alloc");
   CK(dbuf_reserve(pl->d_scan, ms * 4), "alloc");
   CK(dbuf_reserve(pl->d_map, ms * 4), "alloc");
+  const bool use_pmap = g.tiling == FMM2D_TRI;
+  if (use_pmap) CK(dbuf_reserve(pl->d_pmap, 2 * (((int64_t)1 << (2 * (pl->L + 1))) - 1) / 3 * 4), "alloc");
   const int64_t cap = ms;   // upper bound on occupied cells
   CK(dbuf_reserve(pl->d_cell_key, cap * 4), "alloc");
   CK(dbuf_reserve(pl->d_cell_crd, cap * sizeof(int4)), "alloc");
@@ -1677,7 +1679,7 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
                       (uint8_t *)pl->d_cell_hsrc.p, (int *)pl->d_src_start.p, (int *)pl->d_src_end.p,
                       pl->same_sets ? nullptr : (int *)pl->d_tgt_start.p,
                       pl->same_sets ? nullptr : (int *)pl->d_tgt_end.p, (int64_t *)pl->d_lev_first.p,
-                      s), "compact");
+                      use_pmap ? (int *)pl->d_pmap.p : nullptr, s), "compact");
   }
   {
     StageScope sc(pl, ST_TREE, s, pl->same_sets ? 1 : 2);
@@ -1724,7 +1726,7 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
                     (int *)pl->d_near_cnt.p, (int *)pl->d_near_src.p,
                     (const int64_t *)pl->d_lev_first.p, tc ? (int *)pl->d_far_full.p : nullptr,
                     tc ? (int *)pl->d_cls_cnt.p : nullptr, tc ? (int *)pl->d_cls_cells.p : nullptr,
-                    cap_list, s), "lists");
+                    cap_list, use_pmap ? (const int *)pl->d_pmap.p : nullptr, s), "lists");
   }
   // ---- the one synchronisation: level counts for the evaluation and the
   // domain check

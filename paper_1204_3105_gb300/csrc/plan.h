@@ -91,6 +91,7 @@ struct Plan {
   DBuf d_mQ, d_ma, d_lL0, d_lb;
   DBuf d_phi_near, d_phi_far;
   DBuf d_m2m_arrive;                // uniform upward pass: arrivals per cell
+  DBuf d_pmap;                      // uniform triangle tree: position -> slot of the lists
   DBuf d_ad_hash;                   // adaptive tree: (level, instance, position) -> cell table
   DBuf d_l2l_ready;                 // uniform downward pass: counter + ready word per cell
   DBuf d_fnear;                        // near part of the field (fmm2d_evaluate_field)
@@ -179,12 +180,14 @@ cudaError_t exclusive_scan(const int *in, int *out, int64_t n, void *scratch, cu
 cudaError_t launch_mark(const Geo &g, const uint32_t *key_sorted, int64_t n, int *occ, int *hsrc,
                         cudaStream_t s);
 // Cells of every level from the occupancy scan; also the first slot of every
-// level and the total in lev_first[0 .. L+1].
+// level and the total in lev_first[0 .. L+1].  pmap (triangle tiling, else
+// null): the position map of the lists, 2 (4^(L+1) - 1) / 3 ints, every
+// entry written.
 cudaError_t launch_compact(const Geo &g, const int *occ, const int *scan, const int *hsrc,
                            int64_t map_size, int *map, uint32_t *cell_key, int4 *cell_crd,
                            double2 *cell_ctr, uint8_t *cell_cls, uint8_t *cell_hsrc,
                            int *src_start, int *src_end, int *tgt_start, int *tgt_end,
-                           int64_t *lev_first, cudaStream_t s);
+                           int64_t *lev_first, int *pmap, cudaStream_t s);
 // Sorted points relative to their leaf centre, and the leaves' point ranges.
 // lo (optional): the low parts (leaf-relative coordinate minus its FP32 value).
 cudaError_t launch_rel_coords(const Geo &g, bool f32_in, bool f32_out, const void *xy,
@@ -198,7 +201,7 @@ cudaError_t launch_lists(const Geo &g, const Stencils *d_sten, int lo_level, int
                          const uint8_t *cell_hsrc, int *far_cnt, int *far_src, uint16_t *far_op,
                          int *near_cnt, int *near_src, const int64_t *lev_first_dev,
                          int *far_full, int *cls_cnt, int *cls_cells, int64_t cls_cap,
-                         cudaStream_t s);
+                         const int *pmap, cudaStream_t s);
 
 // ---------------------------------------------------------------- adaptive.cu
 // Cell arrays of the adaptive tree (one array over all levels, ordered by

@@ -45,13 +45,31 @@ __device__ __forceinline__ int level_of_map(const Geo &g, int64_t m) {
   return l;
 }
 
+// The triangle tiling's position map: level l holds 2 x 4^l entries, index
+// (i 2^l + j) x 2 + up for the cell at lattice position (i, j, k) (k is then
+// 2^l - 1 - i - j for an up cell, 2^l - 2 - i - j for a down one, Sec. 6),
+// each the cell's slot when it holds sources, else -1.  Levels 0 .. l-1
+// take 2 (4^l - 1) / 3 entries.
+__device__ __forceinline__ int64_t tri_pmap_index(int l, int i, int j, int up) {
+  return 2 * ((((int64_t)1) << (2 * l)) - 1) / 3 + ((((int64_t)i << l) | j) << 1) + up;
+}
+
+// The slot of the triangle cell with sources at level-l position q, or -1.
+__device__ __forceinline__ int tri_pmap_lookup(const int *__restrict__ pmap, int l, int4 q) {
+  const int n = 1 << l, sum = q.x + q.y + q.z;
+  if (q.x < 0 || q.y < 0 || q.z < 0 || q.x >= n || q.y >= n || q.z >= n) return -1;
+  if (sum != n - 1 && sum != n - 2) return -1;
+  return pmap[tri_pmap_index(l, q.x, q.y, sum == n - 1 ? 1 : 0)];
+}
+
 __global__ void k_compact(Geo g, const int *__restrict__ occ, const int *__restrict__ scan,
                           const int *__restrict__ hsrc, int64_t map_size, int *__restrict__ map,
                           uint32_t *__restrict__ cell_key, int4 *__restrict__ cell_crd,
                           double2 *__restrict__ cell_ctr, uint8_t *__restrict__ cell_cls,
                           uint8_t *__restrict__ cell_hsrc, int *__restrict__ src_start,
                           int *__restrict__ src_end, int *__restrict__ tgt_start,
-                          int *__restrict__ tgt_end, int64_t *__restrict__ lev_first) {
+                          int *__restrict__ tgt_end, int64_t *__restrict__ lev_first,
+                          int *__restrict__ pmap) {
   int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (m >= map_size) return;
   const int l = level_of_map(g, m);
@@ -59,11 +77,16 @@ __global__ void k_compact(Geo g, const int *__restrict__ occ, const int *__restr
     if (m == g.map_off[l]) lev_first[l] = scan[m];
     if (m == map_size - 1) lev_first[g.L + 1] = (int64_t)scan[m] + occ[m];
   }
+  const uint32_t key = (uint32_t)(m - g.map_off[l]);
+  if (pmap) {   // triangle tiling: every key's position entry (keys and positions correspond one to one)
+    int i, j, k;
+    tri_key_to_coords(key, l, &i, &j, &k);
+    pmap[tri_pmap_index(l, i, j, tri_up(i, j, k, l) ? 1 : 0)] = (occ[m] && hsrc[m]) ? scan[m] : -1;
+  }
   if (!occ[m]) {
     map[m] = -1;
     return;
   }
-  const uint32_t key = (uint32_t)(m - g.map_off[l]);
   const int slot = scan[m];
   map[m] = slot;
   cell_key[slot] = key;
@@ -113,7 +136,7 @@ __global__ void k_lists(Geo g, const Stencils *__restrict__ st, int lo_level, in
                         uint16_t *__restrict__ far_op, int *__restrict__ near_cnt,
                         int *__restrict__ near_src, const int64_t *__restrict__ lev_first,
                         int *__restrict__ far_full, int *__restrict__ cls_cnt,
-                        int *__restrict__ cls_cells, int64_t cls_cap) {
+                        int *__restrict__ cls_cells, int64_t cls_cap, const int *__restrict__ pmap) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const int64_t first = lev_first[lo_level];
@@ -132,10 +155,14 @@ __global__ void k_lists(Geo g, const Stencils *__restrict__ st, int lo_level, in
     if (e < n_far) {
       const int4 q = make_int4(c.x + st->far_d[cls][e][0], c.y + st->far_d[cls][e][1],
                                c.z + st->far_d[cls][e][2], 0);
-      uint32_t k;
-      if (cell_at(g, l, q, &k)) {
-        s = map[g.map_off[l] + k];
-        if (s >= 0 && !cell_hsrc[s]) s = -1;
+      if (pmap) {
+        s = tri_pmap_lookup(pmap, l, q);
+      } else {
+        uint32_t k;
+        if (cell_at(g, l, q, &k)) {
+          s = map[g.map_off[l] + k];
+          if (s >= 0 && !cell_hsrc[s]) s = -1;
+        }
       }
       if (far_full) far_full[fi * FAR_MAX + e] = s;
     }
@@ -162,10 +189,14 @@ __global__ void k_lists(Geo g, const Stencils *__restrict__ st, int lo_level, in
     if (lane < st->near_len[o]) {
       const int4 q = make_int4(c.x + st->near_d[o][lane][0], c.y + st->near_d[o][lane][1],
                                c.z + st->near_d[o][lane][2], 0);
-      uint32_t k;
-      if (cell_at(g, l, q, &k)) {
-        s = map[g.map_off[l] + k];
-        if (s >= 0 && !cell_hsrc[s]) s = -1;
+      if (pmap) {
+        s = tri_pmap_lookup(pmap, l, q);
+      } else {
+        uint32_t k;
+        if (cell_at(g, l, q, &k)) {
+          s = map[g.map_off[l] + k];
+          if (s >= 0 && !cell_hsrc[s]) s = -1;
+        }
       }
     }
     const unsigned hit = __ballot_sync(0xffffffffu, s >= 0);
@@ -189,10 +220,10 @@ cudaError_t launch_compact(const Geo &g, const int *occ, const int *scan, const 
                            int64_t map_size, int *map, uint32_t *cell_key, int4 *cell_crd,
                            double2 *cell_ctr, uint8_t *cell_cls, uint8_t *cell_hsrc,
                            int *src_start, int *src_end, int *tgt_start, int *tgt_end,
-                           int64_t *lev_first, cudaStream_t s) {
+                           int64_t *lev_first, int *pmap, cudaStream_t s) {
   k_compact<<<nblk(map_size, 256), 256, 0, s>>>(g, occ, scan, hsrc, map_size, map, cell_key,
                                                  cell_crd, cell_ctr, cell_cls, cell_hsrc, src_start,
-                                                 src_end, tgt_start, tgt_end, lev_first);
+                                                 src_end, tgt_start, tgt_end, lev_first, pmap);
   return cudaGetLastError();
 }
 
@@ -218,11 +249,11 @@ cudaError_t launch_lists(const Geo &g, const Stencils *d_sten, int lo_level, int
                          const uint8_t *cell_hsrc, int *far_cnt, int *far_src, uint16_t *far_op,
                          int *near_cnt, int *near_src, const int64_t *lev_first_dev,
                          int *far_full, int *cls_cnt, int *cls_cells, int64_t cls_cap,
-                         cudaStream_t s) {
+                         const int *pmap, cudaStream_t s) {
   if (cap <= 0) return cudaSuccess;
   k_lists<<<nblk(cap * 32, 256), 256, 0, s>>>(g, d_sten, lo_level, l_min, map, cell_cls, cell_crd,
                                           cell_hsrc, far_cnt, far_src, far_op, near_cnt, near_src,
-                                          lev_first_dev, far_full, cls_cnt, cls_cells, cls_cap);
+                                          lev_first_dev, far_full, cls_cnt, cls_cells, cls_cap, pmap);
   return cudaGetLastError();
 }
 
