@@ -233,6 +233,29 @@ fmm2d_status fmm2d_evaluate(fmm2d_plan *plan, const void *strengths_dev, double 
                             void *stream);
 
 /*
+ * fmm2d_evaluate_graph - fmm2d_evaluate (Sec. 2) through a CUDA graph, for
+ * callers that evaluate many strength vectors on one geometry.  The first
+ * call after a build, or with other strength / potential pointers, records
+ * the evaluation's launches (on both of the plan's streams) into a graph and
+ * instantiates it; every call then launches that graph on `stream`, one
+ * launch instead of about twenty.  The graph reads the strengths from, and
+ * writes the potentials to, the recorded addresses: change the values in
+ * those buffers between calls, not the pointers (new pointers re-record).
+ * Results are those of fmm2d_evaluate, bit for bit.
+ *   strengths_dev, potentials_dev: as fmm2d_evaluate (device, caller-owned,
+ *     kept valid while the graph may be replayed).
+ *   stream: a created stream; the legacy default stream (NULL), or a plan
+ *     with profiling on, gets a plain fmm2d_evaluate instead.
+ * Any fmm2d_build / fmm2d_build_forest invalidates the graph (the next call
+ * re-records).  The plan owns the graph (freed by fmm2d_plan_destroy).
+ * Asynchronous on `stream`.  Must not be called while `stream` is being
+ * captured by the caller.  Errors: as fmm2d_evaluate; FMM2D_ECUDA when the
+ * recording or the instantiation fails.
+ */
+fmm2d_status fmm2d_evaluate_graph(fmm2d_plan *plan, const void *strengths_dev,
+                                  double *potentials_dev, void *stream);
+
+/*
  * fmm2d_evaluate_field - fmm2d_evaluate, and also the field
  *     F_j = sum_{i : x_i != y_j} u_i / (y_j - x_i),
  * the derivative of the complex potential of eq. 1 (Sec. 2).  Unlike the

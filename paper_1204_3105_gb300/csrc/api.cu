@@ -1181,6 +1181,7 @@ static fmm2d_status build_adaptive(fmm2d_plan *pl, const void *src, int64_t n_sr
   CK(cudaGetLastError(), "build");
   pl->n_m2l = -1;
   pl->n_p2p_pairs = -1;
+  ++pl->build_gen;
   pl->built = true;
   return FMM2D_OK;
 }
@@ -1747,6 +1748,7 @@ fmm2d_status fmm2d_build(fmm2d_plan *pl, const void *src, int64_t n_src, const v
   CK(cudaGetLastError(), "build");
   pl->n_m2l = -1;
   pl->n_p2p_pairs = -1;
+  ++pl->build_gen;
   pl->built = true;
   return FMM2D_OK;
 }
@@ -1771,6 +1773,15 @@ fmm2d_status fmm2d_build_forest(fmm2d_plan *pl, const void *xy, const int64_t *o
   return build_adaptive(pl, xy, n, xy, n, s, n_inst, offsets);
 }
 
+static fmm2d_status evaluate_dispatch(fmm2d_plan *pl, const void *u, double *out, cudaStream_t s) {
+  if (pl->flags & FMM2D_ADAPTIVE) {
+    if (is_fp64(pl)) return evaluate_adaptive_t<double>(pl, u, out, s);
+    return evaluate_adaptive_t<float>(pl, u, out, s);
+  }
+  if (is_fp64(pl)) return evaluate_t<double>(pl, u, out, s);
+  return evaluate_t<float>(pl, u, out, s);
+}
+
 fmm2d_status fmm2d_evaluate(fmm2d_plan *pl, const void *u, double *out, void *stream) {
   if (!pl) return FMM2D_EINVAL;
   if (!pl->built) return fail(pl, FMM2D_ENOTREADY, "plan is not built");
@@ -1778,12 +1789,57 @@ fmm2d_status fmm2d_evaluate(fmm2d_plan *pl, const void *u, double *out, void *st
   cudaStream_t s = (cudaStream_t)stream;
   pl->last_stream = s;
   if (pl->n_tgt == 0) return FMM2D_OK;
-  if (pl->flags & FMM2D_ADAPTIVE) {
-    if (is_fp64(pl)) return evaluate_adaptive_t<double>(pl, u, out, s);
-    return evaluate_adaptive_t<float>(pl, u, out, s);
+  return evaluate_dispatch(pl, u, out, s);
+}
+
+// The evaluation's launches (both streams, memsets included) recorded once
+// into a CUDA graph and then replayed with one launch per call, while the
+// build and the strength / potential pointers stay the same.  An evaluation
+// makes no allocation and no host synchronisation, so it records whole.
+fmm2d_status fmm2d_evaluate_graph(fmm2d_plan *pl, const void *u, double *out, void *stream) {
+  if (!pl) return FMM2D_EINVAL;
+  if (!pl->built) return fail(pl, FMM2D_ENOTREADY, "plan is not built");
+  if ((pl->n_src > 0 && !u) || (pl->n_tgt > 0 && !out)) return fail(pl, FMM2D_EINVAL, "null pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  // the legacy default stream cannot be captured, and profiling records
+  // events per stage: both evaluate directly
+  if (pl->profiling || s == nullptr || s == cudaStreamLegacy) return fmm2d_evaluate(pl, u, out, stream);
+  pl->last_stream = s;
+  if (pl->n_tgt == 0) return FMM2D_OK;
+  const bool valid = pl->graph_exec && pl->graph_gen == pl->build_gen && pl->graph_u == u &&
+                     pl->graph_out == out;
+  if (!valid) {
+    if (pl->graph_exec) {
+      cudaGraphExecDestroy(pl->graph_exec);
+      pl->graph_exec = nullptr;
+    }
+    cudaStream_t f;
+    CK(far_stream(pl, &f), "far stream");   // created before, not during, the capture
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
+    const fmm2d_status st = evaluate_dispatch(pl, u, out, s);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(s, &g);
+    if (st != FMM2D_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (ec != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(pl, ec, "end capture");
+    }
+    // node priorities kept: the far-field chain stays ahead of P2P, as on its stream
+    const cudaError_t ei = cudaGraphInstantiate(&pl->graph_exec, g, cudaGraphInstantiateFlagUseNodePriority);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      pl->graph_exec = nullptr;
+      return cuda_fail(pl, ei, "graph instantiate");
+    }
+    pl->graph_gen = pl->build_gen;
+    pl->graph_u = u;
+    pl->graph_out = out;
   }
-  if (is_fp64(pl)) return evaluate_t<double>(pl, u, out, s);
-  return evaluate_t<float>(pl, u, out, s);
+  CK(cudaGraphLaunch(pl->graph_exec, s), "graph launch");
+  return FMM2D_OK;
 }
 
 fmm2d_status fmm2d_plan_query(const fmm2d_plan *cpl, fmm2d_info *info) {
@@ -2100,6 +2156,7 @@ void fmm2d_plan_destroy(fmm2d_plan *pl) {
   }
   if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
   if (pl->ev_join) cudaEventDestroy(pl->ev_join);
+  if (pl->graph_exec) cudaGraphExecDestroy(pl->graph_exec);
   delete pl;
 }
 

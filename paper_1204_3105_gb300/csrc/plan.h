@@ -124,6 +124,12 @@ struct Plan {
   // while P2P runs on the caller's stream; two events fork and join them
   cudaStream_t far_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // fmm2d_evaluate_graph: the recorded evaluation, valid for one build
+  // (build_gen counts the builds) and one pair of strength / potential pointers
+  uint64_t build_gen = 0, graph_gen = 0;
+  cudaGraphExec_t graph_exec = nullptr;
+  const void *graph_u = nullptr;
+  double *graph_out = nullptr;
   // parameters the cached geometry / operator tables were built for
   bool geo_valid = false;
   int geo_key_L = -1, geo_key_p = -1;

@@ -39,7 +39,7 @@ SYMBOLS = ["fmm2d_default_params", "fmm2d_plan_create", "fmm2d_plan_set_domain",
            "fmm2d_plan_set_params", "fmm2d_serve_create", "fmm2d_serve_submit", "fmm2d_serve_poll",
            "fmm2d_serve_wait", "fmm2d_serve_stats", "fmm2d_serve_destroy",
            "fmm2d_plan_set_leaf_size", "fmm2d_build_forest", "fmm2d_evaluate_field",
-           "fmm2d_plan_set_debug_stall"]
+           "fmm2d_plan_set_debug_stall", "fmm2d_evaluate_graph"]
 
 
 class Info(ctypes.Structure):
@@ -101,6 +101,7 @@ def lib():
     L.fmm2d_plan_set_domain.argtypes = [vp, dbl, dbl, dbl]
     L.fmm2d_build.argtypes = [vp, vp, i64, vp, i64, vp]
     L.fmm2d_evaluate.argtypes = [vp, vp, vp, vp]
+    L.fmm2d_evaluate_graph.argtypes = [vp, vp, vp, vp]
     L.fmm2d_evaluate_field.argtypes = [vp, vp, vp, vp, vp]
     L.fmm2d_plan_query.argtypes = [vp, ctypes.POINTER(Info)]
     L.fmm2d_debug_export.argtypes = [vp, c_int, c_int, vp, ctypes.c_size_t,
@@ -249,6 +250,13 @@ class Plan:
                                             _stream(stream)), "evaluate")
 
     evaluate = fmm2d_evaluate
+
+    def fmm2d_evaluate_graph(self, strengths, potentials, stream=None):
+        """fmm2d_evaluate replayed from a recorded CUDA graph (same pointers)."""
+        self._check(self.lib.fmm2d_evaluate_graph(self._h, _ptr(strengths), _ptr(potentials),
+                                                  _stream(stream)), "evaluate_graph")
+
+    evaluate_graph = fmm2d_evaluate_graph
 
     def fmm2d_evaluate_field(self, strengths, potentials, field, stream=None):
         """field: 2 * n_tgt float64 device values (Re F, Im F) per target."""
